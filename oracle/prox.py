@@ -1,0 +1,229 @@
+"""Local step of PD and its differential, FP64 (Sec. 4.1, Sec. 4.3).
+
+* Rotation-variant SVD: F = U diag(s) V^T with det U = det V = +1; only the
+  smallest singular value may be negative (inverted element).
+* Corotated local step (Sec. 4.1): p* = R = U V^T, the rotation of the polar
+  decomposition.
+* Neo-Hookean proximal map (eq. nh_prox, nh_prox_normal): in stretch space,
+  sigma* = argmin_{sigma>0} k_bar/2 ||sigma - sigma_F||^2 + psi_bar(sigma) with
+  the mesh-mean material (mu_bar, lambda_bar); p* = U diag(sigma*) V^T.
+  Reading of eq. nh_hessian_stretch: its sigma^-4 is taken as a typo; the
+  stretch Hessian is derived from eq. neohookean,
+    d psi/d s_i      = mu (s_i - 1/s_i) + lam ln J / s_i
+    d2 psi/d s_i^2   = mu (1 + 1/s_i^2) + lam (1 - ln J) / s_i^2
+    d2 psi/d s_i s_j = lam / (s_i s_j)            (i != j).
+  The prox is per unit volume (no V_e), matching eq. nh_prox_normal and Alg. 1.
+* Differential of the isotropic spectral map p(F) = U diag(f(s)) V^T (the
+  "SVD differential" the paper names for eq. tr_ift), with the trust-region
+  blend of eq. tr_blend applied to H_prox = H_psi + k_bar I before inversion.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+# ---------------------------------------------------------------- SVD / polar
+
+def svd_rv(F: np.ndarray):
+    """Rotation-variant SVD of [n,3,3] -> (U [n,3,3], s [n,3], V [n,3,3])."""
+    U, s, Vt = np.linalg.svd(F)
+    V = np.transpose(Vt, (0, 2, 1)).copy()
+    U = U.copy()
+    s = s.copy()
+    du = np.linalg.det(U) < 0
+    U[du, :, 2] *= -1.0
+    s[du, 2] *= -1.0
+    dv = np.linalg.det(V) < 0
+    V[dv, :, 2] *= -1.0
+    s[dv, 2] *= -1.0
+    return U, s, V
+
+
+def compose(U, s, V):
+    return np.einsum("nij,nj,nkj->nik", U, s, V)
+
+
+def corotated_project(F: np.ndarray) -> np.ndarray:
+    U, _, V = svd_rv(F)
+    return np.einsum("nij,nkj->nik", U, V)
+
+
+# ---------------------------------------------------------- Neo-Hookean energy
+
+def nh_psi_F(F: np.ndarray, mu, lam) -> np.ndarray:
+    """eq. neohookean per element; +inf where J <= 0."""
+    J = np.linalg.det(F)
+    out = np.full(F.shape[0], np.inf)
+    ok = J > 0
+    lnJ = np.log(J[ok])
+    mu = np.broadcast_to(mu, J.shape)[ok]
+    lam = np.broadcast_to(lam, J.shape)[ok]
+    out[ok] = 0.5 * mu * (np.einsum("nij,nij->n", F[ok], F[ok]) - 3.0) - mu * lnJ + 0.5 * lam * lnJ ** 2
+    return out
+
+
+def nh_psi_sigma(s, mu, lam):
+    lnJ = np.log(np.prod(s, axis=-1))
+    return 0.5 * mu * (np.sum(s * s, axis=-1) - 3.0) - mu * lnJ + 0.5 * lam * lnJ ** 2
+
+
+def nh_grad_sigma(s, mu, lam):
+    lnJ = np.log(np.prod(s, axis=-1))[..., None]
+    return mu * (s - 1.0 / s) + lam * lnJ / s
+
+
+def nh_hess_sigma(s, mu, lam):
+    lnJ = np.log(np.prod(s, axis=-1))
+    inv = 1.0 / s
+    H = lam * inv[..., :, None] * inv[..., None, :]
+    d = mu * (1.0 + inv ** 2) + lam * (1.0 - lnJ[..., None]) * inv ** 2
+    idx = np.arange(3)
+    H[..., idx, idx] = d
+    return H
+
+
+def nh_prox_sigma(sF: np.ndarray, mu: float, lam: float, k: float, tol: float = 1e-14,
+                  max_iter: int = 60):
+    """Newton on f(s) = k/2||s - sF||^2 + psi_bar(s), s > 0 (eq. nh_prox_normal).
+
+    Start s0 = max(sF, 0.1); Newton direction if it is a descent direction of a
+    positive-definite model, else the scaled gradient -g/k; step halved until
+    s stays positive and either Armijo (c = 1e-4) holds or, for a Newton
+    step, the gradient max-norm halves. Stops at ||g||_inf <= tol*k.
+    Returns (sigma*, iterations used per element).
+    """
+    s = np.maximum(sF, 0.1).astype(np.float64)
+    n = s.shape[0]
+    active = np.ones(n, dtype=bool)
+    iters = np.zeros(n, dtype=np.int64)
+
+    def f(x, ref):
+        return 0.5 * k * np.sum((x - ref) ** 2, axis=-1) + nh_psi_sigma(x, mu, lam)
+
+    for _ in range(max_iter):
+        g = k * (s - sF) + nh_grad_sigma(s, mu, lam)
+        active &= ~(np.abs(g).max(axis=1) <= tol * k)
+        if not active.any():
+            break
+        a = np.nonzero(active)[0]
+        sa, ga, ra = s[a], g[a], sF[a]
+        H = k * np.eye(3) + nh_hess_sigma(sa, mu, lam)
+        pd = np.all(np.linalg.eigvalsh(H) > 0, axis=1)
+        d = -np.linalg.solve(H, ga[..., None])[..., 0]
+        bad = (~pd) | (np.einsum("ni,ni->n", d, ga) >= 0)
+        d[bad] = -ga[bad] / k
+        slope = np.einsum("ni,ni->n", d, ga)
+        t = np.ones(a.shape[0])
+        for _h in range(80):          # positivity
+            neg = np.any(sa + t[:, None] * d <= 0, axis=1)
+            if not neg.any():
+                break
+            t[neg] *= 0.5
+        f0 = f(sa, ra)
+        done = np.zeros(a.shape[0], dtype=bool)
+        for _h in range(60):          # Armijo
+            trial = sa + t[:, None] * d
+            # sufficient decrease of f, or (Newton steps only) a halving of the
+            # gradient's max-norm: in the quadratic-convergence regime the
+            # decrease of f falls below its rounding and Armijo cannot see it
+            gt = k * (trial - ra) + nh_grad_sigma(trial, mu, lam)
+            ok = (f(trial, ra) <= f0 + 1e-4 * t * slope) | (
+                (~bad) & (np.abs(gt).max(axis=1) <= 0.5 * np.abs(ga).max(axis=1)))
+            done |= ok
+            if done.all():
+                break
+            t[~done] *= 0.5
+        stalled = ~done                # no decrease representable: converged to rounding
+        s[a] = np.where(done[:, None], sa + t[:, None] * d, sa)
+        iters[a] += 1
+        active[a[stalled]] = False
+    return s, iters
+
+
+def nh_project(F: np.ndarray, mu_bar: float, lam_bar: float, k_bar: float):
+    """p* for every element, with the SVD pieces needed by the differential."""
+    U, sF, V = svd_rv(F)
+    ss, _ = nh_prox_sigma(sF, mu_bar, lam_bar, k_bar)
+    return compose(U, ss, V), (U, sF, V, ss)
+
+
+# ------------------------------------------------------- trust-region filter
+
+def tr_blend(H: np.ndarray, tau: float) -> np.ndarray:
+    """eq. tr_blend: (1 - tau) H + tau |H|, |H| = Q |Lambda| Q^T, per 3x3 block."""
+    lam, Q = np.linalg.eigh(H)
+    lt = (1.0 - tau) * lam + tau * np.abs(lam)
+    return np.einsum("nij,nj,nkj->nik", Q, lt, Q)
+
+
+def filtered_sigma_jacobian(ss: np.ndarray, mu: float, lam: float, k: float, tau: float):
+    """d sigma*/d sigma_F = k H~(tau)^+ (eq. tr_ift) with H = H_psi(sigma*) + k I.
+
+    Eigen-directions of H~ with eigenvalue <= 1e-12 k get zero response (the
+    pseudo-inverse: clamping a negative eigenvalue makes H~ singular).
+    Also returns the unfiltered k H^-1 and the count of indefinite H.
+    """
+    H = k * np.eye(3) + nh_hess_sigma(ss, mu, lam)
+    lamH, Q = np.linalg.eigh(H)
+    lt = (1.0 - tau) * lamH + tau * np.abs(lamH)
+    inv = np.where(lt > 1e-12 * k, 1.0 / np.where(lt > 1e-12 * k, lt, 1.0), 0.0)
+    Jf = k * np.einsum("nij,nj,nkj->nik", Q, inv, Q)
+    Jraw = k * np.linalg.inv(H)
+    n_indef = int(np.sum(lamH.min(axis=1) < 0))
+    return Jf, Jraw, n_indef
+
+
+# ------------------------------------------------------ spectral differential
+
+def _pair_coeffs(sF, ss, Jraw, corot: bool):
+    """s_ij and t_ij for the three pairs (0,1), (0,2), (1,2)."""
+    pairs = [(0, 1), (0, 2), (1, 2)]
+    S = np.zeros((sF.shape[0], 3))
+    T = np.zeros((sF.shape[0], 3))
+    for c, (i, j) in enumerate(pairs):
+        di = sF[:, i] - sF[:, j]
+        sm = sF[:, i] + sF[:, j]
+        if corot:
+            S[:, c] = 0.0
+        else:
+            close = np.abs(di) <= 1e-8 * np.maximum(1.0, np.abs(sF[:, i]))
+            ratio = (ss[:, i] - ss[:, j]) / np.where(close, 1.0, di)
+            lim = Jraw[:, i, i] - Jraw[:, i, j]
+            S[:, c] = np.where(close, lim, ratio)
+        T[:, c] = (ss[:, i] + ss[:, j]) / np.where(np.abs(sm) > 1e-30, sm, 1e-30)
+    return pairs, S, T
+
+
+def spectral_differential(U, sF, V, ss, Jdiag, Jraw, dF, corot: bool):
+    """dp for perturbations dF [n,3,3] of p = U diag(f(s)) V^T.
+
+    With Mh = U^T dF V: diag(dp_hat) = Jdiag @ diag(Mh); for each pair i<j
+      dp_hat_ij = s_ij (Mh_ij + Mh_ji)/2 + t_ij (Mh_ij - Mh_ji)/2
+      dp_hat_ji = s_ij (Mh_ij + Mh_ji)/2 - t_ij (Mh_ij - Mh_ji)/2
+    with s_ij = (f_i - f_j)/(s_i - s_j) (limit J_ii - J_ij at s_i = s_j) and
+    t_ij = (f_i + f_j)/(s_i + s_j); dp = U dp_hat V^T. Corotated: f = 1.
+    """
+    Mh = np.einsum("nki,nkl,nlj->nij", U, dF, V)
+    dph = np.zeros_like(Mh)
+    if not corot:
+        d = np.einsum("nij,nj->ni", Jdiag, np.diagonal(Mh, axis1=1, axis2=2))
+        for i in range(3):
+            dph[:, i, i] = d[:, i]
+    pairs, S, T = _pair_coeffs(sF, ss, Jraw, corot)
+    for c, (i, j) in enumerate(pairs):
+        sym = 0.5 * (Mh[:, i, j] + Mh[:, j, i])
+        skw = 0.5 * (Mh[:, i, j] - Mh[:, j, i])
+        dph[:, i, j] = S[:, c] * sym + T[:, c] * skw
+        dph[:, j, i] = S[:, c] * sym - T[:, c] * skw
+    return np.einsum("nij,njk,nlk->nil", U, dph, V)
+
+
+def dp_dF_matrix(U, sF, V, ss, Jdiag, Jraw, corot: bool) -> np.ndarray:
+    """Explicit 9x9 dp/dF per element (row-major vec, index 3i+j)."""
+    n = U.shape[0]
+    D = np.zeros((n, 9, 9))
+    for c in range(9):
+        dF = np.zeros((n, 3, 3))
+        dF[:, c // 3, c % 3] = 1.0
+        D[:, :, c] = spectral_differential(U, sF, V, ss, Jdiag, Jraw, dF, corot).reshape(n, 9)
+    return D

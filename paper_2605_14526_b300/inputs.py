@@ -1,0 +1,275 @@
+"""Seeded synthetic workloads for the heterogeneous tetrahedral PD solver.
+
+This module only builds INPUTS: rest positions, tetrahedra, Young's moduli,
+pins, external forces, time-step settings and loss targets. It holds none of
+the method's arithmetic (no masses, no shape-function gradients, no weights,
+no projections); the CPU oracle and the CUDA library each derive those from
+these arrays on their own.
+
+The paper's scenes (Armadillo, Crab, Bouncing Ball, ...) are not available,
+so the workloads below are hex grids split into five tetrahedra per cell, with
+the sizes, stiffness contrasts and solver settings of the benchmark
+configurations (small homogeneous corotated cube; 100x heterogeneous
+Neo-Hookean bar; batched uneven meshes; large heterogeneous block).
+Every random choice draws from ``numpy.random.default_rng(seed)``.
+"""
+from __future__ import annotations
+
+import dataclasses
+from dataclasses import dataclass, field
+
+import numpy as np
+
+COROTATED = "corotated"
+NEOHOOKEAN = "neohookean"
+
+TR_ADAPT, TR_NONE, TR_CLAMP, TR_ABS = 0, 1, 2, 3
+
+
+@dataclass
+class SolverSettings:
+    """Forward/backward iteration settings (Sec. 4.3 dual gate, Alg. 1).
+
+    ``aa_m`` is the Anderson window (number of difference columns, 0 = off);
+    ``fixed_iters`` > 0 runs exactly that many local-global iterations and
+    ignores the gate; ``local_fp32`` selects the FP32 local step.
+    """
+    aa_m: int = 5
+    fixed_iters: int = 0
+    k_max: int = 200
+    eps_step: float = 1e-8
+    eps_res: float = 1e-6
+    eps_abs: float = 1e-12
+    eps_tr: float = 0.1
+    tr_mode: int = TR_ADAPT
+    local_fp32: bool = True
+    adj_tol: float = 1e-10
+    adj_max_iters: int = 500
+
+
+@dataclass
+class Scene:
+    name: str
+    X: np.ndarray            # [n_v,3] float64 rest positions (m)
+    tets: np.ndarray         # [n_e,4] int32, positively oriented
+    pinned: np.ndarray       # [n_v] uint8, 1 = Dirichlet vertex held at X
+    E: np.ndarray            # [n_e] float64 Young's modulus (Pa)
+    nu: float
+    density: float           # kg/m^3
+    alpha: float             # Rayleigh mass coefficient (1/s)
+    beta0: float             # Rayleigh stiffness coefficient scale
+    gravity: np.ndarray      # [3] m/s^2, applied as a body acceleration
+    dt: float
+    model: str
+    steps: int
+    f_ext: np.ndarray        # [steps or 1, n_v, 3] float64 extra nodal forces (N)
+    x0: np.ndarray           # [n_v,3]
+    v0: np.ndarray           # [n_v,3]
+    solver: SolverSettings = field(default_factory=SolverSettings)
+    loss: str = "l2_target"  # "com_z" or "l2_target"
+    target: np.ndarray | None = None
+
+    @property
+    def n_v(self) -> int:
+        return int(self.X.shape[0])
+
+    @property
+    def n_e(self) -> int:
+        return int(self.tets.shape[0])
+
+    def with_steps(self, steps: int) -> "Scene":
+        f = self.f_ext if self.f_ext.shape[0] == 1 else self.f_ext[:steps]
+        return dataclasses.replace(self, steps=steps, f_ext=f)
+
+    def replace(self, **kw) -> "Scene":
+        return dataclasses.replace(self, **kw)
+
+
+# --------------------------------------------------------------------------
+# hex grid -> tetrahedra
+
+
+def _corner_tets(parity: int):
+    """Five-tet split of a unit cell; corners indexed by bits (x | y<<1 | z<<2).
+
+    The two parities mirror each other so that face diagonals of neighbouring
+    cells agree when the parity alternates with (i + j + k) mod 2.
+    """
+    if parity == 0:
+        return [(0, 1, 2, 4), (3, 1, 2, 7), (5, 1, 4, 7), (6, 2, 4, 7), (1, 2, 4, 7)]
+    return [(1, 0, 3, 5), (2, 0, 3, 6), (4, 0, 5, 6), (7, 3, 5, 6), (0, 3, 5, 6)]
+
+
+def hex_grid(nx: int, ny: int, nz: int, cell: float, cell_mask: np.ndarray | None = None,
+             origin=(0.0, 0.0, 0.0)):
+    """Vertices and positively oriented tets of an nx*ny*nz cell grid.
+
+    ``cell_mask`` ([nx,ny,nz] bool) keeps a subset of cells; unused vertices
+    are dropped. Returns (X, tets, cell_of_tet[ijk]).
+    """
+    if cell_mask is None:
+        cell_mask = np.ones((nx, ny, nz), dtype=bool)
+
+    def vid(i, j, k):
+        return i + (nx + 1) * (j + (ny + 1) * k)
+
+    gx, gy, gz = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), np.arange(nz + 1), indexing="ij")
+    X = np.zeros(((nx + 1) * (ny + 1) * (nz + 1), 3))
+    ids = vid(gx, gy, gz).ravel()
+    X[ids, 0] = origin[0] + gx.ravel() * cell
+    X[ids, 1] = origin[1] + gy.ravel() * cell
+    X[ids, 2] = origin[2] + gz.ravel() * cell
+
+    tets, cells = [], []
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                if not cell_mask[i, j, k]:
+                    continue
+                c = [vid(i + (b & 1), j + ((b >> 1) & 1), k + ((b >> 2) & 1)) for b in range(8)]
+                for t in _corner_tets((i + j + k) & 1):
+                    tets.append([c[t[0]], c[t[1]], c[t[2]], c[t[3]]])
+                    cells.append((i, j, k))
+    tets = np.asarray(tets, dtype=np.int64)
+    cells = np.asarray(cells, dtype=np.int64).reshape(-1, 3)
+
+    # orientation: make det[x1-x0, x2-x0, x3-x0] > 0 (swap last two if needed)
+    d = np.einsum("ij,ij->i", np.cross(X[tets[:, 1]] - X[tets[:, 0]], X[tets[:, 2]] - X[tets[:, 0]]),
+                  X[tets[:, 3]] - X[tets[:, 0]])
+    neg = d < 0
+    tets[neg, 2], tets[neg, 3] = tets[neg, 3].copy(), tets[neg, 2].copy()
+
+    used = np.zeros(X.shape[0], dtype=bool)
+    used[tets.ravel()] = True
+    remap = -np.ones(X.shape[0], dtype=np.int64)
+    remap[used] = np.arange(int(used.sum()))
+    return X[used].copy(), remap[tets].astype(np.int32), cells
+
+
+def _block_pick(rng, nb: int, n_soft: int):
+    soft = np.zeros(nb, dtype=bool)
+    soft[rng.choice(nb, size=n_soft, replace=False)] = True
+    return soft
+
+
+# --------------------------------------------------------------------------
+# workloads
+
+
+def small_cube(n: int = 4, cell: float = 0.1, steps: int = 10) -> Scene:
+    """Plain PD cube: n^3 cells, homogeneous corotated E=1e5, nu=0.3, z=0 face
+    pinned, gravity, dt=0.01 s, 20 fixed local-global iterations, FP64."""
+    X, tets, _ = hex_grid(n, n, n, cell)
+    pinned = (np.abs(X[:, 2]) < 1e-12).astype(np.uint8)
+    n_v, n_e = X.shape[0], tets.shape[0]
+    return Scene(
+        name=f"cube{n}", X=X, tets=tets, pinned=pinned, E=np.full(n_e, 1e5), nu=0.3,
+        density=1000.0, alpha=0.0, beta0=0.0, gravity=np.array([0.0, 0.0, -9.81]), dt=0.01,
+        model=COROTATED, steps=steps, f_ext=np.zeros((1, n_v, 3)), x0=X.copy(), v0=np.zeros((n_v, 3)),
+        solver=SolverSettings(aa_m=0, fixed_iters=20, local_fp32=False), loss="com_z", target=None)
+
+
+def twist_velocity(X: np.ndarray, pinned: np.ndarray, omega0: float) -> np.ndarray:
+    """Initial velocity of a twist about the bar's long (x) axis through its
+    centre line, with angular rate growing linearly from 0 at x=min to omega0
+    at x=max; pinned vertices stay at rest."""
+    x = X[:, 0]
+    L = max(float(x.max() - x.min()), 1e-30)
+    c = X.mean(axis=0)
+    om = omega0 * (x - x.min()) / L
+    v = np.zeros_like(X)
+    v[:, 1] = -om * (X[:, 2] - c[2])
+    v[:, 2] = om * (X[:, 1] - c[1])
+    return v * (1 - pinned[:, None])
+
+
+def hetero_bar(nx: int = 32, ny: int = 8, nz: int = 8, block: int = 8, cell: float = 0.1,
+               steps: int = 200, seed: int = 2, n_soft: int | None = None, omega0: float = 2.0) -> Scene:
+    """Heterogeneous Neo-Hookean bar: block^3 cell blocks, half of them soft
+    (E=1e4 Pa, seeded choice) and the rest stiff (E=1e6 Pa), nu=0.45, Rayleigh
+    alpha=0.01, beta0=1e-3, x=0 face pinned, driven by an initial twist
+    (omega0 rad/s at the free end, no gravity: a 1e4 Pa block cannot carry the
+    bar's own weight at any cell size where PD meets the gate below),
+    dt=0.005 s, Anderson m=5, dual gate (b-change 1e-6, q-step 1e-8), FP32 local
+    step. Loss: 0.5 ||x_T - x*||^2 against a seeded target x* = X + N(0, (0.2 cell)^2)."""
+    rng = np.random.default_rng(seed)
+    X, tets, cells = hex_grid(nx, ny, nz, cell)
+    bx, by, bz = max(nx // block, 1), max(ny // block, 1), max(nz // block, 1)
+    nb = bx * by * bz
+    soft = _block_pick(rng, nb, nb // 2 if n_soft is None else n_soft)
+    bid = (np.minimum(cells[:, 0] // block, bx - 1)
+           + bx * (np.minimum(cells[:, 1] // block, by - 1) + by * np.minimum(cells[:, 2] // block, bz - 1)))
+    E = np.where(soft[bid], 1e4, 1e6)
+    pinned = (np.abs(X[:, 0]) < 1e-12).astype(np.uint8)
+    n_v = X.shape[0]
+    target = X + 0.2 * cell * rng.standard_normal(X.shape)
+    return Scene(
+        name=f"bar{nx}x{ny}x{nz}", X=X, tets=tets, pinned=pinned, E=E, nu=0.45, density=1000.0,
+        alpha=0.01, beta0=1e-3, gravity=np.zeros(3), dt=0.005, model=NEOHOOKEAN,
+        steps=steps, f_ext=np.zeros((1, n_v, 3)), x0=X.copy(), v0=twist_velocity(X, pinned, omega0),
+        solver=SolverSettings(aa_m=5, fixed_iters=0, k_max=200, eps_step=1e-8, eps_res=1e-6,
+                              eps_abs=1e-12, local_fp32=True),
+        loss="l2_target", target=target)
+
+
+def tiny_block(n: int = 2, cell: float = 0.01, model: str = NEOHOOKEAN, seed: int = 7,
+               contrast: float = 10.0, steps: int = 2) -> Scene:
+    """n^3-cell block with a per-cell random stiffness in [1e5, contrast*1e5],
+    one face pinned, a seeded initial velocity and seeded nodal forces; used by
+    finite-difference gradient checks."""
+    rng = np.random.default_rng(seed)
+    X, tets, cells = hex_grid(n, n, n, cell)
+    cidx = cells[:, 0] + n * (cells[:, 1] + n * cells[:, 2])
+    Ec = 1e5 * np.exp(np.log(contrast) * rng.random(n ** 3))
+    E = Ec[cidx]
+    pinned = (np.abs(X[:, 0]) < 1e-12).astype(np.uint8)
+    n_v = X.shape[0]
+    v0 = 0.05 * rng.standard_normal((n_v, 3)) * (1 - pinned[:, None])
+    f_ext = 2e-3 * rng.standard_normal((steps, n_v, 3)) * (1 - pinned[None, :, None])
+    target = X + 0.2 * cell * rng.standard_normal(X.shape)
+    return Scene(
+        name=f"tiny{n}", X=X, tets=tets, pinned=pinned, E=E, nu=0.35, density=1000.0,
+        alpha=0.02, beta0=0.05, gravity=np.array([0.0, 0.0, -9.81]), dt=0.005, model=model,
+        steps=steps, f_ext=f_ext, x0=X.copy(), v0=v0,
+        solver=SolverSettings(aa_m=5, fixed_iters=0, k_max=400, eps_step=1e-14, eps_res=1e-14,
+                              eps_abs=1e-15, local_fp32=False),
+        loss="l2_target", target=target)
+
+
+def large_block(n: int = 64, cell: float = 0.1, block: int = 8, seed: int = 5, steps: int = 20) -> Scene:
+    """Large heterogeneous Neo-Hookean block (n^3 cells, 5 tets each), 8^3-cell
+    stiffness blocks (half soft 1e4 Pa / half stiff 1e6 Pa), bottom face
+    pinned, no gravity, seeded random top-face nodal loads (N(0, 5 N) per
+    axis) re-drawn every 20 steps."""
+    rng = np.random.default_rng(seed)
+    X, tets, cells = hex_grid(n, n, n, cell)
+    nbk = max(n // block, 1)
+    nb = nbk ** 3
+    soft = _block_pick(rng, nb, nb // 2)
+    bid = (np.minimum(cells[:, 0] // block, nbk - 1)
+           + nbk * (np.minimum(cells[:, 1] // block, nbk - 1) + nbk * np.minimum(cells[:, 2] // block, nbk - 1)))
+    E = np.where(soft[bid], 1e4, 1e6)
+    pinned = (np.abs(X[:, 2]) < 1e-12).astype(np.uint8)
+    n_v = X.shape[0]
+    top = np.abs(X[:, 2] - X[:, 2].max()) < 1e-12
+    n_phase = (steps + 19) // 20
+    f_ext = np.zeros((steps, n_v, 3))
+    for ph in range(n_phase):
+        load = np.zeros((n_v, 3))
+        load[top] = 5.0 * rng.standard_normal((int(top.sum()), 3))
+        f_ext[20 * ph: 20 * (ph + 1)] = load
+    return Scene(
+        name=f"block{n}", X=X, tets=tets, pinned=pinned, E=E, nu=0.45, density=1000.0,
+        alpha=0.01, beta0=1e-3, gravity=np.zeros(3), dt=0.005, model=NEOHOOKEAN,
+        steps=steps, f_ext=f_ext, x0=X.copy(), v0=np.zeros((n_v, 3)),
+        solver=SolverSettings(aa_m=5, k_max=200, eps_step=1e-8, eps_res=1e-6, eps_abs=1e-12, local_fp32=True),
+        loss="l2_target", target=X + 0.02 * rng.standard_normal(X.shape))
+
+
+def random_rotation(rng) -> np.ndarray:
+    """Uniform random rotation (QR of a Gaussian matrix with sign fix)."""
+    q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+    q = q * np.sign(np.diag(r))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
