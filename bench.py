@@ -1,0 +1,274 @@
+"""Benchmark: forward + backward PD steps/sec on the heterogeneous Neo-Hookean
+bar (32x8x8 hex cells -> 10,240 tets, 2,673 vertices, 100x stiffness contrast,
+200 implicit-Euler steps at dt = 5 ms, Anderson m = 5, dual gate 1e-6 / 1e-8,
+FP32 local step with FP64 accumulation, FP64 factor and solves), against the
+FP64 CPU oracle.
+
+One benchmark step = one full rollout of 200 PD steps forward followed by its
+adjoint (200 PD steps backward). value = PD steps (forward+backward) per
+second over all ranks. Synthetic seeded inputs; L2 is flushed between timed
+rollouts (the bar's working set fits in L2).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd PD steps/sec at <=1e-5 rel err vs FP64 oracle; local-step HBM GB/s vs peak"
+UNIT = "PD steps/s"
+WORKLOAD = "heterogeneous Neo-Hookean bar 32x8x8 cells (10,240 tets, 2,673 vertices), 200 steps fwd+bwd"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+REASONS = ["gpu_idle", "applications_clocks_setting", "sw_power_cap", "hw_slowdown", "sync_boost",
+           "sw_thermal_slowdown", "hw_thermal_slowdown", "hw_power_brake_slowdown", "display_clock_setting"]
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 3:
+                try:
+                    self.samples.append((float(parts[0]), float(parts[1]), int(parts[2], 16)))
+                except ValueError:
+                    pass
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [s[0] for s in self.samples]
+        mask = 0
+        for s in self.samples:
+            mask |= s[2]
+        reasons = [REASONS[i] for i in range(len(REASONS)) if mask >> i & 1 and REASONS[i] != "gpu_idle"]
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(s[1] for s in self.samples), "reasons": reasons,
+                "samples": len(sm)}
+
+
+def oracle_sample(scene, n_steps: int):
+    """The oracle as it stands (exact fixed point + direct adjoint) on the first
+    n_steps steps of the workload, single-threaded. Returns (seconds, steps)."""
+    from threadpoolctl import threadpool_limits
+    from oracle import adjoint, solver
+    sc = scene.with_steps(n_steps)
+    with threadpool_limits(1):
+        t0 = time.perf_counter()
+        pb = solver.build_problem(sc)
+        qT, vT, recs = solver.rollout(pb, sc, mode="exact")
+        _, dq, dv = adjoint.loss_and_grad(sc, pb, qT, vT)
+        adjoint.rollout_backward(pb, recs, dq, dv)
+        dt = time.perf_counter() - t0
+    return dt, n_steps
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle timed on the host on a bounded sample
+    (one PD step forward + backward per benchmark step)."""
+    if rank != 0:
+        return
+    from paper_2605_14526_b300 import inputs
+    scene = inputs.hetero_bar()
+    for _ in range(args.warmup):
+        oracle_sample(scene, 1)
+    tot = 0.0
+    n = 0
+    for _ in range(args.steps):
+        dt, k = oracle_sample(scene, 1)
+        tot += dt
+        n += k
+    value = n / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "first PD step of the rollout, forward + adjoint, per bench step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{n} PD steps (1 per bench step), numpy/scipy FP64, 1 thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    from paper_2605_14526_b300 import binding, inputs
+    from paper_2605_14526_b300.build import build
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build()
+    dev = torch.device("cuda", local_rank)
+    scene = inputs.hetero_bar(seed=2 + rank)
+    T = scene.steps
+    pd = binding.PDContext(scene)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    x0, v0, f0, target = t(scene.x0), t(scene.v0), t(scene.f_ext[0]), t(scene.target)
+    qT, vT = torch.empty_like(x0), torch.empty_like(x0)
+    dq0, dv0 = torch.empty_like(x0), torch.empty_like(x0)
+    dE = torch.empty(scene.n_e, dtype=torch.float64, device=dev)
+    dnu = torch.empty(1, dtype=torch.float64, device=dev)
+    zero = torch.zeros_like(x0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > 126 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    def fwd_bwd():
+        binding.pd_rollout(pd.ctx, T, x0, v0, f0, 0, qT, vT, stream)
+        binding.pd_backward(pd.ctx, qT - target, zero, dq0, dv0, dE, dnu, None, 0, stream)
+
+    for _ in range(args.warmup):
+        fwd_bwd()
+    torch.cuda.synchronize()
+    launches0 = binding.pd_get_stats(pd.ctx).launches
+    total_ms = 0.0
+    iters = adj = 0
+    with ClockSampler(local_rank) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fwd_bwd()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            st = binding.pd_get_stats(pd.ctx)
+            iters += st.iters_total
+            adj += st.adj_iters_total
+    launches = binding.pd_get_stats(pd.ctx).launches - launches0
+    tmax = total_ms
+    if dist:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tmax = float(tt[0])
+    value = world * T * args.steps / (tmax / 1e3)
+
+    # phase timers of the local step (live, CUDA events on the work stream)
+    binding.pd_profile(pd.ctx, True)
+    for _ in range(2):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        binding.pd_rollout(pd.ctx, T, x0, v0, f0, 0, qT, vT, stream)
+    prof = binding.pd_get_profile(pd.ctx)
+    binding.pd_profile(pd.ctx, False)
+    local_ms = prof.local_ms / max(prof.local_launches, 1)
+    solve_ms = prof.solve_ms / max(prof.solve_launches, 1)
+    # algorithmic bytes of one local step + RHS assembly: per tet 16 B indices +
+    # 36 B Dm^-1 + 4 B w_e V_e; per vertex 24 B q read + 24 B b written
+    local_bytes = 56 * scene.n_e + 48 * scene.n_v
+    peak, peak_kind = _peaks()
+    achieved = local_bytes / (local_ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers (copies inside the region)
+    hx0, hv0, hf0 = (np.ascontiguousarray(a) for a in (scene.x0, scene.v0, scene.f_ext[0]))
+    hq, hv = np.zeros_like(hx0), np.zeros_like(hx0)
+    hdq0, hdv0, hdE, hdnu = np.zeros_like(hx0), np.zeros_like(hx0), np.zeros(scene.n_e), np.zeros(1)
+    hz = np.zeros_like(hx0)
+    e2e_s = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        binding.pd_rollout(pd.ctx, T, hx0, hv0, hf0, 0, hq, hv, None)
+        g = np.ascontiguousarray(hq - scene.target)
+        binding.pd_backward(pd.ctx, g, hz, hdq0, hdv0, hdE, hdnu, None, 0, None)
+        e2e_s += time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt[0])
+    e2e = world * T * args.steps / e2e_s
+    nv3b = 3 * 8 * scene.n_v
+    h2d = 3 * nv3b + 2 * nv3b          # x0, v0, f_ext; dL/dq_T, dL/dv_T
+    d2h = 2 * nv3b + 2 * nv3b + 8 * scene.n_e + 8
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (FP32 local step, FP64 RHS/factor/solve)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pd_steps_per_bench_step": T, "l2": "flushed (256 MB write) between rollouts",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "mean_fwd_iters_per_pd_step": iters / (args.steps * T),
+                       "mean_adjoint_iters_per_pd_step": adj / (args.steps * T)},
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "local step + RHS assembly (k_local, k_assemble)",
+                         "peak_kind": peak_kind, "avg_launch_us": local_ms * 1e3, "bytes_per_launch": local_bytes,
+                         "solve_avg_launch_us": solve_ms * 1e3},
+            "clocks": clk.summary()}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, k = oracle_sample(scene, 2)
+        line["cpu_baseline"] = {"value": k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"first {k} PD steps of the same rollout, forward (exact fixed point) + adjoint, FP64, 1 thread"}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

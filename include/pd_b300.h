@@ -1,0 +1,202 @@
+/*
+ * pd_b300.h - C ABI of the B300-native differentiable heterogeneous
+ * Projective Dynamics hot path (arXiv 2605.14526, "DiffPhD").
+ *
+ * One context holds one tetrahedral mesh, its materials, the factored PD
+ * operator and the per-step checkpoints of the last rollout. All compute runs
+ * in the library's CUDA kernels on the device that is current when the
+ * context is created; host code in the library only validates inputs,
+ * assembles and factors the operator (once per material change, Sec. 4.5
+ * "refactorisation policy"), and orders launches.
+ *
+ * Conventions
+ *   - Vertex arrays are [n_v][3] row-major float64 (x, y, z per vertex).
+ *   - Pinned (Dirichlet) vertices are held at their rest position X; their
+ *     outputs are X (positions) / 0 (velocities) and their gradients are 0.
+ *   - "stream" is a cudaStream_t (NULL = legacy default stream). Work is
+ *     enqueued on it; calls that must read device results synchronise it.
+ *   - Every function returns a pd_status; PD_OK = 0. On error, pd_last_error
+ *     returns a message. Nothing aborts; device-side numeric problems are
+ *     recorded in a status word and reported by the next synchronising call.
+ *   - The library never frees memory it does not own.
+ */
+#ifndef PD_B300_H
+#define PD_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PD_OK = 0,
+  PD_ERR_ARG = 1,           /* bad size, index out of range, null pointer */
+  PD_ERR_MESH = 2,          /* a rest tetrahedron with det(Dm) <= 0 */
+  PD_ERR_NOT_FACTORED = 3,  /* pd_step/pd_rollout before pd_factor */
+  PD_ERR_NOT_SPD = 4,       /* non-positive pivot while factoring A */
+  PD_ERR_NOT_CONVERGED = 5, /* a step hit k_max (results are still written) */
+  PD_ERR_NUMERIC = 6,       /* NaN/Inf met in a kernel */
+  PD_ERR_TIMEOUT = 7,       /* a bounded device wait gave up */
+  PD_ERR_CUDA = 8,          /* a CUDA runtime call failed */
+  PD_ERR_OOM = 9,           /* device or host allocation failed */
+  PD_ERR_NO_CHECKPOINT = 10,/* pd_backward without a recorded rollout */
+  PD_ERR_TOO_LARGE = 11     /* a size exceeds a documented limit */
+} pd_status;
+
+enum { PD_COROTATED = 0, PD_NEOHOOKEAN = 1 };
+enum { PD_TR_ADAPT = 0, PD_TR_NONE = 1, PD_TR_CLAMP = 2, PD_TR_ABS = 3 };
+
+/* Mesh, copied by pd_create (host pointers). */
+typedef struct {
+  int32_t n_v, n_e;
+  const double* X;        /* [n_v][3] rest positions (m) */
+  const int32_t* tets;    /* [n_e][4] vertex indices, det[X1-X0,X2-X0,X3-X0] > 0 */
+  const uint8_t* pinned;  /* [n_v] 1 = Dirichlet vertex held at X; may be NULL */
+} pd_mesh;
+
+/* Material (Sec. 3.1 eq. lame; Sec. 4.4 eq. rayleigh), copied by pd_create. */
+typedef struct {
+  int32_t model;          /* PD_COROTATED | PD_NEOHOOKEAN */
+  const double* E;        /* [n_e] Young's modulus per element (Pa), > 0 */
+  double nu;              /* Poisson ratio shared by all elements, in (-1, 0.5) */
+  double density;         /* kg/m^3; lumped mass density*V_e/4 per corner */
+  double alpha;           /* Rayleigh mass-damping coefficient (1/s) */
+  double beta0;           /* stiffness damping scale: beta_e = beta0 mu_e / max mu */
+  double gravity[3];      /* body acceleration added to every vertex (m/s^2) */
+} pd_material;
+
+/* Solver options (Sec. 4.3 Anderson + dual gate; Sec. 4.3 trust region). */
+typedef struct {
+  int32_t aa_m;           /* Anderson window: difference columns (0 = off, <= 8) */
+  int32_t k_max;          /* iteration cap per step */
+  int32_t fixed_iters;    /* > 0: exactly this many local-global iterations, no gate */
+  int32_t local_fp32;     /* 1: FP32 local step with FP64 RHS accumulation; 0: FP64 */
+  int32_t tr_mode;        /* PD_TR_ADAPT | PD_TR_NONE | PD_TR_CLAMP | PD_TR_ABS */
+  int32_t adj_max_iters;  /* cap on backward PCG iterations per step */
+  double eps_step;        /* relative q-step gate */
+  double eps_res;         /* relative b-change gate */
+  double eps_abs;         /* absolute term of both gates */
+  double eps_tr;          /* trust-region ratio tolerance (0.1 in the paper) */
+  double adj_tol;         /* backward: relative preconditioned residual target */
+} pd_options;
+
+/* Statistics of the last pd_rollout / pd_backward (host copy). */
+typedef struct {
+  int32_t steps;            /* steps recorded by the last rollout */
+  int32_t iters_total;      /* local-global iterations summed over steps */
+  int32_t iters_max;        /* largest per-step iteration count */
+  int32_t aa_resets;        /* Anderson reliability-guard trips */
+  int32_t not_converged;    /* steps that hit k_max */
+  int32_t tau_half;         /* steps whose trust-region selection gave tau = 1/2 */
+  int32_t tau_one;          /* ... tau = 1 */
+  int32_t adj_iters_total;  /* backward PCG iterations summed over steps */
+  int32_t adj_iters_max;
+  int32_t adj_not_converged;
+  int32_t status_flags;     /* bit 0: NaN/Inf seen; bit 1: PCG breakdown */
+  int32_t n_free;           /* free vertices */
+  int64_t factor_nnz;       /* stored non-zeros of the inverse factor S */
+  double factor_seconds;    /* host time of the last pd_factor */
+  double last_rho;          /* trust-region ratio of the last step */
+  int64_t launches;         /* kernel launches issued by this context so far */
+} pd_stats;
+
+typedef struct pd_ctx pd_ctx;
+
+/* Default options (m = 5, k_max = 200, gate 1e-8 / 1e-6 / 1e-12, FP32 local,
+ * adaptive trust region with eps_tr = 0.1, backward 1e-9 / 1000 iterations). */
+void pd_default_options(pd_options* out);
+
+/* Create a context: validates the mesh (indices in range, positive rest
+ * volumes, no pinned-only mesh), copies mesh and materials, computes rest
+ * shape data (Dm^-1, V_e, lumped mass) and uploads the per-element arrays.
+ * Sec. 3.1 (eq. lame, dynamics, freefall). Host pointers; dt > 0.
+ * On failure *out may still hold a context whose pd_last_error explains the
+ * error; release it with pd_destroy. */
+int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_options* opt,
+              pd_ctx** out);
+
+/* Replace the Young's moduli ([n_e], host, Pa) and Poisson ratio; marks A stale
+ * so that the next pd_factor refactors (Sec. 4.5 refactorisation policy). */
+int pd_set_materials(pd_ctx* ctx, const double* E, double nu);
+
+/* Assemble and factor the PD operator
+ *   A = (1 + alpha h) M / h^2 + sum_e (w_e + beta_e/h) V_e G_e^T G_e   (Sec. 4.4 eq. A_damped)
+ * with w_e = 2 mu_e (corotated) or 2 mu_e + lambda_e (Neo-Hookean) (Sec. 4.1
+ * eq. pd_weight; Sec. 7.2), beta_e = beta0 mu_e / mu_ref, mu_ref = max mu_e
+ * frozen here. Pins are eliminated. The scalar operator (A = L_A (x) I_3) is
+ * reordered by geometric nested dissection, factored by a supernodal
+ * Cholesky in FP64 on the host, and its inverse factor S = L^-1 P
+ * (A^-1 = S^T S, Sec. 4.5 eq. Ainv_STS, two_spmv) is uploaded. Returns
+ * PD_ERR_NOT_SPD on a non-positive pivot, PD_ERR_TOO_LARGE if nnz(S) exceeds
+ * 2^31 - 1. Blocking. */
+int pd_factor(pd_ctx* ctx);
+
+/* T implicit-Euler PD steps from (q0, v0) (Alg. 1 per step): inertial target,
+ * fused local step + RHS scatter, global solve by two SpMVs with S,
+ * type-II Anderson acceleration (window aa_m) and the dual gate; at the end
+ * of each step the trust-region ratio picks tau* for the backward pass
+ * (Sec. 4.3 eq. tr_step .. tr_rule). Checkpoints q_t for t = 0..T are kept
+ * on the device for pd_backward.
+ *   q0, v0   [n_v][3]; f_ext [T][n_v][3] if f_ext_stride = n_v*3, or one
+ *            [n_v][3] array used at every step if f_ext_stride = 0 (N);
+ *   qT, vT   [n_v][3] outputs.
+ * Pointers may be device pointers (no copies) or host pointers (staged by
+ * the library with cudaMemcpyAsync on the stream). Synchronises the stream
+ * at the end and returns PD_ERR_NOT_CONVERGED if any step hit k_max. */
+int pd_rollout(pd_ctx* ctx, int32_t T, const double* q0, const double* v0, const double* f_ext,
+               int64_t f_ext_stride, double* qT, double* vT, void* stream);
+
+/* One step: pd_rollout with T = 1 (keeps the checkpoint of this step only). */
+int pd_step(pd_ctx* ctx, const double* q_t, const double* v_t, const double* f_ext, double* q_next,
+            double* v_next, void* stream);
+
+/* Adjoint of the last pd_rollout (Alg. 2 per step, walked from T-1 to 0).
+ * Per step: mu = (A - K)^-1 q_bar with K = db/dq (Sec. 4.7 eq. db_dq, the
+ * trust-region-filtered prox differential of eq. tr_blend / tr_ift, or the
+ * polar differential for corotated), solved by conjugate gradients
+ * preconditioned with the same factor (A^-1 = S^T S); then gradient routing
+ *   dL/dq_t = (1+alpha h) M/h^2 mu + B mu/h - v_bar/h,  dL/dv_t = M/h mu,
+ *   dL/df_ext = mu, dL/dw_e = V_e <G_e mu, p_e - G_e q*> (eq. dl_dwe),
+ *   dL/dbeta_e = -(V_e/h) <G_e mu, G_e (q* - q_t)>, plus the mesh-mean terms,
+ * chained to E_e and nu (eq. lame). Inputs dqT, dvT [n_v][3] (dvT may be
+ * NULL); outputs dq0, dv0 [n_v][3], dE [n_e], dnu [1], df_ext [T][n_v][3] if
+ * df_stride = n_v*3 or summed into one [n_v][3] if df_stride = 0 (may be
+ * NULL). Any output pointer may be NULL to skip it. Host or device pointers
+ * as in pd_rollout. Synchronises the stream. */
+int pd_backward(pd_ctx* ctx, const double* dqT, const double* dvT, double* dq0, double* dv0,
+                double* dE, double* dnu, double* df_ext, int64_t df_stride, void* stream);
+
+/* Lumped vertex masses [n_v] (host output, kg): density * V_e / 4 per corner. */
+int pd_get_mass(const pd_ctx* ctx, double* mass_host);
+
+/* Per-step trust-region choices of the last rollout: tau [T] (host output). */
+int pd_get_tau(const pd_ctx* ctx, double* tau_host, int32_t T);
+
+int pd_get_stats(const pd_ctx* ctx, pd_stats* out);
+const char* pd_last_error(const pd_ctx* ctx);
+void pd_destroy(pd_ctx* ctx);
+
+/* Phase timers measured with CUDA events on the work stream while profiling
+ * is enabled (pd_profile). "local" brackets the fused local step + RHS
+ * assembly of every forward iteration; "solve" brackets the two SpMVs with S
+ * of every forward iteration. */
+typedef struct {
+  int64_t local_launches;
+  double local_ms;
+  int64_t solve_launches;
+  double solve_ms;
+} pd_profile_out;
+
+/* enable != 0 turns the phase timers on (and clears them); 0 turns them off. */
+int pd_profile(pd_ctx* ctx, int32_t enable);
+int pd_get_profile(const pd_ctx* ctx, pd_profile_out* out);
+
+/* Library version string. */
+const char* pd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PD_B300_H */

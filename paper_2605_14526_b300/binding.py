@@ -1,0 +1,277 @@
+"""ctypes binding of libpd_b300.so (declared in include/pd_b300.h).
+
+Argument marshalling only: every function below forwards to the C entry point
+of the same name. Arrays may be torch tensors (CUDA or CPU) or numpy arrays;
+they must be contiguous float64 (int32 / uint8 for mesh indices / pins). The
+library must be built (``paper_2605_14526_b300.build.build()``); a missing
+library raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_int32, c_int64, c_uint8, c_void_p
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpd_b300.so")
+
+PD_OK = 0
+STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_MESH", 3: "PD_ERR_NOT_FACTORED", 4: "PD_ERR_NOT_SPD",
+          5: "PD_ERR_NOT_CONVERGED", 6: "PD_ERR_NUMERIC", 7: "PD_ERR_TIMEOUT", 8: "PD_ERR_CUDA",
+          9: "PD_ERR_OOM", 10: "PD_ERR_NO_CHECKPOINT", 11: "PD_ERR_TOO_LARGE"}
+PD_COROTATED, PD_NEOHOOKEAN = 0, 1
+PD_TR_ADAPT, PD_TR_NONE, PD_TR_CLAMP, PD_TR_ABS = 0, 1, 2, 3
+
+
+class pd_mesh(ctypes.Structure):
+    _fields_ = [("n_v", c_int32), ("n_e", c_int32), ("X", c_void_p), ("tets", c_void_p), ("pinned", c_void_p)]
+
+
+class pd_material(ctypes.Structure):
+    _fields_ = [("model", c_int32), ("E", c_void_p), ("nu", c_double), ("density", c_double),
+                ("alpha", c_double), ("beta0", c_double), ("gravity", c_double * 3)]
+
+
+class pd_options(ctypes.Structure):
+    _fields_ = [("aa_m", c_int32), ("k_max", c_int32), ("fixed_iters", c_int32), ("local_fp32", c_int32),
+                ("tr_mode", c_int32), ("adj_max_iters", c_int32), ("eps_step", c_double), ("eps_res", c_double),
+                ("eps_abs", c_double), ("eps_tr", c_double), ("adj_tol", c_double)]
+
+
+class pd_stats(ctypes.Structure):
+    _fields_ = [("steps", c_int32), ("iters_total", c_int32), ("iters_max", c_int32), ("aa_resets", c_int32),
+                ("not_converged", c_int32), ("tau_half", c_int32), ("tau_one", c_int32),
+                ("adj_iters_total", c_int32), ("adj_iters_max", c_int32), ("adj_not_converged", c_int32),
+                ("status_flags", c_int32), ("n_free", c_int32), ("factor_nnz", c_int64),
+                ("factor_seconds", c_double), ("last_rho", c_double), ("launches", c_int64)]
+
+
+class pd_profile_out(ctypes.Structure):
+    _fields_ = [("local_launches", c_int64), ("local_ms", c_double), ("solve_launches", c_int64),
+                ("solve_ms", c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the library (once). Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2605_14526_b300.build.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        P = c_void_p
+        sig = {
+            "pd_default_options": (None, [P]),
+            "pd_create": (c_int, [P, P, c_double, P, P]),
+            "pd_set_materials": (c_int, [P, P, c_double]),
+            "pd_factor": (c_int, [P]),
+            "pd_rollout": (c_int, [P, c_int32, P, P, P, c_int64, P, P, P]),
+            "pd_step": (c_int, [P, P, P, P, P, P, P]),
+            "pd_backward": (c_int, [P, P, P, P, P, P, P, P, c_int64, P]),
+            "pd_get_mass": (c_int, [P, P]),
+            "pd_get_tau": (c_int, [P, P, c_int32]),
+            "pd_get_stats": (c_int, [P, P]),
+            "pd_profile": (c_int, [P, c_int32]),
+            "pd_get_profile": (c_int, [P, P]),
+            "pd_last_error": (ctypes.c_char_p, [P]),
+            "pd_destroy": (None, [P]),
+            "pd_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class PDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(a, dtype=np.float64):
+    """Address of a contiguous array (torch tensor or numpy), or None."""
+    if a is None:
+        return None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            want = {np.float64: torch.float64, np.int32: torch.int32, np.uint8: torch.uint8}[dtype]
+            if a.dtype != want or not a.is_contiguous():
+                raise TypeError(f"tensor must be contiguous {want}")
+            return a.data_ptr()
+    except ImportError:
+        pass
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"array must be a C-contiguous {np.dtype(dtype).name} ndarray")
+    return a.ctypes.data
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(ctx, code):
+    if code != PD_OK:
+        msg = lib().pd_last_error(ctx).decode() if ctx else ""
+        raise PDError(code, msg)
+
+
+# ---------------------------------------------------------------- same names
+
+def pd_default_options() -> pd_options:
+    o = pd_options()
+    lib().pd_default_options(ctypes.byref(o))
+    return o
+
+
+def pd_create(X, tets, pinned, E, model, nu, density, alpha, beta0, gravity, dt, options: pd_options):
+    """Returns an opaque context handle; the host arrays are copied by the library."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    pin = None if pinned is None else np.ascontiguousarray(pinned, dtype=np.uint8)
+    mesh = pd_mesh(int(X.shape[0]), int(tets.shape[0]), _ptr(X), _ptr(tets, np.int32),
+                   None if pin is None else _ptr(pin, np.uint8))
+    mat = pd_material(int(model), _ptr(E), float(nu), float(density), float(alpha), float(beta0),
+                      (c_double * 3)(*[float(g) for g in gravity]))
+    out = c_void_p()
+    code = lib().pd_create(ctypes.byref(mesh), ctypes.byref(mat), float(dt), ctypes.byref(options), ctypes.byref(out))
+    if code != PD_OK:
+        msg = lib().pd_last_error(out).decode() if out.value else ""
+        if out.value:
+            lib().pd_destroy(out)
+        raise PDError(code, msg)
+    return out
+
+
+def pd_set_materials(ctx, E, nu):
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    _check(ctx, lib().pd_set_materials(ctx, _ptr(E), float(nu)))
+
+
+def pd_factor(ctx):
+    _check(ctx, lib().pd_factor(ctx))
+
+
+def pd_rollout(ctx, T, q0, v0, f_ext, f_stride, qT, vT, stream=None, check=True):
+    code = lib().pd_rollout(ctx, int(T), _ptr(q0), _ptr(v0), _ptr(f_ext), int(f_stride), _ptr(qT), _ptr(vT),
+                            _stream(stream))
+    if check:
+        _check(ctx, code)
+    return code
+
+
+def pd_step(ctx, q_t, v_t, f_ext, q_next, v_next, stream=None):
+    _check(ctx, lib().pd_step(ctx, _ptr(q_t), _ptr(v_t), _ptr(f_ext), _ptr(q_next), _ptr(v_next), _stream(stream)))
+
+
+def pd_backward(ctx, dqT, dvT, dq0, dv0, dE, dnu, df_ext, df_stride, stream=None, check=True):
+    code = lib().pd_backward(ctx, _ptr(dqT), _ptr(dvT), _ptr(dq0), _ptr(dv0), _ptr(dE), _ptr(dnu), _ptr(df_ext),
+                             int(df_stride), _stream(stream))
+    if check:
+        _check(ctx, code)
+    return code
+
+
+def pd_get_mass(ctx, n_v):
+    m = np.zeros(n_v)
+    _check(ctx, lib().pd_get_mass(ctx, _ptr(m)))
+    return m
+
+
+def pd_get_tau(ctx, T):
+    t = np.zeros(T)
+    _check(ctx, lib().pd_get_tau(ctx, _ptr(t), int(T)))
+    return t
+
+
+def pd_get_stats(ctx) -> pd_stats:
+    s = pd_stats()
+    _check(ctx, lib().pd_get_stats(ctx, ctypes.byref(s)))
+    return s
+
+
+def pd_profile(ctx, enable: bool):
+    _check(ctx, lib().pd_profile(ctx, 1 if enable else 0))
+
+
+def pd_get_profile(ctx) -> pd_profile_out:
+    p = pd_profile_out()
+    _check(ctx, lib().pd_get_profile(ctx, ctypes.byref(p)))
+    return p
+
+
+def pd_last_error(ctx) -> str:
+    return lib().pd_last_error(ctx).decode()
+
+
+def pd_destroy(ctx):
+    if ctx is not None and ctx.value:
+        lib().pd_destroy(ctx)
+
+
+def pd_version() -> str:
+    return lib().pd_version().decode()
+
+
+# ------------------------------------------------------------ convenience
+
+def options_for(settings) -> pd_options:
+    """pd_options from a workload's SolverSettings."""
+    o = pd_default_options()
+    o.aa_m = settings.aa_m
+    o.k_max = settings.k_max
+    o.fixed_iters = settings.fixed_iters
+    o.local_fp32 = 1 if settings.local_fp32 else 0
+    o.tr_mode = settings.tr_mode
+    o.eps_step = settings.eps_step
+    o.eps_res = settings.eps_res
+    o.eps_abs = settings.eps_abs
+    o.eps_tr = settings.eps_tr
+    return o
+
+
+class PDContext:
+    """Owns one pd_ctx for a workload (``paper_2605_14526_b300.inputs.Scene``)."""
+
+    def __init__(self, scene, options: pd_options | None = None, factor: bool = True):
+        self.scene = scene
+        self.options = options or options_for(scene.solver)
+        model = PD_COROTATED if scene.model == "corotated" else PD_NEOHOOKEAN
+        self.ctx = pd_create(scene.X, scene.tets, scene.pinned, scene.E, model, scene.nu, scene.density,
+                             scene.alpha, scene.beta0, scene.gravity, scene.dt, self.options)
+        self.n_v, self.n_e = scene.n_v, scene.n_e
+        if factor:
+            pd_factor(self.ctx)
+
+    def close(self):
+        pd_destroy(self.ctx)
+        self.ctx = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "ctx", None) is not None:
+                self.close()
+        except Exception:
+            pass
+
+    def set_materials(self, E, nu):
+        pd_set_materials(self.ctx, E, nu)
+        pd_factor(self.ctx)
+
+    def stats(self):
+        return pd_get_stats(self.ctx)
+
+    def mass(self):
+        return pd_get_mass(self.ctx, self.n_v)

@@ -1,0 +1,761 @@
+// C ABI of the PD hot path: context, assembly + factorization (host, FP64),
+// and the launch drivers of the forward rollout and its adjoint.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/pd_b300.h"
+#include "factor.h"
+#include "pd_internal.h"
+#include "pd_launch.h"
+
+using pdk::Ctrl;
+using pdk::Dev;
+
+struct pd_ctx {
+  // host copies
+  int n_v = 0, n_e = 0, n_f = 0;
+  std::vector<double> X;
+  std::vector<int32_t> tets;
+  std::vector<uint8_t> pinned;
+  std::vector<double> E;
+  double nu = 0.3, density = 1000.0, alpha = 0.0, beta0 = 0.0, g[3] = {0, 0, 0};
+  int model = PD_NEOHOOKEAN;
+  double dt = 0.01;
+  pd_options opt{};
+  // rest shape
+  std::vector<double> Bm, vol, mass;
+  // factor state
+  bool factored = false;
+  bool have_order = false;
+  std::vector<int> order_perm;  // free-local elimination order (geometry only)
+  pdf::Factor fac;
+  int64_t nnz_S = 0;
+  double factor_seconds = 0;
+  // device
+  int device = 0;
+  Dev d{};
+  std::vector<void*> allocs;        // context-lifetime device buffers
+  std::vector<void*> factor_allocs; // freed on refactor
+  double* ckpt = nullptr;
+  int ckpt_cap = 0;
+  double* tau = nullptr;
+  double *sq = nullptr, *sv = nullptr;   // rollout state
+  double* stage = nullptr;               // host-pointer staging
+  size_t stage_cap = 0;
+  int* h_flag = nullptr;                 // pinned host flags
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int last_T = 0;
+  pd_stats stats{};
+  // phase timers: event pairs with the step and iteration they bracket; pairs
+  // of iterations that exited early (launched after convergence) are dropped
+  bool profiling = false;
+  std::vector<cudaEvent_t> prof_ev;
+  std::vector<int> prof_kind, prof_step, prof_iter;  // per pair
+  size_t prof_used = 0;                              // events in use
+  pd_profile_out prof{};
+  int* phase_count = nullptr;                        // device [T][2]
+  int64_t launches = 0;
+  std::string err;
+};
+
+namespace {
+
+const char* kVersion = "pd_b300 1.0 (sm_103a)";
+
+int fail(pd_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+#define CK(call)                                                                                 \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) return fail(c, PD_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+int dalloc(pd_ctx* c, T** p, size_t n, bool factor_scope = false) {
+  void* q = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+  if (e != cudaSuccess) return fail(c, PD_ERR_OOM, "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
+  (factor_scope ? c->factor_allocs : c->allocs).push_back(q);
+  *p = reinterpret_cast<T*>(q);
+  return PD_OK;
+}
+
+template <typename T>
+int upload(pd_ctx* c, T** p, const std::vector<T>& h, bool factor_scope = false) {
+  int r = dalloc(c, p, h.size(), factor_scope);
+  if (r) return r;
+  if (!h.empty()) CK(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return PD_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct ScalarCSR {
+  std::vector<int> ptr, idx;
+  std::vector<double> val;
+};
+
+// scalar PD operator pieces from per-element coefficients c_e (N N^T blocks)
+void assemble_scalar(const pd_ctx* c, const std::vector<double>& ce, const std::vector<double>& diag,
+                     std::vector<std::map<int, double>>& rows) {
+  rows.assign(c->n_v, {});
+  for (int e = 0; e < c->n_e; ++e) {
+    const double* gN = &c->Bm[9 * (size_t)e];
+    double G[4][3];
+    for (int j = 0; j < 3; ++j) {
+      G[1][j] = gN[j];
+      G[2][j] = gN[3 + j];
+      G[3][j] = gN[6 + j];
+      G[0][j] = -(G[1][j] + G[2][j] + G[3][j]);
+    }
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) {
+        const double v = ce[e] * (G[a][0] * G[b][0] + G[a][1] * G[b][1] + G[a][2] * G[b][2]);
+        rows[c->tets[4 * e + a]][c->tets[4 * e + b]] += v;
+      }
+  }
+  for (int v = 0; v < c->n_v; ++v)
+    if (!diag.empty()) rows[v][v] += diag[v];
+}
+
+int run_until(pd_ctx* c, cudaStream_t s, const int* d_flag, int max_iter, int chunk,
+              const std::function<void()>& one) {
+  int launched = 0, slot = 0;
+  bool pending = false;
+  int prev = 0;
+  while (launched < max_iter) {
+    for (int i = 0; i < chunk && launched < max_iter; ++i, ++launched) one();
+    CK(cudaMemcpyAsync(&c->h_flag[slot], d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(c->ev[slot], s));
+    if (chunk == 1) {  // synchronous check: nothing launched past the last iteration
+      CK(cudaEventSynchronize(c->ev[slot]));
+      if (c->h_flag[slot]) return PD_OK;
+      continue;
+    }
+    if (pending) {
+      CK(cudaEventSynchronize(c->ev[prev]));
+      if (c->h_flag[prev]) return PD_OK;
+    }
+    pending = true;
+    prev = slot;
+    slot ^= 1;
+  }
+  if (pending) CK(cudaEventSynchronize(c->ev[prev]));
+  return PD_OK;
+}
+
+cudaEvent_t prof_event(pd_ctx* c) {
+  if (c->prof_used == c->prof_ev.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->prof_ev.push_back(e);
+  }
+  return c->prof_ev[c->prof_used++];
+}
+
+// harvest the recorded pairs (stream already synchronised)
+void prof_harvest(pd_ctx* c, int T) {
+  std::vector<int> cnt(2 * (size_t)T, 0);
+  if (cudaMemcpy(cnt.data(), c->phase_count, cnt.size() * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    cudaGetLastError();
+  for (size_t p = 0; 2 * p + 1 < c->prof_used; ++p) {
+    const int kind = c->prof_kind[p], t = c->prof_step[p], it = c->prof_iter[p];
+    if (t < 0 || t >= T || it >= cnt[2 * (size_t)t + kind]) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->prof_ev[2 * p], c->prof_ev[2 * p + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (kind == 0) {
+      c->prof.local_ms += ms;
+      c->prof.local_launches++;
+    } else {
+      c->prof.solve_ms += ms;
+      c->prof.solve_launches++;
+    }
+  }
+  c->prof_used = 0;
+  c->prof_kind.clear();
+  c->prof_step.clear();
+  c->prof_iter.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pd_version(void) { return kVersion; }
+
+void pd_default_options(pd_options* o) {
+  if (!o) return;
+  o->aa_m = 5;
+  o->k_max = 200;
+  o->fixed_iters = 0;
+  o->local_fp32 = 1;
+  o->tr_mode = PD_TR_ADAPT;
+  o->adj_max_iters = 1000;
+  o->eps_step = 1e-8;
+  o->eps_res = 1e-6;
+  o->eps_abs = 1e-12;
+  o->eps_tr = 0.1;
+  o->adj_tol = 1e-9;
+}
+
+const char* pd_last_error(const pd_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_options* opt, pd_ctx** out) {
+  pd_ctx* c = nullptr;
+  if (!out) return PD_ERR_ARG;
+  *out = nullptr;
+  if (!mesh || !mat || !mesh->X || !mesh->tets || !mat->E) return PD_ERR_ARG;
+  if (mesh->n_v < 4 || mesh->n_e < 1 || !(dt > 0)) return PD_ERR_ARG;
+  if (!(mat->nu > -1.0 && mat->nu < 0.5) || !(mat->density > 0)) return PD_ERR_ARG;
+  if (mat->model != PD_COROTATED && mat->model != PD_NEOHOOKEAN) return PD_ERR_ARG;
+  c = new pd_ctx();
+  c->n_v = mesh->n_v;
+  c->n_e = mesh->n_e;
+  c->X.assign(mesh->X, mesh->X + 3 * (size_t)mesh->n_v);
+  c->tets.assign(mesh->tets, mesh->tets + 4 * (size_t)mesh->n_e);
+  c->pinned.assign(mesh->n_v, 0);
+  if (mesh->pinned)
+    for (int v = 0; v < mesh->n_v; ++v) c->pinned[v] = mesh->pinned[v] ? 1 : 0;
+  c->E.assign(mat->E, mat->E + mesh->n_e);
+  c->nu = mat->nu;
+  c->density = mat->density;
+  c->alpha = mat->alpha;
+  c->beta0 = mat->beta0;
+  for (int i = 0; i < 3; ++i) c->g[i] = mat->gravity[i];
+  c->model = mat->model;
+  c->dt = dt;
+  if (opt) c->opt = *opt; else pd_default_options(&c->opt);
+  *out = c;
+  if (c->opt.aa_m < 0 || c->opt.aa_m > pdk::kMaxAA) return fail(c, PD_ERR_ARG, "aa_m must be in [0, %d]", pdk::kMaxAA);
+  if (c->opt.k_max < 1 || c->opt.adj_max_iters < 1) return fail(c, PD_ERR_ARG, "k_max and adj_max_iters must be >= 1");
+  for (size_t i = 0; i < c->tets.size(); ++i)
+    if (c->tets[i] < 0 || c->tets[i] >= c->n_v) return fail(c, PD_ERR_ARG, "tet index out of range at %zu", i);
+  for (int e = 0; e < c->n_e; ++e)
+    if (!(c->E[e] > 0)) return fail(c, PD_ERR_ARG, "E[%d] must be > 0", e);
+  c->n_f = 0;
+  for (int v = 0; v < c->n_v; ++v) c->n_f += c->pinned[v] ? 0 : 1;
+  if (c->n_f == 0) return fail(c, PD_ERR_ARG, "every vertex is pinned");
+
+  // rest shape: Dm = [X1-X0, X2-X0, X3-X0], V = det/6, Bm = Dm^-1, lumped mass
+  c->Bm.assign(9 * (size_t)c->n_e, 0.0);
+  c->vol.assign(c->n_e, 0.0);
+  c->mass.assign(c->n_v, 0.0);
+  for (int e = 0; e < c->n_e; ++e) {
+    const int* t = &c->tets[4 * e];
+    double D[9];
+    for (int i = 0; i < 3; ++i)
+      for (int a = 0; a < 3; ++a) D[3 * i + a] = c->X[3 * t[a + 1] + i] - c->X[3 * t[0] + i];
+    const double det = D[0] * (D[4] * D[8] - D[5] * D[7]) - D[1] * (D[3] * D[8] - D[5] * D[6]) +
+                       D[2] * (D[3] * D[7] - D[4] * D[6]);
+    if (!(det > 0)) return fail(c, PD_ERR_MESH, "element %d has non-positive rest volume", e);
+    const double id = 1.0 / det;
+    double* B = &c->Bm[9 * (size_t)e];
+    B[0] = (D[4] * D[8] - D[5] * D[7]) * id;
+    B[1] = (D[2] * D[7] - D[1] * D[8]) * id;
+    B[2] = (D[1] * D[5] - D[2] * D[4]) * id;
+    B[3] = (D[5] * D[6] - D[3] * D[8]) * id;
+    B[4] = (D[0] * D[8] - D[2] * D[6]) * id;
+    B[5] = (D[2] * D[3] - D[0] * D[5]) * id;
+    B[6] = (D[3] * D[7] - D[4] * D[6]) * id;
+    B[7] = (D[1] * D[6] - D[0] * D[7]) * id;
+    B[8] = (D[0] * D[4] - D[1] * D[3]) * id;
+    c->vol[e] = det / 6.0;
+    for (int a = 0; a < 4; ++a) c->mass[t[a]] += c->density * c->vol[e] / 4.0;
+  }
+  // vertex -> incident corners
+  std::vector<int> inc_ptr(c->n_v + 1, 0), inc_idx(4 * (size_t)c->n_e);
+  for (int e = 0; e < c->n_e; ++e)
+    for (int a = 0; a < 4; ++a) inc_ptr[c->tets[4 * e + a] + 1]++;
+  for (int v = 0; v < c->n_v; ++v) inc_ptr[v + 1] += inc_ptr[v];
+  {
+    std::vector<int> fillp(inc_ptr.begin(), inc_ptr.end() - 1);
+    for (int e = 0; e < c->n_e; ++e)
+      for (int a = 0; a < 4; ++a) inc_idx[fillp[c->tets[4 * e + a]]++] = 4 * e + a;
+  }
+
+  CK(cudaGetDevice(&c->device));
+  Dev& d = c->d;
+  d.n_v = c->n_v;
+  d.n_e = c->n_e;
+  d.n_f = c->n_f;
+  d.model = c->model;
+  std::vector<int4> t4(c->n_e);
+  for (int e = 0; e < c->n_e; ++e) t4[e] = make_int4(c->tets[4 * e], c->tets[4 * e + 1], c->tets[4 * e + 2], c->tets[4 * e + 3]);
+  std::vector<float> Bm32(c->Bm.begin(), c->Bm.end());
+  std::vector<uint8_t> pin = c->pinned;
+  int r;
+  int4* tets_d; float* bm32; double* bm64; double* vol_d; double* X_d; double* mass_d; uint8_t* pin_d;
+  int* ip; int* ii;
+  if ((r = upload(c, &tets_d, t4)) || (r = upload(c, &bm32, Bm32)) || (r = upload(c, &bm64, c->Bm)) ||
+      (r = upload(c, &vol_d, c->vol)) || (r = upload(c, &X_d, c->X)) || (r = upload(c, &mass_d, c->mass)) ||
+      (r = upload(c, &pin_d, pin)) || (r = upload(c, &ip, inc_ptr)) || (r = upload(c, &ii, inc_idx)))
+    return r;
+  d.tets = tets_d; d.Bm32 = bm32; d.Bm64 = bm64; d.vol = vol_d; d.X = X_d; d.mass = mass_d; d.pinned = pin_d;
+  d.inc_ptr = ip; d.inc_idx = ii;
+  const size_t nv3 = 3 * (size_t)c->n_v;
+  double** vecs[] = {&d.q, &d.qprev, &d.qhat, &d.gprev, &d.qt, &d.qtil, &d.b0, &d.b, &d.bprev, &d.mu, &d.r,
+                     &d.z, &d.pdir, &d.w, &d.qbar, &d.gq, &d.gv, &c->sq, &c->sv};
+  for (double** p : vecs)
+    if ((r = dalloc(c, p, nv3))) return r;
+  if ((r = dalloc(c, &d.bperm, 3 * (size_t)c->n_f)) || (r = dalloc(c, &d.y, 3 * (size_t)c->n_f))) return r;
+  const int m = std::max(c->opt.aa_m, 1);
+  if ((r = dalloc(c, &d.dQ, (size_t)m * nv3)) || (r = dalloc(c, &d.dG, (size_t)m * nv3))) return r;
+  double* contrib;
+  double* jac;
+  if ((r = dalloc(c, &contrib, 12 * (size_t)c->n_e)) || (r = dalloc(c, &jac, (size_t)pdk::kJacRec * c->n_e))) return r;
+  d.contrib = contrib;
+  d.jac = jac;
+  if ((r = dalloc(c, &d.red, (size_t)pdk::max_reduction_blocks(c->n_v, c->n_e) * pdk::kRed))) return r;
+  if ((r = dalloc(c, &d.dw, c->n_e)) || (r = dalloc(c, &d.dbeta, c->n_e))) return r;
+  if ((r = dalloc(c, &d.ctrl, 1))) return r;
+  CK(cudaMemset(d.ctrl, 0, sizeof(Ctrl)));
+  CK(cudaMemset(d.dQ, 0, sizeof(double) * m * nv3));
+  CK(cudaMemset(d.dG, 0, sizeof(double) * m * nv3));
+  CK(cudaHostAlloc(&c->h_flag, 2 * sizeof(int), cudaHostAllocDefault));
+  CK(cudaEventCreateWithFlags(&c->ev[0], cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&c->ev[1], cudaEventDisableTiming));
+  return PD_OK;
+}
+
+int pd_set_materials(pd_ctx* c, const double* E, double nu) {
+  if (!c || !E) return PD_ERR_ARG;
+  if (!(nu > -1.0 && nu < 0.5)) return fail(c, PD_ERR_ARG, "nu must be in (-1, 0.5)");
+  for (int e = 0; e < c->n_e; ++e)
+    if (!(E[e] > 0)) return fail(c, PD_ERR_ARG, "E[%d] must be > 0", e);
+  c->E.assign(E, E + c->n_e);
+  c->nu = nu;
+  c->factored = false;
+  return PD_OK;
+}
+
+int pd_factor(pd_ctx* c) {
+  if (!c) return PD_ERR_ARG;
+  auto t0 = std::chrono::steady_clock::now();
+  CK(cudaSetDevice(c->device));
+  for (void* p : c->factor_allocs) cudaFree(p);
+  c->factor_allocs.clear();
+  c->factored = false;
+  const int n_v = c->n_v, n_e = c->n_e;
+  const double h = c->dt;
+  // materials (eq. lame, pd_weight, rayleigh; Sec. 7.2)
+  std::vector<double> mu(n_e), lam(n_e), w(n_e), beta(n_e), coef(n_e), ce(n_e), cb(n_e);
+  double mu_ref = 0, mu_bar = 0, lam_bar = 0, k_bar = 0;
+  for (int e = 0; e < n_e; ++e) {
+    mu[e] = c->E[e] / (2.0 * (1.0 + c->nu));
+    lam[e] = c->E[e] * c->nu / ((1.0 + c->nu) * (1.0 - 2.0 * c->nu));
+    w[e] = 2.0 * mu[e] + (c->model == PD_NEOHOOKEAN ? lam[e] : 0.0);
+    mu_ref = std::max(mu_ref, mu[e]);
+    mu_bar += mu[e];
+    lam_bar += lam[e];
+    k_bar += w[e];
+  }
+  mu_bar /= n_e;
+  lam_bar /= n_e;
+  k_bar /= n_e;
+  for (int e = 0; e < n_e; ++e) {
+    beta[e] = c->beta0 * mu[e] / mu_ref;
+    coef[e] = w[e] * c->vol[e];
+    ce[e] = (w[e] + beta[e] / h) * c->vol[e];
+    cb[e] = beta[e] * c->vol[e];
+  }
+  std::vector<double> diag(n_v);
+  for (int v = 0; v < n_v; ++v) diag[v] = (1.0 + c->alpha * h) * c->mass[v] / (h * h);
+  std::vector<std::map<int, double>> Arows, Brows;
+  assemble_scalar(c, ce, diag, Arows);
+  assemble_scalar(c, cb, {}, Brows);
+  // free-local numbering
+  std::vector<int> f2v, v2f(n_v, -1);
+  for (int v = 0; v < n_v; ++v)
+    if (!c->pinned[v]) {
+      v2f[v] = (int)f2v.size();
+      f2v.push_back(v);
+    }
+  const int nf = (int)f2v.size();
+  pdf::SymCSR Aff;
+  Aff.n = nf;
+  Aff.ptr.assign(nf + 1, 0);
+  std::vector<double> cA(3 * (size_t)n_v, 0.0);
+  ScalarCSR Ad, Bd;
+  Ad.ptr.assign(n_v + 1, 0);
+  Bd.ptr.assign(n_v + 1, 0);
+  for (int v = 0; v < n_v; ++v) {
+    if (!c->pinned[v]) {
+      for (auto& kv : Arows[v]) {
+        if (c->pinned[kv.first]) {
+          for (int i = 0; i < 3; ++i) cA[3 * v + i] += kv.second * c->X[3 * kv.first + i];
+        } else {
+          Aff.idx.push_back(v2f[kv.first]);
+          Aff.val.push_back(kv.second);
+          Ad.idx.push_back(kv.first);
+          Ad.val.push_back(kv.second);
+        }
+      }
+      for (auto& kv : Brows[v]) {
+        Bd.idx.push_back(kv.first);
+        Bd.val.push_back(kv.second);
+      }
+      Aff.ptr[v2f[v] + 1] = (int64_t)Aff.idx.size();
+    }
+    Ad.ptr[v + 1] = (int)Ad.idx.size();
+    Bd.ptr[v + 1] = (int)Bd.idx.size();
+  }
+  // ordering (geometry-only, cached) + symbolic + numeric
+  if (!c->have_order) {
+    std::vector<double> xyz(3 * (size_t)nf);
+    for (int f = 0; f < nf; ++f)
+      for (int i = 0; i < 3; ++i) xyz[3 * f + i] = c->X[3 * f2v[f] + i];
+    c->order_perm = pdf::nested_dissection(nf, Aff.ptr, Aff.idx, xyz.data(), 32);
+    c->have_order = true;
+  }
+  pdf::symbolic(c->fac, Aff, c->order_perm);
+  int64_t bad = pdf::numeric(c->fac, Aff);
+  if (bad) return fail(c, PD_ERR_NOT_SPD, "non-positive pivot at elimination position %lld", (long long)(bad - 1));
+  // self-check of the factor on one right-hand side
+  {
+    std::vector<double> b(nf), x(nf), ax(nf, 0.0);
+    for (int i = 0; i < nf; ++i) b[i] = std::sin(0.37 * i + 1.0);
+    pdf::solve_host(c->fac, b.data(), x.data());
+    double rn = 0, bn = 0;
+    for (int i = 0; i < nf; ++i) {
+      for (int64_t p = Aff.ptr[i]; p < Aff.ptr[i + 1]; ++p) ax[i] += Aff.val[p] * x[Aff.idx[p]];
+      rn += (ax[i] - b[i]) * (ax[i] - b[i]);
+      bn += b[i] * b[i];
+    }
+    if (!(std::sqrt(rn) <= 1e-8 * std::sqrt(bn))) return fail(c, PD_ERR_NOT_SPD, "factor residual %g", std::sqrt(rn / bn));
+  }
+  c->nnz_S = pdf::inverse_factor_nnz(c->fac);
+  if (c->nnz_S > (int64_t)2147483647) return fail(c, PD_ERR_TOO_LARGE, "nnz(S) = %lld exceeds 2^31-1", (long long)c->nnz_S);
+  std::vector<int64_t> s_rowptr, st_ptr;
+  std::vector<double> s_val, st_val;
+  std::vector<int> st_idx;
+  pdf::inverse_factor(c->fac, s_rowptr, s_val, st_ptr, st_idx, st_val);
+  // skyline segments of at most 512 entries, one warp each
+  std::vector<int4> seg;
+  const int SEG = 512;
+  for (int i = 0; i < nf; ++i) {
+    const int len = i - c->fac.first_desc[i] + 1;
+    const int ns = (len + SEG - 1) / SEG;
+    for (int s = 0; s < ns; ++s) seg.push_back(make_int4(i, s * SEG, std::min(SEG, len - s * SEG), ns > 1 ? 1 : 0));
+  }
+  std::vector<int> iperm_v(n_v, -1), perm_v(nf);
+  for (int k = 0; k < nf; ++k) {
+    perm_v[k] = f2v[c->fac.perm[k]];
+    iperm_v[perm_v[k]] = k;
+  }
+  Dev& d = c->d;
+  int r;
+  std::vector<float> coef32(coef.begin(), coef.end());
+  float* c32; double *c64, *mu_d, *lam_d, *E_d, *cA_d, *sv, *stv, *Av, *Bv;
+  int *iperm_d, *perm_d, *sfirst, *sti, *Ap, *Ai, *Bp, *Bi;
+  int64_t *srp, *stp;
+  int4* seg_d;
+  if ((r = upload(c, &c32, coef32, true)) || (r = upload(c, &c64, coef, true)) || (r = upload(c, &mu_d, mu, true)) ||
+      (r = upload(c, &lam_d, lam, true)) || (r = upload(c, &E_d, c->E, true)) || (r = upload(c, &cA_d, cA, true)) ||
+      (r = upload(c, &iperm_d, iperm_v, true)) || (r = upload(c, &perm_d, perm_v, true)) ||
+      (r = upload(c, &srp, s_rowptr, true)) || (r = upload(c, &sfirst, c->fac.first_desc, true)) ||
+      (r = upload(c, &sv, s_val, true)) || (r = upload(c, &seg_d, seg, true)) || (r = upload(c, &stp, st_ptr, true)) ||
+      (r = upload(c, &sti, st_idx, true)) || (r = upload(c, &stv, st_val, true)) || (r = upload(c, &Ap, Ad.ptr, true)) ||
+      (r = upload(c, &Ai, Ad.idx, true)) || (r = upload(c, &Av, Ad.val, true)) || (r = upload(c, &Bp, Bd.ptr, true)) ||
+      (r = upload(c, &Bi, Bd.idx, true)) || (r = upload(c, &Bv, Bd.val, true)))
+    return r;
+  d.coef32 = c32; d.coef64 = c64; d.mu_e = mu_d; d.lam_e = lam_d; d.E = E_d; d.cA = cA_d;
+  d.iperm = iperm_d; d.perm = perm_d; d.s_rowptr = srp; d.s_first = sfirst; d.s_val = sv; d.s_seg = seg_d;
+  d.n_seg = (int)seg.size(); d.st_ptr = stp; d.st_idx = sti; d.st_val = stv;
+  d.A_ptr = Ap; d.A_idx = Ai; d.A_val = Av; d.B_ptr = Bp; d.B_idx = Bi; d.B_val = Bv;
+  d.n_f = nf;
+  d.local_fp32 = c->opt.local_fp32 ? 1 : 0;
+  d.aa_m = c->opt.aa_m; d.k_max = c->opt.k_max; d.fixed_iters = c->opt.fixed_iters; d.tr_mode = c->opt.tr_mode;
+  d.adj_max_iters = c->opt.adj_max_iters;
+  d.h = h; d.alpha_d = c->alpha; d.eps_step = c->opt.eps_step; d.eps_res = c->opt.eps_res; d.eps_abs = c->opt.eps_abs;
+  d.eps_tr = c->opt.eps_tr; d.adj_tol = c->opt.adj_tol;
+  for (int i = 0; i < 3; ++i) d.g[i] = c->g[i];
+  d.mu_bar = mu_bar; d.lam_bar = lam_bar; d.k_bar = k_bar; d.mu_ref = mu_ref; d.beta0 = c->beta0; d.nu = c->nu;
+  c->factored = true;
+  c->factor_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  c->stats.factor_seconds = c->factor_seconds;
+  c->stats.factor_nnz = c->nnz_S;
+  c->stats.n_free = nf;
+  return PD_OK;
+}
+
+static int ensure_stage(pd_ctx* c, size_t n) {
+  if (n <= c->stage_cap) return PD_OK;
+  if (c->stage) cudaFree(c->stage);
+  c->stage = nullptr;
+  c->stage_cap = 0;
+  cudaError_t e = cudaMalloc(&c->stage, n * sizeof(double));
+  if (e != cudaSuccess) return fail(c, PD_ERR_OOM, "staging allocation: %s", cudaGetErrorString(e));
+  c->stage_cap = n;
+  return PD_OK;
+}
+
+int pd_rollout(pd_ctx* c, int32_t T, const double* q0, const double* v0, const double* f_ext, int64_t f_stride,
+               double* qT, double* vT, void* stream) {
+  if (!c) return PD_ERR_ARG;
+  if (!c->factored) return fail(c, PD_ERR_NOT_FACTORED, "pd_factor must run before pd_rollout");
+  if (T < 1 || !q0 || !v0) return fail(c, PD_ERR_ARG, "T >= 1 and q0, v0 are required");
+  const size_t nv3 = 3 * (size_t)c->n_v;
+  if (f_stride != 0 && f_stride != (int64_t)nv3) return fail(c, PD_ERR_ARG, "f_ext_stride must be 0 or 3*n_v");
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  Dev& d = c->d;
+  int r;
+  if (c->ckpt_cap < T) {
+    if (c->ckpt) cudaFree(c->ckpt);
+    if (c->tau) cudaFree(c->tau);
+    if (c->phase_count) cudaFree(c->phase_count);
+    c->ckpt = nullptr;
+    c->tau = nullptr;
+    c->phase_count = nullptr;
+    c->ckpt_cap = 0;
+    if (cudaMalloc(&c->ckpt, (size_t)(T + 1) * nv3 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->tau, (size_t)T * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->phase_count, 2 * (size_t)T * sizeof(int)) != cudaSuccess)
+      return fail(c, PD_ERR_OOM, "checkpoint allocation for %d steps", T);
+    c->ckpt_cap = T;
+  }
+  // host pointers are staged through one device buffer
+  const bool hq = !is_device_ptr(q0), hv = !is_device_ptr(v0), hf = f_ext && !is_device_ptr(f_ext);
+  const bool hqo = qT && !is_device_ptr(qT), hvo = vT && !is_device_ptr(vT);
+  const size_t nf_ext = f_ext ? (f_stride ? (size_t)T * nv3 : nv3) : 0;
+  if ((r = ensure_stage(c, 4 * nv3 + (hf ? nf_ext : 0)))) return r;
+  double* st_q = c->stage;
+  double* st_v = c->stage + nv3;
+  double* st_qo = c->stage + 2 * nv3;
+  double* st_vo = c->stage + 3 * nv3;
+  double* st_f = c->stage + 4 * nv3;
+  const double* q0d = q0;
+  const double* v0d = v0;
+  const double* fd = f_ext;
+  if (hq) { CK(cudaMemcpyAsync(st_q, q0, nv3 * sizeof(double), cudaMemcpyHostToDevice, s)); q0d = st_q; }
+  if (hv) { CK(cudaMemcpyAsync(st_v, v0, nv3 * sizeof(double), cudaMemcpyHostToDevice, s)); v0d = st_v; }
+  if (hf) { CK(cudaMemcpyAsync(st_f, f_ext, nf_ext * sizeof(double), cudaMemcpyHostToDevice, s)); fd = st_f; }
+  d.ckpt = c->ckpt;
+  d.tau = c->tau;
+  d.phase_count = c->phase_count;
+  d.T = T;
+  CK(cudaMemsetAsync(c->tau, 0, (size_t)T * sizeof(double), s));
+  CK(cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), s));  // per-rollout statistics and flags
+  const int max_iter = c->opt.fixed_iters > 0 ? c->opt.fixed_iters : c->opt.k_max + 1;
+  const int* done_flag = &d.ctrl->done;
+  for (int t = 0; t < T; ++t) {
+    const double* qin = t == 0 ? q0d : c->sq;
+    const double* vin = t == 0 ? v0d : c->sv;
+    const double* fstep = fd ? fd + (f_stride ? (size_t)t * nv3 : 0) : nullptr;
+    pdk::launch_step_begin(d, s, qin, vin, fstep, t, c->ckpt + (size_t)t * nv3);
+    c->launches += 1;
+    CK(cudaGetLastError());
+    int it_idx = 0;
+    r = run_until(c, s, done_flag, max_iter, 4, [&]() {
+      c->launches += 6;
+      if (c->profiling) {
+        cudaEvent_t ev[4];
+        for (int i = 0; i < 4; ++i) ev[i] = prof_event(c);
+        for (int kind = 0; kind < 2; ++kind) {
+          c->prof_kind.push_back(kind);
+          c->prof_step.push_back(t);
+          c->prof_iter.push_back(it_idx);
+        }
+        pdk::launch_iteration(d, s, ev);
+      } else {
+        pdk::launch_iteration(d, s, nullptr);
+      }
+      ++it_idx;
+    });
+    if (r) return r;
+    CK(cudaGetLastError());
+    const bool last = t == T - 1;
+    double* qo = last && qT ? (hqo ? st_qo : qT) : c->sq;
+    double* vo = last && vT ? (hvo ? st_vo : vT) : c->sv;
+    pdk::launch_step_end(d, s, qo, vo, c->ckpt + (size_t)(t + 1) * nv3, c->tau);
+    c->launches += c->model == PD_NEOHOOKEAN ? 2 : 1;
+    CK(cudaGetLastError());
+  }
+  if (hqo) CK(cudaMemcpyAsync(qT, st_qo, nv3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (hvo) CK(cudaMemcpyAsync(vT, st_vo, nv3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  Ctrl hc;
+  CK(cudaMemcpyAsync(&hc, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (c->profiling) prof_harvest(c, T);
+  c->last_T = T;
+  pd_stats& st = c->stats;
+  st.steps = T;
+  st.iters_total = hc.iters_total;
+  st.iters_max = hc.iters_max;
+  st.aa_resets = hc.resets;
+  st.not_converged = hc.not_converged;
+  st.tau_half = hc.tau_half;
+  st.tau_one = hc.tau_one;
+  st.status_flags = hc.status;
+  st.last_rho = hc.last_rho;
+  if (hc.status & 1) return fail(c, PD_ERR_NUMERIC, "non-finite value in the right-hand side");
+  if (hc.not_converged) return fail(c, PD_ERR_NOT_CONVERGED, "%d step(s) hit k_max", hc.not_converged);
+  return PD_OK;
+}
+
+int pd_step(pd_ctx* c, const double* q_t, const double* v_t, const double* f_ext, double* q_next, double* v_next,
+            void* stream) {
+  return pd_rollout(c, 1, q_t, v_t, f_ext, 0, q_next, v_next, stream);
+}
+
+int pd_backward(pd_ctx* c, const double* dqT, const double* dvT, double* dq0, double* dv0, double* dE, double* dnu,
+                double* df_ext, int64_t df_stride, void* stream) {
+  if (!c) return PD_ERR_ARG;
+  if (!c->factored) return fail(c, PD_ERR_NOT_FACTORED, "pd_factor must run before pd_backward");
+  if (c->last_T < 1) return fail(c, PD_ERR_NO_CHECKPOINT, "no recorded rollout");
+  if (!dqT) return fail(c, PD_ERR_ARG, "dqT is required");
+  const size_t nv3 = 3 * (size_t)c->n_v;
+  if (df_stride != 0 && df_stride != (int64_t)nv3) return fail(c, PD_ERR_ARG, "df_stride must be 0 or 3*n_v");
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  Dev& d = c->d;
+  const int T = c->last_T;
+  int r;
+  const size_t ndf = df_ext ? (df_stride ? (size_t)T * nv3 : nv3) : 0;
+  const bool h_dq = !is_device_ptr(dqT), h_dv = dvT && !is_device_ptr(dvT);
+  const bool h_q0 = dq0 && !is_device_ptr(dq0), h_v0 = dv0 && !is_device_ptr(dv0);
+  const bool h_E = dE && !is_device_ptr(dE), h_nu = dnu && !is_device_ptr(dnu), h_df = df_ext && !is_device_ptr(df_ext);
+  if ((r = ensure_stage(c, 4 * nv3 + c->n_e + 1 + ndf))) return r;
+  double* st_dq = c->stage;
+  double* st_dv = c->stage + nv3;
+  double* st_q0 = c->stage + 2 * nv3;
+  double* st_v0 = c->stage + 3 * nv3;
+  double* st_E = c->stage + 4 * nv3;
+  double* st_nu = st_E + c->n_e;
+  double* st_df = st_nu + 1;
+  const double* dqTd = dqT;
+  const double* dvTd = dvT;
+  if (h_dq) { CK(cudaMemcpyAsync(st_dq, dqT, nv3 * sizeof(double), cudaMemcpyHostToDevice, s)); dqTd = st_dq; }
+  if (h_dv) { CK(cudaMemcpyAsync(st_dv, dvT, nv3 * sizeof(double), cudaMemcpyHostToDevice, s)); dvTd = st_dv; }
+  double* dq0d = h_q0 ? st_q0 : dq0;
+  double* dv0d = h_v0 ? st_v0 : dv0;
+  double* dEd = h_E ? st_E : dE;
+  double* dnud = h_nu ? st_nu : dnu;
+  double* dfd = h_df ? st_df : df_ext;
+  if (dfd && df_stride == 0) CK(cudaMemsetAsync(dfd, 0, nv3 * sizeof(double), s));
+  pdk::launch_bwd_begin(d, s, dqTd, dvTd);
+  c->launches += 1;
+  CK(cudaGetLastError());
+  const int* done_flag = &d.ctrl->adj_done;
+  for (int t = T - 1; t >= 0; --t) {
+    const double* qstar = c->ckpt + (size_t)(t + 1) * nv3;
+    const double* qt = c->ckpt + (size_t)t * nv3;
+    pdk::launch_bwd_setup(d, s, qstar, c->tau + t);
+    pdk::launch_bwd_init(d, s);
+    c->launches += 5;
+    CK(cudaGetLastError());
+    r = run_until(c, s, done_flag, c->opt.adj_max_iters, 4, [&]() {
+      c->launches += 7;
+      pdk::launch_pcg_iteration(d, s);
+    });
+    if (r) return r;
+    double* df_t = dfd ? (df_stride ? dfd + (size_t)t * nv3 : dfd) : nullptr;
+    pdk::launch_route(d, s, qstar, qt, df_t, df_stride == 0 ? 1 : 0);
+    c->launches += 1;
+    CK(cudaGetLastError());
+  }
+  pdk::launch_chain(d, s, dEd, dnud);
+  pdk::launch_bwd_finish(d, s, dq0d, dv0d);
+  c->launches += 2;
+  CK(cudaGetLastError());
+  if (h_q0) CK(cudaMemcpyAsync(dq0, st_q0, nv3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (h_v0) CK(cudaMemcpyAsync(dv0, st_v0, nv3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (h_E) CK(cudaMemcpyAsync(dE, st_E, c->n_e * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (h_nu) CK(cudaMemcpyAsync(dnu, st_nu, sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (h_df) CK(cudaMemcpyAsync(df_ext, st_df, ndf * sizeof(double), cudaMemcpyDeviceToHost, s));
+  Ctrl hc;
+  CK(cudaMemcpyAsync(&hc, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  c->stats.adj_iters_total = hc.adj_iters_total;
+  c->stats.adj_iters_max = hc.adj_iters_max;
+  c->stats.adj_not_converged = hc.adj_not_converged;
+  c->stats.status_flags = hc.status;
+  if (hc.status & 2) return fail(c, PD_ERR_NUMERIC, "adjoint operator A - K not positive along a CG direction");
+  if (hc.adj_not_converged) return fail(c, PD_ERR_NOT_CONVERGED, "%d adjoint solve(s) hit adj_max_iters", hc.adj_not_converged);
+  return PD_OK;
+}
+
+int pd_profile(pd_ctx* c, int32_t enable) {
+  if (!c) return PD_ERR_ARG;
+  c->profiling = enable != 0;
+  c->prof = pd_profile_out{};
+  c->prof_used = 0;
+  c->prof_kind.clear();
+  c->prof_step.clear();
+  c->prof_iter.clear();
+  return PD_OK;
+}
+
+int pd_get_profile(const pd_ctx* c, pd_profile_out* out) {
+  if (!c || !out) return PD_ERR_ARG;
+  *out = c->prof;
+  return PD_OK;
+}
+
+int pd_get_mass(const pd_ctx* c, double* m) {
+  if (!c || !m) return PD_ERR_ARG;
+  std::memcpy(m, c->mass.data(), c->mass.size() * sizeof(double));
+  return PD_OK;
+}
+
+int pd_get_tau(const pd_ctx* c, double* tau_host, int32_t T) {
+  if (!c || !tau_host || T < 1 || T > c->last_T || !c->tau) return PD_ERR_ARG;
+  if (cudaMemcpy(tau_host, c->tau, (size_t)T * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return PD_ERR_CUDA;
+  return PD_OK;
+}
+
+int pd_get_stats(const pd_ctx* c, pd_stats* out) {
+  if (!c || !out) return PD_ERR_ARG;
+  *out = c->stats;
+  out->launches = c->launches;
+  return PD_OK;
+}
+
+void pd_destroy(pd_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  for (void* p : c->allocs) cudaFree(p);
+  for (void* p : c->factor_allocs) cudaFree(p);
+  if (c->ckpt) cudaFree(c->ckpt);
+  if (c->tau) cudaFree(c->tau);
+  if (c->phase_count) cudaFree(c->phase_count);
+  if (c->stage) cudaFree(c->stage);
+  if (c->h_flag) cudaFreeHost(c->h_flag);
+  for (auto& e : c->prof_ev) cudaEventDestroy(e);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,535 @@
+// Backward kernels (Sec. 4.3 trust region, Sec. 4.7 adjoint, Alg. 2).
+//
+// Per step t (walked from T-1 down to 0) with q* = q_{t+1}:
+//   setup   per element: SVD of F(q*), prox stretches sigma*, the filtered
+//           stretch Jacobian J = k H~(tau)^+ (eq. tr_blend, tr_ift) and the
+//           off-diagonal coefficients of the spectral differential; stored as
+//           a compact record so that K = db/dq is applied matrix-free.
+//   solve   (A - K) mu = q_bar by conjugate gradients preconditioned with the
+//           factor of A (z = S^T S r), K applied per element (eq. db_dq).
+//   route   dL/dq_t, dL/dv_t, dL/df_ext per vertex; dL/dw_e, dL/dbeta_e per
+//           element; mesh-mean sensitivities reduced.
+// After the last step, the chain to E_e and nu (eq. lame and the weights).
+#include <cuda_runtime.h>
+
+#include "pd_common.cuh"
+#include "pd_launch.h"
+
+namespace pdk {
+
+// record layout: U[9] V[9] sF[3] ss[3] J[6] (00 11 22 01 02 12) S[3] T[3] (pairs 01 02 12)
+enum { R_U = 0, R_V = 9, R_SF = 18, R_SS = 21, R_J = 24, R_S = 30, R_T = 33 };
+
+template <typename T>
+__device__ __forceinline__ void filtered_jacobian(const T* ss, const NHMean<T>& m, T tau, T* J) {
+  const T lnJ = dlog(ss[0] * ss[1] * ss[2]);
+  T H[9], Hi[9];
+  nh_hess(ss, m, lnJ, H);
+  if (spd_inv3(H, Hi)) {  // definite: every blend of eq. tr_blend is H itself
+#pragma unroll
+    for (int i = 0; i < 9; ++i) J[i] = m.k * Hi[i];
+    return;
+  }
+  T S[9], Q[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    S[i] = H[i];
+    Q[i] = (i % 4 == 0) ? T(1) : T(0);
+  }
+  for (int sweep = 0; sweep < 10; ++sweep) {
+    jacobi_pq(S, Q, 0, 1);
+    jacobi_pq(S, Q, 0, 2);
+    jacobi_pq(S, Q, 1, 2);
+  }
+  const T thr = (sizeof(T) == 4 ? T(1e-6) : T(1e-12)) * m.k;
+  T inv[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const T lam = S[4 * i];
+    const T lt = (T(1) - tau) * lam + tau * dabs(lam);
+    inv[i] = lt > thr ? T(1) / lt : T(0);  // pseudo-inverse: clamped directions respond with 0
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      J[3 * i + j] = m.k * (Q[3 * i] * inv[0] * Q[3 * j] + Q[3 * i + 1] * inv[1] * Q[3 * j + 1] + Q[3 * i + 2] * inv[2] * Q[3 * j + 2]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTetBlock) k_bwd_setup(Dev d, const double* __restrict__ qstar, const double* tau_t) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.n_e) return;
+  int4 tv;
+  T Bm[9], coef;
+  load_elem<T>(d, e, tv, Bm, coef);
+  T F[9], U[9], V[9], sF[3], ss[3];
+  deform<T>(qstar, tv, Bm, F);
+  svd3<T>(F, U, sF, V);
+  T J[9] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+  T Sp[3], Tp[3];
+  const int pi[3] = {0, 0, 1}, pj[3] = {1, 2, 2};
+  if (d.model == 1) {
+    NHMean<T> m{(T)d.mu_bar, (T)d.lam_bar, (T)d.k_bar};
+    nh_prox<T>(sF, m, ss);
+    filtered_jacobian<T>(ss, m, (T)(*tau_t), J);
+    // (s*_i - s*_j)/(s_i - s_j) = k / (k + mu + (mu - lam ln J*)/(s*_i s*_j)),
+    // exact at the prox stationarity and free of cancellation near s_i = s_j
+    const T lnJ = dlog(ss[0] * ss[1] * ss[2]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int i = pi[c], j = pj[c];
+      Sp[c] = m.k / (m.k + m.mu + (m.mu - m.lam * lnJ) / (ss[i] * ss[j]));
+    }
+  } else {
+    ss[0] = ss[1] = ss[2] = T(1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Sp[c] = T(0);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int i = pi[c], j = pj[c];
+    T sm = sF[i] + sF[j];
+    if (dabs(sm) < T(1e-20)) sm = T(1e-20);
+    Tp[c] = (ss[i] + ss[j]) / sm;
+  }
+  T* r = reinterpret_cast<T*>(d.jac) + kJacRec * (size_t)e;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    r[R_U + i] = U[i];
+    r[R_V + i] = V[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    r[R_SF + i] = sF[i];
+    r[R_SS + i] = ss[i];
+    r[R_S + i] = Sp[i];
+    r[R_T + i] = Tp[i];
+  }
+  r[R_J + 0] = J[0]; r[R_J + 1] = J[4]; r[R_J + 2] = J[8];
+  r[R_J + 3] = J[1]; r[R_J + 4] = J[2]; r[R_J + 5] = J[5];
+}
+
+// contributions of K p for one element: coef * G^T (dp/dF) G p
+template <typename T>
+__global__ void __launch_bounds__(kTetBlock) k_kapply(Dev d, const double* __restrict__ pv) {
+  if (d.ctrl->adj_done) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.n_e) return;
+  int4 tv;
+  T Bm[9], coef;
+  load_elem<T>(d, e, tv, Bm, coef);
+  const T* r = reinterpret_cast<const T*>(d.jac) + kJacRec * (size_t)e;
+  T U[9], V[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    U[i] = r[R_U + i];
+    V[i] = r[R_V + i];
+  }
+  T dF[9];
+  deform<T>(pv, tv, Bm, dF);
+  // Mh = U^T dF V
+  T W[9], Mh[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) W[3 * i + j] = dF[3 * i] * V[j] + dF[3 * i + 1] * V[3 + j] + dF[3 * i + 2] * V[6 + j];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Mh[3 * i + j] = U[i] * W[j] + U[3 + i] * W[3 + j] + U[6 + i] * W[6 + j];
+  T D[9];
+  const T J00 = r[R_J], J11 = r[R_J + 1], J22 = r[R_J + 2], J01 = r[R_J + 3], J02 = r[R_J + 4], J12 = r[R_J + 5];
+  D[0] = J00 * Mh[0] + J01 * Mh[4] + J02 * Mh[8];
+  D[4] = J01 * Mh[0] + J11 * Mh[4] + J12 * Mh[8];
+  D[8] = J02 * Mh[0] + J12 * Mh[4] + J22 * Mh[8];
+  const int pi[3] = {0, 0, 1}, pj[3] = {1, 2, 2};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int i = pi[c], j = pj[c];
+    const T sym = T(0.5) * (Mh[3 * i + j] + Mh[3 * j + i]);
+    const T skw = T(0.5) * (Mh[3 * i + j] - Mh[3 * j + i]);
+    D[3 * i + j] = r[R_S + c] * sym + r[R_T + c] * skw;
+    D[3 * j + i] = r[R_S + c] * sym - r[R_T + c] * skw;
+  }
+  // dp = U D V^T
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) W[3 * i + j] = U[3 * i] * D[j] + U[3 * i + 1] * D[3 + j] + U[3 * i + 2] * D[6 + j];
+  T dp[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dp[3 * i + j] = W[3 * i] * V[3 * j] + W[3 * i + 1] * V[3 * j + 1] + W[3 * i + 2] * V[3 * j + 2];
+  T c12[12];
+  corner_forces<T>(dp, Bm, coef, c12);
+  T* out = reinterpret_cast<T*>(d.contrib) + 12 * (size_t)e;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) out[i] = c12[i];
+}
+
+// ------------------------------------------------------------ PCG
+
+__global__ void k_bwd_begin(Dev d, const double* __restrict__ dqT, const double* __restrict__ dvT) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    Ctrl* c = d.ctrl;
+    c->acc_mu = c->acc_lam = c->acc_k = 0.0;
+    c->adj_iters_total = c->adj_iters_max = c->adj_not_converged = 0;
+  }
+  if (i < d.n_e) {
+    d.dw[i] = 0.0;
+    d.dbeta[i] = 0.0;
+  }
+  if (i < d.n_v) {
+    const bool pin = d.pinned[i];
+    for (int a = 0; a < 3; ++a) {
+      d.gq[3 * i + a] = pin ? 0.0 : dqT[3 * i + a];
+      d.gv[3 * i + a] = (pin || !dvT) ? 0.0 : dvT[3 * i + a];
+    }
+  }
+}
+
+// q_bar = dL/dq* + dL/dv*/h; r = q_bar; mu = 0
+__global__ void k_bwd_init(Dev d) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v == 0) {
+    d.ctrl->adj_k = 0;
+    d.ctrl->adj_done = 0;
+  }
+  if (v >= d.n_v) return;
+  const bool pin = d.pinned[v];
+  for (int a = 0; a < 3; ++a) {
+    const size_t o = 3 * (size_t)v + a;
+    const double qb = pin ? 0.0 : d.gq[o] + d.gv[o] / d.h;
+    d.qbar[o] = qb;
+    d.r[o] = qb;
+    d.mu[o] = 0.0;
+    d.pdir[o] = 0.0;
+    d.z[o] = 0.0;
+  }
+  if (!pin) {
+    const int pos = d.iperm[v];
+    for (int a = 0; a < 3; ++a) {
+      d.bperm[3 * (size_t)pos + a] = d.r[3 * (size_t)v + a];
+      d.y[3 * (size_t)pos + a] = 0.0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kVtxBlock) k_pcg_init_z(Dev d) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  double part[1] = {0.0};
+  if (v < d.n_v && !d.pinned[v]) {
+    for (int a = 0; a < 3; ++a) {
+      const size_t o = 3 * (size_t)v + a;
+      part[0] += d.r[o] * d.z[o];
+      d.pdir[o] = d.z[o];
+    }
+  }
+  block_reduce_store<1>(part, d.red);
+  if (last_block(&d.ctrl->ticket[TK_PCG_INIT])) {
+    if (threadIdx.x == 0) {
+      Ctrl* c = d.ctrl;
+      const double rz = sum_partials(d.red, gridDim.x, 0);
+      c->rz = rz;
+      c->rz0 = rz;
+      if (!(rz > 0.0)) c->adj_done = 1;
+    }
+  }
+}
+
+// w = A p - K p, alpha = r.z / p.w
+template <typename T>
+__global__ void __launch_bounds__(kVtxBlock) k_pcg_w(Dev d) {
+  if (d.ctrl->adj_done) return;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  double part[1] = {0.0};
+  if (v < d.n_v && !d.pinned[v]) {
+    double acc[3] = {0.0, 0.0, 0.0};
+    gather_contrib<T>(d, v, acc);
+    double ap[3] = {0.0, 0.0, 0.0};
+    for (int p = d.A_ptr[v]; p < d.A_ptr[v + 1]; ++p) {
+      const int u = d.A_idx[p];
+      const double a = d.A_val[p];
+      for (int i = 0; i < 3; ++i) ap[i] += a * d.pdir[3 * (size_t)u + i];
+    }
+    for (int i = 0; i < 3; ++i) {
+      const size_t o = 3 * (size_t)v + i;
+      const double w = ap[i] - acc[i];
+      d.w[o] = w;
+      part[0] += d.pdir[o] * w;
+    }
+  }
+  block_reduce_store<1>(part, d.red);
+  if (last_block(&d.ctrl->ticket[TK_PCG_W])) {
+    if (threadIdx.x == 0) {
+      Ctrl* c = d.ctrl;
+      const double pw = sum_partials(d.red, gridDim.x, 0);
+      if (!(pw > 0.0) || !isfinite(pw)) {  // (A - K) not positive along p
+        c->status |= 2;
+        c->adj_done = 1;
+        c->alpha = 0.0;
+      } else {
+        c->alpha = c->rz / pw;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kVtxBlock) k_pcg_r(Dev d) {
+  if (d.ctrl->adj_done) return;
+  const double alpha = d.ctrl->alpha;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= d.n_v || d.pinned[v]) return;
+  const int pos = d.iperm[v];
+  for (int i = 0; i < 3; ++i) {
+    const size_t o = 3 * (size_t)v + i;
+    d.mu[o] += alpha * d.pdir[o];
+    const double rn = d.r[o] - alpha * d.w[o];
+    d.r[o] = rn;
+    d.bperm[3 * (size_t)pos + i] = rn;
+    d.y[3 * (size_t)pos + i] = 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(kVtxBlock) k_pcg_z(Dev d) {
+  if (d.ctrl->adj_done) return;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  double part[1] = {0.0};
+  if (v < d.n_v && !d.pinned[v])
+    for (int i = 0; i < 3; ++i) part[0] += d.r[3 * (size_t)v + i] * d.z[3 * (size_t)v + i];
+  block_reduce_store<1>(part, d.red);
+  if (last_block(&d.ctrl->ticket[TK_PCG_Z])) {
+    if (threadIdx.x == 0) {
+      Ctrl* c = d.ctrl;
+      const double rz = sum_partials(d.red, gridDim.x, 0);
+      c->beta = rz / c->rz;
+      c->rz = rz;
+      c->adj_k += 1;
+      if (!(rz > d.adj_tol * d.adj_tol * c->rz0)) {
+        c->adj_done = 1;
+      } else if (c->adj_k >= d.adj_max_iters) {
+        c->adj_done = 1;
+        c->adj_not_converged += 1;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kVtxBlock) k_pcg_p(Dev d) {
+  if (d.ctrl->adj_done) return;
+  const double beta = d.ctrl->beta;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= d.n_v || d.pinned[v]) return;
+  for (int i = 0; i < 3; ++i) {
+    const size_t o = 3 * (size_t)v + i;
+    d.pdir[o] = d.z[o] + beta * d.pdir[o];
+  }
+}
+
+// ------------------------------------------------------------ routing
+
+template <typename T>
+__global__ void __launch_bounds__(kVtxBlock) k_route(Dev d, const double* __restrict__ qstar,
+                                                     const double* __restrict__ qt, double* __restrict__ df,
+                                                     int df_acc) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  double part[3] = {0.0, 0.0, 0.0};
+  if (tid == 0) {
+    Ctrl* c = d.ctrl;
+    c->adj_iters_total += c->adj_k;
+    if (c->adj_k > c->adj_iters_max) c->adj_iters_max = c->adj_k;
+  }
+  if (tid < d.n_v) {
+    const int v = tid;
+    if (d.pinned[v]) {
+      for (int i = 0; i < 3; ++i) {
+        d.gq[3 * v + i] = 0.0;
+        d.gv[3 * v + i] = 0.0;
+        if (df && !df_acc) df[3 * v + i] = 0.0;
+      }
+    } else {
+      const double m = d.mass[v], h = d.h;
+      double bmu[3] = {0.0, 0.0, 0.0};
+      for (int p = d.B_ptr[v]; p < d.B_ptr[v + 1]; ++p) {
+        const int u = d.B_idx[p];
+        const double b = d.B_val[p];
+        for (int i = 0; i < 3; ++i) bmu[i] += b * d.mu[3 * (size_t)u + i];
+      }
+      for (int i = 0; i < 3; ++i) {
+        const size_t o = 3 * (size_t)v + i;
+        const double mu = d.mu[o];
+        const double gv_next = d.gv[o];
+        d.gq[o] = (1.0 + d.alpha_d * h) * m / (h * h) * mu + bmu[i] / h - gv_next / h;
+        d.gv[o] = m / h * mu;
+        if (df) df[o] = df_acc ? df[o] + mu : mu;
+      }
+    }
+  } else if (tid < d.n_v + d.n_e) {
+    const int e = tid - d.n_v;
+    const int4 tv = d.tets[e];
+    double Bm[9];
+    for (int i = 0; i < 9; ++i) Bm[i] = d.Bm64[9 * (size_t)e + i];
+    double Gm[9], Fs[9], Ft[9];
+    deform<double>(d.mu, tv, Bm, Gm);
+    deform<double>(qstar, tv, Bm, Fs);
+    deform<double>(qt, tv, Bm, Ft);
+    double gb = 0.0;
+    for (int i = 0; i < 9; ++i) gb += Gm[i] * (Fs[i] - Ft[i]);
+    const T* r = reinterpret_cast<const T*>(d.jac) + kJacRec * (size_t)e;
+    double U[9], V[9];
+    for (int i = 0; i < 9; ++i) {
+      U[i] = (double)r[R_U + i];
+      V[i] = (double)r[R_V + i];
+    }
+    double Md[3];  // diagonal of U^T (G mu) V
+    for (int i = 0; i < 3; ++i) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) s += U[3 * k + i] * Gm[3 * k + l] * V[3 * l + i];
+      Md[i] = s;
+    }
+    double dw = 0.0;
+    for (int i = 0; i < 3; ++i) dw += ((double)r[R_SS + i] - (double)r[R_SF + i]) * Md[i];
+    d.dw[e] += d.vol[e] * dw;
+    d.dbeta[e] += -d.vol[e] / d.h * gb;
+    if (d.model == 1) {
+      double ss[3], sf[3];
+      for (int i = 0; i < 3; ++i) {
+        ss[i] = (double)r[R_SS + i];
+        sf[i] = (double)r[R_SF + i];
+      }
+      const double lnJ = log(ss[0] * ss[1] * ss[2]);
+      double Jm[9];
+      Jm[0] = r[R_J]; Jm[4] = r[R_J + 1]; Jm[8] = r[R_J + 2];
+      Jm[1] = Jm[3] = r[R_J + 3]; Jm[2] = Jm[6] = r[R_J + 4]; Jm[5] = Jm[7] = r[R_J + 5];
+      const double k = d.k_bar, coef = d.coef64[e];
+      double gk[3], gm[3], gl[3];
+      for (int i = 0; i < 3; ++i) {
+        gk[i] = ss[i] - sf[i];
+        gm[i] = ss[i] - 1.0 / ss[i];
+        gl[i] = lnJ / ss[i];
+      }
+      for (int i = 0; i < 3; ++i) {
+        double sk = 0.0, sm = 0.0, sl = 0.0;
+        for (int j = 0; j < 3; ++j) {
+          sk += Jm[3 * i + j] * gk[j];
+          sm += Jm[3 * i + j] * gm[j];
+          sl += Jm[3 * i + j] * gl[j];
+        }
+        part[0] += -coef * Md[i] * sm / k;
+        part[1] += -coef * Md[i] * sl / k;
+        part[2] += -coef * Md[i] * sk / k;
+      }
+    }
+  }
+  block_reduce_store<3>(part, d.red);
+  if (last_block(&d.ctrl->ticket[TK_ROUTE])) {
+    if (threadIdx.x == 0) {
+      Ctrl* c = d.ctrl;
+      c->acc_mu += sum_partials(d.red, gridDim.x, 0);
+      c->acc_lam += sum_partials(d.red, gridDim.x, 1);
+      c->acc_k += sum_partials(d.red, gridDim.x, 2);
+    }
+  }
+}
+
+// dL/dE_e and dL/dnu from dL/dw_e, dL/dbeta_e and the mean sensitivities
+__global__ void __launch_bounds__(kVtxBlock) k_chain(Dev d, double* __restrict__ dE, double* __restrict__ dnu) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  double part[4] = {0.0, 0.0, 0.0, 0.0};
+  const Ctrl* c = d.ctrl;
+  if (e < d.n_e) {
+    const double nu = d.nu, E = d.E[e];
+    const bool nh = d.model == 1;
+    const double dmu_dE = 1.0 / (2.0 * (1.0 + nu));
+    const double dlam_dE = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    const double dmu_dnu = -E / (2.0 * (1.0 + nu) * (1.0 + nu));
+    const double den = (1.0 + nu) * (1.0 - 2.0 * nu);
+    const double dlam_dnu = E * (1.0 + 2.0 * nu * nu) / (den * den);
+    const double dw_dE = 2.0 * dmu_dE + (nh ? dlam_dE : 0.0);
+    const double dw_dnu = 2.0 * dmu_dnu + (nh ? dlam_dnu : 0.0);
+    const double cb = d.mu_ref > 0.0 ? d.beta0 / d.mu_ref : 0.0;
+    const double inv_n = 1.0 / d.n_e;
+    if (dE)
+      dE[e] = d.dw[e] * dw_dE + d.dbeta[e] * cb * dmu_dE +
+              (c->acc_mu * dmu_dE + c->acc_lam * dlam_dE + c->acc_k * dw_dE) * inv_n;
+    part[0] = d.dw[e] * dw_dnu + d.dbeta[e] * cb * dmu_dnu;
+    part[1] = dmu_dnu;
+    part[2] = dlam_dnu;
+    part[3] = dw_dnu;
+  }
+  block_reduce_store<4>(part, d.red);
+  if (last_block(&d.ctrl->ticket[TK_CHAIN])) {
+    if (threadIdx.x == 0) {
+      const double inv_n = 1.0 / d.n_e;
+      const double v = sum_partials(d.red, gridDim.x, 0) + (c->acc_mu * sum_partials(d.red, gridDim.x, 1) +
+                                                           c->acc_lam * sum_partials(d.red, gridDim.x, 2) +
+                                                           c->acc_k * sum_partials(d.red, gridDim.x, 3)) * inv_n;
+      if (dnu) *dnu = v;
+      d.ctrl->dnu_acc = v;
+    }
+  }
+}
+
+__global__ void k_bwd_finish(Dev d, double* __restrict__ dq0, double* __restrict__ dv0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * d.n_v) return;
+  if (dq0) dq0[i] = d.gq[i];
+  if (dv0) dv0[i] = d.gv[i];
+}
+
+// ------------------------------------------------------------ wrappers
+
+static inline int nblk(int n, int b) { return (n + b - 1) / b; }
+
+void launch_bwd_begin(const Dev& d, cudaStream_t s, const double* dqT, const double* dvT) {
+  const int n = d.n_v > d.n_e ? d.n_v : d.n_e;
+  k_bwd_begin<<<nblk(n, kVtxBlock), kVtxBlock, 0, s>>>(d, dqT, dvT);
+}
+
+void launch_bwd_setup(const Dev& d, cudaStream_t s, const double* qstar, const double* tau_t) {
+  if (d.local_fp32)
+    k_bwd_setup<float><<<nblk(d.n_e, kTetBlock), kTetBlock, 0, s>>>(d, qstar, tau_t);
+  else
+    k_bwd_setup<double><<<nblk(d.n_e, kTetBlock), kTetBlock, 0, s>>>(d, qstar, tau_t);
+}
+
+void launch_bwd_init(const Dev& d, cudaStream_t s) {
+  k_bwd_init<<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
+  launch_apply_inverse(d, s, d.bperm, d.y, d.z, 0);
+  k_pcg_init_z<<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
+}
+
+void launch_pcg_iteration(const Dev& d, cudaStream_t s) {
+  if (d.local_fp32) {
+    k_kapply<float><<<nblk(d.n_e, kTetBlock), kTetBlock, 0, s>>>(d, d.pdir);
+    k_pcg_w<float><<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
+  } else {
+    k_kapply<double><<<nblk(d.n_e, kTetBlock), kTetBlock, 0, s>>>(d, d.pdir);
+    k_pcg_w<double><<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
+  }
+  k_pcg_r<<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
+  launch_apply_inverse(d, s, d.bperm, d.y, d.z, 2);
+  k_pcg_z<<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
+  k_pcg_p<<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
+}
+
+void launch_route(const Dev& d, cudaStream_t s, const double* qstar, const double* qt, double* df_out, int df_acc) {
+  if (d.local_fp32)
+    k_route<float><<<nblk(d.n_v + d.n_e, kVtxBlock), kVtxBlock, 0, s>>>(d, qstar, qt, df_out, df_acc);
+  else
+    k_route<double><<<nblk(d.n_v + d.n_e, kVtxBlock), kVtxBlock, 0, s>>>(d, qstar, qt, df_out, df_acc);
+}
+
+void launch_chain(const Dev& d, cudaStream_t s, double* dE, double* dnu) {
+  k_chain<<<nblk(d.n_e, kVtxBlock), kVtxBlock, 0, s>>>(d, dE, dnu);
+}
+
+void launch_bwd_finish(const Dev& d, cudaStream_t s, double* dq0, double* dv0) {
+  k_bwd_finish<<<nblk(3 * d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d, dq0, dv0);
+}
+
+}  // namespace pdk

@@ -1,0 +1,136 @@
+// Device helpers shared by the forward and backward kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "pd_internal.h"
+#include "pd_math.cuh"
+
+namespace pdk {
+
+// ------------------------------------------------------------ reductions
+
+template <int NV>
+__device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* red) {
+  __shared__ double sh[32][NV > 0 ? NV : 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    double x = v[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[wid][j] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int w = 0; w < nw; ++w) s += sh[w][threadIdx.x];
+    red[(size_t)blockIdx.x * kRed + threadIdx.x] = s;
+  }
+}
+
+// returns true in every thread of the last block to finish; its partials
+// are then visible. Resets the ticket for the next launch.
+__device__ __forceinline__ bool last_block(unsigned int* ticket) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int v = atomicAdd(ticket, 1u);
+    is_last = (v == gridDim.x - 1);
+    if (is_last) *ticket = 0u;
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+__device__ __forceinline__ double sum_partials(const double* red, int nblocks, int j) {
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += red[(size_t)b * kRed + j];
+  return s;
+}
+
+__device__ __forceinline__ bool finite3(double a, double b, double c) {
+  return isfinite(a) && isfinite(b) && isfinite(c);
+}
+
+// ------------------------------------------------------------ local step
+
+template <typename T>
+__device__ __forceinline__ void load_elem(const Dev& d, int e, int4& tv, T* Bm, T& coef);
+
+template <>
+__device__ __forceinline__ void load_elem<float>(const Dev& d, int e, int4& tv, float* Bm, float& coef) {
+  tv = d.tets[e];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Bm[i] = d.Bm32[9 * (size_t)e + i];
+  coef = d.coef32[e];
+}
+template <>
+__device__ __forceinline__ void load_elem<double>(const Dev& d, int e, int4& tv, double* Bm, double& coef) {
+  tv = d.tets[e];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Bm[i] = d.Bm64[9 * (size_t)e + i];
+  coef = d.coef64[e];
+}
+
+// F = sum_{a=1..3} (x_a - x_0) gradN_a^T, differences taken in FP64
+template <typename T>
+__device__ __forceinline__ void deform(const double* __restrict__ x, int4 tv, const T* Bm, T* F) {
+  const int id[4] = {tv.x, tv.y, tv.z, tv.w};
+  T D[9];  // D[3*i + a-1] = (x_a - x_0)_i
+#pragma unroll
+  for (int a = 1; a < 4; ++a)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) D[3 * i + a - 1] = (T)(x[3 * id[a] + i] - x[3 * id[0] + i]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) F[3 * i + j] = D[3 * i] * Bm[j] + D[3 * i + 1] * Bm[3 + j] + D[3 * i + 2] * Bm[6 + j];
+}
+
+// c_a = coef * P gradN_a for a = 1..3, c_0 = -(c_1 + c_2 + c_3)
+template <typename T>
+__device__ __forceinline__ void corner_forces(const T* P, const T* Bm, T coef, T* out12) {
+  T s[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int a = 1; a < 4; ++a)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const T v = coef * (P[3 * i] * Bm[3 * (a - 1)] + P[3 * i + 1] * Bm[3 * (a - 1) + 1] + P[3 * i + 2] * Bm[3 * (a - 1) + 2]);
+      out12[3 * a + i] = v;
+      s[i] += v;
+    }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) out12[i] = -s[i];
+}
+
+template <typename T>
+__device__ __forceinline__ void project(const Dev& d, const T* F, T* P, T* U, T* sF, T* V, T* ss) {
+  svd3<T>(F, U, sF, V);
+  if (d.model == 0) {
+    ss[0] = ss[1] = ss[2] = T(1);
+  } else {
+    NHMean<T> m{(T)d.mu_bar, (T)d.lam_bar, (T)d.k_bar};
+    nh_prox<T>(sF, m, ss);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) P[3 * i + j] = U[3 * i] * ss[0] * V[3 * j] + U[3 * i + 1] * ss[1] * V[3 * j + 1] + U[3 * i + 2] * ss[2] * V[3 * j + 2];
+}
+
+template <typename T>
+__device__ __forceinline__ void gather_contrib(const Dev& d, int v, double* acc) {
+  const T* cb = reinterpret_cast<const T*>(d.contrib);
+  for (int p = d.inc_ptr[v]; p < d.inc_ptr[v + 1]; ++p) {
+    const int ic = d.inc_idx[p];  // element*4 + corner
+#pragma unroll
+    for (int i = 0; i < 3; ++i) acc[i] += (double)cb[3 * (size_t)ic + i];
+  }
+}
+
+}  // namespace pdk

@@ -1,0 +1,128 @@
+// Internal device-side state of a pd_ctx, shared by the host API and kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pdk {
+
+constexpr int kMaxAA = 8;        // largest Anderson window
+constexpr int kRed = 24;         // doubles per block in the reduction scratch
+constexpr int kVtxBlock = 256;   // threads per block, vertex kernels
+constexpr int kTetBlock = 128;   // threads per block, element kernels
+constexpr int kWarpsSpmv = 8;    // warps per block, skyline SpMV
+constexpr int kJacRec = 36;      // values per element in the backward Jacobian record
+
+// Device-resident control word of the iteration (one per context).
+struct Ctrl {
+  int k;             // local-global iteration index within the step
+  int done;          // step finished (kernels of later iterations exit at once)
+  int converged;     // dual gate passed
+  int pairs;         // Anderson history pairs held (0 .. m+1)
+  int ncols;         // difference columns held (0 .. m)
+  int head;          // ring slot the next difference column goes to
+  int use_hat;       // 1: this iteration takes q_hat (no mixing / guard trip)
+  int t;             // step index in the rollout
+  int n_local, n_solve;  // phases that ran in this step (launches after done exit at once)
+  double gram[kMaxAA * kMaxAA];
+  double gamma[kMaxAA];
+  double dgg[kMaxAA];
+  double dq_norm2, qprev_norm2;   // ||q^{k+1} - q^k||^2, ||q^k||^2 from the last update
+  double db_norm2, bprev_norm2;   // ||b^k - b^{k-1}||^2, ||b^{k-1}||^2
+  // statistics (accumulated over a rollout)
+  int iters_total, iters_max, resets, not_converged, tau_half, tau_one;
+  int adj_iters_total, adj_iters_max, adj_not_converged;
+  int status;        // bit 0: non-finite value; bit 1: PCG breakdown
+  double last_rho;
+  // backward (PCG) scalars
+  int adj_k, adj_done;
+  double rz, rz0, alpha, beta;
+  double acc_mu, acc_lam, acc_k;  // mesh-mean sensitivities accumulated over steps
+  double dnu_acc;
+  unsigned int ticket[16];        // last-block-done counters, one per kernel kind
+};
+
+enum Ticket {
+  TK_ASSEMBLE = 0, TK_SPMV_T = 1, TK_UPDATE = 2, TK_TR = 3, TK_PCG_W = 4, TK_PCG_Z = 5,
+  TK_ROUTE = 6, TK_CHAIN = 7, TK_PCG_INIT = 8
+};
+
+// Everything the kernels need, passed by value.
+struct Dev {
+  int n_v, n_e, n_f;
+  int model;          // 0 corotated, 1 Neo-Hookean
+  int local_fp32;
+  int aa_m, k_max, fixed_iters, tr_mode, adj_max_iters;
+  double h, alpha_d, eps_step, eps_res, eps_abs, eps_tr, adj_tol;
+  double g[3];
+  double mu_bar, lam_bar, k_bar, mu_ref, beta0, nu;
+
+  // mesh
+  const int4* tets;        // [n_e]
+  const float* Bm32;       // [n_e][9] Dm^-1 row-major
+  const double* Bm64;      // [n_e][9]
+  const float* coef32;     // [n_e] w_e V_e
+  const double* coef64;
+  const double* vol;       // [n_e]
+  const double* mu_e;      // [n_e]
+  const double* lam_e;     // [n_e]
+  const double* E;         // [n_e]
+  const double* X;         // [n_v][3]
+  const double* mass;      // [n_v]
+  const uint8_t* pinned;   // [n_v]
+  const int* inc_ptr;      // [n_v+1] vertex -> incident (element*4 + corner)
+  const int* inc_idx;
+  // operators (rows indexed by vertex, pinned rows empty)
+  const int* B_ptr; const int* B_idx; const double* B_val;   // scalar stiffness damping, all columns
+  const int* A_ptr; const int* A_idx; const double* A_val;   // scalar L_A, free columns only
+  const double* cA;        // [n_v][3] constant pinned-column term  A_fp X_p
+  // inverse factor
+  const int* iperm;        // [n_v] elimination position of free vertex (-1 if pinned)
+  const int* perm;         // [n_f] vertex at elimination position
+  const int64_t* s_rowptr; // skyline rows of S
+  const int* s_first;      // first_desc per row
+  const double* s_val;
+  const int4* s_seg;       // segments {row, offset, length, multi}
+  int n_seg;
+  const int64_t* st_ptr;   // S^T CSR (rows = positions)
+  const int* st_idx;
+  const double* st_val;
+
+  // work vectors [n_v][3] unless noted
+  double* q;        // current iterate q^k
+  double* qprev;    // q^{k-1}
+  double* qhat;
+  double* gprev;
+  double* qt;       // q_t of the current step (pinned at X)
+  double* qtil;     // inertial target
+  double* b0;       // q-independent RHS
+  double* b;        // b^k   (two buffers, swapped by parity of k)
+  double* bprev;
+  double* bperm;    // [n_f][3] b in elimination order
+  double* y;        // [n_f][3] S b
+  double* dQ;       // [kMaxAA][n_v][3]
+  double* dG;
+  void* contrib;    // [n_e][12] float or double
+  double* red;      // [blocks][kRed]
+  Ctrl* ctrl;
+
+  // rollout storage
+  double* ckpt;     // [(T+1)][n_v][3]
+  double* tau;      // [T]
+  int* phase_count; // [T][2] local / solve phases run per step
+  int T;
+
+  // backward
+  void* jac;        // [n_e][kJacRec] float or double
+  double* mu;       // adjoint solution
+  double* r;        // residual
+  double* z;        // preconditioned residual
+  double* pdir;     // search direction
+  double* w;        // (A - K) p
+  double* qbar;     // gradient on q*
+  double* gq;       // running dL/dq_t
+  double* gv;       // running dL/dv_t
+  double* dw;       // [n_e] accumulated dL/dw_e
+  double* dbeta;    // [n_e]
+};
+
+}  // namespace pdk

@@ -1,0 +1,30 @@
+// Host-side launch wrappers of the PD kernels (defined in pd_kernels.cu and
+// pd_backward.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "pd_internal.h"
+
+namespace pdk {
+
+int max_reduction_blocks(int n_v, int n_e);
+
+// forward (Alg. 1)
+void launch_step_begin(const Dev& d, cudaStream_t s, const double* qt, const double* vt, const double* fext, int t,
+                       double* ckpt_t);
+// ev: optional 4 events bracketing (local step + assembly) and (two SpMVs)
+void launch_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev);
+void launch_step_end(const Dev& d, cudaStream_t s, double* qn, double* vn, double* ckpt_next, double* tau);
+// A^-1 x for x given in elimination order (check: 0 none, 1 forward done flag, 2 backward done flag)
+void launch_apply_inverse(const Dev& d, cudaStream_t s, const double* xperm, double* y, double* out, int check);
+
+// backward (Alg. 2)
+void launch_bwd_setup(const Dev& d, cudaStream_t s, const double* qstar, const double* tau_t);
+void launch_bwd_init(const Dev& d, cudaStream_t s);
+void launch_pcg_iteration(const Dev& d, cudaStream_t s);
+void launch_route(const Dev& d, cudaStream_t s, const double* qstar, const double* qt, double* df_out, int df_accumulate);
+void launch_chain(const Dev& d, cudaStream_t s, double* dE, double* dnu);
+void launch_bwd_begin(const Dev& d, cudaStream_t s, const double* dqT, const double* dvT);
+void launch_bwd_finish(const Dev& d, cudaStream_t s, double* dq0, double* dv0);
+
+}  // namespace pdk

@@ -1,0 +1,243 @@
+// Per-element math of the PD local step, templated on the arithmetic type
+// (float for the FP32 local step, double for FP64).
+//
+//  * svd3: rotation-variant SVD F = U diag(s) V^T with U, V in SO(3). V comes
+//    from cyclic Jacobi on F^T F (exact Givens angles), sorted by decreasing
+//    eigenvalue; U and s come from a Givens QR of B = F V, whose diagonal is
+//    the signed singular values (only the last may be negative). This is the
+//    scheme of McAdams et al. 2011 (Jacobi eigenanalysis + QR), written with
+//    exact rotations instead of their approximate quaternion ones.
+//  * nh_prox: Newton on the Neo-Hookean stretch-space prox (Sec. 4.1,
+//    eq. nh_prox_normal) with positivity and a sufficient-decrease test.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace pdk {
+
+template <typename T> __device__ __forceinline__ T dsqrt(T x);
+template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
+template <typename T> __device__ __forceinline__ T dlog(T x);
+template <> __device__ __forceinline__ float dlog<float>(float x) { return logf(x); }
+template <> __device__ __forceinline__ double dlog<double>(double x) { return log(x); }
+template <typename T> __device__ __forceinline__ T dabs(T x) { return x < T(0) ? -x : x; }
+
+// symmetric Jacobi rotation zeroing S[p][q]; S and V row-major 3x3
+template <typename T>
+__device__ __forceinline__ void jacobi_pq(T* S, T* V, int p, int q) {
+  const T apq = S[3 * p + q];
+  if (apq == T(0)) return;
+  const T app = S[3 * p + p], aqq = S[3 * q + q];
+  const T theta = (aqq - app) / (T(2) * apq);
+  const T at = dabs(theta);
+  T t = T(1) / (at + dsqrt(at * at + T(1)));
+  if (theta < T(0)) t = -t;
+  const T c = T(1) / dsqrt(t * t + T(1));
+  const T s = t * c;
+  const int r = 3 - p - q;
+  const T arp = S[3 * r + p], arq = S[3 * r + q];
+  const T nrp = c * arp - s * arq, nrq = c * arq + s * arp;
+  S[3 * r + p] = nrp; S[3 * p + r] = nrp;
+  S[3 * r + q] = nrq; S[3 * q + r] = nrq;
+  S[3 * p + p] = app - t * apq;
+  S[3 * q + q] = aqq + t * apq;
+  S[3 * p + q] = T(0); S[3 * q + p] = T(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const T vp = V[3 * k + p], vq = V[3 * k + q];
+    V[3 * k + p] = c * vp - s * vq;
+    V[3 * k + q] = s * vp + c * vq;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void swap_cols_neg(T* V, T* lam, int i, int j) {
+  T tl = lam[i]; lam[i] = lam[j]; lam[j] = tl;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    T a = V[3 * k + i];
+    V[3 * k + i] = V[3 * k + j];
+    V[3 * k + j] = -a;
+  }
+}
+
+// Givens on rows p,q of B zeroing B[q][col]; U accumulates U * G^T
+template <typename T>
+__device__ __forceinline__ void qr_givens(T* B, T* U, int p, int q, int col) {
+  const T a = B[3 * p + col], b = B[3 * q + col];
+  const T r2 = a * a + b * b;
+  T c = T(1), s = T(0);
+  if (r2 > T(0)) {
+    const T ir = T(1) / dsqrt(r2);
+    c = a * ir;
+    s = b * ir;
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const T bp = B[3 * p + k], bq = B[3 * q + k];
+    B[3 * p + k] = c * bp + s * bq;
+    B[3 * q + k] = -s * bp + c * bq;
+    const T up = U[3 * k + p], uq = U[3 * k + q];
+    U[3 * k + p] = c * up + s * uq;
+    U[3 * k + q] = -s * up + c * uq;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void svd3(const T* F, T* U, T* s, T* V) {
+  T S[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      S[3 * i + j] = F[i] * F[j] + F[3 + i] * F[3 + j] + F[6 + i] * F[6 + j];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? T(1) : T(0);
+  const T eps = sizeof(T) == 4 ? T(1e-14) : T(1e-30);
+  for (int sweep = 0; sweep < 8; ++sweep) {
+    const T off = S[1] * S[1] + S[2] * S[2] + S[5] * S[5];
+    const T dia = S[0] * S[0] + S[4] * S[4] + S[8] * S[8];
+    if (off <= eps * dia) break;
+    jacobi_pq(S, V, 0, 1);
+    jacobi_pq(S, V, 0, 2);
+    jacobi_pq(S, V, 1, 2);
+  }
+  T lam[3] = {S[0], S[4], S[8]};
+  if (lam[0] < lam[1]) swap_cols_neg(V, lam, 0, 1);
+  if (lam[0] < lam[2]) swap_cols_neg(V, lam, 0, 2);
+  if (lam[1] < lam[2]) swap_cols_neg(V, lam, 1, 2);
+  T B[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      B[3 * i + j] = F[3 * i] * V[j] + F[3 * i + 1] * V[3 + j] + F[3 * i + 2] * V[6 + j];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) U[i] = (i % 4 == 0) ? T(1) : T(0);
+  qr_givens(B, U, 0, 1, 0);
+  qr_givens(B, U, 0, 2, 0);
+  qr_givens(B, U, 1, 2, 1);
+  s[0] = B[0];
+  s[1] = B[4];
+  s[2] = B[8];
+}
+
+// ------------------------------------------------------------ Neo-Hookean
+
+template <typename T>
+struct NHMean {
+  T mu, lam, k;
+};
+
+template <typename T>
+__device__ __forceinline__ void nh_grad(const T* s, const NHMean<T>& m, const T* sF, T* g, T& lnJ) {
+  lnJ = dlog(s[0] * s[1] * s[2]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const T inv = T(1) / s[i];
+    g[i] = m.k * (s[i] - sF[i]) + m.mu * (s[i] - inv) + m.lam * lnJ * inv;
+  }
+}
+
+// H = k I + H_psi(s) (symmetric, stored as full 3x3)
+template <typename T>
+__device__ __forceinline__ void nh_hess(const T* s, const NHMean<T>& m, T lnJ, T* H) {
+  T inv[3] = {T(1) / s[0], T(1) / s[1], T(1) / s[2]};
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      H[3 * i + j] = (i == j) ? m.k + m.mu * (T(1) + inv[i] * inv[i]) + m.lam * (T(1) - lnJ) * inv[i] * inv[i]
+                              : m.lam * inv[i] * inv[j];
+}
+
+template <typename T>
+__device__ __forceinline__ T nh_obj(const T* s, const NHMean<T>& m, const T* sF) {
+  const T lnJ = dlog(s[0] * s[1] * s[2]);
+  T d2 = T(0), s2 = T(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    d2 += (s[i] - sF[i]) * (s[i] - sF[i]);
+    s2 += s[i] * s[i];
+  }
+  return T(0.5) * m.k * d2 + T(0.5) * m.mu * (s2 - T(3)) - m.mu * lnJ + T(0.5) * m.lam * lnJ * lnJ;
+}
+
+// inverse of symmetric 3x3 by cofactors; returns false unless positive definite
+template <typename T>
+__device__ __forceinline__ bool spd_inv3(const T* H, T* Hi) {
+  const T c00 = H[4] * H[8] - H[5] * H[7];
+  const T c01 = H[5] * H[6] - H[3] * H[8];
+  const T c02 = H[3] * H[7] - H[4] * H[6];
+  const T det = H[0] * c00 + H[1] * c01 + H[2] * c02;
+  const T m2 = H[0] * H[4] - H[1] * H[3];
+  if (!(H[0] > T(0) && m2 > T(0) && det > T(0))) return false;
+  const T id = T(1) / det;
+  Hi[0] = c00 * id;
+  Hi[1] = (H[2] * H[7] - H[1] * H[8]) * id;
+  Hi[2] = (H[1] * H[5] - H[2] * H[4]) * id;
+  Hi[3] = c01 * id;
+  Hi[4] = (H[0] * H[8] - H[2] * H[6]) * id;
+  Hi[5] = (H[2] * H[3] - H[0] * H[5]) * id;
+  Hi[6] = c02 * id;
+  Hi[7] = (H[1] * H[6] - H[0] * H[7]) * id;
+  Hi[8] = m2 * id;
+  return true;
+}
+
+// sigma* = argmin k/2||s - sF||^2 + psi_bar(s), s > 0. Returns iterations.
+template <typename T>
+__device__ __forceinline__ int nh_prox(const T* sF, const NHMean<T>& m, T* s) {
+  const bool f32 = sizeof(T) == 4;
+  const T tol = f32 ? T(2e-7) : T(1e-13);
+  const T loose = f32 ? T(1e-5) : T(1e-11);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) s[i] = sF[i] > T(0.1) ? sF[i] : T(0.1);
+  int it = 0;
+  for (; it < 40; ++it) {
+    T g[3], lnJ;
+    nh_grad(s, m, sF, g, lnJ);
+    const T gmax = fmax(fmax(dabs(g[0]), dabs(g[1])), dabs(g[2]));
+    if (!(gmax > tol * m.k)) break;     // converged (also exits on NaN)
+    T H[9], Hi[9], d[3];
+    nh_hess(s, m, lnJ, H);
+    bool newton = spd_inv3(H, Hi);
+    if (newton) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) d[i] = -(Hi[3 * i] * g[0] + Hi[3 * i + 1] * g[1] + Hi[3 * i + 2] * g[2]);
+      if (d[0] * g[0] + d[1] * g[1] + d[2] * g[2] >= T(0)) newton = false;
+    }
+    if (!newton) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) d[i] = -g[i] / m.k;
+    }
+    const T slope = d[0] * g[0] + d[1] * g[1] + d[2] * g[2];
+    T t = T(1);
+    for (int hh = 0; hh < 60; ++hh) {
+      if (s[0] + t * d[0] > T(0) && s[1] + t * d[1] > T(0) && s[2] + t * d[2] > T(0)) break;
+      t *= T(0.5);
+    }
+    const T f0 = nh_obj(s, m, sF);
+    bool ok = false;
+    T trial[3];
+    for (int hh = 0; hh < 40; ++hh) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) trial[i] = s[i] + t * d[i];
+      T gt[3], lt;
+      nh_grad(trial, m, sF, gt, lt);
+      const T gtmax = fmax(fmax(dabs(gt[0]), dabs(gt[1])), dabs(gt[2]));
+      if ((newton && gtmax <= T(0.5) * gmax) || nh_obj(trial, m, sF) <= f0 + T(1e-4) * t * slope) {
+        ok = true;
+        break;
+      }
+      if (gmax <= loose * m.k) break;   // at the rounding floor of this precision
+      t *= T(0.5);
+    }
+    if (!ok) break;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) s[i] = trial[i];
+  }
+  return it;
+}
+
+}  // namespace pdk

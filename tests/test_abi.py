@@ -1,0 +1,79 @@
+"""The C-ABI library builds for sm_103a, loads, exports every function the
+public header declares, and its structs have the layout the binding uses.
+No compute call is made (no GPU is needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2605_14526_b300 import binding
+from paper_2605_14526_b300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pd_b300.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return ctypes.CDLL(binding.LIB_PATH)
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pd_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "pd_create" in names and "pd_backward" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_header():
+    L = binding.lib()
+    for n in _declared():
+        assert getattr(L, n).restype is not None or n in ("pd_default_options", "pd_destroy"), n
+
+
+def test_default_options_and_version(lib):
+    o = binding.pd_default_options()
+    assert o.aa_m == 5 and o.k_max == 200 and o.local_fp32 == 1
+    assert abs(o.eps_tr - 0.1) < 1e-15 and abs(o.eps_step - 1e-8) < 1e-20
+    assert "sm_103a" in binding.pd_version()
+
+
+def test_struct_layouts_match_c(tmp_path):
+    prog = tmp_path / "layout.c"
+    prog.write_text('''
+#include <stdio.h>
+#include <stddef.h>
+#include "pd_b300.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\\n", sizeof(pd_mesh), sizeof(pd_material), sizeof(pd_options), sizeof(pd_stats),
+         sizeof(pd_profile_out));
+  printf("%zu %zu %zu %zu\\n", offsetof(pd_material, gravity), offsetof(pd_options, eps_step),
+         offsetof(pd_stats, factor_nnz), offsetof(pd_stats, last_rho));
+  return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    sizes = [int(x) for x in out]
+    assert sizes[:5] == [ctypes.sizeof(binding.pd_mesh), ctypes.sizeof(binding.pd_material),
+                         ctypes.sizeof(binding.pd_options), ctypes.sizeof(binding.pd_stats),
+                         ctypes.sizeof(binding.pd_profile_out)]
+    assert sizes[5:] == [binding.pd_material.gravity.offset, binding.pd_options.eps_step.offset,
+                         binding.pd_stats.factor_nnz.offset, binding.pd_stats.last_rho.offset]
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError):
+        binding.lib()

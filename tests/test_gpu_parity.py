@@ -1,0 +1,174 @@
+"""GPU path (C ABI) against the FP64 oracle, element by element.
+
+Tolerances: positions 1e-5 and gradients 1e-4 relative (2-norm over all
+entries) for the FP32 local step; FP64 paths are held far tighter."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import gpu_run, oracle_run, rel
+from oracle import solver
+from paper_2605_14526_b300 import binding, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def test_cube_fixed_iterations_forward_and_backward():
+    """Plain PD cube: 20 fixed iterations, corotated, FP64 (both sides)."""
+    sc = inputs.small_cube()
+    g = gpu_run(sc)
+    o = oracle_run(sc)
+    assert rel(g["qT"], o["qT"]) < 1e-11
+    assert rel(g["vT"], o["vT"]) < 1e-9
+    assert g["stats"].iters_total == 20 * sc.steps
+    for k in ("dq0", "dv0", "dE"):
+        assert rel(g[k], o[k]) < 1e-7, k
+    assert abs(g["dnu"] - o["dnu"]) < 1e-7 * abs(o["dnu"])
+
+
+@pytest.mark.parametrize("model", ["neohookean", "corotated"])
+def test_tiny_fp64_converged_rollout(model):
+    """FP64 local step with tight gates reaches the oracle's fixed points;
+    per-step forces, damping, gravity, seeded initial velocity."""
+    sc = inputs.tiny_block(model=model, steps=3)
+    g = gpu_run(sc)
+    o = oracle_run(sc)
+    assert g["stats"].not_converged == 0
+    assert rel(g["qT"], o["qT"]) < 1e-9
+    for k in ("dq0", "dv0", "dE", "df"):
+        assert rel(g[k], o[k]) < 1e-6, (k, rel(g[k], o[k]))
+    assert abs(g["dnu"] - o["dnu"]) < 1e-6 * abs(o["dnu"])
+
+
+def test_small_bar_fp32_config_gate():
+    """Heterogeneous NH bar (8x4x4 cells, 4^3 blocks), FP32 local step, the
+    benchmark's Anderson window and dual gate, 20 steps."""
+    sc = inputs.hetero_bar(nx=8, ny=4, nz=4, block=4, steps=20)
+    g = gpu_run(sc)
+    o = oracle_run(sc)
+    assert g["stats"].not_converged == 0
+    assert rel(g["qT"], o["qT"]) < 1e-5
+    assert rel(g["vT"], o["vT"]) < 1e-3      # velocity = (q_{T} - q_{T-1})/h amplifies position error by 1/h
+    for k in ("dq0", "dv0", "dE"):
+        assert rel(g[k], o[k]) < 1e-4, (k, rel(g[k], o[k]))
+    assert abs(g["dnu"] - o["dnu"]) < 1e-4 * abs(o["dnu"])
+
+
+def test_full_bar_first_steps():
+    """Full benchmark bar (32x8x8 cells, 10,240 tets) for 3 steps."""
+    sc = inputs.hetero_bar(steps=3)
+    g = gpu_run(sc)
+    o = oracle_run(sc)
+    assert rel(g["qT"], o["qT"]) < 1e-5
+    for k in ("dq0", "dv0", "dE"):
+        assert rel(g[k], o[k]) < 1e-4, (k, rel(g[k], o[k]))
+
+
+def test_full_bar_rollout_converges_and_is_stationary():
+    """All 200 steps of the benchmark bar: every step passes the dual gate and
+    every adjoint solve converges, with finite outputs."""
+    sc = inputs.hetero_bar()
+    g = gpu_run(sc, backward=True)
+    st = g["stats"]
+    assert st.not_converged == 0 and st.status_flags == 0
+    assert st.adj_not_converged == 0
+    assert np.all(np.isfinite(g["qT"])) and np.all(np.isfinite(g["dE"]))
+
+
+def test_host_pointers_match_device_pointers():
+    sc = inputs.hetero_bar(nx=6, ny=2, nz=2, block=2, steps=4)
+    pd = binding.PDContext(sc)
+    T = sc.steps
+    qT_h = np.zeros_like(sc.X)
+    vT_h = np.zeros_like(sc.X)
+    binding.pd_rollout(pd.ctx, T, np.ascontiguousarray(sc.x0), np.ascontiguousarray(sc.v0),
+                       np.ascontiguousarray(sc.f_ext[0]), 0, qT_h, vT_h)
+    g = gpu_run(sc, backward=False)
+    assert np.array_equal(qT_h, g["qT"])
+
+
+def test_error_codes():
+    sc = inputs.hetero_bar(nx=4, ny=2, nz=2, block=2, steps=1)
+    pd = binding.PDContext(sc, factor=False)
+    x = torch.zeros((sc.n_v, 3), dtype=torch.float64, device="cuda:0")
+    with pytest.raises(binding.PDError) as e:
+        binding.pd_rollout(pd.ctx, 1, x, x, None, 0, x, x)
+    assert e.value.code == 3
+    with pytest.raises(binding.PDError) as e:
+        binding.pd_backward(pd.ctx, x, None, None, None, None, None, None, 0)
+    assert e.value.code in (3, 10)
+    bad = sc.tets.copy()
+    bad[0, 2], bad[0, 3] = bad[0, 3], bad[0, 2]
+    with pytest.raises(binding.PDError) as e:
+        binding.PDContext(sc.replace(tets=bad))
+    assert e.value.code == 2
+    oob = sc.tets.copy()
+    oob[1, 0] = sc.n_v
+    with pytest.raises(binding.PDError) as e:
+        binding.PDContext(sc.replace(tets=oob))
+    assert e.value.code == 1
+    with pytest.raises(binding.PDError) as e:
+        binding.PDContext(sc.replace(pinned=np.ones(sc.n_v, dtype=np.uint8)))
+    assert e.value.code == 1
+
+
+def test_single_free_vertex_and_unpinned_body():
+    """Degenerate sizes: one tet with three pins; a free body with no pins."""
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1.0]]) * 0.1
+    tets = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    one = inputs.Scene(name="one", X=X, tets=tets, pinned=np.array([1, 1, 1, 0], dtype=np.uint8),
+                       E=np.array([1e5]), nu=0.3, density=1000.0, alpha=0.0, beta0=0.0,
+                       gravity=np.array([0, 0, -9.81]), dt=0.01, model="neohookean", steps=3,
+                       f_ext=np.zeros((1, 4, 3)), x0=X.copy(), v0=np.zeros((4, 3)),
+                       solver=inputs.SolverSettings(local_fp32=False, eps_step=1e-14, eps_res=1e-14, eps_abs=1e-16),
+                       loss="l2_target", target=X + 0.01)
+    g = gpu_run(one)
+    o = oracle_run(one)
+    assert rel(g["qT"], o["qT"]) < 1e-9
+    assert rel(g["dE"], o["dE"]) < 1e-6
+    free = inputs.tiny_block(steps=2).replace(pinned=np.zeros(27, dtype=np.uint8))
+    g = gpu_run(free)
+    o = oracle_run(free)
+    assert rel(g["qT"], o["qT"]) < 1e-9
+    assert rel(g["dq0"], o["dq0"]) < 1e-6
+
+
+def test_anderson_counts_match_reference():
+    """Iterations and guard trips of the accelerated loop against the oracle's
+    FP64 restatement (FP64 local step on both sides)."""
+    sc = inputs.hetero_bar(nx=8, ny=4, nz=4, block=4, steps=4)
+    sc = sc.replace(solver=inputs.SolverSettings(local_fp32=False))
+    g = gpu_run(sc, backward=False)
+    pb = solver.build_problem(sc)
+    q, v = sc.x0.copy(), sc.v0.copy()
+    iters = 0
+    taus = []
+    for t in range(sc.steps):
+        qn, qp, tau, rho, info = solver.step(pb, q, v, sc.f_ext[0], "aa", sc.solver)
+        iters += info["iters"]
+        taus.append(tau)
+        v = (qn - q) / sc.dt
+        q = qn
+    assert abs(g["stats"].iters_total - iters) <= sc.steps
+    assert rel(g["qT"], q) < 1e-8
+    assert np.array_equal(g["tau"], np.array(taus))
+
+
+def test_autograd_function_gradients():
+    from paper_2605_14526_b300.autograd import rollout
+    sc = inputs.tiny_block(model="neohookean", steps=2)
+    pd = binding.PDContext(sc)
+    dev = "cuda:0"
+    E = torch.tensor(sc.E, dtype=torch.float64, device=dev, requires_grad=True)
+    nu = torch.tensor(sc.nu, dtype=torch.float64, device=dev, requires_grad=True)
+    x0 = torch.tensor(sc.x0, device=dev, requires_grad=True)
+    v0 = torch.tensor(sc.v0, device=dev, requires_grad=True)
+    f = torch.tensor(sc.f_ext, device=dev, requires_grad=True)
+    qT, vT = rollout(E, nu, x0, v0, f, pd, sc.steps)
+    loss = 0.5 * ((qT - torch.tensor(sc.target, device=dev)) ** 2).sum()
+    loss.backward()
+    o = oracle_run(sc)
+    assert rel(E.grad.cpu().numpy(), o["dE"]) < 1e-6
+    assert rel(x0.grad.cpu().numpy(), o["dq0"]) < 1e-6
+    assert rel(f.grad.cpu().numpy(), o["df"]) < 1e-6
+    assert abs(float(nu.grad) - o["dnu"]) < 1e-6 * abs(o["dnu"])
