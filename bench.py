@@ -21,7 +21,11 @@ import sys
 import threading
 import time
 
-import numpy as np
+# the CPU oracle baseline runs single-threaded (set before numpy loads BLAS)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -95,16 +99,14 @@ class ClockSampler:
 def oracle_sample(scene, n_steps: int):
     """The oracle as it stands (exact fixed point + direct adjoint) on the first
     n_steps steps of the workload, single-threaded. Returns (seconds, steps)."""
-    from threadpoolctl import threadpool_limits
     from oracle import adjoint, solver
     sc = scene.with_steps(n_steps)
-    with threadpool_limits(1):
-        t0 = time.perf_counter()
-        pb = solver.build_problem(sc)
-        qT, vT, recs = solver.rollout(pb, sc, mode="exact")
-        _, dq, dv = adjoint.loss_and_grad(sc, pb, qT, vT)
-        adjoint.rollout_backward(pb, recs, dq, dv)
-        dt = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pb = solver.build_problem(sc)
+    qT, vT, recs = solver.rollout(pb, sc, mode="exact")
+    _, dq, dv = adjoint.loss_and_grad(sc, pb, qT, vT)
+    adjoint.rollout_backward(pb, recs, dq, dv)
+    dt = time.perf_counter() - t0
     return dt, n_steps
 
 

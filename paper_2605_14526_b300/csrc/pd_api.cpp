@@ -681,7 +681,7 @@ int pd_backward(pd_ctx* c, const double* dqT, const double* dvT, double* dq0, do
     });
     if (r) return r;
     double* df_t = dfd ? (df_stride ? dfd + (size_t)t * nv3 : dfd) : nullptr;
-    pdk::launch_route(d, s, qstar, qt, df_t, df_stride == 0 ? 1 : 0);
+    pdk::launch_route(d, s, qstar, qt, c->tau + t, df_t, df_stride == 0 ? 1 : 0);
     c->launches += 1;
     CK(cudaGetLastError());
   }

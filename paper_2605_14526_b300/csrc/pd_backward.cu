@@ -8,7 +8,8 @@
 //   solve   (A - K) mu = q_bar by conjugate gradients preconditioned with the
 //           factor of A (z = S^T S r), K applied per element (eq. db_dq).
 //   route   dL/dq_t, dL/dv_t, dL/df_ext per vertex; dL/dw_e, dL/dbeta_e per
-//           element; mesh-mean sensitivities reduced.
+//           element (SVD and prox recomputed in FP64); mesh-mean
+//           sensitivities reduced.
 // After the last step, the chain to E_e and nu (eq. lame and the weights).
 #include <cuda_runtime.h>
 
@@ -331,10 +332,9 @@ __global__ void __launch_bounds__(kVtxBlock) k_pcg_p(Dev d) {
 
 // ------------------------------------------------------------ routing
 
-template <typename T>
 __global__ void __launch_bounds__(kVtxBlock) k_route(Dev d, const double* __restrict__ qstar,
-                                                     const double* __restrict__ qt, double* __restrict__ df,
-                                                     int df_acc) {
+                                                     const double* __restrict__ qt, const double* tau_t,
+                                                     double* __restrict__ df, int df_acc) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   double part[3] = {0.0, 0.0, 0.0};
   if (tid == 0) {
@@ -368,6 +368,9 @@ __global__ void __launch_bounds__(kVtxBlock) k_route(Dev d, const double* __rest
       }
     }
   } else if (tid < d.n_v + d.n_e) {
+    // per element, in FP64: p* - F = U diag(s* - s_F) V^T is a small
+    // difference of O(1) quantities, so the SVD and prox are recomputed here
+    // in double rather than read from the FP32 record
     const int e = tid - d.n_v;
     const int4 tv = d.tets[e];
     double Bm[9];
@@ -378,33 +381,29 @@ __global__ void __launch_bounds__(kVtxBlock) k_route(Dev d, const double* __rest
     deform<double>(qt, tv, Bm, Ft);
     double gb = 0.0;
     for (int i = 0; i < 9; ++i) gb += Gm[i] * (Fs[i] - Ft[i]);
-    const T* r = reinterpret_cast<const T*>(d.jac) + kJacRec * (size_t)e;
-    double U[9], V[9];
-    for (int i = 0; i < 9; ++i) {
-      U[i] = (double)r[R_U + i];
-      V[i] = (double)r[R_V + i];
+    double U[9], V[9], sf[3], ss[3];
+    svd3<double>(Fs, U, sf, V);
+    NHMean<double> m{d.mu_bar, d.lam_bar, d.k_bar};
+    if (d.model == 1) {
+      nh_prox<double>(sf, m, ss);
+    } else {
+      ss[0] = ss[1] = ss[2] = 1.0;
     }
     double Md[3];  // diagonal of U^T (G mu) V
     for (int i = 0; i < 3; ++i) {
-      double s = 0.0;
+      double acc = 0.0;
       for (int k = 0; k < 3; ++k)
-        for (int l = 0; l < 3; ++l) s += U[3 * k + i] * Gm[3 * k + l] * V[3 * l + i];
-      Md[i] = s;
+        for (int l = 0; l < 3; ++l) acc += U[3 * k + i] * Gm[3 * k + l] * V[3 * l + i];
+      Md[i] = acc;
     }
     double dw = 0.0;
-    for (int i = 0; i < 3; ++i) dw += ((double)r[R_SS + i] - (double)r[R_SF + i]) * Md[i];
+    for (int i = 0; i < 3; ++i) dw += (ss[i] - sf[i]) * Md[i];
     d.dw[e] += d.vol[e] * dw;
     d.dbeta[e] += -d.vol[e] / d.h * gb;
     if (d.model == 1) {
-      double ss[3], sf[3];
-      for (int i = 0; i < 3; ++i) {
-        ss[i] = (double)r[R_SS + i];
-        sf[i] = (double)r[R_SF + i];
-      }
-      const double lnJ = log(ss[0] * ss[1] * ss[2]);
       double Jm[9];
-      Jm[0] = r[R_J]; Jm[4] = r[R_J + 1]; Jm[8] = r[R_J + 2];
-      Jm[1] = Jm[3] = r[R_J + 3]; Jm[2] = Jm[6] = r[R_J + 4]; Jm[5] = Jm[7] = r[R_J + 5];
+      filtered_jacobian<double>(ss, m, *tau_t, Jm);
+      const double lnJ = log(ss[0] * ss[1] * ss[2]);
       const double k = d.k_bar, coef = d.coef64[e];
       double gk[3], gm[3], gl[3];
       for (int i = 0; i < 3; ++i) {
@@ -517,11 +516,9 @@ void launch_pcg_iteration(const Dev& d, cudaStream_t s) {
   k_pcg_p<<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
 }
 
-void launch_route(const Dev& d, cudaStream_t s, const double* qstar, const double* qt, double* df_out, int df_acc) {
-  if (d.local_fp32)
-    k_route<float><<<nblk(d.n_v + d.n_e, kVtxBlock), kVtxBlock, 0, s>>>(d, qstar, qt, df_out, df_acc);
-  else
-    k_route<double><<<nblk(d.n_v + d.n_e, kVtxBlock), kVtxBlock, 0, s>>>(d, qstar, qt, df_out, df_acc);
+void launch_route(const Dev& d, cudaStream_t s, const double* qstar, const double* qt, const double* tau_t,
+                  double* df_out, int df_acc) {
+  k_route<<<nblk(d.n_v + d.n_e, kVtxBlock), kVtxBlock, 0, s>>>(d, qstar, qt, tau_t, df_out, df_acc);
 }
 
 void launch_chain(const Dev& d, cudaStream_t s, double* dE, double* dnu) {

