@@ -168,6 +168,14 @@ int pd_step(pd_ctx* ctx, const double* q_t, const double* v_t, const double* f_e
 int pd_backward(pd_ctx* ctx, const double* dqT, const double* dvT, double* dq0, double* dv0,
                 double* dE, double* dnu, double* df_ext, int64_t df_stride, void* stream);
 
+/* x = A^-1 b on the free DoFs with the factored operator of the context,
+ * evaluated as two sparse products x = S^T (S b) (Sec. 4.5 eq. two_spmv).
+ * b, x: [n_v][3] device pointers (caller-owned); rows of pinned vertices of
+ * b are ignored and those of x are set to 0. Uses the context's work
+ * buffers, so it must not overlap a pd_rollout / pd_backward of the same
+ * context on another stream. Enqueued on the stream; does not synchronise. */
+int pd_solve(pd_ctx* ctx, const double* b, double* x, void* stream);
+
 /* Lumped vertex masses [n_v] (host output, kg): density * V_e / 4 per corner. */
 int pd_get_mass(const pd_ctx* ctx, double* mass_host);
 

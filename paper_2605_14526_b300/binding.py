@@ -75,6 +75,7 @@ def lib():
             "pd_get_mass": (c_int, [P, P]),
             "pd_get_tau": (c_int, [P, P, c_int32]),
             "pd_get_stats": (c_int, [P, P]),
+            "pd_solve": (c_int, [P, P, P, P]),
             "pd_profile": (c_int, [P, c_int32]),
             "pd_get_profile": (c_int, [P, P]),
             "pd_last_error": (ctypes.c_char_p, [P]),
@@ -182,6 +183,10 @@ def pd_backward(ctx, dqT, dvT, dq0, dv0, dE, dnu, df_ext, df_stride, stream=None
     if check:
         _check(ctx, code)
     return code
+
+
+def pd_solve(ctx, b, x, stream=None):
+    _check(ctx, lib().pd_solve(ctx, _ptr(b), _ptr(x), _stream(stream)))
 
 
 def pd_get_mass(ctx, n_v):

@@ -706,6 +706,17 @@ int pd_backward(pd_ctx* c, const double* dqT, const double* dvT, double* dq0, do
   return PD_OK;
 }
 
+int pd_solve(pd_ctx* c, const double* b, double* x, void* stream) {
+  if (!c) return PD_ERR_ARG;
+  if (!c->factored) return fail(c, PD_ERR_NOT_FACTORED, "pd_factor must run before pd_solve");
+  if (!b || !x) return fail(c, PD_ERR_ARG, "b and x are required");
+  CK(cudaSetDevice(c->device));
+  pdk::launch_solve(c->d, (cudaStream_t)stream, b, c->d.bperm, c->d.y, x);
+  c->launches += 3;
+  CK(cudaGetLastError());
+  return PD_OK;
+}
+
 int pd_profile(pd_ctx* c, int32_t enable) {
   if (!c) return PD_ERR_ARG;
   c->profiling = enable != 0;
@@ -759,3 +770,4 @@ void pd_destroy(pd_ctx* c) {
 }
 
 }  // extern "C"
+

@@ -451,6 +451,25 @@ __global__ void __launch_bounds__(kVtxBlock) k_tr(Dev d, double* tau_out) {
   }
 }
 
+// ------------------------------------------------------------ standalone solve
+
+// b (vertex order) -> elimination order in xperm; zero the S b accumulator
+// rows and the pinned rows of x
+__global__ void k_solve_in(Dev d, const double* __restrict__ b, double* __restrict__ xperm, double* __restrict__ y,
+                           double* __restrict__ x) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= d.n_v) return;
+  if (d.pinned[v]) {
+    for (int i = 0; i < 3; ++i) x[3 * (size_t)v + i] = 0.0;
+    return;
+  }
+  const int pos = d.iperm[v];
+  for (int i = 0; i < 3; ++i) {
+    xperm[3 * (size_t)pos + i] = b[3 * (size_t)v + i];
+    y[3 * (size_t)pos + i] = 0.0;
+  }
+}
+
 // ------------------------------------------------------------ launch wrappers
 
 static inline int nblk(int n, int b) { return (n + b - 1) / b; }
@@ -472,6 +491,11 @@ int spmvt_blocks(const Dev& d) {
 void launch_apply_inverse(const Dev& d, cudaStream_t s, const double* xperm, double* y, double* out, int check) {
   k_spmv_s<<<spmv_blocks(d), 32 * kWarpsSpmv, 0, s>>>(d, xperm, y, check);
   k_spmv_st<<<spmvt_blocks(d), 32 * kWarpsSpmv, 0, s>>>(d, y, out, check);
+}
+
+void launch_solve(const Dev& d, cudaStream_t s, const double* b, double* xperm, double* y, double* x) {
+  k_solve_in<<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d, b, xperm, y, x);
+  launch_apply_inverse(d, s, xperm, y, x, 0);
 }
 
 void launch_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {

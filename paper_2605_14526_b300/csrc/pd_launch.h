@@ -18,6 +18,9 @@ void launch_step_end(const Dev& d, cudaStream_t s, double* qn, double* vn, doubl
 // A^-1 x for x given in elimination order (check: 0 none, 1 forward done flag, 2 backward done flag)
 void launch_apply_inverse(const Dev& d, cudaStream_t s, const double* xperm, double* y, double* out, int check);
 
+// x = A^-1 b for b, x in vertex order; xperm and y are [n_f][3] work buffers
+void launch_solve(const Dev& d, cudaStream_t s, const double* b, double* xperm, double* y, double* x);
+
 // backward (Alg. 2)
 void launch_bwd_setup(const Dev& d, cudaStream_t s, const double* qstar, const double* tau_t);
 void launch_bwd_init(const Dev& d, cudaStream_t s);

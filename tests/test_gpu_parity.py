@@ -187,3 +187,21 @@ def test_autograd_function_gradients():
     assert rel(x0.grad.cpu().numpy(), o["dq0"]) < 1e-6
     assert rel(f.grad.cpu().numpy(), o["df"]) < 1e-6
     assert abs(float(nu.grad) - o["dnu"]) < 1e-6 * abs(o["dnu"])
+
+
+@pytest.mark.parametrize("shape", [(8, 4, 4, 4), (32, 8, 8, 8)])
+def test_solve_matches_oracle_factor(shape):
+    """pd_solve (x = S^T S b) against the oracle's sparse LU of the same A."""
+    sc = inputs.hetero_bar(nx=shape[0], ny=shape[1], nz=shape[2], block=shape[3], steps=1)
+    pd = binding.PDContext(sc)
+    pb = solver.build_problem(sc)
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal((sc.n_v, 3))
+    bt = torch.tensor(b, device="cuda:0")
+    x = torch.full_like(bt, float("nan"))
+    binding.pd_solve(pd.ctx, bt, x)
+    torch.cuda.synchronize()
+    xo = np.zeros_like(b)
+    xo[pb.free] = solver.solve_A(pb, b[pb.free])
+    assert rel(x.cpu().numpy(), xo) < 1e-11
+    assert np.all(x.cpu().numpy()[pb.fixed] == 0.0)
