@@ -176,6 +176,22 @@ int pd_backward(pd_ctx* ctx, const double* dqT, const double* dvT, double* dq0, 
  * context on another stream. Enqueued on the stream; does not synchronise. */
 int pd_solve(pd_ctx* ctx, const double* b, double* x, void* stream);
 
+/* Same result as pd_solve, for callers that cannot allocate device memory
+ * while they run (code under stream capture or in a real-time loop, hosts
+ * whose device memory belongs to another allocator or a fixed arena). The
+ * call allocates nothing: its two [n_f][3] work vectors live in one
+ * file-scope device array sized for at most 65536 free vertices (3 MiB, held
+ * by every GPU that loads the library until the process exits). The paper has
+ * no counterpart; this is a convenience of this library.
+ *   - Meshes with more than 65536 free vertices: PD_ERR_TOO_LARGE.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call shares the one array: calls that overlap on the GPU (other
+ *     streams, other contexts, other host threads) race. The accumulator is
+ *     cleared by each call before use.
+ * b, x: [n_v][3] device pointers; pinned rows of x are set to 0. */
+int pd_solve_noalloc(pd_ctx* ctx, const double* b, double* x, void* stream);
+
 /* Lumped vertex masses [n_v] (host output, kg): density * V_e / 4 per corner. */
 int pd_get_mass(const pd_ctx* ctx, double* mass_host);
 

@@ -76,6 +76,7 @@ def lib():
             "pd_get_tau": (c_int, [P, P, c_int32]),
             "pd_get_stats": (c_int, [P, P]),
             "pd_solve": (c_int, [P, P, P, P]),
+            "pd_solve_noalloc": (c_int, [P, P, P, P]),
             "pd_profile": (c_int, [P, c_int32]),
             "pd_get_profile": (c_int, [P, P]),
             "pd_last_error": (ctypes.c_char_p, [P]),
@@ -187,6 +188,10 @@ def pd_backward(ctx, dqT, dvT, dq0, dv0, dE, dnu, df_ext, df_stride, stream=None
 
 def pd_solve(ctx, b, x, stream=None):
     _check(ctx, lib().pd_solve(ctx, _ptr(b), _ptr(x), _stream(stream)))
+
+
+def pd_solve_noalloc(ctx, b, x, stream=None):
+    _check(ctx, lib().pd_solve_noalloc(ctx, _ptr(b), _ptr(x), _stream(stream)))
 
 
 def pd_get_mass(ctx, n_v):

@@ -18,6 +18,7 @@
 #include "factor.h"
 #include "pd_internal.h"
 #include "pd_launch.h"
+#include "pd_noalloc.h"
 
 using pdk::Ctrl;
 using pdk::Dev;
@@ -771,3 +772,10 @@ void pd_destroy(pd_ctx* c) {
 
 }  // extern "C"
 
+void pd_internal_state(pd_ctx* c, const pdk::Dev** d, int* device, int* factored) {
+  *d = &c->d;
+  *device = c->device;
+  *factored = c->factored ? 1 : 0;
+}
+
+void pd_internal_set_error(pd_ctx* c, const char* msg) { c->err = msg; }
