@@ -176,15 +176,23 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > 126 MB L2
     stream = torch.cuda.current_stream(dev)
 
-    def fwd_bwd():
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def fwd_bwd(timed=False):
+        if timed:
+            ev[0].record(stream)
         binding.pd_rollout(pd.ctx, T, x0, v0, f0, 0, qT, vT, stream)
+        if timed:
+            ev[1].record(stream)
         binding.pd_backward(pd.ctx, qT - target, zero, dq0, dv0, dE, dnu, None, 0, stream)
+        if timed:
+            ev[2].record(stream)
 
     for _ in range(args.warmup):
         fwd_bwd()
     torch.cuda.synchronize()
     launches0 = binding.pd_get_stats(pd.ctx).launches
-    total_ms = 0.0
+    total_ms = fwd_ms = bwd_ms = 0.0
     iters = adj = 0
     with ClockSampler(local_rank) as clk:
         for _ in range(args.steps):
@@ -192,12 +200,11 @@ def main():
             if dist:
                 dist.barrier()
             torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fwd_bwd()
-            e1.record(stream)
+            fwd_bwd(timed=True)
             torch.cuda.synchronize()
-            total_ms += e0.elapsed_time(e1)
+            fwd_ms += ev[0].elapsed_time(ev[1])
+            bwd_ms += ev[1].elapsed_time(ev[2])
+            total_ms += ev[0].elapsed_time(ev[2])
             st = binding.pd_get_stats(pd.ctx)
             iters += st.iters_total
             adj += st.adj_iters_total
@@ -209,21 +216,40 @@ def main():
         tmax = float(tt[0])
     value = world * T * args.steps / (tmax / 1e3)
 
-    # phase timers of the local step (live, CUDA events on the work stream)
+    # Roofline of the dominant kernel. Each rollout is one launch of the
+    # persistent forward kernel and one of the persistent adjoint kernel; the
+    # CUDA events above bracket them on the work stream. Algorithmic bytes per
+    # launch = iterations x bytes per iteration:
+    #   forward iteration: local step 56 B/element (indices, Dm^-1, w V) + 48 B/vertex
+    #     (q in, b out); solve 20 B per nnz(S) (skyline values + S^T values and
+    #     indices) + 96 B per free vertex (b, y, y, q_hat); Anderson (2m+3) x 24 B/vertex
+    #   adjoint iteration: element record 144 B + 56 B per element, 20 B per nnz(S),
+    #     10 vectors x 24 B per vertex
+    st = binding.pd_get_stats(pd.ctx)
+    nnzS = st.factor_nnz
+    m = pd.options.aa_m
+    fwd_iter_bytes = 56 * scene.n_e + 48 * scene.n_v + 20 * nnzS + 96 * st.n_free + (2 * m + 3) * 24 * scene.n_v
+    bwd_iter_bytes = 200 * scene.n_e + 20 * nnzS + 240 * scene.n_v
+    fwd_bytes = fwd_iter_bytes * iters / args.steps
+    bwd_bytes = bwd_iter_bytes * adj / args.steps
+    peak, peak_kind = _peaks()
+    fwd_launch_ms, bwd_launch_ms = fwd_ms / args.steps, bwd_ms / args.steps
+    if fwd_launch_ms >= bwd_launch_ms:
+        kname, kbytes, kms = "k_fwd_rollout (persistent forward rollout)", fwd_bytes, fwd_launch_ms
+    else:
+        kname, kbytes, kms = "k_bwd_rollout (persistent adjoint)", bwd_bytes, bwd_launch_ms
+    achieved = kbytes / (kms * 1e-3) / 1e9
+
+    # device phase breakdown of one forward rollout (globaltimer, block 0)
     binding.pd_profile(pd.ctx, True)
-    for _ in range(2):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        binding.pd_rollout(pd.ctx, T, x0, v0, f0, 0, qT, vT, stream)
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
+    binding.pd_rollout(pd.ctx, T, x0, v0, f0, 0, qT, vT, stream)
+    torch.cuda.synchronize()
     prof = binding.pd_get_profile(pd.ctx)
     binding.pd_profile(pd.ctx, False)
-    local_ms = prof.local_ms / max(prof.local_launches, 1)
-    solve_ms = prof.solve_ms / max(prof.solve_launches, 1)
-    # algorithmic bytes of one local step + RHS assembly: per tet 16 B indices +
-    # 36 B Dm^-1 + 4 B w_e V_e; per vertex 24 B q read + 24 B b written
-    local_bytes = 56 * scene.n_e + 48 * scene.n_v
-    peak, peak_kind = _peaks()
-    achieved = local_bytes / (local_ms * 1e-3) / 1e9
+    phase_names = ["begin", "local", "assemble_gate", "spmv_s", "spmv_st", "spmv_st_anderson", "update", "end_tr"]
+    phases = {n: round(prof.phase_ms[i], 3) for i, n in enumerate(phase_names) if prof.phase_ms[i] > 0}
 
     # end to end through the C ABI with host buffers (copies inside the region)
     hx0, hv0, hf0 = (np.ascontiguousarray(a) for a in (scene.x0, scene.v0, scene.f_ext[0]))
@@ -258,9 +284,11 @@ def main():
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "local step + RHS assembly (k_local, k_assemble)",
-                         "peak_kind": peak_kind, "avg_launch_us": local_ms * 1e3, "bytes_per_launch": local_bytes,
-                         "solve_avg_launch_us": solve_ms * 1e3},
+                         "frac": achieved / peak, "traffic": None, "kernel": kname, "peak_kind": peak_kind,
+                         "avg_launch_ms": kms, "bytes_per_launch": kbytes,
+                         "fwd_launch_ms": fwd_launch_ms, "bwd_launch_ms": bwd_launch_ms,
+                         "fwd_iter_bytes": fwd_iter_bytes, "bwd_iter_bytes": bwd_iter_bytes},
+            "forward_phase_ms_one_rollout": phases,
             "clocks": clk.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, k = oracle_sample(scene, 2)

@@ -75,6 +75,8 @@ typedef struct {
   int32_t local_fp32;     /* 1: FP32 local step with FP64 RHS accumulation; 0: FP64 */
   int32_t tr_mode;        /* PD_TR_ADAPT | PD_TR_NONE | PD_TR_CLAMP | PD_TR_ABS */
   int32_t adj_max_iters;  /* cap on backward PCG iterations per step */
+  int32_t persistent;     /* 1: one cooperative launch per rollout when its grid fits
+                             (falls back to per-phase kernels otherwise); 0: per-phase kernels */
   double eps_step;        /* relative q-step gate */
   double eps_res;         /* relative b-change gate */
   double eps_abs;         /* absolute term of both gates */
@@ -105,7 +107,8 @@ typedef struct {
 typedef struct pd_ctx pd_ctx;
 
 /* Default options (m = 5, k_max = 200, gate 1e-8 / 1e-6 / 1e-12, FP32 local,
- * adaptive trust region with eps_tr = 0.1, backward 1e-9 / 1000 iterations). */
+ * adaptive trust region with eps_tr = 0.1, backward 1e-9 / 1000 iterations,
+ * persistent launches on). */
 void pd_default_options(pd_options* out);
 
 /* Create a context: validates the mesh (indices in range, positive rest
@@ -202,15 +205,21 @@ int pd_get_stats(const pd_ctx* ctx, pd_stats* out);
 const char* pd_last_error(const pd_ctx* ctx);
 void pd_destroy(pd_ctx* ctx);
 
-/* Phase timers measured with CUDA events on the work stream while profiling
- * is enabled (pd_profile). "local" brackets the fused local step + RHS
- * assembly of every forward iteration; "solve" brackets the two SpMVs with S
- * of every forward iteration. */
+/* Phase timers while profiling is enabled (pd_profile). With per-phase
+ * kernels, CUDA events on the work stream bracket the fused local step + RHS
+ * assembly ("local") and the two SpMVs with S ("solve") of every forward
+ * iteration. Persistent rollouts are timed per phase on the device. */
 typedef struct {
   int64_t local_launches;
   double local_ms;
   int64_t solve_launches;
   double solve_ms;
+  /* persistent rollouts: time per phase measured on the device (globaltimer,
+   * block 0, including the grid barrier that ends the phase), summed over the
+   * rollouts run since profiling was enabled: begin, local step, assembly +
+   * gate, S b, S^T y, Anderson, update, step end + trust region */
+  double phase_ms[8];
+  double work_ms[8];  /* of which block 0's own work before the phase's barrier */
 } pd_profile_out;
 
 /* enable != 0 turns the phase timers on (and clears them); 0 turns them off. */

@@ -36,7 +36,8 @@ class pd_material(ctypes.Structure):
 
 class pd_options(ctypes.Structure):
     _fields_ = [("aa_m", c_int32), ("k_max", c_int32), ("fixed_iters", c_int32), ("local_fp32", c_int32),
-                ("tr_mode", c_int32), ("adj_max_iters", c_int32), ("eps_step", c_double), ("eps_res", c_double),
+                ("tr_mode", c_int32), ("adj_max_iters", c_int32), ("persistent", c_int32),
+                ("eps_step", c_double), ("eps_res", c_double),
                 ("eps_abs", c_double), ("eps_tr", c_double), ("adj_tol", c_double)]
 
 
@@ -50,7 +51,7 @@ class pd_stats(ctypes.Structure):
 
 class pd_profile_out(ctypes.Structure):
     _fields_ = [("local_launches", c_int64), ("local_ms", c_double), ("solve_launches", c_int64),
-                ("solve_ms", c_double)]
+                ("solve_ms", c_double), ("phase_ms", c_double * 8), ("work_ms", c_double * 8)]
 
 
 _lib = None

@@ -223,6 +223,7 @@ void pd_default_options(pd_options* o) {
   o->local_fp32 = 1;
   o->tr_mode = PD_TR_ADAPT;
   o->adj_max_iters = 1000;
+  o->persistent = 1;
   o->eps_step = 1e-8;
   o->eps_res = 1e-6;
   o->eps_abs = 1e-12;
@@ -334,10 +335,15 @@ int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_o
   if ((r = dalloc(c, &d.dQ, (size_t)m * nv3)) || (r = dalloc(c, &d.dG, (size_t)m * nv3))) return r;
   double* contrib;
   double* jac;
-  if ((r = dalloc(c, &contrib, 12 * (size_t)c->n_e)) || (r = dalloc(c, &jac, (size_t)pdk::kJacRec * c->n_e))) return r;
+  double* sstar;
+  if ((r = dalloc(c, &contrib, 12 * (size_t)c->n_e)) || (r = dalloc(c, &jac, (size_t)pdk::kJacRec * c->n_e)) ||
+      (r = dalloc(c, &sstar, 3 * (size_t)c->n_e)))
+    return r;
   d.contrib = contrib;
   d.jac = jac;
-  if ((r = dalloc(c, &d.red, (size_t)pdk::max_reduction_blocks(c->n_v, c->n_e) * pdk::kRed))) return r;
+  d.sstar = sstar;
+  if ((r = dalloc(c, &d.red, (size_t)std::max(pdk::max_reduction_blocks(c->n_v, c->n_e), pdk::kRedRows) * pdk::kRed)))
+    return r;
   if ((r = dalloc(c, &d.dw, c->n_e)) || (r = dalloc(c, &d.dbeta, c->n_e))) return r;
   if ((r = dalloc(c, &d.ctrl, 1))) return r;
   CK(cudaMemset(d.ctrl, 0, sizeof(Ctrl)));
@@ -568,47 +574,72 @@ int pd_rollout(pd_ctx* c, int32_t T, const double* q0, const double* v0, const d
   d.T = T;
   CK(cudaMemsetAsync(c->tau, 0, (size_t)T * sizeof(double), s));
   CK(cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), s));  // per-rollout statistics and flags
-  const int max_iter = c->opt.fixed_iters > 0 ? c->opt.fixed_iters : c->opt.k_max + 1;
-  const int* done_flag = &d.ctrl->done;
-  for (int t = 0; t < T; ++t) {
-    const double* qin = t == 0 ? q0d : c->sq;
-    const double* vin = t == 0 ? v0d : c->sv;
-    const double* fstep = fd ? fd + (f_stride ? (size_t)t * nv3 : 0) : nullptr;
-    pdk::launch_step_begin(d, s, qin, vin, fstep, t, c->ckpt + (size_t)t * nv3);
+  CK(cudaMemsetAsync(d.sstar, 0, 3 * sizeof(double) * (size_t)c->n_e, s));  // no prox warm start across rollouts
+  const int pgrid = c->opt.persistent ? pdk::persistent_grid(d) : 0;
+  if (pgrid > 0) {
+    // one cooperative launch for all T steps
+    pdk::RollArgs ra;
+    ra.T = T;
+    ra.q0 = q0d;
+    ra.v0 = v0d;
+    ra.fext = fd;
+    ra.f_stride = f_stride;
+    ra.qT = qT ? (hqo ? st_qo : qT) : nullptr;
+    ra.vT = vT ? (hvo ? st_vo : vT) : nullptr;
+    ra.ckpt = c->ckpt;
+    ra.sq = c->sq;
+    ra.sv = c->sv;
+    CK(pdk::launch_fwd_rollout(d, s, ra, pgrid));
     c->launches += 1;
-    CK(cudaGetLastError());
-    int it_idx = 0;
-    r = run_until(c, s, done_flag, max_iter, 4, [&]() {
-      c->launches += 6;
-      if (c->profiling) {
-        cudaEvent_t ev[4];
-        for (int i = 0; i < 4; ++i) ev[i] = prof_event(c);
-        for (int kind = 0; kind < 2; ++kind) {
-          c->prof_kind.push_back(kind);
-          c->prof_step.push_back(t);
-          c->prof_iter.push_back(it_idx);
+  } else {
+    const int max_iter = c->opt.fixed_iters > 0 ? c->opt.fixed_iters : c->opt.k_max + 1;
+    const int* done_flag = &d.ctrl->done;
+    for (int t = 0; t < T; ++t) {
+      const double* qin = t == 0 ? q0d : c->sq;
+      const double* vin = t == 0 ? v0d : c->sv;
+      const double* fstep = fd ? fd + (f_stride ? (size_t)t * nv3 : 0) : nullptr;
+      pdk::launch_step_begin(d, s, qin, vin, fstep, t, c->ckpt + (size_t)t * nv3);
+      c->launches += 1;
+      CK(cudaGetLastError());
+      int it_idx = 0;
+      r = run_until(c, s, done_flag, max_iter, 4, [&]() {
+        c->launches += 6;
+        if (c->profiling) {
+          cudaEvent_t ev[4];
+          for (int i = 0; i < 4; ++i) ev[i] = prof_event(c);
+          for (int kind = 0; kind < 2; ++kind) {
+            c->prof_kind.push_back(kind);
+            c->prof_step.push_back(t);
+            c->prof_iter.push_back(it_idx);
+          }
+          pdk::launch_iteration(d, s, ev);
+        } else {
+          pdk::launch_iteration(d, s, nullptr);
         }
-        pdk::launch_iteration(d, s, ev);
-      } else {
-        pdk::launch_iteration(d, s, nullptr);
-      }
-      ++it_idx;
-    });
-    if (r) return r;
-    CK(cudaGetLastError());
-    const bool last = t == T - 1;
-    double* qo = last && qT ? (hqo ? st_qo : qT) : c->sq;
-    double* vo = last && vT ? (hvo ? st_vo : vT) : c->sv;
-    pdk::launch_step_end(d, s, qo, vo, c->ckpt + (size_t)(t + 1) * nv3, c->tau);
-    c->launches += c->model == PD_NEOHOOKEAN ? 2 : 1;
-    CK(cudaGetLastError());
+        ++it_idx;
+      });
+      if (r) return r;
+      CK(cudaGetLastError());
+      const bool last = t == T - 1;
+      double* qo = last && qT ? (hqo ? st_qo : qT) : c->sq;
+      double* vo = last && vT ? (hvo ? st_vo : vT) : c->sv;
+      pdk::launch_step_end(d, s, qo, vo, c->ckpt + (size_t)(t + 1) * nv3, c->tau);
+      c->launches += c->model == PD_NEOHOOKEAN ? 2 : 1;
+      CK(cudaGetLastError());
+    }
   }
   if (hqo) CK(cudaMemcpyAsync(qT, st_qo, nv3 * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (hvo) CK(cudaMemcpyAsync(vT, st_vo, nv3 * sizeof(double), cudaMemcpyDeviceToHost, s));
   Ctrl hc;
   CK(cudaMemcpyAsync(&hc, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  if (c->profiling) prof_harvest(c, T);
+  if (c->profiling) {
+    prof_harvest(c, T);
+    for (int i = 0; i < 8; ++i) {
+      c->prof.phase_ms[i] += hc.phase_ns[i] * 1e-6;
+      c->prof.work_ms[i] += hc.work_ns[i] * 1e-6;
+    }
+  }
   c->last_T = T;
   pd_stats& st = c->stats;
   st.steps = T;
@@ -620,6 +651,7 @@ int pd_rollout(pd_ctx* c, int32_t T, const double* q0, const double* v0, const d
   st.tau_one = hc.tau_one;
   st.status_flags = hc.status;
   st.last_rho = hc.last_rho;
+  if (hc.status & 4) return fail(c, PD_ERR_TIMEOUT, "a grid barrier of the persistent rollout timed out");
   if (hc.status & 1) return fail(c, PD_ERR_NUMERIC, "non-finite value in the right-hand side");
   if (hc.not_converged) return fail(c, PD_ERR_NOT_CONVERGED, "%d step(s) hit k_max", hc.not_converged);
   return PD_OK;
@@ -665,31 +697,50 @@ int pd_backward(pd_ctx* c, const double* dqT, const double* dvT, double* dq0, do
   double* dnud = h_nu ? st_nu : dnu;
   double* dfd = h_df ? st_df : df_ext;
   if (dfd && df_stride == 0) CK(cudaMemsetAsync(dfd, 0, nv3 * sizeof(double), s));
-  pdk::launch_bwd_begin(d, s, dqTd, dvTd);
-  c->launches += 1;
-  CK(cudaGetLastError());
-  const int* done_flag = &d.ctrl->adj_done;
-  for (int t = T - 1; t >= 0; --t) {
-    const double* qstar = c->ckpt + (size_t)(t + 1) * nv3;
-    const double* qt = c->ckpt + (size_t)t * nv3;
-    pdk::launch_bwd_setup(d, s, qstar, c->tau + t);
-    pdk::launch_bwd_init(d, s);
-    c->launches += 5;
-    CK(cudaGetLastError());
-    r = run_until(c, s, done_flag, c->opt.adj_max_iters, 4, [&]() {
-      c->launches += 7;
-      pdk::launch_pcg_iteration(d, s);
-    });
-    if (r) return r;
-    double* df_t = dfd ? (df_stride ? dfd + (size_t)t * nv3 : dfd) : nullptr;
-    pdk::launch_route(d, s, qstar, qt, c->tau + t, df_t, df_stride == 0 ? 1 : 0);
+  const int pgrid = c->opt.persistent ? pdk::persistent_grid_bwd(d) : 0;
+  if (pgrid > 0) {
+    // one cooperative launch for the adjoint of all T steps
+    pdk::BwdArgs ba;
+    ba.T = T;
+    ba.dqT = dqTd;
+    ba.dvT = dvTd;
+    ba.dq0 = dq0d;
+    ba.dv0 = dv0d;
+    ba.dE = dEd;
+    ba.dnu = dnud;
+    ba.df = dfd;
+    ba.df_stride = df_stride;
+    ba.ckpt = c->ckpt;
+    CK(cudaMemsetAsync(&d.ctrl->bar_count, 0, 2 * sizeof(unsigned int), s));
+    CK(pdk::launch_bwd_rollout(d, s, ba, pgrid));
+    c->launches += 1;
+  } else {
+    pdk::launch_bwd_begin(d, s, dqTd, dvTd);
     c->launches += 1;
     CK(cudaGetLastError());
+    const int* done_flag = &d.ctrl->adj_done;
+    for (int t = T - 1; t >= 0; --t) {
+      const double* qstar = c->ckpt + (size_t)(t + 1) * nv3;
+      const double* qt = c->ckpt + (size_t)t * nv3;
+      pdk::launch_bwd_setup(d, s, qstar, c->tau + t);
+      pdk::launch_bwd_init(d, s);
+      c->launches += 5;
+      CK(cudaGetLastError());
+      r = run_until(c, s, done_flag, c->opt.adj_max_iters, 4, [&]() {
+        c->launches += 7;
+        pdk::launch_pcg_iteration(d, s);
+      });
+      if (r) return r;
+      double* df_t = dfd ? (df_stride ? dfd + (size_t)t * nv3 : dfd) : nullptr;
+      pdk::launch_route(d, s, qstar, qt, c->tau + t, df_t, df_stride == 0 ? 1 : 0);
+      c->launches += 1;
+      CK(cudaGetLastError());
+    }
+    pdk::launch_chain(d, s, dEd, dnud);
+    pdk::launch_bwd_finish(d, s, dq0d, dv0d);
+    c->launches += 2;
+    CK(cudaGetLastError());
   }
-  pdk::launch_chain(d, s, dEd, dnud);
-  pdk::launch_bwd_finish(d, s, dq0d, dv0d);
-  c->launches += 2;
-  CK(cudaGetLastError());
   if (h_q0) CK(cudaMemcpyAsync(dq0, st_q0, nv3 * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (h_v0) CK(cudaMemcpyAsync(dv0, st_v0, nv3 * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (h_E) CK(cudaMemcpyAsync(dE, st_E, c->n_e * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -702,6 +753,7 @@ int pd_backward(pd_ctx* c, const double* dqT, const double* dvT, double* dq0, do
   c->stats.adj_iters_max = hc.adj_iters_max;
   c->stats.adj_not_converged = hc.adj_not_converged;
   c->stats.status_flags = hc.status;
+  if (hc.status & 4) return fail(c, PD_ERR_TIMEOUT, "a grid barrier of the persistent adjoint timed out");
   if (hc.status & 2) return fail(c, PD_ERR_NUMERIC, "adjoint operator A - K not positive along a CG direction");
   if (hc.adj_not_converged) return fail(c, PD_ERR_NOT_CONVERGED, "%d adjoint solve(s) hit adj_max_iters", hc.adj_not_converged);
   return PD_OK;

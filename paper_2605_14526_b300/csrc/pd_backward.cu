@@ -1,9 +1,9 @@
-// Backward kernels (Sec. 4.3 trust region, Sec. 4.7 adjoint, Alg. 2).
+// Backward pass (Sec. 4.3 trust region, Sec. 4.7 adjoint, Alg. 2).
 //
 // Per step t (walked from T-1 down to 0) with q* = q_{t+1}:
 //   setup   per element: SVD of F(q*), prox stretches sigma*, the filtered
 //           stretch Jacobian J = k H~(tau)^+ (eq. tr_blend, tr_ift) and the
-//           off-diagonal coefficients of the spectral differential; stored as
+//           off-diagonal coefficients of the spectral differential, stored as
 //           a compact record so that K = db/dq is applied matrix-free.
 //   solve   (A - K) mu = q_bar by conjugate gradients preconditioned with the
 //           factor of A (z = S^T S r), K applied per element (eq. db_dq).
@@ -11,15 +11,23 @@
 //           element (SVD and prox recomputed in FP64); mesh-mean
 //           sensitivities reduced.
 // After the last step, the chain to E_e and nu (eq. lame and the weights).
+// Item bodies and scalar logic are shared by the per-phase kernels and the
+// persistent backward kernel (one cooperative launch for all T steps).
 #include <cuda_runtime.h>
 
-#include "pd_common.cuh"
+#include "pd_grid.cuh"
 #include "pd_launch.h"
+#include "pd_phases.cuh"
 
 namespace pdk {
 
 // record layout: U[9] V[9] sF[3] ss[3] J[6] (00 11 22 01 02 12) S[3] T[3] (pairs 01 02 12)
 enum { R_U = 0, R_V = 9, R_SF = 18, R_SS = 21, R_J = 24, R_S = 30, R_T = 33 };
+
+struct BwdState {
+  int adj_k, adj_done, status, adj_iters_total, adj_iters_max, adj_not_converged;
+  double rz, rz0, alpha, beta, acc_mu, acc_lam, acc_k, dnu_acc;
+};
 
 template <typename T>
 __device__ __forceinline__ void filtered_jacobian(const T* ss, const NHMean<T>& m, T tau, T* J) {
@@ -57,10 +65,10 @@ __device__ __forceinline__ void filtered_jacobian(const T* ss, const NHMean<T>& 
       J[3 * i + j] = m.k * (Q[3 * i] * inv[0] * Q[3 * j] + Q[3 * i + 1] * inv[1] * Q[3 * j + 1] + Q[3 * i + 2] * inv[2] * Q[3 * j + 2]);
 }
 
+// ------------------------------------------------------------ per-item bodies
+
 template <typename T>
-__global__ void __launch_bounds__(kTetBlock) k_bwd_setup(Dev d, const double* __restrict__ qstar, const double* tau_t) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= d.n_e) return;
+__device__ __forceinline__ void bwd_setup_item(const Dev& d, int e, const double* qstar, double tau) {
   int4 tv;
   T Bm[9], coef;
   load_elem<T>(d, e, tv, Bm, coef);
@@ -73,15 +81,12 @@ __global__ void __launch_bounds__(kTetBlock) k_bwd_setup(Dev d, const double* __
   if (d.model == 1) {
     NHMean<T> m{(T)d.mu_bar, (T)d.lam_bar, (T)d.k_bar};
     nh_prox<T>(sF, m, ss);
-    filtered_jacobian<T>(ss, m, (T)(*tau_t), J);
+    filtered_jacobian<T>(ss, m, (T)tau, J);
     // (s*_i - s*_j)/(s_i - s_j) = k / (k + mu + (mu - lam ln J*)/(s*_i s*_j)),
     // exact at the prox stationarity and free of cancellation near s_i = s_j
     const T lnJ = dlog(ss[0] * ss[1] * ss[2]);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int i = pi[c], j = pj[c];
-      Sp[c] = m.k / (m.k + m.mu + (m.mu - m.lam * lnJ) / (ss[i] * ss[j]));
-    }
+    for (int c = 0; c < 3; ++c) Sp[c] = m.k / (m.k + m.mu + (m.mu - m.lam * lnJ) / (ss[pi[c]] * ss[pj[c]]));
   } else {
     ss[0] = ss[1] = ss[2] = T(1);
 #pragma unroll
@@ -89,10 +94,9 @@ __global__ void __launch_bounds__(kTetBlock) k_bwd_setup(Dev d, const double* __
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const int i = pi[c], j = pj[c];
-    T sm = sF[i] + sF[j];
+    T sm = sF[pi[c]] + sF[pj[c]];
     if (dabs(sm) < T(1e-20)) sm = T(1e-20);
-    Tp[c] = (ss[i] + ss[j]) / sm;
+    Tp[c] = (ss[pi[c]] + ss[pj[c]]) / sm;
   }
   T* r = reinterpret_cast<T*>(d.jac) + kJacRec * (size_t)e;
 #pragma unroll
@@ -111,12 +115,9 @@ __global__ void __launch_bounds__(kTetBlock) k_bwd_setup(Dev d, const double* __
   r[R_J + 3] = J[1]; r[R_J + 4] = J[2]; r[R_J + 5] = J[5];
 }
 
-// contributions of K p for one element: coef * G^T (dp/dF) G p
+// corner contributions of K p for one element: coef * G^T (dp/dF) G p
 template <typename T>
-__global__ void __launch_bounds__(kTetBlock) k_kapply(Dev d, const double* __restrict__ pv) {
-  if (d.ctrl->adj_done) return;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= d.n_e) return;
+__device__ __forceinline__ void kapply_item(const Dev& d, int e, const double* pv) {
   int4 tv;
   T Bm[9], coef;
   load_elem<T>(d, e, tv, Bm, coef);
@@ -129,8 +130,7 @@ __global__ void __launch_bounds__(kTetBlock) k_kapply(Dev d, const double* __res
   }
   T dF[9];
   deform<T>(pv, tv, Bm, dF);
-  // Mh = U^T dF V
-  T W[9], Mh[9];
+  T W[9], Mh[9];  // Mh = U^T dF V
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -153,12 +153,11 @@ __global__ void __launch_bounds__(kTetBlock) k_kapply(Dev d, const double* __res
     D[3 * i + j] = r[R_S + c] * sym + r[R_T + c] * skw;
     D[3 * j + i] = r[R_S + c] * sym - r[R_T + c] * skw;
   }
-  // dp = U D V^T
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) W[3 * i + j] = U[3 * i] * D[j] + U[3 * i + 1] * D[3 + j] + U[3 * i + 2] * D[6 + j];
-  T dp[9];
+  T dp[9];  // dp = U D V^T
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -170,15 +169,7 @@ __global__ void __launch_bounds__(kTetBlock) k_kapply(Dev d, const double* __res
   for (int i = 0; i < 12; ++i) out[i] = c12[i];
 }
 
-// ------------------------------------------------------------ PCG
-
-__global__ void k_bwd_begin(Dev d, const double* __restrict__ dqT, const double* __restrict__ dvT) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) {
-    Ctrl* c = d.ctrl;
-    c->acc_mu = c->acc_lam = c->acc_k = 0.0;
-    c->adj_iters_total = c->adj_iters_max = c->adj_not_converged = 0;
-  }
+__device__ __forceinline__ void bwd_begin_item(const Dev& d, int i, const double* dqT, const double* dvT) {
   if (i < d.n_e) {
     d.dw[i] = 0.0;
     d.dbeta[i] = 0.0;
@@ -192,18 +183,14 @@ __global__ void k_bwd_begin(Dev d, const double* __restrict__ dqT, const double*
   }
 }
 
-// q_bar = dL/dq* + dL/dv*/h; r = q_bar; mu = 0
-__global__ void k_bwd_init(Dev d) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v == 0) {
-    d.ctrl->adj_k = 0;
-    d.ctrl->adj_done = 0;
-  }
-  if (v >= d.n_v) return;
+// q_bar = dL/dq* + dL/dv*/h; r = q_bar; mu = 0; r in elimination order
+__device__ __forceinline__ void bwd_init_item(const Dev& d, int v) {
   const bool pin = d.pinned[v];
+  double rv[3];
   for (int a = 0; a < 3; ++a) {
     const size_t o = 3 * (size_t)v + a;
     const double qb = pin ? 0.0 : d.gq[o] + d.gv[o] / d.h;
+    rv[a] = qb;
     d.qbar[o] = qb;
     d.r[o] = qb;
     d.mu[o] = 0.0;
@@ -213,77 +200,44 @@ __global__ void k_bwd_init(Dev d) {
   if (!pin) {
     const int pos = d.iperm[v];
     for (int a = 0; a < 3; ++a) {
-      d.bperm[3 * (size_t)pos + a] = d.r[3 * (size_t)v + a];
+      d.bperm[3 * (size_t)pos + a] = rv[a];
       d.y[3 * (size_t)pos + a] = 0.0;
     }
   }
 }
 
-__global__ void __launch_bounds__(kVtxBlock) k_pcg_init_z(Dev d) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  double part[1] = {0.0};
-  if (v < d.n_v && !d.pinned[v]) {
-    for (int a = 0; a < 3; ++a) {
-      const size_t o = 3 * (size_t)v + a;
-      part[0] += d.r[o] * d.z[o];
-      d.pdir[o] = d.z[o];
-    }
-  }
-  block_reduce_store<1>(part, d.red);
-  if (last_block(&d.ctrl->ticket[TK_PCG_INIT])) {
-    if (threadIdx.x == 0) {
-      Ctrl* c = d.ctrl;
-      const double rz = sum_partials(d.red, gridDim.x, 0);
-      c->rz = rz;
-      c->rz0 = rz;
-      if (!(rz > 0.0)) c->adj_done = 1;
-    }
+// p = z (first direction); partial r . z
+__device__ __forceinline__ void init_z_item(const Dev& d, int v, double* part) {
+  if (d.pinned[v]) return;
+  for (int a = 0; a < 3; ++a) {
+    const size_t o = 3 * (size_t)v + a;
+    part[0] += d.r[o] * d.z[o];
+    d.pdir[o] = d.z[o];
   }
 }
 
-// w = A p - K p, alpha = r.z / p.w
+// w = A p - K p; partial p . w
 template <typename T>
-__global__ void __launch_bounds__(kVtxBlock) k_pcg_w(Dev d) {
-  if (d.ctrl->adj_done) return;
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  double part[1] = {0.0};
-  if (v < d.n_v && !d.pinned[v]) {
-    double acc[3] = {0.0, 0.0, 0.0};
-    gather_contrib<T>(d, v, acc);
-    double ap[3] = {0.0, 0.0, 0.0};
-    for (int p = d.A_ptr[v]; p < d.A_ptr[v + 1]; ++p) {
-      const int u = d.A_idx[p];
-      const double a = d.A_val[p];
-      for (int i = 0; i < 3; ++i) ap[i] += a * d.pdir[3 * (size_t)u + i];
-    }
-    for (int i = 0; i < 3; ++i) {
-      const size_t o = 3 * (size_t)v + i;
-      const double w = ap[i] - acc[i];
-      d.w[o] = w;
-      part[0] += d.pdir[o] * w;
-    }
+__device__ __forceinline__ void pcg_w_item(const Dev& d, int v, double* part) {
+  if (d.pinned[v]) return;
+  double acc[3] = {0.0, 0.0, 0.0};
+  gather_contrib<T>(d, v, acc);
+  double ap[3] = {0.0, 0.0, 0.0};
+  for (int p = d.A_ptr[v]; p < d.A_ptr[v + 1]; ++p) {
+    const int u = d.A_idx[p];
+    const double a = d.A_val[p];
+    for (int i = 0; i < 3; ++i) ap[i] += a * d.pdir[3 * (size_t)u + i];
   }
-  block_reduce_store<1>(part, d.red);
-  if (last_block(&d.ctrl->ticket[TK_PCG_W])) {
-    if (threadIdx.x == 0) {
-      Ctrl* c = d.ctrl;
-      const double pw = sum_partials(d.red, gridDim.x, 0);
-      if (!(pw > 0.0) || !isfinite(pw)) {  // (A - K) not positive along p
-        c->status |= 2;
-        c->adj_done = 1;
-        c->alpha = 0.0;
-      } else {
-        c->alpha = c->rz / pw;
-      }
-    }
+  for (int i = 0; i < 3; ++i) {
+    const size_t o = 3 * (size_t)v + i;
+    const double w = ap[i] - acc[i];
+    d.w[o] = w;
+    part[0] += d.pdir[o] * w;
   }
 }
 
-__global__ void __launch_bounds__(kVtxBlock) k_pcg_r(Dev d) {
-  if (d.ctrl->adj_done) return;
-  const double alpha = d.ctrl->alpha;
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= d.n_v || d.pinned[v]) return;
+__device__ __forceinline__ void pcg_r_item(const Dev& d, int v, double alpha) {
+  if (d.pinned[v]) return;
   const int pos = d.iperm[v];
   for (int i = 0; i < 3; ++i) {
     const size_t o = 3 * (size_t)v + i;
@@ -295,27 +249,249 @@ __global__ void __launch_bounds__(kVtxBlock) k_pcg_r(Dev d) {
   }
 }
 
+__device__ __forceinline__ void pcg_z_item(const Dev& d, int v, double* part) {
+  if (d.pinned[v]) return;
+  for (int i = 0; i < 3; ++i) part[0] += d.r[3 * (size_t)v + i] * d.z[3 * (size_t)v + i];
+}
+
+__device__ __forceinline__ void pcg_p_item(const Dev& d, int v, double beta) {
+  if (d.pinned[v]) return;
+  for (int i = 0; i < 3; ++i) {
+    const size_t o = 3 * (size_t)v + i;
+    d.pdir[o] = d.z[o] + beta * d.pdir[o];
+  }
+}
+
+// dL/dq_t = (1 + alpha h) M/h^2 mu + B mu / h - v_bar/h, dL/dv_t = M/h mu, dL/df = mu
+__device__ __forceinline__ void route_vertex_item(const Dev& d, int v, double* df, int df_acc) {
+  if (d.pinned[v]) {
+    for (int i = 0; i < 3; ++i) {
+      d.gq[3 * v + i] = 0.0;
+      d.gv[3 * v + i] = 0.0;
+      if (df && !df_acc) df[3 * v + i] = 0.0;
+    }
+    return;
+  }
+  const double m = d.mass[v], h = d.h;
+  double bmu[3] = {0.0, 0.0, 0.0};
+  for (int p = d.B_ptr[v]; p < d.B_ptr[v + 1]; ++p) {
+    const int u = d.B_idx[p];
+    const double b = d.B_val[p];
+    for (int i = 0; i < 3; ++i) bmu[i] += b * d.mu[3 * (size_t)u + i];
+  }
+  for (int i = 0; i < 3; ++i) {
+    const size_t o = 3 * (size_t)v + i;
+    const double mu = d.mu[o];
+    const double gv_next = d.gv[o];
+    d.gq[o] = (1.0 + d.alpha_d * h) * m / (h * h) * mu + bmu[i] / h - gv_next / h;
+    d.gv[o] = m / h * mu;
+    if (df) df[o] = df_acc ? df[o] + mu : mu;
+  }
+}
+
+// per element, in FP64: dL/dw_e = V_e <G mu, p* - F>, dL/dbeta_e, and the
+// mean-sensitivity partials; p* - F = U diag(s* - s_F) V^T is a small
+// difference of O(1) quantities, so the SVD and prox are recomputed in double
+__device__ __forceinline__ void route_elem_item(const Dev& d, int e, const double* qstar, const double* qt, double tau,
+                                                double* part) {
+  const int4 tv = d.tets[e];
+  double Bm[9];
+  for (int i = 0; i < 9; ++i) Bm[i] = d.Bm64[9 * (size_t)e + i];
+  double Gm[9], Fs[9], Ft[9];
+  deform<double>(d.mu, tv, Bm, Gm);
+  deform<double>(qstar, tv, Bm, Fs);
+  deform<double>(qt, tv, Bm, Ft);
+  double gb = 0.0;
+  for (int i = 0; i < 9; ++i) gb += Gm[i] * (Fs[i] - Ft[i]);
+  double U[9], V[9], sf[3], ss[3];
+  svd3<double>(Fs, U, sf, V);
+  NHMean<double> m{d.mu_bar, d.lam_bar, d.k_bar};
+  if (d.model == 1) {
+    nh_prox<double>(sf, m, ss);
+  } else {
+    ss[0] = ss[1] = ss[2] = 1.0;
+  }
+  double Md[3];  // diagonal of U^T (G mu) V
+  for (int i = 0; i < 3; ++i) {
+    double acc = 0.0;
+    for (int k = 0; k < 3; ++k)
+      for (int l = 0; l < 3; ++l) acc += U[3 * k + i] * Gm[3 * k + l] * V[3 * l + i];
+    Md[i] = acc;
+  }
+  double dw = 0.0;
+  for (int i = 0; i < 3; ++i) dw += (ss[i] - sf[i]) * Md[i];
+  d.dw[e] += d.vol[e] * dw;
+  d.dbeta[e] += -d.vol[e] / d.h * gb;
+  if (d.model == 1) {
+    double Jm[9];
+    filtered_jacobian<double>(ss, m, tau, Jm);
+    const double lnJ = log(ss[0] * ss[1] * ss[2]);
+    const double k = d.k_bar, coef = d.coef64[e];
+    double gk[3], gm[3], gl[3];
+    for (int i = 0; i < 3; ++i) {
+      gk[i] = ss[i] - sf[i];
+      gm[i] = ss[i] - 1.0 / ss[i];
+      gl[i] = lnJ / ss[i];
+    }
+    for (int i = 0; i < 3; ++i) {
+      double sk = 0.0, sm = 0.0, sl = 0.0;
+      for (int j = 0; j < 3; ++j) {
+        sk += Jm[3 * i + j] * gk[j];
+        sm += Jm[3 * i + j] * gm[j];
+        sl += Jm[3 * i + j] * gl[j];
+      }
+      part[0] += -coef * Md[i] * sm / k;
+      part[1] += -coef * Md[i] * sl / k;
+      part[2] += -coef * Md[i] * sk / k;
+    }
+  }
+}
+
+// dL/dE_e from dL/dw_e, dL/dbeta_e and the mean sensitivities; nu partials
+__device__ __forceinline__ void chain_item(const Dev& d, int e, double* dE, double am, double al, double ak,
+                                           double* part) {
+  const double nu = d.nu, E = d.E[e];
+  const bool nh = d.model == 1;
+  const double dmu_dE = 1.0 / (2.0 * (1.0 + nu));
+  const double dlam_dE = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  const double dmu_dnu = -E / (2.0 * (1.0 + nu) * (1.0 + nu));
+  const double den = (1.0 + nu) * (1.0 - 2.0 * nu);
+  const double dlam_dnu = E * (1.0 + 2.0 * nu * nu) / (den * den);
+  const double dw_dE = 2.0 * dmu_dE + (nh ? dlam_dE : 0.0);
+  const double dw_dnu = 2.0 * dmu_dnu + (nh ? dlam_dnu : 0.0);
+  const double cb = d.mu_ref > 0.0 ? d.beta0 / d.mu_ref : 0.0;
+  const double inv_n = 1.0 / d.n_e;
+  if (dE) dE[e] = d.dw[e] * dw_dE + d.dbeta[e] * cb * dmu_dE + (am * dmu_dE + al * dlam_dE + ak * dw_dE) * inv_n;
+  part[0] += d.dw[e] * dw_dnu + d.dbeta[e] * cb * dmu_dnu;
+  part[1] += dmu_dnu;
+  part[2] += dlam_dnu;
+  part[3] += dw_dnu;
+}
+
+// ------------------------------------------------------------ scalar logic
+
+template <class St>
+__device__ __forceinline__ void init_z_finish(St* c, const double* s) {
+  c->rz = s[0];
+  c->rz0 = s[0];
+  c->adj_k = 0;
+  c->adj_done = s[0] > 0.0 ? 0 : 1;
+}
+
+template <class St>
+__device__ __forceinline__ void pcg_w_finish(St* c, const double* s) {
+  const double pw = s[0];
+  if (!(pw > 0.0) || !isfinite(pw)) {  // (A - K) not positive along p
+    c->status |= 2;
+    c->adj_done = 1;
+    c->alpha = 0.0;
+  } else {
+    c->alpha = c->rz / pw;
+  }
+}
+
+template <class St>
+__device__ __forceinline__ void pcg_z_finish(const Dev& d, St* c, const double* s) {
+  const double rz = s[0];
+  c->beta = rz / c->rz;
+  c->rz = rz;
+  c->adj_k += 1;
+  if (!(rz > d.adj_tol * d.adj_tol * c->rz0)) {
+    c->adj_done = 1;
+  } else if (c->adj_k >= d.adj_max_iters) {
+    c->adj_done = 1;
+    c->adj_not_converged += 1;
+  }
+}
+
+template <class St>
+__device__ __forceinline__ void route_finish(St* c, const double* s) {
+  c->acc_mu += s[0];
+  c->acc_lam += s[1];
+  c->acc_k += s[2];
+  c->adj_iters_total += c->adj_k;
+  if (c->adj_k > c->adj_iters_max) c->adj_iters_max = c->adj_k;
+}
+
+__device__ __forceinline__ double chain_nu(const Dev& d, double am, double al, double ak, const double* s) {
+  const double inv_n = 1.0 / d.n_e;
+  return s[0] + (am * s[1] + al * s[2] + ak * s[3]) * inv_n;
+}
+
+// ------------------------------------------------------------ per-phase kernels
+
+__global__ void k_bwd_begin(Dev d, const double* dqT, const double* dvT) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    Ctrl* c = d.ctrl;
+    c->acc_mu = c->acc_lam = c->acc_k = 0.0;
+    c->adj_iters_total = c->adj_iters_max = c->adj_not_converged = 0;
+  }
+  bwd_begin_item(d, i, dqT, dvT);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTetBlock) k_bwd_setup(Dev d, const double* qstar, const double* tau_t) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < d.n_e) bwd_setup_item<T>(d, e, qstar, *tau_t);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTetBlock) k_kapply(Dev d, const double* pv) {
+  if (d.ctrl->adj_done) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < d.n_e) kapply_item<T>(d, e, pv);
+}
+
+__global__ void k_bwd_init(Dev d) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v == 0) {
+    d.ctrl->adj_k = 0;
+    d.ctrl->adj_done = 0;
+  }
+  if (v < d.n_v) bwd_init_item(d, v);
+}
+
+__global__ void __launch_bounds__(kVtxBlock) k_pcg_init_z(Dev d) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  double part[1] = {0.0};
+  if (v < d.n_v) init_z_item(d, v, part);
+  block_reduce_store<1>(part, d.red);
+  if (last_block(&d.ctrl->ticket[TK_PCG_INIT]) && threadIdx.x == 0) {
+    double s[1] = {sum_partials(d.red, gridDim.x, 0)};
+    init_z_finish(d.ctrl, s);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kVtxBlock) k_pcg_w(Dev d) {
+  if (d.ctrl->adj_done) return;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  double part[1] = {0.0};
+  if (v < d.n_v) pcg_w_item<T>(d, v, part);
+  block_reduce_store<1>(part, d.red);
+  if (last_block(&d.ctrl->ticket[TK_PCG_W]) && threadIdx.x == 0) {
+    double s[1] = {sum_partials(d.red, gridDim.x, 0)};
+    pcg_w_finish(d.ctrl, s);
+  }
+}
+
+__global__ void __launch_bounds__(kVtxBlock) k_pcg_r(Dev d) {
+  if (d.ctrl->adj_done) return;
+  const double alpha = d.ctrl->alpha;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < d.n_v) pcg_r_item(d, v, alpha);
+}
+
 __global__ void __launch_bounds__(kVtxBlock) k_pcg_z(Dev d) {
   if (d.ctrl->adj_done) return;
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   double part[1] = {0.0};
-  if (v < d.n_v && !d.pinned[v])
-    for (int i = 0; i < 3; ++i) part[0] += d.r[3 * (size_t)v + i] * d.z[3 * (size_t)v + i];
+  if (v < d.n_v) pcg_z_item(d, v, part);
   block_reduce_store<1>(part, d.red);
-  if (last_block(&d.ctrl->ticket[TK_PCG_Z])) {
-    if (threadIdx.x == 0) {
-      Ctrl* c = d.ctrl;
-      const double rz = sum_partials(d.red, gridDim.x, 0);
-      c->beta = rz / c->rz;
-      c->rz = rz;
-      c->adj_k += 1;
-      if (!(rz > d.adj_tol * d.adj_tol * c->rz0)) {
-        c->adj_done = 1;
-      } else if (c->adj_k >= d.adj_max_iters) {
-        c->adj_done = 1;
-        c->adj_not_converged += 1;
-      }
-    }
+  if (last_block(&d.ctrl->ticket[TK_PCG_Z]) && threadIdx.x == 0) {
+    double s[1] = {sum_partials(d.red, gridDim.x, 0)};
+    pcg_z_finish(d, d.ctrl, s);
   }
 }
 
@@ -323,161 +499,146 @@ __global__ void __launch_bounds__(kVtxBlock) k_pcg_p(Dev d) {
   if (d.ctrl->adj_done) return;
   const double beta = d.ctrl->beta;
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= d.n_v || d.pinned[v]) return;
-  for (int i = 0; i < 3; ++i) {
-    const size_t o = 3 * (size_t)v + i;
-    d.pdir[o] = d.z[o] + beta * d.pdir[o];
-  }
+  if (v < d.n_v) pcg_p_item(d, v, beta);
 }
 
-// ------------------------------------------------------------ routing
-
-__global__ void __launch_bounds__(kVtxBlock) k_route(Dev d, const double* __restrict__ qstar,
-                                                     const double* __restrict__ qt, const double* tau_t,
-                                                     double* __restrict__ df, int df_acc) {
+__global__ void __launch_bounds__(kVtxBlock) k_route(Dev d, const double* qstar, const double* qt, const double* tau_t,
+                                                     double* df, int df_acc) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   double part[3] = {0.0, 0.0, 0.0};
-  if (tid == 0) {
-    Ctrl* c = d.ctrl;
-    c->adj_iters_total += c->adj_k;
-    if (c->adj_k > c->adj_iters_max) c->adj_iters_max = c->adj_k;
-  }
-  if (tid < d.n_v) {
-    const int v = tid;
-    if (d.pinned[v]) {
-      for (int i = 0; i < 3; ++i) {
-        d.gq[3 * v + i] = 0.0;
-        d.gv[3 * v + i] = 0.0;
-        if (df && !df_acc) df[3 * v + i] = 0.0;
-      }
-    } else {
-      const double m = d.mass[v], h = d.h;
-      double bmu[3] = {0.0, 0.0, 0.0};
-      for (int p = d.B_ptr[v]; p < d.B_ptr[v + 1]; ++p) {
-        const int u = d.B_idx[p];
-        const double b = d.B_val[p];
-        for (int i = 0; i < 3; ++i) bmu[i] += b * d.mu[3 * (size_t)u + i];
-      }
-      for (int i = 0; i < 3; ++i) {
-        const size_t o = 3 * (size_t)v + i;
-        const double mu = d.mu[o];
-        const double gv_next = d.gv[o];
-        d.gq[o] = (1.0 + d.alpha_d * h) * m / (h * h) * mu + bmu[i] / h - gv_next / h;
-        d.gv[o] = m / h * mu;
-        if (df) df[o] = df_acc ? df[o] + mu : mu;
-      }
-    }
-  } else if (tid < d.n_v + d.n_e) {
-    // per element, in FP64: p* - F = U diag(s* - s_F) V^T is a small
-    // difference of O(1) quantities, so the SVD and prox are recomputed here
-    // in double rather than read from the FP32 record
-    const int e = tid - d.n_v;
-    const int4 tv = d.tets[e];
-    double Bm[9];
-    for (int i = 0; i < 9; ++i) Bm[i] = d.Bm64[9 * (size_t)e + i];
-    double Gm[9], Fs[9], Ft[9];
-    deform<double>(d.mu, tv, Bm, Gm);
-    deform<double>(qstar, tv, Bm, Fs);
-    deform<double>(qt, tv, Bm, Ft);
-    double gb = 0.0;
-    for (int i = 0; i < 9; ++i) gb += Gm[i] * (Fs[i] - Ft[i]);
-    double U[9], V[9], sf[3], ss[3];
-    svd3<double>(Fs, U, sf, V);
-    NHMean<double> m{d.mu_bar, d.lam_bar, d.k_bar};
-    if (d.model == 1) {
-      nh_prox<double>(sf, m, ss);
-    } else {
-      ss[0] = ss[1] = ss[2] = 1.0;
-    }
-    double Md[3];  // diagonal of U^T (G mu) V
-    for (int i = 0; i < 3; ++i) {
-      double acc = 0.0;
-      for (int k = 0; k < 3; ++k)
-        for (int l = 0; l < 3; ++l) acc += U[3 * k + i] * Gm[3 * k + l] * V[3 * l + i];
-      Md[i] = acc;
-    }
-    double dw = 0.0;
-    for (int i = 0; i < 3; ++i) dw += (ss[i] - sf[i]) * Md[i];
-    d.dw[e] += d.vol[e] * dw;
-    d.dbeta[e] += -d.vol[e] / d.h * gb;
-    if (d.model == 1) {
-      double Jm[9];
-      filtered_jacobian<double>(ss, m, *tau_t, Jm);
-      const double lnJ = log(ss[0] * ss[1] * ss[2]);
-      const double k = d.k_bar, coef = d.coef64[e];
-      double gk[3], gm[3], gl[3];
-      for (int i = 0; i < 3; ++i) {
-        gk[i] = ss[i] - sf[i];
-        gm[i] = ss[i] - 1.0 / ss[i];
-        gl[i] = lnJ / ss[i];
-      }
-      for (int i = 0; i < 3; ++i) {
-        double sk = 0.0, sm = 0.0, sl = 0.0;
-        for (int j = 0; j < 3; ++j) {
-          sk += Jm[3 * i + j] * gk[j];
-          sm += Jm[3 * i + j] * gm[j];
-          sl += Jm[3 * i + j] * gl[j];
-        }
-        part[0] += -coef * Md[i] * sm / k;
-        part[1] += -coef * Md[i] * sl / k;
-        part[2] += -coef * Md[i] * sk / k;
-      }
-    }
-  }
+  if (tid < d.n_v) route_vertex_item(d, tid, df, df_acc);
+  else if (tid < d.n_v + d.n_e) route_elem_item(d, tid - d.n_v, qstar, qt, *tau_t, part);
   block_reduce_store<3>(part, d.red);
-  if (last_block(&d.ctrl->ticket[TK_ROUTE])) {
-    if (threadIdx.x == 0) {
-      Ctrl* c = d.ctrl;
-      c->acc_mu += sum_partials(d.red, gridDim.x, 0);
-      c->acc_lam += sum_partials(d.red, gridDim.x, 1);
-      c->acc_k += sum_partials(d.red, gridDim.x, 2);
-    }
+  if (last_block(&d.ctrl->ticket[TK_ROUTE]) && threadIdx.x == 0) {
+    double s[3];
+    for (int j = 0; j < 3; ++j) s[j] = sum_partials(d.red, gridDim.x, j);
+    route_finish(d.ctrl, s);
   }
 }
 
-// dL/dE_e and dL/dnu from dL/dw_e, dL/dbeta_e and the mean sensitivities
-__global__ void __launch_bounds__(kVtxBlock) k_chain(Dev d, double* __restrict__ dE, double* __restrict__ dnu) {
+__global__ void __launch_bounds__(kVtxBlock) k_chain(Dev d, double* dE, double* dnu) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   double part[4] = {0.0, 0.0, 0.0, 0.0};
   const Ctrl* c = d.ctrl;
-  if (e < d.n_e) {
-    const double nu = d.nu, E = d.E[e];
-    const bool nh = d.model == 1;
-    const double dmu_dE = 1.0 / (2.0 * (1.0 + nu));
-    const double dlam_dE = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
-    const double dmu_dnu = -E / (2.0 * (1.0 + nu) * (1.0 + nu));
-    const double den = (1.0 + nu) * (1.0 - 2.0 * nu);
-    const double dlam_dnu = E * (1.0 + 2.0 * nu * nu) / (den * den);
-    const double dw_dE = 2.0 * dmu_dE + (nh ? dlam_dE : 0.0);
-    const double dw_dnu = 2.0 * dmu_dnu + (nh ? dlam_dnu : 0.0);
-    const double cb = d.mu_ref > 0.0 ? d.beta0 / d.mu_ref : 0.0;
-    const double inv_n = 1.0 / d.n_e;
-    if (dE)
-      dE[e] = d.dw[e] * dw_dE + d.dbeta[e] * cb * dmu_dE +
-              (c->acc_mu * dmu_dE + c->acc_lam * dlam_dE + c->acc_k * dw_dE) * inv_n;
-    part[0] = d.dw[e] * dw_dnu + d.dbeta[e] * cb * dmu_dnu;
-    part[1] = dmu_dnu;
-    part[2] = dlam_dnu;
-    part[3] = dw_dnu;
-  }
+  if (e < d.n_e) chain_item(d, e, dE, c->acc_mu, c->acc_lam, c->acc_k, part);
   block_reduce_store<4>(part, d.red);
-  if (last_block(&d.ctrl->ticket[TK_CHAIN])) {
-    if (threadIdx.x == 0) {
-      const double inv_n = 1.0 / d.n_e;
-      const double v = sum_partials(d.red, gridDim.x, 0) + (c->acc_mu * sum_partials(d.red, gridDim.x, 1) +
-                                                           c->acc_lam * sum_partials(d.red, gridDim.x, 2) +
-                                                           c->acc_k * sum_partials(d.red, gridDim.x, 3)) * inv_n;
-      if (dnu) *dnu = v;
-      d.ctrl->dnu_acc = v;
-    }
+  if (last_block(&d.ctrl->ticket[TK_CHAIN]) && threadIdx.x == 0) {
+    double s[4];
+    for (int j = 0; j < 4; ++j) s[j] = sum_partials(d.red, gridDim.x, j);
+    const double v = chain_nu(d, c->acc_mu, c->acc_lam, c->acc_k, s);
+    if (dnu) *dnu = v;
+    d.ctrl->dnu_acc = v;
   }
 }
 
-__global__ void k_bwd_finish(Dev d, double* __restrict__ dq0, double* __restrict__ dv0) {
+__global__ void k_bwd_finish(Dev d, double* dq0, double* dv0) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 3 * d.n_v) return;
   if (dq0) dq0[i] = d.gq[i];
   if (dv0) dv0[i] = d.gv[i];
+}
+
+// ------------------------------------------------------------ persistent backward
+
+template <typename T>
+__global__ void __launch_bounds__(kPersistBlock, 2) k_bwd_rollout(Dev d, BwdArgs a) {
+  __shared__ BwdState S;
+  __shared__ double sums[4];
+  const int tid = threadIdx.x;
+  const int gtid = blockIdx.x * blockDim.x + tid;
+  const int gthreads = gridDim.x * blockDim.x;
+  const int lane = tid & 31, gwarp = gtid >> 5, nwarps = gthreads >> 5;
+  const size_t nv3 = 3 * (size_t)d.n_v;
+  const bool writer = blockIdx.x == 0;
+  const Range re = block_range(d.n_e);
+  const Range rv = block_range(d.n_v);
+  const Range rb = block_range(d.n_v > d.n_e ? d.n_v : d.n_e);
+  const Range rt = block_range(d.n_v + d.n_e);
+  if (tid == 0) {
+    S.adj_k = S.adj_done = S.status = S.adj_iters_total = S.adj_iters_max = S.adj_not_converged = 0;
+    S.rz = S.rz0 = S.alpha = S.beta = S.acc_mu = S.acc_lam = S.acc_k = S.dnu_acc = 0.0;
+  }
+  for (int i = rb.lo + tid; i < rb.hi; i += blockDim.x) bwd_begin_item(d, i, a.dqT, a.dvT);
+  bool ok = grid_sync(d);
+  for (int t = a.T - 1; t >= 0 && ok; --t) {
+    const double* qstar = a.ckpt + (size_t)(t + 1) * nv3;
+    const double* qt = a.ckpt + (size_t)t * nv3;
+    const double tau = __ldcg(&d.tau[t]);
+    for (int e = re.lo + tid; e < re.hi; e += blockDim.x) bwd_setup_item<T>(d, e, qstar, tau);
+    for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) bwd_init_item(d, v);
+    if (!(ok = grid_sync(d))) break;
+    for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, sg, lane);
+    if (!(ok = grid_sync(d))) break;
+    for (int j = gwarp; j < d.n_f; j += nwarps) spmv_st_row(d, d.y, d.z, j, lane);
+    if (!(ok = grid_sync(d))) break;
+    double p1[1] = {0.0};
+    for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) init_z_item(d, v, p1);
+    if (!(ok = grid_reduce<1>(d, p1, sums))) break;
+    if (tid == 0) init_z_finish(&S, sums);
+    __syncthreads();
+    while (!S.adj_done) {
+      for (int e = re.lo + tid; e < re.hi; e += blockDim.x) kapply_item<T>(d, e, d.pdir);
+      if (!(ok = grid_sync(d))) break;
+      double pw[1] = {0.0};
+      for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) pcg_w_item<T>(d, v, pw);
+      if (!(ok = grid_reduce<1>(d, pw, sums))) break;
+      if (tid == 0) pcg_w_finish(&S, sums);
+      __syncthreads();
+      if (S.adj_done) break;
+      const double alpha = S.alpha;
+      for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) pcg_r_item(d, v, alpha);
+      if (!(ok = grid_sync(d))) break;
+      for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, sg, lane);
+      if (!(ok = grid_sync(d))) break;
+      for (int j = gwarp; j < d.n_f; j += nwarps) spmv_st_row(d, d.y, d.z, j, lane);
+      if (!(ok = grid_sync(d))) break;
+      double prz[1] = {0.0};
+      for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) pcg_z_item(d, v, prz);
+      if (!(ok = grid_reduce<1>(d, prz, sums))) break;
+      if (tid == 0) pcg_z_finish(d, &S, sums);
+      __syncthreads();
+      if (S.adj_done) break;
+      const double beta = S.beta;
+      for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) pcg_p_item(d, v, beta);
+      if (!(ok = grid_sync(d))) break;
+    }
+    if (!ok) break;
+    double* df_t = a.df ? (a.df_stride ? a.df + (size_t)t * nv3 : a.df) : nullptr;
+    double p3[3] = {0.0, 0.0, 0.0};
+    for (int i = rt.lo + tid; i < rt.hi; i += blockDim.x) {
+      if (i < d.n_v) route_vertex_item(d, i, df_t, a.df_stride == 0 ? 1 : 0);
+      else route_elem_item(d, i - d.n_v, qstar, qt, tau, p3);
+    }
+    if (!(ok = grid_reduce<3>(d, p3, sums))) break;
+    if (tid == 0) route_finish(&S, sums);
+    __syncthreads();
+  }
+  if (ok) {
+    double p4[4] = {0.0, 0.0, 0.0, 0.0};
+    const double am = S.acc_mu, al = S.acc_lam, ak = S.acc_k;
+    for (int e = re.lo + tid; e < re.hi; e += blockDim.x) chain_item(d, e, a.dE, am, al, ak, p4);
+    ok = grid_reduce<4>(d, p4, sums);
+    if (ok && writer && tid == 0) {
+      const double v = chain_nu(d, am, al, ak, sums);
+      if (a.dnu) *a.dnu = v;
+      d.ctrl->dnu_acc = v;
+    }
+    for (int i = rv.lo + tid; i < rv.hi; i += blockDim.x)
+      for (int c = 0; c < 3; ++c) {
+        if (a.dq0) a.dq0[3 * (size_t)i + c] = d.gq[3 * (size_t)i + c];
+        if (a.dv0) a.dv0[3 * (size_t)i + c] = d.gv[3 * (size_t)i + c];
+      }
+  }
+  if (writer && tid == 0) {
+    Ctrl* c = d.ctrl;
+    c->adj_iters_total = S.adj_iters_total;
+    c->adj_iters_max = S.adj_iters_max;
+    c->adj_not_converged = S.adj_not_converged;
+    c->acc_mu = S.acc_mu;
+    c->acc_lam = S.acc_lam;
+    c->acc_k = S.acc_k;
+    atomicOr(&c->status, S.status);
+  }
 }
 
 // ------------------------------------------------------------ wrappers
@@ -527,6 +688,26 @@ void launch_chain(const Dev& d, cudaStream_t s, double* dE, double* dnu) {
 
 void launch_bwd_finish(const Dev& d, cudaStream_t s, double* dq0, double* dv0) {
   k_bwd_finish<<<nblk(3 * d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d, dq0, dv0);
+}
+
+static int coop_grid_b(const void* fn) {
+  int dev = 0, sms = 0, coop = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPersistBlock, 0) != cudaSuccess) return 0;
+  if (per_sm < 1) return 0;
+  return sms * (per_sm < 2 ? per_sm : 2);
+}
+
+int persistent_grid_bwd(const Dev& d) {
+  return coop_grid_b(d.local_fp32 ? (const void*)k_bwd_rollout<float> : (const void*)k_bwd_rollout<double>);
+}
+
+cudaError_t launch_bwd_rollout(const Dev& d, cudaStream_t s, const BwdArgs& a, int grid) {
+  void* args[] = {(void*)&d, (void*)&a};
+  const void* fn = d.local_fp32 ? (const void*)k_bwd_rollout<float> : (const void*)k_bwd_rollout<double>;
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPersistBlock), args, 0, s);
 }
 
 }  // namespace pdk

@@ -31,6 +31,29 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* red)
   }
 }
 
+// block-wide sum of v[NV] (fixed shuffle tree, then warps in order) into
+// out[NV] (shared), visible to the whole block on return
+template <int NV>
+__device__ __forceinline__ void block_reduce_to(double (&v)[NV], double* out) {
+  __shared__ double sh[32][NV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    double x = v[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[wid][j] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int w = 0; w < nw; ++w) s += sh[w][threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
 // returns true in every thread of the last block to finish; its partials
 // are then visible. Resets the ticket for the next launch.
 __device__ __forceinline__ bool last_block(unsigned int* ticket) {

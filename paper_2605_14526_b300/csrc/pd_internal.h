@@ -11,6 +11,8 @@ constexpr int kVtxBlock = 256;   // threads per block, vertex kernels
 constexpr int kTetBlock = 128;   // threads per block, element kernels
 constexpr int kWarpsSpmv = 8;    // warps per block, skyline SpMV
 constexpr int kJacRec = 36;      // values per element in the backward Jacobian record
+constexpr int kPersistBlock = 256;  // threads per block, persistent kernels
+constexpr int kRedRows = 2048;   // rows of the reduction scratch (>= any grid used)
 
 // Device-resident control word of the iteration (one per context).
 struct Ctrl {
@@ -39,7 +41,13 @@ struct Ctrl {
   double acc_mu, acc_lam, acc_k;  // mesh-mean sensitivities accumulated over steps
   double dnu_acc;
   unsigned int ticket[16];        // last-block-done counters, one per kernel kind
+  unsigned int bar_count, bar_gen; // grid barrier of the persistent kernels
+  unsigned long long phase_ns[8];  // persistent kernels: time per phase (globaltimer, block 0)
+  unsigned long long work_ns[8];   // ... of which block 0's own work before the phase's barrier
 };
+
+// phases timed inside the persistent rollout
+enum Phase { PH_BEGIN = 0, PH_LOCAL = 1, PH_ASSEMBLE = 2, PH_SPMV_S = 3, PH_SPMV_ST = 4, PH_AA = 5, PH_UPDATE = 6, PH_END = 7 };
 
 enum Ticket {
   TK_ASSEMBLE = 0, TK_SPMV_T = 1, TK_UPDATE = 2, TK_TR = 3, TK_PCG_W = 4, TK_PCG_Z = 5,
@@ -102,6 +110,7 @@ struct Dev {
   double* dQ;       // [kMaxAA][n_v][3]
   double* dG;
   void* contrib;    // [n_e][12] float or double
+  void* sstar;      // [n_e][3] float or double: last prox stretches (Newton warm start; <= 0 = none)
   double* red;      // [blocks][kRed]
   Ctrl* ctrl;
 
@@ -123,6 +132,34 @@ struct Dev {
   double* gv;       // running dL/dv_t
   double* dw;       // [n_e] accumulated dL/dw_e
   double* dbeta;    // [n_e]
+};
+
+// Arguments of the persistent forward rollout.
+struct RollArgs {
+  int T;
+  const double* q0;
+  const double* v0;
+  const double* fext;
+  long long f_stride;   // 0: one force array for all steps; else 3 n_v
+  double* qT;
+  double* vT;
+  double* ckpt;         // [(T+1)][n_v][3]
+  double* sq;           // state between steps
+  double* sv;
+};
+
+// Arguments of the persistent backward rollout.
+struct BwdArgs {
+  int T;
+  const double* dqT;
+  const double* dvT;    // may be null
+  double* dq0;          // outputs, each may be null
+  double* dv0;
+  double* dE;
+  double* dnu;
+  double* df;
+  long long df_stride;  // 0: summed into one [n_v][3]; else 3 n_v per step
+  const double* ckpt;   // [(T+1)][n_v][3]
 };
 
 }  // namespace pdk

@@ -21,6 +21,14 @@ void launch_apply_inverse(const Dev& d, cudaStream_t s, const double* xperm, dou
 // x = A^-1 b for b, x in vertex order; xperm and y are [n_f][3] work buffers
 void launch_solve(const Dev& d, cudaStream_t s, const double* b, double* xperm, double* y, double* x);
 
+// persistent forward rollout: cooperative grid size (0 if not available) and launch
+int persistent_grid(const Dev& d);
+cudaError_t launch_fwd_rollout(const Dev& d, cudaStream_t s, const RollArgs& a, int grid);
+
+// persistent backward rollout
+int persistent_grid_bwd(const Dev& d);
+cudaError_t launch_bwd_rollout(const Dev& d, cudaStream_t s, const BwdArgs& a, int grid);
+
 // backward (Alg. 2)
 void launch_bwd_setup(const Dev& d, cudaStream_t s, const double* qstar, const double* tau_t);
 void launch_bwd_init(const Dev& d, cudaStream_t s);

@@ -185,14 +185,15 @@ __device__ __forceinline__ bool spd_inv3(const T* H, T* Hi) {
   return true;
 }
 
-// sigma* = argmin k/2||s - sF||^2 + psi_bar(s), s > 0. Returns iterations.
+// sigma* = argmin k/2||s - sF||^2 + psi_bar(s), s > 0, Newton from s0 (> 0).
+// Returns iterations.
 template <typename T>
-__device__ __forceinline__ int nh_prox(const T* sF, const NHMean<T>& m, T* s) {
+__device__ __forceinline__ int nh_prox_from(const T* sF, const NHMean<T>& m, const T* s0, T* s) {
   const bool f32 = sizeof(T) == 4;
   const T tol = f32 ? T(2e-7) : T(1e-13);
   const T loose = f32 ? T(1e-5) : T(1e-11);
 #pragma unroll
-  for (int i = 0; i < 3; ++i) s[i] = sF[i] > T(0.1) ? sF[i] : T(0.1);
+  for (int i = 0; i < 3; ++i) s[i] = s0[i];
   int it = 0;
   for (; it < 40; ++it) {
     T g[3], lnJ;
@@ -217,16 +218,25 @@ __device__ __forceinline__ int nh_prox(const T* sF, const NHMean<T>& m, T* s) {
       if (s[0] + t * d[0] > T(0) && s[1] + t * d[1] > T(0) && s[2] + t * d[2] > T(0)) break;
       t *= T(0.5);
     }
-    const T f0 = nh_obj(s, m, sF);
     bool ok = false;
     T trial[3];
+    T f0 = T(0);
+    bool have_f0 = false;
     for (int hh = 0; hh < 40; ++hh) {
 #pragma unroll
       for (int i = 0; i < 3; ++i) trial[i] = s[i] + t * d[i];
       T gt[3], lt;
       nh_grad(trial, m, sF, gt, lt);
       const T gtmax = fmax(fmax(dabs(gt[0]), dabs(gt[1])), dabs(gt[2]));
-      if ((newton && gtmax <= T(0.5) * gmax) || nh_obj(trial, m, sF) <= f0 + T(1e-4) * t * slope) {
+      if (newton && gtmax <= T(0.5) * gmax) {
+        ok = true;
+        break;
+      }
+      if (!have_f0) {
+        f0 = nh_obj(s, m, sF);
+        have_f0 = true;
+      }
+      if (nh_obj(trial, m, sF) <= f0 + T(1e-4) * t * slope) {
         ok = true;
         break;
       }
@@ -238,6 +248,15 @@ __device__ __forceinline__ int nh_prox(const T* sF, const NHMean<T>& m, T* s) {
     for (int i = 0; i < 3; ++i) s[i] = trial[i];
   }
   return it;
+}
+
+// same, from s0 = max(sF, 0.1)
+template <typename T>
+__device__ __forceinline__ int nh_prox(const T* sF, const NHMean<T>& m, T* s) {
+  T s0[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) s0[i] = sF[i] > T(0.1) ? sF[i] : T(0.1);
+  return nh_prox_from<T>(sF, m, s0, s);
 }
 
 }  // namespace pdk

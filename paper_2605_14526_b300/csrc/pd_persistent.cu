@@ -1,0 +1,176 @@
+// Persistent forward rollout: one cooperative launch runs all T steps of
+// Alg. 1 (step begin, local/global iterations with Anderson mixing and the
+// dual gate, step end, trust-region selection).
+//
+// Synchronisation: phases are separated by a grid barrier built from an
+// acq_rel arrival counter and a release/acquire generation word. In a
+// reduction barrier the last block to arrive sums the per-block partials in
+// a fixed order (deterministic) and publishes the sums; every block then runs
+// the phase's scalar logic (pd_phases.cuh) on its own shared-memory replica
+// of the iteration state, so all blocks take identical decisions without a
+// serial chain of global-memory accesses. The grid is co-resident
+// (cooperative launch) and every wait is bounded: on timeout a status bit is
+// set and every block returns.
+#include <cuda_runtime.h>
+
+#include "pd_grid.cuh"
+#include "pd_launch.h"
+#include "pd_phases.cuh"
+
+namespace pdk {
+
+template <typename T>
+__global__ void __launch_bounds__(kPersistBlock, 2) k_fwd_rollout(Dev d, RollArgs a) {
+  __shared__ FwdState S;
+  __shared__ double sums[2 * kMaxAA];
+  const int tid = threadIdx.x;
+  const int gtid = blockIdx.x * blockDim.x + tid;
+  const int gthreads = gridDim.x * blockDim.x;
+  const int lane = tid & 31, gwarp = gtid >> 5, nwarps = gthreads >> 5;
+  const size_t nv3 = 3 * (size_t)d.n_v;
+  const bool writer = blockIdx.x == 0;
+  const Range re = block_range(d.n_e);
+  const Range rv = block_range(d.n_v);
+  const Range rt = block_range(d.n_e + d.n_v);
+  unsigned long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0}, wk[8] = {0, 0, 0, 0, 0, 0, 0, 0}, t0 = 0;
+  auto mark = [&](int p) {
+    if (writer && tid == 0) {
+      const unsigned long long t1 = gtimer();
+      ph[p] += t1 - t0;
+      t0 = t1;
+    }
+  };
+  // block 0's own work of the current phase (before its barrier); all threads
+  // of block 0 are done when thread 0 passes this __syncthreads
+  auto work_done = [&](int p) {
+    if (writer) {
+      __syncthreads();
+      if (tid == 0) wk[p] += gtimer() - t0;
+    }
+  };
+  if (tid == 0) {
+    S.iters_total = S.iters_max = S.resets = S.not_converged = S.tau_half = S.tau_one = S.status = 0;
+    S.last_rho = 0.0;
+    for (int i = 0; i < kMaxAA * kMaxAA; ++i) S.gram[i] = 0.0;
+    t0 = gtimer();
+  }
+  bool ok = true;
+  for (int t = 0; t < a.T && ok; ++t) {
+    const double* qin = t == 0 ? a.q0 : a.sq;
+    const double* vin = t == 0 ? a.v0 : a.sv;
+    const double* fst = a.fext ? a.fext + (a.f_stride ? (size_t)t * (size_t)a.f_stride : 0) : nullptr;
+    if (tid == 0) ctrl_step_reset(&S, t);
+    for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) step_begin_item(d, v, qin, vin, fst, a.ckpt + (size_t)t * nv3);
+    if (!(ok = grid_sync(d))) break;
+    mark(PH_BEGIN);
+    for (;;) {
+      const int k = S.k;
+      for (int e = re.lo + tid; e < re.hi; e += blockDim.x) local_item<T>(d, e, d.q);
+      work_done(PH_LOCAL);
+      if (!(ok = grid_sync(d))) break;
+      mark(PH_LOCAL);
+      double p3[3] = {0.0, 0.0, 0.0};
+      for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) assemble_item<T>(d, v, k, p3);
+      work_done(PH_ASSEMBLE);
+      if (!(ok = grid_reduce<3>(d, p3, sums))) break;
+      if (tid == 0) assemble_finish(d, &S, k, sums);
+      __syncthreads();
+      mark(PH_ASSEMBLE);
+      if (S.done) break;
+      for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, sg, lane);
+      work_done(PH_SPMV_S);
+      if (!(ok = grid_sync(d))) break;
+      mark(PH_SPMV_S);
+      // S^T y row by row, with the Anderson work of that row's vertex fused in
+      const AAView av = aa_view(d, S.pairs, S.ncols, S.head);
+      double pa[2 * kMaxAA];
+      for (int j = 0; j < 2 * kMaxAA; ++j) pa[j] = 0.0;
+      for (int j = gwarp; j < d.n_f; j += nwarps) {
+        double a0, a1, a2;
+        spmv_st_sum(d, d.y, j, lane, a0, a1, a2);
+        if (lane < 3) {
+          const size_t o = 3 * (size_t)d.perm[j] + lane;
+          const double qh = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
+          d.qhat[o] = qh;
+          aa_component(d, o, qh, av, pa);
+        }
+      }
+      work_done(PH_AA);
+      if (!(ok = grid_reduce<2 * kMaxAA>(d, pa, sums))) break;
+      if (tid == 0) aa_finish(d, &S, av, sums);
+      __syncthreads();
+      mark(PH_AA);
+      const int use_hat = S.use_hat, nc = S.ncols;
+      double gam[kMaxAA];
+      for (int j = 0; j < nc; ++j) gam[j] = S.gamma[j];
+      double pu[2] = {0.0, 0.0};
+      for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) update_item(d, v, use_hat, nc, gam, pu);
+      work_done(PH_UPDATE);
+      if (!(ok = grid_reduce<2>(d, pu, sums))) break;
+      if (tid == 0) update_finish(d, &S, sums);
+      __syncthreads();
+      mark(PH_UPDATE);
+      if (S.done) break;
+    }
+    if (!ok) break;
+    const bool last = t == a.T - 1;
+    double* qo = last && a.qT ? a.qT : a.sq;
+    double* vo = last && a.vT ? a.vT : a.sv;
+    if (tid == 0) step_end_ctrl(d, &S, writer);
+    for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) step_end_item(d, v, qo, vo, a.ckpt + (size_t)(t + 1) * nv3);
+    if (d.model == 1) {
+      double p4[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int i = rt.lo + tid; i < rt.hi; i += blockDim.x) tr_item(d, i, p4);
+      if (!(ok = grid_reduce<4>(d, p4, sums))) break;
+      if (tid == 0) tr_finish(d, &S, sums, writer);
+      __syncthreads();
+    } else {
+      if (!(ok = grid_sync(d))) break;
+    }
+    mark(PH_END);
+  }
+  // block 0 publishes the rollout statistics
+  if (writer && tid == 0) {
+    Ctrl* c = d.ctrl;
+    c->iters_total = S.iters_total;
+    c->iters_max = S.iters_max;
+    c->resets = S.resets;
+    c->not_converged = S.not_converged;
+    c->tau_half = S.tau_half;
+    c->tau_one = S.tau_one;
+    c->last_rho = S.last_rho;
+    c->k = S.k;
+    atomicOr(&c->status, S.status);
+    for (int i = 0; i < 8; ++i) {
+      c->phase_ns[i] += ph[i];
+      c->work_ns[i] += wk[i];
+    }
+  }
+}
+
+// ------------------------------------------------------------ launch
+
+static int coop_grid(const void* fn, int* grid) {
+  int dev = 0, sms = 0, coop = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPersistBlock, 0) != cudaSuccess) return -1;
+  if (per_sm < 1) return -1;
+  *grid = sms * (per_sm < 2 ? per_sm : 2);
+  return 0;
+}
+
+int persistent_grid(const Dev& d) {
+  int g = 0;
+  const void* fn = d.local_fp32 ? (const void*)k_fwd_rollout<float> : (const void*)k_fwd_rollout<double>;
+  return coop_grid(fn, &g) == 0 ? g : 0;
+}
+
+cudaError_t launch_fwd_rollout(const Dev& d, cudaStream_t s, const RollArgs& a, int grid) {
+  void* args[] = {(void*)&d, (void*)&a};
+  const void* fn = d.local_fp32 ? (const void*)k_fwd_rollout<float> : (const void*)k_fwd_rollout<double>;
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPersistBlock), args, 0, s);
+}
+
+}  // namespace pdk

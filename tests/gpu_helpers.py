@@ -10,9 +10,12 @@ from paper_2605_14526_b300.build import build
 DEV = "cuda:0"
 
 
-def gpu_run(scene, options=None, backward=True, per_step_force=None):
+def gpu_run(scene, options=None, backward=True, persistent=1):
     """Forward (and backward) of a workload through the library; device buffers."""
     build()
+    if options is None:
+        options = binding.options_for(scene.solver)
+    options.persistent = persistent
     pd = binding.PDContext(scene, options)
     T = scene.steps
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)

@@ -13,10 +13,12 @@ from paper_2605_14526_b300 import binding, inputs
 pytestmark = pytest.mark.gpu
 
 
-def test_cube_fixed_iterations_forward_and_backward():
-    """Plain PD cube: 20 fixed iterations, corotated, FP64 (both sides)."""
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_cube_fixed_iterations_forward_and_backward(persistent):
+    """Plain PD cube: 20 fixed iterations, corotated, FP64 (both sides);
+    persistent rollout kernel and per-phase kernels."""
     sc = inputs.small_cube()
-    g = gpu_run(sc)
+    g = gpu_run(sc, persistent=persistent)
     o = oracle_run(sc)
     assert rel(g["qT"], o["qT"]) < 1e-11
     assert rel(g["vT"], o["vT"]) < 1e-9
@@ -40,11 +42,12 @@ def test_tiny_fp64_converged_rollout(model):
     assert abs(g["dnu"] - o["dnu"]) < 1e-6 * abs(o["dnu"])
 
 
-def test_small_bar_fp32_config_gate():
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_small_bar_fp32_config_gate(persistent):
     """Heterogeneous NH bar (8x4x4 cells, 4^3 blocks), FP32 local step, the
     benchmark's Anderson window and dual gate, 20 steps."""
     sc = inputs.hetero_bar(nx=8, ny=4, nz=4, block=4, steps=20)
-    g = gpu_run(sc)
+    g = gpu_run(sc, persistent=persistent)
     o = oracle_run(sc)
     assert g["stats"].not_converged == 0
     assert rel(g["qT"], o["qT"]) < 1e-5
@@ -154,6 +157,9 @@ def test_anderson_counts_match_reference():
     sc = inputs.hetero_bar(nx=8, ny=4, nz=4, block=4, steps=4)
     sc = sc.replace(solver=inputs.SolverSettings(local_fp32=False))
     g = gpu_run(sc, backward=False)
+    g0 = gpu_run(sc, backward=False, persistent=0)
+    assert g0["stats"].iters_total == g["stats"].iters_total
+    assert rel(g0["qT"], g["qT"]) < 1e-12
     pb = solver.build_problem(sc)
     q, v = sc.x0.copy(), sc.v0.copy()
     iters = 0
