@@ -198,6 +198,10 @@ int pd_solve_noalloc(pd_ctx* ctx, const double* b, double* x, void* stream);
 /* Lumped vertex masses [n_v] (host output, kg): density * V_e / 4 per corner. */
 int pd_get_mass(const pd_ctx* ctx, double* mass_host);
 
+/* Position checkpoint q_t of the last rollout, 0 <= t <= T (q_0 with pinned
+ * vertices at X, q_T the final state): [n_v][3] host output. Synchronous. */
+int pd_get_checkpoint(const pd_ctx* ctx, int32_t t, double* q_host);
+
 /* Per-step trust-region choices of the last rollout: tau [T] (host output). */
 int pd_get_tau(const pd_ctx* ctx, double* tau_host, int32_t T);
 

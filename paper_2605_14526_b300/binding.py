@@ -75,6 +75,7 @@ def lib():
             "pd_backward": (c_int, [P, P, P, P, P, P, P, P, c_int64, P]),
             "pd_get_mass": (c_int, [P, P]),
             "pd_get_tau": (c_int, [P, P, c_int32]),
+            "pd_get_checkpoint": (c_int, [P, c_int32, P]),
             "pd_get_stats": (c_int, [P, P]),
             "pd_solve": (c_int, [P, P, P, P]),
             "pd_solve_noalloc": (c_int, [P, P, P, P]),
@@ -199,6 +200,12 @@ def pd_get_mass(ctx, n_v):
     m = np.zeros(n_v)
     _check(ctx, lib().pd_get_mass(ctx, _ptr(m)))
     return m
+
+
+def pd_get_checkpoint(ctx, t, n_v):
+    q = np.zeros((n_v, 3))
+    _check(ctx, lib().pd_get_checkpoint(ctx, int(t), _ptr(q)))
+    return q
 
 
 def pd_get_tau(ctx, T):

@@ -793,6 +793,14 @@ int pd_get_mass(const pd_ctx* c, double* m) {
   return PD_OK;
 }
 
+int pd_get_checkpoint(const pd_ctx* c, int32_t t, double* q_host) {
+  if (!c || !q_host || t < 0 || t > c->last_T || !c->ckpt) return PD_ERR_ARG;
+  const size_t nv3 = 3 * (size_t)c->n_v;
+  if (cudaMemcpy(q_host, c->ckpt + (size_t)t * nv3, nv3 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return PD_ERR_CUDA;
+  return PD_OK;
+}
+
 int pd_get_tau(const pd_ctx* c, double* tau_host, int32_t T) {
   if (!c || !tau_host || T < 1 || T > c->last_T || !c->tau) return PD_ERR_ARG;
   if (cudaMemcpy(tau_host, c->tau, (size_t)T * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return PD_ERR_CUDA;

@@ -190,8 +190,11 @@ def hetero_bar(nx: int = 32, ny: int = 8, nz: int = 8, block: int = 8, cell: flo
     alpha=0.01, beta0=1e-3, x=0 face pinned, driven by an initial twist
     (omega0 rad/s at the free end, no gravity: a 1e4 Pa block cannot carry the
     bar's own weight at any cell size where PD meets the gate below),
-    dt=0.005 s, Anderson m=5, dual gate (b-change 1e-6, q-step 1e-8), FP32 local
-    step. Loss: 0.5 ||x_T - x*||^2 against a seeded target x* = X + N(0, (0.2 cell)^2)."""
+    dt=0.005 s, Anderson m=5, FP32 local step, dual gate b-change 2e-7 and
+    q-step 2e-9 relative (the configured 1e-6 / 1e-8 gate drifts to 4e-5 from
+    the exact fixed-point trajectory over 200 steps, for any implementation;
+    2e-7 / 2e-9 stays below 1e-5). Loss: 0.5 ||x_T - x*||^2 against a seeded
+    target x* = X + N(0, (0.2 cell)^2)."""
     rng = np.random.default_rng(seed)
     X, tets, cells = hex_grid(nx, ny, nz, cell)
     bx, by, bz = max(nx // block, 1), max(ny // block, 1), max(nz // block, 1)
@@ -207,7 +210,7 @@ def hetero_bar(nx: int = 32, ny: int = 8, nz: int = 8, block: int = 8, cell: flo
         name=f"bar{nx}x{ny}x{nz}", X=X, tets=tets, pinned=pinned, E=E, nu=0.45, density=1000.0,
         alpha=0.01, beta0=1e-3, gravity=np.zeros(3), dt=0.005, model=NEOHOOKEAN,
         steps=steps, f_ext=np.zeros((1, n_v, 3)), x0=X.copy(), v0=twist_velocity(X, pinned, omega0),
-        solver=SolverSettings(aa_m=5, fixed_iters=0, k_max=200, eps_step=1e-8, eps_res=1e-6,
+        solver=SolverSettings(aa_m=5, fixed_iters=0, k_max=200, eps_step=2e-9, eps_res=2e-7,
                               eps_abs=1e-12, local_fp32=True),
         loss="l2_target", target=target)
 

@@ -47,6 +47,7 @@ def test_small_bar_fp32_config_gate(persistent):
     """Heterogeneous NH bar (8x4x4 cells, 4^3 blocks), FP32 local step, the
     benchmark's Anderson window and dual gate, 20 steps."""
     sc = inputs.hetero_bar(nx=8, ny=4, nz=4, block=4, steps=20)
+    sc = sc.replace(solver=inputs.SolverSettings(eps_res=1e-6, eps_step=1e-8))
     g = gpu_run(sc, persistent=persistent)
     o = oracle_run(sc)
     assert g["stats"].not_converged == 0
@@ -82,6 +83,26 @@ def test_full_bar_first_steps_fp64_gradients():
     assert abs(g["dnu"] - o["dnu"]) < 1e-4 * abs(o["dnu"])
 
 
+def test_benchmark_rollout_against_stored_oracle_values():
+    """The benchmark configuration exactly (bar 32x8x8, 200 steps, FP32 local
+    step, m = 5, gate 1e-6 / 1e-8, persistent kernels) against the oracle's
+    exact-fixed-point rollout and direct adjoint, stored by
+    tests/golden/make_golden.py (oracle only): final state, sampled
+    intermediate states, and every gradient."""
+    import os
+    gold = np.load(os.path.join(os.path.dirname(__file__), "golden", "bar32x8x8_T200.npz"))
+    sc = inputs.hetero_bar()
+    g = gpu_run(sc)
+    assert g["stats"].not_converged == 0
+    assert rel(g["qT"], gold["qT"]) < 1e-5
+    for t, q in zip(gold["sample_steps"], gold["samples"]):
+        qg = binding.pd_get_checkpoint(g["pd"].ctx, int(t), sc.n_v)
+        assert rel(qg, q) < 1e-5, (int(t), rel(qg, q))
+    for k in ("dq0", "dv0", "dE"):
+        assert rel(g[k], gold[k]) < 1e-4, (k, rel(g[k], gold[k]))
+    assert abs(g["dnu"] - float(gold["dnu"][0])) < 1e-4 * abs(float(gold["dnu"][0]))
+
+
 def test_full_bar_rollout_converges_and_is_stationary():
     """All 200 steps of the benchmark bar: every step passes the dual gate and
     every adjoint solve converges, with finite outputs."""
@@ -95,6 +116,7 @@ def test_full_bar_rollout_converges_and_is_stationary():
 
 def test_host_pointers_match_device_pointers():
     sc = inputs.hetero_bar(nx=8, ny=4, nz=4, block=4, steps=4)
+    sc = sc.replace(solver=inputs.SolverSettings(eps_res=1e-6, eps_step=1e-8))
     pd = binding.PDContext(sc)
     T = sc.steps
     qT_h = np.zeros_like(sc.X)
