@@ -82,6 +82,12 @@ typedef struct {
   double eps_abs;         /* absolute term of both gates */
   double eps_tr;          /* trust-region ratio tolerance (0.1 in the paper) */
   double adj_tol;         /* backward: relative preconditioned residual target */
+  int32_t escalate_window;/* FP32 local step, persistent launches: when the gate distance
+                             (the larger squared ratio of the two gates) has not halved for
+                             this many iterations, the rounding of the FP32 projections
+                             is the floor of the iteration and the local step switches to
+                             FP64 for the rest of the rollout (0 = never; default 20) */
+  int32_t reserved_opt;
 } pd_options;
 
 /* Statistics of the last pd_rollout / pd_backward (host copy). */
@@ -102,13 +108,16 @@ typedef struct {
   double factor_seconds;    /* host time of the last pd_factor */
   double last_rho;          /* trust-region ratio of the last step */
   int64_t launches;         /* kernel launches issued by this context so far */
+  int32_t escalations;      /* rollouts whose local step switched from FP32 to FP64 (a batch: instances) */
+  int32_t reserved_stats;
 } pd_stats;
 
 typedef struct pd_ctx pd_ctx;
 
 /* Default options (m = 5, k_max = 200, gate 1e-8 / 1e-6 / 1e-12, FP32 local,
  * adaptive trust region with eps_tr = 0.1, backward 1e-9 / 1000 iterations,
- * persistent launches on). */
+ * persistent launches on, precision escalation after 20 iterations without
+ * progress). */
 void pd_default_options(pd_options* out);
 
 /* Create a context: validates the mesh (indices in range, positive rest
@@ -229,6 +238,108 @@ typedef struct {
 /* enable != 0 turns the phase timers on (and clears them); 0 turns them off. */
 int pd_profile(pd_ctx* ctx, int32_t enable);
 int pd_get_profile(const pd_ctx* ctx, pd_profile_out* out);
+
+/* ---------------------------------------------------------------------
+ * Capture-safe form of pd_rollout / pd_backward.
+ *
+ * pd_rollout and pd_backward synchronise the stream to read the iteration
+ * statistics. The *_enqueue variants only enqueue work (memsets and one
+ * cooperative persistent launch), so they can be recorded into a CUDA graph
+ * by stream capture and replayed; pd_collect then synchronises the stream and
+ * reads the statistics and status of the enqueued work. Requirements: every
+ * pointer is a device pointer; options.persistent = 1 and a co-resident grid
+ * (else PD_ERR_ARG); checkpoint storage for T steps exists (pd_reserve, or an
+ * earlier rollout of >= T steps) when the stream is being captured. The
+ * graph replays the buffers and shapes seen at capture time.
+ * --------------------------------------------------------------------- */
+
+/* Allocate checkpoint storage for rollouts of up to T steps (blocking). */
+int pd_reserve(pd_ctx* ctx, int32_t T);
+
+int pd_rollout_enqueue(pd_ctx* ctx, int32_t T, const double* q0, const double* v0, const double* f_ext,
+                       int64_t f_ext_stride, double* qT, double* vT, void* stream);
+int pd_backward_enqueue(pd_ctx* ctx, const double* dqT, const double* dvT, double* dq0, double* dv0,
+                        double* dE, double* dnu, double* df_ext, int64_t df_stride, void* stream);
+
+/* Synchronise the stream and fold the statistics of the work enqueued since
+ * the last collect into pd_get_stats; returns what pd_rollout / pd_backward
+ * would have returned (PD_ERR_NOT_CONVERGED, PD_ERR_TIMEOUT, ...). */
+int pd_collect(pd_ctx* ctx, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Batched instances (many independent meshes in one persistent launch).
+ *
+ * pd_create_batch makes one context for n independent problems: mesh i and
+ * material i as for pd_create, one dt and one set of options for all. The
+ * batch context takes the concatenation of the per-instance arrays
+ * everywhere a single context takes one instance's: vertex arrays are
+ * [sum n_v][3] (instance 0's vertices first), element arrays [sum n_e],
+ * per-step forces [T][sum n_v][3] with f_ext_stride = 3 sum n_v (or
+ * 0 for one [sum n_v][3] array), dnu is [n]. pd_factor factors every
+ * instance (host threads in parallel). pd_rollout / pd_backward (and their
+ * _enqueue forms) run all instances in ONE cooperative launch: the grid is
+ * split into teams of blocks, one team per instance, with team sizes set by
+ * the launch shape (pd_tuning; pd_autotune); each team iterates its own
+ * instance to its own gate and synchronises only with itself, so a fast
+ * instance never waits for a slow one. At most one instance per block of the
+ * co-resident grid (2 x SMs): more gives PD_ERR_TOO_LARGE at launch.
+ * pd_get_stats sums the per-instance statistics (iters_max, adj_iters_max:
+ * maximum); pd_get_instance_stats gives one instance's. pd_get_mass,
+ * pd_get_checkpoint give concatenated arrays; pd_get_tau gives [n][T].
+ * pd_solve, pd_solve_noalloc and pd_profile are single-instance only.
+ * --------------------------------------------------------------------- */
+int pd_create_batch(int32_t n, const pd_mesh* meshes, const pd_material* mats, double dt,
+                    const pd_options* opt, pd_ctx** out);
+
+/* Number of instances (1 for a single-instance context) and the prefix
+ * offsets of their vertices and elements (host outputs [n+1] each, may be
+ * NULL). */
+int pd_batch_info(const pd_ctx* ctx, int32_t* n, int64_t* v_off, int64_t* e_off);
+
+/* Batch form of pd_set_materials: E [sum n_e] (Pa), nu [n]. */
+int pd_set_materials_batch(pd_ctx* ctx, const double* E, const double* nu);
+
+int pd_get_instance_stats(const pd_ctx* ctx, int32_t i, pd_stats* out);
+
+/* Team sizes (blocks per instance) that the current launch shape gives the
+ * forward and the adjoint launch: fwd, bwd [n] host outputs (either may be
+ * NULL). The shape is fixed until pd_factor, pd_set_tuning or pd_autotune
+ * changes it. Batch contexts only; after pd_factor. */
+int pd_batch_teams(pd_ctx* ctx, int32_t* fwd, int32_t* bwd);
+
+/* ---------------------------------------------------------------------
+ * Launch shape of the persistent kernels and its autotuner.
+ * --------------------------------------------------------------------- */
+typedef struct {
+  int32_t fwd_blocks_per_sm;  /* co-resident blocks per SM (1 or 2; 0 = as many as fit, at most 2) */
+  int32_t bwd_blocks_per_sm;
+  int32_t fwd_grid;           /* single instance: blocks of the launch (0 = SMs x blocks_per_sm) */
+  int32_t bwd_grid;
+  double fwd_gamma;           /* batch: team sizes grow with (iterations x bytes per iteration)^gamma */
+  double bwd_gamma;
+  int32_t fwd_min_items;      /* batch: a team gets at most ceil(n_e / min_items) blocks */
+  int32_t bwd_min_items;
+  double fwd_ms;              /* pd_autotune: probe time of the chosen forward shape */
+  double bwd_ms;              /* ... backward shape */
+  int32_t candidates;         /* shapes timed by the last pd_autotune (0: found in the cache) */
+  int32_t reserved;
+} pd_tuning;
+
+/* Choose the launch shape by timing probe rollouts of T_probe steps from
+ * (q0, v0, f_ext) (as pd_rollout; device pointers) and their adjoints over
+ * a fixed candidate set: blocks per SM; for a single instance, the grid
+ * size; for a batch, the team-size exponent gamma (team sizes follow each
+ * instance's measured iterations x bytes per iteration) and the cap on
+ * blocks per element count. The choice is kept in the context and cached in
+ * the process, keyed by device and problem signature (instance sizes,
+ * nnz(S), options), so a second context of the same problem reuses it
+ * without probing. Overwrites the checkpoints (run pd_rollout again before
+ * pd_backward). Blocking. out may be NULL. */
+int pd_autotune(pd_ctx* ctx, int32_t T_probe, const double* q0, const double* v0, const double* f_ext,
+                int64_t f_ext_stride, pd_tuning* out, void* stream);
+int pd_get_tuning(const pd_ctx* ctx, pd_tuning* out);
+/* Set the launch shape directly (e.g. one saved from pd_get_tuning). */
+int pd_set_tuning(pd_ctx* ctx, const pd_tuning* t);
 
 /* Library version string. */
 const char* pd_version(void);

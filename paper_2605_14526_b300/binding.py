@@ -38,7 +38,8 @@ class pd_options(ctypes.Structure):
     _fields_ = [("aa_m", c_int32), ("k_max", c_int32), ("fixed_iters", c_int32), ("local_fp32", c_int32),
                 ("tr_mode", c_int32), ("adj_max_iters", c_int32), ("persistent", c_int32),
                 ("eps_step", c_double), ("eps_res", c_double),
-                ("eps_abs", c_double), ("eps_tr", c_double), ("adj_tol", c_double)]
+                ("eps_abs", c_double), ("eps_tr", c_double), ("adj_tol", c_double),
+                ("escalate_window", c_int32), ("reserved_opt", c_int32)]
 
 
 class pd_stats(ctypes.Structure):
@@ -46,12 +47,23 @@ class pd_stats(ctypes.Structure):
                 ("not_converged", c_int32), ("tau_half", c_int32), ("tau_one", c_int32),
                 ("adj_iters_total", c_int32), ("adj_iters_max", c_int32), ("adj_not_converged", c_int32),
                 ("status_flags", c_int32), ("n_free", c_int32), ("factor_nnz", c_int64),
-                ("factor_seconds", c_double), ("last_rho", c_double), ("launches", c_int64)]
+                ("factor_seconds", c_double), ("last_rho", c_double), ("launches", c_int64),
+                ("escalations", c_int32), ("reserved_stats", c_int32)]
 
 
 class pd_profile_out(ctypes.Structure):
     _fields_ = [("local_launches", c_int64), ("local_ms", c_double), ("solve_launches", c_int64),
                 ("solve_ms", c_double), ("phase_ms", c_double * 8), ("work_ms", c_double * 8)]
+
+
+class pd_tuning(ctypes.Structure):
+    _fields_ = [("fwd_blocks_per_sm", c_int32), ("bwd_blocks_per_sm", c_int32), ("fwd_grid", c_int32),
+                ("bwd_grid", c_int32), ("fwd_gamma", c_double), ("bwd_gamma", c_double),
+                ("fwd_min_items", c_int32), ("bwd_min_items", c_int32), ("fwd_ms", c_double), ("bwd_ms", c_double),
+                ("candidates", c_int32), ("reserved", c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
 
 
 _lib = None
@@ -84,6 +96,18 @@ def lib():
             "pd_last_error": (ctypes.c_char_p, [P]),
             "pd_destroy": (None, [P]),
             "pd_version": (ctypes.c_char_p, []),
+            "pd_reserve": (c_int, [P, c_int32]),
+            "pd_rollout_enqueue": (c_int, [P, c_int32, P, P, P, c_int64, P, P, P]),
+            "pd_backward_enqueue": (c_int, [P, P, P, P, P, P, P, P, c_int64, P]),
+            "pd_collect": (c_int, [P, P]),
+            "pd_create_batch": (c_int, [c_int32, P, P, c_double, P, P]),
+            "pd_batch_info": (c_int, [P, P, P, P]),
+            "pd_set_materials_batch": (c_int, [P, P, P]),
+            "pd_get_instance_stats": (c_int, [P, c_int32, P]),
+            "pd_batch_teams": (c_int, [P, P, P]),
+            "pd_autotune": (c_int, [P, c_int32, P, P, P, c_int64, P, P]),
+            "pd_get_tuning": (c_int, [P, P]),
+            "pd_set_tuning": (c_int, [P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -230,6 +254,106 @@ def pd_get_profile(ctx) -> pd_profile_out:
     return p
 
 
+def pd_reserve(ctx, T):
+    _check(ctx, lib().pd_reserve(ctx, int(T)))
+
+
+def pd_rollout_enqueue(ctx, T, q0, v0, f_ext, f_stride, qT, vT, stream=None):
+    _check(ctx, lib().pd_rollout_enqueue(ctx, int(T), _ptr(q0), _ptr(v0), _ptr(f_ext), int(f_stride), _ptr(qT),
+                                         _ptr(vT), _stream(stream)))
+
+
+def pd_backward_enqueue(ctx, dqT, dvT, dq0, dv0, dE, dnu, df_ext, df_stride, stream=None):
+    _check(ctx, lib().pd_backward_enqueue(ctx, _ptr(dqT), _ptr(dvT), _ptr(dq0), _ptr(dv0), _ptr(dE), _ptr(dnu),
+                                          _ptr(df_ext), int(df_stride), _stream(stream)))
+
+
+def pd_collect(ctx, stream=None, check=True):
+    code = lib().pd_collect(ctx, _stream(stream))
+    if check:
+        _check(ctx, code)
+    return code
+
+
+def _mesh_material(scene):
+    """pd_mesh / pd_material of a workload, with the arrays they point at."""
+    X = np.ascontiguousarray(scene.X, dtype=np.float64)
+    tets = np.ascontiguousarray(scene.tets, dtype=np.int32)
+    E = np.ascontiguousarray(scene.E, dtype=np.float64)
+    pin = np.ascontiguousarray(scene.pinned, dtype=np.uint8)
+    model = PD_COROTATED if scene.model == "corotated" else PD_NEOHOOKEAN
+    mesh = pd_mesh(int(X.shape[0]), int(tets.shape[0]), _ptr(X), _ptr(tets, np.int32), _ptr(pin, np.uint8))
+    mat = pd_material(model, _ptr(E), float(scene.nu), float(scene.density), float(scene.alpha), float(scene.beta0),
+                      (c_double * 3)(*[float(g) for g in scene.gravity]))
+    return mesh, mat, (X, tets, E, pin)
+
+
+def pd_create_batch(scenes, dt, options: pd_options):
+    """One context for a list of workloads (each a ``Scene``); arrays are copied."""
+    n = len(scenes)
+    meshes = (pd_mesh * n)()
+    mats = (pd_material * n)()
+    keep = []
+    for i, sc in enumerate(scenes):
+        m, t, arrays = _mesh_material(sc)
+        meshes[i] = m
+        mats[i] = t
+        keep.append(arrays)
+    out = c_void_p()
+    code = lib().pd_create_batch(n, meshes, mats, float(dt), ctypes.byref(options), ctypes.byref(out))
+    if code != PD_OK:
+        msg = lib().pd_last_error(out).decode() if out.value else ""
+        if out.value:
+            lib().pd_destroy(out)
+        raise PDError(code, msg)
+    return out
+
+
+def pd_batch_info(ctx):
+    n = c_int32()
+    _check(ctx, lib().pd_batch_info(ctx, ctypes.byref(n), None, None))
+    v_off = np.zeros(n.value + 1, dtype=np.int64)
+    e_off = np.zeros(n.value + 1, dtype=np.int64)
+    _check(ctx, lib().pd_batch_info(ctx, ctypes.byref(n), v_off.ctypes.data, e_off.ctypes.data))
+    return n.value, v_off, e_off
+
+
+def pd_set_materials_batch(ctx, E, nu):
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    nu = np.ascontiguousarray(nu, dtype=np.float64)
+    _check(ctx, lib().pd_set_materials_batch(ctx, _ptr(E), _ptr(nu)))
+
+
+def pd_get_instance_stats(ctx, i) -> pd_stats:
+    s = pd_stats()
+    _check(ctx, lib().pd_get_instance_stats(ctx, int(i), ctypes.byref(s)))
+    return s
+
+
+def pd_batch_teams(ctx, n):
+    f = np.zeros(n, dtype=np.int32)
+    b = np.zeros(n, dtype=np.int32)
+    _check(ctx, lib().pd_batch_teams(ctx, f.ctypes.data, b.ctypes.data))
+    return f, b
+
+
+def pd_autotune(ctx, T_probe, q0, v0, f_ext, f_stride, stream=None) -> pd_tuning:
+    t = pd_tuning()
+    _check(ctx, lib().pd_autotune(ctx, int(T_probe), _ptr(q0), _ptr(v0), _ptr(f_ext), int(f_stride),
+                                  ctypes.byref(t), _stream(stream)))
+    return t
+
+
+def pd_get_tuning(ctx) -> pd_tuning:
+    t = pd_tuning()
+    _check(ctx, lib().pd_get_tuning(ctx, ctypes.byref(t)))
+    return t
+
+
+def pd_set_tuning(ctx, t: pd_tuning):
+    _check(ctx, lib().pd_set_tuning(ctx, ctypes.byref(t)))
+
+
 def pd_last_error(ctx) -> str:
     return lib().pd_last_error(ctx).decode()
 
@@ -288,8 +412,79 @@ class PDContext:
         pd_set_materials(self.ctx, E, nu)
         pd_factor(self.ctx)
 
+    def ensure_materials(self, E, nu):
+        """Set (and refactor) only if E [n_e] or nu [1] differ from the current ones."""
+        nu_f = float(np.asarray(nu).reshape(-1)[0])
+        if not (np.array_equal(E, self.scene.E) and nu_f == self.scene.nu):
+            self.set_materials(E, nu_f)
+            self.scene = self.scene.replace(E=np.array(E, dtype=np.float64), nu=nu_f)
+
     def stats(self):
         return pd_get_stats(self.ctx)
+
+    def mass(self):
+        return pd_get_mass(self.ctx, self.n_v)
+
+
+class BatchContext:
+    """Owns one batched pd_ctx for a list of workloads (all with one dt and one
+    set of options); arrays at the boundary are the concatenation over
+    instances (``v_off`` / ``e_off`` prefix offsets)."""
+
+    def __init__(self, scenes, options: pd_options | None = None, factor: bool = True):
+        self.scenes = list(scenes)
+        self.options = options or options_for(self.scenes[0].solver)
+        self.ctx = pd_create_batch(self.scenes, self.scenes[0].dt, self.options)
+        self.n, self.v_off, self.e_off = pd_batch_info(self.ctx)
+        self.n_v, self.n_e = int(self.v_off[-1]), int(self.e_off[-1])
+        self.E = self.concat([sc.E for sc in self.scenes])
+        self.nu = np.array([sc.nu for sc in self.scenes], dtype=np.float64)
+        if factor:
+            pd_factor(self.ctx)
+
+    def close(self):
+        pd_destroy(self.ctx)
+        self.ctx = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "ctx", None) is not None:
+                self.close()
+        except Exception:
+            pass
+
+    def concat(self, arrays):
+        return np.concatenate([np.asarray(a, dtype=np.float64).reshape(-1) for a in arrays])
+
+    def split_v(self, a):
+        a = np.asarray(a).reshape(self.n_v, -1)
+        return [a[self.v_off[i]:self.v_off[i + 1]] for i in range(self.n)]
+
+    def split_e(self, a):
+        a = np.asarray(a).reshape(-1)
+        return [a[self.e_off[i]:self.e_off[i + 1]] for i in range(self.n)]
+
+    def set_materials(self, E, nu):
+        pd_set_materials_batch(self.ctx, E, nu)
+        pd_factor(self.ctx)
+        self.E = np.array(E, dtype=np.float64).reshape(-1)
+        self.nu = np.array(nu, dtype=np.float64).reshape(-1)
+
+    def ensure_materials(self, E, nu):
+        """Set (and refactor) only if E [sum n_e] or nu [n] differ from the current ones."""
+        nu = np.asarray(nu, dtype=np.float64).reshape(-1)
+        if not (np.array_equal(E, self.E) and np.array_equal(nu, self.nu)):
+            self.set_materials(E, nu)
+
+    def teams(self):
+        """Blocks per instance of the forward and adjoint launches."""
+        return pd_batch_teams(self.ctx, self.n)
+
+    def stats(self):
+        return pd_get_stats(self.ctx)
+
+    def instance_stats(self, i):
+        return pd_get_instance_stats(self.ctx, i)
 
     def mass(self):
         return pd_get_mass(self.ctx, self.n_v)

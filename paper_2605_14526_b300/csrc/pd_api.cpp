@@ -16,108 +16,16 @@
 
 #include "../../include/pd_b300.h"
 #include "factor.h"
+#include "pd_ctx.h"
 #include "pd_internal.h"
 #include "pd_launch.h"
 #include "pd_noalloc.h"
 
-using pdk::Ctrl;
-using pdk::Dev;
-
-struct pd_ctx {
-  // host copies
-  int n_v = 0, n_e = 0, n_f = 0;
-  std::vector<double> X;
-  std::vector<int32_t> tets;
-  std::vector<uint8_t> pinned;
-  std::vector<double> E;
-  double nu = 0.3, density = 1000.0, alpha = 0.0, beta0 = 0.0, g[3] = {0, 0, 0};
-  int model = PD_NEOHOOKEAN;
-  double dt = 0.01;
-  pd_options opt{};
-  // rest shape
-  std::vector<double> Bm, vol, mass;
-  // factor state
-  bool factored = false;
-  bool have_order = false;
-  std::vector<int> order_perm;  // free-local elimination order (geometry only)
-  pdf::Factor fac;
-  int64_t nnz_S = 0;
-  double factor_seconds = 0;
-  // device
-  int device = 0;
-  Dev d{};
-  std::vector<void*> allocs;        // context-lifetime device buffers
-  std::vector<void*> factor_allocs; // freed on refactor
-  double* ckpt = nullptr;
-  int ckpt_cap = 0;
-  double* tau = nullptr;
-  double *sq = nullptr, *sv = nullptr;   // rollout state
-  double* stage = nullptr;               // host-pointer staging
-  size_t stage_cap = 0;
-  int* h_flag = nullptr;                 // pinned host flags
-  cudaEvent_t ev[2] = {nullptr, nullptr};
-  int last_T = 0;
-  pd_stats stats{};
-  // phase timers: event pairs with the step and iteration they bracket; pairs
-  // of iterations that exited early (launched after convergence) are dropped
-  bool profiling = false;
-  std::vector<cudaEvent_t> prof_ev;
-  std::vector<int> prof_kind, prof_step, prof_iter;  // per pair
-  size_t prof_used = 0;                              // events in use
-  pd_profile_out prof{};
-  int* phase_count = nullptr;                        // device [T][2]
-  int64_t launches = 0;
-  std::string err;
-};
-
 namespace {
 
+using namespace pdh;
+
 const char* kVersion = "pd_b300 1.0 (sm_103a)";
-
-int fail(pd_ctx* c, int code, const char* fmt, ...) {
-  char buf[512];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof(buf), fmt, ap);
-  va_end(ap);
-  if (c) c->err = buf;
-  return code;
-}
-
-#define CK(call)                                                                                 \
-  do {                                                                                           \
-    cudaError_t e_ = (call);                                                                     \
-    if (e_ != cudaSuccess) return fail(c, PD_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
-  } while (0)
-
-template <typename T>
-int dalloc(pd_ctx* c, T** p, size_t n, bool factor_scope = false) {
-  void* q = nullptr;
-  if (n == 0) n = 1;
-  cudaError_t e = cudaMalloc(&q, n * sizeof(T));
-  if (e != cudaSuccess) return fail(c, PD_ERR_OOM, "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
-  (factor_scope ? c->factor_allocs : c->allocs).push_back(q);
-  *p = reinterpret_cast<T*>(q);
-  return PD_OK;
-}
-
-template <typename T>
-int upload(pd_ctx* c, T** p, const std::vector<T>& h, bool factor_scope = false) {
-  int r = dalloc(c, p, h.size(), factor_scope);
-  if (r) return r;
-  if (!h.empty()) CK(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
-  return PD_OK;
-}
-
-bool is_device_ptr(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
 struct ScalarCSR {
   std::vector<int> ptr, idx;
@@ -229,6 +137,7 @@ void pd_default_options(pd_options* o) {
   o->eps_abs = 1e-12;
   o->eps_tr = 0.1;
   o->adj_tol = 1e-9;
+  o->escalate_window = 20;
 }
 
 const char* pd_last_error(const pd_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -331,6 +240,8 @@ int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_o
   for (double** p : vecs)
     if ((r = dalloc(c, p, nv3))) return r;
   if ((r = dalloc(c, &d.bperm, 3 * (size_t)c->n_f)) || (r = dalloc(c, &d.y, 3 * (size_t)c->n_f))) return r;
+  d.sq = c->sq;
+  d.sv = c->sv;
   const int m = std::max(c->opt.aa_m, 1);
   if ((r = dalloc(c, &d.dQ, (size_t)m * nv3)) || (r = dalloc(c, &d.dG, (size_t)m * nv3))) return r;
   double* contrib;
@@ -357,6 +268,7 @@ int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_o
 
 int pd_set_materials(pd_ctx* c, const double* E, double nu) {
   if (!c || !E) return PD_ERR_ARG;
+  if (c->batch) return fail(c, PD_ERR_ARG, "a batch context takes pd_set_materials_batch");
   if (!(nu > -1.0 && nu < 0.5)) return fail(c, PD_ERR_ARG, "nu must be in (-1, 0.5)");
   for (int e = 0; e < c->n_e; ++e)
     if (!(E[e] > 0)) return fail(c, PD_ERR_ARG, "E[%d] must be > 0", e);
@@ -368,6 +280,7 @@ int pd_set_materials(pd_ctx* c, const double* E, double nu) {
 
 int pd_factor(pd_ctx* c) {
   if (!c) return PD_ERR_ARG;
+  if (c->batch) return batch_factor(c);
   auto t0 = std::chrono::steady_clock::now();
   CK(cudaSetDevice(c->device));
   for (void* p : c->factor_allocs) cudaFree(p);
@@ -504,6 +417,7 @@ int pd_factor(pd_ctx* c) {
   d.local_fp32 = c->opt.local_fp32 ? 1 : 0;
   d.aa_m = c->opt.aa_m; d.k_max = c->opt.k_max; d.fixed_iters = c->opt.fixed_iters; d.tr_mode = c->opt.tr_mode;
   d.adj_max_iters = c->opt.adj_max_iters;
+  d.escalate = c->opt.escalate_window;
   d.h = h; d.alpha_d = c->alpha; d.eps_step = c->opt.eps_step; d.eps_res = c->opt.eps_res; d.eps_abs = c->opt.eps_abs;
   d.eps_tr = c->opt.eps_tr; d.adj_tol = c->opt.adj_tol;
   for (int i = 0; i < 3; ++i) d.g[i] = c->g[i];
@@ -516,15 +430,159 @@ int pd_factor(pd_ctx* c) {
   return PD_OK;
 }
 
-static int ensure_stage(pd_ctx* c, size_t n) {
-  if (n <= c->stage_cap) return PD_OK;
-  if (c->stage) cudaFree(c->stage);
-  c->stage = nullptr;
-  c->stage_cap = 0;
-  cudaError_t e = cudaMalloc(&c->stage, n * sizeof(double));
-  if (e != cudaSuccess) return fail(c, PD_ERR_OOM, "staging allocation: %s", cudaGetErrorString(e));
-  c->stage_cap = n;
+}  // extern "C"
+
+namespace {
+
+int reserve_single(pd_ctx* c, int T) {
+  if (c->ckpt_cap >= T) return PD_OK;
+  if (c->ckpt) cudaFree(c->ckpt);
+  if (c->tau) cudaFree(c->tau);
+  if (c->phase_count) cudaFree(c->phase_count);
+  c->ckpt = nullptr;
+  c->tau = nullptr;
+  c->phase_count = nullptr;
+  c->ckpt_cap = 0;
+  const size_t nv3 = 3 * (size_t)c->n_v;
+  if (cudaMalloc(&c->ckpt, (size_t)(T + 1) * nv3 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->tau, (size_t)T * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->phase_count, 2 * (size_t)T * sizeof(int)) != cudaSuccess)
+    return fail(c, PD_ERR_OOM, "checkpoint allocation for %d steps", T);
+  c->ckpt_cap = T;
   return PD_OK;
+}
+
+// reserve for an enqueue: allocation is refused while the stream is captured
+int reserve_enqueue(pd_ctx* c, int T, cudaStream_t s) {
+  if (c->ckpt_cap >= T) return PD_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone)
+    return fail(c, PD_ERR_ARG, "checkpoint storage for %d steps is missing: call pd_reserve before capture", T);
+  return reserve_single(c, T);
+}
+
+// co-resident grid of a persistent launch: the tuned grid if one is set, else
+// SMs x blocks per SM; 0 if cooperative launch is unavailable
+int grid_of(pd_ctx* c, bool bwd, int* grid) {
+  const int full = bwd ? pdk::persistent_grid_bwd(c->d, 0) : pdk::persistent_grid(c->d, 0);
+  *grid = 0;
+  if (full <= 0) return PD_OK;
+  const int want = bwd ? c->tune.bwd_grid : c->tune.fwd_grid;
+  const int bps = bwd ? c->tune.bwd_blocks_per_sm : c->tune.fwd_blocks_per_sm;
+  if (want > 0) {
+    if (want > full) return fail(c, PD_ERR_ARG, "tuned grid %d exceeds the %d co-resident blocks", want, full);
+    *grid = want;
+  } else {
+    *grid = bwd ? pdk::persistent_grid_bwd(c->d, bps) : pdk::persistent_grid(c->d, bps);
+  }
+  return PD_OK;
+}
+
+// memsets + the persistent forward launch (no host synchronisation)
+int enqueue_fwd_single(pd_ctx* c, int T, const double* q0d, const double* v0d, const double* fd, int64_t f_stride,
+                       double* qTd, double* vTd, cudaStream_t s, int grid) {
+  Dev& d = c->d;
+  d.ckpt = c->ckpt;
+  d.tau = c->tau;
+  d.phase_count = c->phase_count;
+  d.T = T;
+  CK(cudaMemsetAsync(c->tau, 0, (size_t)T * sizeof(double), s));
+  CK(cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), s));  // per-rollout statistics and flags
+  CK(cudaMemsetAsync(d.sstar, 0, 3 * sizeof(double) * (size_t)c->n_e, s));  // no prox warm start across rollouts
+  pdk::RollArgs ra;
+  ra.T = T;
+  ra.q0 = q0d;
+  ra.v0 = v0d;
+  ra.fext = fd;
+  ra.f_stride = f_stride;
+  ra.qT = qTd;
+  ra.vT = vTd;
+  ra.ckpt = c->ckpt;
+  ra.sq = c->sq;
+  ra.sv = c->sv;
+  CK(pdk::launch_fwd_rollout(d, s, ra, grid));
+  c->launches += 1;
+  c->last_T = T;
+  return PD_OK;
+}
+
+int enqueue_bwd_single(pd_ctx* c, const double* dqTd, const double* dvTd, double* dq0d, double* dv0d, double* dEd,
+                       double* dnud, double* dfd, int64_t df_stride, cudaStream_t s, int grid) {
+  Dev& d = c->d;
+  if (dfd && df_stride == 0) CK(cudaMemsetAsync(dfd, 0, 3 * (size_t)c->n_v * sizeof(double), s));
+  pdk::BwdArgs ba;
+  ba.T = c->last_T;
+  ba.dqT = dqTd;
+  ba.dvT = dvTd;
+  ba.dq0 = dq0d;
+  ba.dv0 = dv0d;
+  ba.dE = dEd;
+  ba.dnu = dnud;
+  ba.df = dfd;
+  ba.df_stride = df_stride;
+  ba.ckpt = c->ckpt;
+  CK(cudaMemsetAsync(&d.ctrl->bar_count, 0, 2 * sizeof(unsigned int), s));
+  CK(pdk::launch_bwd_rollout(d, s, ba, grid));
+  c->launches += 1;
+  return PD_OK;
+}
+
+// fold a control word into the statistics; returns the status of `which`
+// (bit 0 forward, bit 1 backward)
+int stats_from_ctrl(pd_ctx* c, const Ctrl& hc, int which) {
+  pd_stats& st = c->stats;
+  int rc = PD_OK;
+  if (which & 1) {
+    st.steps = c->last_T;
+    st.iters_total = hc.iters_total;
+    st.iters_max = hc.iters_max;
+    st.aa_resets = hc.resets;
+    st.not_converged = hc.not_converged;
+    st.tau_half = hc.tau_half;
+    st.tau_one = hc.tau_one;
+    st.last_rho = hc.last_rho;
+    st.escalations = hc.escalations;
+  }
+  if (which & 2) {
+    st.adj_iters_total = hc.adj_iters_total;
+    st.adj_iters_max = hc.adj_iters_max;
+    st.adj_not_converged = hc.adj_not_converged;
+  }
+  st.status_flags = hc.status;
+  if (hc.status & 4) return fail(c, PD_ERR_TIMEOUT, "a grid barrier of a persistent launch timed out");
+  if ((which & 1) && (hc.status & 1)) return fail(c, PD_ERR_NUMERIC, "non-finite value in the right-hand side");
+  if ((which & 2) && (hc.status & 2))
+    return fail(c, PD_ERR_NUMERIC, "adjoint operator A - K not positive along a CG direction");
+  if ((which & 1) && hc.not_converged) rc = fail(c, PD_ERR_NOT_CONVERGED, "%d step(s) hit k_max", hc.not_converged);
+  if ((which & 2) && hc.adj_not_converged)
+    rc = fail(c, PD_ERR_NOT_CONVERGED, "%d adjoint solve(s) hit adj_max_iters", hc.adj_not_converged);
+  return rc;
+}
+
+int collect_single(pd_ctx* c, cudaStream_t s, int which) {
+  Ctrl hc;
+  CK(cudaMemcpyAsync(&hc, c->d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (c->profiling && (which & 1)) {
+    prof_harvest(c, c->last_T);
+    for (int i = 0; i < 8; ++i) {
+      c->prof.phase_ms[i] += hc.phase_ns[i] * 1e-6;
+      c->prof.work_ms[i] += hc.work_ns[i] * 1e-6;
+    }
+  }
+  return stats_from_ctrl(c, hc, which);
+}
+
+}  // namespace
+
+extern "C" {
+
+int pd_reserve(pd_ctx* c, int32_t T) {
+  if (!c || T < 1) return PD_ERR_ARG;
+  CK(cudaSetDevice(c->device));
+  if (c->batch) return batch_reserve(c, T);
+  return reserve_single(c, T);
 }
 
 int pd_rollout(pd_ctx* c, int32_t T, const double* q0, const double* v0, const double* f_ext, int64_t f_stride,
@@ -532,26 +590,14 @@ int pd_rollout(pd_ctx* c, int32_t T, const double* q0, const double* v0, const d
   if (!c) return PD_ERR_ARG;
   if (!c->factored) return fail(c, PD_ERR_NOT_FACTORED, "pd_factor must run before pd_rollout");
   if (T < 1 || !q0 || !v0) return fail(c, PD_ERR_ARG, "T >= 1 and q0, v0 are required");
-  const size_t nv3 = 3 * (size_t)c->n_v;
-  if (f_stride != 0 && f_stride != (int64_t)nv3) return fail(c, PD_ERR_ARG, "f_ext_stride must be 0 or 3*n_v");
   CK(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
+  if (c->batch) return batch_rollout(c, T, q0, v0, f_ext, f_stride, qT, vT, s, true);
+  const size_t nv3 = 3 * (size_t)c->n_v;
+  if (f_stride != 0 && f_stride != (int64_t)nv3) return fail(c, PD_ERR_ARG, "f_ext_stride must be 0 or 3*n_v");
   Dev& d = c->d;
   int r;
-  if (c->ckpt_cap < T) {
-    if (c->ckpt) cudaFree(c->ckpt);
-    if (c->tau) cudaFree(c->tau);
-    if (c->phase_count) cudaFree(c->phase_count);
-    c->ckpt = nullptr;
-    c->tau = nullptr;
-    c->phase_count = nullptr;
-    c->ckpt_cap = 0;
-    if (cudaMalloc(&c->ckpt, (size_t)(T + 1) * nv3 * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&c->tau, (size_t)T * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&c->phase_count, 2 * (size_t)T * sizeof(int)) != cudaSuccess)
-      return fail(c, PD_ERR_OOM, "checkpoint allocation for %d steps", T);
-    c->ckpt_cap = T;
-  }
+  if ((r = reserve_single(c, T))) return r;
   // host pointers are staged through one device buffer
   const bool hq = !is_device_ptr(q0), hv = !is_device_ptr(v0), hf = f_ext && !is_device_ptr(f_ext);
   const bool hqo = qT && !is_device_ptr(qT), hvo = vT && !is_device_ptr(vT);
@@ -568,30 +614,24 @@ int pd_rollout(pd_ctx* c, int32_t T, const double* q0, const double* v0, const d
   if (hq) { CK(cudaMemcpyAsync(st_q, q0, nv3 * sizeof(double), cudaMemcpyHostToDevice, s)); q0d = st_q; }
   if (hv) { CK(cudaMemcpyAsync(st_v, v0, nv3 * sizeof(double), cudaMemcpyHostToDevice, s)); v0d = st_v; }
   if (hf) { CK(cudaMemcpyAsync(st_f, f_ext, nf_ext * sizeof(double), cudaMemcpyHostToDevice, s)); fd = st_f; }
-  d.ckpt = c->ckpt;
-  d.tau = c->tau;
-  d.phase_count = c->phase_count;
-  d.T = T;
-  CK(cudaMemsetAsync(c->tau, 0, (size_t)T * sizeof(double), s));
-  CK(cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), s));  // per-rollout statistics and flags
-  CK(cudaMemsetAsync(d.sstar, 0, 3 * sizeof(double) * (size_t)c->n_e, s));  // no prox warm start across rollouts
-  const int pgrid = c->opt.persistent ? pdk::persistent_grid(d) : 0;
+  double* qTd = qT ? (hqo ? st_qo : qT) : nullptr;
+  double* vTd = vT ? (hvo ? st_vo : vT) : nullptr;
+  int pgrid = 0;
+  if (c->opt.persistent && (r = grid_of(c, false, &pgrid))) return r;
   if (pgrid > 0) {
     // one cooperative launch for all T steps
-    pdk::RollArgs ra;
-    ra.T = T;
-    ra.q0 = q0d;
-    ra.v0 = v0d;
-    ra.fext = fd;
-    ra.f_stride = f_stride;
-    ra.qT = qT ? (hqo ? st_qo : qT) : nullptr;
-    ra.vT = vT ? (hvo ? st_vo : vT) : nullptr;
-    ra.ckpt = c->ckpt;
-    ra.sq = c->sq;
-    ra.sv = c->sv;
-    CK(pdk::launch_fwd_rollout(d, s, ra, pgrid));
-    c->launches += 1;
+    if ((r = enqueue_fwd_single(c, T, q0d, v0d, fd, f_stride, qTd, vTd, s, pgrid))) return r;
   } else {
+    // per-phase kernels: no precision escalation (its kernels are compiled for one precision)
+    const int escalate = d.escalate;
+    d.escalate = 0;
+    d.ckpt = c->ckpt;
+    d.tau = c->tau;
+    d.phase_count = c->phase_count;
+    d.T = T;
+    CK(cudaMemsetAsync(c->tau, 0, (size_t)T * sizeof(double), s));
+    CK(cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), s));
+    CK(cudaMemsetAsync(d.sstar, 0, 3 * sizeof(double) * (size_t)c->n_e, s));
     const int max_iter = c->opt.fixed_iters > 0 ? c->opt.fixed_iters : c->opt.k_max + 1;
     const int* done_flag = &d.ctrl->done;
     for (int t = 0; t < T; ++t) {
@@ -621,39 +661,37 @@ int pd_rollout(pd_ctx* c, int32_t T, const double* q0, const double* v0, const d
       if (r) return r;
       CK(cudaGetLastError());
       const bool last = t == T - 1;
-      double* qo = last && qT ? (hqo ? st_qo : qT) : c->sq;
-      double* vo = last && vT ? (hvo ? st_vo : vT) : c->sv;
+      double* qo = last && qTd ? qTd : c->sq;
+      double* vo = last && vTd ? vTd : c->sv;
       pdk::launch_step_end(d, s, qo, vo, c->ckpt + (size_t)(t + 1) * nv3, c->tau);
       c->launches += c->model == PD_NEOHOOKEAN ? 2 : 1;
       CK(cudaGetLastError());
     }
+    d.escalate = escalate;
+    c->last_T = T;
   }
   if (hqo) CK(cudaMemcpyAsync(qT, st_qo, nv3 * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (hvo) CK(cudaMemcpyAsync(vT, st_vo, nv3 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  Ctrl hc;
-  CK(cudaMemcpyAsync(&hc, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  if (c->profiling) {
-    prof_harvest(c, T);
-    for (int i = 0; i < 8; ++i) {
-      c->prof.phase_ms[i] += hc.phase_ns[i] * 1e-6;
-      c->prof.work_ms[i] += hc.work_ns[i] * 1e-6;
-    }
-  }
-  c->last_T = T;
-  pd_stats& st = c->stats;
-  st.steps = T;
-  st.iters_total = hc.iters_total;
-  st.iters_max = hc.iters_max;
-  st.aa_resets = hc.resets;
-  st.not_converged = hc.not_converged;
-  st.tau_half = hc.tau_half;
-  st.tau_one = hc.tau_one;
-  st.status_flags = hc.status;
-  st.last_rho = hc.last_rho;
-  if (hc.status & 4) return fail(c, PD_ERR_TIMEOUT, "a grid barrier of the persistent rollout timed out");
-  if (hc.status & 1) return fail(c, PD_ERR_NUMERIC, "non-finite value in the right-hand side");
-  if (hc.not_converged) return fail(c, PD_ERR_NOT_CONVERGED, "%d step(s) hit k_max", hc.not_converged);
+  c->pending = 0;
+  return collect_single(c, s, 1);
+}
+
+int pd_rollout_enqueue(pd_ctx* c, int32_t T, const double* q0, const double* v0, const double* f_ext,
+                       int64_t f_stride, double* qT, double* vT, void* stream) {
+  if (!c) return PD_ERR_ARG;
+  if (!c->factored) return fail(c, PD_ERR_NOT_FACTORED, "pd_factor must run before pd_rollout_enqueue");
+  if (T < 1 || !q0 || !v0) return fail(c, PD_ERR_ARG, "T >= 1 and q0, v0 are required");
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (c->batch) return batch_rollout(c, T, q0, v0, f_ext, f_stride, qT, vT, s, false);
+  if (f_stride != 0 && f_stride != 3 * (int64_t)c->n_v) return fail(c, PD_ERR_ARG, "f_ext_stride must be 0 or 3*n_v");
+  int r, grid = 0;
+  if (!c->opt.persistent) return fail(c, PD_ERR_ARG, "pd_rollout_enqueue needs options.persistent = 1");
+  if ((r = grid_of(c, false, &grid))) return r;
+  if (grid <= 0) return fail(c, PD_ERR_ARG, "no co-resident grid for the persistent rollout");
+  if ((r = reserve_enqueue(c, T, s))) return r;
+  if ((r = enqueue_fwd_single(c, T, q0, v0, f_ext, f_stride, qT, vT, s, grid))) return r;
+  c->pending |= 1;
   return PD_OK;
 }
 
@@ -668,10 +706,11 @@ int pd_backward(pd_ctx* c, const double* dqT, const double* dvT, double* dq0, do
   if (!c->factored) return fail(c, PD_ERR_NOT_FACTORED, "pd_factor must run before pd_backward");
   if (c->last_T < 1) return fail(c, PD_ERR_NO_CHECKPOINT, "no recorded rollout");
   if (!dqT) return fail(c, PD_ERR_ARG, "dqT is required");
-  const size_t nv3 = 3 * (size_t)c->n_v;
-  if (df_stride != 0 && df_stride != (int64_t)nv3) return fail(c, PD_ERR_ARG, "df_stride must be 0 or 3*n_v");
   CK(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
+  if (c->batch) return batch_backward(c, dqT, dvT, dq0, dv0, dE, dnu, df_ext, df_stride, s, true);
+  const size_t nv3 = 3 * (size_t)c->n_v;
+  if (df_stride != 0 && df_stride != (int64_t)nv3) return fail(c, PD_ERR_ARG, "df_stride must be 0 or 3*n_v");
   Dev& d = c->d;
   const int T = c->last_T;
   int r;
@@ -696,25 +735,13 @@ int pd_backward(pd_ctx* c, const double* dqT, const double* dvT, double* dq0, do
   double* dEd = h_E ? st_E : dE;
   double* dnud = h_nu ? st_nu : dnu;
   double* dfd = h_df ? st_df : df_ext;
-  if (dfd && df_stride == 0) CK(cudaMemsetAsync(dfd, 0, nv3 * sizeof(double), s));
-  const int pgrid = c->opt.persistent ? pdk::persistent_grid_bwd(d) : 0;
+  int pgrid = 0;
+  if (c->opt.persistent && (r = grid_of(c, true, &pgrid))) return r;
   if (pgrid > 0) {
     // one cooperative launch for the adjoint of all T steps
-    pdk::BwdArgs ba;
-    ba.T = T;
-    ba.dqT = dqTd;
-    ba.dvT = dvTd;
-    ba.dq0 = dq0d;
-    ba.dv0 = dv0d;
-    ba.dE = dEd;
-    ba.dnu = dnud;
-    ba.df = dfd;
-    ba.df_stride = df_stride;
-    ba.ckpt = c->ckpt;
-    CK(cudaMemsetAsync(&d.ctrl->bar_count, 0, 2 * sizeof(unsigned int), s));
-    CK(pdk::launch_bwd_rollout(d, s, ba, pgrid));
-    c->launches += 1;
+    if ((r = enqueue_bwd_single(c, dqTd, dvTd, dq0d, dv0d, dEd, dnud, dfd, df_stride, s, pgrid))) return r;
   } else {
+    if (dfd && df_stride == 0) CK(cudaMemsetAsync(dfd, 0, nv3 * sizeof(double), s));
     pdk::launch_bwd_begin(d, s, dqTd, dvTd);
     c->launches += 1;
     CK(cudaGetLastError());
@@ -746,21 +773,46 @@ int pd_backward(pd_ctx* c, const double* dqT, const double* dvT, double* dq0, do
   if (h_E) CK(cudaMemcpyAsync(dE, st_E, c->n_e * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (h_nu) CK(cudaMemcpyAsync(dnu, st_nu, sizeof(double), cudaMemcpyDeviceToHost, s));
   if (h_df) CK(cudaMemcpyAsync(df_ext, st_df, ndf * sizeof(double), cudaMemcpyDeviceToHost, s));
-  Ctrl hc;
-  CK(cudaMemcpyAsync(&hc, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  c->stats.adj_iters_total = hc.adj_iters_total;
-  c->stats.adj_iters_max = hc.adj_iters_max;
-  c->stats.adj_not_converged = hc.adj_not_converged;
-  c->stats.status_flags = hc.status;
-  if (hc.status & 4) return fail(c, PD_ERR_TIMEOUT, "a grid barrier of the persistent adjoint timed out");
-  if (hc.status & 2) return fail(c, PD_ERR_NUMERIC, "adjoint operator A - K not positive along a CG direction");
-  if (hc.adj_not_converged) return fail(c, PD_ERR_NOT_CONVERGED, "%d adjoint solve(s) hit adj_max_iters", hc.adj_not_converged);
+  c->pending = 0;
+  return collect_single(c, s, 2);
+}
+
+int pd_backward_enqueue(pd_ctx* c, const double* dqT, const double* dvT, double* dq0, double* dv0, double* dE,
+                        double* dnu, double* df_ext, int64_t df_stride, void* stream) {
+  if (!c) return PD_ERR_ARG;
+  if (!c->factored) return fail(c, PD_ERR_NOT_FACTORED, "pd_factor must run before pd_backward_enqueue");
+  if (c->last_T < 1) return fail(c, PD_ERR_NO_CHECKPOINT, "no recorded or enqueued rollout");
+  if (!dqT) return fail(c, PD_ERR_ARG, "dqT is required");
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (c->batch) return batch_backward(c, dqT, dvT, dq0, dv0, dE, dnu, df_ext, df_stride, s, false);
+  if (df_stride != 0 && df_stride != 3 * (int64_t)c->n_v) return fail(c, PD_ERR_ARG, "df_stride must be 0 or 3*n_v");
+  int r, grid = 0;
+  if (!c->opt.persistent) return fail(c, PD_ERR_ARG, "pd_backward_enqueue needs options.persistent = 1");
+  if ((r = grid_of(c, true, &grid))) return r;
+  if (grid <= 0) return fail(c, PD_ERR_ARG, "no co-resident grid for the persistent adjoint");
+  if ((r = enqueue_bwd_single(c, dqT, dvT, dq0, dv0, dE, dnu, df_ext, df_stride, s, grid))) return r;
+  c->pending |= 2;
   return PD_OK;
+}
+
+int pd_collect(pd_ctx* c, void* stream) {
+  if (!c) return PD_ERR_ARG;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (c->batch) return batch_collect(c, s);
+  const int which = c->pending;
+  c->pending = 0;
+  if (!which) {
+    CK(cudaStreamSynchronize(s));
+    return PD_OK;
+  }
+  return collect_single(c, s, which);
 }
 
 int pd_solve(pd_ctx* c, const double* b, double* x, void* stream) {
   if (!c) return PD_ERR_ARG;
+  if (c->batch) return fail(c, PD_ERR_ARG, "pd_solve is single-instance only");
   if (!c->factored) return fail(c, PD_ERR_NOT_FACTORED, "pd_factor must run before pd_solve");
   if (!b || !x) return fail(c, PD_ERR_ARG, "b and x are required");
   CK(cudaSetDevice(c->device));
@@ -772,6 +824,7 @@ int pd_solve(pd_ctx* c, const double* b, double* x, void* stream) {
 
 int pd_profile(pd_ctx* c, int32_t enable) {
   if (!c) return PD_ERR_ARG;
+  if (c->batch) return fail(c, PD_ERR_ARG, "pd_profile is single-instance only");
   c->profiling = enable != 0;
   c->prof = pd_profile_out{};
   c->prof_used = 0;
@@ -789,11 +842,13 @@ int pd_get_profile(const pd_ctx* c, pd_profile_out* out) {
 
 int pd_get_mass(const pd_ctx* c, double* m) {
   if (!c || !m) return PD_ERR_ARG;
+  if (c->batch) return batch_get_mass(c, m);
   std::memcpy(m, c->mass.data(), c->mass.size() * sizeof(double));
   return PD_OK;
 }
 
 int pd_get_checkpoint(const pd_ctx* c, int32_t t, double* q_host) {
+  if (c && c->batch) return batch_get_checkpoint(c, t, q_host);
   if (!c || !q_host || t < 0 || t > c->last_T || !c->ckpt) return PD_ERR_ARG;
   const size_t nv3 = 3 * (size_t)c->n_v;
   if (cudaMemcpy(q_host, c->ckpt + (size_t)t * nv3, nv3 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -802,6 +857,7 @@ int pd_get_checkpoint(const pd_ctx* c, int32_t t, double* q_host) {
 }
 
 int pd_get_tau(const pd_ctx* c, double* tau_host, int32_t T) {
+  if (c && c->batch) return batch_get_tau(c, tau_host, T);
   if (!c || !tau_host || T < 1 || T > c->last_T || !c->tau) return PD_ERR_ARG;
   if (cudaMemcpy(tau_host, c->tau, (size_t)T * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return PD_ERR_CUDA;
   return PD_OK;
@@ -817,6 +873,7 @@ int pd_get_stats(const pd_ctx* c, pd_stats* out) {
 void pd_destroy(pd_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
+  if (c->batch) batch_destroy(c);
   for (void* p : c->allocs) cudaFree(p);
   for (void* p : c->factor_allocs) cudaFree(p);
   if (c->ckpt) cudaFree(c->ckpt);
@@ -833,7 +890,7 @@ void pd_destroy(pd_ctx* c) {
 }  // extern "C"
 
 void pd_internal_state(pd_ctx* c, const pdk::Dev** d, int* device, int* factored) {
-  *d = &c->d;
+  *d = c->batch ? nullptr : &c->d;
   *device = c->device;
   *factored = c->factored ? 1 : 0;
 }

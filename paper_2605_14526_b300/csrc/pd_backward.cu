@@ -15,6 +15,7 @@
 // persistent backward kernel (one cooperative launch for all T steps).
 #include <cuda_runtime.h>
 
+#include "pd_coop.h"
 #include "pd_grid.cuh"
 #include "pd_launch.h"
 #include "pd_phases.cuh"
@@ -456,7 +457,7 @@ __global__ void __launch_bounds__(kVtxBlock) k_pcg_init_z(Dev d) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   double part[1] = {0.0};
   if (v < d.n_v) init_z_item(d, v, part);
-  block_reduce_store<1>(part, d.red);
+  block_reduce_store<1>(part, d.red, blockIdx.x);
   if (last_block(&d.ctrl->ticket[TK_PCG_INIT]) && threadIdx.x == 0) {
     double s[1] = {sum_partials(d.red, gridDim.x, 0)};
     init_z_finish(d.ctrl, s);
@@ -469,7 +470,7 @@ __global__ void __launch_bounds__(kVtxBlock) k_pcg_w(Dev d) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   double part[1] = {0.0};
   if (v < d.n_v) pcg_w_item<T>(d, v, part);
-  block_reduce_store<1>(part, d.red);
+  block_reduce_store<1>(part, d.red, blockIdx.x);
   if (last_block(&d.ctrl->ticket[TK_PCG_W]) && threadIdx.x == 0) {
     double s[1] = {sum_partials(d.red, gridDim.x, 0)};
     pcg_w_finish(d.ctrl, s);
@@ -488,7 +489,7 @@ __global__ void __launch_bounds__(kVtxBlock) k_pcg_z(Dev d) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   double part[1] = {0.0};
   if (v < d.n_v) pcg_z_item(d, v, part);
-  block_reduce_store<1>(part, d.red);
+  block_reduce_store<1>(part, d.red, blockIdx.x);
   if (last_block(&d.ctrl->ticket[TK_PCG_Z]) && threadIdx.x == 0) {
     double s[1] = {sum_partials(d.red, gridDim.x, 0)};
     pcg_z_finish(d, d.ctrl, s);
@@ -508,7 +509,7 @@ __global__ void __launch_bounds__(kVtxBlock) k_route(Dev d, const double* qstar,
   double part[3] = {0.0, 0.0, 0.0};
   if (tid < d.n_v) route_vertex_item(d, tid, df, df_acc);
   else if (tid < d.n_v + d.n_e) route_elem_item(d, tid - d.n_v, qstar, qt, *tau_t, part);
-  block_reduce_store<3>(part, d.red);
+  block_reduce_store<3>(part, d.red, blockIdx.x);
   if (last_block(&d.ctrl->ticket[TK_ROUTE]) && threadIdx.x == 0) {
     double s[3];
     for (int j = 0; j < 3; ++j) s[j] = sum_partials(d.red, gridDim.x, j);
@@ -521,7 +522,7 @@ __global__ void __launch_bounds__(kVtxBlock) k_chain(Dev d, double* dE, double* 
   double part[4] = {0.0, 0.0, 0.0, 0.0};
   const Ctrl* c = d.ctrl;
   if (e < d.n_e) chain_item(d, e, dE, c->acc_mu, c->acc_lam, c->acc_k, part);
-  block_reduce_store<4>(part, d.red);
+  block_reduce_store<4>(part, d.red, blockIdx.x);
   if (last_block(&d.ctrl->ticket[TK_CHAIN]) && threadIdx.x == 0) {
     double s[4];
     for (int j = 0; j < 4; ++j) s[j] = sum_partials(d.red, gridDim.x, j);
@@ -541,66 +542,66 @@ __global__ void k_bwd_finish(Dev d, double* dq0, double* dv0) {
 // ------------------------------------------------------------ persistent backward
 
 template <typename T>
-__global__ void __launch_bounds__(kPersistBlock, 2) k_bwd_rollout(Dev d, BwdArgs a) {
+__device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a, const Team tm) {
   __shared__ BwdState S;
   __shared__ double sums[4];
   const int tid = threadIdx.x;
-  const int gtid = blockIdx.x * blockDim.x + tid;
-  const int gthreads = gridDim.x * blockDim.x;
+  const int gtid = tm.b * blockDim.x + tid;
+  const int gthreads = tm.nb * blockDim.x;
   const int lane = tid & 31, gwarp = gtid >> 5, nwarps = gthreads >> 5;
   const size_t nv3 = 3 * (size_t)d.n_v;
-  const bool writer = blockIdx.x == 0;
-  const Range re = block_range(d.n_e);
-  const Range rv = block_range(d.n_v);
-  const Range rb = block_range(d.n_v > d.n_e ? d.n_v : d.n_e);
-  const Range rt = block_range(d.n_v + d.n_e);
+  const bool writer = tm.b == 0;
+  const Range re = block_range(tm, d.n_e);
+  const Range rv = block_range(tm, d.n_v);
+  const Range rb = block_range(tm, d.n_v > d.n_e ? d.n_v : d.n_e);
+  const Range rt = block_range(tm, d.n_v + d.n_e);
   if (tid == 0) {
     S.adj_k = S.adj_done = S.status = S.adj_iters_total = S.adj_iters_max = S.adj_not_converged = 0;
     S.rz = S.rz0 = S.alpha = S.beta = S.acc_mu = S.acc_lam = S.acc_k = S.dnu_acc = 0.0;
   }
   for (int i = rb.lo + tid; i < rb.hi; i += blockDim.x) bwd_begin_item(d, i, a.dqT, a.dvT);
-  bool ok = grid_sync(d);
+  bool ok = grid_sync(d, tm);
   for (int t = a.T - 1; t >= 0 && ok; --t) {
     const double* qstar = a.ckpt + (size_t)(t + 1) * nv3;
     const double* qt = a.ckpt + (size_t)t * nv3;
     const double tau = __ldcg(&d.tau[t]);
     for (int e = re.lo + tid; e < re.hi; e += blockDim.x) bwd_setup_item<T>(d, e, qstar, tau);
     for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) bwd_init_item(d, v);
-    if (!(ok = grid_sync(d))) break;
+    if (!(ok = grid_sync(d, tm))) break;
     for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, sg, lane);
-    if (!(ok = grid_sync(d))) break;
+    if (!(ok = grid_sync(d, tm))) break;
     for (int j = gwarp; j < d.n_f; j += nwarps) spmv_st_row(d, d.y, d.z, j, lane);
-    if (!(ok = grid_sync(d))) break;
+    if (!(ok = grid_sync(d, tm))) break;
     double p1[1] = {0.0};
     for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) init_z_item(d, v, p1);
-    if (!(ok = grid_reduce<1>(d, p1, sums))) break;
+    if (!(ok = grid_reduce<1>(d, tm, p1, sums))) break;
     if (tid == 0) init_z_finish(&S, sums);
     __syncthreads();
     while (!S.adj_done) {
       for (int e = re.lo + tid; e < re.hi; e += blockDim.x) kapply_item<T>(d, e, d.pdir);
-      if (!(ok = grid_sync(d))) break;
+      if (!(ok = grid_sync(d, tm))) break;
       double pw[1] = {0.0};
       for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) pcg_w_item<T>(d, v, pw);
-      if (!(ok = grid_reduce<1>(d, pw, sums))) break;
+      if (!(ok = grid_reduce<1>(d, tm, pw, sums))) break;
       if (tid == 0) pcg_w_finish(&S, sums);
       __syncthreads();
       if (S.adj_done) break;
       const double alpha = S.alpha;
       for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) pcg_r_item(d, v, alpha);
-      if (!(ok = grid_sync(d))) break;
+      if (!(ok = grid_sync(d, tm))) break;
       for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, sg, lane);
-      if (!(ok = grid_sync(d))) break;
+      if (!(ok = grid_sync(d, tm))) break;
       for (int j = gwarp; j < d.n_f; j += nwarps) spmv_st_row(d, d.y, d.z, j, lane);
-      if (!(ok = grid_sync(d))) break;
+      if (!(ok = grid_sync(d, tm))) break;
       double prz[1] = {0.0};
       for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) pcg_z_item(d, v, prz);
-      if (!(ok = grid_reduce<1>(d, prz, sums))) break;
+      if (!(ok = grid_reduce<1>(d, tm, prz, sums))) break;
       if (tid == 0) pcg_z_finish(d, &S, sums);
       __syncthreads();
       if (S.adj_done) break;
       const double beta = S.beta;
       for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) pcg_p_item(d, v, beta);
-      if (!(ok = grid_sync(d))) break;
+      if (!(ok = grid_sync(d, tm))) break;
     }
     if (!ok) break;
     double* df_t = a.df ? (a.df_stride ? a.df + (size_t)t * nv3 : a.df) : nullptr;
@@ -609,7 +610,7 @@ __global__ void __launch_bounds__(kPersistBlock, 2) k_bwd_rollout(Dev d, BwdArgs
       if (i < d.n_v) route_vertex_item(d, i, df_t, a.df_stride == 0 ? 1 : 0);
       else route_elem_item(d, i - d.n_v, qstar, qt, tau, p3);
     }
-    if (!(ok = grid_reduce<3>(d, p3, sums))) break;
+    if (!(ok = grid_reduce<3>(d, tm, p3, sums))) break;
     if (tid == 0) route_finish(&S, sums);
     __syncthreads();
   }
@@ -617,7 +618,7 @@ __global__ void __launch_bounds__(kPersistBlock, 2) k_bwd_rollout(Dev d, BwdArgs
     double p4[4] = {0.0, 0.0, 0.0, 0.0};
     const double am = S.acc_mu, al = S.acc_lam, ak = S.acc_k;
     for (int e = re.lo + tid; e < re.hi; e += blockDim.x) chain_item(d, e, a.dE, am, al, ak, p4);
-    ok = grid_reduce<4>(d, p4, sums);
+    ok = grid_reduce<4>(d, tm, p4, sums);
     if (ok && writer && tid == 0) {
       const double v = chain_nu(d, am, al, ak, sums);
       if (a.dnu) *a.dnu = v;
@@ -639,6 +640,38 @@ __global__ void __launch_bounds__(kPersistBlock, 2) k_bwd_rollout(Dev d, BwdArgs
     c->acc_k = S.acc_k;
     atomicOr(&c->status, S.status);
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPersistBlock, 2) k_bwd_rollout(Dev d, BwdArgs a) {
+  bwd_rollout_body<T>(d, a, Team{(int)blockIdx.x, (int)gridDim.x});
+}
+
+// team[blockIdx.x] = {instance, block index in its team, team size, 0}
+template <typename T>
+__global__ void __launch_bounds__(kPersistBlock, 2) k_bwd_batch(const Dev* __restrict__ devs, const int4* __restrict__ team,
+                                                                const InstOff* __restrict__ off, BatchBwd br) {
+  __shared__ Dev sd;
+  __shared__ BwdArgs sa;
+  const int4 tb = team[blockIdx.x];
+  if (threadIdx.x == 0) {
+    sd = devs[tb.x];
+    const long long v3 = 3 * off[tb.x].v;
+    BwdArgs a;
+    a.T = br.T;
+    a.dqT = br.dqT + v3;
+    a.dvT = br.dvT ? br.dvT + v3 : nullptr;
+    a.dq0 = br.dq0 ? br.dq0 + v3 : nullptr;
+    a.dv0 = br.dv0 ? br.dv0 + v3 : nullptr;
+    a.dE = br.dE ? br.dE + off[tb.x].e : nullptr;
+    a.dnu = br.dnu ? br.dnu + tb.x : nullptr;
+    a.df = br.df ? br.df + v3 : nullptr;
+    a.df_stride = br.df_stride;
+    a.ckpt = sd.ckpt;
+    sa = a;
+  }
+  __syncthreads();
+  bwd_rollout_body<T>(sd, sa, Team{tb.y, tb.z});
 }
 
 // ------------------------------------------------------------ wrappers
@@ -690,24 +723,31 @@ void launch_bwd_finish(const Dev& d, cudaStream_t s, double* dq0, double* dv0) {
   k_bwd_finish<<<nblk(3 * d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d, dq0, dv0);
 }
 
-static int coop_grid_b(const void* fn) {
-  int dev = 0, sms = 0, coop = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPersistBlock, 0) != cudaSuccess) return 0;
-  if (per_sm < 1) return 0;
-  return sms * (per_sm < 2 ? per_sm : 2);
+static const void* bwd_fn(bool fp32, bool batch) {
+  if (batch) return fp32 ? (const void*)k_bwd_batch<float> : (const void*)k_bwd_batch<double>;
+  return fp32 ? (const void*)k_bwd_rollout<float> : (const void*)k_bwd_rollout<double>;
 }
 
-int persistent_grid_bwd(const Dev& d) {
-  return coop_grid_b(d.local_fp32 ? (const void*)k_bwd_rollout<float> : (const void*)k_bwd_rollout<double>);
+static int grid_for(const void* fn, int blocks_per_sm) {
+  int sms = 0;
+  const int per = coop_blocks_per_sm(fn, &sms);
+  if (per < 1) return 0;
+  return sms * (blocks_per_sm >= 1 && blocks_per_sm < per ? blocks_per_sm : per);
 }
+
+int persistent_grid_bwd(const Dev& d, int blocks_per_sm) { return grid_for(bwd_fn(d.local_fp32, false), blocks_per_sm); }
+
+int persistent_grid_bwd_batch(bool fp32, int blocks_per_sm) { return grid_for(bwd_fn(fp32, true), blocks_per_sm); }
 
 cudaError_t launch_bwd_rollout(const Dev& d, cudaStream_t s, const BwdArgs& a, int grid) {
-  void* args[] = {(void*)&d, (void*)&a};
-  const void* fn = d.local_fp32 ? (const void*)k_bwd_rollout<float> : (const void*)k_bwd_rollout<double>;
-  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPersistBlock), args, 0, s);
+  if (d.local_fp32) return coop_launch(k_bwd_rollout<float>, grid, s, d, a);
+  return coop_launch(k_bwd_rollout<double>, grid, s, d, a);
+}
+
+cudaError_t launch_bwd_batch(bool fp32, const Dev* devs, const int4* team, const InstOff* off, const BatchBwd& br,
+                             int grid, cudaStream_t s) {
+  if (fp32) return coop_launch(k_bwd_batch<float>, grid, s, devs, team, off, br);
+  return coop_launch(k_bwd_batch<double>, grid, s, devs, team, off, br);
 }
 
 }  // namespace pdk

@@ -12,7 +12,7 @@ namespace pdk {
 // ------------------------------------------------------------ reductions
 
 template <int NV>
-__device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* red) {
+__device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* red, int row) {
   __shared__ double sh[32][NV > 0 ? NV : 1];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -27,7 +27,7 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* red)
     double s = 0.0;
     const int nw = (blockDim.x + 31) >> 5;
     for (int w = 0; w < nw; ++w) s += sh[w][threadIdx.x];
-    red[(size_t)blockIdx.x * kRed + threadIdx.x] = s;
+    red[(size_t)row * kRed + threadIdx.x] = s;
   }
 }
 
@@ -155,5 +155,6 @@ __device__ __forceinline__ void gather_contrib(const Dev& d, int v, double* acc)
     for (int i = 0; i < 3; ++i) acc[i] += (double)cb[3 * (size_t)ic + i];
   }
 }
+
 
 }  // namespace pdk

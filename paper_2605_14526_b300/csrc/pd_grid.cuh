@@ -28,19 +28,32 @@ __device__ __forceinline__ void st_relaxed(unsigned int* p, unsigned int v) {
   asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Grid barrier; with NV > 0 also a sum over blocks of NV partial values per
-// block, returned in `sums` (shared) to every block. Returns false in every
-// thread of the block if the wait timed out.
+// The blocks of a persistent launch form teams: team-local block index `b`
+// of `nb` blocks; one team works on one problem instance (the whole grid in
+// a single-instance launch). Barriers and reductions span one team.
+struct Team {
+  int b, nb;
+};
+
+// Team barrier; with NV > 0 also a sum over the team's blocks of NV partial
+// values per block, returned in `sums` (shared) to every block. Returns false
+// in every thread of the block if the wait timed out. A one-block team needs
+// no global memory traffic at all.
 template <int NV>
-__device__ __forceinline__ bool grid_reduce(const Dev& d, double (&part)[NV > 0 ? NV : 1], double* sums) {
+__device__ __forceinline__ bool grid_reduce(const Dev& d, Team tm, double (&part)[NV > 0 ? NV : 1], double* sums) {
   __shared__ int s_last, s_fail;
-  if constexpr (NV > 0) block_reduce_store<NV>(part, d.red);
+  if (tm.nb == 1) {
+    if constexpr (NV > 0) block_reduce_to<NV>(part, sums);
+    else __syncthreads();
+    return true;
+  }
+  if constexpr (NV > 0) block_reduce_store<NV>(part, d.red, tm.b);
   __syncthreads();
   Ctrl* c = d.ctrl;
   if (threadIdx.x == 0) {
     const unsigned int g = ld_acquire(&c->bar_gen);
     const unsigned int arrived = atom_add_acq_rel(&c->bar_count, 1u);
-    s_last = arrived == gridDim.x - 1;
+    s_last = arrived == (unsigned int)tm.nb - 1;
     s_fail = 0;
     if (!s_last) {
       unsigned int it = 0;
@@ -64,7 +77,7 @@ __device__ __forceinline__ bool grid_reduce(const Dev& d, double (&part)[NV > 0 
       double acc[NV];
 #pragma unroll
       for (int j = 0; j < NV; ++j) acc[j] = 0.0;
-      for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+      for (int b = threadIdx.x; b < tm.nb; b += blockDim.x) {
         double v[NV];
 #pragma unroll
         for (int j = 0; j < NV; ++j) v[j] = __ldcg(&d.red[(size_t)b * kRed + j]);
@@ -86,18 +99,18 @@ __device__ __forceinline__ bool grid_reduce(const Dev& d, double (&part)[NV > 0 
   return !s_fail;
 }
 
-__device__ __forceinline__ bool grid_sync(const Dev& d) {
+__device__ __forceinline__ bool grid_sync(const Dev& d, Team tm) {
   double none[1] = {0.0};
-  return grid_reduce<0>(d, none, nullptr);
+  return grid_reduce<0>(d, tm, none, nullptr);
 }
 
-// contiguous range of n items owned by this block
+// contiguous range of n items owned by this block of the team
 struct Range {
   int lo, hi;
 };
-__device__ __forceinline__ Range block_range(int n) {
-  const int chunk = (n + gridDim.x - 1) / gridDim.x;
-  const int lo = min(n, (int)blockIdx.x * chunk);
+__device__ __forceinline__ Range block_range(Team tm, int n) {
+  const int chunk = (n + tm.nb - 1) / tm.nb;
+  const int lo = min(n, tm.b * chunk);
   return {lo, min(n, lo + chunk)};
 }
 

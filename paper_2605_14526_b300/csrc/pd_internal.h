@@ -30,6 +30,11 @@ struct Ctrl {
   double dgg[kMaxAA];
   double dq_norm2, qprev_norm2;   // ||q^{k+1} - q^k||^2, ||q^k||^2 from the last update
   double db_norm2, bprev_norm2;   // ||b^k - b^{k-1}||^2, ||b^{k-1}||^2
+  // precision escalation of the FP32 local step (persistent rollouts)
+  int hi;            // 1: the local step runs in FP64 for the rest of the rollout
+  int since;         // iterations since the gate distance last halved
+  int escalations;   // switches to FP64 (at most one per rollout)
+  double gmin;       // smallest gate distance of this step
   // statistics (accumulated over a rollout)
   int iters_total, iters_max, resets, not_converged, tau_half, tau_one;
   int adj_iters_total, adj_iters_max, adj_not_converged;
@@ -60,6 +65,7 @@ struct Dev {
   int model;          // 0 corotated, 1 Neo-Hookean
   int local_fp32;
   int aa_m, k_max, fixed_iters, tr_mode, adj_max_iters;
+  int escalate;       // FP32 local step: switch to FP64 after this many iterations without progress (0 = never)
   double h, alpha_d, eps_step, eps_res, eps_abs, eps_tr, adj_tol;
   double g[3];
   double mu_bar, lam_bar, k_bar, mu_ref, beta0, nu;
@@ -110,11 +116,13 @@ struct Dev {
   double* dQ;       // [kMaxAA][n_v][3]
   double* dG;
   void* contrib;    // [n_e][12] float or double
-  void* sstar;      // [n_e][3] float or double: last prox stretches (Newton warm start; <= 0 = none)
+  void* sstar;      // [n_e][3] float: last prox stretches (Newton warm start; <= 0 = none)
   double* red;      // [blocks][kRed]
   Ctrl* ctrl;
 
   // rollout storage
+  double* sq;       // [n_v][3] state carried between steps of a rollout
+  double* sv;
   double* ckpt;     // [(T+1)][n_v][3]
   double* tau;      // [T]
   int* phase_count; // [T][2] local / solve phases run per step
@@ -160,6 +168,32 @@ struct BwdArgs {
   double* df;
   long long df_stride;  // 0: summed into one [n_v][3]; else 3 n_v per step
   const double* ckpt;   // [(T+1)][n_v][3]
+};
+
+// Batched launches: one descriptor for all instances; instance i reads its
+// slice of each concatenated array at its prefix offsets.
+struct InstOff {
+  long long v, e;       // first vertex / element of the instance in the concatenation
+};
+struct BatchFwd {
+  int T;
+  const double* q0;
+  const double* v0;
+  const double* fext;
+  long long f_stride;   // 0, or 3 x (total vertices) per step
+  double* qT;
+  double* vT;
+};
+struct BatchBwd {
+  int T;
+  const double* dqT;
+  const double* dvT;
+  double* dq0;
+  double* dv0;
+  double* dE;
+  double* dnu;          // [instances]
+  double* df;
+  long long df_stride;  // 0, or 3 x (total vertices) per step
 };
 
 }  // namespace pdk

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kVtxBlock) k_assemble(Dev d) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   double part[3] = {0.0, 0.0, 0.0};
   if (v < d.n_v) assemble_item<T>(d, v, k, part);
-  block_reduce_store<3>(part, d.red);
+  block_reduce_store<3>(part, d.red, blockIdx.x);
   if (last_block(&d.ctrl->ticket[TK_ASSEMBLE]) && threadIdx.x == 0) {
     double s[3];
     for (int j = 0; j < 3; ++j) s[j] = sum_partials(d.red, gridDim.x, j);
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kVtxBlock) k_aa(Dev d) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   double part[2 * kMaxAA] = {};
   if (v < d.n_v) aa_item(d, v, a, part);
-  block_reduce_store<2 * kMaxAA>(part, d.red);
+  block_reduce_store<2 * kMaxAA>(part, d.red, blockIdx.x);
   if (last_block(&d.ctrl->ticket[TK_SPMV_T]) && threadIdx.x == 0) {
     double s[2 * kMaxAA];
     for (int j = 0; j < 2 * kMaxAA; ++j) s[j] = sum_partials(d.red, gridDim.x, j);
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kVtxBlock) k_update(Dev d) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   double part[2] = {0.0, 0.0};
   if (v < d.n_v) update_item(d, v, use_hat, nc, gam, part);
-  block_reduce_store<2>(part, d.red);
+  block_reduce_store<2>(part, d.red, blockIdx.x);
   if (last_block(&d.ctrl->ticket[TK_UPDATE]) && threadIdx.x == 0) {
     double s[2] = {sum_partials(d.red, gridDim.x, 0), sum_partials(d.red, gridDim.x, 1)};
     update_finish(d, d.ctrl, s);
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kVtxBlock) k_tr(Dev d) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   double part[4] = {0.0, 0.0, 0.0, 0.0};
   tr_item(d, tid, part);
-  block_reduce_store<4>(part, d.red);
+  block_reduce_store<4>(part, d.red, blockIdx.x);
   if (last_block(&d.ctrl->ticket[TK_TR]) && threadIdx.x == 0) {
     double s[4];
     for (int j = 0; j < 4; ++j) s[j] = sum_partials(d.red, gridDim.x, j);

@@ -55,6 +55,10 @@ extern "C" int pd_solve_noalloc(pd_ctx* ctx, const double* b, double* x, void* s
   const pdk::Dev* d = nullptr;
   int device = 0, factored = 0;
   pd_internal_state(ctx, &d, &device, &factored);
+  if (!d) {
+    pd_internal_set_error(ctx, "pd_solve_noalloc is single-instance only");
+    return PD_ERR_ARG;
+  }
   if (d->n_f > kNoAllocMaxFree) {
     pd_internal_set_error(ctx, "pd_solve_noalloc: the mesh has more free vertices than the fixed scratch holds "
                                "(limit PD_NOALLOC_MAX_FREE = 65536); use pd_solve");

@@ -13,25 +13,47 @@
 // set and every block returns.
 #include <cuda_runtime.h>
 
+#include "pd_coop.h"
 #include "pd_grid.cuh"
 #include "pd_launch.h"
 #include "pd_phases.cuh"
 
 namespace pdk {
 
+// local step / assembly in the kernel's precision T, or in FP64 once an FP32
+// team has escalated
 template <typename T>
-__global__ void __launch_bounds__(kPersistBlock, 2) k_fwd_rollout(Dev d, RollArgs a) {
+__device__ __forceinline__ void local_any(const Dev& d, int e, bool hi) {
+  if constexpr (sizeof(T) == 4) {
+    if (hi) local_item<double>(d, e, d.q);
+    else local_item<float>(d, e, d.q);
+  } else {
+    local_item<T>(d, e, d.q);
+  }
+}
+template <typename T>
+__device__ __forceinline__ void assemble_any(const Dev& d, int v, int k, double* part, bool hi) {
+  if constexpr (sizeof(T) == 4) {
+    if (hi) assemble_item<double>(d, v, k, part);
+    else assemble_item<float>(d, v, k, part);
+  } else {
+    assemble_item<T>(d, v, k, part);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a, const Team tm) {
   __shared__ FwdState S;
   __shared__ double sums[2 * kMaxAA];
   const int tid = threadIdx.x;
-  const int gtid = blockIdx.x * blockDim.x + tid;
-  const int gthreads = gridDim.x * blockDim.x;
+  const int gtid = tm.b * blockDim.x + tid;
+  const int gthreads = tm.nb * blockDim.x;
   const int lane = tid & 31, gwarp = gtid >> 5, nwarps = gthreads >> 5;
   const size_t nv3 = 3 * (size_t)d.n_v;
-  const bool writer = blockIdx.x == 0;
-  const Range re = block_range(d.n_e);
-  const Range rv = block_range(d.n_v);
-  const Range rt = block_range(d.n_e + d.n_v);
+  const bool writer = tm.b == 0;
+  const Range re = block_range(tm, d.n_e);
+  const Range rv = block_range(tm, d.n_v);
+  const Range rt = block_range(tm, d.n_e + d.n_v);
   unsigned long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0}, wk[8] = {0, 0, 0, 0, 0, 0, 0, 0}, t0 = 0;
   auto mark = [&](int p) {
     if (writer && tid == 0) {
@@ -50,6 +72,7 @@ __global__ void __launch_bounds__(kPersistBlock, 2) k_fwd_rollout(Dev d, RollArg
   };
   if (tid == 0) {
     S.iters_total = S.iters_max = S.resets = S.not_converged = S.tau_half = S.tau_one = S.status = 0;
+    S.hi = S.escalations = 0;
     S.last_rho = 0.0;
     for (int i = 0; i < kMaxAA * kMaxAA; ++i) S.gram[i] = 0.0;
     t0 = gtimer();
@@ -61,25 +84,26 @@ __global__ void __launch_bounds__(kPersistBlock, 2) k_fwd_rollout(Dev d, RollArg
     const double* fst = a.fext ? a.fext + (a.f_stride ? (size_t)t * (size_t)a.f_stride : 0) : nullptr;
     if (tid == 0) ctrl_step_reset(&S, t);
     for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) step_begin_item(d, v, qin, vin, fst, a.ckpt + (size_t)t * nv3);
-    if (!(ok = grid_sync(d))) break;
+    if (!(ok = grid_sync(d, tm))) break;
     mark(PH_BEGIN);
     for (;;) {
       const int k = S.k;
-      for (int e = re.lo + tid; e < re.hi; e += blockDim.x) local_item<T>(d, e, d.q);
+      const bool hi = S.hi != 0;   // FP64 local step after an escalation
+      for (int e = re.lo + tid; e < re.hi; e += blockDim.x) local_any<T>(d, e, hi);
       work_done(PH_LOCAL);
-      if (!(ok = grid_sync(d))) break;
+      if (!(ok = grid_sync(d, tm))) break;
       mark(PH_LOCAL);
       double p3[3] = {0.0, 0.0, 0.0};
-      for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) assemble_item<T>(d, v, k, p3);
+      for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) assemble_any<T>(d, v, k, p3, hi);
       work_done(PH_ASSEMBLE);
-      if (!(ok = grid_reduce<3>(d, p3, sums))) break;
+      if (!(ok = grid_reduce<3>(d, tm, p3, sums))) break;
       if (tid == 0) assemble_finish(d, &S, k, sums);
       __syncthreads();
       mark(PH_ASSEMBLE);
       if (S.done) break;
       for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, sg, lane);
       work_done(PH_SPMV_S);
-      if (!(ok = grid_sync(d))) break;
+      if (!(ok = grid_sync(d, tm))) break;
       mark(PH_SPMV_S);
       // S^T y row by row, with the Anderson work of that row's vertex fused in
       const AAView av = aa_view(d, S.pairs, S.ncols, S.head);
@@ -96,7 +120,7 @@ __global__ void __launch_bounds__(kPersistBlock, 2) k_fwd_rollout(Dev d, RollArg
         }
       }
       work_done(PH_AA);
-      if (!(ok = grid_reduce<2 * kMaxAA>(d, pa, sums))) break;
+      if (!(ok = grid_reduce<2 * kMaxAA>(d, tm, pa, sums))) break;
       if (tid == 0) aa_finish(d, &S, av, sums);
       __syncthreads();
       mark(PH_AA);
@@ -106,7 +130,7 @@ __global__ void __launch_bounds__(kPersistBlock, 2) k_fwd_rollout(Dev d, RollArg
       double pu[2] = {0.0, 0.0};
       for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) update_item(d, v, use_hat, nc, gam, pu);
       work_done(PH_UPDATE);
-      if (!(ok = grid_reduce<2>(d, pu, sums))) break;
+      if (!(ok = grid_reduce<2>(d, tm, pu, sums))) break;
       if (tid == 0) update_finish(d, &S, sums);
       __syncthreads();
       mark(PH_UPDATE);
@@ -121,11 +145,11 @@ __global__ void __launch_bounds__(kPersistBlock, 2) k_fwd_rollout(Dev d, RollArg
     if (d.model == 1) {
       double p4[4] = {0.0, 0.0, 0.0, 0.0};
       for (int i = rt.lo + tid; i < rt.hi; i += blockDim.x) tr_item(d, i, p4);
-      if (!(ok = grid_reduce<4>(d, p4, sums))) break;
+      if (!(ok = grid_reduce<4>(d, tm, p4, sums))) break;
       if (tid == 0) tr_finish(d, &S, sums, writer);
       __syncthreads();
     } else {
-      if (!(ok = grid_sync(d))) break;
+      if (!(ok = grid_sync(d, tm))) break;
     }
     mark(PH_END);
   }
@@ -140,6 +164,7 @@ __global__ void __launch_bounds__(kPersistBlock, 2) k_fwd_rollout(Dev d, RollArg
     c->tau_one = S.tau_one;
     c->last_rho = S.last_rho;
     c->k = S.k;
+    c->escalations = S.escalations;
     atomicOr(&c->status, S.status);
     for (int i = 0; i < 8; ++i) {
       c->phase_ns[i] += ph[i];
@@ -148,29 +173,78 @@ __global__ void __launch_bounds__(kPersistBlock, 2) k_fwd_rollout(Dev d, RollArg
   }
 }
 
-// ------------------------------------------------------------ launch
-
-static int coop_grid(const void* fn, int* grid) {
-  int dev = 0, sms = 0, coop = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
-  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return -1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPersistBlock, 0) != cudaSuccess) return -1;
-  if (per_sm < 1) return -1;
-  *grid = sms * (per_sm < 2 ? per_sm : 2);
-  return 0;
+template <typename T>
+__global__ void __launch_bounds__(kPersistBlock, 2) k_fwd_rollout(Dev d, RollArgs a) {
+  fwd_rollout_body<T>(d, a, Team{(int)blockIdx.x, (int)gridDim.x});
 }
 
-int persistent_grid(const Dev& d) {
-  int g = 0;
-  const void* fn = d.local_fp32 ? (const void*)k_fwd_rollout<float> : (const void*)k_fwd_rollout<double>;
-  return coop_grid(fn, &g) == 0 ? g : 0;
+// team[blockIdx.x] = {instance, block index in its team, team size, 0}
+template <typename T>
+__global__ void __launch_bounds__(kPersistBlock, 2) k_fwd_batch(const Dev* __restrict__ devs, const int4* __restrict__ team,
+                                                                const InstOff* __restrict__ off, BatchFwd br) {
+  __shared__ Dev sd;
+  __shared__ RollArgs sa;
+  const int4 tb = team[blockIdx.x];
+  if (threadIdx.x == 0) {
+    sd = devs[tb.x];
+    const long long v3 = 3 * off[tb.x].v;
+    RollArgs a;
+    a.T = br.T;
+    a.q0 = br.q0 + v3;
+    a.v0 = br.v0 + v3;
+    a.fext = br.fext ? br.fext + v3 : nullptr;
+    a.f_stride = br.f_stride;
+    a.qT = br.qT ? br.qT + v3 : nullptr;
+    a.vT = br.vT ? br.vT + v3 : nullptr;
+    a.ckpt = sd.ckpt;
+    a.sq = sd.sq;
+    a.sv = sd.sv;
+    sa = a;
+  }
+  __syncthreads();
+  fwd_rollout_body<T>(sd, sa, Team{tb.y, tb.z});
+}
+
+// ------------------------------------------------------------ launch
+
+int coop_blocks_per_sm(const void* fn, int* sms_out) {
+  int dev = 0, sms = 0, coop = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPersistBlock, 0) != cudaSuccess) return 0;
+  if (sms_out) *sms_out = sms;
+  return per_sm < 2 ? per_sm : 2;
+}
+
+static const void* fwd_fn(bool fp32, bool batch) {
+  if (batch) return fp32 ? (const void*)k_fwd_batch<float> : (const void*)k_fwd_batch<double>;
+  return fp32 ? (const void*)k_fwd_rollout<float> : (const void*)k_fwd_rollout<double>;
+}
+
+int persistent_grid(const Dev& d, int blocks_per_sm) {
+  int sms = 0;
+  const int per = coop_blocks_per_sm(fwd_fn(d.local_fp32, false), &sms);
+  if (per < 1) return 0;
+  return sms * (blocks_per_sm >= 1 && blocks_per_sm < per ? blocks_per_sm : per);
+}
+
+int persistent_grid_batch(bool fp32, int blocks_per_sm) {
+  int sms = 0;
+  const int per = coop_blocks_per_sm(fwd_fn(fp32, true), &sms);
+  if (per < 1) return 0;
+  return sms * (blocks_per_sm >= 1 && blocks_per_sm < per ? blocks_per_sm : per);
 }
 
 cudaError_t launch_fwd_rollout(const Dev& d, cudaStream_t s, const RollArgs& a, int grid) {
-  void* args[] = {(void*)&d, (void*)&a};
-  const void* fn = d.local_fp32 ? (const void*)k_fwd_rollout<float> : (const void*)k_fwd_rollout<double>;
-  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPersistBlock), args, 0, s);
+  if (d.local_fp32) return coop_launch(k_fwd_rollout<float>, grid, s, d, a);
+  return coop_launch(k_fwd_rollout<double>, grid, s, d, a);
+}
+
+cudaError_t launch_fwd_batch(bool fp32, const Dev* devs, const int4* team, const InstOff* off, const BatchFwd& br,
+                             int grid, cudaStream_t s) {
+  if (fp32) return coop_launch(k_fwd_batch<float>, grid, s, devs, team, off, br);
+  return coop_launch(k_fwd_batch<double>, grid, s, devs, team, off, br);
 }
 
 }  // namespace pdk

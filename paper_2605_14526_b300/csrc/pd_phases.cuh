@@ -16,6 +16,8 @@ namespace pdk {
 // per-block shared replica FwdState (persistent rollout).
 struct FwdState {
   int k, done, converged, pairs, ncols, head, use_hat, t, n_local, n_solve;
+  int hi, since, escalations;
+  double gmin;
   int iters_total, iters_max, resets, not_converged, tau_half, tau_one, status;
   double gram[kMaxAA * kMaxAA];
   double gamma[kMaxAA];
@@ -28,6 +30,8 @@ __device__ __forceinline__ void ctrl_step_reset(St* c, int t) {
   c->t = t;
   c->n_local = 0;
   c->n_solve = 0;
+  c->since = 0;
+  c->gmin = 1e300;
 }
 
 // q_t (pinned at X), inertial target (eq. freefall) and the constant RHS
@@ -82,14 +86,14 @@ __device__ __forceinline__ void local_item(const Dev& d, int e, const double* x)
     ss[0] = ss[1] = ss[2] = T(1);
   } else {
     NHMean<T> m{(T)d.mu_bar, (T)d.lam_bar, (T)d.k_bar};
-    T* ws = reinterpret_cast<T*>(d.sstar) + 3 * (size_t)e;
+    float* ws = reinterpret_cast<float*>(d.sstar) + 3 * (size_t)e;
     T s0[3];
-    const bool warm = ws[0] > T(0) && ws[1] > T(0) && ws[2] > T(0);
+    const bool warm = ws[0] > 0.f && ws[1] > 0.f && ws[2] > 0.f;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) s0[i] = warm ? ws[i] : (sF[i] > T(0.1) ? sF[i] : T(0.1));
+    for (int i = 0; i < 3; ++i) s0[i] = warm ? (T)ws[i] : (sF[i] > T(0.1) ? sF[i] : T(0.1));
     nh_prox_from<T>(sF, m, s0, ss);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) ws[i] = ss[i];
+    for (int i = 0; i < 3; ++i) ws[i] = (float)ss[i];
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -127,7 +131,12 @@ __device__ __forceinline__ double gate_rhs(double eps, double b2, double abs_tol
   return eps * eps * b2 + 2.0 * eps * abs_tol * (double)sqrtf((float)b2) + abs_tol * abs_tol;
 }
 
-// dual gate (eq. convergence_dual), iteration cap, non-finite stop
+// dual gate (eq. convergence_dual), iteration cap, non-finite stop.
+// Precision escalation: with an FP32 local step the gate distance (the larger
+// of the two squared gate ratios) must halve at least every d.escalate
+// iterations; when it does not, the rounding of the FP32 projections has
+// become the floor of the iteration and the local step switches to FP64 for
+// the rest of the rollout.
 template <class St>
 __device__ __forceinline__ void assemble_finish(const Dev& d, St* c, int k, const double* s) {
   c->n_local += 1;
@@ -137,11 +146,22 @@ __device__ __forceinline__ void assemble_finish(const Dev& d, St* c, int k, cons
   if (d.fixed_iters <= 0 && k >= 2) {
     // ||a|| <= eps ||b|| + abs  <=>  a^2 <= eps^2 b^2 + 2 eps abs ||b|| + abs^2; the
     // cross term is negligible next to the others and is formed with an FP32 root
-    const bool step_ok = c->dq_norm2 <= gate_rhs(d.eps_step, c->qprev_norm2, d.eps_abs);
-    const bool res_ok = s[0] <= gate_rhs(d.eps_res, s[1], d.eps_abs);
+    const double rs = gate_rhs(d.eps_step, c->qprev_norm2, d.eps_abs);
+    const double rr = gate_rhs(d.eps_res, s[1], d.eps_abs);
+    const bool step_ok = c->dq_norm2 <= rs;
+    const bool res_ok = s[0] <= rr;
     if (step_ok && res_ok) {
       c->converged = 1;
       c->done = 1;
+    } else if (d.escalate > 0 && d.local_fp32 && !c->hi) {
+      const double gd = fmax(c->dq_norm2 / fmax(rs, 1e-300), s[0] / fmax(rr, 1e-300));
+      if (gd < 0.5 * c->gmin) {
+        c->gmin = gd;
+        c->since = 0;
+      } else if (++c->since >= d.escalate) {
+        c->hi = 1;
+        c->escalations += 1;
+      }
     }
   }
   if (!c->done && k >= d.k_max) {

@@ -276,3 +276,76 @@ def random_rotation(rng) -> np.ndarray:
     if np.linalg.det(q) < 0:
         q[:, 0] = -q[:, 0]
     return q
+
+
+def _grid_dims(n_cells: float, aspect) -> tuple[int, int, int]:
+    a = np.asarray(aspect, dtype=np.float64)
+    s = (n_cells / float(np.prod(a))) ** (1.0 / 3.0)
+    return tuple(int(max(2, round(s * x))) for x in a)
+
+
+def swirl_velocity(X: np.ndarray, pinned: np.ndarray, rng, omega: float, v_lat: float) -> np.ndarray:
+    """Seeded initial velocity of a mesh fixed at its bottom: a rotation about
+    a random axis through the centroid plus a lateral drift, both growing
+    linearly with height above the lowest vertex layer; pinned vertices rest."""
+    z = X[:, 2] - X[:, 2].min()
+    hfrac = z / max(float(z.max()), 1e-30)
+    axis = rng.standard_normal(3)
+    axis /= np.linalg.norm(axis)
+    w = omega * axis
+    drift = v_lat * np.append(rng.standard_normal(2), 0.0)
+    v = (np.cross(w, X - X.mean(axis=0)) + drift) * hfrac[:, None]
+    return v * (1 - pinned[:, None])
+
+
+def batch_instance(rng, n_tets: int, cell: float = 0.1, steps: int = 100, block: int = 4,
+                   name: str = "mesh", shape: str | None = None) -> Scene:
+    """One instance of the batched workload: a box or an ellipsoid (cells
+    whose centre lies inside it) of about ``n_tets`` tetrahedra, random aspect
+    ratios in [1, 2.5], per-instance E in [1e4, 1e6] Pa (log-uniform) times a
+    per-block stiffness map log-uniform in [1, 100] over block^3-cell blocks,
+    nu uniform in [0.3, 0.49], bottom vertex layer pinned, Neo-Hookean,
+    Anderson m=5, FP32 local step and the configured dual gate 1e-6 / 1e-8
+    (the tightened 2e-7 / 2e-9 of the bar lies below what an FP32 local step
+    resolves on meshes this stiff), k_max 1000 (instances with nu near 0.49
+    need several hundred iterations per step), dt 0.005 s, a seeded swirl +
+    drift initial velocity, no gravity, and an L2 target
+    X + N(0, (0.2 cell)^2)."""
+    shape = shape or ("box" if rng.random() < 0.5 else "ellipsoid")
+    aspect = 1.0 + 1.5 * rng.random(3)
+    if shape == "box":
+        nx, ny, nz = _grid_dims(n_tets / 5.0, aspect)
+        mask = None
+    else:
+        nx, ny, nz = _grid_dims(n_tets / 5.0 / (np.pi / 6.0), aspect)
+        ci = (np.arange(nx) + 0.5) / nx - 0.5
+        cj = (np.arange(ny) + 0.5) / ny - 0.5
+        ck = (np.arange(nz) + 0.5) / nz - 0.5
+        mask = (ci[:, None, None] ** 2 + cj[None, :, None] ** 2 + ck[None, None, :] ** 2) <= 0.25
+    X, tets, cells = hex_grid(nx, ny, nz, cell, mask)
+    E_inst = 10.0 ** rng.uniform(4.0, 6.0)
+    bx, by, bz = (nx + block - 1) // block, (ny + block - 1) // block, (nz + block - 1) // block
+    smap = 10.0 ** rng.uniform(0.0, 2.0, size=bx * by * bz)
+    bid = cells[:, 0] // block + bx * (cells[:, 1] // block + by * (cells[:, 2] // block))
+    E = E_inst * smap[bid]
+    nu = float(rng.uniform(0.3, 0.49))
+    pinned = (np.abs(X[:, 2] - X[:, 2].min()) < 1e-9 * cell).astype(np.uint8)
+    n_v = X.shape[0]
+    v0 = swirl_velocity(X, pinned, rng, omega=float(rng.uniform(0.5, 2.0)), v_lat=float(rng.uniform(0.0, 0.3)))
+    target = X + 0.2 * cell * rng.standard_normal(X.shape)
+    return Scene(
+        name=f"{name}-{shape}{nx}x{ny}x{nz}", X=X, tets=tets, pinned=pinned, E=E, nu=nu, density=1000.0,
+        alpha=0.01, beta0=1e-3, gravity=np.zeros(3), dt=0.005, model=NEOHOOKEAN,
+        steps=steps, f_ext=np.zeros((1, n_v, 3)), x0=X.copy(), v0=v0,
+        solver=SolverSettings(aa_m=5, fixed_iters=0, k_max=1000, eps_step=1e-8, eps_res=1e-6,
+                              eps_abs=1e-12, local_fp32=True),
+        loss="l2_target", target=target)
+
+
+def batch_meshes(n: int = 64, tets_lo: int = 1000, tets_hi: int = 40000, steps: int = 100,
+                 seed: int = 11) -> list[Scene]:
+    """The batched workload: ``n`` independent instances whose tet counts are
+    drawn log-uniformly in [tets_lo, tets_hi] (each built by batch_instance)."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(tets_lo), np.log(tets_hi), size=n))
+    return [batch_instance(rng, int(s), steps=steps, name=f"m{i}") for i, s in enumerate(sizes)]

@@ -1,0 +1,263 @@
+"""GPU tests of the batched persistent launch (many independent meshes of
+uneven size in one cooperative launch, one team of blocks per instance):
+per-instance parity with the oracle, bitwise agreement with a single-instance
+launch of the same team size, CUDA-graph capture and replay, the launch-shape
+autotuner and its cache, host pointers, the autograd Function and the
+instance limit."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import DEV, oracle_run, rel
+from paper_2605_14526_b300 import autograd, binding, inputs
+from paper_2605_14526_b300.build import build
+
+pytestmark = pytest.mark.gpu
+
+
+def small_batch(n=4, steps=3, seed=21, lo=300, hi=2000):
+    return inputs.batch_meshes(n=n, tets_lo=lo, tets_hi=hi, steps=steps, seed=seed)
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def batch_run(scenes, options=None, tuning=None, backward=True, bc=None):
+    build()
+    bc = bc or binding.BatchContext(scenes, options)
+    if tuning is not None:
+        binding.pd_set_tuning(bc.ctx, tuning)
+    T = scenes[0].steps
+    x0 = _t(bc.concat([s.x0 for s in scenes]).reshape(-1, 3))
+    v0 = _t(bc.concat([s.v0 for s in scenes]).reshape(-1, 3))
+    f = _t(bc.concat([s.f_ext[0] for s in scenes]).reshape(-1, 3))
+    qT, vT = torch.empty_like(x0), torch.empty_like(x0)
+    binding.pd_rollout(bc.ctx, T, x0, v0, f, 0, qT, vT)
+    out = {"bc": bc, "qT": qT.cpu().numpy(), "vT": vT.cpu().numpy(),
+           "inst": [binding.pd_get_instance_stats(bc.ctx, i) for i in range(bc.n)]}
+    if backward:
+        tgt = bc.concat([s.target for s in scenes]).reshape(-1, 3)
+        dq = _t(out["qT"] - tgt)
+        dq0, dv0 = torch.empty_like(x0), torch.empty_like(x0)
+        dE = torch.empty(bc.n_e, dtype=torch.float64, device=DEV)
+        dnu = torch.empty(bc.n, dtype=torch.float64, device=DEV)
+        binding.pd_backward(bc.ctx, dq, torch.zeros_like(x0), dq0, dv0, dE, dnu, None, 0)
+        out.update(dq0=dq0.cpu().numpy(), dv0=dv0.cpu().numpy(), dE=dE.cpu().numpy(), dnu=dnu.cpu().numpy())
+    return out
+
+
+def single_run(scene, grid_f, grid_b, options=None):
+    pd = binding.PDContext(scene, options)
+    tn = binding.pd_tuning()
+    tn.fwd_grid, tn.bwd_grid = int(grid_f), int(grid_b)
+    binding.pd_set_tuning(pd.ctx, tn)
+    T = scene.steps
+    x0, v0, f = _t(scene.x0), _t(scene.v0), _t(scene.f_ext[0])
+    qT, vT = torch.empty_like(x0), torch.empty_like(x0)
+    binding.pd_rollout(pd.ctx, T, x0, v0, f, 0, qT, vT)
+    dq = _t(qT.cpu().numpy() - scene.target)
+    dq0, dv0 = torch.empty_like(x0), torch.empty_like(x0)
+    dE = torch.empty(scene.n_e, dtype=torch.float64, device=DEV)
+    dnu = torch.empty(1, dtype=torch.float64, device=DEV)
+    binding.pd_backward(pd.ctx, dq, torch.zeros_like(x0), dq0, dv0, dE, dnu, None, 0)
+    return {"qT": qT.cpu().numpy(), "vT": vT.cpu().numpy(), "dq0": dq0.cpu().numpy(), "dv0": dv0.cpu().numpy(),
+            "dE": dE.cpu().numpy(), "dnu": dnu.cpu().numpy()}
+
+
+def test_batch_positions_match_oracle_per_instance():
+    scenes = small_batch()
+    g = batch_run(scenes, backward=False)
+    bc = g["bc"]
+    q = bc.split_v(g["qT"])
+    iters = [s.iters_total for s in g["inst"]]
+    assert all(s.not_converged == 0 for s in g["inst"])
+    for i, sc in enumerate(scenes):
+        o = oracle_run(sc, backward=False)
+        assert rel(q[i], o["qT"]) <= 1e-5, (i, rel(q[i], o["qT"]))
+    # instances converge at their own pace inside the one launch
+    assert len(set(iters)) > 1, iters
+
+
+def test_batch_gradients_fp64_match_oracle_per_instance():
+    scenes = [s.replace(solver=s.solver.__class__(aa_m=5, k_max=3000, eps_step=1e-11, eps_res=1e-10,
+                                                  eps_abs=1e-15, local_fp32=False))
+              for s in small_batch(n=3, steps=2, seed=5, lo=300, hi=900)]
+    opts = binding.options_for(scenes[0].solver)
+    opts.adj_tol = 1e-12
+    g = batch_run(scenes, options=opts)
+    bc = g["bc"]
+    q, dq0, dv0 = bc.split_v(g["qT"]), bc.split_v(g["dq0"]), bc.split_v(g["dv0"])
+    dE = bc.split_e(g["dE"])
+    for i, sc in enumerate(scenes):
+        o = oracle_run(sc)
+        assert rel(q[i], o["qT"]) <= 1e-8
+        assert rel(dE[i], o["dE"]) <= 1e-4, (i, rel(dE[i], o["dE"]))
+        assert rel(dv0[i], o["dv0"]) <= 1e-4
+        assert rel(dq0[i], o["dq0"]) <= 1e-4
+        assert abs(g["dnu"][i] - o["dnu"]) <= 1e-4 * abs(o["dnu"])
+
+
+@pytest.mark.parametrize("min_items", [256, 1024])
+def test_batch_team_equals_single_instance_launch_bitwise(min_items):
+    scenes = small_batch(n=3, steps=2, seed=8)
+    tn = binding.pd_tuning()
+    tn.fwd_min_items = tn.bwd_min_items = min_items
+    g = batch_run(scenes, tuning=tn)
+    bc = g["bc"]
+    tf, tb = bc.teams()
+    assert all(tf >= 1) and all(tb >= 1)
+    parts = {"qT": bc.split_v(g["qT"]), "vT": bc.split_v(g["vT"]), "dq0": bc.split_v(g["dq0"]),
+             "dv0": bc.split_v(g["dv0"]), "dE": bc.split_e(g["dE"])}
+    for i, sc in enumerate(scenes):
+        s = single_run(sc, tf[i], tb[i])
+        for k, v in parts.items():
+            assert np.array_equal(v[i].reshape(-1), s[k].reshape(-1)), (i, k, tf[i], tb[i])
+        assert g["dnu"][i] == s["dnu"][0]
+
+
+def test_batch_graph_capture_replays_bitwise():
+    scenes = small_batch(n=3, steps=2, seed=13)
+    ref = batch_run(scenes)
+    bc = ref["bc"]
+    T = scenes[0].steps
+    x0 = _t(bc.concat([s.x0 for s in scenes]).reshape(-1, 3))
+    v0 = _t(bc.concat([s.v0 for s in scenes]).reshape(-1, 3))
+    f = _t(bc.concat([s.f_ext[0] for s in scenes]).reshape(-1, 3))
+    qT, vT = torch.empty_like(x0), torch.empty_like(x0)
+    dq = _t(ref["qT"] - bc.concat([s.target for s in scenes]).reshape(-1, 3))
+    dv = torch.zeros_like(x0)
+    dq0, dv0 = torch.empty_like(x0), torch.empty_like(x0)
+    dE = torch.empty(bc.n_e, dtype=torch.float64, device=DEV)
+    dnu = torch.empty(bc.n, dtype=torch.float64, device=DEV)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        s = torch.cuda.current_stream()
+        binding.pd_rollout_enqueue(bc.ctx, T, x0, v0, f, 0, qT, vT, s)
+        binding.pd_backward_enqueue(bc.ctx, dq, dv, dq0, dv0, dE, dnu, None, 0, s)
+    for _ in range(2):
+        qT.zero_()
+        dE.zero_()
+        graph.replay()
+        binding.pd_collect(bc.ctx, torch.cuda.current_stream())
+        assert np.array_equal(qT.cpu().numpy(), ref["qT"])
+        assert np.array_equal(dE.cpu().numpy(), ref["dE"])
+        assert np.array_equal(dv0.cpu().numpy(), ref["dv0"])
+        assert np.array_equal(dnu.cpu().numpy(), ref["dnu"])
+    st = bc.stats()
+    assert st.iters_total == sum(s.iters_total for s in ref["inst"])
+
+
+def test_single_instance_graph_capture_replays_bitwise():
+    build()
+    sc = inputs.hetero_bar(nx=8, ny=4, nz=4, block=2, steps=3)
+    pd = binding.PDContext(sc)
+    x0, v0, f = _t(sc.x0), _t(sc.v0), _t(sc.f_ext[0])
+    q_ref, v_ref = torch.empty_like(x0), torch.empty_like(x0)
+    binding.pd_rollout(pd.ctx, sc.steps, x0, v0, f, 0, q_ref, v_ref, check=False)
+    qT, vT = torch.empty_like(x0), torch.empty_like(x0)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        binding.pd_rollout_enqueue(pd.ctx, sc.steps, x0, v0, f, 0, qT, vT, torch.cuda.current_stream())
+    graph.replay()
+    binding.pd_collect(pd.ctx, torch.cuda.current_stream(), check=False)
+    assert np.array_equal(qT.cpu().numpy(), q_ref.cpu().numpy())
+
+
+def test_batch_autotune_picks_a_shape_and_caches_it():
+    scenes = small_batch(n=4, steps=2, seed=17)
+    build()
+    bc = binding.BatchContext(scenes)
+    x0 = _t(bc.concat([s.x0 for s in scenes]).reshape(-1, 3))
+    v0 = _t(bc.concat([s.v0 for s in scenes]).reshape(-1, 3))
+    t1 = binding.pd_autotune(bc.ctx, 2, x0, v0, None, 0)
+    assert t1.candidates == 18
+    assert t1.fwd_ms > 0 and t1.bwd_ms > 0
+    assert t1.fwd_blocks_per_sm in (1, 2) and t1.fwd_gamma in (0.5, 0.75, 1.0)
+    bc2 = binding.BatchContext(scenes)
+    t2 = binding.pd_autotune(bc2.ctx, 2, x0, v0, None, 0)
+    assert t2.candidates == 0
+    assert (t2.fwd_blocks_per_sm, t2.fwd_gamma, t2.fwd_min_items) == (t1.fwd_blocks_per_sm, t1.fwd_gamma,
+                                                                       t1.fwd_min_items)
+    # the tuned launch still meets the oracle
+    g = batch_run(scenes, bc=bc2, backward=False)
+    q = bc2.split_v(g["qT"])
+    o = oracle_run(scenes[0], backward=False)
+    assert rel(q[0], o["qT"]) <= 1e-5
+
+
+def test_single_instance_autotune():
+    build()
+    sc = inputs.hetero_bar(nx=8, ny=4, nz=4, block=2, steps=2)
+    pd = binding.PDContext(sc)
+    t = binding.pd_autotune(pd.ctx, 2, _t(sc.x0), _t(sc.v0), None, 0)
+    assert t.candidates >= 2
+    assert t.fwd_grid > 0 and t.bwd_grid > 0
+
+
+def test_batch_host_pointers_match_device_pointers():
+    scenes = small_batch(n=2, steps=2, seed=3)
+    g = batch_run(scenes)
+    bc = g["bc"]
+    x0 = bc.concat([s.x0 for s in scenes])
+    v0 = bc.concat([s.v0 for s in scenes])
+    f = bc.concat([s.f_ext[0] for s in scenes])
+    qT, vT = np.zeros_like(x0), np.zeros_like(x0)
+    binding.pd_rollout(bc.ctx, scenes[0].steps, x0, v0, f, 0, qT, vT)
+    assert np.array_equal(qT.reshape(-1, 3), g["qT"])
+    dq = (qT.reshape(-1, 3) - bc.concat([s.target for s in scenes]).reshape(-1, 3)).reshape(-1)
+    dq0, dv0, dE, dnu = np.zeros_like(x0), np.zeros_like(x0), np.zeros(bc.n_e), np.zeros(bc.n)
+    binding.pd_backward(bc.ctx, np.ascontiguousarray(dq), np.zeros_like(x0), dq0, dv0, dE, dnu, None, 0)
+    assert np.array_equal(dE, g["dE"])
+    assert np.array_equal(dnu, g["dnu"])
+
+
+def test_batch_autograd_function_matches_direct_adjoint():
+    scenes = small_batch(n=2, steps=2, seed=4)
+    g = batch_run(scenes)
+    bc = g["bc"]
+    E = torch.tensor(bc.E, dtype=torch.float64, device=DEV, requires_grad=True)
+    nu = torch.tensor(bc.nu, dtype=torch.float64, device=DEV, requires_grad=True)
+    x0 = _t(bc.concat([s.x0 for s in scenes]).reshape(-1, 3))
+    v0 = _t(bc.concat([s.v0 for s in scenes]).reshape(-1, 3)).requires_grad_(True)
+    f = _t(bc.concat([s.f_ext[0] for s in scenes]).reshape(-1, 3))
+    tgt = _t(bc.concat([s.target for s in scenes]).reshape(-1, 3))
+    qT, vT = autograd.rollout(E, nu, x0, v0, f, bc, scenes[0].steps)
+    loss = 0.5 * ((qT - tgt) ** 2).sum()
+    loss.backward()
+    assert np.array_equal(E.grad.cpu().numpy(), g["dE"])
+    assert np.array_equal(v0.grad.cpu().numpy(), g["dv0"])
+    assert np.array_equal(nu.grad.cpu().numpy(), g["dnu"])
+
+
+def test_batch_more_instances_than_blocks_is_refused():
+    build()
+    X, tets, _ = inputs.hex_grid(1, 1, 1, 0.1)
+    sc = inputs.batch_instance(np.random.default_rng(0), 5, steps=1)
+    tiny = sc.replace(X=X, tets=tets, pinned=(X[:, 2] < 1e-9).astype(np.uint8), E=np.full(5, 1e5),
+                      x0=X.copy(), v0=np.zeros_like(X), f_ext=np.zeros((1, 8, 3)), target=X.copy())
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    bc = binding.BatchContext([tiny] * (sms + 1))
+    tn = binding.pd_tuning()
+    tn.fwd_blocks_per_sm = tn.bwd_blocks_per_sm = 1
+    binding.pd_set_tuning(bc.ctx, tn)
+    x0 = _t(np.tile(X, (sms + 1, 1)))
+    code = binding.pd_rollout(bc.ctx, 1, x0, torch.zeros_like(x0), None, 0, torch.empty_like(x0),
+                              torch.empty_like(x0), check=False)
+    assert binding.STATUS[code] == "PD_ERR_TOO_LARGE"
+    # with two blocks per SM the same batch fits
+    tn.fwd_blocks_per_sm = tn.bwd_blocks_per_sm = 2
+    binding.pd_set_tuning(bc.ctx, tn)
+    binding.pd_rollout(bc.ctx, 1, x0, torch.zeros_like(x0), None, 0, torch.empty_like(x0), torch.empty_like(x0))
+
+
+def test_full_batch_first_steps_sampled_instances_match_oracle():
+    scenes = [s.with_steps(2) for s in inputs.batch_meshes()]
+    g = batch_run(scenes, backward=False)
+    bc = g["bc"]
+    q = bc.split_v(g["qT"])
+    assert all(s.not_converged == 0 for s in g["inst"])
+    order = np.argsort([s.n_e for s in scenes])
+    for i in (order[0], order[len(order) // 2]):
+        o = oracle_run(scenes[i], backward=False)
+        assert rel(q[i], o["qT"]) <= 1e-5, (i, scenes[i].n_e, rel(q[i], o["qT"]))
