@@ -11,6 +11,13 @@ second over all ranks. Synthetic seeded inputs; L2 is flushed between timed
 rollouts (the bar's working set fits in L2).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py --workload batch    # 64 uneven meshes x 100 steps in one launch
+
+The batch workload (not the default line) times the batched persistent launch:
+64 seeded box/ellipsoid meshes of 1k-40k tets (about 0.58M tets in total) with
+per-instance materials, 100 steps forward + adjoint per benchmark step, after
+the launch-shape autotuner has picked the team sizes; value = instance PD
+steps (forward+backward) per second.
 """
 from __future__ import annotations
 
@@ -137,6 +144,147 @@ def run_reference(args, rank, world):
     print(json.dumps(line))
 
 
+BATCH_WORKLOAD = ("64 seeded box/ellipsoid Neo-Hookean meshes, 1k-40k tets each (log-uniform), per-instance "
+                  "E in [1e4,1e6] x 4^3-block maps in [1,100], nu in [0.3,0.49], 100 steps fwd+bwd, one launch")
+
+
+def run_batch(args, rank, world, local_rank, dev, dist):
+    """Batched workload: all instances in one persistent launch per rollout
+    and one per adjoint, launch shape from the autotuner."""
+    import torch
+    from paper_2605_14526_b300 import binding, inputs
+
+    scenes = inputs.batch_meshes(seed=11 + rank)
+    T = scenes[0].steps
+    bc = binding.BatchContext(scenes)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    x0 = t(bc.concat([s.x0 for s in scenes]).reshape(-1, 3))
+    v0 = t(bc.concat([s.v0 for s in scenes]).reshape(-1, 3))
+    target = t(bc.concat([s.target for s in scenes]).reshape(-1, 3))
+    qT, vT = torch.empty_like(x0), torch.empty_like(x0)
+    dq0, dv0 = torch.empty_like(x0), torch.empty_like(x0)
+    dE = torch.empty(bc.n_e, dtype=torch.float64, device=dev)
+    dnu = torch.empty(bc.n, dtype=torch.float64, device=dev)
+    zero = torch.zeros_like(x0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def fwd_bwd(timed=False):
+        if timed:
+            ev[0].record(stream)
+        binding.pd_rollout(bc.ctx, T, x0, v0, None, 0, qT, vT, stream)
+        if timed:
+            ev[1].record(stream)
+        binding.pd_backward(bc.ctx, qT - target, zero, dq0, dv0, dE, dnu, None, 0, stream)
+        if timed:
+            ev[2].record(stream)
+
+    # one full rollout + adjoint measures each instance's iterations per step,
+    # which weigh the team sizes; the autotuner then times candidate shapes
+    fwd_bwd()
+    t0 = time.perf_counter()
+    tune = binding.pd_autotune(bc.ctx, 10, x0, v0, None, 0, stream)
+    tune_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        fwd_bwd()
+    torch.cuda.synchronize()
+    launches0 = binding.pd_get_stats(bc.ctx).launches
+    total_ms = fwd_ms = bwd_ms = 0.0
+    inst_f = np.zeros(bc.n)
+    inst_b = np.zeros(bc.n)
+    esc = 0
+    with ClockSampler(local_rank) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            fwd_bwd(timed=True)
+            torch.cuda.synchronize()
+            fwd_ms += ev[0].elapsed_time(ev[1])
+            bwd_ms += ev[1].elapsed_time(ev[2])
+            total_ms += ev[0].elapsed_time(ev[2])
+            for i in range(bc.n):
+                si = binding.pd_get_instance_stats(bc.ctx, i)
+                inst_f[i] += si.iters_total
+                inst_b[i] += si.adj_iters_total
+            esc += binding.pd_get_stats(bc.ctx).escalations
+    launches = binding.pd_get_stats(bc.ctx).launches - launches0
+    tmax = total_ms
+    if dist:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tmax = float(tt[0])
+    value = world * bc.n * T * args.steps / (tmax / 1e3)
+    st = binding.pd_get_stats(bc.ctx)
+    m = bc.options.aa_m
+    fwd_bytes = bwd_bytes = 0.0
+    for i, sc in enumerate(scenes):
+        si = binding.pd_get_instance_stats(bc.ctx, i)
+        fb = 56 * sc.n_e + 48 * sc.n_v + 20 * si.factor_nnz + 96 * si.n_free + (2 * m + 3) * 24 * sc.n_v
+        bb = 200 * sc.n_e + 20 * si.factor_nnz + 240 * sc.n_v
+        fwd_bytes += fb * inst_f[i] / args.steps
+        bwd_bytes += bb * inst_b[i] / args.steps
+    fwd_launch_ms, bwd_launch_ms = fwd_ms / args.steps, bwd_ms / args.steps
+    if fwd_launch_ms >= bwd_launch_ms:
+        kname, kbytes, kms = "k_fwd_batch (batched persistent forward)", fwd_bytes, fwd_launch_ms
+    else:
+        kname, kbytes, kms = "k_bwd_batch (batched persistent adjoint)", bwd_bytes, bwd_launch_ms
+    achieved = kbytes / (kms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    tf, tb = bc.teams()
+
+    # end to end with host buffers
+    hx0 = bc.concat([s.x0 for s in scenes])
+    hv0 = bc.concat([s.v0 for s in scenes])
+    htg = bc.concat([s.target for s in scenes])
+    hq, hv = np.zeros_like(hx0), np.zeros_like(hx0)
+    hdq0, hdv0, hdE, hdnu = np.zeros_like(hx0), np.zeros_like(hx0), np.zeros(bc.n_e), np.zeros(bc.n)
+    hz = np.zeros_like(hx0)
+    e2e_s = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        binding.pd_rollout(bc.ctx, T, hx0, hv0, None, 0, hq, hv, None)
+        g = np.ascontiguousarray(hq - htg)
+        binding.pd_backward(bc.ctx, g, hz, hdq0, hdv0, hdE, hdnu, None, 0, None)
+        e2e_s += time.perf_counter() - t0
+    e2e = world * bc.n * T * args.steps / e2e_s
+    nv3b = 3 * 8 * bc.n_v
+    line = {"metric": METRIC, "value": value, "unit": "instance PD steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (FP32 local step, FP64 RHS/factor/solve)", "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "instances": bc.n, "tets": bc.n_e, "vertices": bc.n_v,
+                       "nnz_S": int(st.factor_nnz), "pd_steps_per_instance_per_bench_step": T,
+                       "l2": "flushed (256 MB write) between rollouts; inverse factors total "
+                             f"{20 * st.factor_nnz / 1e9:.2f} GB per iteration, above L2",
+                       "gate": f"b-change {bc.options.eps_res:g}, q-step {bc.options.eps_step:g} (relative)",
+                       "autotune": {**tune.as_dict(), "seconds": tune_s},
+                       "teams_fwd": [int(x) for x in tf], "teams_bwd": [int(x) for x in tb],
+                       "fwd_iters_per_step_mean": float(inst_f.sum() / (args.steps * T * bc.n)),
+                       "fwd_iters_per_step_max_instance": float(inst_f.max() / (args.steps * T)),
+                       "adj_iters_per_step_mean": float(inst_b.sum() / (args.steps * T * bc.n)),
+                       "fp64_escalations_per_rollout": esc / args.steps,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "e2e": {"value": e2e, "unit": "instance PD steps/s", "h2d_bytes_per_step": 2 * nv3b + 2 * nv3b,
+                    "d2h_bytes_per_step": 2 * nv3b + 2 * nv3b + 8 * bc.n_e + 8 * bc.n},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": kname, "peak_kind": peak_kind, "avg_launch_ms": kms,
+                         "bytes_per_launch": kbytes, "fwd_launch_ms": fwd_launch_ms, "bwd_launch_ms": bwd_launch_ms},
+            "clocks": clk.summary()}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        order = np.argsort([s.n_e for s in scenes])
+        mid = scenes[order[len(order) // 2]]
+        dt, k = oracle_sample(mid, 1)
+        line["cpu_baseline"] = {"value": k / dt, "unit": "instance PD steps/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first PD step of the median instance ({mid.n_e} tets), forward + adjoint, FP64, 1 thread"}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -144,6 +292,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="bar", choices=["bar", "batch"])
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -164,6 +313,11 @@ def main():
         dist.init_process_group("nccl")
     build()
     dev = torch.device("cuda", local_rank)
+    if args.workload == "batch":
+        run_batch(args, rank, world, local_rank, dev, dist)
+        if dist:
+            dist.destroy_process_group()
+        return
     scene = inputs.hetero_bar(seed=2 + rank)
     T = scene.steps
     pd = binding.PDContext(scene)

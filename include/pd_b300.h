@@ -86,7 +86,7 @@ typedef struct {
                              (the larger squared ratio of the two gates) has not halved for
                              this many iterations, the rounding of the FP32 projections
                              is the floor of the iteration and the local step switches to
-                             FP64 for the rest of the rollout (0 = never; default 20) */
+                             FP64 for the rest of the rollout (0 = never; default 100) */
   int32_t reserved_opt;
 } pd_options;
 
@@ -110,13 +110,16 @@ typedef struct {
   int64_t launches;         /* kernel launches issued by this context so far */
   int32_t escalations;      /* rollouts whose local step switched from FP32 to FP64 (a batch: instances) */
   int32_t reserved_stats;
+  double fwd_device_seconds;  /* persistent launches: the last forward's wall time measured on the device
+                                 (a batch: the instance's team; pd_get_stats gives the largest) */
+  double bwd_device_seconds;  /* ... of the last adjoint */
 } pd_stats;
 
 typedef struct pd_ctx pd_ctx;
 
 /* Default options (m = 5, k_max = 200, gate 1e-8 / 1e-6 / 1e-12, FP32 local,
  * adaptive trust region with eps_tr = 0.1, backward 1e-9 / 1000 iterations,
- * persistent launches on, precision escalation after 20 iterations without
+ * persistent launches on, precision escalation after 100 iterations without
  * progress). */
 void pd_default_options(pd_options* out);
 
@@ -315,7 +318,7 @@ typedef struct {
   int32_t bwd_blocks_per_sm;
   int32_t fwd_grid;           /* single instance: blocks of the launch (0 = SMs x blocks_per_sm) */
   int32_t bwd_grid;
-  double fwd_gamma;           /* batch: team sizes grow with (iterations x bytes per iteration)^gamma */
+  double fwd_gamma;           /* batch: an instance's time is taken to scale as (team size)^-gamma */
   double bwd_gamma;
   int32_t fwd_min_items;      /* batch: a team gets at most ceil(n_e / min_items) blocks */
   int32_t bwd_min_items;
@@ -328,13 +331,19 @@ typedef struct {
 /* Choose the launch shape by timing probe rollouts of T_probe steps from
  * (q0, v0, f_ext) (as pd_rollout; device pointers) and their adjoints over
  * a fixed candidate set: blocks per SM; for a single instance, the grid
- * size; for a batch, the team-size exponent gamma (team sizes follow each
- * instance's measured iterations x bytes per iteration) and the cap on
- * blocks per element count. The choice is kept in the context and cached in
- * the process, keyed by device and problem signature (instance sizes,
- * nnz(S), options), so a second context of the same problem reuses it
- * without probing. Overwrites the checkpoints (run pd_rollout again before
- * pd_backward). Blocking. out may be NULL. */
+ * size; for a batch (two blocks per SM), the exponent gamma (0.5, 0.75, 1)
+ * and the cap on blocks per element count (32, 128 or 512 elements per block
+ * at least). Batch team sizes minimise the largest predicted instance time,
+ * where an instance's time with b blocks is predicted from its own measured
+ * time in the last full pd_rollout / pd_backward (each team times itself on
+ * the device) scaled by (measured team size / b)^gamma; run one rollout and
+ * adjoint over the real horizon first (a short probe does not see the slow
+ * steps). Without a measurement the prediction is iterations x bytes per
+ * iteration / b^gamma. The choice is kept in
+ * the context and cached in the process, keyed by device and problem
+ * signature (instance sizes, nnz(S), options), so a second context of the
+ * same problem reuses it without probing. Overwrites the checkpoints (run
+ * pd_rollout again before pd_backward). Blocking. out may be NULL. */
 int pd_autotune(pd_ctx* ctx, int32_t T_probe, const double* q0, const double* v0, const double* f_ext,
                 int64_t f_ext_stride, pd_tuning* out, void* stream);
 int pd_get_tuning(const pd_ctx* ctx, pd_tuning* out);

@@ -48,7 +48,8 @@ class pd_stats(ctypes.Structure):
                 ("adj_iters_total", c_int32), ("adj_iters_max", c_int32), ("adj_not_converged", c_int32),
                 ("status_flags", c_int32), ("n_free", c_int32), ("factor_nnz", c_int64),
                 ("factor_seconds", c_double), ("last_rho", c_double), ("launches", c_int64),
-                ("escalations", c_int32), ("reserved_stats", c_int32)]
+                ("escalations", c_int32), ("reserved_stats", c_int32),
+                ("fwd_device_seconds", c_double), ("bwd_device_seconds", c_double)]
 
 
 class pd_profile_out(ctypes.Structure):

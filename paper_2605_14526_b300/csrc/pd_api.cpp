@@ -137,7 +137,7 @@ void pd_default_options(pd_options* o) {
   o->eps_abs = 1e-12;
   o->eps_tr = 0.1;
   o->adj_tol = 1e-9;
-  o->escalate_window = 20;
+  o->escalate_window = 100;
 }
 
 const char* pd_last_error(const pd_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -543,11 +543,13 @@ int stats_from_ctrl(pd_ctx* c, const Ctrl& hc, int which) {
     st.tau_one = hc.tau_one;
     st.last_rho = hc.last_rho;
     st.escalations = hc.escalations;
+    st.fwd_device_seconds = hc.elapsed_ns[0] * 1e-9;
   }
   if (which & 2) {
     st.adj_iters_total = hc.adj_iters_total;
     st.adj_iters_max = hc.adj_iters_max;
     st.adj_not_converged = hc.adj_not_converged;
+    st.bwd_device_seconds = hc.elapsed_ns[1] * 1e-9;
   }
   st.status_flags = hc.status;
   if (hc.status & 4) return fail(c, PD_ERR_TIMEOUT, "a grid barrier of a persistent launch timed out");

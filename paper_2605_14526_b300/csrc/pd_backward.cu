@@ -555,6 +555,7 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
   const Range rv = block_range(tm, d.n_v);
   const Range rb = block_range(tm, d.n_v > d.n_e ? d.n_v : d.n_e);
   const Range rt = block_range(tm, d.n_v + d.n_e);
+  const unsigned long long tstart = gtimer();
   if (tid == 0) {
     S.adj_k = S.adj_done = S.status = S.adj_iters_total = S.adj_iters_max = S.adj_not_converged = 0;
     S.rz = S.rz0 = S.alpha = S.beta = S.acc_mu = S.acc_lam = S.acc_k = S.dnu_acc = 0.0;
@@ -638,6 +639,7 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
     c->acc_mu = S.acc_mu;
     c->acc_lam = S.acc_lam;
     c->acc_k = S.acc_k;
+    c->elapsed_ns[1] = gtimer() - tstart;
     atomicOr(&c->status, S.status);
   }
 }

@@ -43,7 +43,11 @@ struct pd_batch {
   std::vector<int> tsize[2];       // team sizes of the current maps
   bool devs_dirty = true, team_dirty[2] = {true, true};
   std::vector<double> work[2];     // bytes per iteration of each instance (forward, backward)
-  std::vector<double> iters[2];    // iterations of each instance in the last rollout / adjoint (>= 1)
+  std::vector<double> iters[2];    // iterations per step of each instance in the last rollout / adjoint
+  std::vector<double> tmeas[2];    // seconds per step of each instance's team in the last launch ...
+  std::vector<int> bmeas[2];       // ... with this many blocks
+  bool have_iters[2] = {false, false};
+  bool freeze_iters = false;       // the autotuner's probes leave the weights alone
   std::vector<Ctrl> hctrl;
   std::vector<pd_stats> inst;
 };
@@ -59,25 +63,36 @@ bool capturing(cudaStream_t s) {
   return cs != cudaStreamCaptureStatusNone;
 }
 
-// Team sizes: every instance gets one block, then blocks go one at a time to
-// the instance with the largest load per block, load = (iterations x bytes
-// per iteration)^gamma, until the co-resident grid is used up or every team
-// holds ceil(n_e / min_items) blocks.
+// Team sizes minimise the largest predicted instance time: every instance
+// gets one block, then blocks go one at a time to the instance whose
+// predicted time is largest, until the co-resident grid is used up or every
+// team holds ceil(n_e / min_items) blocks. Predicted time with b blocks:
+// the instance's measured time in the last launch scaled by
+// (measured team size / b)^gamma, or, before any measurement, iterations x
+// bytes per iteration / b^gamma.
 std::vector<int> team_sizes(const pd_batch& B, int dir, int G, double gamma, int min_items) {
   const int n = B.n;
-  std::vector<double> load(n);
+  std::vector<double> base(n), ref(n);
   std::vector<int> cap(n), b(n, 1);
+  const bool timed = B.tmeas[dir].size() == (size_t)n && B.bmeas[dir].size() == (size_t)n;
   for (int i = 0; i < n; ++i) {
-    load[i] = std::pow(std::max(B.iters[dir][i], 1.0) * B.work[dir][i], gamma);
+    if (timed && B.tmeas[dir][i] > 0) {
+      base[i] = B.tmeas[dir][i];
+      ref[i] = std::max(B.bmeas[dir][i], 1);
+    } else {
+      base[i] = std::max(B.iters[dir][i], 1.0) * B.work[dir][i];
+      ref[i] = 1.0;
+    }
     cap[i] = std::max(1, (B.kids[i]->n_e + min_items - 1) / min_items);
   }
+  auto pred = [&](int i) { return base[i] * std::pow(ref[i] / b[i], gamma); };
   int used = n;
   while (used < G) {
     int best = -1;
-    double bl = -1.0;
+    double bt = -1.0;
     for (int i = 0; i < n; ++i)
-      if (b[i] < cap[i] && load[i] / b[i] > bl) {
-        bl = load[i] / b[i];
+      if (b[i] < cap[i] && pred(i) > bt) {
+        bt = pred(i);
         best = i;
       }
     if (best < 0) break;
@@ -142,8 +157,12 @@ int collect_batch(pd_ctx* c, cudaStream_t s, int which) {
     st.steps = c->last_T;
     st.iters_total = st.iters_max = st.aa_resets = st.not_converged = st.tau_half = st.tau_one = 0;
     st.escalations = 0;
+    st.fwd_device_seconds = 0.0;
   }
-  if (which & 2) st.adj_iters_total = st.adj_iters_max = st.adj_not_converged = 0;
+  if (which & 2) {
+    st.adj_iters_total = st.adj_iters_max = st.adj_not_converged = 0;
+    st.bwd_device_seconds = 0.0;
+  }
   for (int i = 0; i < B.n; ++i) {
     const Ctrl& h = B.hctrl[i];
     pd_stats& si = B.inst[i];
@@ -157,6 +176,8 @@ int collect_batch(pd_ctx* c, cudaStream_t s, int which) {
       si.tau_one = h.tau_one;
       si.last_rho = h.last_rho;
       si.escalations = h.escalations;
+      si.fwd_device_seconds = h.elapsed_ns[0] * 1e-9;
+      st.fwd_device_seconds = std::max(st.fwd_device_seconds, si.fwd_device_seconds);
       st.escalations += h.escalations;
       st.iters_total += h.iters_total;
       st.iters_max = std::max(st.iters_max, h.iters_max);
@@ -165,20 +186,35 @@ int collect_batch(pd_ctx* c, cudaStream_t s, int which) {
       st.tau_half += h.tau_half;
       st.tau_one += h.tau_one;
       nc += h.not_converged ? 1 : 0;
-      B.iters[0][i] = std::max(1, h.iters_total);
+      if (!B.freeze_iters) B.iters[0][i] = std::max(1.0, (double)h.iters_total / std::max(c->last_T, 1));
     }
     if (which & 2) {
       si.adj_iters_total = h.adj_iters_total;
       si.adj_iters_max = h.adj_iters_max;
       si.adj_not_converged = h.adj_not_converged;
+      si.bwd_device_seconds = h.elapsed_ns[1] * 1e-9;
+      st.bwd_device_seconds = std::max(st.bwd_device_seconds, si.bwd_device_seconds);
       st.adj_iters_total += h.adj_iters_total;
       st.adj_iters_max = std::max(st.adj_iters_max, h.adj_iters_max);
       st.adj_not_converged += h.adj_not_converged;
       anc += h.adj_not_converged ? 1 : 0;
-      B.iters[1][i] = std::max(1, h.adj_iters_total);
+      if (!B.freeze_iters) B.iters[1][i] = std::max(1.0, (double)h.adj_iters_total / std::max(c->last_T, 1));
     }
     si.status_flags = h.status;
     status |= h.status;
+    if (!B.freeze_iters) {
+      for (int dir = 0; dir < 2; ++dir) {
+        if (!(which & (1 << dir))) continue;
+        B.tmeas[dir].resize(B.n, 0.0);
+        B.bmeas[dir].resize(B.n, 1);
+        B.tmeas[dir][i] = (double)h.elapsed_ns[dir] * 1e-9 / std::max(c->last_T, 1);
+        B.bmeas[dir][i] = B.tsize[dir].size() == (size_t)B.n ? B.tsize[dir][i] : 1;
+      }
+    }
+  }
+  if (!B.freeze_iters) {
+    if (which & 1) B.have_iters[0] = true;
+    if (which & 2) B.have_iters[1] = true;
   }
   st.status_flags = status;
   if (status & 4) return fail(c, PD_ERR_TIMEOUT, "a team barrier of the batched persistent launch timed out");
@@ -658,9 +694,9 @@ int pd_autotune(pd_ctx* c, int32_t T_probe, const double* q0, const double* v0, 
   };
   std::vector<Cand> cands;
   if (c->batch) {
-    for (int bps : {1, 2})
-      for (double gm : {0.5, 0.75, 1.0})
-        for (int mi : {128, 512, 2048}) cands.push_back({bps, 0, gm, mi});
+    // two blocks per SM (fewer co-resident blocks never helps a batch)
+    for (double gm : {0.5, 0.75, 1.0})
+      for (int mi : {32, 128, 512}) cands.push_back({2, 0, gm, mi});
   } else {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -679,10 +715,15 @@ int pd_autotune(pd_ctx* c, int32_t T_probe, const double* q0, const double* v0, 
     c->tune = t;
     mark_shape_changed(c);
   };
-  // a first forward + adjoint at the starting shape measures the per-instance
-  // iteration counts that weigh the team sizes
+  // the team sizes are weighed by per-instance iterations per step: those of
+  // the last full rollout / adjoint if there was one (representative of the
+  // whole horizon), else of a first probe at the starting shape; the
+  // candidates' probes then leave the weights unchanged
   double warm = 0;
+  const bool measured = c->batch && c->batch->have_iters[0] && c->batch->have_iters[1];
+  if (measured) c->batch->freeze_iters = true;
   if ((rc = probe(0, &warm)) == PD_OK) rc = probe(1, &warm);
+  if (c->batch) c->batch->freeze_iters = true;
   for (int dir = 0; dir < 2 && rc == PD_OK; ++dir) {
     if (dir == 1) {  // the adjoint probes need the checkpoints of one forward
       apply(best[0]);
@@ -690,8 +731,11 @@ int pd_autotune(pd_ctx* c, int32_t T_probe, const double* q0, const double* v0, 
     }
     for (const Cand& k : cands) {
       apply(k);
-      double t1 = 0, t2 = 0;
-      if ((rc = probe(dir, &t1)) || (rc = probe(dir, &t2))) break;
+      // batches are probed once per shape (long launches, little noise);
+      // a single instance twice, keeping the faster
+      double t1 = 0, t2 = 1e300;
+      if ((rc = probe(dir, &t1))) break;
+      if (!c->batch && (rc = probe(dir, &t2))) break;
       const double t = std::min(t1, t2);
       if (t < best_ms[dir]) {
         best_ms[dir] = t;
@@ -699,6 +743,7 @@ int pd_autotune(pd_ctx* c, int32_t T_probe, const double* q0, const double* v0, 
       }
     }
   }
+  if (c->batch) c->batch->freeze_iters = false;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(qT);

@@ -49,6 +49,7 @@ struct Ctrl {
   unsigned int bar_count, bar_gen; // grid barrier of the persistent kernels
   unsigned long long phase_ns[8];  // persistent kernels: time per phase (globaltimer, block 0)
   unsigned long long work_ns[8];   // ... of which block 0's own work before the phase's barrier
+  unsigned long long elapsed_ns[2]; // persistent launches: wall time of the forward / adjoint (team block 0)
 };
 
 // phases timed inside the persistent rollout

@@ -54,7 +54,7 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
   const Range re = block_range(tm, d.n_e);
   const Range rv = block_range(tm, d.n_v);
   const Range rt = block_range(tm, d.n_e + d.n_v);
-  unsigned long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0}, wk[8] = {0, 0, 0, 0, 0, 0, 0, 0}, t0 = 0;
+  unsigned long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0}, wk[8] = {0, 0, 0, 0, 0, 0, 0, 0}, t0 = 0, tstart = 0;
   auto mark = [&](int p) {
     if (writer && tid == 0) {
       const unsigned long long t1 = gtimer();
@@ -76,6 +76,7 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
     S.last_rho = 0.0;
     for (int i = 0; i < kMaxAA * kMaxAA; ++i) S.gram[i] = 0.0;
     t0 = gtimer();
+    tstart = t0;
   }
   bool ok = true;
   for (int t = 0; t < a.T && ok; ++t) {
@@ -170,6 +171,7 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
       c->phase_ns[i] += ph[i];
       c->work_ns[i] += wk[i];
     }
+    c->elapsed_ns[0] = gtimer() - tstart;
   }
 }
 
