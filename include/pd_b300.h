@@ -87,7 +87,10 @@ typedef struct {
                              this many iterations, the rounding of the FP32 projections
                              is the floor of the iteration and the local step switches to
                              FP64 for the rest of the rollout (0 = never; default 100) */
-  int32_t reserved_opt;
+  int32_t warm_start;     /* start of each step's iteration: 0 q_t (Alg. 1); 1 the learned
+                             warm start (pd_mlp_load); 2 constant-velocity extrapolation
+                             2 x_t - x_{t-1}. Persistent launches only; a warm-started step
+                             that hits k_max is run again from q_t (pd_stats.warm_fallbacks) */
 } pd_options;
 
 /* Statistics of the last pd_rollout / pd_backward (host copy). */
@@ -109,7 +112,7 @@ typedef struct {
   double last_rho;          /* trust-region ratio of the last step */
   int64_t launches;         /* kernel launches issued by this context so far */
   int32_t escalations;      /* rollouts whose local step switched from FP32 to FP64 (a batch: instances) */
-  int32_t reserved_stats;
+  int32_t warm_fallbacks;   /* warm-started steps that hit k_max and were run again from q_t */
   double fwd_device_seconds;  /* persistent launches: the last forward's wall time measured on the device
                                  (a batch: the instance's team; pd_get_stats gives the largest) */
   double bwd_device_seconds;  /* ... of the last adjoint */
@@ -349,6 +352,70 @@ int pd_autotune(pd_ctx* ctx, int32_t T_probe, const double* q0, const double* v0
 int pd_get_tuning(const pd_ctx* ctx, pd_tuning* out);
 /* Set the launch shape directly (e.g. one saved from pd_get_tuning). */
 int pd_set_tuning(pd_ctx* ctx, const pd_tuning* t);
+
+/* ---------------------------------------------------------------------
+ * Learned warm start (not part of the paper's method).
+ *
+ * A per-vertex network predicts the correction r to the constant-velocity
+ * guess, and each step's local-global iteration starts from
+ *   q0 = 2 x_t - x_{t-1} + r,   x_{t-1} = x_t - h v_t,
+ * instead of q_t (Alg. 1), on free vertices (options.warm_start = 1). The
+ * network: features f = [x_t - x_{t-1}, x_t - X, log10(E_v / 1e5)] (E_v the
+ * volume-weighted mean Young's modulus of the elements around v),
+ * normalised (f - mean) / scale; 4 dense layers 7 -> 128 -> 128 -> 128 -> 3
+ * with ReLU between them; output times oscale. Parameters (FP32, 34,435) in
+ * one flat vector: W1 [128][7], b1 [128], W2 [128][128], b2 [128],
+ * W3 [128][128], b3 [128], W4 [3][128], b4 [3]; normalisation (17 floats):
+ * feature mean [7], feature scale [7], output scale [3]. Inference and
+ * training forward passes use the weights rounded to BF16 (nearest even),
+ * biases in FP32, FP32 arithmetic. The converged step does not depend on
+ * the start: the network only changes iteration counts, and a warm-started
+ * step that hits k_max is run again from q_t.
+ * --------------------------------------------------------------------- */
+#define PD_MLP_PARAMS 34435
+#define PD_MLP_NORM 17
+
+typedef struct pd_mlp pd_mlp;
+
+/* Trainer on the current device: FP32 master parameters theta [PD_MLP_PARAMS]
+ * and normalisation norm [PD_MLP_NORM] (host arrays, copied), Adam moments at
+ * zero. On failure *out may hold a trainer whose pd_mlp_last_error explains. */
+int pd_mlp_create(const float* theta, const float* norm, pd_mlp** out);
+/* Host copies of the master parameters and the normalisation (either may be NULL). */
+int pd_mlp_params(const pd_mlp* net, float* theta, float* norm);
+/* Set the normalisation from n samples (device arrays feat [n][7], targ
+ * [n][3], raw units): feature mean and standard deviation (1 where it is
+ * below 1e-12), output scale = root mean square of each target component. */
+int pd_mlp_fit_normalization(pd_mlp* net, const float* feat, const float* targ, int64_t n, void* stream);
+/* r [n][3] (raw units) for raw features feat [n][7] (device arrays). */
+int pd_mlp_forward(pd_mlp* net, const float* feat, float* r, int64_t n, void* stream);
+/* Loss = mean over the n samples and 3 outputs of (net(f) - targ / oscale)^2
+ * (host *loss, may be NULL) and its gradient with respect to the parameters
+ * (device grad [PD_MLP_PARAMS], may be NULL), by backpropagation. */
+int pd_mlp_grad(pd_mlp* net, const float* feat, const float* targ, int64_t n, float* grad, double* loss, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8; Kingma & Ba 2015,
+ * Algorithm 1) of learning rate lr on the loss of the n samples. */
+int pd_mlp_train_step(pd_mlp* net, const float* feat, const float* targ, int64_t n, double lr, double* loss,
+                      void* stream);
+const char* pd_mlp_last_error(const pd_mlp* net);
+void pd_mlp_destroy(pd_mlp* net);
+
+/* Training samples of one frame of a trajectory of the context's mesh:
+ * raw features feat [n_v][7] of (x_{t-1}, x_t) and, if x_tp1 is given, raw
+ * targets targ [n_v][3] = x_{t+1} - (2 x_t - x_{t-1}) (device arrays, every
+ * vertex in order; pinned vertices give zero rows). Single instance. */
+int pd_mlp_sample(pd_ctx* ctx, const double* x_tm1, const double* x_t, const double* x_tp1, float* feat,
+                  float* targ, void* stream);
+
+/* Attach a network to a context (a batch: to every instance): weights =
+ * FP32 parameters [PD_MLP_PARAMS] followed by the normalisation
+ * [PD_MLP_NORM], bytes = 4 x (PD_MLP_PARAMS + PD_MLP_NORM), host memory. */
+int pd_mlp_load(pd_ctx* ctx, const void* weights, size_t bytes);
+
+/* The warm start as the rollout computes it: q0 [n_v][3] from x_t, x_{t-1}
+ * (device arrays) with options.warm_start (1: the loaded network; 2 or 0:
+ * constant velocity); pinned vertices at X. Single instance. */
+int pd_warm_start(pd_ctx* ctx, const double* x_t, const double* x_tm1, double* q0, void* stream);
 
 /* Library version string. */
 const char* pd_version(void);

@@ -39,7 +39,7 @@ class pd_options(ctypes.Structure):
                 ("tr_mode", c_int32), ("adj_max_iters", c_int32), ("persistent", c_int32),
                 ("eps_step", c_double), ("eps_res", c_double),
                 ("eps_abs", c_double), ("eps_tr", c_double), ("adj_tol", c_double),
-                ("escalate_window", c_int32), ("reserved_opt", c_int32)]
+                ("escalate_window", c_int32), ("warm_start", c_int32)]
 
 
 class pd_stats(ctypes.Structure):
@@ -48,7 +48,7 @@ class pd_stats(ctypes.Structure):
                 ("adj_iters_total", c_int32), ("adj_iters_max", c_int32), ("adj_not_converged", c_int32),
                 ("status_flags", c_int32), ("n_free", c_int32), ("factor_nnz", c_int64),
                 ("factor_seconds", c_double), ("last_rho", c_double), ("launches", c_int64),
-                ("escalations", c_int32), ("reserved_stats", c_int32),
+                ("escalations", c_int32), ("warm_fallbacks", c_int32),
                 ("fwd_device_seconds", c_double), ("bwd_device_seconds", c_double)]
 
 
@@ -109,6 +109,17 @@ def lib():
             "pd_autotune": (c_int, [P, c_int32, P, P, P, c_int64, P, P]),
             "pd_get_tuning": (c_int, [P, P]),
             "pd_set_tuning": (c_int, [P, P]),
+            "pd_mlp_create": (c_int, [P, P, P]),
+            "pd_mlp_params": (c_int, [P, P, P]),
+            "pd_mlp_fit_normalization": (c_int, [P, P, P, c_int64, P]),
+            "pd_mlp_forward": (c_int, [P, P, P, c_int64, P]),
+            "pd_mlp_grad": (c_int, [P, P, P, c_int64, P, P, P]),
+            "pd_mlp_train_step": (c_int, [P, P, P, c_int64, c_double, P, P]),
+            "pd_mlp_last_error": (ctypes.c_char_p, [P]),
+            "pd_mlp_destroy": (None, [P]),
+            "pd_mlp_sample": (c_int, [P, P, P, P, P, P, P]),
+            "pd_mlp_load": (c_int, [P, P, ctypes.c_size_t]),
+            "pd_warm_start": (c_int, [P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -131,7 +142,8 @@ def _ptr(a, dtype=np.float64):
     try:
         import torch
         if isinstance(a, torch.Tensor):
-            want = {np.float64: torch.float64, np.int32: torch.int32, np.uint8: torch.uint8}[dtype]
+            want = {np.float64: torch.float64, np.float32: torch.float32, np.int32: torch.int32,
+                    np.uint8: torch.uint8}[dtype]
             if a.dtype != want or not a.is_contiguous():
                 raise TypeError(f"tensor must be contiguous {want}")
             return a.data_ptr()
@@ -355,6 +367,79 @@ def pd_set_tuning(ctx, t: pd_tuning):
     _check(ctx, lib().pd_set_tuning(ctx, ctypes.byref(t)))
 
 
+MLP_PARAMS, MLP_NORM = 34435, 17
+
+
+def _mcheck(net, code):
+    if code != PD_OK:
+        msg = lib().pd_mlp_last_error(net).decode() if net else ""
+        raise PDError(code, msg)
+
+
+def pd_mlp_create(theta, norm):
+    theta = np.ascontiguousarray(theta, dtype=np.float32)
+    norm = np.ascontiguousarray(norm, dtype=np.float32)
+    if theta.size != MLP_PARAMS or norm.size != MLP_NORM:
+        raise ValueError("theta must hold 34435 and norm 17 values")
+    out = c_void_p()
+    code = lib().pd_mlp_create(_ptr(theta, np.float32), _ptr(norm, np.float32), ctypes.byref(out))
+    if code != PD_OK:
+        msg = lib().pd_mlp_last_error(out).decode() if out.value else ""
+        if out.value:
+            lib().pd_mlp_destroy(out)
+        raise PDError(code, msg)
+    return out
+
+
+def pd_mlp_params(net):
+    theta = np.zeros(MLP_PARAMS, dtype=np.float32)
+    norm = np.zeros(MLP_NORM, dtype=np.float32)
+    _mcheck(net, lib().pd_mlp_params(net, _ptr(theta, np.float32), _ptr(norm, np.float32)))
+    return theta, norm
+
+
+def pd_mlp_fit_normalization(net, feat, targ, n, stream=None):
+    _mcheck(net, lib().pd_mlp_fit_normalization(net, _ptr(feat, np.float32), _ptr(targ, np.float32), int(n),
+                                                _stream(stream)))
+
+
+def pd_mlp_forward(net, feat, r, n, stream=None):
+    _mcheck(net, lib().pd_mlp_forward(net, _ptr(feat, np.float32), _ptr(r, np.float32), int(n), _stream(stream)))
+
+
+def pd_mlp_grad(net, feat, targ, n, grad=None, stream=None) -> float:
+    loss = c_double()
+    _mcheck(net, lib().pd_mlp_grad(net, _ptr(feat, np.float32), _ptr(targ, np.float32), int(n),
+                                   _ptr(grad, np.float32), ctypes.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def pd_mlp_train_step(net, feat, targ, n, lr, stream=None, want_loss=True):
+    loss = c_double()
+    _mcheck(net, lib().pd_mlp_train_step(net, _ptr(feat, np.float32), _ptr(targ, np.float32), int(n), float(lr),
+                                         ctypes.byref(loss) if want_loss else None, _stream(stream)))
+    return loss.value if want_loss else None
+
+
+def pd_mlp_destroy(net):
+    if net is not None and net.value:
+        lib().pd_mlp_destroy(net)
+
+
+def pd_mlp_sample(ctx, x_tm1, x_t, x_tp1, feat, targ, stream=None):
+    _check(ctx, lib().pd_mlp_sample(ctx, _ptr(x_tm1), _ptr(x_t), _ptr(x_tp1), _ptr(feat, np.float32),
+                                    _ptr(targ, np.float32), _stream(stream)))
+
+
+def pd_mlp_load(ctx, blob):
+    blob = np.ascontiguousarray(blob, dtype=np.float32)
+    _check(ctx, lib().pd_mlp_load(ctx, _ptr(blob, np.float32), blob.nbytes))
+
+
+def pd_warm_start(ctx, x_t, x_tm1, q0, stream=None):
+    _check(ctx, lib().pd_warm_start(ctx, _ptr(x_t), _ptr(x_tm1), _ptr(q0), _stream(stream)))
+
+
 def pd_last_error(ctx) -> str:
     return lib().pd_last_error(ctx).decode()
 
@@ -489,3 +574,29 @@ class BatchContext:
 
     def mass(self):
         return pd_get_mass(self.ctx, self.n_v)
+
+
+class MLP:
+    """Owns one pd_mlp trainer (warm-start network) on the current device."""
+
+    def __init__(self, theta, norm):
+        self.net = pd_mlp_create(theta, norm)
+
+    def close(self):
+        pd_mlp_destroy(self.net)
+        self.net = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "net", None) is not None:
+                self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        return pd_mlp_params(self.net)
+
+    def blob(self):
+        """FP32 parameters followed by the normalisation, as pd_mlp_load takes them."""
+        theta, norm = self.params()
+        return np.concatenate([theta, norm]).astype(np.float32)

@@ -138,6 +138,7 @@ void pd_default_options(pd_options* o) {
   o->eps_tr = 0.1;
   o->adj_tol = 1e-9;
   o->escalate_window = 100;
+  o->warm_start = 0;
 }
 
 const char* pd_last_error(const pd_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -409,6 +410,20 @@ int pd_factor(pd_ctx* c) {
       (r = upload(c, &Ai, Ad.idx, true)) || (r = upload(c, &Av, Ad.val, true)) || (r = upload(c, &Bp, Bd.ptr, true)) ||
       (r = upload(c, &Bi, Bd.idx, true)) || (r = upload(c, &Bv, Bd.val, true)))
     return r;
+  // warm-start feature: log10 of the volume-weighted mean E around each vertex
+  {
+    std::vector<double> num(n_v, 0.0), den(n_v, 0.0);
+    for (int e = 0; e < n_e; ++e)
+      for (int a = 0; a < 4; ++a) {
+        num[c->tets[4 * e + a]] += c->vol[e] * c->E[e];
+        den[c->tets[4 * e + a]] += c->vol[e];
+      }
+    std::vector<float> le(n_v, 0.f);
+    for (int v = 0; v < n_v; ++v) le[v] = den[v] > 0 ? (float)std::log10(num[v] / den[v] / 1e5) : 0.f;
+    float* le_d;
+    if ((r = upload(c, &le_d, le, true))) return r;
+    d.logE = le_d;
+  }
   d.coef32 = c32; d.coef64 = c64; d.mu_e = mu_d; d.lam_e = lam_d; d.E = E_d; d.cA = cA_d;
   d.iperm = iperm_d; d.perm = perm_d; d.s_rowptr = srp; d.s_first = sfirst; d.s_val = sv; d.s_seg = seg_d;
   d.n_seg = (int)seg.size(); d.st_ptr = stp; d.st_idx = sti; d.st_val = stv;
@@ -418,6 +433,7 @@ int pd_factor(pd_ctx* c) {
   d.aa_m = c->opt.aa_m; d.k_max = c->opt.k_max; d.fixed_iters = c->opt.fixed_iters; d.tr_mode = c->opt.tr_mode;
   d.adj_max_iters = c->opt.adj_max_iters;
   d.escalate = c->opt.escalate_window;
+  d.warm = c->opt.warm_start;
   d.h = h; d.alpha_d = c->alpha; d.eps_step = c->opt.eps_step; d.eps_res = c->opt.eps_res; d.eps_abs = c->opt.eps_abs;
   d.eps_tr = c->opt.eps_tr; d.adj_tol = c->opt.adj_tol;
   for (int i = 0; i < 3; ++i) d.g[i] = c->g[i];
@@ -543,6 +559,7 @@ int stats_from_ctrl(pd_ctx* c, const Ctrl& hc, int which) {
     st.tau_one = hc.tau_one;
     st.last_rho = hc.last_rho;
     st.escalations = hc.escalations;
+    st.warm_fallbacks = hc.fallbacks;
     st.fwd_device_seconds = hc.elapsed_ns[0] * 1e-9;
   }
   if (which & 2) {
@@ -592,6 +609,10 @@ int pd_rollout(pd_ctx* c, int32_t T, const double* q0, const double* v0, const d
   if (!c) return PD_ERR_ARG;
   if (!c->factored) return fail(c, PD_ERR_NOT_FACTORED, "pd_factor must run before pd_rollout");
   if (T < 1 || !q0 || !v0) return fail(c, PD_ERR_ARG, "T >= 1 and q0, v0 are required");
+  if (c->opt.warm_start < 0 || c->opt.warm_start > 2) return fail(c, PD_ERR_ARG, "warm_start must be 0, 1 or 2");
+  if (c->opt.warm_start && !c->opt.persistent) return fail(c, PD_ERR_ARG, "the warm start needs persistent launches");
+  if (c->opt.warm_start == 1 && !(c->batch ? batch_has_mlp(c) : c->d.mlp.w != nullptr))
+    return fail(c, PD_ERR_ARG, "warm_start = 1 needs a network (pd_mlp_load)");
   CK(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
   if (c->batch) return batch_rollout(c, T, q0, v0, f_ext, f_stride, qT, vT, s, true);
@@ -683,6 +704,9 @@ int pd_rollout_enqueue(pd_ctx* c, int32_t T, const double* q0, const double* v0,
   if (!c) return PD_ERR_ARG;
   if (!c->factored) return fail(c, PD_ERR_NOT_FACTORED, "pd_factor must run before pd_rollout_enqueue");
   if (T < 1 || !q0 || !v0) return fail(c, PD_ERR_ARG, "T >= 1 and q0, v0 are required");
+  if (c->opt.warm_start < 0 || c->opt.warm_start > 2) return fail(c, PD_ERR_ARG, "warm_start must be 0, 1 or 2");
+  if (c->opt.warm_start == 1 && !(c->batch ? batch_has_mlp(c) : c->d.mlp.w != nullptr))
+    return fail(c, PD_ERR_ARG, "warm_start = 1 needs a network (pd_mlp_load)");
   CK(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
   if (c->batch) return batch_rollout(c, T, q0, v0, f_ext, f_stride, qT, vT, s, false);
@@ -810,6 +834,13 @@ int pd_collect(pd_ctx* c, void* stream) {
     return PD_OK;
   }
   return collect_single(c, s, which);
+}
+
+int pd_mlp_load(pd_ctx* c, const void* weights, size_t bytes) {
+  if (!c || !weights) return PD_ERR_ARG;
+  CK(cudaSetDevice(c->device));
+  if (c->batch) return batch_mlp_load(c, weights, bytes);
+  return mlp_upload(c, weights, bytes, &c->d.mlp, c->allocs);
 }
 
 int pd_solve(pd_ctx* c, const double* b, double* x, void* stream) {

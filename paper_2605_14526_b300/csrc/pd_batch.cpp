@@ -157,6 +157,7 @@ int collect_batch(pd_ctx* c, cudaStream_t s, int which) {
     st.steps = c->last_T;
     st.iters_total = st.iters_max = st.aa_resets = st.not_converged = st.tau_half = st.tau_one = 0;
     st.escalations = 0;
+    st.warm_fallbacks = 0;
     st.fwd_device_seconds = 0.0;
   }
   if (which & 2) {
@@ -176,6 +177,8 @@ int collect_batch(pd_ctx* c, cudaStream_t s, int which) {
       si.tau_one = h.tau_one;
       si.last_rho = h.last_rho;
       si.escalations = h.escalations;
+      si.warm_fallbacks = h.fallbacks;
+      st.warm_fallbacks += h.fallbacks;
       si.fwd_device_seconds = h.elapsed_ns[0] * 1e-9;
       st.fwd_device_seconds = std::max(st.fwd_device_seconds, si.fwd_device_seconds);
       st.escalations += h.escalations;
@@ -463,6 +466,18 @@ int batch_get_tau(const pd_ctx* c, double* tau_host, int T) {
       return PD_ERR_CUDA;
   return PD_OK;
 }
+
+int batch_mlp_load(pd_ctx* c, const void* blob, size_t bytes) {
+  pd_batch& B = *c->batch;
+  pdk::MlpDev m{};
+  const int r = mlp_upload(c, blob, bytes, &m, c->allocs);
+  if (r) return r;
+  for (pd_ctx* k : B.kids) k->d.mlp = m;
+  B.devs_dirty = true;
+  return PD_OK;
+}
+
+bool batch_has_mlp(const pd_ctx* c) { return !c->batch->kids.empty() && c->batch->kids[0]->d.mlp.w != nullptr; }
 
 void batch_destroy(pd_ctx* c) {
   pd_batch* B = c->batch;

@@ -84,6 +84,10 @@ int batch_get_mass(const pd_ctx* c, double* m);
 int batch_get_checkpoint(const pd_ctx* c, int t, double* q_host);
 int batch_get_tau(const pd_ctx* c, double* tau_host, int T);
 void batch_destroy(pd_ctx* c);
+// warm-start network blob -> device layout (pd_mlp.cu); buffers appended to owner
+int mlp_upload(pd_ctx* c, const void* blob, size_t bytes, pdk::MlpDev* out, std::vector<void*>& owner);
+int batch_mlp_load(pd_ctx* c, const void* blob, size_t bytes);
+bool batch_has_mlp(const pd_ctx* c);
 
 namespace pdh {
 

@@ -31,6 +31,7 @@ struct Ctrl {
   double dq_norm2, qprev_norm2;   // ||q^{k+1} - q^k||^2, ||q^k||^2 from the last update
   double db_norm2, bprev_norm2;   // ||b^k - b^{k-1}||^2, ||b^{k-1}||^2
   // precision escalation of the FP32 local step (persistent rollouts)
+  int fallbacks;     // warm-started steps that hit k_max and were re-run from q_t
   int hi;            // 1: the local step runs in FP64 for the rest of the rollout
   int since;         // iterations since the gate distance last halved
   int escalations;   // switches to FP64 (at most one per rollout)
@@ -60,6 +61,19 @@ enum Ticket {
   TK_ROUTE = 6, TK_CHAIN = 7, TK_PCG_INIT = 8
 };
 
+// Warm-start network (7 -> 128 -> 128 -> 128 -> 3, ReLU) as the kernels read
+// it: BF16 weights (bit patterns) in input-major order W1t [7][128],
+// W2t [128][128], W3t [128][128], W4t [128][3]; FP32 biases b1, b2, b3 [128],
+// b4 [3]; normalisation of the features and scale of the output.
+constexpr int kMlpIn = 7, kMlpH = 128, kMlpOut = 3;
+constexpr int kMlpWeights = kMlpIn * kMlpH + 2 * kMlpH * kMlpH + kMlpH * kMlpOut;
+constexpr int kMlpBiases = 3 * kMlpH + kMlpOut;
+struct MlpDev {
+  const uint16_t* w;   // [kMlpWeights]
+  const float* b;      // [kMlpBiases]
+  float fmean[kMlpIn], fscale[kMlpIn], oscale[kMlpOut];
+};
+
 // Everything the kernels need, passed by value.
 struct Dev {
   int n_v, n_e, n_f;
@@ -67,6 +81,7 @@ struct Dev {
   int local_fp32;
   int aa_m, k_max, fixed_iters, tr_mode, adj_max_iters;
   int escalate;       // FP32 local step: switch to FP64 after this many iterations without progress (0 = never)
+  int warm;           // start of each step: 0 q_t, 1 network warm start, 2 constant-velocity extrapolation
   double h, alpha_d, eps_step, eps_res, eps_abs, eps_tr, adj_tol;
   double g[3];
   double mu_bar, lam_bar, k_bar, mu_ref, beta0, nu;
@@ -82,6 +97,8 @@ struct Dev {
   const double* lam_e;     // [n_e]
   const double* E;         // [n_e]
   const double* X;         // [n_v][3]
+  const float* logE;       // [n_v] log10(E_v / 1e5), E_v the volume-weighted mean E around v
+  MlpDev mlp;
   const double* mass;      // [n_v]
   const uint8_t* pinned;   // [n_v]
   const int* inc_ptr;      // [n_v+1] vertex -> incident (element*4 + corner)

@@ -15,6 +15,7 @@
 
 #include "pd_coop.h"
 #include "pd_grid.cuh"
+#include "pd_mlp.cuh"
 #include "pd_launch.h"
 #include "pd_phases.cuh"
 
@@ -72,7 +73,7 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
   };
   if (tid == 0) {
     S.iters_total = S.iters_max = S.resets = S.not_converged = S.tau_half = S.tau_one = S.status = 0;
-    S.hi = S.escalations = 0;
+    S.hi = S.escalations = S.fallbacks = 0;
     S.last_rho = 0.0;
     for (int i = 0; i < kMaxAA * kMaxAA; ++i) S.gram[i] = 0.0;
     t0 = gtimer();
@@ -87,55 +88,83 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
     for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) step_begin_item(d, v, qin, vin, fst, a.ckpt + (size_t)t * nv3);
     if (!(ok = grid_sync(d, tm))) break;
     mark(PH_BEGIN);
-    for (;;) {
-      const int k = S.k;
-      const bool hi = S.hi != 0;   // FP64 local step after an escalation
-      for (int e = re.lo + tid; e < re.hi; e += blockDim.x) local_any<T>(d, e, hi);
-      work_done(PH_LOCAL);
-      if (!(ok = grid_sync(d, tm))) break;
-      mark(PH_LOCAL);
-      double p3[3] = {0.0, 0.0, 0.0};
-      for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) assemble_any<T>(d, v, k, p3, hi);
-      work_done(PH_ASSEMBLE);
-      if (!(ok = grid_reduce<3>(d, tm, p3, sums))) break;
-      if (tid == 0) assemble_finish(d, &S, k, sums);
-      __syncthreads();
-      mark(PH_ASSEMBLE);
-      if (S.done) break;
-      for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, sg, lane);
-      work_done(PH_SPMV_S);
-      if (!(ok = grid_sync(d, tm))) break;
-      mark(PH_SPMV_S);
-      // S^T y row by row, with the Anderson work of that row's vertex fused in
-      const AAView av = aa_view(d, S.pairs, S.ncols, S.head);
-      double pa[2 * kMaxAA];
-      for (int j = 0; j < 2 * kMaxAA; ++j) pa[j] = 0.0;
-      for (int j = gwarp; j < d.n_f; j += nwarps) {
-        double a0, a1, a2;
-        spmv_st_sum(d, d.y, j, lane, a0, a1, a2);
-        if (lane < 3) {
-          const size_t o = 3 * (size_t)d.perm[j] + lane;
-          const double qh = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
-          d.qhat[o] = qh;
-          aa_component(d, o, qh, av, pa);
-        }
+    // warm start (network or constant-velocity extrapolation); a warm-started
+    // step that hits k_max is run again from q_t, the plain start of Alg. 1
+    const int nc0 = S.not_converged;
+    bool warm_now = d.warm != 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      if (warm_now) {
+        for (int v = gwarp; v < d.n_v; v += nwarps) warm_vertex(d, v, d.qt, nullptr, vin, d.q, d.qprev, lane);
+        if (!(ok = grid_sync(d, tm))) break;
       }
-      work_done(PH_AA);
-      if (!(ok = grid_reduce<2 * kMaxAA>(d, tm, pa, sums))) break;
-      if (tid == 0) aa_finish(d, &S, av, sums);
-      __syncthreads();
-      mark(PH_AA);
-      const int use_hat = S.use_hat, nc = S.ncols;
-      double gam[kMaxAA];
-      for (int j = 0; j < nc; ++j) gam[j] = S.gamma[j];
-      double pu[2] = {0.0, 0.0};
-      for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) update_item(d, v, use_hat, nc, gam, pu);
-      work_done(PH_UPDATE);
-      if (!(ok = grid_reduce<2>(d, tm, pu, sums))) break;
-      if (tid == 0) update_finish(d, &S, sums);
-      __syncthreads();
-      mark(PH_UPDATE);
-      if (S.done) break;
+      for (;;) {
+        const int k = S.k;
+        const bool hi = S.hi != 0;   // FP64 local step after an escalation
+        for (int e = re.lo + tid; e < re.hi; e += blockDim.x) local_any<T>(d, e, hi);
+        work_done(PH_LOCAL);
+        if (!(ok = grid_sync(d, tm))) break;
+        mark(PH_LOCAL);
+        double p3[3] = {0.0, 0.0, 0.0};
+        for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) assemble_any<T>(d, v, k, p3, hi);
+        work_done(PH_ASSEMBLE);
+        if (!(ok = grid_reduce<3>(d, tm, p3, sums))) break;
+        if (tid == 0) assemble_finish(d, &S, k, sums);
+        __syncthreads();
+        mark(PH_ASSEMBLE);
+        if (S.done) break;
+        for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, sg, lane);
+        work_done(PH_SPMV_S);
+        if (!(ok = grid_sync(d, tm))) break;
+        mark(PH_SPMV_S);
+        // S^T y row by row, with the Anderson work of that row's vertex fused in
+        const AAView av = aa_view(d, S.pairs, S.ncols, S.head);
+        double pa[2 * kMaxAA];
+        for (int j = 0; j < 2 * kMaxAA; ++j) pa[j] = 0.0;
+        for (int j = gwarp; j < d.n_f; j += nwarps) {
+          double a0, a1, a2;
+          spmv_st_sum(d, d.y, j, lane, a0, a1, a2);
+          if (lane < 3) {
+            const size_t o = 3 * (size_t)d.perm[j] + lane;
+            const double qh = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
+            d.qhat[o] = qh;
+            aa_component(d, o, qh, av, pa);
+          }
+        }
+        work_done(PH_AA);
+        if (!(ok = grid_reduce<2 * kMaxAA>(d, tm, pa, sums))) break;
+        if (tid == 0) aa_finish(d, &S, av, sums);
+        __syncthreads();
+        mark(PH_AA);
+        const int use_hat = S.use_hat, nc = S.ncols;
+        double gam[kMaxAA];
+        for (int j = 0; j < nc; ++j) gam[j] = S.gamma[j];
+        double pu[2] = {0.0, 0.0};
+        for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) update_item(d, v, use_hat, nc, gam, pu);
+        work_done(PH_UPDATE);
+        if (!(ok = grid_reduce<2>(d, tm, pu, sums))) break;
+        if (tid == 0) update_finish(d, &S, sums);
+        __syncthreads();
+        mark(PH_UPDATE);
+        if (S.done) break;
+      }
+      if (!ok) break;
+      const bool redo = warm_now && S.not_converged > nc0;
+      __syncthreads();   // every thread has read S before thread 0 resets it
+      if (!redo) break;
+      if (tid == 0) {
+        S.not_converged = nc0;
+        S.fallbacks += 1;
+        ctrl_step_reset(&S, t);
+      }
+      for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x)
+        for (int i = 0; i < 3; ++i) {
+          const size_t o = 3 * (size_t)v + i;
+          d.q[o] = d.qt[o];
+          d.qprev[o] = d.qt[o];
+          d.gprev[o] = 0.0;
+        }
+      if (!(ok = grid_sync(d, tm))) break;
+      warm_now = false;
     }
     if (!ok) break;
     const bool last = t == a.T - 1;
@@ -166,6 +195,7 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
     c->last_rho = S.last_rho;
     c->k = S.k;
     c->escalations = S.escalations;
+    c->fallbacks = S.fallbacks;
     atomicOr(&c->status, S.status);
     for (int i = 0; i < 8; ++i) {
       c->phase_ns[i] += ph[i];

@@ -16,7 +16,7 @@ namespace pdk {
 // per-block shared replica FwdState (persistent rollout).
 struct FwdState {
   int k, done, converged, pairs, ncols, head, use_hat, t, n_local, n_solve;
-  int hi, since, escalations;
+  int hi, since, escalations, fallbacks;
   double gmin;
   int iters_total, iters_max, resets, not_converged, tau_half, tau_one, status;
   double gram[kMaxAA * kMaxAA];

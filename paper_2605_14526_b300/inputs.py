@@ -349,3 +349,17 @@ def batch_meshes(n: int = 64, tets_lo: int = 1000, tets_hi: int = 40000, steps: 
     rng = np.random.default_rng(seed)
     sizes = np.exp(rng.uniform(np.log(tets_lo), np.log(tets_hi), size=n))
     return [batch_instance(rng, int(s), steps=steps, name=f"m{i}") for i, s in enumerate(sizes)]
+
+
+def mlp_init(seed: int = 0, hidden: int = 128) -> np.ndarray:
+    """Initial parameters of the warm-start network (7 -> H -> H -> H -> 3):
+    weights uniform in +-sqrt(6 / fan_in) (He et al. 2015, uniform form),
+    biases zero; flat FP32 vector in the library's layout W1, b1, W2, b2, W3,
+    b3, W4, b4."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_in, fan_out in ((7, hidden), (hidden, hidden), (hidden, hidden), (hidden, 3)):
+        lim = np.sqrt(6.0 / fan_in)
+        parts.append(rng.uniform(-lim, lim, size=fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)
