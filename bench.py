@@ -228,9 +228,9 @@ def run_batch(args, rank, world, local_rank, dev, dist):
         bwd_bytes += bb * inst_b[i] / args.steps
     fwd_launch_ms, bwd_launch_ms = fwd_ms / args.steps, bwd_ms / args.steps
     if fwd_launch_ms >= bwd_launch_ms:
-        kname, kbytes, kms = "k_fwd_batch (batched persistent forward)", fwd_bytes, fwd_launch_ms
+        kname, kbytes, kms = "k_fwd_rollout (persistent forward, one team per instance)", fwd_bytes, fwd_launch_ms
     else:
-        kname, kbytes, kms = "k_bwd_batch (batched persistent adjoint)", bwd_bytes, bwd_launch_ms
+        kname, kbytes, kms = "k_bwd_rollout (persistent adjoint, one team per instance)", bwd_bytes, bwd_launch_ms
     achieved = kbytes / (kms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
     tf, tb = bc.teams()

@@ -481,7 +481,8 @@ int reserve_enqueue(pd_ctx* c, int T, cudaStream_t s) {
 // co-resident grid of a persistent launch: the tuned grid if one is set, else
 // SMs x blocks per SM; 0 if cooperative launch is unavailable
 int grid_of(pd_ctx* c, bool bwd, int* grid) {
-  const int full = bwd ? pdk::persistent_grid_bwd(c->d, 0) : pdk::persistent_grid(c->d, 0);
+  const bool fp32 = c->opt.local_fp32 != 0;
+  const int full = bwd ? pdk::persistent_grid_bwd(fp32, 0) : pdk::persistent_grid(fp32, 0);
   *grid = 0;
   if (full <= 0) return PD_OK;
   const int want = bwd ? c->tune.bwd_grid : c->tune.fwd_grid;
@@ -490,7 +491,42 @@ int grid_of(pd_ctx* c, bool bwd, int* grid) {
     if (want > full) return fail(c, PD_ERR_ARG, "tuned grid %d exceeds the %d co-resident blocks", want, full);
     *grid = want;
   } else {
-    *grid = bwd ? pdk::persistent_grid_bwd(c->d, bps) : pdk::persistent_grid(c->d, bps);
+    *grid = bwd ? pdk::persistent_grid_bwd(fp32, bps) : pdk::persistent_grid(fp32, bps);
+  }
+  return PD_OK;
+}
+
+// device state of a single-instance persistent launch: the Dev record when
+// it changed, the team map of direction dir when the grid changed; refused
+// while the stream is captured (run once before capture)
+int prepare_single(pd_ctx* c, cudaStream_t s, int dir, int grid) {
+  const bool cap = capturing(s);
+  const bool same_d = c->d_valid && std::memcmp(&c->d_uploaded, &c->d, sizeof(Dev)) == 0;
+  if ((!c->d_dev || !same_d || c->team_grid[dir] != grid) && cap)
+    return fail(c, PD_ERR_ARG, "the launch state changed since the last launch: run it once before capture");
+  if (!c->d_dev) {
+    const bool fp32 = c->opt.local_fp32 != 0;
+    c->team_cap = std::max(std::max(pdk::persistent_grid(fp32, 0), pdk::persistent_grid_bwd(fp32, 0)), 1);
+    int r;
+    if ((r = dalloc(c, &c->d_dev, 1)) || (r = dalloc(c, &c->d_off, 2)) || (r = dalloc(c, &c->d_team[0], c->team_cap)) ||
+        (r = dalloc(c, &c->d_team[1], c->team_cap)))
+      return r;
+    const pdk::InstOff off[2] = {{0, 0}, {c->n_v, c->n_e}};
+    CK(cudaMemcpy(c->d_off, off, sizeof(off), cudaMemcpyHostToDevice));
+  }
+  if (grid > c->team_cap) return fail(c, PD_ERR_ARG, "grid %d exceeds the team map (%d)", grid, c->team_cap);
+  if (!same_d) {
+    c->d_uploaded = c->d;
+    CK(cudaMemcpyAsync(c->d_dev, &c->d_uploaded, sizeof(Dev), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    c->d_valid = true;
+  }
+  if (c->team_grid[dir] != grid) {
+    std::vector<int4> map(grid);
+    for (int b = 0; b < grid; ++b) map[b] = make_int4(0, b, grid, 0);
+    CK(cudaMemcpyAsync(c->d_team[dir], map.data(), grid * sizeof(int4), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    c->team_grid[dir] = grid;
   }
   return PD_OK;
 }
@@ -501,23 +537,22 @@ int enqueue_fwd_single(pd_ctx* c, int T, const double* q0d, const double* v0d, c
   Dev& d = c->d;
   d.ckpt = c->ckpt;
   d.tau = c->tau;
-  d.phase_count = c->phase_count;
-  d.T = T;
+  d.phase_count = nullptr;
+  d.T = 0;
+  int r;
+  if ((r = prepare_single(c, s, 0, grid))) return r;
   CK(cudaMemsetAsync(c->tau, 0, (size_t)T * sizeof(double), s));
   CK(cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), s));  // per-rollout statistics and flags
   CK(cudaMemsetAsync(d.sstar, 0, 3 * sizeof(double) * (size_t)c->n_e, s));  // no prox warm start across rollouts
-  pdk::RollArgs ra;
-  ra.T = T;
-  ra.q0 = q0d;
-  ra.v0 = v0d;
-  ra.fext = fd;
-  ra.f_stride = f_stride;
-  ra.qT = qTd;
-  ra.vT = vTd;
-  ra.ckpt = c->ckpt;
-  ra.sq = c->sq;
-  ra.sv = c->sv;
-  CK(pdk::launch_fwd_rollout(d, s, ra, grid));
+  pdk::BatchFwd br;
+  br.T = T;
+  br.q0 = q0d;
+  br.v0 = v0d;
+  br.fext = fd;
+  br.f_stride = f_stride;
+  br.qT = qTd;
+  br.vT = vTd;
+  CK(pdk::launch_fwd_rollout(d.local_fp32 != 0, c->d_dev, c->d_team[0], c->d_off, br, grid, s));
   c->launches += 1;
   c->last_T = T;
   return PD_OK;
@@ -526,20 +561,21 @@ int enqueue_fwd_single(pd_ctx* c, int T, const double* q0d, const double* v0d, c
 int enqueue_bwd_single(pd_ctx* c, const double* dqTd, const double* dvTd, double* dq0d, double* dv0d, double* dEd,
                        double* dnud, double* dfd, int64_t df_stride, cudaStream_t s, int grid) {
   Dev& d = c->d;
+  int r;
+  if ((r = prepare_single(c, s, 1, grid))) return r;
   if (dfd && df_stride == 0) CK(cudaMemsetAsync(dfd, 0, 3 * (size_t)c->n_v * sizeof(double), s));
-  pdk::BwdArgs ba;
-  ba.T = c->last_T;
-  ba.dqT = dqTd;
-  ba.dvT = dvTd;
-  ba.dq0 = dq0d;
-  ba.dv0 = dv0d;
-  ba.dE = dEd;
-  ba.dnu = dnud;
-  ba.df = dfd;
-  ba.df_stride = df_stride;
-  ba.ckpt = c->ckpt;
+  pdk::BatchBwd br;
+  br.T = c->last_T;
+  br.dqT = dqTd;
+  br.dvT = dvTd;
+  br.dq0 = dq0d;
+  br.dv0 = dv0d;
+  br.dE = dEd;
+  br.dnu = dnud;
+  br.df = dfd;
+  br.df_stride = df_stride;
   CK(cudaMemsetAsync(&d.ctrl->bar_count, 0, 2 * sizeof(unsigned int), s));
-  CK(pdk::launch_bwd_rollout(d, s, ba, grid));
+  CK(pdk::launch_bwd_rollout(d.local_fp32 != 0, c->d_dev, c->d_team[1], c->d_off, br, grid, s));
   c->launches += 1;
   return PD_OK;
 }

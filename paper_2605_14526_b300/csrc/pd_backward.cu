@@ -644,14 +644,9 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kPersistBlock, 2) k_bwd_rollout(Dev d, BwdArgs a) {
-  bwd_rollout_body<T>(d, a, Team{(int)blockIdx.x, (int)gridDim.x});
-}
-
 // team[blockIdx.x] = {instance, block index in its team, team size, 0}
 template <typename T>
-__global__ void __launch_bounds__(kPersistBlock, 2) k_bwd_batch(const Dev* __restrict__ devs, const int4* __restrict__ team,
+__global__ void __launch_bounds__(kPersistBlock, 2) k_bwd_rollout(const Dev* __restrict__ devs, const int4* __restrict__ team,
                                                                 const InstOff* __restrict__ off, BatchBwd br) {
   __shared__ Dev sd;
   __shared__ BwdArgs sa;
@@ -725,31 +720,21 @@ void launch_bwd_finish(const Dev& d, cudaStream_t s, double* dq0, double* dv0) {
   k_bwd_finish<<<nblk(3 * d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d, dq0, dv0);
 }
 
-static const void* bwd_fn(bool fp32, bool batch) {
-  if (batch) return fp32 ? (const void*)k_bwd_batch<float> : (const void*)k_bwd_batch<double>;
+static const void* bwd_fn(bool fp32) {
   return fp32 ? (const void*)k_bwd_rollout<float> : (const void*)k_bwd_rollout<double>;
 }
 
-static int grid_for(const void* fn, int blocks_per_sm) {
+int persistent_grid_bwd(bool fp32, int blocks_per_sm) {
   int sms = 0;
-  const int per = coop_blocks_per_sm(fn, &sms);
+  const int per = coop_blocks_per_sm(bwd_fn(fp32), &sms);
   if (per < 1) return 0;
   return sms * (blocks_per_sm >= 1 && blocks_per_sm < per ? blocks_per_sm : per);
 }
 
-int persistent_grid_bwd(const Dev& d, int blocks_per_sm) { return grid_for(bwd_fn(d.local_fp32, false), blocks_per_sm); }
-
-int persistent_grid_bwd_batch(bool fp32, int blocks_per_sm) { return grid_for(bwd_fn(fp32, true), blocks_per_sm); }
-
-cudaError_t launch_bwd_rollout(const Dev& d, cudaStream_t s, const BwdArgs& a, int grid) {
-  if (d.local_fp32) return coop_launch(k_bwd_rollout<float>, grid, s, d, a);
-  return coop_launch(k_bwd_rollout<double>, grid, s, d, a);
-}
-
-cudaError_t launch_bwd_batch(bool fp32, const Dev* devs, const int4* team, const InstOff* off, const BatchBwd& br,
-                             int grid, cudaStream_t s) {
-  if (fp32) return coop_launch(k_bwd_batch<float>, grid, s, devs, team, off, br);
-  return coop_launch(k_bwd_batch<double>, grid, s, devs, team, off, br);
+cudaError_t launch_bwd_rollout(bool fp32, const Dev* devs, const int4* team, const InstOff* off, const BatchBwd& br,
+                               int grid, cudaStream_t s) {
+  if (fp32) return coop_launch(k_bwd_rollout<float>, grid, s, devs, team, off, br);
+  return coop_launch(k_bwd_rollout<double>, grid, s, devs, team, off, br);
 }
 
 }  // namespace pdk

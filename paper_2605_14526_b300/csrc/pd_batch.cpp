@@ -54,14 +54,6 @@ struct pd_batch {
 
 namespace {
 
-bool capturing(cudaStream_t s) {
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return cs != cudaStreamCaptureStatusNone;
-}
 
 // Team sizes minimise the largest predicted instance time: every instance
 // gets one block, then blocks go one at a time to the instance whose
@@ -108,7 +100,7 @@ int shape_teams(pd_ctx* c, int dir, std::vector<int>& b) {
   const bool fp32 = c->opt.local_fp32 != 0;
   const pd_tuning& tn = c->tune;
   const int bps = dir ? tn.bwd_blocks_per_sm : tn.fwd_blocks_per_sm;
-  const int G = dir ? pdk::persistent_grid_bwd_batch(fp32, bps) : pdk::persistent_grid_batch(fp32, bps);
+  const int G = dir ? pdk::persistent_grid_bwd(fp32, bps) : pdk::persistent_grid(fp32, bps);
   if (G <= 0) return fail(c, PD_ERR_CUDA, "cooperative launch of the batched kernel is not available");
   if (B.n > G) return fail(c, PD_ERR_TOO_LARGE, "%d instances exceed the %d co-resident blocks", B.n, G);
   if (G > B.team_cap) return fail(c, PD_ERR_ARG, "co-resident grid %d exceeds the team map (%d)", G, B.team_cap);
@@ -349,7 +341,7 @@ int batch_rollout(pd_ctx* c, int T, const double* q0, const double* v0, const do
   br.f_stride = f_stride;
   br.qT = qTd;
   br.vT = vTd;
-  CK(pdk::launch_fwd_batch(c->opt.local_fp32 != 0, B.d_devs, B.d_team[0], B.d_off, br, B.grid[0], s));
+  CK(pdk::launch_fwd_rollout(c->opt.local_fp32 != 0, B.d_devs, B.d_team[0], B.d_off, br, B.grid[0], s));
   c->launches += 1;
   c->last_T = T;
   for (pd_ctx* k : B.kids) k->last_T = T;
@@ -415,7 +407,7 @@ int batch_backward(pd_ctx* c, const double* dqT, const double* dvT, double* dq0,
   br.dnu = dnud;
   br.df = dfd;
   br.df_stride = df_stride;
-  CK(pdk::launch_bwd_batch(c->opt.local_fp32 != 0, B.d_devs, B.d_team[1], B.d_off, br, B.grid[1], s));
+  CK(pdk::launch_bwd_rollout(c->opt.local_fp32 != 0, B.d_devs, B.d_team[1], B.d_off, br, B.grid[1], s));
   c->launches += 1;
   if (!sync) {
     c->pending |= 2;
@@ -561,7 +553,7 @@ int pd_create_batch(int32_t n, const pd_mesh* meshes, const pd_material* mats, d
   B.hctrl.assign(n, Ctrl{});
   B.inst.assign(n, pd_stats{});
   const bool fp32 = c->opt.local_fp32 != 0;
-  B.team_cap = std::max(std::max(pdk::persistent_grid_batch(fp32, 0), pdk::persistent_grid_bwd_batch(fp32, 0)), 1);
+  B.team_cap = std::max(std::max(pdk::persistent_grid(fp32, 0), pdk::persistent_grid_bwd(fp32, 0)), 1);
   CK(cudaMalloc(&B.ctrl, n * sizeof(Ctrl)));
   CK(cudaMemset(B.ctrl, 0, n * sizeof(Ctrl)));
   CK(cudaMalloc(&B.sstar, 3 * (size_t)std::max<long long>(B.off[n].e, 1) * sizeof(double)));
@@ -715,7 +707,8 @@ int pd_autotune(pd_ctx* c, int32_t T_probe, const double* q0, const double* v0, 
   } else {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    const int full = std::min(pdk::persistent_grid(c->d, 0), pdk::persistent_grid_bwd(c->d, 0));
+    const bool fp32 = c->opt.local_fp32 != 0;
+    const int full = std::min(pdk::persistent_grid(fp32, 0), pdk::persistent_grid_bwd(fp32, 0));
     for (int gsz : {sms / 2, sms, (3 * sms) / 2, 2 * sms})
       if (gsz >= 1 && gsz <= full) cands.push_back({0, gsz, 1.0, 256});
   }

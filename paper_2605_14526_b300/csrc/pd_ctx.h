@@ -70,6 +70,16 @@ struct pd_ctx {
   pd_batch* batch = nullptr;
   // last asynchronous operation awaiting pd_collect: 0 none, 1 rollout, 2 backward
   int pending = 0;
+  // persistent launches of a single instance run the batched kernel with one
+  // team: device copy of d (re-uploaded when d changes), prefix offsets and
+  // the block -> team maps of the forward and the adjoint grid
+  Dev* d_dev = nullptr;
+  pdk::InstOff* d_off = nullptr;
+  int4* d_team[2] = {nullptr, nullptr};
+  int team_cap = 0;
+  int team_grid[2] = {0, 0};
+  Dev d_uploaded{};
+  bool d_valid = false;
 };
 
 // batched instances (pd_batch.cpp)
@@ -135,6 +145,15 @@ inline bool is_device_ptr(const void* p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+inline bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cs != cudaStreamCaptureStatusNone;
 }
 
 inline int ensure_stage(pd_ctx* c, size_t n) {

@@ -25,22 +25,18 @@ void launch_solve(const Dev& d, cudaStream_t s, const double* b, double* xperm, 
 // cooperative launch is unavailable); *sms gets the SM count
 int coop_blocks_per_sm(const void* fn, int* sms);
 
-// persistent forward rollout: cooperative grid size (0 if not available; at
-// most blocks_per_sm blocks per SM when that is >= 1) and launch
-int persistent_grid(const Dev& d, int blocks_per_sm);
-cudaError_t launch_fwd_rollout(const Dev& d, cudaStream_t s, const RollArgs& a, int grid);
-// batched form: devs and off are device arrays with one entry per instance,
-// team[grid] maps each block to {instance, index in its team, team size}
-int persistent_grid_batch(bool fp32, int blocks_per_sm);
-cudaError_t launch_fwd_batch(bool fp32, const Dev* devs, const int4* team, const InstOff* off, const BatchFwd& br,
-                             int grid, cudaStream_t s);
-
-// persistent backward rollout (single and batched)
-int persistent_grid_bwd(const Dev& d, int blocks_per_sm);
-cudaError_t launch_bwd_rollout(const Dev& d, cudaStream_t s, const BwdArgs& a, int grid);
-int persistent_grid_bwd_batch(bool fp32, int blocks_per_sm);
-cudaError_t launch_bwd_batch(bool fp32, const Dev* devs, const int4* team, const InstOff* off, const BatchBwd& br,
-                             int grid, cudaStream_t s);
+// Persistent rollout / adjoint of one or many instances (one team of blocks
+// per instance): co-resident grid size (0 if cooperative launch is not
+// available; at most blocks_per_sm blocks per SM when that is >= 1) and the
+// launch. devs and off are device arrays with one entry per instance (off:
+// n + 1 prefix offsets), team[grid] maps each block to {instance, index in
+// its team, team size, 0}.
+int persistent_grid(bool fp32, int blocks_per_sm);
+cudaError_t launch_fwd_rollout(bool fp32, const Dev* devs, const int4* team, const InstOff* off, const BatchFwd& br,
+                               int grid, cudaStream_t s);
+int persistent_grid_bwd(bool fp32, int blocks_per_sm);
+cudaError_t launch_bwd_rollout(bool fp32, const Dev* devs, const int4* team, const InstOff* off, const BatchBwd& br,
+                               int grid, cudaStream_t s);
 
 // backward (Alg. 2)
 void launch_bwd_setup(const Dev& d, cudaStream_t s, const double* qstar, const double* tau_t);

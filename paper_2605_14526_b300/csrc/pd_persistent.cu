@@ -205,14 +205,9 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kPersistBlock, 2) k_fwd_rollout(Dev d, RollArgs a) {
-  fwd_rollout_body<T>(d, a, Team{(int)blockIdx.x, (int)gridDim.x});
-}
-
 // team[blockIdx.x] = {instance, block index in its team, team size, 0}
 template <typename T>
-__global__ void __launch_bounds__(kPersistBlock, 2) k_fwd_batch(const Dev* __restrict__ devs, const int4* __restrict__ team,
+__global__ void __launch_bounds__(kPersistBlock, 2) k_fwd_rollout(const Dev* __restrict__ devs, const int4* __restrict__ team,
                                                                 const InstOff* __restrict__ off, BatchFwd br) {
   __shared__ Dev sd;
   __shared__ RollArgs sa;
@@ -249,34 +244,21 @@ int coop_blocks_per_sm(const void* fn, int* sms_out) {
   return per_sm < 2 ? per_sm : 2;
 }
 
-static const void* fwd_fn(bool fp32, bool batch) {
-  if (batch) return fp32 ? (const void*)k_fwd_batch<float> : (const void*)k_fwd_batch<double>;
+static const void* fwd_fn(bool fp32) {
   return fp32 ? (const void*)k_fwd_rollout<float> : (const void*)k_fwd_rollout<double>;
 }
 
-int persistent_grid(const Dev& d, int blocks_per_sm) {
+int persistent_grid(bool fp32, int blocks_per_sm) {
   int sms = 0;
-  const int per = coop_blocks_per_sm(fwd_fn(d.local_fp32, false), &sms);
+  const int per = coop_blocks_per_sm(fwd_fn(fp32), &sms);
   if (per < 1) return 0;
   return sms * (blocks_per_sm >= 1 && blocks_per_sm < per ? blocks_per_sm : per);
 }
 
-int persistent_grid_batch(bool fp32, int blocks_per_sm) {
-  int sms = 0;
-  const int per = coop_blocks_per_sm(fwd_fn(fp32, true), &sms);
-  if (per < 1) return 0;
-  return sms * (blocks_per_sm >= 1 && blocks_per_sm < per ? blocks_per_sm : per);
-}
-
-cudaError_t launch_fwd_rollout(const Dev& d, cudaStream_t s, const RollArgs& a, int grid) {
-  if (d.local_fp32) return coop_launch(k_fwd_rollout<float>, grid, s, d, a);
-  return coop_launch(k_fwd_rollout<double>, grid, s, d, a);
-}
-
-cudaError_t launch_fwd_batch(bool fp32, const Dev* devs, const int4* team, const InstOff* off, const BatchFwd& br,
-                             int grid, cudaStream_t s) {
-  if (fp32) return coop_launch(k_fwd_batch<float>, grid, s, devs, team, off, br);
-  return coop_launch(k_fwd_batch<double>, grid, s, devs, team, off, br);
+cudaError_t launch_fwd_rollout(bool fp32, const Dev* devs, const int4* team, const InstOff* off, const BatchFwd& br,
+                               int grid, cudaStream_t s) {
+  if (fp32) return coop_launch(k_fwd_rollout<float>, grid, s, devs, team, off, br);
+  return coop_launch(k_fwd_rollout<double>, grid, s, devs, team, off, br);
 }
 
 }  // namespace pdk
