@@ -19,6 +19,10 @@ CASES = {
     "cube": lambda s: inputs.small_cube(steps=s),
     "bar": lambda s: inputs.hetero_bar(steps=s),
     "smallbar": lambda s: inputs.hetero_bar(nx=8, ny=4, nz=4, block=4, steps=s),
+    # 8 uneven meshes of 1k-10k tets in one batched launch
+    "batch8": lambda s: inputs.batch_meshes(n=8, tets_lo=1000, tets_hi=10000, steps=s, seed=11),
+    # the full batched workload (64 meshes)
+    "batch64": lambda s: inputs.batch_meshes(steps=s),
 }
 
 
@@ -32,28 +36,41 @@ def main():
     args = ap.parse_args()
     build()
     sc = CASES[args.case](args.steps)
-    opt = binding.options_for(sc.solver)
-    opt.persistent = args.persistent
-    pd = binding.PDContext(sc, opt)
     dev = "cuda:0"
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
-    x0, v0, f0 = t(sc.x0), t(sc.v0), t(sc.f_ext[0])
+    if isinstance(sc, list):   # a batch of instances in one launch
+        scenes = sc
+        sc = scenes[0]
+        opt = binding.options_for(sc.solver)
+        opt.persistent = args.persistent
+        pd = binding.BatchContext(scenes, opt)
+        x0 = t(pd.concat([s.x0 for s in scenes]).reshape(-1, 3))
+        v0 = t(pd.concat([s.v0 for s in scenes]).reshape(-1, 3))
+        f0 = t(pd.concat([s.f_ext[0] for s in scenes]).reshape(-1, 3))
+        n_e = pd.n_e
+    else:
+        opt = binding.options_for(sc.solver)
+        opt.persistent = args.persistent
+        pd = binding.PDContext(sc, opt)
+        x0, v0, f0 = t(sc.x0), t(sc.v0), t(sc.f_ext[0])
+        n_e = sc.n_e
     qT, vT = torch.empty_like(x0), torch.empty_like(x0)
     dq0, dv0 = torch.empty_like(x0), torch.empty_like(x0)
-    dE = torch.empty(sc.n_e, dtype=torch.float64, device=dev)
+    dE = torch.empty(n_e, dtype=torch.float64, device=dev)
+    dnu = torch.empty(getattr(pd, "n", 1), dtype=torch.float64, device=dev)
     names = ["begin", "local", "assemble+gate", "S b", "S^T y", "anderson", "update", "end+tr"]
     for r in range(args.repeat):
-        if args.phases and r == args.repeat - 1:
+        if args.phases and r == args.repeat - 1 and not hasattr(pd, "n"):
             binding.pd_profile(pd.ctx, True)
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record()
         binding.pd_rollout(pd.ctx, sc.steps, x0, v0, f0, 0, qT, vT)
         e1.record()
-        binding.pd_backward(pd.ctx, qT, None, dq0, dv0, dE, None, None, 0)
+        binding.pd_backward(pd.ctx, qT, None, dq0, dv0, dE, dnu, None, 0)
         e2.record()
         torch.cuda.synchronize()
         print(f"repeat {r}: forward {e0.elapsed_time(e1):.2f} ms, backward {e1.elapsed_time(e2):.2f} ms")
-    if args.phases:
+    if args.phases and not hasattr(pd, "n"):
         p = binding.pd_get_profile(pd.ctx)
         print("forward phases (ms): " + ", ".join(f"{n} {p.phase_ms[i]:.3f}" for i, n in enumerate(names)))
         print("  block-0 work (ms): " + ", ".join(f"{n} {p.work_ms[i]:.3f}" for i, n in enumerate(names)))
