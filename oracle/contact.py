@@ -1,0 +1,205 @@
+"""Oracle of the frictional contact step (TEST INFRASTRUCTURE ONLY).
+
+Sec. 4.6 (Signorini-Coulomb complementarity, eq. fb_n, eq. contact_system,
+eq. q_update) with the reading the paper leaves open: the factor of A is kept
+fixed; contacts are vertex-ground (z >= z_g, normal +z) and vertex-box-bottom
+(z <= z_box(t), normal -z) at the position level; friction is Tresca with
+disk radius mu * lambda_n from the normal solve of the same iteration
+("staggered"), acting on the tangential displacement since q_t.
+
+Because A = L_A (x) I_3 and the normals are +-z, the normal and the
+tangential problems of one local-global iteration decouple by axis and share
+the scalar Delassus matrix W = (L_A^-1)_CC of the candidate vertices C:
+
+  q_u      = A^-1 b(q)                                    (the plain global step)
+  g_c      = n_c (q_u,z[v_c] - z_c)                       (gaps; z_c the obstacle height)
+  normal   0 <= lam_n  _|_  D W D lam_n + g >= 0          (D = diag(n_c))
+  friction lam_f = argmin 1/2 sum_axes lam^T W lam + lam^T s,  |lam_f,c| <= mu lam_n,c
+           s_c = q_u,xy[v_c] - q_t,xy[v_c]
+  q        = q_u + A^-1 J^T lam,  J^T lam = (lam_f,c, n_c lam_n,c) at v_c
+
+Both subproblems are strictly convex QPs in W (SPD), so their solutions are
+unique. The normal LCP is solved exactly by Murty's least-index principal
+pivoting method (finite for positive definite matrices); the friction QP by
+block projected Gauss-Seidel on the disks; both solutions are checked against
+their KKT conditions. A step is the fixed point of the contact-corrected
+local-global map (Anderson-mixed Picard iterations, to 1e-13 by default).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import solver
+
+
+def delassus(pb: solver.Problem, verts: np.ndarray) -> np.ndarray:
+    """W = (L_A^-1)_CC for candidate vertices (all free), one solve per column."""
+    pos = np.searchsorted(pb.free, verts)
+    assert np.array_equal(pb.free[pos], verts), "contact candidates must be free vertices"
+    K = verts.size
+    W = np.zeros((K, K))
+    for j in range(K):
+        e = np.zeros(pb.free.size)
+        e[pos[j]] = 1.0
+        W[:, j] = pb.lu.solve(e)[pos]
+    return 0.5 * (W + W.T)
+
+
+def lcp_murty(M: np.ndarray, q: np.ndarray, max_iter: int = 100000):
+    """w = M z + q >= 0, z >= 0, z^T w = 0 for positive definite M, by Murty's
+    least-index principal pivoting: complementary basis given by the set of
+    indices with z basic; at each step the least index whose basic variable
+    is negative switches side."""
+    K = q.size
+    basic_z = np.zeros(K, dtype=bool)
+    for _ in range(max_iter):
+        z = np.zeros(K)
+        a = np.nonzero(basic_z)[0]
+        if a.size:
+            z[a] = np.linalg.solve(M[np.ix_(a, a)], -q[a])
+        w = M @ z + q
+        w[a] = 0.0
+        bad = np.nonzero((basic_z & (z < 0)) | (~basic_z & (w < 0)))[0]
+        if bad.size == 0:
+            return z
+        basic_z[bad[0]] = not basic_z[bad[0]]
+    raise RuntimeError("principal pivoting did not terminate")
+
+
+def lcp_kkt(M, q, z) -> float:
+    """Largest violation of z >= 0, w >= 0, z_i w_i = 0 (scaled)."""
+    w = M @ z + q
+    s = max(np.abs(q).max(), 1e-300)
+    return float(max(-z.min(initial=0.0) * np.abs(M).max() / s, -w.min(initial=0.0) / s,
+                     np.abs(z * w).max(initial=0.0) * np.abs(M).max() / s ** 2))
+
+
+def tresca_kkt(W, s, rho, lam) -> float:
+    """KKT violation of min 1/2 lam^T (W (x) I2) lam + s^T lam over disks
+    |lam_c| <= rho_c: with slip u = s + W lam, a contact inside its disk has
+    u_c = 0, a contact on its boundary has u_c = -t lam_c, t >= 0."""
+    u = s + W @ lam
+    sc = max(np.abs(s).max(), 1e-300)
+    viol = 0.0
+    for c in range(lam.shape[0]):
+        r = np.linalg.norm(lam[c])
+        viol = max(viol, (r - rho[c]) / max(rho.max(), 1e-300))
+        if r < rho[c] * (1 - 1e-10) or rho[c] == 0.0:
+            if rho[c] > 0:
+                viol = max(viol, np.linalg.norm(u[c]) / sc)
+        else:
+            # u_c must be a non-positive multiple of lam_c
+            cross = u[c, 0] * lam[c, 1] - u[c, 1] * lam[c, 0]
+            viol = max(viol, abs(cross) / (sc * max(r, 1e-300)), max(0.0, u[c] @ lam[c]) / (sc * max(r, 1e-300)))
+    return float(viol)
+
+
+def tresca(W: np.ndarray, s: np.ndarray, rho: np.ndarray, lam0=None, tol: float = 1e-12):
+    """lam [K,2] minimising 1/2 sum_axes lam^T W lam + s^T lam over the disks
+    |lam_c| <= rho_c: block projected Gauss-Seidel (from lam0), checked
+    against the KKT conditions."""
+    lam0 = np.zeros_like(s) if lam0 is None else np.asarray(lam0, dtype=np.float64)
+    lam = tresca_pgs(W, s, rho, lam0, tol)
+    assert tresca_kkt(W, s, rho, lam) <= 1e-9, "friction QP not solved"
+    return lam
+
+
+def tresca_pgs(W, s, rho, lam0, tol=1e-12, max_sweeps=200000):
+    """Block projected Gauss-Seidel on the disks (exact block minimiser, then
+    projection onto the disk), from lam0."""
+    lam = lam0.copy()
+    K = s.shape[0]
+    for _ in range(max_sweeps):
+        dmax = 0.0
+        for c in range(K):
+            if rho[c] <= 0:
+                lam[c] = 0.0
+                continue
+            r = s[c] + W[c] @ lam
+            new = lam[c] - r / W[c, c]
+            nn = np.linalg.norm(new)
+            if nn > rho[c]:
+                new *= rho[c] / nn
+            dmax = max(dmax, np.abs(new - lam[c]).max())
+            lam[c] = new
+        if dmax <= 1e-15 * max(rho.max(), 1e-300) and tresca_kkt(W, s, rho, lam) <= tol:
+            break
+    return lam
+
+
+class ContactProblem:
+    """Candidate set, its Delassus matrix and the obstacle heights of a scene."""
+
+    def __init__(self, pb: solver.Problem, spec):
+        self.spec = spec
+        self.verts = np.concatenate([spec.ground, spec.box]).astype(np.int64)
+        self.normal = np.concatenate([np.ones(spec.ground.size), -np.ones(spec.box.size)])
+        order = np.argsort(self.verts, kind="stable")
+        self.verts, self.normal = self.verts[order], self.normal[order]
+        self.pos = np.searchsorted(pb.free, self.verts)
+        self.W = delassus(pb, self.verts)
+
+    def heights(self, t: int) -> np.ndarray:
+        return np.where(self.normal > 0, self.spec.ground_z, self.spec.box_z(t))
+
+
+def correct(pb: solver.Problem, cp: ContactProblem, q_u_free, q_t, t: int, lam_f0=None):
+    """Contact-corrected global step: (q_free, lam_n, lam_f) from the plain
+    global step q_u (free DoFs); lam_f0 warm-starts the friction solve."""
+    D = cp.normal
+    g = D * (q_u_free[cp.pos, 2] - cp.heights(t))
+    M = (D[:, None] * cp.W) * D[None, :]
+    lam_n = lcp_murty(M, g)
+    assert lcp_kkt(M, g, lam_n) <= 1e-9, "normal LCP not solved"
+    slip = q_u_free[cp.pos, :2] - q_t[cp.verts, :2]
+    lam_f = tresca(cp.W, slip, cp.spec.mu * lam_n, lam_f0)
+    r = np.zeros((pb.free.size, 3))
+    r[cp.pos, 0] = lam_f[:, 0]
+    r[cp.pos, 1] = lam_f[:, 1]
+    r[cp.pos, 2] = D * lam_n
+    return q_u_free + solver.solve_A(pb, r), lam_n, lam_f
+
+
+def contact_picard(pb, cp, b0, q, q_t, t, lam_f0=None):
+    """One contact-corrected local-global iteration q <- T(q)."""
+    q_u = solver.solve_A(pb, solver.free_rhs(pb, solver.rhs(pb, b0, q)))
+    qf, lam_n, lam_f = correct(pb, cp, q_u, q_t, t, lam_f0)
+    return solver.full(pb, qf), lam_n, lam_f
+
+
+def step(pb, cp, q_t, v_t, f_ext, t, tol=1e-13, max_iter=5000, m=5):
+    """One contact step: the fixed point q* = T(q*) of the contact-corrected
+    local-global map from q_t, reached by type-II Anderson mixing of T
+    (solver.aa_mix; it changes the path, not the fixed point) until
+    ||T(q) - q|| <= tol ||q||. Returns (q_{t+1}, lam_n, lam_f, iterations)."""
+    b0 = solver.rhs_const(pb, q_t, v_t, f_ext)
+    q = q_t.copy()
+    hq, hg = [], []
+    lam_f = None
+    for k in range(1, max_iter + 1):
+        qh, lam_n, lam_f = contact_picard(pb, cp, b0, q, q_t, t, lam_f)
+        g = qh - q
+        if np.linalg.norm(g) <= tol * np.linalg.norm(qh):
+            return qh, lam_n, lam_f, k
+        hq.append(q)
+        hg.append(g)
+        if len(hq) > m + 1:
+            hq.pop(0)
+            hg.pop(0)
+        q, reset = solver.aa_mix(hq, hg, qh, g)
+        if reset:
+            hq, hg = [], []
+    raise RuntimeError("contact step did not converge")
+
+
+def rollout(pb, scene, cp=None):
+    cp = cp or ContactProblem(pb, scene.contact)
+    q, v = scene.x0.copy(), scene.v0.copy()
+    recs = []
+    for t in range(scene.steps):
+        f = scene.f_ext[t if scene.f_ext.shape[0] > 1 else 0]
+        qn, lam_n, lam_f, k = step(pb, cp, q, v, f, t)
+        recs.append({"q_t": q, "v_t": v, "q_next": qn, "lam_n": lam_n, "lam_f": lam_f, "iters": k})
+        v = (qn - q) / pb.h
+        q = qn
+    return q, v, recs, cp

@@ -68,6 +68,8 @@ class Scene:
     solver: SolverSettings = field(default_factory=SolverSettings)
     loss: str = "l2_target"  # "com_z" or "l2_target"
     target: np.ndarray | None = None
+    contact: object = None            # ContactSpec or None
+    loss_vertices: np.ndarray | None = None   # vertices of the L2 loss (None = all)
 
     @property
     def n_v(self) -> int:
@@ -363,3 +365,67 @@ def mlp_init(seed: int = 0, hidden: int = 128) -> np.ndarray:
         parts.append(rng.uniform(-lim, lim, size=fan_out * fan_in))
         parts.append(np.zeros(fan_out))
     return np.concatenate(parts).astype(np.float32)
+
+
+@dataclass
+class ContactSpec:
+    """Frictional contacts of a workload (reading of Sec. 4.6): vertex-ground
+    (z >= ground_z, normal +z) for ``ground`` vertices and vertex-box-bottom
+    (z <= box_z(t), normal -z) for ``box`` vertices; the rigid box moves down
+    by ``box_travel`` over the first ``box_steps`` steps and is then held.
+    Coulomb coefficient ``mu`` (Tresca disks of radius mu * lambda_n)."""
+    ground: np.ndarray          # [Kg] vertex indices
+    box: np.ndarray             # [Kb] vertex indices
+    ground_z: float
+    box_z0: float
+    box_travel: float
+    box_steps: int
+    mu: float
+
+    def box_z(self, t: int) -> float:
+        """Height of the box bottom at the end of step t (0-based)."""
+        return self.box_z0 - self.box_travel * min(t + 1, self.box_steps) / self.box_steps
+
+
+def contact_pad(nx: int = 48, ny: int = 48, nz: int = 12, cell: float = 0.01, footprint: int = 16,
+                steps: int = 300, box_steps: int = 150, travel: float = 0.02, seed: int = 13,
+                E_shell: float = 1e5, E_core: float = 1e7) -> Scene:
+    """Contact-rich soft pad: nx*ny*nz cells of `cell` m with interior vertices
+    jittered by up to 15% of a cell (seeded), a stiff core (E 1e7 Pa, cells at
+    least 2 cells from the outer surface) in a soft shell (1e5 Pa), nu = 0.45,
+    Neo-Hookean, resting on the ground z = 0 under gravity and pressed by a
+    rigid box whose footprint x footprint cells centred on the top face moves
+    down `travel` m over `box_steps` steps and is then held; Coulomb mu = 0.5;
+    no pins; dt = 0.002 s; Anderson m = 5, FP32 local step, gate 1e-6 / 1e-8.
+    Loss: L2 of the top-surface positions at T against X + N(0, (0.1 cell)^2).
+    E_shell / E_core override the moduli (smaller parity cases)."""
+    rng = np.random.default_rng(seed)
+    X, tets, cells = hex_grid(nx, ny, nz, cell)
+    n = np.array([nx, ny, nz])
+    ijk = np.rint(X / cell).astype(np.int64)
+    interior = np.all((ijk > 0) & (ijk < n[None, :]), axis=1)
+    X = X.copy()
+    X[interior] += cell * rng.uniform(-0.15, 0.15, size=(int(interior.sum()), 3))
+    c = cells
+    depth = np.minimum.reduce([c[:, 0], nx - 1 - c[:, 0], c[:, 1], ny - 1 - c[:, 1], c[:, 2], nz - 1 - c[:, 2]])
+    E = np.where(depth >= 2, E_core, E_shell)
+    n_v = X.shape[0]
+    ground = np.nonzero(ijk[:, 2] == 0)[0]
+    lo = (nx - footprint) // 2
+    lo_y = (ny - footprint) // 2
+    top = (ijk[:, 2] == nz) & (ijk[:, 0] >= lo) & (ijk[:, 0] <= lo + footprint) & \
+        (ijk[:, 1] >= lo_y) & (ijk[:, 1] <= lo_y + footprint)
+    box = np.nonzero(top)[0]
+    top_all = np.nonzero(ijk[:, 2] == nz)[0]
+    target = X + 0.1 * cell * rng.standard_normal(X.shape)
+    sc = Scene(
+        name=f"pad{nx}x{ny}x{nz}", X=X, tets=tets, pinned=np.zeros(n_v, dtype=np.uint8), E=E, nu=0.45,
+        density=1000.0, alpha=0.01, beta0=1e-3, gravity=np.array([0.0, 0.0, -9.81]), dt=0.002,
+        model=NEOHOOKEAN, steps=steps, f_ext=np.zeros((1, n_v, 3)), x0=X.copy(), v0=np.zeros((n_v, 3)),
+        solver=SolverSettings(aa_m=5, fixed_iters=0, k_max=400, eps_step=1e-8, eps_res=1e-6, eps_abs=1e-12,
+                              local_fp32=True),
+        loss="l2_target", target=target)
+    sc.contact = ContactSpec(ground=ground, box=box, ground_z=0.0, box_z0=nz * cell, box_travel=travel,
+                             box_steps=box_steps, mu=0.5)
+    sc.loss_vertices = top_all
+    return sc
