@@ -116,9 +116,30 @@ typedef struct {
   double fwd_device_seconds;  /* persistent launches: the last forward's wall time measured on the device
                                  (a batch: the instance's team; pd_get_stats gives the largest) */
   double bwd_device_seconds;  /* ... of the last adjoint */
+  int32_t contact_iters;      /* contact: inner solver passes over W in the last rollout */
+  int32_t contact_unconverged;/* contact: inner solves that hit contact_max_iters */
 } pd_stats;
 
 typedef struct pd_ctx pd_ctx;
+
+/* Frictional contacts (Sec. 4.6; vertex-obstacle, position level), set with
+ * pd_set_contacts before pd_factor. Ground vertices stay at z >= ground_z
+ * (normal +z); box vertices stay at z <= z_box(t) (normal -z), the bottom of
+ * a rigid box that moves down by box_travel over the first box_steps steps
+ * of a rollout, z_box(t) = box_z0 - box_travel min(t + 1, box_steps) /
+ * box_steps at the end of step t. Coulomb friction with coefficient mu, as
+ * Tresca disks of radius mu lambda_n on the tangential displacement since
+ * q_t. Candidates must be free vertices; every index appears once. */
+typedef struct {
+  int32_t n_ground, n_box;
+  const int32_t* ground;  /* [n_ground] vertex indices (host, copied) */
+  const int32_t* box;     /* [n_box] */
+  double ground_z, box_z0, box_travel;
+  int32_t box_steps;
+  double mu;
+  double tol;             /* relative tolerance of the inner solves (0: 1e-12) */
+  int32_t max_iters;      /* cap on inner passes per solve (0: 2000) */
+} pd_contact_desc;
 
 /* Default options (m = 5, k_max = 200, gate 1e-8 / 1e-6 / 1e-12, FP32 local,
  * adaptive trust region with eps_tr = 0.1, backward 1e-9 / 1000 iterations,
@@ -134,6 +155,18 @@ void pd_default_options(pd_options* out);
  * error; release it with pd_destroy. */
 int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_options* opt,
               pd_ctx** out);
+
+/* Frictional contacts of a single-instance context (NULL or n_ground +
+ * n_box = 0 removes them). pd_factor then also forms the dense scalar
+ * Delassus matrix W = (L_A^-1)_CC of the K candidates (K host solves with the
+ * factor, FP64; K^2 x 8 bytes on the device). Each local-global iteration of
+ * a rollout computes q_u = A^-1 b(q) at the candidates, solves the normal
+ * LCP 0 <= lam_n _|_ D W D lam_n + g >= 0 and the Tresca QP of the friction
+ * on W (FISTA with adaptive restart), and takes q = A^-1 (b + J^T lam)
+ * (eq. q_update) through the same two products with S. Persistent launches
+ * only; the adjoint of a contact rollout is not built (pd_backward returns
+ * PD_ERR_ARG). */
+int pd_set_contacts(pd_ctx* ctx, const pd_contact_desc* desc);
 
 /* Replace the Young's moduli ([n_e], host, Pa) and Poisson ratio; marks A stale
  * so that the next pd_factor refactors (Sec. 4.5 refactorisation policy). */

@@ -49,7 +49,14 @@ class pd_stats(ctypes.Structure):
                 ("status_flags", c_int32), ("n_free", c_int32), ("factor_nnz", c_int64),
                 ("factor_seconds", c_double), ("last_rho", c_double), ("launches", c_int64),
                 ("escalations", c_int32), ("warm_fallbacks", c_int32),
-                ("fwd_device_seconds", c_double), ("bwd_device_seconds", c_double)]
+                ("fwd_device_seconds", c_double), ("bwd_device_seconds", c_double),
+                ("contact_iters", c_int32), ("contact_unconverged", c_int32)]
+
+
+class pd_contact_desc(ctypes.Structure):
+    _fields_ = [("n_ground", c_int32), ("n_box", c_int32), ("ground", c_void_p), ("box", c_void_p),
+                ("ground_z", c_double), ("box_z0", c_double), ("box_travel", c_double), ("box_steps", c_int32),
+                ("mu", c_double), ("tol", c_double), ("max_iters", c_int32)]
 
 
 class pd_profile_out(ctypes.Structure):
@@ -120,6 +127,7 @@ def lib():
             "pd_mlp_sample": (c_int, [P, P, P, P, P, P, P]),
             "pd_mlp_load": (c_int, [P, P, ctypes.c_size_t]),
             "pd_warm_start": (c_int, [P, P, P, P, P]),
+            "pd_set_contacts": (c_int, [P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -440,6 +448,19 @@ def pd_warm_start(ctx, x_t, x_tm1, q0, stream=None):
     _check(ctx, lib().pd_warm_start(ctx, _ptr(x_t), _ptr(x_tm1), _ptr(q0), _stream(stream)))
 
 
+def pd_set_contacts(ctx, spec, tol=0.0, max_iters=0):
+    """Contacts of a workload (``inputs.ContactSpec``), or None to remove them."""
+    if spec is None:
+        _check(ctx, lib().pd_set_contacts(ctx, None))
+        return
+    g = np.ascontiguousarray(spec.ground, dtype=np.int32)
+    b = np.ascontiguousarray(spec.box, dtype=np.int32)
+    desc = pd_contact_desc(int(g.size), int(b.size), _ptr(g, np.int32) if g.size else None,
+                           _ptr(b, np.int32) if b.size else None, float(spec.ground_z), float(spec.box_z0),
+                           float(spec.box_travel), int(spec.box_steps), float(spec.mu), float(tol), int(max_iters))
+    _check(ctx, lib().pd_set_contacts(ctx, ctypes.byref(desc)))
+
+
 def pd_last_error(ctx) -> str:
     return lib().pd_last_error(ctx).decode()
 
@@ -480,6 +501,8 @@ class PDContext:
         self.ctx = pd_create(scene.X, scene.tets, scene.pinned, scene.E, model, scene.nu, scene.density,
                              scene.alpha, scene.beta0, scene.gravity, scene.dt, self.options)
         self.n_v, self.n_e = scene.n_v, scene.n_e
+        if getattr(scene, "contact", None) is not None:
+            pd_set_contacts(self.ctx, scene.contact)
         if factor:
             pd_factor(self.ctx)
 

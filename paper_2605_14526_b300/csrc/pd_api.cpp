@@ -267,6 +267,44 @@ int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_o
   return PD_OK;
 }
 
+int pd_set_contacts(pd_ctx* c, const pd_contact_desc* desc) {
+  if (!c) return PD_ERR_ARG;
+  if (c->batch) return fail(c, PD_ERR_ARG, "pd_set_contacts is single-instance only");
+  c->con_ground.clear();
+  c->con_box.clear();
+  c->con = pd_contact_desc{};
+  c->factored = false;
+  if (!desc || desc->n_ground + desc->n_box == 0) return PD_OK;
+  if (desc->n_ground < 0 || desc->n_box < 0 || (desc->n_ground && !desc->ground) || (desc->n_box && !desc->box))
+    return fail(c, PD_ERR_ARG, "contact candidate arrays");
+  if (desc->n_box > 0 && desc->box_steps < 1) return fail(c, PD_ERR_ARG, "box_steps must be >= 1");
+  if (!(desc->mu >= 0)) return fail(c, PD_ERR_ARG, "mu must be >= 0");
+  std::vector<char> seen(c->n_v, 0);
+  auto take = [&](const int32_t* p, int n, std::vector<int>& out) -> int {
+    for (int i = 0; i < n; ++i) {
+      const int v = p[i];
+      if (v < 0 || v >= c->n_v) return fail(c, PD_ERR_ARG, "contact vertex %d out of range", v);
+      if (c->pinned[v]) return fail(c, PD_ERR_ARG, "contact vertex %d is pinned", v);
+      if (seen[v]) return fail(c, PD_ERR_ARG, "contact vertex %d listed twice", v);
+      seen[v] = 1;
+      out.push_back(v);
+    }
+    return PD_OK;
+  };
+  int r;
+  if ((r = take(desc->ground, desc->n_ground, c->con_ground)) || (r = take(desc->box, desc->n_box, c->con_box))) {
+    c->con_ground.clear();
+    c->con_box.clear();
+    return r;
+  }
+  c->con = *desc;
+  c->con.ground = nullptr;
+  c->con.box = nullptr;
+  if (!(c->con.tol > 0)) c->con.tol = 1e-12;
+  if (c->con.max_iters <= 0) c->con.max_iters = 2000;
+  return PD_OK;
+}
+
 int pd_set_materials(pd_ctx* c, const double* E, double nu) {
   if (!c || !E) return PD_ERR_ARG;
   if (c->batch) return fail(c, PD_ERR_ARG, "a batch context takes pd_set_materials_batch");
@@ -438,6 +476,76 @@ int pd_factor(pd_ctx* c) {
   d.eps_tr = c->opt.eps_tr; d.adj_tol = c->opt.adj_tol;
   for (int i = 0; i < 3; ++i) d.g[i] = c->g[i];
   d.mu_bar = mu_bar; d.lam_bar = lam_bar; d.k_bar = k_bar; d.mu_ref = mu_ref; d.beta0 = c->beta0; d.nu = c->nu;
+  // contacts: candidates in elimination order, W = (L_A^-1)_CC by host solves
+  d.n_con = 0;
+  if (!c->con_ground.empty() || !c->con_box.empty()) {
+    std::vector<std::pair<int, int>> cand;  // (position, index into ground+box)
+    std::vector<int> all(c->con_ground);
+    all.insert(all.end(), c->con_box.begin(), c->con_box.end());
+    for (size_t i = 0; i < all.size(); ++i) cand.push_back({iperm_v[all[i]], (int)i});
+    std::sort(cand.begin(), cand.end());
+    const int K = (int)cand.size();
+    std::vector<int> cv(K), cp(K), cf(K);
+    std::vector<double> cn(K), W((size_t)K * K);
+    for (int k = 0; k < K; ++k) {
+      cv[k] = all[cand[k].second];
+      cp[k] = cand[k].first;
+      cn[k] = cand[k].second < (int)c->con_ground.size() ? 1.0 : -1.0;
+      cf[k] = v2f[cv[k]];
+    }
+#pragma omp parallel
+    {
+      std::vector<double> e(nf, 0.0), x(nf);
+#pragma omp for schedule(dynamic, 4)
+      for (int j = 0; j < K; ++j) {
+        e[cf[j]] = 1.0;
+        pdf::solve_host(c->fac, e.data(), x.data());
+        e[cf[j]] = 0.0;
+        for (int i = 0; i < K; ++i) W[(size_t)i * K + j] = x[cf[i]];
+      }
+    }
+    for (int i = 0; i < K; ++i)   // symmetric part (W is symmetric up to rounding)
+      for (int j = i + 1; j < K; ++j) {
+        const double a = 0.5 * (W[(size_t)i * K + j] + W[(size_t)j * K + i]);
+        W[(size_t)i * K + j] = W[(size_t)j * K + i] = a;
+      }
+    // largest eigenvalue by power iteration (the FISTA step is 1 / lambda_max)
+    std::vector<double> u(K, 1.0), w(K);
+    double lmax = 0.0;
+    for (int it = 0; it < 300; ++it) {
+      double nn = 0.0;
+      for (int i = 0; i < K; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < K; ++j) s += W[(size_t)i * K + j] * u[j];
+        w[i] = s;
+        nn += s * s;
+      }
+      nn = std::sqrt(nn);
+      double un = 0.0;
+      for (int i = 0; i < K; ++i) un += u[i] * u[i];
+      lmax = nn / std::sqrt(un);
+      for (int i = 0; i < K; ++i) u[i] = w[i] / nn;
+    }
+    int *cv_d, *cp_d;
+    double *cn_d, *W_d, *buf_d;
+    if ((r = upload(c, &cv_d, cv, true)) || (r = upload(c, &cp_d, cp, true)) || (r = upload(c, &cn_d, cn, true)) ||
+        (r = upload(c, &W_d, W, true)) || (r = dalloc(c, &buf_d, 12 * (size_t)K, true)))
+      return r;
+    d.n_con = K;
+    d.con_v = cv_d;
+    d.con_pos = cp_d;
+    d.con_n = cn_d;
+    d.con_W = W_d;
+    d.con_buf = buf_d;
+    d.con_L = 1.001 * lmax;   // a little above lambda_max: the step stays below 1 / L
+    d.con_mu = c->con.mu;
+    d.con_zg = c->con.ground_z;
+    d.con_zb0 = c->con.box_z0;
+    d.con_travel = c->con.box_travel;
+    d.con_steps = c->con.box_steps > 0 ? c->con.box_steps : 1;
+    d.con_tol = c->con.tol;
+    d.con_max_iters = c->con.max_iters;
+  }
   c->factored = true;
   c->factor_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   c->stats.factor_seconds = c->factor_seconds;
@@ -544,6 +652,7 @@ int enqueue_fwd_single(pd_ctx* c, int T, const double* q0d, const double* v0d, c
   CK(cudaMemsetAsync(c->tau, 0, (size_t)T * sizeof(double), s));
   CK(cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), s));  // per-rollout statistics and flags
   CK(cudaMemsetAsync(d.sstar, 0, 3 * sizeof(double) * (size_t)c->n_e, s));  // no prox warm start across rollouts
+  if (d.n_con > 0) CK(cudaMemsetAsync(d.con_buf, 0, 12 * sizeof(double) * (size_t)d.n_con, s));
   pdk::BatchFwd br;
   br.T = T;
   br.q0 = q0d;
@@ -597,6 +706,8 @@ int stats_from_ctrl(pd_ctx* c, const Ctrl& hc, int which) {
     st.escalations = hc.escalations;
     st.warm_fallbacks = hc.fallbacks;
     st.fwd_device_seconds = hc.elapsed_ns[0] * 1e-9;
+    st.contact_iters = hc.con_iters;
+    st.contact_unconverged = hc.con_unconverged;
   }
   if (which & 2) {
     st.adj_iters_total = hc.adj_iters_total;
@@ -647,6 +758,7 @@ int pd_rollout(pd_ctx* c, int32_t T, const double* q0, const double* v0, const d
   if (T < 1 || !q0 || !v0) return fail(c, PD_ERR_ARG, "T >= 1 and q0, v0 are required");
   if (c->opt.warm_start < 0 || c->opt.warm_start > 2) return fail(c, PD_ERR_ARG, "warm_start must be 0, 1 or 2");
   if (c->opt.warm_start && !c->opt.persistent) return fail(c, PD_ERR_ARG, "the warm start needs persistent launches");
+  if (!c->batch && c->d.n_con > 0 && !c->opt.persistent) return fail(c, PD_ERR_ARG, "contact needs persistent launches");
   if (c->opt.warm_start == 1 && !(c->batch ? batch_has_mlp(c) : c->d.mlp.w != nullptr))
     return fail(c, PD_ERR_ARG, "warm_start = 1 needs a network (pd_mlp_load)");
   CK(cudaSetDevice(c->device));
@@ -768,6 +880,7 @@ int pd_backward(pd_ctx* c, const double* dqT, const double* dvT, double* dq0, do
   if (!c->factored) return fail(c, PD_ERR_NOT_FACTORED, "pd_factor must run before pd_backward");
   if (c->last_T < 1) return fail(c, PD_ERR_NO_CHECKPOINT, "no recorded rollout");
   if (!dqT) return fail(c, PD_ERR_ARG, "dqT is required");
+  if (!c->batch && c->d.n_con > 0) return fail(c, PD_ERR_ARG, "the adjoint of a contact rollout is not built");
   CK(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
   if (c->batch) return batch_backward(c, dqT, dvT, dq0, dv0, dE, dnu, df_ext, df_stride, s, true);
@@ -845,6 +958,7 @@ int pd_backward_enqueue(pd_ctx* c, const double* dqT, const double* dvT, double*
   if (!c->factored) return fail(c, PD_ERR_NOT_FACTORED, "pd_factor must run before pd_backward_enqueue");
   if (c->last_T < 1) return fail(c, PD_ERR_NO_CHECKPOINT, "no recorded or enqueued rollout");
   if (!dqT) return fail(c, PD_ERR_ARG, "dqT is required");
+  if (!c->batch && c->d.n_con > 0) return fail(c, PD_ERR_ARG, "the adjoint of a contact rollout is not built");
   CK(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
   if (c->batch) return batch_backward(c, dqT, dvT, dq0, dv0, dE, dnu, df_ext, df_stride, s, false);

@@ -1,0 +1,187 @@
+// Frictional contact inside the local-global iteration (Sec. 4.6, eq. fb_n,
+// eq. contact_system, eq. q_update), with the factor of A kept fixed.
+//
+// Contacts are vertex-ground (z >= z_g, normal +z) and vertex-box-bottom
+// (z <= z_box(t), normal -z); A = L_A (x) I_3 and the normals are +-z, so the
+// normal and the tangential subproblems decouple by axis and share the scalar
+// Delassus matrix W = (L_A^-1)_CC of the candidates C. Per iteration:
+//   q_u,C  = rows C of S^T (S b)                    (the plain global step at C)
+//   normal 0 <= lam_n _|_ D W D lam_n + g >= 0,   g_c = n_c (q_u,z - z_c)
+//   Tresca lam_f = argmin 1/2 sum_axes lam^T W lam + s^T lam over |lam_f,c| <= mu lam_n,c,
+//          s_c = q_u,xy - q_t,xy
+//   y     <- S b + S J^T lam;  q = S^T y = A^-1 (b + J^T lam)
+// Both subproblems are strictly convex QPs; each is solved by FISTA (Beck &
+// Teboulle 2009) with gradient-based adaptive restart (O'Donoghue & Candes
+// 2015), step 1 / lambda_max(W), warm-started from the previous iteration's
+// multipliers, one team-parallel row pass over W per inner iteration. The
+// paper solves the linearised FB system by dense LDL^T each inner iteration;
+// on this part's FP64 rate that costs K^3/3 per refactorisation, while the
+// FISTA pass costs K^2.
+#pragma once
+#include "pd_phases.cuh"
+
+namespace pdk {
+
+__device__ __forceinline__ double con_height(const Dev& d, int c, int t) {
+  if (d.con_n[c] > 0.0) return d.con_zg;
+  const int k = min(t + 1, d.con_steps);
+  return d.con_zb0 - d.con_travel * (double)k / (double)d.con_steps;
+}
+
+// work buffer layout: lam_n [3][K] (rotating prev / cur / next), lam_f [3][K][2],
+// gap [K], slip [K][2]
+__device__ __forceinline__ double* con_lamn(const Dev& d, int r) { return d.con_buf + (size_t)(r % 3) * d.n_con; }
+__device__ __forceinline__ double* con_lamf(const Dev& d, int r) {
+  return d.con_buf + 3 * (size_t)d.n_con + (size_t)(r % 3) * 2 * d.n_con;
+}
+__device__ __forceinline__ double* con_gap(const Dev& d) { return d.con_buf + 9 * (size_t)d.n_con; }
+__device__ __forceinline__ double* con_slip(const Dev& d) { return d.con_buf + 10 * (size_t)d.n_con; }
+
+// warp per candidate: q_u at the candidate (row pos_c of S^T y), its gap and
+// its slip since q_t
+__device__ __forceinline__ void contact_gather(const Dev& d, int c, int t, int lane) {
+  double a0, a1, a2;
+  spmv_st_sum(d, d.y, d.con_pos[c], lane, a0, a1, a2);
+  if (lane == 0) {
+    const int v = d.con_v[c];
+    con_gap(d)[c] = d.con_n[c] * (a2 - con_height(d, c, t));
+    con_slip(d)[2 * c] = a0 - d.qt[3 * (size_t)v];
+    con_slip(d)[2 * c + 1] = a1 - d.qt[3 * (size_t)v + 1];
+  }
+}
+
+// FISTA state (one instance per subproblem, in the team's shared state)
+template <class St>
+__device__ __forceinline__ void fista_reset(St* S) {
+  S->f_t = 1.0;
+  S->f_beta = 0.0;   // the first pass starts from the warm multipliers (no momentum)
+  S->f_it = 0;
+  S->f_done = 0;
+}
+
+// after a pass: sums = {||next - cur||^2, ||next||^2, restart indicator};
+// rot is the rotation index of the subproblem's multipliers
+template <class St>
+__device__ __forceinline__ void fista_finish(const Dev& d, St* S, int* rot, const double* sums) {
+  *rot += 1;         // next becomes cur
+  S->f_it += 1;
+  S->con_iters += 1;
+  const bool conv = sums[0] <= d.con_tol * d.con_tol * sums[1] + 1e-300;
+  if (conv) {
+    S->f_done = 1;
+  } else if (S->f_it >= d.con_max_iters) {
+    S->f_done = 1;
+    S->con_unconverged += 1;
+  } else if (sums[2] > 0.0) {   // the step went against the momentum: restart
+    S->f_t = 1.0;
+    S->f_beta = 0.0;
+  } else {
+    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * S->f_t * S->f_t));
+    S->f_beta = (S->f_t - 1.0) / tn;
+    S->f_t = tn;
+  }
+}
+
+// normal LCP pass, warp per row c: z = cur + beta (cur - prev) on the fly;
+// next_c = max(0, z_c - ((D W D z)_c + g_c) / L)
+__device__ __forceinline__ void normal_row(const Dev& d, int c, int rot, double beta, int lane, double* part) {
+  const int K = d.n_con;
+  const double* prev = con_lamn(d, rot);
+  const double* cur = con_lamn(d, rot + 1);
+  double* nxt = con_lamn(d, rot + 2);
+  const double* Wr = d.con_W + (size_t)c * K;
+  double acc = 0.0;
+  for (int j = lane; j < K; j += 32) {
+    const double z = cur[j] + beta * (cur[j] - prev[j]);
+    acc += Wr[j] * d.con_n[j] * z;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    const double zc = cur[c] + beta * (cur[c] - prev[c]);
+    const double grad = d.con_n[c] * acc + con_gap(d)[c];
+    const double nv = fmax(0.0, zc - grad / d.con_L);
+    nxt[c] = nv;
+    const double dl = nv - cur[c];
+    part[0] += dl * dl;
+    part[1] += nv * nv;
+    part[2] += (zc - nv) * dl;
+  }
+}
+
+// Tresca pass, warp per row c: two components, disk radius mu * lam_n,c
+__device__ __forceinline__ void friction_row(const Dev& d, int c, int rot, double beta, const double* lam_n, int lane,
+                                             double* part) {
+  const int K = d.n_con;
+  const double* prev = con_lamf(d, rot);
+  const double* cur = con_lamf(d, rot + 1);
+  double* nxt = con_lamf(d, rot + 2);
+  const double* Wr = d.con_W + (size_t)c * K;
+  double ax = 0.0, ay = 0.0;
+  for (int j = lane; j < K; j += 32) {
+    const double w = Wr[j];
+    ax += w * (cur[2 * j] + beta * (cur[2 * j] - prev[2 * j]));
+    ay += w * (cur[2 * j + 1] + beta * (cur[2 * j + 1] - prev[2 * j + 1]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ax += __shfl_xor_sync(0xffffffffu, ax, o);
+    ay += __shfl_xor_sync(0xffffffffu, ay, o);
+  }
+  if (lane == 0) {
+    const double zx = cur[2 * c] + beta * (cur[2 * c] - prev[2 * c]);
+    const double zy = cur[2 * c + 1] + beta * (cur[2 * c + 1] - prev[2 * c + 1]);
+    double nx = zx - (ax + con_slip(d)[2 * c]) / d.con_L;
+    double ny = zy - (ay + con_slip(d)[2 * c + 1]) / d.con_L;
+    const double rho = d.con_mu * lam_n[c];
+    const double r = sqrt(nx * nx + ny * ny);
+    if (r > rho) {
+      const double s = r > 0.0 ? rho / r : 0.0;
+      nx *= s;
+      ny *= s;
+    }
+    nxt[2 * c] = nx;
+    nxt[2 * c + 1] = ny;
+    const double dx = nx - cur[2 * c], dy = ny - cur[2 * c + 1];
+    part[0] += dx * dx + dy * dy;
+    part[1] += nx * nx + ny * ny;
+    part[2] += (zx - nx) * dx + (zy - ny) * dy;
+  }
+}
+
+// y_i += sum over candidates c with pos_c in [first_desc(i), i] of
+// S[i, pos_c] (lam_f,c, n_c lam_n,c): the contact impulse J^T lam pushed
+// through the first product with S (warp per row i; candidates sorted by
+// position, found by binary search)
+__device__ __forceinline__ void contact_y_row(const Dev& d, int i, const double* lam_n, const double* lam_f, int lane) {
+  const int lo = d.s_first[i];
+  int a = 0, b = d.n_con;   // first candidate with pos >= lo
+  while (a < b) {
+    const int m = (a + b) >> 1;
+    if (d.con_pos[m] < lo) a = m + 1;
+    else b = m;
+  }
+  const double* srow = d.s_val + d.s_rowptr[i];
+  double r0 = 0.0, r1 = 0.0, r2 = 0.0;
+  for (int c = a + lane; c < d.n_con; c += 32) {
+    const int p = d.con_pos[c];
+    if (p > i) break;
+    const double s = srow[p - lo];
+    r0 += s * lam_f[2 * c];
+    r1 += s * lam_f[2 * c + 1];
+    r2 += s * d.con_n[c] * lam_n[c];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    r0 += __shfl_xor_sync(0xffffffffu, r0, o);
+    r1 += __shfl_xor_sync(0xffffffffu, r1, o);
+    r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+  }
+  if (lane == 0) {
+    d.y[3 * (size_t)i] += r0;
+    d.y[3 * (size_t)i + 1] += r1;
+    d.y[3 * (size_t)i + 2] += r2;
+  }
+}
+
+}  // namespace pdk

@@ -80,6 +80,9 @@ struct pd_ctx {
   int team_grid[2] = {0, 0};
   Dev d_uploaded{};
   bool d_valid = false;
+  // frictional contacts (pd_set_contacts)
+  std::vector<int> con_ground, con_box;
+  pd_contact_desc con{};
 };
 
 // batched instances (pd_batch.cpp)

@@ -51,6 +51,7 @@ struct Ctrl {
   unsigned long long phase_ns[8];  // persistent kernels: time per phase (globaltimer, block 0)
   unsigned long long work_ns[8];   // ... of which block 0's own work before the phase's barrier
   unsigned long long elapsed_ns[2]; // persistent launches: wall time of the forward / adjoint (team block 0)
+  int con_iters, con_unconverged;   // contact: inner (FISTA) iterations, inner solves that hit their cap
 };
 
 // phases timed inside the persistent rollout
@@ -137,6 +138,18 @@ struct Dev {
   void* sstar;      // [n_e][3] float: last prox stretches (Newton warm start; <= 0 = none)
   double* red;      // [blocks][kRed]
   Ctrl* ctrl;
+
+  // frictional contacts (vertex-ground, vertex-box; Sec. 4.6): candidates
+  // sorted by elimination position, dense scalar Delassus W = (L_A^-1)_CC
+  int n_con;               // 0: no contact
+  const int* con_v;        // [K] vertex
+  const int* con_pos;      // [K] elimination position (ascending)
+  const double* con_n;     // [K] normal sign: +1 ground (z >= z_g), -1 box (z <= z_box(t))
+  const double* con_W;     // [K][K]
+  double con_L;            // largest eigenvalue of W (FISTA step 1/L)
+  double con_mu, con_zg, con_zb0, con_travel, con_tol;
+  int con_steps, con_max_iters;
+  double* con_buf;         // work: lam_n [3][K], lam_f [3][2K], gap [K], slip [2K]
 
   // rollout storage
   double* sq;       // [n_v][3] state carried between steps of a rollout

@@ -16,6 +16,7 @@
 #include "pd_coop.h"
 #include "pd_grid.cuh"
 #include "pd_mlp.cuh"
+#include "pd_contact.cuh"
 #include "pd_launch.h"
 #include "pd_phases.cuh"
 
@@ -74,6 +75,7 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
   if (tid == 0) {
     S.iters_total = S.iters_max = S.resets = S.not_converged = S.tau_half = S.tau_one = S.status = 0;
     S.hi = S.escalations = S.fallbacks = 0;
+    S.rot_n = S.rot_f = S.con_iters = S.con_unconverged = 0;
     S.last_rho = 0.0;
     for (int i = 0; i < kMaxAA * kMaxAA; ++i) S.gram[i] = 0.0;
     t0 = gtimer();
@@ -116,6 +118,40 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
         work_done(PH_SPMV_S);
         if (!(ok = grid_sync(d, tm))) break;
         mark(PH_SPMV_S);
+        if (d.n_con > 0) {
+          // contact: q_u at the candidates, normal LCP, Tresca friction, then
+          // y <- y + S J^T lam so that the S^T pass below gives A^-1 (b + J^T lam)
+          for (int c = gwarp; c < d.n_con; c += nwarps) contact_gather(d, c, t, lane);
+          if (!(ok = grid_sync(d, tm))) break;
+          if (tid == 0) fista_reset(&S);
+          __syncthreads();
+          while (!S.f_done) {
+            const int rot = S.rot_n;
+            const double beta = S.f_beta;
+            double pc[3] = {0.0, 0.0, 0.0};
+            for (int c = gwarp; c < d.n_con; c += nwarps) normal_row(d, c, rot, beta, lane, pc);
+            if (!(ok = grid_reduce<3>(d, tm, pc, sums))) break;
+            if (tid == 0) fista_finish(d, &S, &S.rot_n, sums);
+            __syncthreads();
+          }
+          if (!ok) break;
+          const double* lam_n = con_lamn(d, S.rot_n + 1);
+          if (tid == 0) fista_reset(&S);
+          __syncthreads();
+          while (!S.f_done) {
+            const int rot = S.rot_f;
+            const double beta = S.f_beta;
+            double pc[3] = {0.0, 0.0, 0.0};
+            for (int c = gwarp; c < d.n_con; c += nwarps) friction_row(d, c, rot, beta, lam_n, lane, pc);
+            if (!(ok = grid_reduce<3>(d, tm, pc, sums))) break;
+            if (tid == 0) fista_finish(d, &S, &S.rot_f, sums);
+            __syncthreads();
+          }
+          if (!ok) break;
+          const double* lam_f = con_lamf(d, S.rot_f + 1);
+          for (int i = gwarp; i < d.n_f; i += nwarps) contact_y_row(d, i, lam_n, lam_f, lane);
+          if (!(ok = grid_sync(d, tm))) break;
+        }
         // S^T y row by row, with the Anderson work of that row's vertex fused in
         const AAView av = aa_view(d, S.pairs, S.ncols, S.head);
         double pa[2 * kMaxAA];
@@ -196,6 +232,8 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
     c->k = S.k;
     c->escalations = S.escalations;
     c->fallbacks = S.fallbacks;
+    c->con_iters = S.con_iters;
+    c->con_unconverged = S.con_unconverged;
     atomicOr(&c->status, S.status);
     for (int i = 0; i < 8; ++i) {
       c->phase_ns[i] += ph[i];

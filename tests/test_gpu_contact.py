@@ -1,0 +1,65 @@
+"""GPU tests of frictional contact (vertex-ground and vertex-box contacts,
+normal LCP + Tresca friction on the Delassus matrix, eq. q_update) against
+the contact oracle."""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import DEV, rel
+from oracle import contact, solver
+from paper_2605_14526_b300 import binding, inputs
+from paper_2605_14526_b300.build import build
+
+pytestmark = pytest.mark.gpu
+
+
+def _pad(steps=2):
+    return inputs.contact_pad(nx=8, ny=8, nz=5, footprint=4, steps=steps, box_steps=6, travel=0.004, E_core=1e6)
+
+
+@pytest.fixture(scope="module")
+def oracle_pad():
+    sc = _pad()
+    pb = solver.build_problem(sc)
+    qT, vT, recs, cp = contact.rollout(pb, sc)
+    return sc, qT, recs, cp
+
+
+def _gpu(sc, **solver_kw):
+    build()
+    sc = sc.replace(solver=dataclasses.replace(sc.solver, **solver_kw)) if solver_kw else sc
+    pd = binding.PDContext(sc)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+    x0, v0 = t(sc.x0), t(sc.v0)
+    qT, vT = torch.empty_like(x0), torch.empty_like(x0)
+    code = binding.pd_rollout(pd.ctx, sc.steps, x0, v0, None, 0, qT, vT, check=False)
+    return code, qT.cpu().numpy(), binding.pd_get_stats(pd.ctx), pd
+
+
+def test_contact_rollout_fp64_matches_oracle(oracle_pad):
+    sc, qT, recs, cp = oracle_pad
+    code, q, st, _ = _gpu(sc, local_fp32=False, eps_res=1e-10, eps_step=1e-12, k_max=3000)
+    assert binding.STATUS[code] == "PD_OK", st.not_converged
+    assert st.contact_unconverged == 0
+    assert rel(q, qT) <= 1e-7, rel(q, qT)
+
+
+def test_contact_rollout_fp32_configured_gate_matches_oracle(oracle_pad):
+    sc, qT, recs, cp = oracle_pad
+    code, q, st, _ = _gpu(sc, k_max=3000)
+    assert binding.STATUS[code] == "PD_OK"
+    assert rel(q, qT) <= 1e-5, rel(q, qT)
+    # no candidate penetrates its obstacle beyond the gate's resolution
+    gap = cp.normal * (q[cp.verts, 2] - cp.heights(sc.steps - 1))
+    assert gap.min() >= -1e-6 * np.abs(q[:, 2]).max()
+
+
+def test_contact_adjoint_is_refused():
+    sc = _pad(steps=1)
+    code, q, st, pd = _gpu(sc)
+    x = torch.zeros((sc.n_v, 3), dtype=torch.float64, device=DEV)
+    code = binding.pd_backward(pd.ctx, x, None, torch.empty_like(x), torch.empty_like(x), None, None, None, 0,
+                               check=False)
+    assert binding.STATUS[code] == "PD_ERR_ARG"
