@@ -118,6 +118,13 @@ def backward_step(pb: Problem, q_t, q_star, tau: float, qbar_next, vbar_next) ->
     mu_f = adjoint_solve(pb, q_star, tau, qbar[pb.free])
     mu = np.zeros_like(q_star)
     mu[pb.free] = mu_f
+    return route_step(pb, q_t, q_star, tau, mu, vbar_next)
+
+
+def route_step(pb: Problem, q_t, q_star, tau: float, mu, vbar_next) -> StepGrad:
+    """Gradient routing of one step (eq. dl_dq, eq. dl_dv_dfext, eq. dl_dwe with
+    the readings of the module docstring) for a given adjoint vector mu."""
+    h = pb.h
     m = pb.rest.mass[:, None]
     dq_t = (1.0 + pb.alpha * h) * m / h ** 2 * mu + (pb.B @ mu) / h - vbar_next / h
     dv_t = m / h * mu

@@ -203,3 +203,85 @@ def rollout(pb, scene, cp=None):
         v = (qn - q) / pb.h
         q = qn
     return q, v, recs, cp
+
+
+# ---------------------------------------------------------------- adjoint
+
+def active_sets(cp: ContactProblem, lam_n, lam_f, stick_tol: float = 1e-9):
+    """Normal-active contacts (lam_n > 0) and sticking ones among them
+    (friction strictly inside its disk)."""
+    act = lam_n > 0.0
+    stick = act & (np.linalg.norm(lam_f, axis=1) < cp.spec.mu * lam_n * (1.0 - stick_tol))
+    return act, stick
+
+
+def constraint_rows(pb, cp: ContactProblem, act, stick):
+    """G on the free DoFs (rows: z of normal-active candidates with sign n_c,
+    then x and y of sticking ones) and the (candidate, axis) of each row."""
+    import scipy.sparse as sp
+    rows, cols, vals, tags = [], [], [], []
+    for c in np.nonzero(act)[0]:
+        rows.append(len(tags)); cols.append(3 * cp.pos[c] + 2); vals.append(cp.normal[c]); tags.append((c, 2))
+    for c in np.nonzero(stick)[0]:
+        for ax in (0, 1):
+            rows.append(len(tags)); cols.append(3 * cp.pos[c] + ax); vals.append(1.0); tags.append((c, ax))
+    G = sp.csr_matrix((vals, (rows, cols)), shape=(len(tags), 3 * pb.free.size))
+    return G, tags
+
+
+def backward_step(pb, cp: ContactProblem, rec, tau: float, qbar_next, vbar_next):
+    """Adjoint of one contact step with the active sets of the converged step
+    held fixed (reading): active normal contacts and sticking friction are
+    equality constraints G q = h (h: obstacle heights; q_t,xy for sticking
+    contacts), a sliding contact's friction force is held at its converged
+    value. With R = A q - b(q) - G^T lam_eq - f_slide = 0 and G q = h:
+      (A - K) a + G^T nu = q_bar,  G a = 0,
+      dL/dtheta = a^T db/dtheta + nu^T dh/dtheta,
+    so the routing of the plain step applies with a, and dL/dq_t gains
+    J_S^T nu_S from the sticking rows. Direct sparse LU of the KKT matrix."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    from . import adjoint
+    h = pb.h
+    qbar = qbar_next + vbar_next / h
+    q_star, q_t = rec["q_next"], rec["q_t"]
+    act, stick = active_sets(cp, rec["lam_n"], rec["lam_f"])
+    G, tags = constraint_rows(pb, cp, act, stick)
+    K = adjoint.assemble_K(pb, q_star, tau)
+    f3 = (3 * pb.free[:, None] + np.arange(3)[None, :]).ravel()
+    M = sp.kron(pb.LA_ff, sp.identity(3), format="csr") - K[f3][:, f3]
+    nc = G.shape[0]
+    KKT = sp.bmat([[M.T, G.T], [G, None]], format="csc")
+    rhs = np.concatenate([qbar[pb.free].ravel(), np.zeros(nc)])
+    sol = spla.spsolve(KKT, rhs)
+    a = np.zeros_like(q_star)
+    a[pb.free] = sol[:3 * pb.free.size].reshape(-1, 3)
+    nu = sol[3 * pb.free.size:]
+    g = adjoint.route_step(pb, q_t, q_star, tau, a, vbar_next)
+    for (c, ax), val in zip(tags, nu):
+        if ax < 2:
+            g.dq_t[cp.verts[c], ax] += val
+    return g
+
+
+def rollout_backward(pb, cp: ContactProblem, records, dqT, dvT, taus=None):
+    """Walk the contact steps backwards (taus: the trust-region choice per
+    step; an exact fixed point gives tau = 1/2, R8)."""
+    from . import adjoint
+    qbar, vbar = dqT.copy(), dvT.copy()
+    n_e = pb.tets.shape[0]
+    dw_tot, db_tot = np.zeros(n_e), np.zeros(n_e)
+    dmu = dlam = dk = 0.0
+    dfs = []
+    for t in reversed(range(len(records))):
+        tau = 0.5 if taus is None else taus[t]
+        g = backward_step(pb, cp, records[t], tau, qbar, vbar)
+        qbar, vbar = g.dq_t, g.dv_t
+        dw_tot += g.dw
+        db_tot += g.dbeta
+        dmu += g.dmu_bar
+        dlam += g.dlam_bar
+        dk += g.dk_bar
+        dfs.append(g.df_ext)
+    dE, dnu = adjoint.chain_material(pb, dw_tot, db_tot, dmu, dlam, dk)
+    return adjoint.RolloutGrad(qbar, vbar, dE, dnu, np.stack(dfs[::-1]), dw_tot)

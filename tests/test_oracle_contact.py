@@ -2,7 +2,8 @@
 from the oracle itself: brute-force enumeration of the LCP's complementary
 bases, an independent constrained minimiser for the friction QP, closed
 forms (single contact, no friction, unbounded friction), the Delassus matrix
-from a dense inverse, and momentum balance of a converged contact step."""
+from a dense inverse, momentum balance of a converged contact step, and
+central finite differences of a contact rollout's loss for the adjoint."""
 import itertools
 
 import numpy as np
@@ -113,3 +114,52 @@ def test_contact_step_momentum_balance(mu):
     assert np.all(lam_n >= 0) and np.abs(lam_n * gap).max() <= 1e-12 * max(lam_n.max(), 1.0)
     if mu == 0.0:
         assert np.array_equal(lam_f, np.zeros_like(lam_f))
+
+
+def _loss(sc, pb, cp, v0, E=None):
+    if E is not None:
+        pb = solver.build_problem(sc, E=E)
+        cp = contact.ContactProblem(pb, sc.contact)
+    q, v = sc.x0.copy(), v0.copy()
+    recs = []
+    for t in range(sc.steps):
+        qn, ln, lf, _ = contact.step(pb, cp, q, v, sc.f_ext[0], t, tol=1e-14)
+        recs.append({"q_t": q, "v_t": v, "q_next": qn, "lam_n": ln, "lam_f": lf})
+        v = (qn - q) / pb.h
+        q = qn
+    d = q - sc.target
+    return 0.5 * float(np.sum(d * d)), q, recs
+
+
+@pytest.mark.parametrize("mu", [0.0, 50.0])
+def test_contact_adjoint_matches_finite_differences(mu):
+    # frictionless (no friction rows) and all-stick (every friction row an
+    # equality): the fixed-active-set adjoint is then the exact derivative
+    sc = _tiny_pad(steps=2)
+    sc.contact.mu = mu
+    rng = np.random.default_rng(5)
+    v0 = 0.02 * rng.standard_normal(sc.X.shape)
+    pb = solver.build_problem(sc)
+    cp = contact.ContactProblem(pb, sc.contact)
+    L, qT, recs = _loss(sc, pb, cp, v0)
+    act, stick = contact.active_sets(cp, recs[-1]["lam_n"], recs[-1]["lam_f"])
+    assert act.any()
+    if mu > 0:
+        assert np.array_equal(act, stick)
+    g = contact.rollout_backward(pb, cp, recs, qT - sc.target, np.zeros_like(qT))
+    dv = rng.standard_normal(sc.X.shape)
+    eps = 1e-6
+    fd = (_loss(sc, pb, cp, v0 + eps * dv)[0] - _loss(sc, pb, cp, v0 - eps * dv)[0]) / (2 * eps)
+    assert abs(fd - np.sum(g.dv0 * dv)) <= 1e-5 * abs(fd) + 1e-12
+    dx = rng.standard_normal(sc.X.shape)
+    sc2 = sc.replace(x0=sc.x0 + eps * dx)
+    sc3 = sc.replace(x0=sc.x0 - eps * dx)
+    fdx = (_loss(sc2, pb, cp, v0)[0] - _loss(sc3, pb, cp, v0)[0]) / (2 * eps)
+    assert abs(fdx - np.sum(g.dx0 * dx)) <= 1e-5 * abs(fdx) + 1e-12
+    e = int(np.argmax(np.abs(g.dE)))
+    E1, E2 = sc.E.copy(), sc.E.copy()
+    hE = 1e-6 * sc.E[e]
+    E1[e] += hE
+    E2[e] -= hE
+    fde = (_loss(sc, pb, cp, v0, E1)[0] - _loss(sc, pb, cp, v0, E2)[0]) / (2 * hE)
+    assert abs(fde - g.dE[e]) <= 1e-4 * abs(fde) + 1e-15
