@@ -531,6 +531,13 @@ int pd_factor(pd_ctx* c) {
     if ((r = upload(c, &cv_d, cv, true)) || (r = upload(c, &cp_d, cp, true)) || (r = upload(c, &cn_d, cn, true)) ||
         (r = upload(c, &W_d, W, true)) || (r = dalloc(c, &buf_d, 12 * (size_t)K, true)))
       return r;
+    double* bwd_d;
+    if ((r = dalloc(c, &bwd_d, 18 * (size_t)K, true))) return r;
+    d.con_bwd = bwd_d;
+    if (c->con_ckpt) cudaFree(c->con_ckpt);   // sized with the checkpoints (reserve)
+    c->con_ckpt = nullptr;
+    d.con_ckpt = nullptr;
+    c->con_ckpt_cap = 0;
     d.n_con = K;
     d.con_v = cv_d;
     d.con_pos = cp_d;
@@ -558,7 +565,20 @@ int pd_factor(pd_ctx* c) {
 
 namespace {
 
+int reserve_contact(pd_ctx* c, int T) {
+  if (c->d.n_con == 0 || c->con_ckpt_cap >= T) return PD_OK;
+  if (c->con_ckpt) cudaFree(c->con_ckpt);
+  c->con_ckpt = nullptr;
+  c->con_ckpt_cap = 0;
+  if (cudaMalloc(&c->con_ckpt, (size_t)T * 3 * c->d.n_con * sizeof(double)) != cudaSuccess)
+    return fail(c, PD_ERR_OOM, "contact checkpoint allocation for %d steps", T);
+  c->con_ckpt_cap = T;
+  c->d.con_ckpt = c->con_ckpt;
+  return PD_OK;
+}
+
 int reserve_single(pd_ctx* c, int T) {
+  if (int r = reserve_contact(c, T)) return r;
   if (c->ckpt_cap >= T) return PD_OK;
   if (c->ckpt) cudaFree(c->ckpt);
   if (c->tau) cudaFree(c->tau);
@@ -578,7 +598,7 @@ int reserve_single(pd_ctx* c, int T) {
 
 // reserve for an enqueue: allocation is refused while the stream is captured
 int reserve_enqueue(pd_ctx* c, int T, cudaStream_t s) {
-  if (c->ckpt_cap >= T) return PD_OK;
+  if (c->ckpt_cap >= T && (c->d.n_con == 0 || c->con_ckpt_cap >= T)) return PD_OK;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   CK(cudaStreamIsCapturing(s, &cs));
   if (cs != cudaStreamCaptureStatusNone)
@@ -714,6 +734,10 @@ int stats_from_ctrl(pd_ctx* c, const Ctrl& hc, int which) {
     st.adj_iters_max = hc.adj_iters_max;
     st.adj_not_converged = hc.adj_not_converged;
     st.bwd_device_seconds = hc.elapsed_ns[1] * 1e-9;
+    if (!(which & 1)) {
+      st.contact_iters = hc.con_iters;
+      st.contact_unconverged = hc.con_unconverged;
+    }
   }
   st.status_flags = hc.status;
   if (hc.status & 4) return fail(c, PD_ERR_TIMEOUT, "a grid barrier of a persistent launch timed out");
@@ -880,7 +904,6 @@ int pd_backward(pd_ctx* c, const double* dqT, const double* dvT, double* dq0, do
   if (!c->factored) return fail(c, PD_ERR_NOT_FACTORED, "pd_factor must run before pd_backward");
   if (c->last_T < 1) return fail(c, PD_ERR_NO_CHECKPOINT, "no recorded rollout");
   if (!dqT) return fail(c, PD_ERR_ARG, "dqT is required");
-  if (!c->batch && c->d.n_con > 0) return fail(c, PD_ERR_ARG, "the adjoint of a contact rollout is not built");
   CK(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
   if (c->batch) return batch_backward(c, dqT, dvT, dq0, dv0, dE, dnu, df_ext, df_stride, s, true);
@@ -958,7 +981,6 @@ int pd_backward_enqueue(pd_ctx* c, const double* dqT, const double* dvT, double*
   if (!c->factored) return fail(c, PD_ERR_NOT_FACTORED, "pd_factor must run before pd_backward_enqueue");
   if (c->last_T < 1) return fail(c, PD_ERR_NO_CHECKPOINT, "no recorded or enqueued rollout");
   if (!dqT) return fail(c, PD_ERR_ARG, "dqT is required");
-  if (!c->batch && c->d.n_con > 0) return fail(c, PD_ERR_ARG, "the adjoint of a contact rollout is not built");
   CK(cudaSetDevice(c->device));
   cudaStream_t s = (cudaStream_t)stream;
   if (c->batch) return batch_backward(c, dqT, dvT, dq0, dv0, dE, dnu, df_ext, df_stride, s, false);
@@ -1062,6 +1084,7 @@ void pd_destroy(pd_ctx* c) {
   if (c->ckpt) cudaFree(c->ckpt);
   if (c->tau) cudaFree(c->tau);
   if (c->phase_count) cudaFree(c->phase_count);
+  if (c->con_ckpt) cudaFree(c->con_ckpt);
   if (c->stage) cudaFree(c->stage);
   if (c->h_flag) cudaFreeHost(c->h_flag);
   for (auto& e : c->prof_ev) cudaEventDestroy(e);

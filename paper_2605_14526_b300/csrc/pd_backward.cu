@@ -18,6 +18,7 @@
 #include "pd_coop.h"
 #include "pd_grid.cuh"
 #include "pd_launch.h"
+#include "pd_contact.cuh"
 #include "pd_phases.cuh"
 
 namespace pdk {
@@ -28,6 +29,9 @@ enum { R_U = 0, R_V = 9, R_SF = 18, R_SS = 21, R_J = 24, R_S = 30, R_T = 33 };
 struct BwdState {
   int adj_k, adj_done, status, adj_iters_total, adj_iters_max, adj_not_converged;
   double rz, rz0, alpha, beta, acc_mu, acc_lam, acc_k, dnu_acc;
+  // contact projection: the masked CG on W_a, one scalar set per axis
+  double cg_rr[3], cg_rr0[3], cg_alpha[3], cg_beta[3];
+  int cg_done, cg_it, cg_rot, con_cg, con_cg_unconverged;
 };
 
 template <typename T>
@@ -556,21 +560,78 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
   const Range rb = block_range(tm, d.n_v > d.n_e ? d.n_v : d.n_e);
   const Range rt = block_range(tm, d.n_v + d.n_e);
   const unsigned long long tstart = gtimer();
+  const Range rcn = block_range(tm, d.n_con);
   if (tid == 0) {
     S.adj_k = S.adj_done = S.status = S.adj_iters_total = S.adj_iters_max = S.adj_not_converged = 0;
     S.rz = S.rz0 = S.alpha = S.beta = S.acc_mu = S.acc_lam = S.acc_k = S.dnu_acc = 0.0;
+    S.con_cg = S.con_cg_unconverged = 0;
   }
+  // contact: after y = S r, project the preconditioned residual onto null(G):
+  // w = W_a^-1 G A^-1 r by CG on the active rows (per axis), then
+  // y <- y - S G^T w, so that the S^T pass gives A^-1 (r - G^T w)
+  auto project = [&](const double* ck) -> bool {
+    double pu[3] = {0.0, 0.0, 0.0};
+    for (int c = gwarp; c < d.n_con; c += nwarps) proj_gather(d, ck, c, lane, pu);
+    if (!grid_reduce<3>(d, tm, pu, sums)) return false;
+    if (tid == 0) {
+      for (int k = 0; k < 3; ++k) S.cg_rr[k] = S.cg_rr0[k] = sums[k];
+      S.cg_rot = 0;
+      S.cg_it = 0;
+      S.cg_done = (sums[0] == 0.0 && sums[1] == 0.0 && sums[2] == 0.0) ? 1 : 0;
+    }
+    __syncthreads();
+    while (!S.cg_done) {
+      const int rot = S.cg_rot;
+      double pa[3] = {0.0, 0.0, 0.0};
+      for (int c = gwarp; c < d.n_con; c += nwarps) proj_ap_row(d, ck, c, rot, lane, pa);
+      if (!grid_reduce<3>(d, tm, pa, sums)) return false;
+      if (tid == 0)
+        for (int k = 0; k < 3; ++k) S.cg_alpha[k] = (S.cg_rr[k] > 0.0 && sums[k] > 0.0) ? S.cg_rr[k] / sums[k] : 0.0;
+      __syncthreads();
+      const double al[3] = {S.cg_alpha[0], S.cg_alpha[1], S.cg_alpha[2]};
+      double pr[3] = {0.0, 0.0, 0.0};
+      for (int c = rcn.lo + tid; c < rcn.hi; c += blockDim.x) proj_update(d, c, rot, al, pr);
+      if (!grid_reduce<3>(d, tm, pr, sums)) return false;
+      if (tid == 0) {
+        bool all = true;
+        for (int k = 0; k < 3; ++k) {
+          S.cg_beta[k] = S.cg_rr[k] > 0.0 ? sums[k] / S.cg_rr[k] : 0.0;
+          S.cg_rr[k] = sums[k];
+          if (!(sums[k] <= 1e-28 * S.cg_rr0[k])) all = false;
+        }
+        S.cg_it += 1;
+        S.con_cg += 1;
+        if (all) S.cg_done = 1;
+        else if (S.cg_it >= d.con_max_iters) {
+          S.cg_done = 1;
+          S.con_cg_unconverged += 1;
+        }
+      }
+      __syncthreads();
+      if (S.cg_done) break;
+      const double be[3] = {S.cg_beta[0], S.cg_beta[1], S.cg_beta[2]};
+      for (int c = rcn.lo + tid; c < rcn.hi; c += blockDim.x) proj_dir(d, c, rot, be);
+      if (tid == 0) S.cg_rot = rot + 1;
+      if (!grid_sync(d, tm)) return false;
+    }
+    for (int c = rcn.lo + tid; c < rcn.hi; c += blockDim.x) proj_impulse(d, c);
+    if (!grid_sync(d, tm)) return false;
+    for (int i = gwarp; i < d.n_f; i += nwarps) contact_y_row(d, i, cb_nz(d), cb_nxy(d), lane);
+    return grid_sync(d, tm);
+  };
   for (int i = rb.lo + tid; i < rb.hi; i += blockDim.x) bwd_begin_item(d, i, a.dqT, a.dvT);
   bool ok = grid_sync(d, tm);
   for (int t = a.T - 1; t >= 0 && ok; --t) {
     const double* qstar = a.ckpt + (size_t)(t + 1) * nv3;
     const double* qt = a.ckpt + (size_t)t * nv3;
     const double tau = __ldcg(&d.tau[t]);
+    const double* ck = (d.n_con > 0 && d.con_ckpt) ? d.con_ckpt + (size_t)t * 3 * d.n_con : nullptr;
     for (int e = re.lo + tid; e < re.hi; e += blockDim.x) bwd_setup_item<T>(d, e, qstar, tau);
     for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) bwd_init_item(d, v);
     if (!(ok = grid_sync(d, tm))) break;
     for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, sg, lane);
     if (!(ok = grid_sync(d, tm))) break;
+    if (ck && !(ok = project(ck))) break;
     for (int j = gwarp; j < d.n_f; j += nwarps) spmv_st_row(d, d.y, d.z, j, lane);
     if (!(ok = grid_sync(d, tm))) break;
     double p1[1] = {0.0};
@@ -592,6 +653,7 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
       if (!(ok = grid_sync(d, tm))) break;
       for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, sg, lane);
       if (!(ok = grid_sync(d, tm))) break;
+      if (ck && !(ok = project(ck))) break;
       for (int j = gwarp; j < d.n_f; j += nwarps) spmv_st_row(d, d.y, d.z, j, lane);
       if (!(ok = grid_sync(d, tm))) break;
       double prz[1] = {0.0};
@@ -614,6 +676,16 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
     if (!(ok = grid_reduce<3>(d, tm, p3, sums))) break;
     if (tid == 0) route_finish(&S, sums);
     __syncthreads();
+    if (ck) {
+      // sticking contacts: the constraint q_xy = q_t,xy routes nu_S to dL/dq_t
+      for (int c = rcn.lo + tid; c < rcn.hi; c += blockDim.x)
+        if (con_stick(d, ck, c)) {
+          const int v = d.con_v[c];
+          d.gq[3 * (size_t)v] += cb_x(d)[3 * c];
+          d.gq[3 * (size_t)v + 1] += cb_x(d)[3 * c + 1];
+        }
+      if (!(ok = grid_sync(d, tm))) break;
+    }
   }
   if (ok) {
     double p4[4] = {0.0, 0.0, 0.0, 0.0};
@@ -640,6 +712,8 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
     c->acc_lam = S.acc_lam;
     c->acc_k = S.acc_k;
     c->elapsed_ns[1] = gtimer() - tstart;
+    c->con_iters += S.con_cg;
+    c->con_unconverged += S.con_cg_unconverged;
     atomicOr(&c->status, S.status);
   }
 }

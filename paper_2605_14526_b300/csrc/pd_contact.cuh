@@ -184,4 +184,100 @@ __device__ __forceinline__ void contact_y_row(const Dev& d, int i, const double*
   }
 }
 
+// ---------------------------------------------------------------- adjoint
+//
+// With the active sets of step t held fixed (normal-active: lam_n > 0;
+// sticking: |lam_f| < mu lam_n (1 - 1e-9)), the adjoint solves
+//   (A - K) a + G^T nu = q_bar,  G a = 0
+// by the same preconditioned CG with the preconditioner projected
+// A-orthogonally onto null(G): z = A^-1 (r - G^T w), w = W_a^-1 G A^-1 r,
+// W_a = G A^-1 G^T (the Delassus matrix on the active rows, per axis). The
+// last w is nu; its sticking rows enter dL/dq_t (the constraint
+// q_xy = q_t,xy of a sticking contact depends on q_t).
+
+__device__ __forceinline__ bool con_act(const Dev& d, const double* ck, int c) { return ck[c] > 0.0; }
+__device__ __forceinline__ bool con_stick(const Dev& d, const double* ck, int c) {
+  const int K = d.n_con;
+  const double lx = ck[K + 2 * c], ly = ck[K + 2 * c + 1];
+  return ck[c] > 0.0 && sqrt(lx * lx + ly * ly) < d.con_mu * ck[c] * (1.0 - 1e-9);
+}
+// adjoint work buffers ([K][3] each unless noted)
+__device__ __forceinline__ double* cb_x(const Dev& d) { return d.con_bwd; }
+__device__ __forceinline__ double* cb_r(const Dev& d) { return d.con_bwd + 3 * (size_t)d.n_con; }
+__device__ __forceinline__ double* cb_p(const Dev& d, int r) { return d.con_bwd + (6 + 3 * (r & 1)) * (size_t)d.n_con; }
+__device__ __forceinline__ double* cb_ap(const Dev& d) { return d.con_bwd + 12 * (size_t)d.n_con; }
+__device__ __forceinline__ double* cb_nz(const Dev& d) { return d.con_bwd + 15 * (size_t)d.n_con; }    // [K]
+__device__ __forceinline__ double* cb_nxy(const Dev& d) { return d.con_bwd + 16 * (size_t)d.n_con; }   // [K][2]
+
+// warp per candidate: u = G A^-1 r (masked rows of S^T y) as the CG
+// residual; w = 0; p = u; partial |u|^2 per axis
+__device__ __forceinline__ void proj_gather(const Dev& d, const double* ck, int c, int lane, double* part) {
+  double a0, a1, a2;
+  spmv_st_sum(d, d.y, d.con_pos[c], lane, a0, a1, a2);
+  if (lane == 0) {
+    const bool st = con_stick(d, ck, c), ac = con_act(d, ck, c);
+    const double u[3] = {st ? a0 : 0.0, st ? a1 : 0.0, ac ? d.con_n[c] * a2 : 0.0};
+    for (int k = 0; k < 3; ++k) {
+      cb_x(d)[3 * c + k] = 0.0;
+      cb_r(d)[3 * c + k] = u[k];
+      cb_p(d, 0)[3 * c + k] = u[k];
+      part[k] += u[k] * u[k];
+    }
+  }
+}
+
+// warp per row: W_a p (axis 2 with the normal signs), partial p . W_a p
+__device__ __forceinline__ void proj_ap_row(const Dev& d, const double* ck, int c, int rot, int lane, double* part) {
+  const int K = d.n_con;
+  const double* p = cb_p(d, rot);
+  const double* Wr = d.con_W + (size_t)c * K;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int j = lane; j < K; j += 32) {
+    const double w = Wr[j];
+    s0 += w * p[3 * j];
+    s1 += w * p[3 * j + 1];
+    s2 += w * d.con_n[j] * p[3 * j + 2];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if (lane == 0) {
+    const bool st = con_stick(d, ck, c), ac = con_act(d, ck, c);
+    const double ap[3] = {st ? s0 : 0.0, st ? s1 : 0.0, ac ? d.con_n[c] * s2 : 0.0};
+    for (int k = 0; k < 3; ++k) {
+      cb_ap(d)[3 * c + k] = ap[k];
+      part[k] += p[3 * c + k] * ap[k];
+    }
+  }
+}
+
+// thread per candidate: w += alpha p, r -= alpha W_a p; partial |r|^2 per axis
+__device__ __forceinline__ void proj_update(const Dev& d, int c, int rot, const double* alpha, double* part) {
+  const double* p = cb_p(d, rot);
+  for (int k = 0; k < 3; ++k) {
+    const size_t o = 3 * (size_t)c + k;
+    cb_x(d)[o] += alpha[k] * p[o];
+    const double r = cb_r(d)[o] - alpha[k] * cb_ap(d)[o];
+    cb_r(d)[o] = r;
+    part[k] += r * r;
+  }
+}
+
+// thread per candidate: next direction p' = r + beta p (other buffer)
+__device__ __forceinline__ void proj_dir(const Dev& d, int c, int rot, const double* beta) {
+  const double* p = cb_p(d, rot);
+  double* pn = cb_p(d, rot + 1);
+  for (int k = 0; k < 3; ++k) pn[3 * c + k] = cb_r(d)[3 * c + k] + beta[k] * p[3 * c + k];
+}
+
+// thread per candidate: the impulse parts of -G^T w for the y correction
+__device__ __forceinline__ void proj_impulse(const Dev& d, int c) {
+  cb_nxy(d)[2 * c] = -cb_x(d)[3 * c];
+  cb_nxy(d)[2 * c + 1] = -cb_x(d)[3 * c + 1];
+  cb_nz(d)[c] = -cb_x(d)[3 * c + 2];
+}
+
 }  // namespace pdk

@@ -83,6 +83,8 @@ struct pd_ctx {
   // frictional contacts (pd_set_contacts)
   std::vector<int> con_ground, con_box;
   pd_contact_desc con{};
+  double* con_ckpt = nullptr;   // [T][3K] converged multipliers per step
+  int con_ckpt_cap = 0;
 };
 
 // batched instances (pd_batch.cpp)

@@ -203,6 +203,18 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
       warm_now = false;
     }
     if (!ok) break;
+    if (d.n_con > 0 && d.con_ckpt) {
+      // converged multipliers of this step (active sets of the adjoint)
+      const Range rc = block_range(tm, d.n_con);
+      const double* ln = con_lamn(d, S.rot_n + 1);
+      const double* lf = con_lamf(d, S.rot_f + 1);
+      double* ck = d.con_ckpt + (size_t)t * 3 * d.n_con;
+      for (int c = rc.lo + tid; c < rc.hi; c += blockDim.x) {
+        ck[c] = ln[c];
+        ck[d.n_con + 2 * c] = lf[2 * c];
+        ck[d.n_con + 2 * c + 1] = lf[2 * c + 1];
+      }
+    }
     const bool last = t == a.T - 1;
     double* qo = last && a.qT ? a.qT : a.sq;
     double* vo = last && a.vT ? a.vT : a.sv;

@@ -1,6 +1,6 @@
 """GPU tests of frictional contact (vertex-ground and vertex-box contacts,
-normal LCP + Tresca friction on the Delassus matrix, eq. q_update) against
-the contact oracle."""
+normal LCP + Tresca friction on the Delassus matrix, eq. q_update) and of
+their adjoint (fixed active sets, projected CG) against the contact oracle."""
 import dataclasses
 
 import numpy as np
@@ -56,10 +56,20 @@ def test_contact_rollout_fp32_configured_gate_matches_oracle(oracle_pad):
     assert gap.min() >= -1e-6 * np.abs(q[:, 2]).max()
 
 
-def test_contact_adjoint_is_refused():
-    sc = _pad(steps=1)
-    code, q, st, pd = _gpu(sc)
-    x = torch.zeros((sc.n_v, 3), dtype=torch.float64, device=DEV)
-    code = binding.pd_backward(pd.ctx, x, None, torch.empty_like(x), torch.empty_like(x), None, None, None, 0,
-                               check=False)
-    assert binding.STATUS[code] == "PD_ERR_ARG"
+def test_contact_adjoint_fp64_matches_oracle(oracle_pad):
+    sc, qT_o, recs, cp = oracle_pad
+    pb = solver.build_problem(sc)
+    g_o = contact.rollout_backward(pb, cp, recs, qT_o - sc.target, np.zeros_like(qT_o))
+    code, q, st, pd = _gpu(sc, local_fp32=False, eps_res=1e-10, eps_step=1e-12, k_max=3000)
+    assert binding.STATUS[code] == "PD_OK"
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+    x = t(q - sc.target)
+    dq0, dv0 = torch.empty_like(x), torch.empty_like(x)
+    dE = torch.empty(sc.n_e, dtype=torch.float64, device=DEV)
+    dnu = torch.empty(1, dtype=torch.float64, device=DEV)
+    code = binding.pd_backward(pd.ctx, x, None, dq0, dv0, dE, dnu, None, 0, check=False)
+    sb = binding.pd_get_stats(pd.ctx)
+    assert binding.STATUS[code] == "PD_OK", (sb.adj_not_converged, sb.contact_unconverged)
+    assert rel(dv0.cpu().numpy(), g_o.dv0) <= 1e-4, rel(dv0.cpu().numpy(), g_o.dv0)
+    assert rel(dq0.cpu().numpy(), g_o.dx0) <= 1e-4, rel(dq0.cpu().numpy(), g_o.dx0)
+    assert rel(dE.cpu().numpy(), g_o.dE) <= 1e-4, rel(dE.cpu().numpy(), g_o.dE)
