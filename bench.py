@@ -285,6 +285,94 @@ def run_batch(args, rank, world, local_rank, dev, dist):
         print(json.dumps(line))
 
 
+CONTACT_WORKLOAD = ("contact-rich pad 48x48x12 cells of 1 cm (138,240 tets, 31,213 vertices), stiff core 1e7 / "
+                    "shell 1e5 Pa, pressed by a box onto the ground, Coulomb mu 0.5 (2,690 contact candidates), "
+                    "dt 2 ms, fwd+bwd")
+
+
+def run_contact(args, rank, world, local_rank, dev, dist):
+    """Contact workload: the first --contact-steps PD steps of the 300-step
+    rollout (forward with the contact solves, then its adjoint) per benchmark
+    step; the full 300-step rollout takes about 5 minutes on one GPU."""
+    import torch
+    from paper_2605_14526_b300 import binding, inputs
+
+    sc = inputs.contact_pad(seed=13 + rank)
+    T = min(args.contact_steps, sc.steps)
+    opts = binding.options_for(sc.solver)
+    opts.k_max = 2000
+    t0 = time.perf_counter()
+    pd = binding.PDContext(sc, opts)
+    factor_s = time.perf_counter() - t0
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    x0, v0 = t(sc.x0), t(sc.v0)
+    qT, vT = torch.empty_like(x0), torch.empty_like(x0)
+    dq0, dv0 = torch.empty_like(x0), torch.empty_like(x0)
+    dE = torch.empty(sc.n_e, dtype=torch.float64, device=dev)
+    dnu = torch.empty(1, dtype=torch.float64, device=dev)
+    top = torch.as_tensor(sc.loss_vertices, device=dev)
+    target = t(sc.target)
+    stream = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def fwd_bwd(timed=False):
+        if timed:
+            ev[0].record(stream)
+        binding.pd_rollout(pd.ctx, T, x0, v0, None, 0, qT, vT, stream)
+        if timed:
+            ev[1].record(stream)
+        dq = torch.zeros_like(x0)
+        dq[top] = qT[top] - target[top]
+        binding.pd_backward(pd.ctx, dq, None, dq0, dv0, dE, dnu, None, 0, stream)
+        if timed:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        fwd_bwd()
+    torch.cuda.synchronize()
+    launches0 = binding.pd_get_stats(pd.ctx).launches
+    fwd_ms = bwd_ms = 0.0
+    it = adj = cpass_f = cpass_b = 0
+    with ClockSampler(local_rank) as clk:
+        for _ in range(args.steps):
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            fwd_bwd(timed=True)
+            torch.cuda.synchronize()
+            fwd_ms += ev[0].elapsed_time(ev[1])
+            bwd_ms += ev[1].elapsed_time(ev[2])
+            st = binding.pd_get_stats(pd.ctx)
+            it += st.iters_total
+            adj += st.adj_iters_total
+            cpass_b += st.contact_iters
+    launches = binding.pd_get_stats(pd.ctx).launches - launches0
+    tot = fwd_ms + bwd_ms
+    value = world * T * args.steps / (tot / 1e3)
+    st = binding.pd_get_stats(pd.ctx)
+    fwd_iter_bytes = 56 * sc.n_e + 48 * sc.n_v + 20 * st.factor_nnz + 96 * st.n_free + 13 * 24 * sc.n_v
+    achieved = fwd_iter_bytes * it / args.steps / (fwd_ms / args.steps * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    line = {"metric": METRIC, "value": value, "unit": "PD steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (FP32 local step, FP64 RHS/factor/solve/contact)", "data": "synthetic",
+            "config": {"workload": CONTACT_WORKLOAD, "pd_steps_per_bench_step": T,
+                       "note": f"first {T} of the configured 300 steps per benchmark step",
+                       "factor_and_delassus_s": factor_s, "nnz_S": int(st.factor_nnz),
+                       "fwd_iters_per_step": it / (args.steps * T), "adj_iters_per_step": adj / (args.steps * T),
+                       "fwd_ms_per_pd_step": fwd_ms / (args.steps * T), "bwd_ms_per_pd_step": bwd_ms / (args.steps * T),
+                       "adjoint_contact_cg_passes_per_step": cpass_b / (args.steps * T),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "e2e": None,
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "fp64", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "k_fwd_rollout (persistent forward with contact)",
+                         "peak_kind": peak_kind, "note": "algorithmic bytes exclude the contact passes over W"},
+            "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -292,7 +380,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="bar", choices=["bar", "batch"])
+    ap.add_argument("--workload", default="bar", choices=["bar", "batch", "contact"])
+    ap.add_argument("--contact-steps", type=int, default=20,
+                    help="contact workload: PD steps of the 300-step rollout timed per benchmark step")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -313,6 +403,11 @@ def main():
         dist.init_process_group("nccl")
     build()
     dev = torch.device("cuda", local_rank)
+    if args.workload == "contact":
+        run_contact(args, rank, world, local_rank, dev, dist)
+        if dist:
+            dist.destroy_process_group()
+        return
     if args.workload == "batch":
         run_batch(args, rank, world, local_rank, dev, dist)
         if dist:

@@ -597,7 +597,7 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
         for (int k = 0; k < 3; ++k) {
           S.cg_beta[k] = S.cg_rr[k] > 0.0 ? sums[k] / S.cg_rr[k] : 0.0;
           S.cg_rr[k] = sums[k];
-          if (!(sums[k] <= 1e-28 * S.cg_rr0[k])) all = false;
+          if (!(sums[k] <= 1e-26 * S.cg_rr0[k])) all = false;
         }
         S.cg_it += 1;
         S.con_cg += 1;

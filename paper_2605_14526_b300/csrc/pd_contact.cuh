@@ -50,9 +50,15 @@ __device__ __forceinline__ void contact_gather(const Dev& d, int c, int t, int l
   }
 }
 
-// FISTA state (one instance per subproblem, in the team's shared state)
+// FISTA state (one instance per subproblem, in the team's shared state).
+// The inner tolerance follows the outer iteration: 1e-2 x the relative
+// b-change of the last local step, clamped to [con_tol, 1e-4], so early outer
+// iterations take cheap inexact inner solves and the converged step an
+// inner solve at con_tol (the fixed point does not depend on the path).
 template <class St>
-__device__ __forceinline__ void fista_reset(St* S) {
+__device__ __forceinline__ void fista_reset(const Dev& d, St* S) {
+  const double rel = S->bprev_norm2 > 0.0 ? sqrt(S->db_norm2 / S->bprev_norm2) : 1.0;
+  S->f_tol = fmax(d.con_tol, fmin(1e-4, 1e-2 * rel));
   S->f_t = 1.0;
   S->f_beta = 0.0;   // the first pass starts from the warm multipliers (no momentum)
   S->f_it = 0;
@@ -66,7 +72,7 @@ __device__ __forceinline__ void fista_finish(const Dev& d, St* S, int* rot, cons
   *rot += 1;         // next becomes cur
   S->f_it += 1;
   S->con_iters += 1;
-  const bool conv = sums[0] <= d.con_tol * d.con_tol * sums[1] + 1e-300;
+  const bool conv = sums[0] <= S->f_tol * S->f_tol * sums[1] + 1e-300;
   if (conv) {
     S->f_done = 1;
   } else if (S->f_it >= d.con_max_iters) {

@@ -123,7 +123,7 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
           // y <- y + S J^T lam so that the S^T pass below gives A^-1 (b + J^T lam)
           for (int c = gwarp; c < d.n_con; c += nwarps) contact_gather(d, c, t, lane);
           if (!(ok = grid_sync(d, tm))) break;
-          if (tid == 0) fista_reset(&S);
+          if (tid == 0) fista_reset(d, &S);
           __syncthreads();
           while (!S.f_done) {
             const int rot = S.rot_n;
@@ -136,7 +136,7 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
           }
           if (!ok) break;
           const double* lam_n = con_lamn(d, S.rot_n + 1);
-          if (tid == 0) fista_reset(&S);
+          if (tid == 0) fista_reset(d, &S);
           __syncthreads();
           while (!S.f_done) {
             const int rot = S.rot_f;

@@ -20,7 +20,7 @@ struct FwdState {
   double gmin;
   // contact inner solves (FISTA): momentum and restart of the running solve,
   // buffer rotation of the normal and the friction multipliers
-  double f_t, f_beta;
+  double f_t, f_beta, f_tol;
   int f_it, f_done, rot_n, rot_f, con_iters, con_unconverged;
   int iters_total, iters_max, resets, not_converged, tau_half, tau_one, status;
   double gram[kMaxAA * kMaxAA];
