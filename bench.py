@@ -498,7 +498,7 @@ def main():
     torch.cuda.synchronize()
     prof = binding.pd_get_profile(pd.ctx)
     binding.pd_profile(pd.ctx, False)
-    phase_names = ["begin", "local", "assemble_gate", "spmv_s", "spmv_st", "spmv_st_anderson", "update", "end_tr"]
+    phase_names = ["begin", "local", "assemble_gate", "spmv_s", "spmv_st_anderson_dots", "anderson_solve", "update", "end_tr"]
     phases = {n: round(prof.phase_ms[i], 3) for i, n in enumerate(phase_names) if prof.phase_ms[i] > 0}
 
     # end to end through the C ABI with host buffers (copies inside the region)

@@ -269,7 +269,8 @@ typedef struct {
   /* persistent rollouts: time per phase measured on the device (globaltimer,
    * block 0, including the grid barrier that ends the phase), summed over the
    * rollouts run since profiling was enabled: begin, local step, assembly +
-   * gate, S b, S^T y, Anderson, update, step end + trust region */
+   * gate, S b, S^T y with the Anderson dot products (through their
+   * reduction), the small Anderson solve, update, step end + trust region */
   double phase_ms[8];
   double work_ms[8];  /* of which block 0's own work before the phase's barrier */
 } pd_profile_out;

@@ -228,10 +228,24 @@ __device__ __forceinline__ void pcg_w_item(const Dev& d, int v, double* part) {
   double acc[3] = {0.0, 0.0, 0.0};
   gather_contrib<T>(d, v, acc);
   double ap[3] = {0.0, 0.0, 0.0};
-  for (int p = d.A_ptr[v]; p < d.A_ptr[v + 1]; ++p) {
-    const int u = d.A_idx[p];
-    const double a = d.A_val[p];
-    for (int i = 0; i < 3; ++i) ap[i] += a * d.pdir[3 * (size_t)u + i];
+  const int beg = d.A_ptr[v], end = d.A_ptr[v + 1];
+  for (int p0 = beg; p0 < end; p0 += 8) {   // chunks of 8: overlapped loads, same order
+    int uu[8];
+    double av[8], pv[8][3];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      uu[k] = p0 + k < end ? d.A_idx[p0 + k] : -1;
+      av[k] = p0 + k < end ? d.A_val[p0 + k] : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) pv[k][i] = uu[k] >= 0 ? d.pdir[3 * (size_t)uu[k] + i] : 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (uu[k] >= 0)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) ap[i] += av[k] * pv[k][i];
   }
   for (int i = 0; i < 3; ++i) {
     const size_t o = 3 * (size_t)v + i;

@@ -146,13 +146,28 @@ __device__ __forceinline__ void project(const Dev& d, const T* F, T* P, T* U, T*
     for (int j = 0; j < 3; ++j) P[3 * i + j] = U[3 * i] * ss[0] * V[3 * j] + U[3 * i + 1] * ss[1] * V[3 * j + 1] + U[3 * i + 2] * ss[2] * V[3 * j + 2];
 }
 
+// acc += the corner contributions of vertex v, in incidence order. Indices
+// and values are loaded in chunks of 8 before they are added, so the
+// dependent index -> value loads of a chunk overlap instead of running one
+// incidence at a time (same summation order, same bits).
 template <typename T>
 __device__ __forceinline__ void gather_contrib(const Dev& d, int v, double* acc) {
   const T* cb = reinterpret_cast<const T*>(d.contrib);
-  for (int p = d.inc_ptr[v]; p < d.inc_ptr[v + 1]; ++p) {
-    const int ic = d.inc_idx[p];  // element*4 + corner
+  const int beg = d.inc_ptr[v], end = d.inc_ptr[v + 1];
+  for (int p0 = beg; p0 < end; p0 += 8) {
+    int ic[8];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) acc[i] += (double)cb[3 * (size_t)ic + i];
+    for (int u = 0; u < 8; ++u) ic[u] = p0 + u < end ? d.inc_idx[p0 + u] : -1;
+    T val[8][3];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) val[u][i] = ic[u] >= 0 ? cb[3 * (size_t)ic[u] + i] : T(0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (ic[u] >= 0)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) acc[i] += (double)val[u][i];
   }
 }
 

@@ -99,6 +99,7 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
         for (int v = gwarp; v < d.n_v; v += nwarps) warm_vertex(d, v, d.qt, nullptr, vin, d.q, d.qprev, lane);
         if (!(ok = grid_sync(d, tm))) break;
       }
+      double pu[2] = {0.0, 0.0};   // step norms of the last update, reduced with the next assembly
       for (;;) {
         const int k = S.k;
         const bool hi = S.hi != 0;   // FP64 local step after an escalation
@@ -106,11 +107,11 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
         work_done(PH_LOCAL);
         if (!(ok = grid_sync(d, tm))) break;
         mark(PH_LOCAL);
-        double p3[3] = {0.0, 0.0, 0.0};
-        for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) assemble_any<T>(d, v, k, p3, hi);
+        double p5[5] = {0.0, 0.0, 0.0, pu[0], pu[1]};
+        for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) assemble_any<T>(d, v, k, p5, hi);
         work_done(PH_ASSEMBLE);
-        if (!(ok = grid_reduce<3>(d, tm, p3, sums))) break;
-        if (tid == 0) assemble_finish(d, &S, k, sums);
+        if (!(ok = grid_reduce<5>(d, tm, p5, sums))) break;
+        if (tid == 0) assemble_finish(d, &S, k, sums, true);
         __syncthreads();
         mark(PH_ASSEMBLE);
         if (S.done) break;
@@ -168,17 +169,19 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
         }
         work_done(PH_AA);
         if (!(ok = grid_reduce<2 * kMaxAA>(d, tm, pa, sums))) break;
+        mark(PH_SPMV_ST);   // S^T y + Anderson dots, through their reduction
         if (tid == 0) aa_finish(d, &S, av, sums);
         __syncthreads();
-        mark(PH_AA);
+        mark(PH_AA);        // the small Anderson solve
         const int use_hat = S.use_hat, nc = S.ncols;
         double gam[kMaxAA];
-        for (int j = 0; j < nc; ++j) gam[j] = S.gamma[j];
-        double pu[2] = {0.0, 0.0};
+#pragma unroll
+        for (int j = 0; j < kMaxAA; ++j) gam[j] = j < nc ? S.gamma[j] : 0.0;
+        pu[0] = pu[1] = 0.0;
         for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) update_item(d, v, use_hat, nc, gam, pu);
         work_done(PH_UPDATE);
-        if (!(ok = grid_reduce<2>(d, tm, pu, sums))) break;
-        if (tid == 0) update_finish(d, &S, sums);
+        if (!(ok = grid_sync(d, tm))) break;
+        if (tid == 0) update_count(d, &S);
         __syncthreads();
         mark(PH_UPDATE);
         if (S.done) break;

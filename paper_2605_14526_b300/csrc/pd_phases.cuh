@@ -142,11 +142,15 @@ __device__ __forceinline__ double gate_rhs(double eps, double b2, double abs_tol
 // become the floor of the iteration and the local step switches to FP64 for
 // the rest of the rollout.
 template <class St>
-__device__ __forceinline__ void assemble_finish(const Dev& d, St* c, int k, const double* s) {
+__device__ __forceinline__ void assemble_finish(const Dev& d, St* c, int k, const double* s, bool carried = false) {
   c->n_local += 1;
   if (s[2] > 0.0) c->status |= 1;
   c->db_norm2 = s[0];
   c->bprev_norm2 = s[1];
+  if (carried && k >= 1) {  // the previous update's step norms travel with this reduction
+    c->dq_norm2 = s[3];
+    c->qprev_norm2 = s[4];
+  }
   if (d.fixed_iters <= 0 && k >= 2) {
     // ||a|| <= eps ||b|| + abs  <=>  a^2 <= eps^2 b^2 + 2 eps abs ||b|| + abs^2; the
     // cross term is negligible next to the others and is formed with an FP32 root
@@ -308,10 +312,13 @@ __device__ __forceinline__ void aa_component(const Dev& d, size_t o, double qh, 
     d.dQ[a.slot * nv3 + o] = q - d.qprev[o];
   }
   d.gprev[o] = g;
-  for (int j = 0; j < a.ncols_new; ++j) {
-    const double dgj = (a.add && j == a.slot) ? dg_new : d.dG[j * nv3 + o];
-    if (a.add) part[j] += dg_new * dgj;
-    part[kMaxAA + j] += dgj * g;
+#pragma unroll
+  for (int j = 0; j < kMaxAA; ++j) {   // compile-time j: the partials stay in registers
+    if (j < a.ncols_new) {
+      const double dgj = (a.add && j == a.slot) ? dg_new : d.dG[j * nv3 + o];
+      if (a.add) part[j] += dg_new * dgj;
+      part[kMaxAA + j] += dgj * g;
+    }
   }
 }
 
@@ -410,7 +417,9 @@ __device__ __forceinline__ void update_item(const Dev& d, int v, int use_hat, in
     const size_t o = 3 * (size_t)v + i;
     double qn = d.qhat[o];
     if (!use_hat)
-      for (int j = 0; j < nc; ++j) qn -= gam[j] * (d.dQ[j * nv3 + o] + d.dG[j * nv3 + o]);
+#pragma unroll
+      for (int j = 0; j < kMaxAA; ++j)
+        if (j < nc) qn -= gam[j] * (d.dQ[j * nv3 + o] + d.dG[j * nv3 + o]);
     const double qo = d.q[o];
     part[0] += (qn - qo) * (qn - qo);
     part[1] += qo * qo;
@@ -424,6 +433,13 @@ template <class St>
 __device__ __forceinline__ void update_finish(const Dev& d, St* c, const double* s) {
   c->dq_norm2 = s[0];
   c->qprev_norm2 = s[1];
+  c->k += 1;
+  if (d.fixed_iters > 0 && c->k >= d.fixed_iters) c->done = 1;
+}
+
+// update bookkeeping when the step norms are carried into the next assembly
+template <class St>
+__device__ __forceinline__ void update_count(const Dev& d, St* c) {
   c->k += 1;
   if (d.fixed_iters > 0 && c->k >= d.fixed_iters) c->done = 1;
 }

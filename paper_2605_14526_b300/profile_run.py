@@ -58,7 +58,7 @@ def main():
     dq0, dv0 = torch.empty_like(x0), torch.empty_like(x0)
     dE = torch.empty(n_e, dtype=torch.float64, device=dev)
     dnu = torch.empty(getattr(pd, "n", 1), dtype=torch.float64, device=dev)
-    names = ["begin", "local", "assemble+gate", "S b", "S^T y", "anderson", "update", "end+tr"]
+    names = ["begin", "local", "assemble+gate", "S b", "S^T y+AA dots (to reduction)", "AA solve", "update", "end+tr"]
     for r in range(args.repeat):
         if args.phases and r == args.repeat - 1 and not hasattr(pd, "n"):
             binding.pd_profile(pd.ctx, True)
