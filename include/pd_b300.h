@@ -238,8 +238,10 @@ int pd_solve(pd_ctx* ctx, const double* b, double* x, void* stream);
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture.
  *   - Every call shares the one array: calls that overlap on the GPU (other
- *     streams, other contexts, other host threads) race. The accumulator is
- *     cleared by each call before use.
+ *     streams, other contexts, other host threads) race. Each call overwrites
+ *     it; the partial sums of long rows of S go to buffers that pd_factor
+ *     sets aside for this call alone, so it shares nothing with the
+ *     context's rollouts.
  * b, x: [n_v][3] device pointers; pinned rows of x are set to 0. */
 int pd_solve_noalloc(pd_ctx* ctx, const double* b, double* x, void* stream);
 
@@ -273,6 +275,10 @@ typedef struct {
    * reduction), the small Anderson solve, update, step end + trust region */
   double phase_ms[8];
   double work_ms[8];  /* of which block 0's own work before the phase's barrier */
+  double work_max_ms[8]; /* the largest total over the blocks of each block's own work per phase
+                            (the critical block; the rest of phase_ms is barrier and reduction) */
+  double last_ms[8];     /* per iteration, the phase's start (block 0) to the last block's arrival
+                            at the phase's closing barrier, summed: the critical path's work */
 } pd_profile_out;
 
 /* enable != 0 turns the phase timers on (and clears them); 0 turns them off. */

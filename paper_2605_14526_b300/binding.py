@@ -61,7 +61,8 @@ class pd_contact_desc(ctypes.Structure):
 
 class pd_profile_out(ctypes.Structure):
     _fields_ = [("local_launches", c_int64), ("local_ms", c_double), ("solve_launches", c_int64),
-                ("solve_ms", c_double), ("phase_ms", c_double * 8), ("work_ms", c_double * 8)]
+                ("solve_ms", c_double), ("phase_ms", c_double * 8), ("work_ms", c_double * 8),
+                ("work_max_ms", c_double * 8), ("last_ms", c_double * 8)]
 
 
 class pd_tuning(ctypes.Structure):

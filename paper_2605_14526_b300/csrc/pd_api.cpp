@@ -240,7 +240,7 @@ int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_o
                      &d.z, &d.pdir, &d.w, &d.qbar, &d.gq, &d.gv, &c->sq, &c->sv};
   for (double** p : vecs)
     if ((r = dalloc(c, p, nv3))) return r;
-  if ((r = dalloc(c, &d.bperm, 3 * (size_t)c->n_f)) || (r = dalloc(c, &d.y, 3 * (size_t)c->n_f))) return r;
+  if ((r = dalloc(c, &d.bperm, 3 * (size_t)c->n_f)) || (r = dalloc(c, &d.y, 3 * (size_t)c->n_f))) return r;  // float2
   d.sq = c->sq;
   d.sv = c->sv;
   const int m = std::max(c->opt.aa_m, 1);
@@ -419,14 +419,29 @@ int pd_factor(pd_ctx* c) {
   std::vector<double> s_val, st_val;
   std::vector<int> st_idx;
   pdf::inverse_factor(c->fac, s_rowptr, s_val, st_ptr, st_idx, st_val);
-  // skyline segments of at most 512 entries, one warp each
+  // skyline segments of at most kSegLen entries, one warp each; the segments
+  // of a split row own consecutive partial slots
   std::vector<int4> seg;
-  const int SEG = 512;
+  int n_slot = 0;
   for (int i = 0; i < nf; ++i) {
     const int len = i - c->fac.first_desc[i] + 1;
-    const int ns = (len + SEG - 1) / SEG;
-    for (int s = 0; s < ns; ++s) seg.push_back(make_int4(i, s * SEG, std::min(SEG, len - s * SEG), ns > 1 ? 1 : 0));
+    const int ns = (len + pdk::kSegLen - 1) / pdk::kSegLen;
+    for (int s = 0; s < ns; ++s)
+      seg.push_back(make_int4(i, s * pdk::kSegLen, std::min(pdk::kSegLen, len - s * pdk::kSegLen), ns > 1 ? 1 + n_slot : 0));
+    if (ns > 1) n_slot += ns;
   }
+  // S and S^T as double-float pairs for the device products
+  auto split = [](const std::vector<double>& v) {
+    std::vector<float2> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+      const float h = (float)v[i];
+      o[i] = make_float2(h, (float)(v[i] - (double)h));
+    }
+    return o;
+  };
+  const std::vector<float2> s_hl = split(s_val), st_hl = split(st_val);
+  std::vector<double>().swap(s_val);
+  std::vector<double>().swap(st_val);
   std::vector<int> iperm_v(n_v, -1), perm_v(nf);
   for (int k = 0; k < nf; ++k) {
     perm_v[k] = f2v[c->fac.perm[k]];
@@ -435,7 +450,9 @@ int pd_factor(pd_ctx* c) {
   Dev& d = c->d;
   int r;
   std::vector<float> coef32(coef.begin(), coef.end());
-  float* c32; double *c64, *mu_d, *lam_d, *E_d, *cA_d, *sv, *stv, *Av, *Bv;
+  float* c32; double *c64, *mu_d, *lam_d, *E_d, *cA_d, *Av, *Bv;
+  float2 *sv, *stv, *spart, *spart_na;
+  int *scnt, *scnt_na;
   int *iperm_d, *perm_d, *sfirst, *sti, *Ap, *Ai, *Bp, *Bi;
   int64_t *srp, *stp;
   int4* seg_d;
@@ -443,10 +460,13 @@ int pd_factor(pd_ctx* c) {
       (r = upload(c, &lam_d, lam, true)) || (r = upload(c, &E_d, c->E, true)) || (r = upload(c, &cA_d, cA, true)) ||
       (r = upload(c, &iperm_d, iperm_v, true)) || (r = upload(c, &perm_d, perm_v, true)) ||
       (r = upload(c, &srp, s_rowptr, true)) || (r = upload(c, &sfirst, c->fac.first_desc, true)) ||
-      (r = upload(c, &sv, s_val, true)) || (r = upload(c, &seg_d, seg, true)) || (r = upload(c, &stp, st_ptr, true)) ||
-      (r = upload(c, &sti, st_idx, true)) || (r = upload(c, &stv, st_val, true)) || (r = upload(c, &Ap, Ad.ptr, true)) ||
+      (r = upload(c, &sv, s_hl, true)) || (r = upload(c, &seg_d, seg, true)) || (r = upload(c, &stp, st_ptr, true)) ||
+      (r = upload(c, &sti, st_idx, true)) || (r = upload(c, &stv, st_hl, true)) || (r = upload(c, &Ap, Ad.ptr, true)) ||
       (r = upload(c, &Ai, Ad.idx, true)) || (r = upload(c, &Av, Ad.val, true)) || (r = upload(c, &Bp, Bd.ptr, true)) ||
-      (r = upload(c, &Bi, Bd.idx, true)) || (r = upload(c, &Bv, Bd.val, true)))
+      (r = upload(c, &Bi, Bd.idx, true)) || (r = upload(c, &Bv, Bd.val, true)) ||
+      (r = dalloc(c, &spart, 3 * (size_t)n_slot, true)) || (r = dalloc(c, &spart_na, 3 * (size_t)n_slot, true)) ||
+      (r = upload(c, &scnt, std::vector<int>(std::max(n_slot, 1), 0), true)) ||
+      (r = upload(c, &scnt_na, std::vector<int>(std::max(n_slot, 1), 0), true)))
     return r;
   // warm-start feature: log10 of the volume-weighted mean E around each vertex
   {
@@ -463,8 +483,9 @@ int pd_factor(pd_ctx* c) {
     d.logE = le_d;
   }
   d.coef32 = c32; d.coef64 = c64; d.mu_e = mu_d; d.lam_e = lam_d; d.E = E_d; d.cA = cA_d;
-  d.iperm = iperm_d; d.perm = perm_d; d.s_rowptr = srp; d.s_first = sfirst; d.s_val = sv; d.s_seg = seg_d;
-  d.n_seg = (int)seg.size(); d.st_ptr = stp; d.st_idx = sti; d.st_val = stv;
+  d.iperm = iperm_d; d.perm = perm_d; d.s_rowptr = srp; d.s_first = sfirst; d.s_hl = sv; d.s_seg = seg_d;
+  d.n_seg = (int)seg.size(); d.st_ptr = stp; d.st_idx = sti; d.st_hl = stv;
+  d.n_slot = n_slot; d.s_part = spart; d.s_cnt = scnt; d.s_part_na = spart_na; d.s_cnt_na = scnt_na;
   d.A_ptr = Ap; d.A_idx = Ai; d.A_val = Av; d.B_ptr = Bp; d.B_idx = Bi; d.B_val = Bv;
   d.n_f = nf;
   d.local_fp32 = c->opt.local_fp32 ? 1 : 0;
@@ -759,6 +780,8 @@ int collect_single(pd_ctx* c, cudaStream_t s, int which) {
     for (int i = 0; i < 8; ++i) {
       c->prof.phase_ms[i] += hc.phase_ns[i] * 1e-6;
       c->prof.work_ms[i] += hc.work_ns[i] * 1e-6;
+      c->prof.work_max_ms[i] += hc.work_max_ns[i] * 1e-6;
+      c->prof.last_ms[i] += hc.last_ns[i] * 1e-6;
     }
   }
   return stats_from_ctrl(c, hc, which);
@@ -1021,7 +1044,7 @@ int pd_solve(pd_ctx* c, const double* b, double* x, void* stream) {
   if (!c->factored) return fail(c, PD_ERR_NOT_FACTORED, "pd_factor must run before pd_solve");
   if (!b || !x) return fail(c, PD_ERR_ARG, "b and x are required");
   CK(cudaSetDevice(c->device));
-  pdk::launch_solve(c->d, (cudaStream_t)stream, b, c->d.bperm, c->d.y, x);
+  pdk::launch_solve(c->d, (cudaStream_t)stream, b, c->d.bperm, c->d.y, c->d.s_part, c->d.s_cnt, x);
   c->launches += 3;
   CK(cudaGetLastError());
   return PD_OK;
@@ -1031,6 +1054,7 @@ int pd_profile(pd_ctx* c, int32_t enable) {
   if (!c) return PD_ERR_ARG;
   if (c->batch) return fail(c, PD_ERR_ARG, "pd_profile is single-instance only");
   c->profiling = enable != 0;
+  c->d.prof = c->profiling ? 1 : 0;
   c->prof = pd_profile_out{};
   c->prof_used = 0;
   c->prof_kind.clear();

@@ -204,10 +204,7 @@ __device__ __forceinline__ void bwd_init_item(const Dev& d, int v) {
   }
   if (!pin) {
     const int pos = d.iperm[v];
-    for (int a = 0; a < 3; ++a) {
-      d.bperm[3 * (size_t)pos + a] = rv[a];
-      d.y[3 * (size_t)pos + a] = 0.0;
-    }
+    for (int a = 0; a < 3; ++a) d.bperm[3 * (size_t)pos + a] = df_split(rv[a]);
   }
 }
 
@@ -263,8 +260,7 @@ __device__ __forceinline__ void pcg_r_item(const Dev& d, int v, double alpha) {
     d.mu[o] += alpha * d.pdir[o];
     const double rn = d.r[o] - alpha * d.w[o];
     d.r[o] = rn;
-    d.bperm[3 * (size_t)pos + i] = rn;
-    d.y[3 * (size_t)pos + i] = 0.0;
+    d.bperm[3 * (size_t)pos + i] = df_split(rn);
   }
 }
 
@@ -643,7 +639,7 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
     for (int e = re.lo + tid; e < re.hi; e += blockDim.x) bwd_setup_item<T>(d, e, qstar, tau);
     for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) bwd_init_item(d, v);
     if (!(ok = grid_sync(d, tm))) break;
-    for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, sg, lane);
+    for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, d.s_part, d.s_cnt, sg, lane);
     if (!(ok = grid_sync(d, tm))) break;
     if (ck && !(ok = project(ck))) break;
     for (int j = gwarp; j < d.n_f; j += nwarps) spmv_st_row(d, d.y, d.z, j, lane);
@@ -665,7 +661,7 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
       const double alpha = S.alpha;
       for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) pcg_r_item(d, v, alpha);
       if (!(ok = grid_sync(d, tm))) break;
-      for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, sg, lane);
+      for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, d.s_part, d.s_cnt, sg, lane);
       if (!(ok = grid_sync(d, tm))) break;
       if (ck && !(ok = project(ck))) break;
       for (int j = gwarp; j < d.n_f; j += nwarps) spmv_st_row(d, d.y, d.z, j, lane);
@@ -777,7 +773,7 @@ void launch_bwd_setup(const Dev& d, cudaStream_t s, const double* qstar, const d
 
 void launch_bwd_init(const Dev& d, cudaStream_t s) {
   k_bwd_init<<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
-  launch_apply_inverse(d, s, d.bperm, d.y, d.z, 0);
+  launch_apply_inverse(d, s, d.bperm, d.y, d.s_part, d.s_cnt, d.z, 0);
   k_pcg_init_z<<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
 }
 
@@ -790,7 +786,7 @@ void launch_pcg_iteration(const Dev& d, cudaStream_t s) {
     k_pcg_w<double><<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
   }
   k_pcg_r<<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
-  launch_apply_inverse(d, s, d.bperm, d.y, d.z, 2);
+  launch_apply_inverse(d, s, d.bperm, d.y, d.s_part, d.s_cnt, d.z, 2);
   k_pcg_z<<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
   k_pcg_p<<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
 }

@@ -11,46 +11,72 @@ namespace pdk {
 
 // ------------------------------------------------------------ reductions
 
+__host__ __device__ constexpr int pow2_ceil(int n) { return n <= 1 ? 1 : 2 * pow2_ceil((n + 1) / 2); }
+
+// Warp sum of v[NV] by recursive halving: at each of the first log2(P)
+// levels (P = NV rounded up to a power of two, at most 32) a lane keeps one
+// half of its values and adds its partner's copy of that half, so all NV
+// sums take P - 1 + 5 - log2(P) shuffles instead of 5 NV. Returns this
+// lane's sum, of value index *idx (the same sum in the 32 / P lanes that
+// share idx); the order of the additions is fixed.
 template <int NV>
-__device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* red, int row) {
-  __shared__ double sh[32][NV > 0 ? NV : 1];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+__device__ __forceinline__ double warp_sum_scatter(const double (&v)[NV], int lane, int& idx) {
+  constexpr int P = pow2_ceil(NV);
+  static_assert(P <= 32, "at most 32 values");
+  double w[P];
 #pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    double x = v[j];
+  for (int j = 0; j < P; ++j) w[j] = j < NV ? v[j] : 0.0;
+  int base = 0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0) sh[wid][j] = x;
+  for (int h = P / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const double send = up ? w[k] : w[k + h];
+      const double keep = up ? w[k + h] : w[k];
+      w[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+    if (up) base += h;
   }
-  __syncthreads();
-  if (threadIdx.x < NV) {
-    double s = 0.0;
-    const int nw = (blockDim.x + 31) >> 5;
-    for (int w = 0; w < nw; ++w) s += sh[w][threadIdx.x];
-    red[(size_t)row * kRed + threadIdx.x] = s;
-  }
+  double x = w[0];
+#pragma unroll
+  for (int o = 16 / P; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  idx = base;
+  return x;
 }
 
-// block-wide sum of v[NV] (fixed shuffle tree, then warps in order) into
-// out[NV] (shared), visible to the whole block on return
+// block-wide sum of v[NV] (warp sums in a fixed order, then the warps in
+// order) into sh_out[NV] (shared), read by threads < NV
 template <int NV>
-__device__ __forceinline__ void block_reduce_to(double (&v)[NV], double* out) {
+__device__ __forceinline__ double block_sum_lane(double (&v)[NV]) {
   __shared__ double sh[32][NV];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    double x = v[j];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0) sh[wid][j] = x;
-  }
+  constexpr int P = pow2_ceil(NV);
+  int idx;
+  const double x = warp_sum_scatter<NV>(v, lane, idx);
+  if ((lane & (32 / P - 1)) == 0 && idx < NV) sh[wid][idx] = x;
   __syncthreads();
+  double s = 0.0;
   if (threadIdx.x < NV) {
-    double s = 0.0;
     const int nw = (blockDim.x + 31) >> 5;
     for (int w = 0; w < nw; ++w) s += sh[w][threadIdx.x];
-    out[threadIdx.x] = s;
   }
+  return s;
+}
+
+// block-wide sum of v[NV] stored to row `row` of the reduction scratch
+template <int NV>
+__device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* red, int row) {
+  const double s = block_sum_lane<NV>(v);
+  if (threadIdx.x < NV) red[(size_t)row * kRed + threadIdx.x] = s;
+}
+
+// block-wide sum of v[NV] into out[NV] (shared), visible to the whole block
+// on return
+template <int NV>
+__device__ __forceinline__ void block_reduce_to(double (&v)[NV], double* out) {
+  const double s = block_sum_lane<NV>(v);
+  if (threadIdx.x < NV) out[threadIdx.x] = s;
   __syncthreads();
 }
 

@@ -167,12 +167,12 @@ __device__ __forceinline__ void contact_y_row(const Dev& d, int i, const double*
     if (d.con_pos[m] < lo) a = m + 1;
     else b = m;
   }
-  const double* srow = d.s_val + d.s_rowptr[i];
+  const float2* srow = d.s_hl + d.s_rowptr[i];
   double r0 = 0.0, r1 = 0.0, r2 = 0.0;
   for (int c = a + lane; c < d.n_con; c += 32) {
     const int p = d.con_pos[c];
     if (p > i) break;
-    const double s = srow[p - lo];
+    const double s = df_join(srow[p - lo]);
     r0 += s * lam_f[2 * c];
     r1 += s * lam_f[2 * c + 1];
     r2 += s * d.con_n[c] * lam_n[c];
@@ -184,9 +184,10 @@ __device__ __forceinline__ void contact_y_row(const Dev& d, int i, const double*
     r2 += __shfl_xor_sync(0xffffffffu, r2, o);
   }
   if (lane == 0) {
-    d.y[3 * (size_t)i] += r0;
-    d.y[3 * (size_t)i + 1] += r1;
-    d.y[3 * (size_t)i + 2] += r2;
+    float2* yi = d.y + 3 * (size_t)i;
+    yi[0] = df_split(df_join(yi[0]) + r0);
+    yi[1] = df_split(df_join(yi[1]) + r1);
+    yi[2] = df_split(df_join(yi[2]) + r2);
   }
 }
 

@@ -28,6 +28,12 @@ __device__ __forceinline__ void st_relaxed(unsigned int* p, unsigned int v) {
   asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // The blocks of a persistent launch form teams: team-local block index `b`
 // of `nb` blocks; one team works on one problem instance (the whole grid in
 // a single-instance launch). Barriers and reductions span one team.
@@ -42,6 +48,7 @@ struct Team {
 template <int NV>
 __device__ __forceinline__ bool grid_reduce(const Dev& d, Team tm, double (&part)[NV > 0 ? NV : 1], double* sums) {
   __shared__ int s_last, s_fail;
+  __shared__ unsigned long long s_tarr;
   if (tm.nb == 1) {
     if constexpr (NV > 0) block_reduce_to<NV>(part, sums);
     else __syncthreads();
@@ -54,6 +61,7 @@ __device__ __forceinline__ bool grid_reduce(const Dev& d, Team tm, double (&part
     const unsigned int g = ld_acquire(&c->bar_gen);
     const unsigned int arrived = atom_add_acq_rel(&c->bar_count, 1u);
     s_last = arrived == (unsigned int)tm.nb - 1;
+    if (d.prof && s_last) s_tarr = gtimer();
     s_fail = 0;
     if (!s_last) {
       unsigned int it = 0;
@@ -77,6 +85,7 @@ __device__ __forceinline__ bool grid_reduce(const Dev& d, Team tm, double (&part
       double acc[NV];
 #pragma unroll
       for (int j = 0; j < NV; ++j) acc[j] = 0.0;
+#pragma unroll 4
       for (int b = threadIdx.x; b < tm.nb; b += blockDim.x) {
         double v[NV];
 #pragma unroll
@@ -89,6 +98,7 @@ __device__ __forceinline__ bool grid_reduce(const Dev& d, Team tm, double (&part
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+      if (d.prof) c->t_last = s_tarr;
       st_relaxed(&c->bar_count, 0u);
       red_release(&c->bar_gen, 1u);
     }
@@ -112,12 +122,6 @@ __device__ __forceinline__ Range block_range(Team tm, int n) {
   const int chunk = (n + tm.nb - 1) / tm.nb;
   const int lo = min(n, tm.b * chunk);
   return {lo, min(n, lo + chunk)};
-}
-
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
 }
 
 }  // namespace pdk

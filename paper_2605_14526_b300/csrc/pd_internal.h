@@ -10,6 +10,7 @@ constexpr int kRed = 24;         // doubles per block in the reduction scratch
 constexpr int kVtxBlock = 256;   // threads per block, vertex kernels
 constexpr int kTetBlock = 128;   // threads per block, element kernels
 constexpr int kWarpsSpmv = 8;    // warps per block, skyline SpMV
+constexpr int kSegLen = 512;     // entries per segment of a skyline row of S (one warp each)
 constexpr int kJacRec = 36;      // values per element in the backward Jacobian record
 constexpr int kPersistBlock = 256;  // threads per block, persistent kernels
 constexpr int kRedRows = 2048;   // rows of the reduction scratch (>= any grid used)
@@ -51,6 +52,9 @@ struct Ctrl {
   unsigned long long phase_ns[8];  // persistent kernels: time per phase (globaltimer, block 0)
   unsigned long long work_ns[8];   // ... of which block 0's own work before the phase's barrier
   unsigned long long elapsed_ns[2]; // persistent launches: wall time of the forward / adjoint (team block 0)
+  unsigned long long work_max_ns[8]; // profiling: largest per-block total work per phase
+  unsigned long long last_ns[8];     // profiling: phase start to the last block's arrival at its barrier
+  unsigned long long t_last;         // profiling: arrival time of the last block at the latest team barrier
   int con_iters, con_unconverged;   // contact: inner (FISTA) iterations, inner solves that hit their cap
 };
 
@@ -83,6 +87,7 @@ struct Dev {
   int aa_m, k_max, fixed_iters, tr_mode, adj_max_iters;
   int escalate;       // FP32 local step: switch to FP64 after this many iterations without progress (0 = never)
   int warm;           // start of each step: 0 q_t, 1 network warm start, 2 constant-velocity extrapolation
+  int prof;           // 1: every block times its own work per phase (pd_profile)
   double h, alpha_d, eps_step, eps_res, eps_abs, eps_tr, adj_tol;
   double g[3];
   double mu_bar, lam_bar, k_bar, mu_ref, beta0, nu;
@@ -113,12 +118,17 @@ struct Dev {
   const int* perm;         // [n_f] vertex at elimination position
   const int64_t* s_rowptr; // skyline rows of S
   const int* s_first;      // first_desc per row
-  const double* s_val;
-  const int4* s_seg;       // segments {row, offset, length, multi}
+  const float2* s_hl;      // S entries as double-float pairs (hi, lo)
+  const int4* s_seg;       // segments {row, offset, length, 0 or 1 + first partial slot of a split row}
   int n_seg;
+  int n_slot;              // partial slots of the split rows
+  float2* s_part;          // [n_slot][3] partial sums of split rows
+  int* s_cnt;              // [n_slot] finished segments of a split row (at its first slot)
+  float2* s_part_na;       // the same two buffers for pd_solve_noalloc, which shares no work
+  int* s_cnt_na;           // buffer with the rollouts of its context
   const int64_t* st_ptr;   // S^T CSR (rows = positions)
   const int* st_idx;
-  const double* st_val;
+  const float2* st_hl;
 
   // work vectors [n_v][3] unless noted
   double* q;        // current iterate q^k
@@ -130,8 +140,8 @@ struct Dev {
   double* b0;       // q-independent RHS
   double* b;        // b^k   (two buffers, swapped by parity of k)
   double* bprev;
-  double* bperm;    // [n_f][3] b in elimination order
-  double* y;        // [n_f][3] S b
+  float2* bperm;    // [n_f][3] b in elimination order (double-float)
+  float2* y;        // [n_f][3] S b (double-float)
   double* dQ;       // [kMaxAA][n_v][3]
   double* dG;
   void* contrib;    // [n_e][12] float or double

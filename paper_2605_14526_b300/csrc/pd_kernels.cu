@@ -48,16 +48,17 @@ __global__ void __launch_bounds__(kVtxBlock) k_assemble(Dev d) {
   }
 }
 
-__global__ void __launch_bounds__(32 * kWarpsSpmv) k_spmv_s(Dev d, const double* xin, double* y, int check_done) {
+__global__ void __launch_bounds__(32 * kWarpsSpmv) k_spmv_s(Dev d, const float2* xin, float2* y, float2* part, int* cnt,
+                                                             int check_done) {
   if (check_done == 1 && d.ctrl->done) return;
   if (check_done == 2 && d.ctrl->adj_done) return;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int sg = warp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, xin, y, sg, lane);
+  for (int sg = warp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, xin, y, part, cnt, sg, lane);
 }
 
-__global__ void __launch_bounds__(32 * kWarpsSpmv) k_spmv_st(Dev d, const double* y, double* out, int check_done) {
+__global__ void __launch_bounds__(32 * kWarpsSpmv) k_spmv_st(Dev d, const float2* y, double* out, int check_done) {
   if (check_done == 1 && d.ctrl->done) return;
   if (check_done == 2 && d.ctrl->adj_done) return;
   const int lane = threadIdx.x & 31;
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(kVtxBlock) k_tr(Dev d) {
 
 // b (vertex order) -> elimination order in xperm; zero the S b accumulator
 // rows and the pinned rows of x
-__global__ void k_solve_in(Dev d, const double* b, double* xperm, double* y, double* x) {
+__global__ void k_solve_in(Dev d, const double* b, float2* xperm, double* x) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= d.n_v) return;
   if (d.pinned[v]) {
@@ -126,10 +127,7 @@ __global__ void k_solve_in(Dev d, const double* b, double* xperm, double* y, dou
     return;
   }
   const int pos = d.iperm[v];
-  for (int i = 0; i < 3; ++i) {
-    xperm[3 * (size_t)pos + i] = b[3 * (size_t)v + i];
-    y[3 * (size_t)pos + i] = 0.0;
-  }
+  for (int i = 0; i < 3; ++i) xperm[3 * (size_t)pos + i] = df_split(b[3 * (size_t)v + i]);
 }
 
 // ------------------------------------------------------------ launch wrappers
@@ -150,14 +148,16 @@ int spmvt_blocks(const Dev& d) {
   return b < 1 ? 1 : (b > 4096 ? 4096 : b);
 }
 
-void launch_apply_inverse(const Dev& d, cudaStream_t s, const double* xperm, double* y, double* out, int check) {
-  k_spmv_s<<<spmv_blocks(d), 32 * kWarpsSpmv, 0, s>>>(d, xperm, y, check);
+void launch_apply_inverse(const Dev& d, cudaStream_t s, const float2* xperm, float2* y, float2* part, int* cnt,
+                          double* out, int check) {
+  k_spmv_s<<<spmv_blocks(d), 32 * kWarpsSpmv, 0, s>>>(d, xperm, y, part, cnt, check);
   k_spmv_st<<<spmvt_blocks(d), 32 * kWarpsSpmv, 0, s>>>(d, y, out, check);
 }
 
-void launch_solve(const Dev& d, cudaStream_t s, const double* b, double* xperm, double* y, double* x) {
-  k_solve_in<<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d, b, xperm, y, x);
-  launch_apply_inverse(d, s, xperm, y, x, 0);
+void launch_solve(const Dev& d, cudaStream_t s, const double* b, float2* xperm, float2* y, float2* part, int* cnt,
+                  double* x) {
+  k_solve_in<<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d, b, xperm, x);
+  launch_apply_inverse(d, s, xperm, y, part, cnt, x, 0);
 }
 
 void launch_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
@@ -173,7 +173,7 @@ void launch_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
     cudaEventRecord(ev[1], s);
     cudaEventRecord(ev[2], s);
   }
-  launch_apply_inverse(d, s, d.bperm, d.y, d.qhat, 1);
+  launch_apply_inverse(d, s, d.bperm, d.y, d.s_part, d.s_cnt, d.qhat, 1);
   if (ev) cudaEventRecord(ev[3], s);
   k_aa<<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
   k_update<<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);

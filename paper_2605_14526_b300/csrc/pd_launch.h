@@ -16,10 +16,12 @@ void launch_step_begin(const Dev& d, cudaStream_t s, const double* qt, const dou
 void launch_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev);
 void launch_step_end(const Dev& d, cudaStream_t s, double* qn, double* vn, double* ckpt_next, double* tau);
 // A^-1 x for x given in elimination order (check: 0 none, 1 forward done flag, 2 backward done flag)
-void launch_apply_inverse(const Dev& d, cudaStream_t s, const double* xperm, double* y, double* out, int check);
+void launch_apply_inverse(const Dev& d, cudaStream_t s, const float2* xperm, float2* y, float2* part, int* cnt,
+                          double* out, int check);
 
 // x = A^-1 b for b, x in vertex order; xperm and y are [n_f][3] work buffers
-void launch_solve(const Dev& d, cudaStream_t s, const double* b, double* xperm, double* y, double* x);
+void launch_solve(const Dev& d, cudaStream_t s, const double* b, float2* xperm, float2* y, float2* part, int* cnt,
+                  double* x);
 
 // co-resident blocks per SM of a persistent kernel (at most 2; 0 if
 // cooperative launch is unavailable); *sms gets the SM count

@@ -79,7 +79,9 @@ extern "C" int pd_solve_noalloc(pd_ctx* ctx, const double* b, double* x, void* s
     pd_internal_set_error(ctx, cudaGetErrorString(e));
     return PD_ERR_CUDA;
   }
-  pdk::launch_solve(*d, static_cast<cudaStream_t>(stream), b, scratch, scratch + 3 * (size_t)kNoAllocMaxFree, x);
+  float2* xs = reinterpret_cast<float2*>(scratch);   // double-float pairs, 8 bytes like a double
+  pdk::launch_solve(*d, static_cast<cudaStream_t>(stream), b, xs, xs + 3 * (size_t)kNoAllocMaxFree, d->s_part_na,
+                    d->s_cnt_na, x);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     pd_internal_set_error(ctx, cudaGetErrorString(e));

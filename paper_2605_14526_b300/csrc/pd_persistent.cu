@@ -56,20 +56,38 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
   const Range re = block_range(tm, d.n_e);
   const Range rv = block_range(tm, d.n_v);
   const Range rt = block_range(tm, d.n_e + d.n_v);
-  unsigned long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0}, wk[8] = {0, 0, 0, 0, 0, 0, 0, 0}, t0 = 0, tstart = 0;
+  // phase timers (thread 0 only; kept in shared memory, off the registers):
+  // ph block 0's phase times, wk block 0's own work, wall with d.prof every
+  // block's own work per phase (from the end of the previous phase to the end
+  // of its work; the largest total over the team is the critical block's),
+  // lst with d.prof the time from block 0's phase start to the last block's
+  // arrival at the phase's closing barrier
+  __shared__ unsigned long long ph[8], wk[8], wall[8], lst[8], tmr[3];   // tmr: t0, ta, tstart
+  if (tid == 0) {
+    for (int i = 0; i < 8; ++i) ph[i] = wk[i] = wall[i] = lst[i] = 0;
+    tmr[0] = tmr[1] = tmr[2] = 0;
+  }
   auto mark = [&](int p) {
-    if (writer && tid == 0) {
-      const unsigned long long t1 = gtimer();
-      ph[p] += t1 - t0;
-      t0 = t1;
+    if (tid == 0 && (writer || d.prof)) {
+      const unsigned long long t1 = gtimer(), t0 = tmr[0];
+      if (writer) ph[p] += t1 - t0;
+      if (writer && d.prof && tm.nb > 1) {
+        const unsigned long long tl = *(volatile unsigned long long*)&d.ctrl->t_last;
+        if (tl > t0 && tl < t1) lst[p] += tl - t0;
+      }
+      tmr[0] = tmr[1] = t1;
     }
   };
   // block 0's own work of the current phase (before its barrier); all threads
   // of block 0 are done when thread 0 passes this __syncthreads
   auto work_done = [&](int p) {
-    if (writer) {
+    if (writer || d.prof) {
       __syncthreads();
-      if (tid == 0) wk[p] += gtimer() - t0;
+      if (tid == 0) {
+        const unsigned long long t1 = gtimer();
+        if (writer) wk[p] += t1 - tmr[0];
+        if (d.prof) wall[p] += t1 - tmr[1];
+      }
     }
   };
   if (tid == 0) {
@@ -78,8 +96,7 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
     S.rot_n = S.rot_f = S.con_iters = S.con_unconverged = 0;
     S.last_rho = 0.0;
     for (int i = 0; i < kMaxAA * kMaxAA; ++i) S.gram[i] = 0.0;
-    t0 = gtimer();
-    tstart = t0;
+    tmr[0] = tmr[1] = tmr[2] = gtimer();
   }
   bool ok = true;
   for (int t = 0; t < a.T && ok; ++t) {
@@ -115,7 +132,7 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
         __syncthreads();
         mark(PH_ASSEMBLE);
         if (S.done) break;
-        for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, sg, lane);
+        for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, d.s_part, d.s_cnt, sg, lane);
         work_done(PH_SPMV_S);
         if (!(ok = grid_sync(d, tm))) break;
         mark(PH_SPMV_S);
@@ -254,8 +271,13 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
       c->phase_ns[i] += ph[i];
       c->work_ns[i] += wk[i];
     }
-    c->elapsed_ns[0] = gtimer() - tstart;
+    c->elapsed_ns[0] = gtimer() - tmr[2];
   }
+  if (d.prof && tid == 0)
+    for (int i = 0; i < 8; ++i) {
+      atomicMax(&d.ctrl->work_max_ns[i], wall[i]);
+      if (writer) d.ctrl->last_ns[i] += lst[i];
+    }
 }
 
 // team[blockIdx.x] = {instance, block index in its team, team size, 0}

@@ -6,6 +6,7 @@
 // arrays are rewritten by other blocks between grid barriers.
 #pragma once
 #include "pd_common.cuh"
+#include "pd_df.cuh"
 
 namespace pdk {
 
@@ -125,8 +126,7 @@ __device__ __forceinline__ void assemble_item(const Dev& d, int v, int k, double
       part[1] += bp * bp;
     }
     d.b[3 * v + i] = acc[i];
-    d.bperm[3 * (size_t)pos + i] = acc[i];
-    d.y[3 * (size_t)pos + i] = 0.0;
+    d.bperm[3 * (size_t)pos + i] = df_split(acc[i]);
   }
   if (!finite3(acc[0], acc[1], acc[2])) part[2] += 1.0;
 }
@@ -180,99 +180,132 @@ __device__ __forceinline__ void assemble_finish(const Dev& d, St* c, int k, cons
 }
 
 // ------------------------------------------------------------ solve A^-1 = S^T S
+//
+// Both products run in double-float arithmetic (pd_df.cuh): S is stored as
+// float pairs, the right-hand side b in elimination order (bperm) and the
+// intermediate y = S b as float pairs, and the result S^T y is returned in
+// FP64.
 
-// one segment of a skyline row of S: y_row += S[row, seg] x[seg] (3 RHS);
-// four independent accumulator sets per lane keep several loads in flight
-__device__ __forceinline__ void spmv_s_segment(const Dev& d, const double* xin, double* y, int sg, int lane) {
-  const int4 seg = d.s_seg[sg];  // x = row, y = offset in row, z = length, w = multi
+// one segment of a skyline row of S: S[row, seg] x[seg] (3 RHS); four
+// independent accumulator sets per lane keep several loads in flight. A row
+// of one segment is written directly; the segments of a split row write
+// their partial sums to consecutive slots and the last one to finish adds
+// the slots in slot order, so the result does not depend on the schedule.
+__device__ __forceinline__ void spmv_s_segment(const Dev& d, const float2* xin, float2* y, float2* part, int* cnt,
+                                               int sg, int lane) {
+  const int4 seg = d.s_seg[sg];  // x = row, y = offset in row, z = length, w = 0 or 1 + first slot of a split row
   const int row = seg.x;
-  const double* sv = d.s_val + d.s_rowptr[row] + seg.y;
-  const double* xv = xin + 3 * (size_t)(d.s_first[row] + seg.y);
-  double a[4][3] = {};
+  const float2* sv = d.s_hl + d.s_rowptr[row] + seg.y;
+  const float2* xv = xin + 3 * (size_t)(d.s_first[row] + seg.y);
+  float ah[4][3], al[4][3];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ah[u][i] = al[u][i] = 0.0f;
   int p = lane;
   for (; p + 96 < seg.z; p += 128) {
+    float2 sa[4], xa[4][3];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const double s = sv[p + 32 * u];
-      const double* x = xv + 3 * (size_t)(p + 32 * u);
-      a[u][0] += s * x[0];
-      a[u][1] += s * x[1];
-      a[u][2] += s * x[2];
+      sa[u] = sv[p + 32 * u];
+      const float2* x = xv + 3 * (size_t)(p + 32 * u);
+      xa[u][0] = x[0];
+      xa[u][1] = x[1];
+      xa[u][2] = x[2];
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) df_mac(ah[u][i], al[u][i], sa[u], xa[u][i]);
   }
   for (; p < seg.z; p += 32) {
-    const double s = sv[p];
-    const double* x = xv + 3 * (size_t)p;
-    a[0][0] += s * x[0];
-    a[0][1] += s * x[1];
-    a[0][2] += s * x[2];
-  }
-  double a0 = (a[0][0] + a[1][0]) + (a[2][0] + a[3][0]);
-  double a1 = (a[0][1] + a[1][1]) + (a[2][1] + a[3][1]);
-  double a2 = (a[0][2] + a[1][2]) + (a[2][2] + a[3][2]);
+    const float2 sa = sv[p];
+    const float2* x = xv + 3 * (size_t)p;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    for (int i = 0; i < 3; ++i) df_mac(ah[0][i], al[0][i], sa, x[i]);
   }
+  float2 r[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    r[i] = df_warp_sum(df_add(df_add(make_float2(ah[0][i], al[0][i]), make_float2(ah[1][i], al[1][i])),
+                              df_add(make_float2(ah[2][i], al[2][i]), make_float2(ah[3][i], al[3][i]))));
+  float2* yr = y + 3 * (size_t)row;
+  if (seg.w == 0) {
+    if (lane < 3) yr[lane] = r[lane == 0 ? 0 : (lane == 1 ? 1 : 2)];
+    return;
+  }
+  const int slot0 = seg.w - 1;
+  const int ns = (row - d.s_first[row] + kSegLen) / kSegLen;   // segments of the row
+  float2* pr = part + 3 * (size_t)slot0;
+  int last = 0;
   if (lane == 0) {
-    double* yr = y + 3 * (size_t)row;
-    if (seg.w) {
-      atomicAdd(yr, a0);
-      atomicAdd(yr + 1, a1);
-      atomicAdd(yr + 2, a2);
-    } else {
-      yr[0] = a0;
-      yr[1] = a1;
-      yr[2] = a2;
-    }
+    float2* ps = pr + 3 * (size_t)(seg.y / kSegLen);
+    ps[0] = r[0];
+    ps[1] = r[1];
+    ps[2] = r[2];
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;" : "=r"(old) : "l"(cnt + slot0) : "memory");
+    last = old == ns - 1;
   }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (!last) return;
+  __syncwarp();   // lane 0's acquire orders the other lanes' loads after every segment's release
+  float2 t[3] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+  for (int k = lane; k < ns; k += 32)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t[i] = df_add(t[i], __ldcg(pr + 3 * (size_t)k + i));
+#pragma unroll
+  for (int i = 0; i < 3; ++i) t[i] = df_warp_sum(t[i]);
+  if (lane < 3) yr[lane] = t[lane == 0 ? 0 : (lane == 1 ? 1 : 2)];
+  if (lane == 0) cnt[slot0] = 0;   // next use is ordered after a barrier or a kernel boundary
 }
 
-// row j of S^T: sum over the ancestors i of j of S_ij y_i, returned to every
-// lane; indices of four entries are loaded before their y values
-__device__ __forceinline__ void spmv_st_sum(const Dev& d, const double* y, int j, int lane, double& r0, double& r1,
+// row j of S^T: sum over the ancestors i of j of S_ij y_i, returned in FP64
+// to every lane; the indices of four entries are loaded before their y values
+__device__ __forceinline__ void spmv_st_sum(const Dev& d, const float2* y, int j, int lane, double& r0, double& r1,
                                             double& r2) {
   const int64_t beg = d.st_ptr[j], end = d.st_ptr[j + 1];
-  double a[4][3] = {};
+  float ah[4][3], al[4][3];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ah[u][i] = al[u][i] = 0.0f;
   int64_t p = beg + lane;
   for (; p + 96 < end; p += 128) {
     int ix[4];
-    double sv[4];
+    float2 sa[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       ix[u] = d.st_idx[p + 32 * u];
-      sv[u] = d.st_val[p + 32 * u];
+      sa[u] = d.st_hl[p + 32 * u];
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const double* yv = y + 3 * (size_t)ix[u];
-      a[u][0] += sv[u] * yv[0];
-      a[u][1] += sv[u] * yv[1];
-      a[u][2] += sv[u] * yv[2];
+      const float2* yv = y + 3 * (size_t)ix[u];
+      const float2 y0 = yv[0], y1 = yv[1], y2 = yv[2];
+      df_mac(ah[u][0], al[u][0], sa[u], y0);
+      df_mac(ah[u][1], al[u][1], sa[u], y1);
+      df_mac(ah[u][2], al[u][2], sa[u], y2);
     }
   }
   for (; p < end; p += 32) {
-    const double s = d.st_val[p];
-    const double* yv = y + 3 * (size_t)d.st_idx[p];
-    a[0][0] += s * yv[0];
-    a[0][1] += s * yv[1];
-    a[0][2] += s * yv[2];
-  }
-  r0 = (a[0][0] + a[1][0]) + (a[2][0] + a[3][0]);
-  r1 = (a[0][1] + a[1][1]) + (a[2][1] + a[3][1]);
-  r2 = (a[0][2] + a[1][2]) + (a[2][2] + a[3][2]);
+    const float2 sa = d.st_hl[p];
+    const float2* yv = y + 3 * (size_t)d.st_idx[p];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    r0 += __shfl_xor_sync(0xffffffffu, r0, o);
-    r1 += __shfl_xor_sync(0xffffffffu, r1, o);
-    r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    for (int i = 0; i < 3; ++i) df_mac(ah[0][i], al[0][i], sa, yv[i]);
   }
+  float2 r[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    r[i] = df_warp_sum(df_add(df_add(make_float2(ah[0][i], al[0][i]), make_float2(ah[1][i], al[1][i])),
+                              df_add(make_float2(ah[2][i], al[2][i]), make_float2(ah[3][i], al[3][i]))));
+  r0 = df_join(r[0]);
+  r1 = df_join(r[1]);
+  r2 = df_join(r[2]);
 }
 
 // row j of S^T written to out[perm[j]]
-__device__ __forceinline__ void spmv_st_row(const Dev& d, const double* y, double* out, int j, int lane) {
+__device__ __forceinline__ void spmv_st_row(const Dev& d, const float2* y, double* out, int j, int lane) {
   double a0, a1, a2;
   spmv_st_sum(d, y, j, lane, a0, a1, a2);
   if (lane == 0) {
@@ -330,6 +363,124 @@ __device__ __forceinline__ void aa_item(const Dev& d, int v, const AAView& a, do
   }
 }
 
+// (G + reg I) gamma = rhs for NC columns, reg = max(1e-6 tr(G) / NC, 1e-12),
+// by mixed-precision iterative refinement (Wilkinson; Moler 1967): an FP32
+// Cholesky factor of the trace-normalised matrix and three passes with FP64
+// residuals. Sizes are compile-time, so every array lives in registers
+// (one thread runs this; a dependent chain through local memory, or an FP64
+// factorisation at this part's FP64 rate, costs several microseconds).
+// Returns false on a non-positive pivot; gn = ||gamma||^2.
+template <int NC>
+__device__ __forceinline__ bool aa_solve(const double* G, const double* rhs, double* gam, double& gn) {
+  static_assert(NC >= 1 && NC <= kMaxAA, "window");
+  double tr = 0.0;
+#pragma unroll
+  for (int j = 0; j < NC; ++j) tr += G[j * kMaxAA + j];
+  const double reg = fmax(1e-6 * tr * (1.0 / NC), 1e-12);
+  const float sc = 1.0f / (float)(tr + NC * reg);
+  float L[NC][NC], ipiv[NC];
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    float t = (float)(G[j * kMaxAA + j] + reg) * sc;
+#pragma unroll
+    for (int k = 0; k < j; ++k) t -= L[j][k] * L[j][k];
+    ok = ok && t > 0.0f;
+    const float r = sqrtf(fmaxf(t, 1e-30f));
+    ipiv[j] = 1.0f / r;
+#pragma unroll
+    for (int i = j + 1; i < NC; ++i) {
+      float u = (float)G[i * kMaxAA + j] * sc;
+#pragma unroll
+      for (int k = 0; k < j; ++k) u -= L[i][k] * L[j][k];
+      L[i][j] = u * ipiv[j];
+    }
+    L[j][j] = r;
+  }
+  double g[NC];
+#pragma unroll
+  for (int i = 0; i < NC; ++i) g[i] = 0.0;
+  if (!ok) return false;
+#pragma unroll
+  for (int pass = 0; pass < 3; ++pass) {
+    double res[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {   // residual in FP64 (rows independent)
+      double r = rhs[i] - reg * g[i];
+#pragma unroll
+      for (int j = 0; j < NC; ++j) r -= G[i * kMaxAA + j] * g[j];
+      res[i] = r;
+    }
+    float y[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {   // forward solve in FP32
+      float u = (float)res[i] * sc;
+#pragma unroll
+      for (int k = 0; k < i; ++k) u -= L[i][k] * y[k];
+      y[i] = u * ipiv[i];
+    }
+#pragma unroll
+    for (int i = NC - 1; i >= 0; --i) {   // backward solve
+      float u = y[i];
+#pragma unroll
+      for (int k = i + 1; k < NC; ++k) u -= L[k][i] * y[k];
+      y[i] = u * ipiv[i];
+    }
+#pragma unroll
+    for (int i = 0; i < NC; ++i) g[i] += (double)y[i];
+  }
+  gn = 0.0;
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    gn += g[i] * g[i];
+    gam[i] = g[i];
+  }
+  return true;
+}
+
+// the same solve for a window size known only at run time (NC > 5: unrolled
+// copies of those sizes would not fit the persistent kernels' registers)
+__device__ __forceinline__ bool aa_solve_any(int nc, const double* G, const double* rhs, double* gam, double& gn) {
+  double tr = 0.0;
+  for (int j = 0; j < nc; ++j) tr += G[j * kMaxAA + j];
+  const double reg = fmax(1e-6 * tr / nc, 1e-12);
+  const float sc = 1.0f / (float)(tr + nc * reg);
+  float L[kMaxAA * kMaxAA], ipiv[kMaxAA];
+  for (int j = 0; j < nc; ++j) {
+    float t = (float)(G[j * kMaxAA + j] + reg) * sc;
+    for (int k = 0; k < j; ++k) t -= L[j * kMaxAA + k] * L[j * kMaxAA + k];
+    if (!(t > 0.0f)) return false;
+    const float r = sqrtf(t);
+    ipiv[j] = 1.0f / r;
+    for (int i = j + 1; i < nc; ++i) {
+      float u = (float)G[i * kMaxAA + j] * sc;
+      for (int k = 0; k < j; ++k) u -= L[i * kMaxAA + k] * L[j * kMaxAA + k];
+      L[i * kMaxAA + j] = u * ipiv[j];
+    }
+    L[j * kMaxAA + j] = r;
+  }
+  for (int i = 0; i < nc; ++i) gam[i] = 0.0;
+  for (int pass = 0; pass < 3; ++pass) {
+    float y[kMaxAA];
+    for (int i = 0; i < nc; ++i) {
+      double r = rhs[i] - reg * gam[i];
+      for (int j = 0; j < nc; ++j) r -= G[i * kMaxAA + j] * gam[j];
+      float u = (float)r * sc;
+      for (int k = 0; k < i; ++k) u -= L[i * kMaxAA + k] * y[k];
+      y[i] = u * ipiv[i];
+    }
+    for (int i = nc - 1; i >= 0; --i) {
+      float u = y[i];
+      for (int k = i + 1; k < nc; ++k) u -= L[k * kMaxAA + i] * y[k];
+      y[i] = u * ipiv[i];
+    }
+    for (int i = 0; i < nc; ++i) gam[i] += (double)y[i];
+  }
+  gn = 0.0;
+  for (int i = 0; i < nc; ++i) gn += gam[i] * gam[i];
+  return true;
+}
+
 // Gram update, regularised normal equations, reliability guard (eq. aa_gamma)
 template <class St>
 __device__ __forceinline__ void aa_finish(const Dev& d, St* c, const AAView& a, const double* s) {
@@ -348,54 +499,16 @@ __device__ __forceinline__ void aa_finish(const Dev& d, St* c, const AAView& a, 
   c->pairs = c->pairs < m + 1 ? c->pairs + 1 : m + 1;
   const int nc = c->ncols;
   if (nc < 1) return;
-  // (G + reg I) gamma = dG^T g with reg = max(1e-6 tr(G) / nc, 1e-12), solved by
-  // mixed-precision iterative refinement (Wilkinson; Moler 1967): an FP32
-  // Cholesky factor of the trace-normalised matrix and FP64 residuals. A
-  // single-thread FP64 factorisation costs several microseconds on this part.
-  const double inv_n[kMaxAA + 1] = {0.0, 1.0, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 5, 1.0 / 6, 1.0 / 7, 1.0 / 8};
-  double tr = 0.0;
-  for (int j = 0; j < nc; ++j) tr += c->gram[j * kMaxAA + j];
-  const double reg = fmax(1e-6 * tr * inv_n[nc], 1e-12);
-  const float sc = 1.0f / (float)(tr + nc * reg);
-  float L[kMaxAA * kMaxAA], ipiv[kMaxAA];
-  bool ok = true;
-  for (int j = 0; j < nc && ok; ++j) {
-    float t = (float)(c->gram[j * kMaxAA + j] + reg) * sc;
-    for (int k2 = 0; k2 < j; ++k2) t -= L[j * kMaxAA + k2] * L[j * kMaxAA + k2];
-    if (!(t > 0.0f)) {
-      ok = false;
-      break;
-    }
-    const float r = sqrtf(t);
-    ipiv[j] = 1.0f / r;
-    for (int i = j + 1; i < nc; ++i) {
-      float u = (float)c->gram[i * kMaxAA + j] * sc;
-      for (int k2 = 0; k2 < j; ++k2) u -= L[i * kMaxAA + k2] * L[j * kMaxAA + k2];
-      L[i * kMaxAA + j] = u * ipiv[j];
-    }
-    L[j * kMaxAA + j] = r;
-  }
-  double gam[kMaxAA];
-  for (int i = 0; i < nc; ++i) gam[i] = 0.0;
+  double* gam = c->gamma;   // read only when the guard accepts it
   double gn = 0.0;
-  if (ok) {
-    for (int pass = 0; pass < 3; ++pass) {
-      float y[kMaxAA];
-      for (int i = 0; i < nc; ++i) {  // residual in FP64, forward solve in FP32
-        double r = s[kMaxAA + i] - reg * gam[i];
-        for (int j = 0; j < nc; ++j) r -= c->gram[i * kMaxAA + j] * gam[j];
-        float u = (float)r * sc;
-        for (int k2 = 0; k2 < i; ++k2) u -= L[i * kMaxAA + k2] * y[k2];
-        y[i] = u * ipiv[i];
-      }
-      for (int i = nc - 1; i >= 0; --i) {
-        float u = y[i];
-        for (int k2 = i + 1; k2 < nc; ++k2) u -= L[k2 * kMaxAA + i] * y[k2];
-        y[i] = u * ipiv[i];
-      }
-      for (int i = 0; i < nc; ++i) gam[i] += (double)y[i];
-    }
-    for (int i = 0; i < nc; ++i) gn += gam[i] * gam[i];
+  bool ok;
+  switch (nc) {
+    case 1: ok = aa_solve<1>(c->gram, s + kMaxAA, gam, gn); break;
+    case 2: ok = aa_solve<2>(c->gram, s + kMaxAA, gam, gn); break;
+    case 3: ok = aa_solve<3>(c->gram, s + kMaxAA, gam, gn); break;
+    case 4: ok = aa_solve<4>(c->gram, s + kMaxAA, gam, gn); break;
+    case 5: ok = aa_solve<5>(c->gram, s + kMaxAA, gam, gn); break;
+    default: ok = aa_solve_any(nc, c->gram, s + kMaxAA, gam, gn); break;
   }
   if (!ok || !(gn <= 100.0)) {  // reliability guard ||gamma||_2 > 10: take q_hat, clear the history
     c->resets += 1;
@@ -404,7 +517,6 @@ __device__ __forceinline__ void aa_finish(const Dev& d, St* c, const AAView& a, 
     c->head = 0;
     for (int i = 0; i < kMaxAA * kMaxAA; ++i) c->gram[i] = 0.0;
   } else {
-    for (int i = 0; i < nc; ++i) c->gamma[i] = gam[i];
     c->use_hat = 0;
   }
 }

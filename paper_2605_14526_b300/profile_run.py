@@ -74,6 +74,8 @@ def main():
         p = binding.pd_get_profile(pd.ctx)
         print("forward phases (ms): " + ", ".join(f"{n} {p.phase_ms[i]:.3f}" for i, n in enumerate(names)))
         print("  block-0 work (ms): " + ", ".join(f"{n} {p.work_ms[i]:.3f}" for i, n in enumerate(names)))
+        print("  critical-block work (ms): " + ", ".join(f"{n} {p.work_max_ms[i]:.3f}" for i, n in enumerate(names)))
+        print("  to last arrival (ms): " + ", ".join(f"{n} {p.last_ms[i]:.3f}" for i, n in enumerate(names)))
     st = binding.pd_get_stats(pd.ctx)
     print(f"{args.case}: {st.iters_total} forward iterations, {st.adj_iters_total} adjoint iterations, "
           f"{st.launches} launches")

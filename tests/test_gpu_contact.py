@@ -16,7 +16,10 @@ pytestmark = pytest.mark.gpu
 
 
 def _pad(steps=2):
-    return inputs.contact_pad(nx=8, ny=8, nz=5, footprint=4, steps=steps, box_steps=6, travel=0.004, E_core=1e6)
+    # seed 27: every contact of both steps is well inside its active set
+    # (checked on the oracle's solution in the adjoint test)
+    return inputs.contact_pad(nx=8, ny=8, nz=5, footprint=4, steps=steps, box_steps=6, travel=0.004, E_core=1e6,
+                              seed=27)
 
 
 @pytest.fixture(scope="module")
@@ -56,8 +59,33 @@ def test_contact_rollout_fp32_configured_gate_matches_oracle(oracle_pad):
     assert gap.min() >= -1e-6 * np.abs(q[:, 2]).max()
 
 
+def _active_set_margins(sc, recs, cp):
+    """Smallest distance of the oracle's solution to an active-set change:
+    positive normal multipliers relative to the largest, 1 - |lam_f| / (mu
+    lam_n) of the sticking contacts, and the smallest slip of a sliding
+    contact relative to the largest. Near zero, the fixed-active-set adjoint
+    (the derivative of the rollout where the sets do not change) is not
+    defined by the solution, and rounding decides which one-sided derivative
+    a solver returns."""
+    mu = sc.contact.mu
+    out = []
+    for r in recs:
+        ln, lf = r["lam_n"], r["lam_f"]
+        act = ln > 0
+        ratio = np.linalg.norm(lf, axis=1) / np.maximum(mu * ln, 1e-300)
+        stick = act & (ratio < 1 - 1e-9)
+        slide = act & ~stick
+        slip = np.linalg.norm(r["q_next"][cp.verts, :2] - r["q_t"][cp.verts, :2], axis=1)
+        out.append((ln[act].min() / ln.max() if act.any() else 1.0,
+                    1.0 - ratio[stick].max() if stick.any() else 1.0,
+                    slip[slide].min() / slip[slide].max() if slide.any() else 1.0))
+    return np.min(np.array(out), axis=0)
+
+
 def test_contact_adjoint_fp64_matches_oracle(oracle_pad):
     sc, qT_o, recs, cp = oracle_pad
+    m = _active_set_margins(sc, recs, cp)
+    assert np.all(m >= [1e-3, 1e-2, 5e-2]), m
     pb = solver.build_problem(sc)
     g_o = contact.rollout_backward(pb, cp, recs, qT_o - sc.target, np.zeros_like(qT_o))
     code, q, st, pd = _gpu(sc, local_fp32=False, eps_res=1e-10, eps_step=1e-12, k_max=3000)
