@@ -237,14 +237,14 @@ int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_o
   d.inc_ptr = ip; d.inc_idx = ii;
   const size_t nv3 = 3 * (size_t)c->n_v;
   double** vecs[] = {&d.q, &d.qprev, &d.qhat, &d.gprev, &d.qt, &d.qtil, &d.b0, &d.b, &d.bprev, &d.mu, &d.r,
-                     &d.z, &d.pdir, &d.w, &d.qbar, &d.gq, &d.gv, &c->sq, &c->sv};
+                     &d.z, &d.pdir, &d.pdir2, &d.w, &d.qbar, &d.gq, &d.gv, &c->sq, &c->sv};
   for (double** p : vecs)
     if ((r = dalloc(c, p, nv3))) return r;
   if ((r = dalloc(c, &d.bperm, 3 * (size_t)c->n_f)) || (r = dalloc(c, &d.y, 3 * (size_t)c->n_f))) return r;  // float2
   d.sq = c->sq;
   d.sv = c->sv;
   const int m = std::max(c->opt.aa_m, 1);
-  if ((r = dalloc(c, &d.dQ, (size_t)m * nv3)) || (r = dalloc(c, &d.dG, (size_t)m * nv3))) return r;
+  if ((r = dalloc(c, &d.dQG, (size_t)m * nv3)) || (r = dalloc(c, &d.dG, (size_t)m * nv3))) return r;
   double* contrib;
   double* jac;
   double* sstar;
@@ -259,7 +259,7 @@ int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_o
   if ((r = dalloc(c, &d.dw, c->n_e)) || (r = dalloc(c, &d.dbeta, c->n_e))) return r;
   if ((r = dalloc(c, &d.ctrl, 1))) return r;
   CK(cudaMemset(d.ctrl, 0, sizeof(Ctrl)));
-  CK(cudaMemset(d.dQ, 0, sizeof(double) * m * nv3));
+  CK(cudaMemset(d.dQG, 0, sizeof(double) * m * nv3));
   CK(cudaMemset(d.dG, 0, sizeof(double) * m * nv3));
   CK(cudaHostAlloc(&c->h_flag, 2 * sizeof(int), cudaHostAllocDefault));
   CK(cudaEventCreateWithFlags(&c->ev[0], cudaEventDisableTiming));

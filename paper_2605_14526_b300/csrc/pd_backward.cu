@@ -121,8 +121,16 @@ __device__ __forceinline__ void bwd_setup_item(const Dev& d, int e, const double
 }
 
 // corner contributions of K p for one element: coef * G^T (dp/dF) G p
+// the CG direction of this iteration at one coordinate: z + beta p_old
+// (p_old = 0, beta = 0 on the first iteration); the element and the vertex
+// phases of the persistent adjoint both read it through this function
+__device__ __forceinline__ double p_next(const Dev& d, const double* pold, size_t o, double beta) {
+  return __fma_rn(beta, pold[o], d.z[o]);
+}
+
 template <typename T>
-__device__ __forceinline__ void kapply_item(const Dev& d, int e, const double* pv) {
+__device__ __forceinline__ void kapply_item(const Dev& d, int e, const double* pv, const double* pold = nullptr,
+                                            double beta = 0.0) {
   int4 tv;
   T Bm[9], coef;
   load_elem<T>(d, e, tv, Bm, coef);
@@ -134,7 +142,17 @@ __device__ __forceinline__ void kapply_item(const Dev& d, int e, const double* p
     V[i] = r[R_V + i];
   }
   T dF[9];
-  deform<T>(pv, tv, Bm, dF);
+  if (pold) {   // direction formed on the fly (pinned rows of z and p_old are 0)
+    const int id[4] = {tv.x, tv.y, tv.z, tv.w};
+    double xv[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) xv[a][i] = p_next(d, pold, 3 * (size_t)id[a] + i, beta);
+    deform_x<T>(xv, Bm, dF);
+  } else {
+    deform<T>(pv, tv, Bm, dF);
+  }
   T W[9], Mh[9];  // Mh = U^T dF V
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -200,6 +218,7 @@ __device__ __forceinline__ void bwd_init_item(const Dev& d, int v) {
     d.r[o] = qb;
     d.mu[o] = 0.0;
     d.pdir[o] = 0.0;
+    d.pdir2[o] = 0.0;
     d.z[o] = 0.0;
   }
   if (!pin) {
@@ -252,12 +271,43 @@ __device__ __forceinline__ void pcg_w_item(const Dev& d, int v, double* part) {
   }
 }
 
-__device__ __forceinline__ void pcg_r_item(const Dev& d, int v, double alpha) {
+// persistent adjoint, one warp per vertex: p = z + beta p_old stored to
+// pnew, w = A p - K p (lanes over the row of A and the incident corners, a
+// fixed shuffle tree), partial p . w
+template <typename T>
+__device__ __forceinline__ void pcg_w_warp(const Dev& d, int v, const double* pold, double* pnew, double beta, int lane,
+                                           double* part) {
+  if (d.pinned[v]) return;
+  const T* cb = reinterpret_cast<const T*>(d.contrib);
+  double c[3] = {0.0, 0.0, 0.0};
+  for (int p = d.A_ptr[v] + lane; p < d.A_ptr[v + 1]; p += 32) {
+    const int u = d.A_idx[p];
+    const double a = d.A_val[p];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) c[i] += a * p_next(d, pold, 3 * (size_t)u + i, beta);
+  }
+  for (int p = d.inc_ptr[v] + lane; p < d.inc_ptr[v + 1]; p += 32) {
+    const int ic = d.inc_idx[p];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) c[i] -= (double)cb[3 * (size_t)ic + i];
+  }
+  int i;
+  const double w = warp_sum_scatter<3>(c, lane, i);   // component i in lanes 8i .. 8i+7
+  if ((lane & 7) != 0 || i >= 3) return;
+  const size_t o = 3 * (size_t)v + i;
+  const double pn = p_next(d, pold, o, beta);
+  pnew[o] = pn;
+  d.w[o] = w;
+  part[0] += pn * w;
+}
+
+__device__ __forceinline__ void pcg_r_item(const Dev& d, int v, double alpha, const double* pdir = nullptr) {
   if (d.pinned[v]) return;
   const int pos = d.iperm[v];
+  const double* pd = pdir ? pdir : d.pdir;
   for (int i = 0; i < 3; ++i) {
     const size_t o = 3 * (size_t)v + i;
-    d.mu[o] += alpha * d.pdir[o];
+    d.mu[o] += alpha * pd[o];
     const double rn = d.r[o] - alpha * d.w[o];
     d.r[o] = rn;
     d.bperm[3 * (size_t)pos + i] = df_split(rn);
@@ -642,39 +692,55 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
     for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, d.s_part, d.s_cnt, sg, lane);
     if (!(ok = grid_sync(d, tm))) break;
     if (ck && !(ok = project(ck))) break;
-    for (int j = gwarp; j < d.n_f; j += nwarps) spmv_st_row(d, d.y, d.z, j, lane);
-    if (!(ok = grid_sync(d, tm))) break;
+    // S^T y row by row with the partial r . z of the row fused in (first
+    // direction p = z: beta = 0 and p_old = 0 on the first iteration)
+    auto st_rz = [&](double* prz) {
+      for (int j = gwarp; j < d.n_f; j += nwarps) {
+        double a0, a1, a2;
+        spmv_st_sum(d, d.y, j, lane, a0, a1, a2);
+        if (lane < 3) {
+          const size_t o = 3 * (size_t)d.perm[j] + lane;
+          const double zv = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
+          d.z[o] = zv;
+          prz[0] += d.r[o] * zv;
+        }
+      }
+    };
     double p1[1] = {0.0};
-    for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) init_z_item(d, v, p1);
+    st_rz(p1);
     if (!(ok = grid_reduce<1>(d, tm, p1, sums))) break;
-    if (tid == 0) init_z_finish(&S, sums);
+    if (tid == 0) {
+      init_z_finish(&S, sums);
+      S.beta = 0.0;
+    }
     __syncthreads();
-    while (!S.adj_done) {
-      for (int e = re.lo + tid; e < re.hi; e += blockDim.x) kapply_item<T>(d, e, d.pdir);
+    // one CG iteration: K p (elements, p formed on the fly) | p stored, w = A p
+    // - K p, p . w | r, mu, b | S b | S^T y, r . z; the directions alternate
+    // between two buffers so that the owners can store p while the
+    // neighbours still read p_old
+    for (int it = 0; !S.adj_done; ++it) {
+      const double beta = S.beta;
+      const double* pold = (it & 1) ? d.pdir2 : d.pdir;
+      double* pnew = (it & 1) ? d.pdir : d.pdir2;
+      for (int e = re.lo + tid; e < re.hi; e += blockDim.x) kapply_item<T>(d, e, nullptr, pold, beta);
       if (!(ok = grid_sync(d, tm))) break;
       double pw[1] = {0.0};
-      for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) pcg_w_item<T>(d, v, pw);
+      for (int v = rv.lo + (tid >> 5); v < rv.hi; v += blockDim.x >> 5) pcg_w_warp<T>(d, v, pold, pnew, beta, lane, pw);
       if (!(ok = grid_reduce<1>(d, tm, pw, sums))) break;
       if (tid == 0) pcg_w_finish(&S, sums);
       __syncthreads();
       if (S.adj_done) break;
       const double alpha = S.alpha;
-      for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) pcg_r_item(d, v, alpha);
+      for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) pcg_r_item(d, v, alpha, pnew);
       if (!(ok = grid_sync(d, tm))) break;
       for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, d.s_part, d.s_cnt, sg, lane);
       if (!(ok = grid_sync(d, tm))) break;
       if (ck && !(ok = project(ck))) break;
-      for (int j = gwarp; j < d.n_f; j += nwarps) spmv_st_row(d, d.y, d.z, j, lane);
-      if (!(ok = grid_sync(d, tm))) break;
       double prz[1] = {0.0};
-      for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) pcg_z_item(d, v, prz);
+      st_rz(prz);
       if (!(ok = grid_reduce<1>(d, tm, prz, sums))) break;
       if (tid == 0) pcg_z_finish(d, &S, sums);
       __syncthreads();
-      if (S.adj_done) break;
-      const double beta = S.beta;
-      for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) pcg_p_item(d, v, beta);
-      if (!(ok = grid_sync(d, tm))) break;
     }
     if (!ok) break;
     double* df_t = a.df ? (a.df_stride ? a.df + (size_t)t * nv3 : a.df) : nullptr;

@@ -141,6 +141,20 @@ __device__ __forceinline__ void deform(const double* __restrict__ x, int4 tv, co
     for (int j = 0; j < 3; ++j) F[3 * i + j] = D[3 * i] * Bm[j] + D[3 * i + 1] * Bm[3 + j] + D[3 * i + 2] * Bm[6 + j];
 }
 
+// the same from the four vertex positions already loaded
+template <typename T>
+__device__ __forceinline__ void deform_x(const double (&xv)[4][3], const T* Bm, T* F) {
+  T D[9];
+#pragma unroll
+  for (int a = 1; a < 4; ++a)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) D[3 * i + a - 1] = (T)(xv[a][i] - xv[0][i]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) F[3 * i + j] = D[3 * i] * Bm[j] + D[3 * i + 1] * Bm[3 + j] + D[3 * i + 2] * Bm[6 + j];
+}
+
 // c_a = coef * P gradN_a for a = 1..3, c_0 = -(c_1 + c_2 + c_3)
 template <typename T>
 __device__ __forceinline__ void corner_forces(const T* P, const T* Bm, T coef, T* out12) {

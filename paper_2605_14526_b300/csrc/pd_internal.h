@@ -142,7 +142,7 @@ struct Dev {
   double* bprev;
   float2* bperm;    // [n_f][3] b in elimination order (double-float)
   float2* y;        // [n_f][3] S b (double-float)
-  double* dQ;       // [kMaxAA][n_v][3]
+  double* dQG;      // [kMaxAA][n_v][3] history sums dQ_j + dG_j
   double* dG;
   void* contrib;    // [n_e][12] float or double
   void* sstar;      // [n_e][3] float: last prox stretches (Newton warm start; <= 0 = none)
@@ -177,6 +177,7 @@ struct Dev {
   double* r;        // residual
   double* z;        // preconditioned residual
   double* pdir;     // search direction
+  double* pdir2;    // second buffer of the direction (persistent adjoint: old / new alternate)
   double* w;        // (A - K) p
   double* qbar;     // gradient on q*
   double* gq;       // running dL/dq_t

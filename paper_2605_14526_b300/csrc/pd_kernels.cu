@@ -37,9 +37,9 @@ template <typename T>
 __global__ void __launch_bounds__(kVtxBlock) k_assemble(Dev d) {
   if (d.ctrl->done) return;
   const int k = d.ctrl->k;
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // warp per vertex
   double part[3] = {0.0, 0.0, 0.0};
-  if (v < d.n_v) assemble_item<T>(d, v, k, part);
+  if (v < d.n_v) assemble_warp<T>(d, v, k, part, threadIdx.x & 31);
   block_reduce_store<3>(part, d.red, blockIdx.x);
   if (last_block(&d.ctrl->ticket[TK_ASSEMBLE]) && threadIdx.x == 0) {
     double s[3];
@@ -164,10 +164,10 @@ void launch_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
   if (ev) cudaEventRecord(ev[0], s);
   if (d.local_fp32) {
     k_local<float><<<nblk(d.n_e, kTetBlock), kTetBlock, 0, s>>>(d, d.q);
-    k_assemble<float><<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
+    k_assemble<float><<<nblk(32 * d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
   } else {
     k_local<double><<<nblk(d.n_e, kTetBlock), kTetBlock, 0, s>>>(d, d.q);
-    k_assemble<double><<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
+    k_assemble<double><<<nblk(32 * d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
   }
   if (ev) {
     cudaEventRecord(ev[1], s);
@@ -186,7 +186,7 @@ void launch_step_end(const Dev& d, cudaStream_t s, double* qn, double* vn, doubl
 }
 
 int max_reduction_blocks(int n_v, int n_e) {
-  int a = nblk(n_v, kVtxBlock), b = nblk(n_e + n_v, kVtxBlock), c = nblk(n_e, kTetBlock);
+  int a = nblk(32 * n_v, kVtxBlock), b = nblk(n_e + n_v, kVtxBlock), c = nblk(n_e, kTetBlock);
   int m = a > b ? a : b;
   return m > c ? m : c;
 }

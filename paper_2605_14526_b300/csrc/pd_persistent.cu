@@ -34,12 +34,12 @@ __device__ __forceinline__ void local_any(const Dev& d, int e, bool hi) {
   }
 }
 template <typename T>
-__device__ __forceinline__ void assemble_any(const Dev& d, int v, int k, double* part, bool hi) {
+__device__ __forceinline__ void assemble_any(const Dev& d, int v, int k, double* part, bool hi, int lane) {
   if constexpr (sizeof(T) == 4) {
-    if (hi) assemble_item<double>(d, v, k, part);
-    else assemble_item<float>(d, v, k, part);
+    if (hi) assemble_warp<double>(d, v, k, part, lane);
+    else assemble_warp<float>(d, v, k, part, lane);
   } else {
-    assemble_item<T>(d, v, k, part);
+    assemble_warp<T>(d, v, k, part, lane);
   }
 }
 
@@ -125,7 +125,7 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
         if (!(ok = grid_sync(d, tm))) break;
         mark(PH_LOCAL);
         double p5[5] = {0.0, 0.0, 0.0, pu[0], pu[1]};
-        for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) assemble_any<T>(d, v, k, p5, hi);
+        for (int v = rv.lo + (tid >> 5); v < rv.hi; v += blockDim.x >> 5) assemble_any<T>(d, v, k, p5, hi, lane);
         work_done(PH_ASSEMBLE);
         if (!(ok = grid_reduce<5>(d, tm, p5, sums))) break;
         if (tid == 0) assemble_finish(d, &S, k, sums, true);
@@ -191,11 +191,10 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
         __syncthreads();
         mark(PH_AA);        // the small Anderson solve
         const int use_hat = S.use_hat, nc = S.ncols;
-        double gam[kMaxAA];
-#pragma unroll
-        for (int j = 0; j < kMaxAA; ++j) gam[j] = j < nc ? S.gamma[j] : 0.0;
         pu[0] = pu[1] = 0.0;
-        for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) update_item(d, v, use_hat, nc, gam, pu);
+        // one thread per free coordinate of the block's vertices
+        for (int x = 3 * rv.lo + tid; x < 3 * rv.hi; x += blockDim.x)
+          if (!d.pinned[x / 3]) update_comp(d, (size_t)x, use_hat, nc, S.gamma, pu);
         work_done(PH_UPDATE);
         if (!(ok = grid_sync(d, tm))) break;
         if (tid == 0) update_count(d, &S);

@@ -74,6 +74,20 @@ __device__ __forceinline__ void step_begin_item(const Dev& d, int v, const doubl
   }
 }
 
+// q^{k+1} of one coordinate of a free vertex: q_hat - sum_j gamma_j (dQ_j +
+// dG_j), or q_hat when the guard rejected gamma; the history keeps the sums
+// dQ_j + dG_j (dQG), the only form in which the update uses dQ
+__device__ __forceinline__ double next_iterate(const Dev& d, size_t o, int use_hat, int nc, const double* gam) {
+  double qn = d.qhat[o];
+  if (!use_hat) {
+    const size_t nv3 = 3 * (size_t)d.n_v;
+#pragma unroll
+    for (int j = 0; j < kMaxAA; ++j)
+      if (j < nc) qn = __fma_rn(-gam[j], d.dQG[j * nv3 + o], qn);
+  }
+  return qn;
+}
+
 // ------------------------------------------------------------ local step
 
 // Local step fused with the per-element part of the RHS scatter (Alg. 1,
@@ -112,23 +126,34 @@ __device__ __forceinline__ void local_item(const Dev& d, int e, const double* x)
 }
 
 // b^k = b0 + sum of corner contributions (FP64) in vertex order and in
-// elimination order; partials ||b^k - b^{k-1}||^2, ||b^{k-1}||^2, non-finite
+// elimination order (double-float); partials ||b^k - b^{k-1}||^2,
+// ||b^{k-1}||^2, non-finite. One warp per vertex: lanes take the incident
+// corners, a fixed shuffle tree adds them, and the lane holding component i
+// finishes it.
 template <typename T>
-__device__ __forceinline__ void assemble_item(const Dev& d, int v, int k, double* part) {
+__device__ __forceinline__ void assemble_warp(const Dev& d, int v, int k, double* part, int lane) {
   if (d.pinned[v]) return;
-  double acc[3] = {d.b0[3 * v], d.b0[3 * v + 1], d.b0[3 * v + 2]};
-  gather_contrib<T>(d, v, acc);
-  const int pos = d.iperm[v];
-  for (int i = 0; i < 3; ++i) {
-    const double bp = d.bprev[3 * v + i];
-    if (k > 0) {
-      part[0] += (acc[i] - bp) * (acc[i] - bp);
-      part[1] += bp * bp;
-    }
-    d.b[3 * v + i] = acc[i];
-    d.bperm[3 * (size_t)pos + i] = df_split(acc[i]);
+  const T* cb = reinterpret_cast<const T*>(d.contrib);
+  const int beg = d.inc_ptr[v], end = d.inc_ptr[v + 1];
+  double c[3] = {0.0, 0.0, 0.0};
+  for (int p = beg + lane; p < end; p += 32) {
+    const int ic = d.inc_idx[p];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) c[i] += (double)cb[3 * (size_t)ic + i];
   }
-  if (!finite3(acc[0], acc[1], acc[2])) part[2] += 1.0;
+  int i;
+  const double sum = warp_sum_scatter<3>(c, lane, i);   // component i in lanes 8i .. 8i+7
+  if ((lane & 7) != 0 || i >= 3) return;
+  const size_t o = 3 * (size_t)v + i;
+  const double acc = d.b0[o] + sum;
+  const double bp = d.bprev[o];
+  if (k > 0) {
+    part[0] += (acc - bp) * (acc - bp);
+    part[1] += bp * bp;
+  }
+  d.b[o] = acc;
+  d.bperm[3 * (size_t)d.iperm[v] + i] = df_split(acc);
+  if (!isfinite(acc)) part[2] += 1.0;
 }
 
 __device__ __forceinline__ double gate_rhs(double eps, double b2, double abs_tol) {
@@ -342,7 +367,7 @@ __device__ __forceinline__ void aa_component(const Dev& d, size_t o, double qh, 
   if (a.add) {
     dg_new = g - d.gprev[o];
     d.dG[a.slot * nv3 + o] = dg_new;
-    d.dQ[a.slot * nv3 + o] = q - d.qprev[o];
+    d.dQG[a.slot * nv3 + o] = __dadd_rn(q - d.qprev[o], dg_new);
   }
   d.gprev[o] = g;
 #pragma unroll
@@ -522,23 +547,20 @@ __device__ __forceinline__ void aa_finish(const Dev& d, St* c, const AAView& a, 
 }
 
 // q^{k+1} = q_hat - (dQ + dG) gamma (or q_hat); step-norm partials
+__device__ __forceinline__ void update_comp(const Dev& d, size_t o, int use_hat, int nc, const double* gam,
+                                            double* part) {
+  const double qn = next_iterate(d, o, use_hat, nc, gam);
+  const double qo = d.q[o];
+  part[0] += (qn - qo) * (qn - qo);
+  part[1] += qo * qo;
+  d.qprev[o] = qo;
+  d.q[o] = qn;
+  d.bprev[o] = d.b[o];
+}
+
 __device__ __forceinline__ void update_item(const Dev& d, int v, int use_hat, int nc, const double* gam, double* part) {
   if (d.pinned[v]) return;
-  const size_t nv3 = 3 * (size_t)d.n_v;
-  for (int i = 0; i < 3; ++i) {
-    const size_t o = 3 * (size_t)v + i;
-    double qn = d.qhat[o];
-    if (!use_hat)
-#pragma unroll
-      for (int j = 0; j < kMaxAA; ++j)
-        if (j < nc) qn -= gam[j] * (d.dQ[j * nv3 + o] + d.dG[j * nv3 + o]);
-    const double qo = d.q[o];
-    part[0] += (qn - qo) * (qn - qo);
-    part[1] += qo * qo;
-    d.qprev[o] = qo;
-    d.q[o] = qn;
-    d.bprev[o] = d.b[o];
-  }
+  for (int i = 0; i < 3; ++i) update_comp(d, 3 * (size_t)v + i, use_hat, nc, gam, part);
 }
 
 template <class St>
