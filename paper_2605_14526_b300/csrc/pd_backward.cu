@@ -816,6 +816,7 @@ __global__ void __launch_bounds__(kPersistBlock, 2) k_bwd_rollout(const Dev* __r
     a.df_stride = br.df_stride;
     a.ckpt = sd.ckpt;
     sa = a;
+    team_red_count() = 0;
   }
   __syncthreads();
   bwd_rollout_body<T>(sd, sa, Team{tb.y, tb.z});

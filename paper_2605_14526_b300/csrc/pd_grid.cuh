@@ -1,8 +1,9 @@
-// Grid-wide synchronisation of the persistent kernels (cooperative launch).
-// Barrier: acq_rel arrival counter + release/acquire generation word; every
-// wait is bounded (status bit 4 on timeout, the caller returns). Reduction
-// barrier: the last block to arrive adds the per-block partials in a fixed
-// order and publishes the sums to every block (deterministic).
+// Team-wide synchronisation of the persistent kernels (cooperative launch).
+// Barrier: a monotonic arrival counter (release RMW per block, acquire
+// polling); every wait is bounded (status bit 4 on timeout, the caller
+// returns). Reduction: every block stores its partials, passes the barrier
+// and adds all the team's partials itself in a fixed order (deterministic,
+// the same sums in every block).
 #pragma once
 #include "pd_common.cuh"
 
@@ -10,23 +11,6 @@ namespace pdk {
 
 constexpr unsigned int kSpinLimit = 1u << 22;   // polls (~0.4 us each with the sleep): ~2 s per wait at most
 constexpr int kStatusTimeout = 4;
-
-__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int* p, unsigned int v) {
-  unsigned int old;
-  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
-}
-__device__ __forceinline__ void red_release(unsigned int* p, unsigned int v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ void st_relaxed(unsigned int* p, unsigned int v) {
-  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
@@ -41,71 +25,146 @@ struct Team {
   int b, nb;
 };
 
+__device__ __forceinline__ unsigned long long atom_add_release64(unsigned long long* p, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.release.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned long long atom_add_acq_rel64(unsigned long long* p, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void st_release64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Arrival and wait of thread 0 at a team barrier: the arrival counter only
+// grows, so arrival number n belongs to the barrier n / nb, which opens when
+// the counter reaches (n / nb + 1) nb. Each arrival is a release RMW and the
+// wait an acquire load that reads the last of them, so the waiter sees every
+// write the team made before arriving. Bounded: status bit 4 on timeout.
+__device__ __forceinline__ bool team_arrive_wait(const Dev& d, Team tm) {
+  Ctrl* c = d.ctrl;
+  const unsigned long long n = atom_add_release64(&c->bar_arrive, 1ull);
+  const unsigned long long open = (n / (unsigned long long)tm.nb + 1ull) * (unsigned long long)tm.nb;
+  if (d.prof && n + 1 == open) c->t_last = gtimer();   // profiling: the last arrival
+  unsigned int it = 0;
+  while (ld_acquire64(&c->bar_arrive) < open) {
+    if (++it > kSpinLimit) {
+      atomicOr(&c->status, kStatusTimeout);
+      return false;
+    }
+    __nanosleep(32);
+  }
+  return true;
+}
+
+// reduction count of this block (one shared word for every reduction of the
+// kernel); thread 0 sets it to 0 at kernel start
+__device__ __forceinline__ int& team_red_count() {
+  __shared__ int n;
+  return n;
+}
+
 // Team barrier; with NV > 0 also a sum over the team's blocks of NV partial
-// values per block, returned in `sums` (shared) to every block. Returns false
-// in every thread of the block if the wait timed out. A one-block team needs
-// no global memory traffic at all.
+// values per block, returned in `sums` (shared) to every block, identical in
+// every block (fixed order). Returns false in every thread of the block if a
+// wait timed out. A one-block team needs no global memory traffic at all.
+// Partial rows live in buffer `parity`, which alternates between
+// consecutive reductions, so a block already at the next reduction cannot
+// overwrite rows that a slower block is still reading.
+//  - NV < kPublishMin: each block stores its row in kRedRep copies, passes
+//    the barrier and adds all rows itself (copy b mod kRedRep): no second
+//    round trip for a result.
+//  - NV >= kPublishMin: the block that arrives last adds the rows and
+//    publishes the sums with a release store of the barrier's number; the
+//    others wait for that number and read the sums (every block reading
+//    every long row costs more than the extra round trip).
+constexpr int kPublishMin = 8;
+
 template <int NV>
 __device__ __forceinline__ bool grid_reduce(const Dev& d, Team tm, double (&part)[NV > 0 ? NV : 1], double* sums) {
-  __shared__ int s_last, s_fail;
-  __shared__ unsigned long long s_tarr;
+  static_assert(NV <= kRedTeam, "values per team reduction");
+  __shared__ int s_fail, s_last;
+  __shared__ unsigned long long s_open;
+  int& s_parity = team_red_count();
   if (tm.nb == 1) {
     if constexpr (NV > 0) block_reduce_to<NV>(part, sums);
     else __syncthreads();
     return true;
   }
-  if constexpr (NV > 0) block_reduce_store<NV>(part, d.red, tm.b);
-  __syncthreads();
-  Ctrl* c = d.ctrl;
-  if (threadIdx.x == 0) {
-    const unsigned int g = ld_acquire(&c->bar_gen);
-    const unsigned int arrived = atom_add_acq_rel(&c->bar_count, 1u);
-    s_last = arrived == (unsigned int)tm.nb - 1;
-    if (d.prof && s_last) s_tarr = gtimer();
-    s_fail = 0;
-    if (!s_last) {
-      unsigned int it = 0;
-      while (ld_acquire(&c->bar_gen) == g) {
-        if (++it > kSpinLimit) {
-          atomicOr(&c->status, kStatusTimeout);
-          s_fail = 1;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
+  constexpr bool publish = NV >= kPublishMin;
+  constexpr int reps = publish ? 1 : kRedRep;
+  const int par = s_parity & 1;
+  if constexpr (NV > 0) {
+    const double v = block_sum_lane<NV>(part);   // threads < NV hold the block's sums
+    if (threadIdx.x < NV)
+#pragma unroll
+      for (int r = 0; r < reps; ++r)
+        d.red[((size_t)(par * kRedRep + r) * kRedRows + tm.b) * kRedTeam + threadIdx.x] = v;
   }
   __syncthreads();
-  double* pub = d.red + (size_t)(kRedRows - 1) * kRed;   // published sums
-  if (s_last) {
-    if constexpr (NV > 0) {
-      // thread t adds the partials of blocks t, t + blockDim.x, ... (all NV
-      // values of a block loaded at once, independent loads), then a fixed
-      // shuffle/shared-memory tree: deterministic, ~2 L2 round trips
+  Ctrl* c = d.ctrl;
+  if constexpr (!publish) {
+    if (threadIdx.x == 0) s_fail = team_arrive_wait(d, tm) ? 0 : 1;
+    __syncthreads();
+  } else {
+    if (threadIdx.x == 0) {
+      const unsigned long long n = atom_add_acq_rel64(&c->bar_arrive, 1ull);
+      const unsigned long long open = (n / (unsigned long long)tm.nb + 1ull) * (unsigned long long)tm.nb;
+      if (d.prof && n + 1 == open) c->t_last = gtimer();
+      s_last = n + 1 == open;
+      s_open = open;
+      s_fail = 0;
+      if (!s_last) {
+        unsigned int it = 0;
+        while (ld_acquire64(&c->pub_open) < open) {
+          if (++it > kSpinLimit) {
+            atomicOr(&c->status, kStatusTimeout);
+            s_fail = 1;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // every thread read `par` before the barrier's __syncthreads; the
+  // increment is visible after the next one (each path below has one)
+  if (NV > 0 && threadIdx.x == 0) s_parity += 1;
+  if constexpr (NV > 0) {
+    double* pub = d.red + (size_t)(2 * kRedRep * kRedRows) * kRedTeam + par * kRedTeam;   // published sums
+    if (!publish || s_last) {
+      const double* rows = d.red + (size_t)(par * kRedRep + (publish ? 0 : tm.b % kRedRep)) * kRedRows * kRedTeam;
       double acc[NV];
 #pragma unroll
       for (int j = 0; j < NV; ++j) acc[j] = 0.0;
-#pragma unroll 4
+#pragma unroll 2
       for (int b = threadIdx.x; b < tm.nb; b += blockDim.x) {
         double v[NV];
 #pragma unroll
-        for (int j = 0; j < NV; ++j) v[j] = __ldcg(&d.red[(size_t)b * kRed + j]);
+        for (int j = 0; j < NV; ++j) v[j] = __ldcg(&rows[(size_t)b * kRedTeam + j]);
 #pragma unroll
         for (int j = 0; j < NV; ++j) acc[j] += v[j];
       }
       block_reduce_to<NV>(acc, sums);
-      if (threadIdx.x < NV) pub[threadIdx.x] = sums[threadIdx.x];
+      if (publish) {
+        if (threadIdx.x < NV) pub[threadIdx.x] = sums[threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == 0) st_release64(&c->pub_open, s_open);
+      }
+    } else {
+      if (threadIdx.x < NV) sums[threadIdx.x] = __ldcg(&pub[threadIdx.x]);
+      __syncthreads();
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      if (d.prof) c->t_last = s_tarr;
-      st_relaxed(&c->bar_count, 0u);
-      red_release(&c->bar_gen, 1u);
-    }
-  } else if constexpr (NV > 0) {
-    if (threadIdx.x < NV) sums[threadIdx.x] = __ldcg(&pub[threadIdx.x]);
   }
-  __syncthreads();
   return !s_fail;
 }
 

@@ -14,6 +14,8 @@ constexpr int kSegLen = 512;     // entries per segment of a skyline row of S (o
 constexpr int kJacRec = 36;      // values per element in the backward Jacobian record
 constexpr int kPersistBlock = 256;  // threads per block, persistent kernels
 constexpr int kRedRows = 2048;   // rows of the reduction scratch (>= any grid used)
+constexpr int kRedRep = 4;       // copies of each block's partials in the team reductions
+constexpr int kRedTeam = 16;     // values per row in the team reductions (>= 2 kMaxAA)
 
 // Device-resident control word of the iteration (one per context).
 struct Ctrl {
@@ -48,7 +50,8 @@ struct Ctrl {
   double acc_mu, acc_lam, acc_k;  // mesh-mean sensitivities accumulated over steps
   double dnu_acc;
   unsigned int ticket[16];        // last-block-done counters, one per kernel kind
-  unsigned int bar_count, bar_gen; // grid barrier of the persistent kernels
+  unsigned long long bar_arrive;  // team barrier of the persistent kernels: arrivals so far (monotonic)
+  unsigned long long pub_open;    // team reductions with many values: barrier whose sums are published
   unsigned long long phase_ns[8];  // persistent kernels: time per phase (globaltimer, block 0)
   unsigned long long work_ns[8];   // ... of which block 0's own work before the phase's barrier
   unsigned long long elapsed_ns[2]; // persistent launches: wall time of the forward / adjoint (team block 0)

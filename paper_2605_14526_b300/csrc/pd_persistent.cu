@@ -301,6 +301,7 @@ __global__ void __launch_bounds__(kPersistBlock, 2) k_fwd_rollout(const Dev* __r
     a.sq = sd.sq;
     a.sv = sd.sv;
     sa = a;
+    team_red_count() = 0;
   }
   __syncthreads();
   fwd_rollout_body<T>(sd, sa, Team{tb.y, tb.z});
