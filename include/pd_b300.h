@@ -357,7 +357,9 @@ int pd_batch_teams(pd_ctx* ctx, int32_t* fwd, int32_t* bwd);
  * Launch shape of the persistent kernels and its autotuner.
  * --------------------------------------------------------------------- */
 typedef struct {
-  int32_t fwd_blocks_per_sm;  /* co-resident blocks per SM (1 or 2; 0 = as many as fit, at most 2) */
+  int32_t fwd_blocks_per_sm;  /* forward: 1 = one block of 384 threads per SM (registers for every
+                                 phase, no spills), 2 = two blocks of 256 per SM (more co-resident
+                                 blocks for batches); 0 = 1 for a single instance, 2 for a batch */
   int32_t bwd_blocks_per_sm;
   int32_t fwd_grid;           /* single instance: blocks of the launch (0 = SMs x blocks_per_sm) */
   int32_t bwd_grid;

@@ -255,7 +255,7 @@ int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_o
   d.jac = jac;
   d.sstar = sstar;
   if ((r = dalloc(c, &d.red, std::max((size_t)pdk::max_reduction_blocks(c->n_v, c->n_e) * pdk::kRed,
-                                      (size_t)2 * pdk::kRedRep * pdk::kRedRows * pdk::kRedTeam + 2 * pdk::kRedTeam))))
+                                      (size_t)2 * pdk::kRedRep * pdk::kRedRows * pdk::kRedTeam + 2 * pdk::kPubMax))))
     return r;
   if ((r = dalloc(c, &d.dw, c->n_e)) || (r = dalloc(c, &d.dbeta, c->n_e))) return r;
   if ((r = dalloc(c, &d.ctrl, 1))) return r;
@@ -632,7 +632,7 @@ int reserve_enqueue(pd_ctx* c, int T, cudaStream_t s) {
 // SMs x blocks per SM; 0 if cooperative launch is unavailable
 int grid_of(pd_ctx* c, bool bwd, int* grid) {
   const bool fp32 = c->opt.local_fp32 != 0;
-  const int full = bwd ? pdk::persistent_grid_bwd(fp32, 0) : pdk::persistent_grid(fp32, 0);
+  const int full = bwd ? pdk::persistent_grid_bwd(fp32, 0) : pdk::persistent_grid_max(fp32);
   *grid = 0;
   if (full <= 0) return PD_OK;
   const int want = bwd ? c->tune.bwd_grid : c->tune.fwd_grid;
@@ -656,7 +656,7 @@ int prepare_single(pd_ctx* c, cudaStream_t s, int dir, int grid) {
     return fail(c, PD_ERR_ARG, "the launch state changed since the last launch: run it once before capture");
   if (!c->d_dev) {
     const bool fp32 = c->opt.local_fp32 != 0;
-    c->team_cap = std::max(std::max(pdk::persistent_grid(fp32, 0), pdk::persistent_grid_bwd(fp32, 0)), 1);
+    c->team_cap = std::max(std::max(pdk::persistent_grid_max(fp32), pdk::persistent_grid_bwd(fp32, 0)), 1);
     int r;
     if ((r = dalloc(c, &c->d_dev, 1)) || (r = dalloc(c, &c->d_off, 2)) || (r = dalloc(c, &c->d_team[0], c->team_cap)) ||
         (r = dalloc(c, &c->d_team[1], c->team_cap)))

@@ -796,7 +796,7 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
 
 // team[blockIdx.x] = {instance, block index in its team, team size, 0}
 template <typename T>
-__global__ void __launch_bounds__(kPersistBlock, 2) k_bwd_rollout(const Dev* __restrict__ devs, const int4* __restrict__ team,
+__global__ void __launch_bounds__(kBwdBlock, kBwdMinBlocks) k_bwd_rollout(const Dev* __restrict__ devs, const int4* __restrict__ team,
                                                                 const InstOff* __restrict__ off, BatchBwd br) {
   __shared__ Dev sd;
   __shared__ BwdArgs sa;
@@ -877,15 +877,15 @@ static const void* bwd_fn(bool fp32) {
 
 int persistent_grid_bwd(bool fp32, int blocks_per_sm) {
   int sms = 0;
-  const int per = coop_blocks_per_sm(bwd_fn(fp32), &sms);
+  const int per = coop_blocks_per_sm(bwd_fn(fp32), kBwdBlock, &sms);
   if (per < 1) return 0;
   return sms * (blocks_per_sm >= 1 && blocks_per_sm < per ? blocks_per_sm : per);
 }
 
 cudaError_t launch_bwd_rollout(bool fp32, const Dev* devs, const int4* team, const InstOff* off, const BatchBwd& br,
                                int grid, cudaStream_t s) {
-  if (fp32) return coop_launch(k_bwd_rollout<float>, grid, s, devs, team, off, br);
-  return coop_launch(k_bwd_rollout<double>, grid, s, devs, team, off, br);
+  if (fp32) return coop_launch(k_bwd_rollout<float>, grid, kBwdBlock, s, devs, team, off, br);
+  return coop_launch(k_bwd_rollout<double>, grid, kBwdBlock, s, devs, team, off, br);
 }
 
 }  // namespace pdk

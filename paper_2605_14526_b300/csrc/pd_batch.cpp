@@ -99,7 +99,8 @@ int shape_teams(pd_ctx* c, int dir, std::vector<int>& b) {
   pd_batch& B = *c->batch;
   const bool fp32 = c->opt.local_fp32 != 0;
   const pd_tuning& tn = c->tune;
-  const int bps = dir ? tn.bwd_blocks_per_sm : tn.fwd_blocks_per_sm;
+  int bps = dir ? tn.bwd_blocks_per_sm : tn.fwd_blocks_per_sm;
+  if (!dir && bps == 0) bps = 2;   // a batch defaults to the narrow forward shape (more co-resident blocks)
   const int G = dir ? pdk::persistent_grid_bwd(fp32, bps) : pdk::persistent_grid(fp32, bps);
   if (G <= 0) return fail(c, PD_ERR_CUDA, "cooperative launch of the batched kernel is not available");
   if (B.n > G) return fail(c, PD_ERR_TOO_LARGE, "%d instances exceed the %d co-resident blocks", B.n, G);
@@ -553,7 +554,7 @@ int pd_create_batch(int32_t n, const pd_mesh* meshes, const pd_material* mats, d
   B.hctrl.assign(n, Ctrl{});
   B.inst.assign(n, pd_stats{});
   const bool fp32 = c->opt.local_fp32 != 0;
-  B.team_cap = std::max(std::max(pdk::persistent_grid(fp32, 0), pdk::persistent_grid_bwd(fp32, 0)), 1);
+  B.team_cap = std::max(std::max(pdk::persistent_grid_max(fp32), pdk::persistent_grid_bwd(fp32, 0)), 1);
   CK(cudaMalloc(&B.ctrl, n * sizeof(Ctrl)));
   CK(cudaMemset(B.ctrl, 0, n * sizeof(Ctrl)));
   CK(cudaMalloc(&B.sstar, 3 * (size_t)std::max<long long>(B.off[n].e, 1) * sizeof(double)));
@@ -708,7 +709,7 @@ int pd_autotune(pd_ctx* c, int32_t T_probe, const double* q0, const double* v0, 
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     const bool fp32 = c->opt.local_fp32 != 0;
-    const int full = std::min(pdk::persistent_grid(fp32, 0), pdk::persistent_grid_bwd(fp32, 0));
+    const int full = std::min(pdk::persistent_grid_max(fp32), pdk::persistent_grid_bwd(fp32, 0));
     for (int gsz : {sms / 2, sms, (3 * sms) / 2, 2 * sms})
       if (gsz >= 1 && gsz <= full) cands.push_back({0, gsz, 1.0, 256});
   }

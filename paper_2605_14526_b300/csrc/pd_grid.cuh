@@ -88,84 +88,132 @@ __device__ __forceinline__ int& team_red_count() {
 //    every long row costs more than the extra round trip).
 constexpr int kPublishMin = 8;
 
-template <int NV>
-__device__ __forceinline__ bool grid_reduce(const Dev& d, Team tm, double (&part)[NV > 0 ? NV : 1], double* sums) {
-  static_assert(NV <= kRedTeam, "values per team reduction");
+struct NoFinish {
+  __device__ void operator()(const double*, double*) const {}
+};
+
+// The publishing path on its own, with NX extra values: thread 0 of the
+// block that adds the rows runs fin(sums, extra) and publishes extra[0..NX)
+// after the NV sums; every block returns sums[0..NV+NX). Lets one block run
+// scalar work that depends on the sums (the Anderson solve) and hand the
+// result to the others instead of every block repeating it.
+// The same with the block's sums already formed: thread t < NV holds the
+// block's value t in v (the block is synchronised on entry).
+template <int NV, int NX, class Fin>
+__device__ __forceinline__ bool grid_reduce_pub_v(const Dev& d, Team tm, double v, double* sums, Fin fin) {
+  static_assert(NV <= kRedTeam && NV + NX <= kPubMax, "values per team reduction");
   __shared__ int s_fail, s_last;
   __shared__ unsigned long long s_open;
   int& s_parity = team_red_count();
+  const int par = s_parity & 1;
   if (tm.nb == 1) {
-    if constexpr (NV > 0) block_reduce_to<NV>(part, sums);
-    else __syncthreads();
+    if (threadIdx.x < NV) sums[threadIdx.x] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) fin(sums, sums + NV);
+    __syncthreads();
     return true;
   }
-  constexpr bool publish = NV >= kPublishMin;
-  constexpr int reps = publish ? 1 : kRedRep;
-  const int par = s_parity & 1;
-  if constexpr (NV > 0) {
-    const double v = block_sum_lane<NV>(part);   // threads < NV hold the block's sums
-    if (threadIdx.x < NV)
-#pragma unroll
-      for (int r = 0; r < reps; ++r)
-        d.red[((size_t)(par * kRedRep + r) * kRedRows + tm.b) * kRedTeam + threadIdx.x] = v;
-  }
+  if (threadIdx.x < NV) d.red[((size_t)(par * kRedRep) * kRedRows + tm.b) * kRedTeam + threadIdx.x] = v;
   __syncthreads();
   Ctrl* c = d.ctrl;
-  if constexpr (!publish) {
-    if (threadIdx.x == 0) s_fail = team_arrive_wait(d, tm) ? 0 : 1;
-    __syncthreads();
-  } else {
-    if (threadIdx.x == 0) {
-      const unsigned long long n = atom_add_acq_rel64(&c->bar_arrive, 1ull);
-      const unsigned long long open = (n / (unsigned long long)tm.nb + 1ull) * (unsigned long long)tm.nb;
-      if (d.prof && n + 1 == open) c->t_last = gtimer();
-      s_last = n + 1 == open;
-      s_open = open;
-      s_fail = 0;
-      if (!s_last) {
-        unsigned int it = 0;
-        while (ld_acquire64(&c->pub_open) < open) {
-          if (++it > kSpinLimit) {
-            atomicOr(&c->status, kStatusTimeout);
-            s_fail = 1;
-            break;
-          }
-          __nanosleep(32);
+  if (threadIdx.x == 0) {
+    const unsigned long long n = atom_add_acq_rel64(&c->bar_arrive, 1ull);
+    const unsigned long long open = (n / (unsigned long long)tm.nb + 1ull) * (unsigned long long)tm.nb;
+    if (d.prof && n + 1 == open) c->t_last = gtimer();
+    s_last = n + 1 == open;
+    s_open = open;
+    s_fail = 0;
+    if (!s_last) {
+      unsigned int it = 0;
+      while (ld_acquire64(&c->pub_open) < open) {
+        if (++it > kSpinLimit) {
+          atomicOr(&c->status, kStatusTimeout);
+          s_fail = 1;
+          break;
         }
+        __nanosleep(32);
       }
     }
+    s_parity += 1;   // every thread read `par` before the __syncthreads above
+  }
+  __syncthreads();
+  double* pub = d.red + (size_t)(2 * kRedRep * kRedRows) * kRedTeam + par * kPubMax;   // published values
+  if (s_last) {
+    const double* rows = d.red + (size_t)(par * kRedRep) * kRedRows * kRedTeam;
+    double acc[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) acc[j] = 0.0;
+#pragma unroll 2
+    for (int b = threadIdx.x; b < tm.nb; b += blockDim.x) {
+      double w[NV];
+#pragma unroll
+      for (int j = 0; j < NV; ++j) w[j] = __ldcg(&rows[(size_t)b * kRedTeam + j]);
+#pragma unroll
+      for (int j = 0; j < NV; ++j) acc[j] += w[j];
+    }
+    block_reduce_to<NV>(acc, sums);
+    if (threadIdx.x == 0) fin(sums, sums + NV);
+    __syncthreads();
+    if (threadIdx.x < NV + NX) pub[threadIdx.x] = sums[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == 0) st_release64(&c->pub_open, s_open);
+  } else {
+    if (threadIdx.x < NV + NX) sums[threadIdx.x] = __ldcg(&pub[threadIdx.x]);
     __syncthreads();
   }
-  // every thread read `par` before the barrier's __syncthreads; the
-  // increment is visible after the next one (each path below has one)
-  if (NV > 0 && threadIdx.x == 0) s_parity += 1;
-  if constexpr (NV > 0) {
-    double* pub = d.red + (size_t)(2 * kRedRep * kRedRows) * kRedTeam + par * kRedTeam;   // published sums
-    if (!publish || s_last) {
-      const double* rows = d.red + (size_t)(par * kRedRep + (publish ? 0 : tm.b % kRedRep)) * kRedRows * kRedTeam;
+  return !s_fail;
+}
+
+template <int NV, int NX, class Fin>
+__device__ __forceinline__ bool grid_reduce_pub(const Dev& d, Team tm, double (&part)[NV], double* sums, Fin fin) {
+  const double v = block_sum_lane<NV>(part);   // threads < NV hold the block's sums
+  return grid_reduce_pub_v<NV, NX>(d, tm, v, sums, fin);
+}
+
+template <int NV>
+__device__ __forceinline__ bool grid_reduce(const Dev& d, Team tm, double (&part)[NV > 0 ? NV : 1], double* sums) {
+  static_assert(NV <= kRedTeam, "values per team reduction");
+  if constexpr (NV >= kPublishMin) {
+    return grid_reduce_pub<NV, 0>(d, tm, part, sums, NoFinish{});
+  } else {
+    __shared__ int s_fail;
+    int& s_parity = team_red_count();
+    if (tm.nb == 1) {
+      if constexpr (NV > 0) block_reduce_to<NV>(part, sums);
+      else __syncthreads();
+      return true;
+    }
+    const int par = s_parity & 1;
+    if constexpr (NV > 0) {
+      const double v = block_sum_lane<NV>(part);   // threads < NV hold the block's sums
+      if (threadIdx.x < NV)
+#pragma unroll
+        for (int r = 0; r < kRedRep; ++r)
+          d.red[((size_t)(par * kRedRep + r) * kRedRows + tm.b) * kRedTeam + threadIdx.x] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_fail = team_arrive_wait(d, tm) ? 0 : 1;
+      if (NV > 0) s_parity += 1;   // every thread read `par` before the __syncthreads above
+    }
+    __syncthreads();
+    if constexpr (NV > 0) {
+      const double* rows = d.red + (size_t)(par * kRedRep + tm.b % kRedRep) * kRedRows * kRedTeam;
       double acc[NV];
 #pragma unroll
       for (int j = 0; j < NV; ++j) acc[j] = 0.0;
 #pragma unroll 2
       for (int b = threadIdx.x; b < tm.nb; b += blockDim.x) {
-        double v[NV];
+        double w[NV];
 #pragma unroll
-        for (int j = 0; j < NV; ++j) v[j] = __ldcg(&rows[(size_t)b * kRedTeam + j]);
+        for (int j = 0; j < NV; ++j) w[j] = __ldcg(&rows[(size_t)b * kRedTeam + j]);
 #pragma unroll
-        for (int j = 0; j < NV; ++j) acc[j] += v[j];
+        for (int j = 0; j < NV; ++j) acc[j] += w[j];
       }
       block_reduce_to<NV>(acc, sums);
-      if (publish) {
-        if (threadIdx.x < NV) pub[threadIdx.x] = sums[threadIdx.x];
-        __syncthreads();
-        if (threadIdx.x == 0) st_release64(&c->pub_open, s_open);
-      }
-    } else {
-      if (threadIdx.x < NV) sums[threadIdx.x] = __ldcg(&pub[threadIdx.x]);
-      __syncthreads();
     }
+    return !s_fail;
   }
-  return !s_fail;
 }
 
 __device__ __forceinline__ bool grid_sync(const Dev& d, Team tm) {

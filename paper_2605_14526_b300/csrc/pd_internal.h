@@ -12,10 +12,20 @@ constexpr int kTetBlock = 128;   // threads per block, element kernels
 constexpr int kWarpsSpmv = 8;    // warps per block, skyline SpMV
 constexpr int kSegLen = 512;     // entries per segment of a skyline row of S (one warp each)
 constexpr int kJacRec = 36;      // values per element in the backward Jacobian record
-constexpr int kPersistBlock = 256;  // threads per block, persistent kernels
+// persistent kernels: threads per block and the resident blocks per SM the
+// register budget is sized for. The forward comes in two shapes: one wide
+// block per SM (its registers hold the local step, the S products and the
+// Anderson solve without spilling; used when the grid needs at most one
+// block per SM) and two narrow blocks per SM (more co-resident blocks, for
+// batches of many instances). The adjoint uses two blocks of 256.
+constexpr int kFwdWideBlock = 384;
+constexpr int kFwdNarrowBlock = 256;
+constexpr int kBwdBlock = 256;
+constexpr int kBwdMinBlocks = 2;
 constexpr int kRedRows = 2048;   // rows of the reduction scratch (>= any grid used)
 constexpr int kRedRep = 4;       // copies of each block's partials in the team reductions
 constexpr int kRedTeam = 16;     // values per row in the team reductions (>= 2 kMaxAA)
+constexpr int kPubMax = 32;      // values a team reduction publishes (sums + extra)
 
 // Device-resident control word of the iteration (one per context).
 struct Ctrl {

@@ -25,7 +25,7 @@ void launch_solve(const Dev& d, cudaStream_t s, const double* b, float2* xperm, 
 
 // co-resident blocks per SM of a persistent kernel (at most 2; 0 if
 // cooperative launch is unavailable); *sms gets the SM count
-int coop_blocks_per_sm(const void* fn, int* sms);
+int coop_blocks_per_sm(const void* fn, int block, int* sms);
 
 // Persistent rollout / adjoint of one or many instances (one team of blocks
 // per instance): co-resident grid size (0 if cooperative launch is not
@@ -34,6 +34,7 @@ int coop_blocks_per_sm(const void* fn, int* sms);
 // n + 1 prefix offsets), team[grid] maps each block to {instance, index in
 // its team, team size, 0}.
 int persistent_grid(bool fp32, int blocks_per_sm);
+int persistent_grid_max(bool fp32);   // the larger grid of the two forward shapes
 cudaError_t launch_fwd_rollout(bool fp32, const Dev* devs, const int4* team, const InstOff* off, const BatchFwd& br,
                                int grid, cudaStream_t s);
 int persistent_grid_bwd(bool fp32, int blocks_per_sm);

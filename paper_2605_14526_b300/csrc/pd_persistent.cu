@@ -23,11 +23,13 @@
 namespace pdk {
 
 // local step / assembly in the kernel's precision T, or in FP64 once an FP32
-// team has escalated
+// team has escalated (the FP64 local step is a real call: it runs rarely and,
+// inlined, its registers would count against every phase of the body)
+__device__ __noinline__ void local_item_hi(const Dev& d, int e) { local_item<double>(d, e, d.q); }
 template <typename T>
 __device__ __forceinline__ void local_any(const Dev& d, int e, bool hi) {
   if constexpr (sizeof(T) == 4) {
-    if (hi) local_item<double>(d, e, d.q);
+    if (hi) local_item_hi(d, e);
     else local_item<float>(d, e, d.q);
   } else {
     local_item<T>(d, e, d.q);
@@ -43,10 +45,18 @@ __device__ __forceinline__ void assemble_any(const Dev& d, int v, int k, double*
   }
 }
 
+// the network warm start as a real call: it runs once per step and, inlined,
+// its registers would count against every phase of the body
+__device__ __noinline__ void warm_vertex_call(const Dev& d, int v, const double* vin, int lane) {
+  warm_vertex(d, v, d.qt, nullptr, vin, d.q, d.qprev, lane);
+}
+
 template <typename T>
 __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a, const Team tm) {
   __shared__ FwdState S;
-  __shared__ double sums[2 * kMaxAA];
+  __shared__ double sums[kPubMax];
+  __shared__ int s_fin;
+  __shared__ double s_pa[kFwdWideBlock / 32][3][2 * kMaxAA];
   const int tid = threadIdx.x;
   const int gtid = tm.b * blockDim.x + tid;
   const int gthreads = tm.nb * blockDim.x;
@@ -113,7 +123,7 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
     bool warm_now = d.warm != 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
       if (warm_now) {
-        for (int v = gwarp; v < d.n_v; v += nwarps) warm_vertex(d, v, d.qt, nullptr, vin, d.q, d.qprev, lane);
+        for (int v = gwarp; v < d.n_v; v += nwarps) warm_vertex_call(d, v, vin, lane);
         if (!(ok = grid_sync(d, tm))) break;
       }
       double pu[2] = {0.0, 0.0};   // step norms of the last update, reduced with the next assembly
@@ -171,9 +181,12 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
           if (!(ok = grid_sync(d, tm))) break;
         }
         // S^T y row by row, with the Anderson work of that row's vertex fused in
+        // the Anderson partials of lanes 0..2 accumulate in shared memory (in
+        // registers they would stay live across the S^T loop)
         const AAView av = aa_view(d, S.pairs, S.ncols, S.head);
-        double pa[2 * kMaxAA];
-        for (int j = 0; j < 2 * kMaxAA; ++j) pa[j] = 0.0;
+        double* pa = &s_pa[tid >> 5][lane < 3 ? lane : 0][0];
+        if (lane < 3)
+          for (int j = 0; j < 2 * kMaxAA; ++j) pa[j] = 0.0;
         for (int j = gwarp; j < d.n_f; j += nwarps) {
           double a0, a1, a2;
           spmv_st_sum(d, d.y, j, lane, a0, a1, a2);
@@ -185,11 +198,32 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
           }
         }
         work_done(PH_AA);
-        if (!(ok = grid_reduce<2 * kMaxAA>(d, tm, pa, sums))) break;
-        mark(PH_SPMV_ST);   // S^T y + Anderson dots, through their reduction
-        if (tid == 0) aa_finish(d, &S, av, sums);
         __syncthreads();
-        mark(PH_AA);        // the small Anderson solve
+        double pav = 0.0;   // the block's partial of value tid (fixed order)
+        if (tid < 2 * kMaxAA)
+          for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            for (int l = 0; l < 3; ++l) pav += s_pa[w][l][tid];
+        // the block that adds the dots also runs the small Anderson solve and
+        // publishes the guard's verdict and gamma with the sums; the others
+        // repeat only the history bookkeeping
+        if (tid == 0) s_fin = 0;
+        auto fin = [&](const double* sm, double* ex) {
+          ex[0] = (double)aa_finish(d, &S, av, sm);
+          for (int j = 0; j < kMaxAA; ++j) ex[1 + j] = S.gamma[j];
+          s_fin = 1;
+        };
+        if (!(ok = grid_reduce_pub_v<2 * kMaxAA, 1 + kMaxAA>(d, tm, pav, sums, fin))) break;
+        mark(PH_SPMV_ST);   // S^T y + Anderson dots and solve, through their reduction
+        if (tid == 0 && !s_fin) {
+          const int verdict = (int)sums[2 * kMaxAA];
+          aa_book(&S, av, sums);
+          if (verdict >= 0) {
+            for (int j = 0; j < kMaxAA; ++j) S.gamma[j] = sums[2 * kMaxAA + 1 + j];
+            aa_guard(&S, verdict == 1);
+          }
+        }
+        __syncthreads();
+        mark(PH_AA);        // applying the published step
         const int use_hat = S.use_hat, nc = S.ncols;
         pu[0] = pu[1] = 0.0;
         // one thread per free coordinate of the block's vertices
@@ -280,9 +314,9 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
 }
 
 // team[blockIdx.x] = {instance, block index in its team, team size, 0}
-template <typename T>
-__global__ void __launch_bounds__(kPersistBlock, 2) k_fwd_rollout(const Dev* __restrict__ devs, const int4* __restrict__ team,
-                                                                const InstOff* __restrict__ off, BatchFwd br) {
+template <typename T, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_fwd_rollout(const Dev* __restrict__ devs, const int4* __restrict__ team,
+                                                             const InstOff* __restrict__ off, BatchFwd br) {
   __shared__ Dev sd;
   __shared__ RollArgs sa;
   const int4 tb = team[blockIdx.x];
@@ -309,31 +343,55 @@ __global__ void __launch_bounds__(kPersistBlock, 2) k_fwd_rollout(const Dev* __r
 
 // ------------------------------------------------------------ launch
 
-int coop_blocks_per_sm(const void* fn, int* sms_out) {
+int coop_blocks_per_sm(const void* fn, int block, int* sms_out) {
   int dev = 0, sms = 0, coop = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPersistBlock, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0) != cudaSuccess) return 0;
   if (sms_out) *sms_out = sms;
   return per_sm < 2 ? per_sm : 2;
 }
 
-static const void* fwd_fn(bool fp32) {
-  return fp32 ? (const void*)k_fwd_rollout<float> : (const void*)k_fwd_rollout<double>;
+template <typename T>
+static const void* fwd_fn(bool wide) {
+  return wide ? (const void*)k_fwd_rollout<T, kFwdWideBlock, 1> : (const void*)k_fwd_rollout<T, kFwdNarrowBlock, 2>;
 }
 
+// blocks per SM of one forward shape that a cooperative launch can hold
+static int fwd_per_sm(bool fp32, bool wide, int* sms) {
+  const int per = coop_blocks_per_sm(fp32 ? fwd_fn<float>(wide) : fwd_fn<double>(wide), wide ? kFwdWideBlock : kFwdNarrowBlock, sms);
+  return wide ? (per < 1 ? per : 1) : per;
+}
+
+// blocks_per_sm 2: the narrow shape at two blocks per SM; otherwise the
+// wide shape at one
 int persistent_grid(bool fp32, int blocks_per_sm) {
   int sms = 0;
-  const int per = coop_blocks_per_sm(fwd_fn(fp32), &sms);
+  const bool wide = blocks_per_sm != 2;
+  const int per = fwd_per_sm(fp32, wide, &sms);
   if (per < 1) return 0;
-  return sms * (blocks_per_sm >= 1 && blocks_per_sm < per ? blocks_per_sm : per);
+  return sms * (wide ? 1 : per);
 }
 
+int persistent_grid_max(bool fp32) {
+  const int a = persistent_grid(fp32, 1), b = persistent_grid(fp32, 2);
+  return a > b ? a : b;
+}
+
+// a grid of at most one block per SM takes the wide shape
 cudaError_t launch_fwd_rollout(bool fp32, const Dev* devs, const int4* team, const InstOff* off, const BatchFwd& br,
                                int grid, cudaStream_t s) {
-  if (fp32) return coop_launch(k_fwd_rollout<float>, grid, s, devs, team, off, br);
-  return coop_launch(k_fwd_rollout<double>, grid, s, devs, team, off, br);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (grid <= sms) {
+    if (fp32) return coop_launch(k_fwd_rollout<float, kFwdWideBlock, 1>, grid, kFwdWideBlock, s, devs, team, off, br);
+    return coop_launch(k_fwd_rollout<double, kFwdWideBlock, 1>, grid, kFwdWideBlock, s, devs, team, off, br);
+  }
+  if (fp32) return coop_launch(k_fwd_rollout<float, kFwdNarrowBlock, 2>, grid, kFwdNarrowBlock, s, devs, team, off, br);
+  return coop_launch(k_fwd_rollout<double, kFwdNarrowBlock, 2>, grid, kFwdNarrowBlock, s, devs, team, off, br);
 }
 
 }  // namespace pdk

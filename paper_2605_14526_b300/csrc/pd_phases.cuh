@@ -506,13 +506,14 @@ __device__ __forceinline__ bool aa_solve_any(int nc, const double* G, const doub
   return true;
 }
 
-// Gram update, regularised normal equations, reliability guard (eq. aa_gamma)
+// history bookkeeping of one Anderson step: Gram row from the reduced dots,
+// window pointers; returns the columns held (0: no mixing this iteration)
 template <class St>
-__device__ __forceinline__ void aa_finish(const Dev& d, St* c, const AAView& a, const double* s) {
+__device__ __forceinline__ int aa_book(St* c, const AAView& a, const double* s) {
   c->n_solve += 1;
   const int m = a.m;
   c->use_hat = 1;
-  if (m == 0) return;
+  if (m == 0) return 0;
   if (a.add) {
     for (int j = 0; j < a.ncols_new; ++j) {
       c->gram[a.slot * kMaxAA + j] = s[j];
@@ -522,8 +523,30 @@ __device__ __forceinline__ void aa_finish(const Dev& d, St* c, const AAView& a, 
     c->head = (a.slot + 1) % m;
   }
   c->pairs = c->pairs < m + 1 ? c->pairs + 1 : m + 1;
-  const int nc = c->ncols;
-  if (nc < 1) return;
+  return c->ncols;
+}
+
+// reliability guard outcome: accept gamma, or take q_hat and clear the history
+template <class St>
+__device__ __forceinline__ void aa_guard(St* c, bool accept) {
+  if (!accept) {
+    c->resets += 1;
+    c->pairs = 0;
+    c->ncols = 0;
+    c->head = 0;
+    for (int i = 0; i < kMaxAA * kMaxAA; ++i) c->gram[i] = 0.0;
+  } else {
+    c->use_hat = 0;
+  }
+}
+
+// Gram update, regularised normal equations, reliability guard
+// ||gamma||_2 <= 10 (eq. aa_gamma); returns the guard's verdict (1 accept,
+// 0 reject, -1 no solve this iteration)
+template <class St>
+__device__ __forceinline__ int aa_finish(const Dev& d, St* c, const AAView& a, const double* s) {
+  const int nc = aa_book(c, a, s);
+  if (nc < 1) return -1;
   double* gam = c->gamma;   // read only when the guard accepts it
   double gn = 0.0;
   bool ok;
@@ -535,15 +558,9 @@ __device__ __forceinline__ void aa_finish(const Dev& d, St* c, const AAView& a, 
     case 5: ok = aa_solve<5>(c->gram, s + kMaxAA, gam, gn); break;
     default: ok = aa_solve_any(nc, c->gram, s + kMaxAA, gam, gn); break;
   }
-  if (!ok || !(gn <= 100.0)) {  // reliability guard ||gamma||_2 > 10: take q_hat, clear the history
-    c->resets += 1;
-    c->pairs = 0;
-    c->ncols = 0;
-    c->head = 0;
-    for (int i = 0; i < kMaxAA * kMaxAA; ++i) c->gram[i] = 0.0;
-  } else {
-    c->use_hat = 0;
-  }
+  const bool accept = ok && gn <= 100.0;
+  aa_guard(c, accept);
+  return accept ? 1 : 0;
 }
 
 // q^{k+1} = q_hat - (dQ + dG) gamma (or q_hat); step-norm partials
