@@ -170,49 +170,56 @@ __device__ __forceinline__ bool grid_reduce_pub(const Dev& d, Team tm, double (&
   return grid_reduce_pub_v<NV, NX>(d, tm, v, sums, fin);
 }
 
+// Every block adds all the team's rows itself: thread t < NV holds the
+// block's value t in v on entry (NV = 0: a plain barrier).
+template <int NV>
+__device__ __forceinline__ bool grid_reduce_all_v(const Dev& d, Team tm, double v, double* sums) {
+  static_assert(NV <= kRedTeam, "values per team reduction");
+  __shared__ int s_fail;
+  int& s_parity = team_red_count();
+  if (tm.nb == 1) {
+    if (NV > 0 && threadIdx.x < NV) sums[threadIdx.x] = v;
+    __syncthreads();
+    return true;
+  }
+  const int par = s_parity & 1;
+  if (NV > 0 && threadIdx.x < NV)
+#pragma unroll
+    for (int r = 0; r < kRedRep; ++r)
+      d.red[((size_t)(par * kRedRep + r) * kRedRows + tm.b) * kRedTeam + threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_fail = team_arrive_wait(d, tm) ? 0 : 1;
+    if (NV > 0) s_parity += 1;   // every thread read `par` before the __syncthreads above
+  }
+  __syncthreads();
+  if constexpr (NV > 0) {
+    const double* rows = d.red + (size_t)(par * kRedRep + tm.b % kRedRep) * kRedRows * kRedTeam;
+    double acc[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) acc[j] = 0.0;
+#pragma unroll 2
+    for (int b = threadIdx.x; b < tm.nb; b += blockDim.x) {
+      double w[NV];
+#pragma unroll
+      for (int j = 0; j < NV; ++j) w[j] = __ldcg(&rows[(size_t)b * kRedTeam + j]);
+#pragma unroll
+      for (int j = 0; j < NV; ++j) acc[j] += w[j];
+    }
+    block_reduce_to<NV>(acc, sums);
+  }
+  return !s_fail;
+}
+
 template <int NV>
 __device__ __forceinline__ bool grid_reduce(const Dev& d, Team tm, double (&part)[NV > 0 ? NV : 1], double* sums) {
   static_assert(NV <= kRedTeam, "values per team reduction");
   if constexpr (NV >= kPublishMin) {
     return grid_reduce_pub<NV, 0>(d, tm, part, sums, NoFinish{});
+  } else if constexpr (NV > 0) {
+    return grid_reduce_all_v<NV>(d, tm, block_sum_lane<NV>(part), sums);
   } else {
-    __shared__ int s_fail;
-    int& s_parity = team_red_count();
-    if (tm.nb == 1) {
-      if constexpr (NV > 0) block_reduce_to<NV>(part, sums);
-      else __syncthreads();
-      return true;
-    }
-    const int par = s_parity & 1;
-    if constexpr (NV > 0) {
-      const double v = block_sum_lane<NV>(part);   // threads < NV hold the block's sums
-      if (threadIdx.x < NV)
-#pragma unroll
-        for (int r = 0; r < kRedRep; ++r)
-          d.red[((size_t)(par * kRedRep + r) * kRedRows + tm.b) * kRedTeam + threadIdx.x] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      s_fail = team_arrive_wait(d, tm) ? 0 : 1;
-      if (NV > 0) s_parity += 1;   // every thread read `par` before the __syncthreads above
-    }
-    __syncthreads();
-    if constexpr (NV > 0) {
-      const double* rows = d.red + (size_t)(par * kRedRep + tm.b % kRedRep) * kRedRows * kRedTeam;
-      double acc[NV];
-#pragma unroll
-      for (int j = 0; j < NV; ++j) acc[j] = 0.0;
-#pragma unroll 2
-      for (int b = threadIdx.x; b < tm.nb; b += blockDim.x) {
-        double w[NV];
-#pragma unroll
-        for (int j = 0; j < NV; ++j) w[j] = __ldcg(&rows[(size_t)b * kRedTeam + j]);
-#pragma unroll
-        for (int j = 0; j < NV; ++j) acc[j] += w[j];
-      }
-      block_reduce_to<NV>(acc, sums);
-    }
-    return !s_fail;
+    return grid_reduce_all_v<0>(d, tm, 0.0, sums);
   }
 }
 

@@ -55,7 +55,6 @@ template <typename T>
 __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a, const Team tm) {
   __shared__ FwdState S;
   __shared__ double sums[kPubMax];
-  __shared__ int s_fin;
   __shared__ double s_pa[kFwdWideBlock / 32][3][2 * kMaxAA];
   const int tid = threadIdx.x;
   const int gtid = tm.b * blockDim.x + tid;
@@ -203,27 +202,14 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
         if (tid < 2 * kMaxAA)
           for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
             for (int l = 0; l < 3; ++l) pav += s_pa[w][l][tid];
-        // the block that adds the dots also runs the small Anderson solve and
-        // publishes the guard's verdict and gamma with the sums; the others
-        // repeat only the history bookkeeping
-        if (tid == 0) s_fin = 0;
-        auto fin = [&](const double* sm, double* ex) {
-          ex[0] = (double)aa_finish(d, &S, av, sm);
-          for (int j = 0; j < kMaxAA; ++j) ex[1 + j] = S.gamma[j];
-          s_fin = 1;
-        };
-        if (!(ok = grid_reduce_pub_v<2 * kMaxAA, 1 + kMaxAA>(d, tm, pav, sums, fin))) break;
-        mark(PH_SPMV_ST);   // S^T y + Anderson dots and solve, through their reduction
-        if (tid == 0 && !s_fin) {
-          const int verdict = (int)sums[2 * kMaxAA];
-          aa_book(&S, av, sums);
-          if (verdict >= 0) {
-            for (int j = 0; j < kMaxAA; ++j) S.gamma[j] = sums[2 * kMaxAA + 1 + j];
-            aa_guard(&S, verdict == 1);
-          }
-        }
+        // every block adds the team's dots and runs the small Anderson solve
+        // itself (identical sums, identical gamma): no second round trip for
+        // a published result
+        if (!(ok = grid_reduce_all_v<2 * kMaxAA>(d, tm, pav, sums))) break;
+        mark(PH_SPMV_ST);   // S^T y + Anderson dots, through their reduction
+        if (tid == 0) aa_finish(d, &S, av, sums);
         __syncthreads();
-        mark(PH_AA);        // applying the published step
+        mark(PH_AA);        // the small Anderson solve
         const int use_hat = S.use_hat, nc = S.ncols;
         pu[0] = pu[1] = 0.0;
         // one thread per free coordinate of the block's vertices
