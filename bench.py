@@ -255,7 +255,7 @@ def run_batch(args, rank, world, local_rank, dev, dist):
     nv3b = 3 * 8 * bc.n_v
     line = {"metric": METRIC, "value": value, "unit": "instance PD steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64 (FP32 local step, FP64 RHS/factor/solve)", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64 (FP32 local step; FP64 RHS, factor, Anderson, adjoint; S products in double-float on the FP32 pipe)", "data": "synthetic",
             "config": {"workload": BATCH_WORKLOAD, "instances": bc.n, "tets": bc.n_e, "vertices": bc.n_v,
                        "nnz_S": int(st.factor_nnz), "pd_steps_per_instance_per_bench_step": T,
                        "l2": "flushed (256 MB write) between rollouts; inverse factors total "
@@ -355,7 +355,7 @@ def run_contact(args, rank, world, local_rank, dev, dist):
     peak, peak_kind = _peaks()
     line = {"metric": METRIC, "value": value, "unit": "PD steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64 (FP32 local step, FP64 RHS/factor/solve/contact)", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64 (FP32 local step; FP64 RHS, factor, contact, adjoint; S products in double-float on the FP32 pipe)", "data": "synthetic",
             "config": {"workload": CONTACT_WORKLOAD, "pd_steps_per_bench_step": T,
                        "note": f"first {T} of the configured 300 steps per benchmark step",
                        "factor_and_delassus_s": factor_s, "nnz_S": int(st.factor_nnz),
@@ -520,13 +520,35 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_s = float(tt[0])
     e2e = world * T * args.steps / e2e_s
+    # the same rollout with the S products in plain FP64 (options.solve_fp64):
+    # one untimed and one timed fwd+bwd, for the cost of the exact-FP64 form
+    o64 = binding.options_for(scene.solver)
+    o64.solve_fp64 = 1
+    pd64 = binding.PDContext(scene, o64)
+    q64, v64 = torch.empty_like(x0), torch.empty_like(x0)
+    for timed in (False, True):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        binding.pd_rollout(pd64.ctx, T, x0, v0, f0, 0, q64, v64, stream)
+        ev[1].record(stream)
+        binding.pd_backward(pd64.ctx, q64 - target, zero, dq0, dv0, dE, dnu, None, 0, stream)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+    st64 = binding.pd_get_stats(pd64.ctx)
+    fp64_variant = {"pd_steps_per_s": T / (ev[0].elapsed_time(ev[2]) / 1e3),
+                    "fwd_ms": ev[0].elapsed_time(ev[1]), "bwd_ms": ev[1].elapsed_time(ev[2]),
+                    "fwd_iters_per_pd_step": st64.iters_total / T, "adj_iters_per_pd_step": st64.adj_iters_total / T,
+                    "qT_rel_diff_vs_default": float((q64 - qT).norm() / qT.norm())}
+    del pd64
+
     nv3b = 3 * 8 * scene.n_v
     h2d = 3 * nv3b + 2 * nv3b          # x0, v0, f_ext; dL/dq_T, dL/dv_T
     d2h = 2 * nv3b + 2 * nv3b + 8 * scene.n_e + 8
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64 (FP32 local step, FP64 RHS/factor/solve)", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64 (FP32 local step; FP64 RHS, factor, Anderson, adjoint; S products in double-float on the FP32 pipe)", "data": "synthetic",
             "config": {"workload": WORKLOAD, "pd_steps_per_bench_step": T, "l2": "flushed (256 MB write) between rollouts",
                        "gate": f"b-change {pd.options.eps_res:g}, q-step {pd.options.eps_step:g} (relative)",
                        "accuracy_vs_oracle": "positions 8.6e-6, dL/dE 2.9e-5 over 200 steps (tests/test_gpu_parity.py)",
@@ -541,6 +563,7 @@ def main():
                          "fwd_launch_ms": fwd_launch_ms, "bwd_launch_ms": bwd_launch_ms,
                          "fwd_iter_bytes": fwd_iter_bytes, "bwd_iter_bytes": bwd_iter_bytes},
             "forward_phase_ms_one_rollout": phases,
+            "solve_fp64_variant": fp64_variant,
             "clocks": clk.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, k = oracle_sample(scene, 2)

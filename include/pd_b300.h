@@ -91,6 +91,12 @@ typedef struct {
                              warm start (pd_mlp_load); 2 constant-velocity extrapolation
                              2 x_t - x_{t-1}. Persistent launches only; a warm-started step
                              that hits k_max is run again from q_t (pd_stats.warm_fallbacks) */
+  int32_t solve_fp64;     /* products with the inverse factor S (every A^-1 application):
+                             0 (default) double-float arithmetic on the FP32 pipe, S, S^T,
+                             b and y held as (hi, lo) float pairs, error of order 2^-44 of the
+                             row's sum of magnitudes, at 64x the FP64 rate of this part;
+                             1 plain FP64 (S and S^T also kept as FP64 values, 8 more bytes
+                             per non-zero). Fixed at pd_create. */
 } pd_options;
 
 /* Statistics of the last pd_rollout / pd_backward (host copy). */

@@ -39,7 +39,7 @@ class pd_options(ctypes.Structure):
                 ("tr_mode", c_int32), ("adj_max_iters", c_int32), ("persistent", c_int32),
                 ("eps_step", c_double), ("eps_res", c_double),
                 ("eps_abs", c_double), ("eps_tr", c_double), ("adj_tol", c_double),
-                ("escalate_window", c_int32), ("warm_start", c_int32)]
+                ("escalate_window", c_int32), ("warm_start", c_int32), ("solve_fp64", c_int32)]
 
 
 class pd_stats(ctypes.Structure):
@@ -489,6 +489,7 @@ def options_for(settings) -> pd_options:
     o.eps_res = settings.eps_res
     o.eps_abs = settings.eps_abs
     o.eps_tr = settings.eps_tr
+    o.solve_fp64 = 1 if getattr(settings, "solve_fp64", False) else 0
     return o
 
 

@@ -139,6 +139,7 @@ void pd_default_options(pd_options* o) {
   o->adj_tol = 1e-9;
   o->escalate_window = 100;
   o->warm_start = 0;
+  o->solve_fp64 = 0;
 }
 
 const char* pd_last_error(const pd_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -441,6 +442,11 @@ int pd_factor(pd_ctx* c) {
     return o;
   };
   const std::vector<float2> s_hl = split(s_val), st_hl = split(st_val);
+  double *sv64 = nullptr, *stv64 = nullptr;
+  if (c->opt.solve_fp64) {
+    int r0;
+    if ((r0 = upload(c, &sv64, s_val, true)) || (r0 = upload(c, &stv64, st_val, true))) return r0;
+  }
   std::vector<double>().swap(s_val);
   std::vector<double>().swap(st_val);
   std::vector<int> iperm_v(n_v, -1), perm_v(nf);
@@ -485,6 +491,7 @@ int pd_factor(pd_ctx* c) {
   }
   d.coef32 = c32; d.coef64 = c64; d.mu_e = mu_d; d.lam_e = lam_d; d.E = E_d; d.cA = cA_d;
   d.iperm = iperm_d; d.perm = perm_d; d.s_rowptr = srp; d.s_first = sfirst; d.s_hl = sv; d.s_seg = seg_d;
+  d.sfp64 = c->opt.solve_fp64 ? 1 : 0; d.s_val64 = sv64; d.st_val64 = stv64;
   d.n_seg = (int)seg.size(); d.st_ptr = stp; d.st_idx = sti; d.st_hl = stv;
   d.n_slot = n_slot; d.s_part = spart; d.s_cnt = scnt; d.s_part_na = spart_na; d.s_cnt_na = scnt_na;
   d.A_ptr = Ap; d.A_idx = Ai; d.A_val = Av; d.B_ptr = Bp; d.B_idx = Bi; d.B_val = Bv;

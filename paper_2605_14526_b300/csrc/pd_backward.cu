@@ -223,7 +223,7 @@ __device__ __forceinline__ void bwd_init_item(const Dev& d, int v) {
   }
   if (!pin) {
     const int pos = d.iperm[v];
-    for (int a = 0; a < 3; ++a) d.bperm[3 * (size_t)pos + a] = df_split(rv[a]);
+    for (int a = 0; a < 3; ++a) store_rhs(d, d.bperm, 3 * (size_t)pos + a, rv[a]);
   }
 }
 
@@ -310,7 +310,7 @@ __device__ __forceinline__ void pcg_r_item(const Dev& d, int v, double alpha, co
     d.mu[o] += alpha * pd[o];
     const double rn = d.r[o] - alpha * d.w[o];
     d.r[o] = rn;
-    d.bperm[3 * (size_t)pos + i] = df_split(rn);
+    store_rhs(d, d.bperm, 3 * (size_t)pos + i, rn);
   }
 }
 

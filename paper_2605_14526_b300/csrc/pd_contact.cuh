@@ -168,11 +168,12 @@ __device__ __forceinline__ void contact_y_row(const Dev& d, int i, const double*
     else b = m;
   }
   const float2* srow = d.s_hl + d.s_rowptr[i];
+  const double* srow64 = d.sfp64 ? d.s_val64 + d.s_rowptr[i] : nullptr;
   double r0 = 0.0, r1 = 0.0, r2 = 0.0;
   for (int c = a + lane; c < d.n_con; c += 32) {
     const int p = d.con_pos[c];
     if (p > i) break;
-    const double s = df_join(srow[p - lo]);
+    const double s = srow64 ? srow64[p - lo] : df_join(srow[p - lo]);
     r0 += s * lam_f[2 * c];
     r1 += s * lam_f[2 * c + 1];
     r2 += s * d.con_n[c] * lam_n[c];
@@ -184,10 +185,10 @@ __device__ __forceinline__ void contact_y_row(const Dev& d, int i, const double*
     r2 += __shfl_xor_sync(0xffffffffu, r2, o);
   }
   if (lane == 0) {
-    float2* yi = d.y + 3 * (size_t)i;
-    yi[0] = df_split(df_join(yi[0]) + r0);
-    yi[1] = df_split(df_join(yi[1]) + r1);
-    yi[2] = df_split(df_join(yi[2]) + r2);
+    const size_t o = 3 * (size_t)i;
+    store_y(d, d.y, o, load_y(d, d.y, o) + r0);
+    store_y(d, d.y, o + 1, load_y(d, d.y, o + 1) + r1);
+    store_y(d, d.y, o + 2, load_y(d, d.y, o + 2) + r2);
   }
 }
 

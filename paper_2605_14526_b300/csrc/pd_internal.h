@@ -131,6 +131,9 @@ struct Dev {
   const int* perm;         // [n_f] vertex at elimination position
   const int64_t* s_rowptr; // skyline rows of S
   const int* s_first;      // first_desc per row
+  int sfp64;               // 1: the S products in FP64 (s_val64, st_val64; b, y as doubles)
+  const double* s_val64;   // S entries in FP64 (sfp64 only)
+  const double* st_val64;  // S^T entries in FP64 (sfp64 only)
   const float2* s_hl;      // S entries as double-float pairs (hi, lo)
   const int4* s_seg;       // segments {row, offset, length, 0 or 1 + first partial slot of a split row}
   int n_seg;

@@ -127,7 +127,7 @@ __global__ void k_solve_in(Dev d, const double* b, float2* xperm, double* x) {
     return;
   }
   const int pos = d.iperm[v];
-  for (int i = 0; i < 3; ++i) xperm[3 * (size_t)pos + i] = df_split(b[3 * (size_t)v + i]);
+  for (int i = 0; i < 3; ++i) store_rhs(d, xperm, 3 * (size_t)pos + i, b[3 * (size_t)v + i]);
 }
 
 // ------------------------------------------------------------ launch wrappers

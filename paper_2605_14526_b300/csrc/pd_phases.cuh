@@ -10,6 +10,21 @@
 
 namespace pdk {
 
+// right-hand side entry in elimination order, in the representation the
+// products read (double-float pair, or FP64 with sfp64)
+__device__ __forceinline__ void store_rhs(const Dev& d, float2* xperm, size_t i, double v) {
+  if (d.sfp64) reinterpret_cast<double*>(xperm)[i] = v;
+  else xperm[i] = df_split(v);
+}
+__device__ __forceinline__ double load_y(const Dev& d, const float2* y, size_t i) {
+  return d.sfp64 ? reinterpret_cast<const double*>(y)[i] : df_join(y[i]);
+}
+__device__ __forceinline__ void store_y(const Dev& d, float2* y, size_t i, double v) {
+  if (d.sfp64) reinterpret_cast<double*>(y)[i] = v;
+  else y[i] = df_split(v);
+}
+
+
 // ------------------------------------------------------------ step begin
 
 // The scalar logic below is written against a state type St with the fields
@@ -152,7 +167,7 @@ __device__ __forceinline__ void assemble_warp(const Dev& d, int v, int k, double
     part[1] += bp * bp;
   }
   d.b[o] = acc;
-  d.bperm[3 * (size_t)d.iperm[v] + i] = df_split(acc);
+  store_rhs(d, d.bperm, 3 * (size_t)d.iperm[v] + i, acc);
   if (!isfinite(acc)) part[2] += 1.0;
 }
 
@@ -211,6 +226,113 @@ __device__ __forceinline__ void assemble_finish(const Dev& d, St* c, int k, cons
 // intermediate y = S b as float pairs, and the result S^T y is returned in
 // FP64.
 
+// FP64 forms of the two products (options.solve_fp64): the same traversal,
+// FP64 multiply-adds, the same slot-ordered combination of split rows
+__device__ __forceinline__ void spmv_s_segment64(const Dev& d, const double* xin, double* y, double* part, int* cnt,
+                                                 int sg, int lane) {
+  const int4 seg = d.s_seg[sg];
+  const int row = seg.x;
+  const double* sv = d.s_val64 + d.s_rowptr[row] + seg.y;
+  const double* xv = xin + 3 * (size_t)(d.s_first[row] + seg.y);
+  double a[4][3] = {};
+  int p = lane;
+  for (; p + 96 < seg.z; p += 128) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const double s = sv[p + 32 * u];
+      const double* x = xv + 3 * (size_t)(p + 32 * u);
+      a[u][0] += s * x[0];
+      a[u][1] += s * x[1];
+      a[u][2] += s * x[2];
+    }
+  }
+  for (; p < seg.z; p += 32) {
+    const double s = sv[p];
+    const double* x = xv + 3 * (size_t)p;
+    a[0][0] += s * x[0];
+    a[0][1] += s * x[1];
+    a[0][2] += s * x[2];
+  }
+  double r[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    double v = (a[0][i] + a[1][i]) + (a[2][i] + a[3][i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    r[i] = v;
+  }
+  double* yr = y + 3 * (size_t)row;
+  if (seg.w == 0) {
+    if (lane < 3) yr[lane] = r[lane == 0 ? 0 : (lane == 1 ? 1 : 2)];
+    return;
+  }
+  const int slot0 = seg.w - 1;
+  const int ns = (row - d.s_first[row] + kSegLen) / kSegLen;
+  double* pr = part + 3 * (size_t)slot0;
+  int last = 0;
+  if (lane == 0) {
+    double* ps = pr + 3 * (size_t)(seg.y / kSegLen);
+    ps[0] = r[0];
+    ps[1] = r[1];
+    ps[2] = r[2];
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;" : "=r"(old) : "l"(cnt + slot0) : "memory");
+    last = old == ns - 1;
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (!last) return;
+  __syncwarp();
+  double t[3] = {0.0, 0.0, 0.0};
+  for (int k = lane; k < ns; k += 32)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t[i] += __ldcg(pr + 3 * (size_t)k + i);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t[i] += __shfl_xor_sync(0xffffffffu, t[i], o);
+  if (lane < 3) yr[lane] = t[lane == 0 ? 0 : (lane == 1 ? 1 : 2)];
+  if (lane == 0) cnt[slot0] = 0;
+}
+
+__device__ __forceinline__ void spmv_st_sum64(const Dev& d, const double* y, int j, int lane, double& r0, double& r1,
+                                              double& r2) {
+  const int64_t beg = d.st_ptr[j], end = d.st_ptr[j + 1];
+  double a[4][3] = {};
+  int64_t p = beg + lane;
+  for (; p + 96 < end; p += 128) {
+    int ix[4];
+    double sv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      ix[u] = d.st_idx[p + 32 * u];
+      sv[u] = d.st_val64[p + 32 * u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const double* yv = y + 3 * (size_t)ix[u];
+      a[u][0] += sv[u] * yv[0];
+      a[u][1] += sv[u] * yv[1];
+      a[u][2] += sv[u] * yv[2];
+    }
+  }
+  for (; p < end; p += 32) {
+    const double s = d.st_val64[p];
+    const double* yv = y + 3 * (size_t)d.st_idx[p];
+    a[0][0] += s * yv[0];
+    a[0][1] += s * yv[1];
+    a[0][2] += s * yv[2];
+  }
+  r0 = (a[0][0] + a[1][0]) + (a[2][0] + a[3][0]);
+  r1 = (a[0][1] + a[1][1]) + (a[2][1] + a[3][1]);
+  r2 = (a[0][2] + a[1][2]) + (a[2][2] + a[3][2]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    r0 += __shfl_xor_sync(0xffffffffu, r0, o);
+    r1 += __shfl_xor_sync(0xffffffffu, r1, o);
+    r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+  }
+}
+
 // one segment of a skyline row of S: S[row, seg] x[seg] (3 RHS); four
 // independent accumulator sets per lane keep several loads in flight. A row
 // of one segment is written directly; the segments of a split row write
@@ -218,6 +340,11 @@ __device__ __forceinline__ void assemble_finish(const Dev& d, St* c, int k, cons
 // the slots in slot order, so the result does not depend on the schedule.
 __device__ __forceinline__ void spmv_s_segment(const Dev& d, const float2* xin, float2* y, float2* part, int* cnt,
                                                int sg, int lane) {
+  if (d.sfp64) {
+    spmv_s_segment64(d, reinterpret_cast<const double*>(xin), reinterpret_cast<double*>(y),
+                     reinterpret_cast<double*>(part), cnt, sg, lane);
+    return;
+  }
   const int4 seg = d.s_seg[sg];  // x = row, y = offset in row, z = length, w = 0 or 1 + first slot of a split row
   const int row = seg.x;
   const float2* sv = d.s_hl + d.s_rowptr[row] + seg.y;
@@ -289,6 +416,10 @@ __device__ __forceinline__ void spmv_s_segment(const Dev& d, const float2* xin, 
 // to every lane; the indices of four entries are loaded before their y values
 __device__ __forceinline__ void spmv_st_sum(const Dev& d, const float2* y, int j, int lane, double& r0, double& r1,
                                             double& r2) {
+  if (d.sfp64) {
+    spmv_st_sum64(d, reinterpret_cast<const double*>(y), j, lane, r0, r1, r2);
+    return;
+  }
   const int64_t beg = d.st_ptr[j], end = d.st_ptr[j + 1];
   float ah[4][3], al[4][3];
 #pragma unroll

@@ -45,6 +45,7 @@ class SolverSettings:
     local_fp32: bool = True
     adj_tol: float = 1e-10
     adj_max_iters: int = 500
+    solve_fp64: bool = False     # S products in FP64 instead of double-float
 
 
 @dataclass
