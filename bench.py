@@ -301,6 +301,10 @@ def run_contact(args, rank, world, local_rank, dev, dist):
     T = min(args.contact_steps, sc.steps)
     opts = binding.options_for(sc.solver)
     opts.k_max = 2000
+    # FP64 products by default here: the adjoint's projected CG (fixed active
+    # sets) needs fewer iterations with them, which more than pays for the
+    # slower products
+    opts.solve_fp64 = 1 if args.solve_fp64 != 0 else 0
     t0 = time.perf_counter()
     pd = binding.PDContext(sc, opts)
     factor_s = time.perf_counter() - t0
@@ -355,8 +359,9 @@ def run_contact(args, rank, world, local_rank, dev, dist):
     peak, peak_kind = _peaks()
     line = {"metric": METRIC, "value": value, "unit": "PD steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64 (FP32 local step; FP64 RHS, factor, contact, adjoint; S products in double-float on the FP32 pipe)", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64 (FP32 local step; FP64 RHS, factor, contact, adjoint" + ("; FP64 S products)" if opts.solve_fp64 else "; S products in double-float on the FP32 pipe)"), "data": "synthetic",
             "config": {"workload": CONTACT_WORKLOAD, "pd_steps_per_bench_step": T,
+                       "s_products": "fp64" if opts.solve_fp64 else "double-float",
                        "note": f"first {T} of the configured 300 steps per benchmark step",
                        "factor_and_delassus_s": factor_s, "nnz_S": int(st.factor_nnz),
                        "fwd_iters_per_step": it / (args.steps * T), "adj_iters_per_step": adj / (args.steps * T),
@@ -381,6 +386,9 @@ def main():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="bar", choices=["bar", "batch", "contact"])
+    ap.add_argument("--solve-fp64", type=int, default=-1,
+                    help="S products in plain FP64 (1) or double-float (0); default: the workload's choice "
+                         "(double-float for bar and batch, FP64 for contact)")
     ap.add_argument("--contact-steps", type=int, default=20,
                     help="contact workload: PD steps of the 300-step rollout timed per benchmark step")
     args = ap.parse_args()
