@@ -97,6 +97,10 @@ typedef struct {
                              row's sum of magnitudes, at 64x the FP64 rate of this part;
                              1 plain FP64 (S and S^T also kept as FP64 values, 8 more bytes
                              per non-zero). Fixed at pd_create. */
+  int32_t wait_polls;     /* persistent launches: polls (about 0.5 us each) a block spends at
+                             a team barrier before it gives up, sets the timeout flag and
+                             returns; the call then fails with PD_ERR_TIMEOUT and the context
+                             stays usable (0 = 4194304, about 2 s). Fixed at pd_create. */
 } pd_options;
 
 /* Statistics of the last pd_rollout / pd_backward (host copy). */

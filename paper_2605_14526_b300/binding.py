@@ -39,7 +39,8 @@ class pd_options(ctypes.Structure):
                 ("tr_mode", c_int32), ("adj_max_iters", c_int32), ("persistent", c_int32),
                 ("eps_step", c_double), ("eps_res", c_double),
                 ("eps_abs", c_double), ("eps_tr", c_double), ("adj_tol", c_double),
-                ("escalate_window", c_int32), ("warm_start", c_int32), ("solve_fp64", c_int32)]
+                ("escalate_window", c_int32), ("warm_start", c_int32), ("solve_fp64", c_int32),
+                ("wait_polls", c_int32)]
 
 
 class pd_stats(ctypes.Structure):

@@ -140,6 +140,7 @@ void pd_default_options(pd_options* o) {
   o->escalate_window = 100;
   o->warm_start = 0;
   o->solve_fp64 = 0;
+  o->wait_polls = 0;
 }
 
 const char* pd_last_error(const pd_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -492,6 +493,7 @@ int pd_factor(pd_ctx* c) {
   d.coef32 = c32; d.coef64 = c64; d.mu_e = mu_d; d.lam_e = lam_d; d.E = E_d; d.cA = cA_d;
   d.iperm = iperm_d; d.perm = perm_d; d.s_rowptr = srp; d.s_first = sfirst; d.s_hl = sv; d.s_seg = seg_d;
   d.sfp64 = c->opt.solve_fp64 ? 1 : 0; d.s_val64 = sv64; d.st_val64 = stv64;
+  d.spin_limit = c->opt.wait_polls > 0 ? (unsigned int)c->opt.wait_polls : (1u << 22);
   d.n_seg = (int)seg.size(); d.st_ptr = stp; d.st_idx = sti; d.st_hl = stv;
   d.n_slot = n_slot; d.s_part = spart; d.s_cnt = scnt; d.s_part_na = spart_na; d.s_cnt_na = scnt_na;
   d.A_ptr = Ap; d.A_idx = Ai; d.A_val = Av; d.B_ptr = Bp; d.B_idx = Bi; d.B_val = Bv;
@@ -769,7 +771,12 @@ int stats_from_ctrl(pd_ctx* c, const Ctrl& hc, int which) {
     }
   }
   st.status_flags = hc.status;
-  if (hc.status & 4) return fail(c, PD_ERR_TIMEOUT, "a grid barrier of a persistent launch timed out");
+  if (hc.status & 4) {
+    // blocks that gave up may have left split-row counters set: clear them
+    // for pd_solve (persistent launches clear them at their start)
+    if (c->d.s_cnt && c->d.n_slot > 0) cudaMemset(c->d.s_cnt, 0, sizeof(int) * (size_t)c->d.n_slot);
+    return fail(c, PD_ERR_TIMEOUT, "a grid barrier of a persistent launch timed out");
+  }
   if ((which & 1) && (hc.status & 1)) return fail(c, PD_ERR_NUMERIC, "non-finite value in the right-hand side");
   if ((which & 2) && (hc.status & 2))
     return fail(c, PD_ERR_NUMERIC, "adjoint operator A - K not positive along a CG direction");

@@ -680,6 +680,10 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
     return grid_sync(d, tm);
   };
   for (int i = rb.lo + tid; i < rb.hi; i += blockDim.x) bwd_begin_item(d, i, a.dqT, a.dvT);
+  {   // split-row counters start at zero (a launch that timed out may have left some set)
+    const Range rc = block_range(tm, d.n_slot);
+    for (int i = rc.lo + tid; i < rc.hi; i += blockDim.x) d.s_cnt[i] = 0;
+  }
   bool ok = grid_sync(d, tm);
   for (int t = a.T - 1; t >= 0 && ok; --t) {
     const double* qstar = a.ckpt + (size_t)(t + 1) * nv3;

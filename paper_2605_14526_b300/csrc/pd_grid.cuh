@@ -9,7 +9,6 @@
 
 namespace pdk {
 
-constexpr unsigned int kSpinLimit = 1u << 22;   // polls (~0.4 us each with the sleep): ~2 s per wait at most
 constexpr int kStatusTimeout = 4;
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -56,7 +55,7 @@ __device__ __forceinline__ bool team_arrive_wait(const Dev& d, Team tm) {
   if (d.prof && n + 1 == open) c->t_last = gtimer();   // profiling: the last arrival
   unsigned int it = 0;
   while (ld_acquire64(&c->bar_arrive) < open) {
-    if (++it > kSpinLimit) {
+    if (++it > d.spin_limit) {
       atomicOr(&c->status, kStatusTimeout);
       return false;
     }
@@ -126,7 +125,7 @@ __device__ __forceinline__ bool grid_reduce_pub_v(const Dev& d, Team tm, double 
     if (!s_last) {
       unsigned int it = 0;
       while (ld_acquire64(&c->pub_open) < open) {
-        if (++it > kSpinLimit) {
+        if (++it > d.spin_limit) {
           atomicOr(&c->status, kStatusTimeout);
           s_fail = 1;
           break;

@@ -132,6 +132,7 @@ struct Dev {
   const int64_t* s_rowptr; // skyline rows of S
   const int* s_first;      // first_desc per row
   int sfp64;               // 1: the S products in FP64 (s_val64, st_val64; b, y as doubles)
+  unsigned int spin_limit; // polls of a team-barrier wait before it gives up
   const double* s_val64;   // S entries in FP64 (sfp64 only)
   const double* st_val64;  // S^T entries in FP64 (sfp64 only)
   const float2* s_hl;      // S entries as double-float pairs (hi, lo)

@@ -107,6 +107,12 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
     for (int i = 0; i < kMaxAA * kMaxAA; ++i) S.gram[i] = 0.0;
     tmr[0] = tmr[1] = tmr[2] = gtimer();
   }
+  // split-row counters start at zero (a launch that timed out may have left
+  // some set); the first S b comes after the step's first team barrier
+  {
+    const Range rc = block_range(tm, d.n_slot);
+    for (int i = rc.lo + tid; i < rc.hi; i += blockDim.x) d.s_cnt[i] = 0;
+  }
   bool ok = true;
   for (int t = 0; t < a.T && ok; ++t) {
     const double* qin = t == 0 ? a.q0 : a.sq;
