@@ -207,10 +207,12 @@ def rollout(pb, scene, cp=None):
 
 # ---------------------------------------------------------------- adjoint
 
-def active_sets(cp: ContactProblem, lam_n, lam_f, stick_tol: float = 1e-9):
+def active_sets(cp: ContactProblem, lam_n, lam_f, stick_tol: float = 1e-6):
     """Normal-active contacts (lam_n > 0) and sticking ones among them
-    (friction strictly inside its disk)."""
-    act = lam_n > 0.0
+    (friction inside its disk by more than stick_tol of the radius: an
+    iterative inner solver ends a sliding contact's friction within its
+    tolerance of the disk boundary, so the split sits above that)."""
+    act = lam_n > 1e-9 * lam_n.sum()   # above rounding of an inner iterate
     stick = act & (np.linalg.norm(lam_f, axis=1) < cp.spec.mu * lam_n * (1.0 - stick_tol))
     return act, stick
 

@@ -560,7 +560,7 @@ int pd_factor(pd_ctx* c) {
     int *cv_d, *cp_d;
     double *cn_d, *W_d, *buf_d;
     if ((r = upload(c, &cv_d, cv, true)) || (r = upload(c, &cp_d, cp, true)) || (r = upload(c, &cn_d, cn, true)) ||
-        (r = upload(c, &W_d, W, true)) || (r = dalloc(c, &buf_d, 12 * (size_t)K, true)))
+        (r = upload(c, &W_d, W, true)) || (r = dalloc(c, &buf_d, 14 * (size_t)K, true)))
       return r;
     double* bwd_d;
     if ((r = dalloc(c, &bwd_d, 18 * (size_t)K, true))) return r;
@@ -703,7 +703,7 @@ int enqueue_fwd_single(pd_ctx* c, int T, const double* q0d, const double* v0d, c
   CK(cudaMemsetAsync(c->tau, 0, (size_t)T * sizeof(double), s));
   CK(cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), s));  // per-rollout statistics and flags
   CK(cudaMemsetAsync(d.sstar, 0, 3 * sizeof(double) * (size_t)c->n_e, s));  // no prox warm start across rollouts
-  if (d.n_con > 0) CK(cudaMemsetAsync(d.con_buf, 0, 12 * sizeof(double) * (size_t)d.n_con, s));
+  if (d.n_con > 0) CK(cudaMemsetAsync(d.con_buf, 0, 14 * sizeof(double) * (size_t)d.n_con, s));
   pdk::BatchFwd br;
   br.T = T;
   br.q0 = q0d;

@@ -36,6 +36,9 @@ __device__ __forceinline__ double* con_lamf(const Dev& d, int r) {
 }
 __device__ __forceinline__ double* con_gap(const Dev& d) { return d.con_buf + 9 * (size_t)d.n_con; }
 __device__ __forceinline__ double* con_slip(const Dev& d) { return d.con_buf + 10 * (size_t)d.n_con; }
+// the pass's extrapolated multipliers z = cur + beta (cur - prev): n_c z_c for
+// the normal pass, (z_x, z_y) for the friction pass
+__device__ __forceinline__ double* con_z(const Dev& d) { return d.con_buf + 12 * (size_t)d.n_con; }
 
 // warp per candidate: q_u at the candidate (row pos_c of S^T y), its gap and
 // its slip since q_t
@@ -88,23 +91,33 @@ __device__ __forceinline__ void fista_finish(const Dev& d, St* S, int* rot, cons
   }
 }
 
-// normal LCP pass, warp per row c: z = cur + beta (cur - prev) on the fly;
-// next_c = max(0, z_c - ((D W D z)_c + g_c) / L)
-__device__ __forceinline__ void normal_row(const Dev& d, int c, int rot, double beta, int lane, double* part) {
-  const int K = d.n_con;
+// extrapolation of a pass, item c (block range over the candidates); the
+// rows below read it after a team barrier, so each W entry costs one FMA
+__device__ __forceinline__ void normal_z_item(const Dev& d, int c, int rot, double beta) {
   const double* prev = con_lamn(d, rot);
+  const double* cur = con_lamn(d, rot + 1);
+  con_z(d)[c] = d.con_n[c] * (cur[c] + beta * (cur[c] - prev[c]));
+}
+__device__ __forceinline__ void friction_z_item(const Dev& d, int c, int rot, double beta) {
+  const double* prev = con_lamf(d, rot);
+  const double* cur = con_lamf(d, rot + 1);
+  for (int k = 0; k < 2; ++k) con_z(d)[2 * c + k] = cur[2 * c + k] + beta * (cur[2 * c + k] - prev[2 * c + k]);
+}
+
+// normal LCP pass, warp per row c: next_c = max(0, z_c - ((D W D z)_c + g_c) / L)
+// with D z from the extrapolation buffer
+__device__ __forceinline__ void normal_row(const Dev& d, int c, int rot, int lane, double* part) {
+  const int K = d.n_con;
   const double* cur = con_lamn(d, rot + 1);
   double* nxt = con_lamn(d, rot + 2);
   const double* Wr = d.con_W + (size_t)c * K;
+  const double* z = con_z(d);
   double acc = 0.0;
-  for (int j = lane; j < K; j += 32) {
-    const double z = cur[j] + beta * (cur[j] - prev[j]);
-    acc += Wr[j] * d.con_n[j] * z;
-  }
+  for (int j = lane; j < K; j += 32) acc += Wr[j] * z[j];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) {
-    const double zc = cur[c] + beta * (cur[c] - prev[c]);
+    const double zc = d.con_n[c] * z[c];   // n_c = +-1
     const double grad = d.con_n[c] * acc + con_gap(d)[c];
     const double nv = fmax(0.0, zc - grad / d.con_L);
     nxt[c] = nv;
@@ -116,29 +129,29 @@ __device__ __forceinline__ void normal_row(const Dev& d, int c, int rot, double 
 }
 
 // Tresca pass, warp per row c: two components, disk radius mu * lam_n,c
-__device__ __forceinline__ void friction_row(const Dev& d, int c, int rot, double beta, const double* lam_n, int lane,
+__device__ __forceinline__ void friction_row(const Dev& d, int c, int rot, const double* lam_n, int lane,
                                              double* part) {
   const int K = d.n_con;
-  const double* prev = con_lamf(d, rot);
   const double* cur = con_lamf(d, rot + 1);
   double* nxt = con_lamf(d, rot + 2);
   const double* Wr = d.con_W + (size_t)c * K;
-  double ax = 0.0, ay = 0.0;
+  const double2* z = reinterpret_cast<const double2*>(con_z(d));
+  double sx = 0.0, sy = 0.0;
   for (int j = lane; j < K; j += 32) {
     const double w = Wr[j];
-    ax += w * (cur[2 * j] + beta * (cur[2 * j] - prev[2 * j]));
-    ay += w * (cur[2 * j + 1] + beta * (cur[2 * j + 1] - prev[2 * j + 1]));
+    const double2 zz = z[j];
+    sx += w * zz.x;
+    sy += w * zz.y;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    ax += __shfl_xor_sync(0xffffffffu, ax, o);
-    ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
   }
   if (lane == 0) {
-    const double zx = cur[2 * c] + beta * (cur[2 * c] - prev[2 * c]);
-    const double zy = cur[2 * c + 1] + beta * (cur[2 * c + 1] - prev[2 * c + 1]);
-    double nx = zx - (ax + con_slip(d)[2 * c]) / d.con_L;
-    double ny = zy - (ay + con_slip(d)[2 * c + 1]) / d.con_L;
+    const double zx = z[c].x, zy = z[c].y;
+    double nx = zx - (sx + con_slip(d)[2 * c]) / d.con_L;
+    double ny = zy - (sy + con_slip(d)[2 * c + 1]) / d.con_L;
     const double rho = d.con_mu * lam_n[c];
     const double r = sqrt(nx * nx + ny * ny);
     if (r > rho) {
@@ -195,7 +208,7 @@ __device__ __forceinline__ void contact_y_row(const Dev& d, int i, const double*
 // ---------------------------------------------------------------- adjoint
 //
 // With the active sets of step t held fixed (normal-active: lam_n > 0;
-// sticking: |lam_f| < mu lam_n (1 - 1e-9)), the adjoint solves
+// sticking: |lam_f| < mu lam_n (1 - 1e-6)), the adjoint solves
 //   (A - K) a + G^T nu = q_bar,  G a = 0
 // by the same preconditioned CG with the preconditioner projected
 // A-orthogonally onto null(G): z = A^-1 (r - G^T w), w = W_a^-1 G A^-1 r,
@@ -203,11 +216,15 @@ __device__ __forceinline__ void contact_y_row(const Dev& d, int i, const double*
 // last w is nu; its sticking rows enter dL/dq_t (the constraint
 // q_xy = q_t,xy of a sticking contact depends on q_t).
 
-__device__ __forceinline__ bool con_act(const Dev& d, const double* ck, int c) { return ck[c] > 0.0; }
-__device__ __forceinline__ bool con_stick(const Dev& d, const double* ck, int c) {
+// normal-active: lam_n above thr = 1e-9 x the step's total normal impulse (an
+// inactive contact's inner iterate can keep a rounding-level lam_n)
+__device__ __forceinline__ bool con_act(const Dev& d, const double* ck, int c, double thr) { return ck[c] > thr; }
+__device__ __forceinline__ bool con_stick(const Dev& d, const double* ck, int c, double thr) {
   const int K = d.n_con;
   const double lx = ck[K + 2 * c], ly = ck[K + 2 * c + 1];
-  return ck[c] > 0.0 && sqrt(lx * lx + ly * ly) < d.con_mu * ck[c] * (1.0 - 1e-9);
+  // the split sits above the inner FISTA's tolerance: a sliding contact's last
+  // iterate may end inside its disk by that much
+  return ck[c] > thr && sqrt(lx * lx + ly * ly) < d.con_mu * ck[c] * (1.0 - 1e-6);
 }
 // adjoint work buffers ([K][3] each unless noted)
 __device__ __forceinline__ double* cb_x(const Dev& d) { return d.con_bwd; }
@@ -219,11 +236,11 @@ __device__ __forceinline__ double* cb_nxy(const Dev& d) { return d.con_bwd + 16 
 
 // warp per candidate: u = G A^-1 r (masked rows of S^T y) as the CG
 // residual; w = 0; p = u; partial |u|^2 per axis
-__device__ __forceinline__ void proj_gather(const Dev& d, const double* ck, int c, int lane, double* part) {
+__device__ __forceinline__ void proj_gather(const Dev& d, const double* ck, double thr, int c, int lane, double* part) {
   double a0, a1, a2;
   spmv_st_sum(d, d.y, d.con_pos[c], lane, a0, a1, a2);
   if (lane == 0) {
-    const bool st = con_stick(d, ck, c), ac = con_act(d, ck, c);
+    const bool st = con_stick(d, ck, c, thr), ac = con_act(d, ck, c, thr);
     const double u[3] = {st ? a0 : 0.0, st ? a1 : 0.0, ac ? d.con_n[c] * a2 : 0.0};
     for (int k = 0; k < 3; ++k) {
       cb_x(d)[3 * c + k] = 0.0;
@@ -235,7 +252,7 @@ __device__ __forceinline__ void proj_gather(const Dev& d, const double* ck, int 
 }
 
 // warp per row: W_a p (axis 2 with the normal signs), partial p . W_a p
-__device__ __forceinline__ void proj_ap_row(const Dev& d, const double* ck, int c, int rot, int lane, double* part) {
+__device__ __forceinline__ void proj_ap_row(const Dev& d, const double* ck, double thr, int c, int rot, int lane, double* part) {
   const int K = d.n_con;
   const double* p = cb_p(d, rot);
   const double* Wr = d.con_W + (size_t)c * K;
@@ -253,7 +270,7 @@ __device__ __forceinline__ void proj_ap_row(const Dev& d, const double* ck, int 
     s2 += __shfl_xor_sync(0xffffffffu, s2, o);
   }
   if (lane == 0) {
-    const bool st = con_stick(d, ck, c), ac = con_act(d, ck, c);
+    const bool st = con_stick(d, ck, c, thr), ac = con_act(d, ck, c, thr);
     const double ap[3] = {st ? s0 : 0.0, st ? s1 : 0.0, ac ? d.con_n[c] * s2 : 0.0};
     for (int k = 0; k < 3; ++k) {
       cb_ap(d)[3 * c + k] = ap[k];

@@ -176,7 +176,7 @@ struct Dev {
   double con_L;            // largest eigenvalue of W (FISTA step 1/L)
   double con_mu, con_zg, con_zb0, con_travel, con_tol;
   int con_steps, con_max_iters;
-  double* con_buf;         // work: lam_n [3][K], lam_f [3][2K], gap [K], slip [2K]
+  double* con_buf;         // work: lam_n [3][K], lam_f [3][2K], gap [K], slip [2K], z [2K]
   double* con_ckpt;        // [T][3K]: converged lam_n [K], lam_f [K][2] of each step (adjoint)
   double* con_bwd;         // adjoint work [18K]: w, r, p (2 buffers), W p [K][3]; -G^T w parts
 

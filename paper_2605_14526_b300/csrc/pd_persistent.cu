@@ -158,11 +158,14 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
           if (!(ok = grid_sync(d, tm))) break;
           if (tid == 0) fista_reset(d, &S);
           __syncthreads();
+          const Range rk = block_range(tm, d.n_con);
           while (!S.f_done) {
             const int rot = S.rot_n;
             const double beta = S.f_beta;
+            for (int c = rk.lo + tid; c < rk.hi; c += blockDim.x) normal_z_item(d, c, rot, beta);
+            if (!(ok = grid_sync(d, tm))) break;
             double pc[3] = {0.0, 0.0, 0.0};
-            for (int c = gwarp; c < d.n_con; c += nwarps) normal_row(d, c, rot, beta, lane, pc);
+            for (int c = gwarp; c < d.n_con; c += nwarps) normal_row(d, c, rot, lane, pc);
             if (!(ok = grid_reduce<3>(d, tm, pc, sums))) break;
             if (tid == 0) fista_finish(d, &S, &S.rot_n, sums);
             __syncthreads();
@@ -174,8 +177,10 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
           while (!S.f_done) {
             const int rot = S.rot_f;
             const double beta = S.f_beta;
+            for (int c = rk.lo + tid; c < rk.hi; c += blockDim.x) friction_z_item(d, c, rot, beta);
+            if (!(ok = grid_sync(d, tm))) break;
             double pc[3] = {0.0, 0.0, 0.0};
-            for (int c = gwarp; c < d.n_con; c += nwarps) friction_row(d, c, rot, beta, lam_n, lane, pc);
+            for (int c = gwarp; c < d.n_con; c += nwarps) friction_row(d, c, rot, lam_n, lane, pc);
             if (!(ok = grid_reduce<3>(d, tm, pc, sums))) break;
             if (tid == 0) fista_finish(d, &S, &S.rot_f, sums);
             __syncthreads();

@@ -73,7 +73,7 @@ def _active_set_margins(sc, recs, cp):
         ln, lf = r["lam_n"], r["lam_f"]
         act = ln > 0
         ratio = np.linalg.norm(lf, axis=1) / np.maximum(mu * ln, 1e-300)
-        stick = act & (ratio < 1 - 1e-9)
+        stick = act & (ratio < 1 - 1e-6)
         slide = act & ~stick
         slip = np.linalg.norm(r["q_next"][cp.verts, :2] - r["q_t"][cp.verts, :2], axis=1)
         out.append((ln[act].min() / ln.max() if act.any() else 1.0,
