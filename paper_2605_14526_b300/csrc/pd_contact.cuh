@@ -233,6 +233,8 @@ __device__ __forceinline__ double* cb_p(const Dev& d, int r) { return d.con_bwd 
 __device__ __forceinline__ double* cb_ap(const Dev& d) { return d.con_bwd + 12 * (size_t)d.n_con; }
 __device__ __forceinline__ double* cb_nz(const Dev& d) { return d.con_bwd + 15 * (size_t)d.n_con; }    // [K]
 __device__ __forceinline__ double* cb_nxy(const Dev& d) { return d.con_bwd + 16 * (size_t)d.n_con; }   // [K][2]
+// n_c p_z of the current CG direction (the W rows then cost three FMAs per entry)
+__device__ __forceinline__ double* cb_pz(const Dev& d) { return d.con_bwd + 18 * (size_t)d.n_con; }   // [K]
 
 // warp per candidate: u = G A^-1 r (masked rows of S^T y) as the CG
 // residual; w = 0; p = u; partial |u|^2 per axis
@@ -248,6 +250,7 @@ __device__ __forceinline__ void proj_gather(const Dev& d, const double* ck, doub
       cb_p(d, 0)[3 * c + k] = u[k];
       part[k] += u[k] * u[k];
     }
+    cb_pz(d)[c] = d.con_n[c] * u[2];
   }
 }
 
@@ -255,13 +258,14 @@ __device__ __forceinline__ void proj_gather(const Dev& d, const double* ck, doub
 __device__ __forceinline__ void proj_ap_row(const Dev& d, const double* ck, double thr, int c, int rot, int lane, double* part) {
   const int K = d.n_con;
   const double* p = cb_p(d, rot);
+  const double* pz = cb_pz(d);
   const double* Wr = d.con_W + (size_t)c * K;
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
   for (int j = lane; j < K; j += 32) {
     const double w = Wr[j];
     s0 += w * p[3 * j];
     s1 += w * p[3 * j + 1];
-    s2 += w * d.con_n[j] * p[3 * j + 2];
+    s2 += w * pz[j];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -296,6 +300,7 @@ __device__ __forceinline__ void proj_dir(const Dev& d, int c, int rot, const dou
   const double* p = cb_p(d, rot);
   double* pn = cb_p(d, rot + 1);
   for (int k = 0; k < 3; ++k) pn[3 * c + k] = cb_r(d)[3 * c + k] + beta[k] * p[3 * c + k];
+  cb_pz(d)[c] = d.con_n[c] * pn[3 * c + 2];
 }
 
 // thread per candidate: the impulse parts of -G^T w for the y correction
