@@ -301,10 +301,7 @@ def run_contact(args, rank, world, local_rank, dev, dist):
     T = min(args.contact_steps, sc.steps)
     opts = binding.options_for(sc.solver)
     opts.k_max = 2000
-    # FP64 products by default here: the adjoint's projected CG (fixed active
-    # sets) needs fewer iterations with them, which more than pays for the
-    # slower products
-    opts.solve_fp64 = 1 if args.solve_fp64 != 0 else 0
+    opts.solve_fp64 = 1 if args.solve_fp64 == 1 else 0
     t0 = time.perf_counter()
     pd = binding.PDContext(sc, opts)
     factor_s = time.perf_counter() - t0
@@ -387,8 +384,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="bar", choices=["bar", "batch", "contact"])
     ap.add_argument("--solve-fp64", type=int, default=-1,
-                    help="S products in plain FP64 (1) or double-float (0); default: the workload's choice "
-                         "(double-float for bar and batch, FP64 for contact)")
+                    help="contact workload: S products in plain FP64 (1) instead of double-float (default)")
     ap.add_argument("--contact-steps", type=int, default=20,
                     help="contact workload: PD steps of the 300-step rollout timed per benchmark step")
     args = ap.parse_args()

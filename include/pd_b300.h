@@ -174,9 +174,19 @@ int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_o
  * LCP 0 <= lam_n _|_ D W D lam_n + g >= 0 and the Tresca QP of the friction
  * on W (FISTA with adaptive restart), and takes q = A^-1 (b + J^T lam)
  * (eq. q_update) through the same two products with S. Persistent launches
- * only; the adjoint of a contact rollout is not built (pd_backward returns
- * PD_ERR_ARG). */
+ * only. pd_backward differentiates a contact rollout with each step's active
+ * sets held fixed (normal-active and sticking contacts as equality
+ * constraints, projected preconditioned CG). */
 int pd_set_contacts(pd_ctx* ctx, const pd_contact_desc* desc);
+
+/* Contact impulses of step t (0 <= t < T) of the last rollout: n_out = the
+ * number K of candidates; vertex [K] (the candidate's vertex), lam_n [K]
+ * (normal impulse, >= 0, along +z for ground and -z for box candidates),
+ * lam_f [K][2] (tangential x, y impulse). Any of the three arrays may be
+ * NULL (only n_out is written when all are). Host outputs; synchronous.
+ * Candidates come in elimination order, not in the order of the descriptor. */
+int pd_get_contact_impulses(const pd_ctx* ctx, int32_t t, int32_t* n_out, int32_t* vertex, double* lam_n,
+                            double* lam_f);
 
 /* Replace the Young's moduli ([n_e], host, Pa) and Poisson ratio; marks A stale
  * so that the next pd_factor refactors (Sec. 4.5 refactorisation policy). */

@@ -138,6 +138,10 @@ class ContactProblem:
         self.verts, self.normal = self.verts[order], self.normal[order]
         self.pos = np.searchsorted(pb.free, self.verts)
         self.W = delassus(pb, self.verts)
+        # slip below which a contact counts as sticking: 1e-7 of the rest
+        # mesh's bounding-box diagonal
+        X = pb.X
+        self.slip_tol = 1e-7 * float(np.linalg.norm(X.max(axis=0) - X.min(axis=0)))
 
     def heights(self, t: int) -> np.ndarray:
         return np.where(self.normal > 0, self.spec.ground_z, self.spec.box_z(t))
@@ -207,13 +211,18 @@ def rollout(pb, scene, cp=None):
 
 # ---------------------------------------------------------------- adjoint
 
-def active_sets(cp: ContactProblem, lam_n, lam_f, stick_tol: float = 1e-6):
-    """Normal-active contacts (lam_n > 0) and sticking ones among them
-    (friction inside its disk by more than stick_tol of the radius: an
-    iterative inner solver ends a sliding contact's friction within its
-    tolerance of the disk boundary, so the split sits above that)."""
-    act = lam_n > 1e-9 * lam_n.sum()   # above rounding of an inner iterate
-    stick = act & (np.linalg.norm(lam_f, axis=1) < cp.spec.mu * lam_n * (1.0 - stick_tol))
+def active_sets(cp: ContactProblem, lam_n, q_next, q_t):
+    """Normal-active contacts (lam_n above 1e-9 of the step's total normal
+    impulse) and sticking ones among them: those whose tangential slip
+    q_xy - q_t,xy over the step is at most cp.slip_tol. At an exact solution
+    a contact with friction strictly inside its disk does not slip and a
+    sliding one has its friction on the disk boundary, so this is the same
+    split as the one by the multipliers; it reads the positions, which an
+    iterative inner solver determines far better than the multipliers in
+    the ill-conditioned directions of W."""
+    act = lam_n > 1e-9 * lam_n.sum()
+    slip = np.linalg.norm(q_next[cp.verts, :2] - q_t[cp.verts, :2], axis=1)
+    stick = act & (slip <= cp.slip_tol) & (cp.spec.mu > 0.0)   # no friction: never held
     return act, stick
 
 
@@ -247,7 +256,7 @@ def backward_step(pb, cp: ContactProblem, rec, tau: float, qbar_next, vbar_next)
     h = pb.h
     qbar = qbar_next + vbar_next / h
     q_star, q_t = rec["q_next"], rec["q_t"]
-    act, stick = active_sets(cp, rec["lam_n"], rec["lam_f"])
+    act, stick = active_sets(cp, rec["lam_n"], rec["q_next"], rec["q_t"])
     G, tags = constraint_rows(pb, cp, act, stick)
     K = adjoint.assemble_K(pb, q_star, tau)
     f3 = (3 * pb.free[:, None] + np.arange(3)[None, :]).ravel()

@@ -97,6 +97,7 @@ def lib():
             "pd_backward": (c_int, [P, P, P, P, P, P, P, P, c_int64, P]),
             "pd_get_mass": (c_int, [P, P]),
             "pd_get_tau": (c_int, [P, P, c_int32]),
+            "pd_get_contact_impulses": (c_int, [P, c_int32, P, P, P, P]),
             "pd_get_checkpoint": (c_int, [P, c_int32, P]),
             "pd_get_stats": (c_int, [P, P]),
             "pd_solve": (c_int, [P, P, P, P]),
@@ -253,6 +254,19 @@ def pd_get_checkpoint(ctx, t, n_v):
     q = np.zeros((n_v, 3))
     _check(ctx, lib().pd_get_checkpoint(ctx, int(t), _ptr(q)))
     return q
+
+
+def pd_get_contact_impulses(ctx, t):
+    """(vertex [K], lam_n [K], lam_f [K,2]) of step t of the last rollout."""
+    n = ctypes.c_int32(0)
+    _check(ctx, lib().pd_get_contact_impulses(ctx, int(t), ctypes.byref(n), None, None, None))
+    K = n.value
+    v = np.zeros(K, dtype=np.int32)
+    ln = np.zeros(K)
+    lf = np.zeros((K, 2))
+    if K:
+        _check(ctx, lib().pd_get_contact_impulses(ctx, int(t), ctypes.byref(n), _ptr(v, np.int32), _ptr(ln), _ptr(lf)))
+    return v, ln, lf
 
 
 def pd_get_tau(ctx, T):

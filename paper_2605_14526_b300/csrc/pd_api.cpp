@@ -563,7 +563,7 @@ int pd_factor(pd_ctx* c) {
         (r = upload(c, &W_d, W, true)) || (r = dalloc(c, &buf_d, 14 * (size_t)K, true)))
       return r;
     double* bwd_d;
-    if ((r = dalloc(c, &bwd_d, 19 * (size_t)K, true))) return r;
+    if ((r = dalloc(c, &bwd_d, 20 * (size_t)K, true))) return r;
     d.con_bwd = bwd_d;
     if (c->con_ckpt) cudaFree(c->con_ckpt);   // sized with the checkpoints (reserve)
     c->con_ckpt = nullptr;
@@ -576,6 +576,16 @@ int pd_factor(pd_ctx* c) {
     d.con_W = W_d;
     d.con_buf = buf_d;
     d.con_L = 1.001 * lmax;   // a little above lambda_max: the step stays below 1 / L
+    {   // sticking slip tolerance: 1e-7 of the rest mesh's bounding-box diagonal
+      double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+      for (int v = 0; v < c->n_v; ++v)
+        for (int k = 0; k < 3; ++k) {
+          lo[k] = std::min(lo[k], c->X[3 * v + k]);
+          hi[k] = std::max(hi[k], c->X[3 * v + k]);
+        }
+      d.con_slip_tol = 1e-7 * std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                                        (hi[2] - lo[2]) * (hi[2] - lo[2]));
+    }
     d.con_mu = c->con.mu;
     d.con_zg = c->con.ground_z;
     d.con_zb0 = c->con.box_z0;
@@ -1104,6 +1114,29 @@ int pd_get_tau(const pd_ctx* c, double* tau_host, int32_t T) {
   if (c && c->batch) return batch_get_tau(c, tau_host, T);
   if (!c || !tau_host || T < 1 || T > c->last_T || !c->tau) return PD_ERR_ARG;
   if (cudaMemcpy(tau_host, c->tau, (size_t)T * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return PD_ERR_CUDA;
+  return PD_OK;
+}
+
+int pd_get_contact_impulses(const pd_ctx* c, int32_t t, int32_t* n_out, int32_t* vertex, double* lam_n,
+                            double* lam_f) {
+  if (!c || !n_out || c->batch) return PD_ERR_ARG;
+  const int K = c->d.n_con;
+  *n_out = K;
+  if (K == 0 || (!vertex && !lam_n && !lam_f)) return PD_OK;
+  if (!c->d.con_ckpt || t < 0 || t >= c->last_T) return PD_ERR_ARG;
+  std::vector<double> ck(3 * (size_t)K);
+  if (cudaMemcpy(ck.data(), c->d.con_ckpt + (size_t)t * 3 * K, ck.size() * sizeof(double), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return PD_ERR_CUDA;
+  if (vertex && cudaMemcpy(vertex, c->d.con_v, (size_t)K * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return PD_ERR_CUDA;
+  for (int i = 0; i < K; ++i) {
+    if (lam_n) lam_n[i] = ck[i];
+    if (lam_f) {
+      lam_f[2 * i] = ck[K + 2 * i];
+      lam_f[2 * i + 1] = ck[K + 2 * i + 1];
+    }
+  }
   return PD_OK;
 }
 

@@ -461,6 +461,10 @@ __device__ __forceinline__ void pcg_z_finish(const Dev& d, St* c, const double* 
   c->beta = rz / c->rz;
   c->rz = rz;
   c->adj_k += 1;
+  // also ends when r . z stops being positive: with contact constraints the
+  // projected preconditioner is positive only up to the consistency of W with
+  // the device's A^-1, and r . z falls through zero once the residual reaches
+  // that level (the accuracy the projection allows)
   if (!(rz > d.adj_tol * d.adj_tol * c->rz0)) {
     c->adj_done = 1;
   } else if (c->adj_k >= d.adj_max_iters) {
@@ -629,10 +633,9 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
   // contact: after y = S r, project the preconditioned residual onto null(G):
   // w = W_a^-1 G A^-1 r by CG on the active rows (per axis), then
   // y <- y - S G^T w, so that the S^T pass gives A^-1 (r - G^T w)
-  __shared__ double s_con_thr;   // normal-active threshold of the current step
   auto project = [&](const double* ck) -> bool {
     double pu[3] = {0.0, 0.0, 0.0};
-    for (int c = gwarp; c < d.n_con; c += nwarps) proj_gather(d, ck, s_con_thr, c, lane, pu);
+    for (int c = gwarp; c < d.n_con; c += nwarps) proj_gather(d, c, lane, pu);
     if (!grid_reduce<3>(d, tm, pu, sums)) return false;
     if (tid == 0) {
       for (int k = 0; k < 3; ++k) S.cg_rr[k] = S.cg_rr0[k] = sums[k];
@@ -644,7 +647,7 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
     while (!S.cg_done) {
       const int rot = S.cg_rot;
       double pa[3] = {0.0, 0.0, 0.0};
-      for (int c = gwarp; c < d.n_con; c += nwarps) proj_ap_row(d, ck, s_con_thr, c, rot, lane, pa);
+      for (int c = gwarp; c < d.n_con; c += nwarps) proj_ap_row(d, c, rot, lane, pa);
       if (!grid_reduce<3>(d, tm, pa, sums)) return false;
       if (tid == 0)
         for (int k = 0; k < 3; ++k) S.cg_alpha[k] = (S.cg_rr[k] > 0.0 && sums[k] > 0.0) ? S.cg_rr[k] / sums[k] : 0.0;
@@ -695,8 +698,8 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
       double ps[1] = {0.0};
       for (int c = rcn.lo + tid; c < rcn.hi; c += blockDim.x) ps[0] += ck[c];
       if (!(ok = grid_reduce<1>(d, tm, ps, sums))) break;
-      if (tid == 0) s_con_thr = 1e-9 * sums[0];
-      __syncthreads();
+      const double thr = 1e-9 * sums[0];
+      for (int c = rcn.lo + tid; c < rcn.hi; c += blockDim.x) contact_flag_item(d, ck, thr, qstar, qt, c);
     }
     for (int e = re.lo + tid; e < re.hi; e += blockDim.x) bwd_setup_item<T>(d, e, qstar, tau);
     for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) bwd_init_item(d, v);
@@ -767,7 +770,7 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
     if (ck) {
       // sticking contacts: the constraint q_xy = q_t,xy routes nu_S to dL/dq_t
       for (int c = rcn.lo + tid; c < rcn.hi; c += blockDim.x)
-        if (con_stick(d, ck, c, s_con_thr)) {
+        if (con_stick(d, c)) {
           const int v = d.con_v[c];
           d.gq[3 * (size_t)v] += cb_x(d)[3 * c];
           d.gq[3 * (size_t)v + 1] += cb_x(d)[3 * c + 1];

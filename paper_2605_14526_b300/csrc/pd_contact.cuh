@@ -208,7 +208,7 @@ __device__ __forceinline__ void contact_y_row(const Dev& d, int i, const double*
 // ---------------------------------------------------------------- adjoint
 //
 // With the active sets of step t held fixed (normal-active: lam_n > 0;
-// sticking: |lam_f| < mu lam_n (1 - 1e-6)), the adjoint solves
+// sticking: no slip, see contact_flag_item), the adjoint solves
 //   (A - K) a + G^T nu = q_bar,  G a = 0
 // by the same preconditioned CG with the preconditioner projected
 // A-orthogonally onto null(G): z = A^-1 (r - G^T w), w = W_a^-1 G A^-1 r,
@@ -216,15 +216,25 @@ __device__ __forceinline__ void contact_y_row(const Dev& d, int i, const double*
 // last w is nu; its sticking rows enter dL/dq_t (the constraint
 // q_xy = q_t,xy of a sticking contact depends on q_t).
 
+// active sets of the step, one flag per candidate (bit 0 normal-active,
+// bit 1 sticking), formed at the step's start by contact_flag_item
+__device__ __forceinline__ double* cb_flag(const Dev& d) { return d.con_bwd + 19 * (size_t)d.n_con; }   // [K]
+__device__ __forceinline__ bool con_act(const Dev& d, int c) { return ((int)cb_flag(d)[c] & 1) != 0; }
+__device__ __forceinline__ bool con_stick(const Dev& d, int c) { return ((int)cb_flag(d)[c] & 2) != 0; }
+
 // normal-active: lam_n above thr = 1e-9 x the step's total normal impulse (an
-// inactive contact's inner iterate can keep a rounding-level lam_n)
-__device__ __forceinline__ bool con_act(const Dev& d, const double* ck, int c, double thr) { return ck[c] > thr; }
-__device__ __forceinline__ bool con_stick(const Dev& d, const double* ck, int c, double thr) {
-  const int K = d.n_con;
-  const double lx = ck[K + 2 * c], ly = ck[K + 2 * c + 1];
-  // the split sits above the inner FISTA's tolerance: a sliding contact's last
-  // iterate may end inside its disk by that much
-  return ck[c] > thr && sqrt(lx * lx + ly * ly) < d.con_mu * ck[c] * (1.0 - 1e-6);
+// inactive contact's inner iterate can keep a rounding-level lam_n);
+// sticking: active, with friction, and a tangential slip over the step of at
+// most con_slip_tol (an exact solution does not slip where the friction is
+// strictly inside its disk; the positions are determined far better than the
+// multipliers in the ill-conditioned directions of W)
+__device__ __forceinline__ void contact_flag_item(const Dev& d, const double* ck, double thr, const double* qnext,
+                                                  const double* qt, int c) {
+  const bool act = ck[c] > thr;
+  const size_t v = 3 * (size_t)d.con_v[c];
+  const double sx = qnext[v] - qt[v], sy = qnext[v + 1] - qt[v + 1];
+  const bool stick = act && d.con_mu > 0.0 && sqrt(sx * sx + sy * sy) <= d.con_slip_tol;
+  cb_flag(d)[c] = (double)((act ? 1 : 0) | (stick ? 2 : 0));
 }
 // adjoint work buffers ([K][3] each unless noted)
 __device__ __forceinline__ double* cb_x(const Dev& d) { return d.con_bwd; }
@@ -238,11 +248,11 @@ __device__ __forceinline__ double* cb_pz(const Dev& d) { return d.con_bwd + 18 *
 
 // warp per candidate: u = G A^-1 r (masked rows of S^T y) as the CG
 // residual; w = 0; p = u; partial |u|^2 per axis
-__device__ __forceinline__ void proj_gather(const Dev& d, const double* ck, double thr, int c, int lane, double* part) {
+__device__ __forceinline__ void proj_gather(const Dev& d, int c, int lane, double* part) {
   double a0, a1, a2;
   spmv_st_sum(d, d.y, d.con_pos[c], lane, a0, a1, a2);
   if (lane == 0) {
-    const bool st = con_stick(d, ck, c, thr), ac = con_act(d, ck, c, thr);
+    const bool st = con_stick(d, c), ac = con_act(d, c);
     const double u[3] = {st ? a0 : 0.0, st ? a1 : 0.0, ac ? d.con_n[c] * a2 : 0.0};
     for (int k = 0; k < 3; ++k) {
       cb_x(d)[3 * c + k] = 0.0;
@@ -255,7 +265,7 @@ __device__ __forceinline__ void proj_gather(const Dev& d, const double* ck, doub
 }
 
 // warp per row: W_a p (axis 2 with the normal signs), partial p . W_a p
-__device__ __forceinline__ void proj_ap_row(const Dev& d, const double* ck, double thr, int c, int rot, int lane, double* part) {
+__device__ __forceinline__ void proj_ap_row(const Dev& d, int c, int rot, int lane, double* part) {
   const int K = d.n_con;
   const double* p = cb_p(d, rot);
   const double* pz = cb_pz(d);
@@ -274,7 +284,7 @@ __device__ __forceinline__ void proj_ap_row(const Dev& d, const double* ck, doub
     s2 += __shfl_xor_sync(0xffffffffu, s2, o);
   }
   if (lane == 0) {
-    const bool st = con_stick(d, ck, c, thr), ac = con_act(d, ck, c, thr);
+    const bool st = con_stick(d, c), ac = con_act(d, c);
     const double ap[3] = {st ? s0 : 0.0, st ? s1 : 0.0, ac ? d.con_n[c] * s2 : 0.0};
     for (int k = 0; k < 3; ++k) {
       cb_ap(d)[3 * c + k] = ap[k];

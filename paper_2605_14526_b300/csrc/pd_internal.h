@@ -175,10 +175,11 @@ struct Dev {
   const double* con_W;     // [K][K]
   double con_L;            // largest eigenvalue of W (FISTA step 1/L)
   double con_mu, con_zg, con_zb0, con_travel, con_tol;
+  double con_slip_tol;     // adjoint: slip over a step at most this counts as sticking
   int con_steps, con_max_iters;
   double* con_buf;         // work: lam_n [3][K], lam_f [3][2K], gap [K], slip [2K], z [2K]
   double* con_ckpt;        // [T][3K]: converged lam_n [K], lam_f [K][2] of each step (adjoint)
-  double* con_bwd;         // adjoint work [19K]: w, r, p (2 buffers), W p [K][3]; -G^T w parts
+  double* con_bwd;         // adjoint work [20K]: w, r, p (2 buffers), W p [K][3]; -G^T w parts
 
   // rollout storage
   double* sq;       // [n_v][3] state carried between steps of a rollout

@@ -101,3 +101,18 @@ def test_contact_adjoint_fp64_matches_oracle(oracle_pad):
     assert rel(dv0.cpu().numpy(), g_o.dv0) <= 1e-4, rel(dv0.cpu().numpy(), g_o.dv0)
     assert rel(dq0.cpu().numpy(), g_o.dx0) <= 1e-4, rel(dq0.cpu().numpy(), g_o.dx0)
     assert rel(dE.cpu().numpy(), g_o.dE) <= 1e-4, rel(dE.cpu().numpy(), g_o.dE)
+
+
+def test_contact_impulses_match_oracle(oracle_pad):
+    """pd_get_contact_impulses: the converged normal and friction impulses of
+    every step against the oracle's exact LCP / Tresca solutions."""
+    sc, qT, recs, cp = oracle_pad
+    code, q, st, pd = _gpu(sc, local_fp32=False, eps_res=1e-10, eps_step=1e-12, k_max=3000)
+    assert binding.STATUS[code] == "PD_OK"
+    for t in range(sc.steps):
+        v, ln, lf = binding.pd_get_contact_impulses(pd.ctx, t)
+        o = np.argsort(v)
+        assert np.array_equal(v[o], cp.verts)
+        assert rel(ln[o], recs[t]["lam_n"]) <= 1e-6
+        assert rel(lf[o], recs[t]["lam_f"]) <= 1e-5
+        assert np.all(ln >= 0.0)

@@ -142,7 +142,7 @@ def test_contact_adjoint_matches_finite_differences(mu):
     pb = solver.build_problem(sc)
     cp = contact.ContactProblem(pb, sc.contact)
     L, qT, recs = _loss(sc, pb, cp, v0)
-    act, stick = contact.active_sets(cp, recs[-1]["lam_n"], recs[-1]["lam_f"])
+    act, stick = contact.active_sets(cp, recs[-1]["lam_n"], recs[-1]["q_next"], recs[-1]["q_t"])
     assert act.any()
     if mu > 0:
         assert np.array_equal(act, stick)
