@@ -3,7 +3,8 @@ bar (32x8x8 hex cells -> 10,240 tets, 2,673 vertices, 100x stiffness contrast,
 200 implicit-Euler steps at dt = 5 ms, Anderson m = 5, dual gate tightened to
 2e-7 (b-change) / 2e-9 (q-step) so that the 200-step trajectory stays within
 1e-5 of the oracle's exact fixed points, FP32 local step with FP64
-accumulation, FP64 factor and solves), against the FP64 CPU oracle.
+accumulation, FP64 factor, products with the inverse factor in double-float
+on the FP32 pipe), against the FP64 CPU oracle.
 
 One benchmark step = one full rollout of 200 PD steps forward followed by its
 adjoint (200 PD steps backward). value = PD steps (forward+backward) per
@@ -301,7 +302,7 @@ def run_contact(args, rank, world, local_rank, dev, dist):
     T = min(args.contact_steps, sc.steps)
     opts = binding.options_for(sc.solver)
     opts.k_max = 2000
-    opts.solve_fp64 = 1 if args.solve_fp64 == 1 else 0
+    opts.solve_fp64 = 1   # contact contexts always run FP64 products (the library enforces it)
     t0 = time.perf_counter()
     pd = binding.PDContext(sc, opts)
     factor_s = time.perf_counter() - t0
@@ -383,8 +384,6 @@ def main():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="bar", choices=["bar", "batch", "contact"])
-    ap.add_argument("--solve-fp64", type=int, default=-1,
-                    help="contact workload: S products in plain FP64 (1) instead of double-float (default)")
     ap.add_argument("--contact-steps", type=int, default=20,
                     help="contact workload: PD steps of the 300-step rollout timed per benchmark step")
     args = ap.parse_args()

@@ -96,7 +96,10 @@ typedef struct {
                              b and y held as (hi, lo) float pairs, error of order 2^-44 of the
                              row's sum of magnitudes, at 64x the FP64 rate of this part;
                              1 plain FP64 (S and S^T also kept as FP64 values, 8 more bytes
-                             per non-zero). Fixed at pd_create. */
+                             per non-zero). Fixed at pd_create. A context with contacts
+                             (pd_set_contacts) always uses FP64 products: its Delassus
+                             matrix comes from the FP64 factor and the adjoint's
+                             projection needs A^-1 to agree with it. */
   int32_t wait_polls;     /* persistent launches: polls (about 0.5 us each) a block spends at
                              a team barrier before it gives up, sets the timeout flag and
                              returns; the call then fails with PD_ERR_TIMEOUT and the context

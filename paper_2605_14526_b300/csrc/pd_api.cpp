@@ -444,7 +444,11 @@ int pd_factor(pd_ctx* c) {
   };
   const std::vector<float2> s_hl = split(s_val), st_hl = split(st_val);
   double *sv64 = nullptr, *stv64 = nullptr;
-  if (c->opt.solve_fp64) {
+  // contact contexts keep the products in FP64: W is formed from the FP64
+  // factor, and the adjoint's projection needs the device's A^-1 to agree
+  // with it (with double-float products its projected CG does not settle)
+  const bool s64 = c->opt.solve_fp64 || !c->con_ground.empty() || !c->con_box.empty();
+  if (s64) {
     int r0;
     if ((r0 = upload(c, &sv64, s_val, true)) || (r0 = upload(c, &stv64, st_val, true))) return r0;
   }
@@ -492,7 +496,7 @@ int pd_factor(pd_ctx* c) {
   }
   d.coef32 = c32; d.coef64 = c64; d.mu_e = mu_d; d.lam_e = lam_d; d.E = E_d; d.cA = cA_d;
   d.iperm = iperm_d; d.perm = perm_d; d.s_rowptr = srp; d.s_first = sfirst; d.s_hl = sv; d.s_seg = seg_d;
-  d.sfp64 = c->opt.solve_fp64 ? 1 : 0; d.s_val64 = sv64; d.st_val64 = stv64;
+  d.sfp64 = s64 ? 1 : 0; d.s_val64 = sv64; d.st_val64 = stv64;
   d.spin_limit = c->opt.wait_polls > 0 ? (unsigned int)c->opt.wait_polls : (1u << 22);
   d.n_seg = (int)seg.size(); d.st_ptr = stp; d.st_idx = sti; d.st_hl = stv;
   d.n_slot = n_slot; d.s_part = spart; d.s_cnt = scnt; d.s_part_na = spart_na; d.s_cnt_na = scnt_na;

@@ -32,6 +32,7 @@ struct BwdState {
   // contact projection: the masked CG on W_a, one scalar set per axis
   double cg_rr[3], cg_rr0[3], cg_alpha[3], cg_beta[3];
   int cg_done, cg_it, cg_rot, con_cg, con_cg_unconverged;
+  int restart, restarts;   // contact: restarts of the outer CG from its true residual
 };
 
 template <typename T>
@@ -299,6 +300,34 @@ __device__ __forceinline__ void pcg_w_warp(const Dev& d, int v, const double* po
   pnew[o] = pn;
   d.w[o] = w;
   part[0] += pn * w;
+}
+
+// true residual of the adjoint equations, one warp per vertex: r = q_bar -
+// (A mu - K mu) with K mu from the corner contributions of kapply_item(mu);
+// r also goes to the right-hand side of the next product with S
+template <typename T>
+__device__ __forceinline__ void resid_warp(const Dev& d, int v, int lane) {
+  if (d.pinned[v]) return;
+  const T* cb = reinterpret_cast<const T*>(d.contrib);
+  double c[3] = {0.0, 0.0, 0.0};
+  for (int p = d.A_ptr[v] + lane; p < d.A_ptr[v + 1]; p += 32) {
+    const int u = d.A_idx[p];
+    const double a = d.A_val[p];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) c[i] += a * d.mu[3 * (size_t)u + i];
+  }
+  for (int p = d.inc_ptr[v] + lane; p < d.inc_ptr[v + 1]; p += 32) {
+    const int ic = d.inc_idx[p];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) c[i] -= (double)cb[3 * (size_t)ic + i];
+  }
+  int i;
+  const double w = warp_sum_scatter<3>(c, lane, i);
+  if ((lane & 7) != 0 || i >= 3) return;
+  const size_t o = 3 * (size_t)v + i;
+  const double r = d.qbar[o] - w;
+  d.r[o] = r;
+  store_rhs(d, d.bperm, 3 * (size_t)d.iperm[v] + i, r);
 }
 
 __device__ __forceinline__ void pcg_r_item(const Dev& d, int v, double alpha, const double* pdir = nullptr) {
@@ -727,6 +756,7 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
     if (tid == 0) {
       init_z_finish(&S, sums);
       S.beta = 0.0;
+      S.restart = S.restarts = 0;
     }
     __syncthreads();
     // one CG iteration: K p (elements, p formed on the fly) | p stored, w = A p
@@ -734,6 +764,30 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
     // between two buffers so that the owners can store p while the
     // neighbours still read p_old
     for (int it = 0; !S.adj_done; ++it) {
+      if (S.restart) {
+        // contact: r . z fell through zero while the residual was still above
+        // the target (the projection of the preconditioner is only as
+        // consistent as W with the device's A^-1, and the recursive residual
+        // drifts); start again from the true residual q_bar - (A - K) mu
+        for (int e = re.lo + tid; e < re.hi; e += blockDim.x) kapply_item<T>(d, e, d.mu);
+        if (!(ok = grid_sync(d, tm))) break;
+        for (int v = rv.lo + (tid >> 5); v < rv.hi; v += blockDim.x >> 5) resid_warp<T>(d, v, lane);
+        if (!(ok = grid_sync(d, tm))) break;
+        for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, d.s_part, d.s_cnt, sg, lane);
+        if (!(ok = grid_sync(d, tm))) break;
+        if (ck && !(ok = project(ck))) break;
+        double prz0[1] = {0.0};
+        st_rz(prz0);
+        if (!(ok = grid_reduce<1>(d, tm, prz0, sums))) break;
+        if (tid == 0) {
+          S.rz = sums[0];
+          S.beta = 0.0;
+          S.restart = 0;
+          if (!(S.rz > d.adj_tol * d.adj_tol * S.rz0)) S.adj_done = 1;
+        }
+        __syncthreads();
+        if (S.adj_done) break;
+      }
       const double beta = S.beta;
       const double* pold = (it & 1) ? d.pdir2 : d.pdir;
       double* pnew = (it & 1) ? d.pdir : d.pdir2;
@@ -754,7 +808,17 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
       double prz[1] = {0.0};
       st_rz(prz);
       if (!(ok = grid_reduce<1>(d, tm, prz, sums))) break;
-      if (tid == 0) pcg_z_finish(d, &S, sums);
+      if (tid == 0) {
+        pcg_z_finish(d, &S, sums);
+        // contact: a negative r . z above the projection's floor (1e-16 of
+        // the first r . z, i.e. a relative residual of about 1e-8) is a
+        // breakdown, not convergence: restart (at most 4 times a step)
+        if (ck && S.adj_done && S.rz < -1e-16 * S.rz0 && S.restarts < 4 && S.adj_k < d.adj_max_iters) {
+          S.adj_done = 0;
+          S.restart = 1;
+          S.restarts += 1;
+        }
+      }
       __syncthreads();
     }
     if (!ok) break;
