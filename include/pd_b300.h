@@ -301,7 +301,8 @@ typedef struct {
   double work_max_ms[8]; /* the largest total over the blocks of each block's own work per phase
                             (the critical block; the rest of phase_ms is barrier and reduction) */
   double last_ms[8];     /* per iteration, the phase's start (block 0) to the last block's arrival
-                            at the phase's closing barrier, summed: the critical path's work */
+                            at the phase's closing barrier, summed; approximate (block 0 may read
+                            the last arrival's timestamp before it lands and then skips it) */
 } pd_profile_out;
 
 /* enable != 0 turns the phase timers on (and clears them); 0 turns them off. */
