@@ -257,7 +257,7 @@ int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_o
   d.jac = jac;
   d.sstar = sstar;
   if ((r = dalloc(c, &d.red, std::max((size_t)pdk::max_reduction_blocks(c->n_v, c->n_e) * pdk::kRed,
-                                      (size_t)2 * pdk::kRedRep * pdk::kRedRows * pdk::kRedTeam + 2 * pdk::kPubMax))))
+                                      (size_t)2 * pdk::kRedRep * pdk::kRedRows * pdk::kRedTeam))))
     return r;
   if ((r = dalloc(c, &d.dw, c->n_e)) || (r = dalloc(c, &d.dbeta, c->n_e))) return r;
   if ((r = dalloc(c, &d.ctrl, 1))) return r;
@@ -748,7 +748,7 @@ int enqueue_bwd_single(pd_ctx* c, const double* dqTd, const double* dvTd, double
   br.dnu = dnud;
   br.df = dfd;
   br.df_stride = df_stride;
-  CK(cudaMemsetAsync(&d.ctrl->bar_arrive, 0, 2 * sizeof(unsigned long long), s));   // bar_arrive, pub_open
+  CK(cudaMemsetAsync(&d.ctrl->bar_arrive, 0, sizeof(unsigned long long), s));
   CK(pdk::launch_bwd_rollout(d.local_fp32 != 0, c->d_dev, c->d_team[1], c->d_off, br, grid, s));
   c->launches += 1;
   return PD_OK;

@@ -396,7 +396,7 @@ int batch_backward(pd_ctx* c, const double* dqT, const double* dvT, double* dq0,
   }
   if ((r = prepare(c, s, 1))) return r;
   // barrier counters of every team start at zero (a timed-out launch may leave them set)
-  CK(cudaMemset2DAsync(&B.ctrl[0].bar_arrive, sizeof(Ctrl), 0, 2 * sizeof(unsigned long long), B.n, s));
+  CK(cudaMemset2DAsync(&B.ctrl[0].bar_arrive, sizeof(Ctrl), 0, sizeof(unsigned long long), B.n, s));
   if (dfd && df_stride == 0) CK(cudaMemsetAsync(dfd, 0, nv3 * sizeof(double), s));
   pdk::BatchBwd br;
   br.T = T;

@@ -29,14 +29,6 @@ __device__ __forceinline__ unsigned long long atom_add_release64(unsigned long l
   asm volatile("atom.release.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
   return old;
 }
-__device__ __forceinline__ unsigned long long atom_add_acq_rel64(unsigned long long* p, unsigned long long v) {
-  unsigned long long old;
-  asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
-  return old;
-}
-__device__ __forceinline__ void st_release64(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
 __device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -75,99 +67,12 @@ __device__ __forceinline__ int& team_red_count() {
 // values per block, returned in `sums` (shared) to every block, identical in
 // every block (fixed order). Returns false in every thread of the block if a
 // wait timed out. A one-block team needs no global memory traffic at all.
-// Partial rows live in buffer `parity`, which alternates between
-// consecutive reductions, so a block already at the next reduction cannot
-// overwrite rows that a slower block is still reading.
-//  - NV < kPublishMin: each block stores its row in kRedRep copies, passes
-//    the barrier and adds all rows itself (copy b mod kRedRep): no second
-//    round trip for a result.
-//  - NV >= kPublishMin: the block that arrives last adds the rows and
-//    publishes the sums with a release store of the barrier's number; the
-//    others wait for that number and read the sums (every block reading
-//    every long row costs more than the extra round trip).
-constexpr int kPublishMin = 8;
-
-struct NoFinish {
-  __device__ void operator()(const double*, double*) const {}
-};
-
-// The publishing path on its own, with NX extra values: thread 0 of the
-// block that adds the rows runs fin(sums, extra) and publishes extra[0..NX)
-// after the NV sums; every block returns sums[0..NV+NX). Lets one block run
-// scalar work that depends on the sums (the Anderson solve) and hand the
-// result to the others instead of every block repeating it.
-// The same with the block's sums already formed: thread t < NV holds the
-// block's value t in v (the block is synchronised on entry).
-template <int NV, int NX, class Fin>
-__device__ __forceinline__ bool grid_reduce_pub_v(const Dev& d, Team tm, double v, double* sums, Fin fin) {
-  static_assert(NV <= kRedTeam && NV + NX <= kPubMax, "values per team reduction");
-  __shared__ int s_fail, s_last;
-  __shared__ unsigned long long s_open;
-  int& s_parity = team_red_count();
-  const int par = s_parity & 1;
-  if (tm.nb == 1) {
-    if (threadIdx.x < NV) sums[threadIdx.x] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) fin(sums, sums + NV);
-    __syncthreads();
-    return true;
-  }
-  if (threadIdx.x < NV) d.red[((size_t)(par * kRedRep) * kRedRows + tm.b) * kRedTeam + threadIdx.x] = v;
-  __syncthreads();
-  Ctrl* c = d.ctrl;
-  if (threadIdx.x == 0) {
-    const unsigned long long n = atom_add_acq_rel64(&c->bar_arrive, 1ull);
-    const unsigned long long open = (n / (unsigned long long)tm.nb + 1ull) * (unsigned long long)tm.nb;
-    if (d.prof && n + 1 == open) c->t_last = gtimer();
-    s_last = n + 1 == open;
-    s_open = open;
-    s_fail = 0;
-    if (!s_last) {
-      unsigned int it = 0;
-      while (ld_acquire64(&c->pub_open) < open) {
-        if (++it > d.spin_limit) {
-          atomicOr(&c->status, kStatusTimeout);
-          s_fail = 1;
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    s_parity += 1;   // every thread read `par` before the __syncthreads above
-  }
-  __syncthreads();
-  double* pub = d.red + (size_t)(2 * kRedRep * kRedRows) * kRedTeam + par * kPubMax;   // published values
-  if (s_last) {
-    const double* rows = d.red + (size_t)(par * kRedRep) * kRedRows * kRedTeam;
-    double acc[NV];
-#pragma unroll
-    for (int j = 0; j < NV; ++j) acc[j] = 0.0;
-#pragma unroll 2
-    for (int b = threadIdx.x; b < tm.nb; b += blockDim.x) {
-      double w[NV];
-#pragma unroll
-      for (int j = 0; j < NV; ++j) w[j] = __ldcg(&rows[(size_t)b * kRedTeam + j]);
-#pragma unroll
-      for (int j = 0; j < NV; ++j) acc[j] += w[j];
-    }
-    block_reduce_to<NV>(acc, sums);
-    if (threadIdx.x == 0) fin(sums, sums + NV);
-    __syncthreads();
-    if (threadIdx.x < NV + NX) pub[threadIdx.x] = sums[threadIdx.x];
-    __syncthreads();
-    if (threadIdx.x == 0) st_release64(&c->pub_open, s_open);
-  } else {
-    if (threadIdx.x < NV + NX) sums[threadIdx.x] = __ldcg(&pub[threadIdx.x]);
-    __syncthreads();
-  }
-  return !s_fail;
-}
-
-template <int NV, int NX, class Fin>
-__device__ __forceinline__ bool grid_reduce_pub(const Dev& d, Team tm, double (&part)[NV], double* sums, Fin fin) {
-  const double v = block_sum_lane<NV>(part);   // threads < NV hold the block's sums
-  return grid_reduce_pub_v<NV, NX>(d, tm, v, sums, fin);
-}
+// Each block stores its row of partials in kRedRep copies, passes the
+// barrier and adds all the team's rows itself (copy b mod kRedRep): no
+// second round trip for a published result. Partial rows live in buffer
+// `parity`, which alternates between consecutive reductions, so a block
+// already at the next reduction cannot overwrite rows that a slower block is
+// still reading.
 
 // Every block adds all the team's rows itself: thread t < NV holds the
 // block's value t in v on entry (NV = 0: a plain barrier).
@@ -213,9 +118,7 @@ __device__ __forceinline__ bool grid_reduce_all_v(const Dev& d, Team tm, double 
 template <int NV>
 __device__ __forceinline__ bool grid_reduce(const Dev& d, Team tm, double (&part)[NV > 0 ? NV : 1], double* sums) {
   static_assert(NV <= kRedTeam, "values per team reduction");
-  if constexpr (NV >= kPublishMin) {
-    return grid_reduce_pub<NV, 0>(d, tm, part, sums, NoFinish{});
-  } else if constexpr (NV > 0) {
+  if constexpr (NV > 0) {
     return grid_reduce_all_v<NV>(d, tm, block_sum_lane<NV>(part), sums);
   } else {
     return grid_reduce_all_v<0>(d, tm, 0.0, sums);

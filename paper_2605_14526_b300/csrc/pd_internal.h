@@ -25,7 +25,6 @@ constexpr int kBwdMinBlocks = 2;
 constexpr int kRedRows = 2048;   // rows of the reduction scratch (>= any grid used)
 constexpr int kRedRep = 4;       // copies of each block's partials in the team reductions
 constexpr int kRedTeam = 16;     // values per row in the team reductions (>= 2 kMaxAA)
-constexpr int kPubMax = 32;      // values a team reduction publishes (sums + extra)
 
 // Device-resident control word of the iteration (one per context).
 struct Ctrl {
@@ -61,7 +60,6 @@ struct Ctrl {
   double dnu_acc;
   unsigned int ticket[16];        // last-block-done counters, one per kernel kind
   unsigned long long bar_arrive;  // team barrier of the persistent kernels: arrivals so far (monotonic)
-  unsigned long long pub_open;    // team reductions with many values: barrier whose sums are published
   unsigned long long phase_ns[8];  // persistent kernels: time per phase (globaltimer, block 0)
   unsigned long long work_ns[8];   // ... of which block 0's own work before the phase's barrier
   unsigned long long elapsed_ns[2]; // persistent launches: wall time of the forward / adjoint (team block 0)

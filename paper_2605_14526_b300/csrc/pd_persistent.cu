@@ -2,13 +2,12 @@
 // Alg. 1 (step begin, local/global iterations with Anderson mixing and the
 // dual gate, step end, trust-region selection).
 //
-// Synchronisation: phases are separated by a grid barrier built from an
-// acq_rel arrival counter and a release/acquire generation word. In a
-// reduction barrier the last block to arrive sums the per-block partials in
-// a fixed order (deterministic) and publishes the sums; every block then runs
-// the phase's scalar logic (pd_phases.cuh) on its own shared-memory replica
-// of the iteration state, so all blocks take identical decisions without a
-// serial chain of global-memory accesses. The grid is co-resident
+// Synchronisation: phases are separated by team barriers on a monotonic
+// arrival counter (pd_grid.cuh). In a reduction every block adds all the
+// team's partial rows in a fixed order (deterministic, the same bits in
+// every block) and then runs the phase's scalar logic (pd_phases.cuh) on its
+// own shared-memory replica of the iteration state, so all blocks take
+// identical decisions without a serial chain of global-memory accesses. The grid is co-resident
 // (cooperative launch) and every wait is bounded: on timeout a status bit is
 // set and every block returns.
 #include <cuda_runtime.h>
@@ -54,7 +53,7 @@ __device__ __noinline__ void warm_vertex_call(const Dev& d, int v, const double*
 template <typename T>
 __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a, const Team tm) {
   __shared__ FwdState S;
-  __shared__ double sums[kPubMax];
+  __shared__ double sums[2 * kMaxAA];
   __shared__ double s_pa[kFwdWideBlock / 32][3][2 * kMaxAA];
   const int tid = threadIdx.x;
   const int gtid = tm.b * blockDim.x + tid;
