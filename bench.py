@@ -44,6 +44,17 @@ UNIT = "PD steps/s"
 WORKLOAD = "heterogeneous Neo-Hookean bar 32x8x8 cells (10,240 tets, 2,673 vertices), 200 steps fwd+bwd"
 
 
+
+def max_over_ranks(value, dist, device):
+    """The largest value over the ranks (a job's time is its slowest rank's);
+    the value itself when the job has one rank."""
+    if not dist:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -212,11 +223,7 @@ def run_batch(args, rank, world, local_rank, dev, dist):
                 inst_b[i] += si.adj_iters_total
             esc += binding.pd_get_stats(bc.ctx).escalations
     launches = binding.pd_get_stats(bc.ctx).launches - launches0
-    tmax = total_ms
-    if dist:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tmax = float(tt[0])
+    tmax = max_over_ranks(total_ms, dist, dev)
     value = world * bc.n * T * args.steps / (tmax / 1e3)
     st = binding.pd_get_stats(bc.ctx)
     m = bc.options.aa_m
@@ -349,7 +356,7 @@ def run_contact(args, rank, world, local_rank, dev, dist):
             adj += st.adj_iters_total
             cpass_b += st.contact_iters
     launches = binding.pd_get_stats(pd.ctx).launches - launches0
-    tot = fwd_ms + bwd_ms
+    tot = max_over_ranks(fwd_ms + bwd_ms, dist, dev)
     value = world * T * args.steps / (tot / 1e3)
     st = binding.pd_get_stats(pd.ctx)
     fwd_iter_bytes = 56 * sc.n_e + 48 * sc.n_v + 20 * st.factor_nnz + 96 * st.n_free + 13 * 24 * sc.n_v
@@ -462,11 +469,7 @@ def main():
             iters += st.iters_total
             adj += st.adj_iters_total
     launches = binding.pd_get_stats(pd.ctx).launches - launches0
-    tmax = total_ms
-    if dist:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tmax = float(tt[0])
+    tmax = max_over_ranks(total_ms, dist, dev)
     value = world * T * args.steps / (tmax / 1e3)
 
     # Roofline of the dominant kernel. Each rollout is one launch of the
@@ -518,10 +521,7 @@ def main():
         g = np.ascontiguousarray(hq - scene.target)
         binding.pd_backward(pd.ctx, g, hz, hdq0, hdv0, hdE, hdnu, None, 0, None)
         e2e_s += time.perf_counter() - t0
-    if dist:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt[0])
+    e2e_s = max_over_ranks(e2e_s, dist, dev)
     e2e = world * T * args.steps / e2e_s
     # the same rollout with the S products in plain FP64 (options.solve_fp64):
     # one untimed and one timed fwd+bwd, for the cost of the exact-FP64 form
