@@ -567,7 +567,7 @@ int pd_factor(pd_ctx* c) {
         (r = upload(c, &W_d, W, true)) || (r = dalloc(c, &buf_d, 14 * (size_t)K, true)))
       return r;
     double* bwd_d;
-    if ((r = dalloc(c, &bwd_d, 20 * (size_t)K, true))) return r;
+    if ((r = dalloc(c, &bwd_d, 23 * (size_t)K, true))) return r;
     d.con_bwd = bwd_d;
     if (c->con_ckpt) cudaFree(c->con_ckpt);   // sized with the checkpoints (reserve)
     c->con_ckpt = nullptr;

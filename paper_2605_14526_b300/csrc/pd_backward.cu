@@ -661,8 +661,9 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
   }
   // contact: after y = S r, project the preconditioned residual onto null(G):
   // w = W_a^-1 G A^-1 r by CG on the active rows (per axis), then
-  // y <- y - S G^T w, so that the S^T pass gives A^-1 (r - G^T w)
-  auto project = [&](const double* ck) -> bool {
+  // y <- y - S G^T w, so that the S^T pass gives A^-1 (r - G^T w), and
+  // r <- r - G^T w, nu <- nu + w (residual update; reset: nu <- w)
+  auto project = [&](const double* ck, bool reset) -> bool {
     double pu[3] = {0.0, 0.0, 0.0};
     for (int c = gwarp; c < d.n_con; c += nwarps) proj_gather(d, c, lane, pu);
     if (!grid_reduce<3>(d, tm, pu, sums)) return false;
@@ -707,7 +708,7 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
       if (tid == 0) S.cg_rot = rot + 1;
       if (!grid_sync(d, tm)) return false;
     }
-    for (int c = rcn.lo + tid; c < rcn.hi; c += blockDim.x) proj_impulse(d, c);
+    for (int c = rcn.lo + tid; c < rcn.hi; c += blockDim.x) proj_impulse(d, c, reset);
     if (!grid_sync(d, tm)) return false;
     for (int i = gwarp; i < d.n_f; i += nwarps) contact_y_row(d, i, cb_nz(d), cb_nxy(d), lane);
     return grid_sync(d, tm);
@@ -735,7 +736,7 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
     if (!(ok = grid_sync(d, tm))) break;
     for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, d.s_part, d.s_cnt, sg, lane);
     if (!(ok = grid_sync(d, tm))) break;
-    if (ck && !(ok = project(ck))) break;
+    if (ck && !(ok = project(ck, true))) break;
     // S^T y row by row with the partial r . z of the row fused in (first
     // direction p = z: beta = 0 and p_old = 0 on the first iteration)
     auto st_rz = [&](double* prz) {
@@ -775,7 +776,7 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
         if (!(ok = grid_sync(d, tm))) break;
         for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, d.s_part, d.s_cnt, sg, lane);
         if (!(ok = grid_sync(d, tm))) break;
-        if (ck && !(ok = project(ck))) break;
+        if (ck && !(ok = project(ck, true))) break;
         double prz0[1] = {0.0};
         st_rz(prz0);
         if (!(ok = grid_reduce<1>(d, tm, prz0, sums))) break;
@@ -804,7 +805,7 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
       if (!(ok = grid_sync(d, tm))) break;
       for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, d.s_part, d.s_cnt, sg, lane);
       if (!(ok = grid_sync(d, tm))) break;
-      if (ck && !(ok = project(ck))) break;
+      if (ck && !(ok = project(ck, false))) break;
       double prz[1] = {0.0};
       st_rz(prz);
       if (!(ok = grid_reduce<1>(d, tm, prz, sums))) break;
@@ -836,8 +837,8 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
       for (int c = rcn.lo + tid; c < rcn.hi; c += blockDim.x)
         if (con_stick(d, c)) {
           const int v = d.con_v[c];
-          d.gq[3 * (size_t)v] += cb_x(d)[3 * c];
-          d.gq[3 * (size_t)v + 1] += cb_x(d)[3 * c + 1];
+          d.gq[3 * (size_t)v] += cb_nu(d)[3 * c];
+          d.gq[3 * (size_t)v + 1] += cb_nu(d)[3 * c + 1];
         }
       if (!(ok = grid_sync(d, tm))) break;
     }

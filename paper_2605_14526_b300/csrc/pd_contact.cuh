@@ -212,9 +212,15 @@ __device__ __forceinline__ void contact_y_row(const Dev& d, int i, const double*
 //   (A - K) a + G^T nu = q_bar,  G a = 0
 // by the same preconditioned CG with the preconditioner projected
 // A-orthogonally onto null(G): z = A^-1 (r - G^T w), w = W_a^-1 G A^-1 r,
-// W_a = G A^-1 G^T (the Delassus matrix on the active rows, per axis). The
-// last w is nu; its sticking rows enter dL/dq_t (the constraint
-// q_xy = q_t,xy of a sticking contact depends on q_t).
+// W_a = G A^-1 G^T (the Delassus matrix on the active rows, per axis).
+// Every projection also takes its share G^T w out of the residual,
+// r <- r - G^T w, and adds w to nu (the residual update of Gould, Hribar and
+// Nocedal 2001): r keeps no part that the projection removes, so r . z is no
+// longer the small difference of the projected preconditioner's two large
+// terms, and the CG reaches its tolerance instead of breaking down at the
+// rounding level of W_a. On exit (A - K) a + G^T nu = q_bar - r; the
+// sticking rows of nu enter dL/dq_t (the constraint q_xy = q_t,xy of a
+// sticking contact depends on q_t).
 
 // active sets of the step, one flag per candidate (bit 0 normal-active,
 // bit 1 sticking), formed at the step's start by contact_flag_item
@@ -245,6 +251,8 @@ __device__ __forceinline__ double* cb_nz(const Dev& d) { return d.con_bwd + 15 *
 __device__ __forceinline__ double* cb_nxy(const Dev& d) { return d.con_bwd + 16 * (size_t)d.n_con; }   // [K][2]
 // n_c p_z of the current CG direction (the W rows then cost three FMAs per entry)
 __device__ __forceinline__ double* cb_pz(const Dev& d) { return d.con_bwd + 18 * (size_t)d.n_con; }   // [K]
+// nu: the sum of the step's projection multipliers w (since its last restart)
+__device__ __forceinline__ double* cb_nu(const Dev& d) { return d.con_bwd + 20 * (size_t)d.n_con; }
 
 // warp per candidate: u = G A^-1 r (masked rows of S^T y) as the CG
 // residual; w = 0; p = u; partial |u|^2 per axis
@@ -313,11 +321,23 @@ __device__ __forceinline__ void proj_dir(const Dev& d, int c, int rot, const dou
   cb_pz(d)[c] = d.con_n[c] * pn[3 * c + 2];
 }
 
-// thread per candidate: the impulse parts of -G^T w for the y correction
-__device__ __forceinline__ void proj_impulse(const Dev& d, int c) {
-  cb_nxy(d)[2 * c] = -cb_x(d)[3 * c];
-  cb_nxy(d)[2 * c + 1] = -cb_x(d)[3 * c + 1];
-  cb_nz(d)[c] = -cb_x(d)[3 * c + 2];
+// thread per candidate: the impulse parts of -G^T w for the y correction;
+// residual update r <- r - G^T w at the candidate's vertex (every vertex is
+// at most one candidate) and nu <- w (reset: the step's first projection or
+// a restart) or nu + w. Masked rows have w = 0 and change nothing.
+__device__ __forceinline__ void proj_impulse(const Dev& d, int c, bool reset) {
+  const double wx = cb_x(d)[3 * c], wy = cb_x(d)[3 * c + 1], wz = cb_x(d)[3 * c + 2];
+  cb_nxy(d)[2 * c] = -wx;
+  cb_nxy(d)[2 * c + 1] = -wy;
+  cb_nz(d)[c] = -wz;
+  const size_t o = 3 * (size_t)d.con_v[c];
+  d.r[o] -= wx;
+  d.r[o + 1] -= wy;
+  d.r[o + 2] -= d.con_n[c] * wz;
+  double* nu = cb_nu(d) + 3 * (size_t)c;
+  nu[0] = reset ? wx : nu[0] + wx;
+  nu[1] = reset ? wy : nu[1] + wy;
+  nu[2] = reset ? wz : nu[2] + wz;
 }
 
 }  // namespace pdk

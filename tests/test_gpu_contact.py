@@ -98,9 +98,12 @@ def test_contact_adjoint_fp64_matches_oracle(oracle_pad):
     code = binding.pd_backward(pd.ctx, x, None, dq0, dv0, dE, dnu, None, 0, check=False)
     sb = binding.pd_get_stats(pd.ctx)
     assert binding.STATUS[code] == "PD_OK", (sb.adj_not_converged, sb.contact_unconverged)
-    assert rel(dv0.cpu().numpy(), g_o.dv0) <= 1e-4, rel(dv0.cpu().numpy(), g_o.dv0)
-    assert rel(dq0.cpu().numpy(), g_o.dx0) <= 1e-4, rel(dq0.cpu().numpy(), g_o.dx0)
-    assert rel(dE.cpu().numpy(), g_o.dE) <= 1e-4, rel(dE.cpu().numpy(), g_o.dE)
+    # the projected CG with residual update reaches its tolerance (no
+    # breakdown), so the gradients follow the forward's accuracy
+    assert sb.adj_not_converged == 0
+    assert rel(dv0.cpu().numpy(), g_o.dv0) <= 1e-6, rel(dv0.cpu().numpy(), g_o.dv0)
+    assert rel(dq0.cpu().numpy(), g_o.dx0) <= 1e-6, rel(dq0.cpu().numpy(), g_o.dx0)
+    assert rel(dE.cpu().numpy(), g_o.dE) <= 1e-6, rel(dE.cpu().numpy(), g_o.dE)
 
 
 def test_contact_impulses_match_oracle(oracle_pad):
