@@ -766,10 +766,10 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
     // neighbours still read p_old
     for (int it = 0; !S.adj_done; ++it) {
       if (S.restart) {
-        // contact: r . z fell through zero while the residual was still above
-        // the target (the projection of the preconditioner is only as
-        // consistent as W with the device's A^-1, and the recursive residual
-        // drifts); start again from the true residual q_bar - (A - K) mu
+        // contact (a guard: with the residual update r . z is not expected
+        // to fall through zero): r . z fell below zero while the residual
+        // was still above the target; start again from the true residual
+        // q_bar - (A - K) mu, whose projection resets nu
         for (int e = re.lo + tid; e < re.hi; e += blockDim.x) kapply_item<T>(d, e, d.mu);
         if (!(ok = grid_sync(d, tm))) break;
         for (int v = rv.lo + (tid >> 5); v < rv.hi; v += blockDim.x >> 5) resid_warp<T>(d, v, lane);
