@@ -1,0 +1,33 @@
+// The library's per-element math (pd_math.cuh: rotation-variant 3x3 SVD,
+// Neo-Hookean stretch prox, 3x3 SPD inverse) compiled as host C++ so that the
+// CPU tests can check it against numpy / scipy. __device__ and
+// __forceinline__ are defined away; everything else is the header as the GPU
+// build compiles it.
+#define __device__
+#define __forceinline__ inline
+#include "../../paper_2605_14526_b300/csrc/pd_math.cuh"
+
+using namespace pdk;
+
+template <typename T>
+static void svd_n(int n, const T* F, T* U, T* s, T* V) {
+  for (int i = 0; i < n; ++i) svd3<T>(F + 9 * i, U + 9 * i, s + 3 * i, V + 9 * i);
+}
+
+template <typename T>
+static void prox_n(int n, const T* sF, T mu, T lam, T k, T* s, int* iters) {
+  const NHMean<T> m{mu, lam, k};
+  for (int i = 0; i < n; ++i) iters[i] = nh_prox<T>(sF + 3 * i, m, s + 3 * i);
+}
+
+extern "C" {
+void svd3_f32(int n, const float* F, float* U, float* s, float* V) { svd_n<float>(n, F, U, s, V); }
+void svd3_f64(int n, const double* F, double* U, double* s, double* V) { svd_n<double>(n, F, U, s, V); }
+void nh_prox_f32(int n, const float* sF, float mu, float lam, float k, float* s, int* it) {
+  prox_n<float>(n, sF, mu, lam, k, s, it);
+}
+void nh_prox_f64(int n, const double* sF, double mu, double lam, double k, double* s, int* it) {
+  prox_n<double>(n, sF, mu, lam, k, s, it);
+}
+int spd_inv3_f64(const double* H, double* Hi) { return spd_inv3<double>(H, Hi) ? 1 : 0; }
+}
