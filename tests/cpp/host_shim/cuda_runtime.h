@@ -4,3 +4,17 @@
 #pragma once
 #include <cmath>
 inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
+
+// explicitly rounded single-precision operations (round to nearest even, as
+// the host's SSE arithmetic does; build with -ffp-contract=off so that no
+// product and sum is fused behind the code's back)
+struct float2 { float x, y; };
+inline float2 make_float2(float x, float y) { return float2{x, y}; }
+inline float __double2float_rn(double x) { return (float)x; }
+inline float __fmul_rn(float a, float b) { return a * b; }
+inline float __fadd_rn(float a, float b) { return a + b; }
+inline float __fsub_rn(float a, float b) { return a - b; }
+inline float __fmaf_rn(float a, float b, float c) { return std::fmaf(a, b, c); }
+// declared only: a warp shuffle has no host meaning, and the host builds
+// call none of the functions that use it
+float __shfl_xor_sync(unsigned mask, float v, int lane_mask);
