@@ -9,6 +9,7 @@ inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
 // the host's SSE arithmetic does; build with -ffp-contract=off so that no
 // product and sum is fused behind the code's back)
 struct float2 { float x, y; };
+struct int4 { int x, y, z, w; };
 inline float2 make_float2(float x, float y) { return float2{x, y}; }
 inline float __double2float_rn(double x) { return (float)x; }
 inline float __fmul_rn(float a, float b) { return a * b; }
