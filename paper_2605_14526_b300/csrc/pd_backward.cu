@@ -35,42 +35,6 @@ struct BwdState {
   int restart, restarts;   // contact: restarts of the outer CG from its true residual
 };
 
-template <typename T>
-__device__ __forceinline__ void filtered_jacobian(const T* ss, const NHMean<T>& m, T tau, T* J) {
-  const T lnJ = dlog(ss[0] * ss[1] * ss[2]);
-  T H[9], Hi[9];
-  nh_hess(ss, m, lnJ, H);
-  if (spd_inv3(H, Hi)) {  // definite: every blend of eq. tr_blend is H itself
-#pragma unroll
-    for (int i = 0; i < 9; ++i) J[i] = m.k * Hi[i];
-    return;
-  }
-  T S[9], Q[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    S[i] = H[i];
-    Q[i] = (i % 4 == 0) ? T(1) : T(0);
-  }
-  for (int sweep = 0; sweep < 10; ++sweep) {
-    jacobi_pq(S, Q, 0, 1);
-    jacobi_pq(S, Q, 0, 2);
-    jacobi_pq(S, Q, 1, 2);
-  }
-  const T thr = (sizeof(T) == 4 ? T(1e-6) : T(1e-12)) * m.k;
-  T inv[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const T lam = S[4 * i];
-    const T lt = (T(1) - tau) * lam + tau * dabs(lam);
-    inv[i] = lt > thr ? T(1) / lt : T(0);  // pseudo-inverse: clamped directions respond with 0
-  }
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      J[3 * i + j] = m.k * (Q[3 * i] * inv[0] * Q[3 * j] + Q[3 * i + 1] * inv[1] * Q[3 * j + 1] + Q[3 * i + 2] * inv[2] * Q[3 * j + 2]);
-}
-
 // ------------------------------------------------------------ per-item bodies
 
 template <typename T>

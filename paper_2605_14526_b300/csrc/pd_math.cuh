@@ -9,6 +9,8 @@
 //    exact rotations instead of their approximate quaternion ones.
 //  * nh_prox: Newton on the Neo-Hookean stretch-space prox (Sec. 4.1,
 //    eq. nh_prox_normal) with positivity and a sufficient-decrease test.
+//  * filtered_jacobian: the prox's stretch Jacobian through the
+//    trust-region blend of its Hessian (Sec. 4.3, eq. tr_blend, tr_ift).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -257,6 +259,49 @@ __device__ __forceinline__ int nh_prox(const T* sF, const NHMean<T>& m, T* s) {
 #pragma unroll
   for (int i = 0; i < 3; ++i) s0[i] = sF[i] > T(0.1) ? sF[i] : T(0.1);
   return nh_prox_from<T>(sF, m, s0, s);
+}
+
+// d sigma* / d sigma_F of the prox (eq. tr_ift): k H~^+ with H = k I +
+// H_psi(sigma*) and H~ = (1 - tau) H + tau |H| (eq. tr_blend), as a full 3x3
+// matrix. A definite H is its own blend and is inverted directly; otherwise
+// H is diagonalised by Jacobi sweeps, the eigenvalues are blended, and
+// directions whose blended eigenvalue is at most 1e-6 k (FP32) or 1e-12 k
+// (FP64) respond with 0 (the pseudo-inverse: clamping a negative eigenvalue
+// to 0 makes H~ singular).
+template <typename T>
+__device__ __forceinline__ void filtered_jacobian(const T* ss, const NHMean<T>& m, T tau, T* J) {
+  const T lnJ = dlog(ss[0] * ss[1] * ss[2]);
+  T H[9], Hi[9];
+  nh_hess(ss, m, lnJ, H);
+  if (spd_inv3(H, Hi)) {  // definite: every blend of eq. tr_blend is H itself
+#pragma unroll
+    for (int i = 0; i < 9; ++i) J[i] = m.k * Hi[i];
+    return;
+  }
+  T S[9], Q[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    S[i] = H[i];
+    Q[i] = (i % 4 == 0) ? T(1) : T(0);
+  }
+  for (int sweep = 0; sweep < 10; ++sweep) {
+    jacobi_pq(S, Q, 0, 1);
+    jacobi_pq(S, Q, 0, 2);
+    jacobi_pq(S, Q, 1, 2);
+  }
+  const T thr = (sizeof(T) == 4 ? T(1e-6) : T(1e-12)) * m.k;
+  T inv[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const T lam = S[4 * i];
+    const T lt = (T(1) - tau) * lam + tau * dabs(lam);
+    inv[i] = lt > thr ? T(1) / lt : T(0);  // pseudo-inverse: clamped directions respond with 0
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      J[3 * i + j] = m.k * (Q[3 * i] * inv[0] * Q[3 * j] + Q[3 * i + 1] * inv[1] * Q[3 * j + 1] + Q[3 * i + 2] * inv[2] * Q[3 * j + 2]);
 }
 
 }  // namespace pdk

@@ -1,8 +1,8 @@
 // The library's per-element math (pd_math.cuh: rotation-variant 3x3 SVD,
-// Neo-Hookean stretch prox, 3x3 SPD inverse) compiled as host C++ so that the
-// CPU tests can check it against numpy / scipy. __device__ and
-// __forceinline__ are defined away; everything else is the header as the GPU
-// build compiles it.
+// Neo-Hookean stretch prox, 3x3 SPD inverse, the prox's filtered stretch
+// Jacobian) compiled as host C++ so that the CPU tests can check it against
+// numpy, scipy and the oracle. __device__ and __forceinline__ are defined
+// away; everything else is the header as the GPU build compiles it.
 #define __device__
 #define __forceinline__ inline
 #include "../../paper_2605_14526_b300/csrc/pd_math.cuh"
@@ -30,4 +30,12 @@ void nh_prox_f64(int n, const double* sF, double mu, double lam, double k, doubl
   prox_n<double>(n, sF, mu, lam, k, s, it);
 }
 int spd_inv3_f64(const double* H, double* Hi) { return spd_inv3<double>(H, Hi) ? 1 : 0; }
+void filtered_jacobian_f64(int n, const double* ss, double mu, double lam, double k, double tau, double* J) {
+  const NHMean<double> m{mu, lam, k};
+  for (int i = 0; i < n; ++i) filtered_jacobian<double>(ss + 3 * i, m, tau, J + 9 * i);
+}
+void filtered_jacobian_f32(int n, const float* ss, float mu, float lam, float k, float tau, float* J) {
+  const NHMean<float> m{mu, lam, k};
+  for (int i = 0; i < n; ++i) filtered_jacobian<float>(ss + 3 * i, m, tau, J + 9 * i);
+}
 }

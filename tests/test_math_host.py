@@ -5,7 +5,9 @@ be negative) against numpy's SVD, and the Neo-Hookean stretch prox
 (Sec. 4.1, eq. nh_prox: sigma* minimises k/2 |sigma - sigma_F|^2 + psi(sigma)
 with the compressible Neo-Hookean psi) against scipy's bounded minimiser of
 that objective, with the special cases the method fixes: no change at rest,
-rotation invariance, an inverted element projected to positive stretches."""
+rotation invariance, an inverted element projected to positive stretches.
+The prox's filtered stretch Jacobian of the backward pass (Sec. 4.3,
+eq. tr_blend, tr_ift) is compared with the oracle's."""
 import ctypes
 import os
 import subprocess
@@ -13,6 +15,8 @@ import subprocess
 import numpy as np
 import pytest
 import scipy.optimize as so
+
+from oracle import prox as oprox
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -168,3 +172,39 @@ def test_spd_inverse(lib):
         assert np.abs(Hi @ H - np.eye(3)).max() <= 1e-10 * np.linalg.cond(H)
     Hn = np.ascontiguousarray(np.diag([1.0, -1.0, 2.0]))
     assert lib.spd_inv3_f64(_p(Hn), _p(np.zeros((3, 3)))) == 0
+
+
+def _fjac(lib, ss, mu, lam, k, tau, dtype):
+    ss = np.ascontiguousarray(ss, dtype=dtype)
+    n = ss.shape[0]
+    J = np.zeros((n, 3, 3), dtype)
+    if dtype == np.float32:
+        lib.filtered_jacobian_f32(ctypes.c_int(n), _p(ss), ctypes.c_float(mu), ctypes.c_float(lam), ctypes.c_float(k),
+                                  ctypes.c_float(tau), _p(J))
+    else:
+        lib.filtered_jacobian_f64(ctypes.c_int(n), _p(ss), ctypes.c_double(mu), ctypes.c_double(lam),
+                                  ctypes.c_double(k), ctypes.c_double(tau), _p(J))
+    return J.astype(np.float64)
+
+
+@pytest.mark.parametrize("tau", [0.0, 0.5, 1.0])
+@pytest.mark.parametrize("kscale", [1.0, 0.05])
+def test_filtered_jacobian_against_oracle(lib, tau, kscale):
+    """Definite and indefinite prox Hessians (wide stretches; a small weight
+    k makes most of them indefinite), every trust-region blend: the FP64
+    build matches the oracle's eigen-decomposition form, clamped directions
+    included; the FP32 build matches where the blended Hessian is not close
+    to singular."""
+    rng = np.random.default_rng(int(10 * tau + 100 * kscale))
+    k = K * kscale
+    ss = np.exp(0.6 * rng.standard_normal((2000, 3)))
+    Jo, _, n_indef = oprox.filtered_sigma_jacobian(ss, MU, LAM, k, tau)
+    assert n_indef > 50                      # the filtered branch is exercised
+    scale = np.abs(Jo).max(axis=(1, 2))
+    J64 = _fjac(lib, ss, MU, LAM, k, tau, np.float64)
+    assert (np.abs(J64 - Jo).max(axis=(1, 2)) / scale).max() <= 1e-10
+    J32 = _fjac(lib, ss.astype(np.float32).astype(np.float64), MU, LAM, k, tau, np.float32)
+    lam_h = np.linalg.eigvalsh(k * np.eye(3) + oprox.nh_hess_sigma(ss, MU, LAM))
+    blended = (1.0 - tau) * lam_h + tau * np.abs(lam_h)
+    far = np.abs(blended).min(axis=1) > 0.1 * k
+    assert (np.abs(J32 - Jo).max(axis=(1, 2))[far] / scale[far]).max() <= 1e-4
