@@ -179,7 +179,8 @@ int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_o
  * (eq. q_update) through the same two products with S. Persistent launches
  * only. pd_backward differentiates a contact rollout with each step's active
  * sets held fixed (normal-active and sticking contacts as equality
- * constraints, projected preconditioned CG). */
+ * constraints; preconditioned CG projected onto their null space, with the
+ * constraint multipliers taken out of the residual at every projection). */
 int pd_set_contacts(pd_ctx* ctx, const pd_contact_desc* desc);
 
 /* Contact impulses of step t (0 <= t < T) of the last rollout: n_out = the
