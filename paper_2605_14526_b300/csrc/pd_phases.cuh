@@ -8,6 +8,7 @@
 #include "pd_common.cuh"
 #include "pd_df.cuh"
 #include "pd_aa_solve.cuh"
+#include "pd_local.cuh"
 
 namespace pdk {
 
@@ -102,43 +103,6 @@ __device__ __forceinline__ double next_iterate(const Dev& d, size_t o, int use_h
       if (j < nc) qn = __fma_rn(-gam[j], d.dQG[j * nv3 + o], qn);
   }
   return qn;
-}
-
-// ------------------------------------------------------------ local step
-
-// Local step fused with the per-element part of the RHS scatter (Alg. 1,
-// eq. nh_prox / corotated projection, eq. A_basic). The prox Newton starts
-// from this element's sigma* of its previous local step when one is stored.
-template <typename T>
-__device__ __forceinline__ void local_item(const Dev& d, int e, const double* x) {
-  int4 tv;
-  T Bm[9], coef;
-  load_elem<T>(d, e, tv, Bm, coef);
-  T F[9], U[9], V[9], sF[3], ss[3], P[9], c[12];
-  deform<T>(x, tv, Bm, F);
-  svd3<T>(F, U, sF, V);
-  if (d.model == 0) {
-    ss[0] = ss[1] = ss[2] = T(1);
-  } else {
-    NHMean<T> m{(T)d.mu_bar, (T)d.lam_bar, (T)d.k_bar};
-    float* ws = reinterpret_cast<float*>(d.sstar) + 3 * (size_t)e;
-    T s0[3];
-    const bool warm = ws[0] > 0.f && ws[1] > 0.f && ws[2] > 0.f;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) s0[i] = warm ? (T)ws[i] : (sF[i] > T(0.1) ? sF[i] : T(0.1));
-    nh_prox_from<T>(sF, m, s0, ss);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) ws[i] = (float)ss[i];
-  }
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      P[3 * i + j] = U[3 * i] * ss[0] * V[3 * j] + U[3 * i + 1] * ss[1] * V[3 * j + 1] + U[3 * i + 2] * ss[2] * V[3 * j + 2];
-  corner_forces<T>(P, Bm, coef, c);
-  T* out = reinterpret_cast<T*>(d.contrib) + 12 * (size_t)e;
-#pragma unroll
-  for (int i = 0; i < 12; ++i) out[i] = c[i];
 }
 
 // b^k = b0 + sum of corner contributions (FP64) in vertex order and in

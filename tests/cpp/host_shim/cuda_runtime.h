@@ -16,6 +16,17 @@ inline float __fmul_rn(float a, float b) { return a * b; }
 inline float __fadd_rn(float a, float b) { return a + b; }
 inline float __fsub_rn(float a, float b) { return a - b; }
 inline float __fmaf_rn(float a, float b, float c) { return std::fmaf(a, b, c); }
-// declared only: a warp shuffle has no host meaning, and the host builds
-// call none of the functions that use it
+using std::isfinite;
+
+// declared only: warp, block and grid intrinsics have no host meaning, and
+// the host builds call none of the functions that use them
+#define __host__
+#define __shared__ static
+struct host_dim3 { unsigned x, y, z; };
+extern host_dim3 threadIdx, blockIdx, blockDim, gridDim;
 float __shfl_xor_sync(unsigned mask, float v, int lane_mask);
+double __shfl_xor_sync(unsigned mask, double v, int lane_mask);
+int __shfl_xor_sync(unsigned mask, int v, int lane_mask);
+void __syncthreads();
+void __threadfence();
+unsigned atomicAdd(unsigned* p, unsigned v);
