@@ -6,8 +6,8 @@
  * operator and the per-step checkpoints of the last rollout. All compute runs
  * in the library's CUDA kernels on the device that is current when the
  * context is created; host code in the library only validates inputs,
- * assembles and factors the operator (once per material change, Sec. 4.5
- * "refactorisation policy"), and orders launches.
+ * assembles and factors the operator (once per material change: Sec. 4.5
+ * on when to refactor), and orders launches.
  *
  * Conventions
  *   - Vertex arrays are [n_v][3] row-major float64 (x, y, z per vertex).
