@@ -9,8 +9,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpd_b300.so")
 SOURCES = ["factor.cpp", "pd_api.cpp", "pd_batch.cpp", "pd_kernels.cu", "pd_backward.cu", "pd_noalloc.cu", "pd_persistent.cu", "pd_mlp.cu"]
-HEADERS = ["factor.h", "pd_internal.h", "pd_launch.h", "pd_math.cuh", "pd_common.cuh", "pd_noalloc.h", "pd_phases.cuh",
-           "pd_grid.cuh", "pd_coop.h", "pd_ctx.h", "pd_mlp.cuh", "pd_contact.cuh"]
+# every header of csrc/ (a header edit makes the library stale)
+HEADERS = sorted(f for f in os.listdir(CSRC) if f.endswith((".h", ".cuh")))
 ROOT_INCLUDE = os.path.join(os.path.dirname(HERE), "include", "pd_b300.h")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
