@@ -3,8 +3,10 @@ bar (32x8x8 hex cells -> 10,240 tets, 2,673 vertices, 100x stiffness contrast,
 200 implicit-Euler steps at dt = 5 ms, Anderson m = 5, dual gate tightened to
 2e-7 (b-change) / 2e-9 (q-step) so that the 200-step trajectory stays within
 1e-5 of the oracle's exact fixed points, FP32 local step with FP64
-accumulation, FP64 factor, products with the inverse factor in double-float
-on the FP32 pipe), against the FP64 CPU oracle.
+accumulation, FP64 factor and FP64 products with the inverse factor), against
+the FP64 CPU oracle. The same rollout with the inverse-factor products in
+double-float arithmetic on the FP32 pipe is timed beside it
+(``double_float_variant``).
 
 One benchmark step = one full rollout of 200 PD steps forward followed by its
 adjoint (200 PD steps backward). value = PD steps (forward+backward) per
@@ -130,6 +132,34 @@ def oracle_sample(scene, n_steps: int):
     return dt, n_steps
 
 
+def oracle_sample_mid(scene, steps=(100, 150)):
+    """The oracle on one PD step (forward to the exact fixed point + direct
+    adjoint) from each of the mid-rollout states t = 100 and t = 150 of the
+    bar (the twisting part of the trajectory), read from the oracle's stored
+    rollout; falls back to the first two steps without it. Single-threaded.
+    Returns (seconds, steps, description)."""
+    from oracle import adjoint, solver
+    gold_path = os.path.join(ROOT, "tests", "golden", "bar32x8x8_T200.npz")
+    gold = np.load(gold_path) if os.path.exists(gold_path) else None
+    if gold is None or "samples_v" not in gold.files:
+        dt, k = oracle_sample(scene, 2)
+        return dt, k, f"first {k} PD steps of the same rollout, forward (exact fixed point) + adjoint, FP64, 1 thread"
+    sc = scene.with_steps(1)
+    t0 = time.perf_counter()
+    pb = solver.build_problem(sc)
+    picked = []
+    for i, t in enumerate(gold["sample_steps"]):
+        if int(t) not in steps:
+            continue
+        picked.append(int(t))
+        qT, vT, recs = solver.rollout(pb, sc, mode="exact", x0=gold["samples"][i], v0=gold["samples_v"][i])
+        _, dq, dv = adjoint.loss_and_grad(sc, pb, qT, vT)
+        adjoint.rollout_backward(pb, recs, dq, dv)
+    dt = time.perf_counter() - t0
+    return dt, len(picked), (f"PD steps {picked} of the same rollout (from the oracle's stored states), forward "
+                             "(exact fixed point) + adjoint each, FP64, 1 thread")
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 CPU oracle timed on the host on a bounded sample
     (one PD step forward + backward per benchmark step)."""
@@ -138,20 +168,21 @@ def run_reference(args, rank, world):
     from paper_2605_14526_b300 import inputs
     scene = inputs.hetero_bar()
     for _ in range(args.warmup):
-        oracle_sample(scene, 1)
+        oracle_sample_mid(scene, steps=(100,))
     tot = 0.0
     n = 0
+    what = ""
     for _ in range(args.steps):
-        dt, k = oracle_sample(scene, 1)
+        dt, k, what = oracle_sample_mid(scene, steps=(100,))
         tot += dt
         n += k
     value = n / tot
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "first PD step of the rollout, forward + adjoint, per bench step"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{n} PD steps (1 per bench step), numpy/scipy FP64, 1 thread"},
+            "config": {"workload": WORKLOAD, "sample": "one PD step of the rollout, forward + adjoint, per bench step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{n} PD steps (1 per bench step): {what}"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -425,7 +456,11 @@ def main():
         return
     scene = inputs.hetero_bar(seed=2 + rank)
     T = scene.steps
-    pd = binding.PDContext(scene)
+    # the headline keeps the solve in FP64 (the factor and the products with
+    # the inverse factor)
+    opts = binding.options_for(scene.solver)
+    opts.solve_fp64 = 1
+    pd = binding.PDContext(scene, opts)
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
     x0, v0, f0, target = t(scene.x0), t(scene.v0), t(scene.f_ext[0]), t(scene.target)
     qT, vT = torch.empty_like(x0), torch.empty_like(x0)
@@ -471,6 +506,8 @@ def main():
     launches = binding.pd_get_stats(pd.ctx).launches - launches0
     tmax = max_over_ranks(total_ms, dist, dev)
     value = world * T * args.steps / (tmax / 1e3)
+    qT_timed_t = qT.clone()
+    qT_timed, dE_timed, dq0_timed, dv0_timed = (a.cpu().numpy() for a in (qT, dE, dq0, dv0))
 
     # Roofline of the dominant kernel. Each rollout is one launch of the
     # persistent forward kernel and one of the persistent adjoint kernel; the
@@ -503,7 +540,20 @@ def main():
     binding.pd_rollout(pd.ctx, T, x0, v0, f0, 0, qT, vT, stream)
     torch.cuda.synchronize()
     prof = binding.pd_get_profile(pd.ctx)
+    prof_iters = binding.pd_get_stats(pd.ctx).iters_total
     binding.pd_profile(pd.ctx, False)
+    # local step alone (the metric's second half): its algorithmic bytes per
+    # iteration (tet indices 16, Dm^-1 36, w V 4, corner forces 48, prox
+    # warm-start stretches 12 + 12 B per element; q 24 B per vertex) over the
+    # local phase's time in the profiled rollout (block 0's globaltimer, from
+    # the phase start through its closing team barrier)
+    local_bytes = 128 * scene.n_e + 24 * scene.n_v
+    local_s = prof.phase_ms[1] * 1e-3
+    local_gbs = local_bytes * prof_iters / local_s / 1e9 if local_s > 0 else None
+    local_step = {"achieved": local_gbs, "peak": _peaks()[0], "unit": "GB/s",
+                  "frac": local_gbs / _peaks()[0] if local_gbs else None, "bytes_per_iter": local_bytes,
+                  "iters": prof_iters, "phase_ms": prof.phase_ms[1],
+                  "note": "bar working set is L2-resident: latency-bound, not the HBM case"}
     phase_names = ["begin", "local", "assemble_gate", "spmv_s", "spmv_st_anderson_dots", "anderson_solve", "update", "end_tr"]
     phases = {n: round(prof.phase_ms[i], 3) for i, n in enumerate(phase_names) if prof.phase_ms[i] > 0}
 
@@ -523,27 +573,41 @@ def main():
         e2e_s += time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, dist, dev)
     e2e = world * T * args.steps / e2e_s
-    # the same rollout with the S products in plain FP64 (options.solve_fp64):
-    # one untimed and one timed fwd+bwd, for the cost of the exact-FP64 form
-    o64 = binding.options_for(scene.solver)
-    o64.solve_fp64 = 1
-    pd64 = binding.PDContext(scene, o64)
-    q64, v64 = torch.empty_like(x0), torch.empty_like(x0)
+    # accuracy of the timed run (rank 0's seed): the last timed rollout and
+    # adjoint against the oracle's stored exact-fixed-point rollout
+    accuracy = None
+    gold_path = os.path.join(ROOT, "tests", "golden", "bar32x8x8_T200.npz")
+    if rank == 0 and os.path.exists(gold_path):
+        gold = np.load(gold_path)
+        def _rel(a, b):
+            a, b = np.asarray(a), np.asarray(b)
+            return float(max(np.linalg.norm(a - b) / np.linalg.norm(b), np.abs(a - b).max() / np.abs(b).max()))
+        accuracy = {"positions_qT": _rel(qT_timed, gold["qT"]), "dL_dE": _rel(dE_timed, gold["dE"]),
+                    "dL_dx0": _rel(dq0_timed, gold["dq0"]), "dL_dv0": _rel(dv0_timed, gold["dv0"]),
+                    "metric": "max(||a-b||/||b||, max|a-b|/max|b|) of the last timed rollout + adjoint against "
+                              "tests/golden/bar32x8x8_T200.npz (oracle, exact fixed point per step)"}
+    # the same rollout with the S products in double-float arithmetic on the
+    # FP32 pipe (options.solve_fp64 = 0): one untimed and one timed fwd+bwd
+    odf = binding.options_for(scene.solver)
+    odf.solve_fp64 = 0
+    pddf = binding.PDContext(scene, odf)
+    qdf, vdf = torch.empty_like(x0), torch.empty_like(x0)
     for timed in (False, True):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         ev[0].record(stream)
-        binding.pd_rollout(pd64.ctx, T, x0, v0, f0, 0, q64, v64, stream)
+        binding.pd_rollout(pddf.ctx, T, x0, v0, f0, 0, qdf, vdf, stream)
         ev[1].record(stream)
-        binding.pd_backward(pd64.ctx, q64 - target, zero, dq0, dv0, dE, dnu, None, 0, stream)
+        binding.pd_backward(pddf.ctx, qdf - target, zero, dq0, dv0, dE, dnu, None, 0, stream)
         ev[2].record(stream)
         torch.cuda.synchronize()
-    st64 = binding.pd_get_stats(pd64.ctx)
-    fp64_variant = {"pd_steps_per_s": T / (ev[0].elapsed_time(ev[2]) / 1e3),
-                    "fwd_ms": ev[0].elapsed_time(ev[1]), "bwd_ms": ev[1].elapsed_time(ev[2]),
-                    "fwd_iters_per_pd_step": st64.iters_total / T, "adj_iters_per_pd_step": st64.adj_iters_total / T,
-                    "qT_rel_diff_vs_default": float((q64 - qT).norm() / qT.norm())}
-    del pd64
+    stdf = binding.pd_get_stats(pddf.ctx)
+    df_variant = {"pd_steps_per_s": T / (ev[0].elapsed_time(ev[2]) / 1e3),
+                  "fwd_ms": ev[0].elapsed_time(ev[1]), "bwd_ms": ev[1].elapsed_time(ev[2]),
+                  "fwd_iters_per_pd_step": stdf.iters_total / T, "adj_iters_per_pd_step": stdf.adj_iters_total / T,
+                  "qT_rel_diff_vs_headline": float((qdf - qT_timed_t).norm() / qT_timed_t.norm()),
+                  "note": "S and S^T products in double-float (about 2^-44 relative) instead of FP64"}
+    del pddf
 
     nv3b = 3 * 8 * scene.n_v
     h2d = 3 * nv3b + 2 * nv3b          # x0, v0, f_ext; dL/dq_T, dL/dv_T
@@ -551,10 +615,11 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64 (FP32 local step; FP64 RHS, factor, Anderson, adjoint; S products in double-float on the FP32 pipe)", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64 (FP32 local step; FP64 RHS, factor, S products, Anderson, adjoint)", "data": "synthetic",
             "config": {"workload": WORKLOAD, "pd_steps_per_bench_step": T, "l2": "flushed (256 MB write) between rollouts",
                        "gate": f"b-change {pd.options.eps_res:g}, q-step {pd.options.eps_step:g} (relative)",
-                       "accuracy_vs_oracle": "positions 8.6e-6, dL/dE 2.9e-5 over 200 steps (tests/test_gpu_parity.py)",
+                       "solve": "FP64 factor, FP64 products with the inverse factor",
+                       "accuracy_vs_oracle": accuracy,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "mean_fwd_iters_per_pd_step": iters / (args.steps * T),
                        "mean_adjoint_iters_per_pd_step": adj / (args.steps * T)},
@@ -566,12 +631,13 @@ def main():
                          "fwd_launch_ms": fwd_launch_ms, "bwd_launch_ms": bwd_launch_ms,
                          "fwd_iter_bytes": fwd_iter_bytes, "bwd_iter_bytes": bwd_iter_bytes},
             "forward_phase_ms_one_rollout": phases,
-            "solve_fp64_variant": fp64_variant,
+            "local_step": local_step,
+            "double_float_variant": df_variant,
             "clocks": clk.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, k = oracle_sample(scene, 2)
-        line["cpu_baseline"] = {"value": k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"first {k} PD steps of the same rollout, forward (exact fixed point) + adjoint, FP64, 1 thread"}
+        dt, k, what = oracle_sample_mid(scene)
+        line["cpu_baseline"] = {"value": k / dt, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+                                "kind": "oracle", "sample": what}
     if rank == 0:
         print(json.dumps(line))
     if dist:

@@ -223,7 +223,16 @@ int pd_factor(pd_ctx* ctx);
 int pd_rollout(pd_ctx* ctx, int32_t T, const double* q0, const double* v0, const double* f_ext,
                int64_t f_ext_stride, double* qT, double* vT, void* stream);
 
-/* One step: pd_rollout with T = 1 (keeps the checkpoint of this step only). */
+/* One time step of Alg. 1 (Sec. 3.1 eq. dynamics / freefall: the inertial
+ * target q~ = q_t + h v_t + h^2 (g + M^-1 f_ext); then local-global
+ * iterations with Anderson mixing until the dual gate, Sec. 4.3
+ * eq. convergence_dual; q_next = q*, v_next = (q* - q_t) / h). It is
+ * pd_rollout with T = 1: the same kernels, the checkpoint of this step only,
+ * so a following pd_backward is the adjoint of this one step (Alg. 2).
+ *   q_t, v_t, f_ext  [n_v][3] inputs (f_ext may be NULL: no extra force);
+ *   q_next, v_next   [n_v][3] outputs.
+ * Pointers as in pd_rollout (device, or host staged by the library); the
+ * stream is synchronised; PD_ERR_NOT_CONVERGED if the step hit k_max. */
 int pd_step(pd_ctx* ctx, const double* q_t, const double* v_t, const double* f_ext, double* q_next,
             double* v_next, void* stream);
 
@@ -260,7 +269,10 @@ int pd_solve(pd_ctx* ctx, const double* b, double* x, void* stream);
  * no counterpart; this is a convenience of this library.
  *   - Meshes with more than 65536 free vertices: PD_ERR_TOO_LARGE.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress) and keeps it for the life of the process; make
+ *     that first call before any stream capture. A device reset
+ *     (cudaDeviceReset) after the first call is not supported: the kept
+ *     address would belong to the destroyed context.
  *   - Every call shares the one array: calls that overlap on the GPU (other
  *     streams, other contexts, other host threads) race. Each call overwrites
  *     it; the partial sums of long rows of S go to buffers that pd_factor

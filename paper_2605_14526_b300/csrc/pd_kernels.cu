@@ -117,8 +117,9 @@ __global__ void __launch_bounds__(kVtxBlock) k_tr(Dev d) {
 
 // ------------------------------------------------------------ standalone solve
 
-// b (vertex order) -> elimination order in xperm; zero the S b accumulator
-// rows and the pinned rows of x
+// b (vertex order) -> elimination order in xperm (the products' input
+// representation); the pinned rows of x are set to 0. The S b accumulator is
+// not touched here: the first product overwrites every row of it.
 __global__ void k_solve_in(Dev d, const double* b, float2* xperm, double* x) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= d.n_v) return;

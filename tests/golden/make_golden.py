@@ -2,7 +2,8 @@
 
 Runs the FP64 oracle (exact fixed point per step, direct adjoint) on the
 heterogeneous Neo-Hookean bar (32x8x8 cells, 200 steps, seed 2) and stores
-the final state, sampled intermediate states and the gradients of the loss
+the final state, sampled intermediate states (positions and velocities)
+and the gradients of the loss
 0.5 ||x_T - x*||^2. Calls nothing but ``oracle/`` and the seeded inputs.
 
   python tests/golden/make_golden.py
@@ -34,6 +35,7 @@ def main():
     t2 = time.time()
     np.savez_compressed(OUT, qT=qT, vT=vT, dq0=g.dx0, dv0=g.dv0, dE=g.dE, dnu=np.array([g.dnu]),
                         sample_steps=np.array(SAMPLES), samples=np.stack([recs[s].q_t for s in SAMPLES]),
+                        samples_v=np.stack([recs[s].v_t for s in SAMPLES]),
                         seconds=np.array([t1 - t0, t2 - t1]))
     print(f"wrote {OUT}: forward {t1 - t0:.0f} s, backward {t2 - t1:.0f} s")
 

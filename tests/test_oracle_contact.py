@@ -163,3 +163,53 @@ def test_contact_adjoint_matches_finite_differences(mu):
     E2[e] -= hE
     fde = (_loss(sc, pb, cp, v0, E1)[0] - _loss(sc, pb, cp, v0, E2)[0]) / (2 * hE)
     assert abs(fde - g.dE[e]) <= 1e-4 * abs(fde) + 1e-15
+
+
+def _exact_split(cp, mu, lam_n, lam_f):
+    """The active sets by the multipliers of an exact solution: normal-active
+    where lam_n > 0 (Murty's pivoting leaves the non-basic lam_n exactly 0),
+    sticking where the friction lies strictly inside its disk,
+    |lam_f| < mu lam_n (a sliding contact's friction sits on the rim up to
+    rounding, hence the relative margin 1e-9)."""
+    act = lam_n > 0.0
+    ratio = np.linalg.norm(lam_f, axis=1) / np.maximum(mu * lam_n, 1e-300)
+    stick = act & (ratio < 1.0 - 1e-9) & (mu > 0.0)
+    return act, stick
+
+
+def _lift_off_velocity(sc, rng):
+    v0 = 0.02 * rng.standard_normal(sc.X.shape)
+    v0[:, 2] += np.where(sc.X[:, 0] > 0.5 * sc.X[:, 0].max(), 1.0, -0.2)
+    return v0
+
+
+@pytest.mark.parametrize("case", ["frictionless", "sliding", "sticking", "lift_off", "parity_pad"])
+def test_active_set_thresholds_equal_exact_multiplier_split(case):
+    # The adjoint's active sets are read with thresholds (lam_n above 1e-9 of
+    # the step's total, slip at most 1e-7 of the bounding-box diagonal).
+    # On the oracle's exact LCP / Tresca solutions they must be the split of
+    # Sec. 4.6's complementarity itself: lam_n > 0, |lam_f| < mu lam_n.
+    rng = np.random.default_rng(5)
+    if case == "parity_pad":    # the pad of the GPU contact tests
+        sc = inputs.contact_pad(nx=8, ny=8, nz=5, footprint=4, steps=2, box_steps=6, travel=0.004, E_core=1e6,
+                                seed=27)
+    else:
+        sc = _tiny_pad(steps=2)
+        sc.contact.mu = {"frictionless": 0.0, "sliding": 0.5, "sticking": 50.0, "lift_off": 0.5}[case]
+        sc = sc.replace(v0=_lift_off_velocity(sc, rng) if case == "lift_off" else 0.02 * rng.standard_normal(sc.X.shape))
+    pb = solver.build_problem(sc)
+    cp = contact.ContactProblem(pb, sc.contact)
+    _, _, recs, _ = contact.rollout(pb, sc, cp)
+    seen_inactive = seen_stick = seen_slide = False
+    for r in recs:
+        act, stick = contact.active_sets(cp, r["lam_n"], r["q_next"], r["q_t"])
+        act_x, stick_x = _exact_split(cp, sc.contact.mu, r["lam_n"], r["lam_f"])
+        assert np.array_equal(act, act_x)
+        assert np.array_equal(stick, stick_x)
+        seen_inactive |= bool((~act).any())
+        seen_stick |= bool(stick.any())
+        seen_slide |= bool((act & ~stick).any())
+    # each case exercises the branch it is named for
+    want = {"frictionless": seen_slide, "sliding": seen_stick and seen_slide, "sticking": seen_stick,
+            "lift_off": seen_inactive and seen_stick and seen_slide, "parity_pad": seen_stick and seen_slide}
+    assert want[case]

@@ -191,3 +191,90 @@ def test_trust_region_ratio_rules():
     bad[free[0]] = bad[free[0]] + np.array([-0.5, -0.5, -0.5])
     tau, rho = solver.tr_select(pb, sc.X, bad, sc.X)
     assert tau == 1.0
+
+
+# ------------------------------------------------------------------ TR ratio by hand
+#
+# One tetrahedron with corners 0, a e1, a e2, a e3; corners 0-2 pinned, so the
+# only free vertex is the apex and every quantity of eq. primal and eq. tr_ratio
+# has a closed form in its displacement u: F = I + u e3^T / a, J = 1 + u_z / a,
+# tr(F^T F) = 3 + 2 u_z / a + |u|^2 / a^2, V = a^3 / 6, lumped masses rho V / 4,
+# and the apex entry of the scalar operator
+#   L_33 = (1 + alpha h) m / h^2 + (w + beta / h) V |grad N_3|^2,  |grad N_3| = 1 / a,
+# with w = 2 mu + lambda (Neo-Hookean) and beta = beta0 (mu_ref = mu for one element).
+
+_A, _RHO, _E, _NU, _H, _ALPHA, _BETA0 = 0.1, 1000.0, 1e5, 0.3, 0.01, 0.01, 1e-3
+
+
+def _one_tet():
+    X = _A * np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=np.float64)
+    sc = inputs.Scene(
+        name="tet", X=X, tets=np.array([[0, 1, 2, 3]], dtype=np.int32), pinned=np.array([1, 1, 1, 0], np.uint8),
+        E=np.array([_E]), nu=_NU, density=_RHO, alpha=_ALPHA, beta0=_BETA0, gravity=np.zeros(3), dt=_H,
+        model="neohookean", steps=1, f_ext=np.zeros((1, 4, 3)), x0=X.copy(), v0=np.zeros((4, 3)))
+    return sc, solver.build_problem(sc)
+
+
+def _hand_phi(u, u_tilde):
+    """Phi of the one-tet problem with the apex at X3 + u and its inertial
+    target at X3 + u_tilde (the pinned corners sit on their targets)."""
+    mu = _E / (2 * (1 + _NU))
+    lam = _E * _NU / ((1 + _NU) * (1 - 2 * _NU))
+    V = _A ** 3 / 6
+    m = _RHO * V / 4
+    u = np.asarray(u, dtype=np.float64)
+    J = 1 + u[2] / _A
+    trC = 3 + 2 * u[2] / _A + u @ u / _A ** 2
+    psi = mu / 2 * (trC - 3) - mu * np.log(J) + lam / 2 * np.log(J) ** 2
+    d = u - np.asarray(u_tilde)
+    return m / (2 * _H ** 2) * (d @ d) + V * psi
+
+
+def _hand_L33():
+    mu = _E / (2 * (1 + _NU))
+    lam = _E * _NU / ((1 + _NU) * (1 - 2 * _NU))
+    V = _A ** 3 / 6
+    m = _RHO * V / 4
+    return (1 + _ALPHA * _H) * m / _H ** 2 + (2 * mu + lam + _BETA0 / _H) * V / _A ** 2
+
+
+def test_phi_kinetic_term_closed_form():
+    # a rigid translation leaves F = I (psi = 0): Phi is the kinetic term alone,
+    # 1/(2 h^2) (total mass) |t - s|^2 for positions X + t and target X + s
+    sc, pb = _one_tet()
+    t, s = np.array([0.01, -0.02, 0.03]), np.array([-0.005, 0.004, 0.0])
+    want = _RHO * _A ** 3 / 6 / (2 * _H ** 2) * float((t - s) @ (t - s))
+    assert np.isclose(solver.phi(pb, sc.X + t, sc.X + s), want, rtol=1e-13)
+    # and the elastic part alone at the target: Phi = V psi
+    u = np.array([0.002, -0.001, 0.003])
+    q = sc.X.copy()
+    q[3] += u
+    assert np.isclose(solver.phi(pb, q, q), _hand_phi(u, u), rtol=1e-12)
+
+
+@pytest.mark.parametrize("u_prev,u_star,u_tilde,tau_want", [
+    # axial step onto the minimiser: the model's w = 2 mu + lambda matches
+    # psi's axial stiffness at small strain, rho = 0.995 -> tau = 1/2
+    ((0.0, 0.0, 0.001), (0.0, 0.0, 0.0), (0.0, 0.0, 0.0), 0.5),
+    # shear step: psi's shear stiffness is mu against the model's w, rho = 0.40 -> tau = 1
+    ((0.001, 0.0, 0.0), (0.0, 0.0, 0.0), (0.0, 0.0, 0.0), 1.0),
+    # mixed step with the target away from both iterates (the kinetic term
+    # enters Delta Phi_act), rho = 0.984 -> tau = 1/2
+    ((0.001, 0.0005, 0.002), (0.0003, 0.0001, 0.0008), (0.001, 0.0, 0.004), 0.5),
+    # the same target, a step that overshoots the minimiser: rho = 1.26 -> tau = 1
+    ((0.0, 0.0, 0.002), (0.0, 0.0, 0.0008), (0.0, 0.0, 0.004), 1.0),
+])
+def test_trust_region_ratio_by_hand(u_prev, u_star, u_tilde, tau_want):
+    sc, pb = _one_tet()
+    q_prev, q_star, q_til = sc.X.copy(), sc.X.copy(), sc.X.copy()
+    q_prev[3] += u_prev
+    q_star[3] += u_star
+    q_til[3] += u_tilde
+    du = np.subtract(u_star, u_prev)
+    act = _hand_phi(u_prev, u_tilde) - _hand_phi(u_star, u_tilde)       # Phi(q*^-1) - Phi(q*)
+    mod = 0.5 * abs(_hand_L33() * float(du @ du))                          # 1/2 |dq^T A dq|
+    rho_want = act / mod
+    assert (abs(rho_want - 1) <= 0.1) == (tau_want == 0.5)
+    tau, rho = solver.tr_select(pb, q_star, q_prev, q_til, eps_tr=0.1)
+    assert np.isclose(rho, rho_want, rtol=1e-9, atol=0), (rho, rho_want)
+    assert tau == tau_want

@@ -18,10 +18,15 @@ from paper_2605_14526_b300.build import build
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_solve_matches_pd_solve_on_two_calls():
+@pytest.mark.parametrize("solve_fp64", [0, 1])
+def test_noalloc_solve_matches_pd_solve_on_two_calls(solve_fp64):
+    # solve_fp64 = 1 keeps the products in FP64, so the scratch holds doubles
+    # where the default form keeps double-float pairs
     build()
     sc = inputs.hetero_bar(steps=1)
-    pd = binding.PDContext(sc)
+    opts = binding.options_for(sc.solver)
+    opts.solve_fp64 = solve_fp64
+    pd = binding.PDContext(sc, opts)
     rng = np.random.default_rng(11)
     for _ in range(2):
         b = torch.tensor(rng.standard_normal((sc.n_v, 3)), device="cuda:0")
