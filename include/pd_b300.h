@@ -47,6 +47,8 @@ typedef enum {
 
 enum { PD_COROTATED = 0, PD_NEOHOOKEAN = 1 };
 enum { PD_TR_ADAPT = 0, PD_TR_NONE = 1, PD_TR_CLAMP = 2, PD_TR_ABS = 3 };
+/* How every A^-1 application is computed (pd_options.solve_mode). */
+enum { PD_SOLVE_AUTO = 0, PD_SOLVE_S = 1, PD_SOLVE_T = 2 };
 
 /* Mesh, copied by pd_create (host pointers). */
 typedef struct {
@@ -104,6 +106,21 @@ typedef struct {
                              a team barrier before it gives up, sets the timeout flag and
                              returns; the call then fails with PD_ERR_TIMEOUT and the context
                              stays usable (0 = 4194304, about 2 s). Fixed at pd_create. */
+  int32_t solve_mode;     /* how A^-1 is applied (Sec. 4.5; read at pd_factor):
+                             PD_SOLVE_S: the two products with the inverse factor S = L^-1 P
+                               (eq. Ainv_STS / two_spmv); S holds every descendant of a
+                               column of the elimination tree, so it grows like n^(5/3) on
+                               3-D meshes (10% of n^2 on a 2,592-vertex bar, 2.5e9 entries
+                               at 270k vertices);
+                             PD_SOLVE_T: forward and backward triangular solves with the
+                               factor L itself, level-scheduled over the separator tree
+                               (one pass per tree height), each node's block column of L
+                               replaced by its partitioned inverse [L_ss^-1; L_bs L_ss^-1]
+                               (about nnz(L) entries, stored row- and column-major), FP64
+                               arithmetic; not with contacts;
+                             PD_SOLVE_AUTO (0, default): T when there are no contacts and
+                               nnz(S) > 8e6 and nnz(S) > 4 nnz(L) (S no longer near the L2
+                               size and several times L), or nnz(S) exceeds 2^31 - 1; else S. */
 } pd_options;
 
 /* Statistics of the last pd_rollout / pd_backward (host copy). */
@@ -120,7 +137,8 @@ typedef struct {
   int32_t adj_not_converged;
   int32_t status_flags;     /* bit 0: NaN/Inf seen; bit 1: PCG breakdown */
   int32_t n_free;           /* free vertices */
-  int64_t factor_nnz;       /* stored non-zeros of the inverse factor S */
+  int64_t factor_nnz;       /* stored entries of the solve: non-zeros of the inverse factor S
+                               (mode S) or of one copy of the partitioned inverse (mode T) */
   double factor_seconds;    /* host time of the last pd_factor */
   double last_rho;          /* trust-region ratio of the last step */
   int64_t launches;         /* kernel launches issued by this context so far */
@@ -131,6 +149,10 @@ typedef struct {
   double bwd_device_seconds;  /* ... of the last adjoint */
   int32_t contact_iters;      /* contact: inner solver passes over W in the last rollout */
   int32_t contact_unconverged;/* contact: inner solves that hit contact_max_iters */
+  int32_t solve_mode;         /* PD_SOLVE_S or PD_SOLVE_T as chosen by pd_factor (a batch: the
+                                 largest over its instances) */
+  int32_t solve_levels;       /* mode T: heights of the separator tree (passes per sweep) */
+  int64_t nnz_L;              /* non-zeros of the factor L (a batch: summed) */
 } pd_stats;
 
 typedef struct pd_ctx pd_ctx;
@@ -202,10 +224,14 @@ int pd_set_materials(pd_ctx* ctx, const double* E, double nu);
  * eq. pd_weight; Sec. 7.2), beta_e = beta0 mu_e / mu_ref, mu_ref = max mu_e
  * frozen here. Pins are eliminated. The scalar operator (A = L_A (x) I_3) is
  * reordered by geometric nested dissection, factored by a supernodal
- * Cholesky in FP64 on the host, and its inverse factor S = L^-1 P
- * (A^-1 = S^T S, Sec. 4.5 eq. Ainv_STS, two_spmv) is uploaded. Returns
- * PD_ERR_NOT_SPD on a non-positive pivot, PD_ERR_TOO_LARGE if nnz(S) exceeds
- * 2^31 - 1. Blocking. */
+ * Cholesky in FP64 on the host, and uploaded in the form the solve mode
+ * (pd_options.solve_mode) applies: the inverse factor S = L^-1 P
+ * (A^-1 = S^T S, Sec. 4.5 eq. Ainv_STS, two_spmv), or the partitioned
+ * inverse of L by separator-tree node for the level-scheduled triangular
+ * solves (mode T). Returns PD_ERR_NOT_SPD on a non-positive pivot,
+ * PD_ERR_TOO_LARGE if mode S is asked for and nnz(S) exceeds 2^31 - 1,
+ * PD_ERR_ARG for mode T with contacts, PD_ERR_NUMERIC if the host check of
+ * the mode-T structures against the factor fails. Blocking. */
 int pd_factor(pd_ctx* ctx);
 
 /* T implicit-Euler PD steps from (q0, v0) (Alg. 1 per step): inertial target,

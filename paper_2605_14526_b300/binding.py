@@ -23,6 +23,7 @@ STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_MESH", 3: "PD_ERR_NOT_FACTORED
           9: "PD_ERR_OOM", 10: "PD_ERR_NO_CHECKPOINT", 11: "PD_ERR_TOO_LARGE"}
 PD_COROTATED, PD_NEOHOOKEAN = 0, 1
 PD_TR_ADAPT, PD_TR_NONE, PD_TR_CLAMP, PD_TR_ABS = 0, 1, 2, 3
+PD_SOLVE_AUTO, PD_SOLVE_S, PD_SOLVE_T = 0, 1, 2
 
 
 class pd_mesh(ctypes.Structure):
@@ -40,7 +41,7 @@ class pd_options(ctypes.Structure):
                 ("eps_step", c_double), ("eps_res", c_double),
                 ("eps_abs", c_double), ("eps_tr", c_double), ("adj_tol", c_double),
                 ("escalate_window", c_int32), ("warm_start", c_int32), ("solve_fp64", c_int32),
-                ("wait_polls", c_int32)]
+                ("wait_polls", c_int32), ("solve_mode", c_int32)]
 
 
 class pd_stats(ctypes.Structure):
@@ -51,7 +52,8 @@ class pd_stats(ctypes.Structure):
                 ("factor_seconds", c_double), ("last_rho", c_double), ("launches", c_int64),
                 ("escalations", c_int32), ("warm_fallbacks", c_int32),
                 ("fwd_device_seconds", c_double), ("bwd_device_seconds", c_double),
-                ("contact_iters", c_int32), ("contact_unconverged", c_int32)]
+                ("contact_iters", c_int32), ("contact_unconverged", c_int32),
+                ("solve_mode", c_int32), ("solve_levels", c_int32), ("nnz_L", c_int64)]
 
 
 class pd_contact_desc(ctypes.Structure):
@@ -505,6 +507,7 @@ def options_for(settings) -> pd_options:
     o.eps_abs = settings.eps_abs
     o.eps_tr = settings.eps_tr
     o.solve_fp64 = 1 if getattr(settings, "solve_fp64", False) else 0
+    o.solve_mode = int(getattr(settings, "solve_mode", PD_SOLVE_AUTO))
     return o
 
 

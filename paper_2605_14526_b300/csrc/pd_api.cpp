@@ -16,6 +16,7 @@
 
 #include "../../include/pd_b300.h"
 #include "factor.h"
+#include "tsolve.h"
 #include "pd_ctx.h"
 #include "pd_internal.h"
 #include "pd_launch.h"
@@ -141,6 +142,7 @@ void pd_default_options(pd_options* o) {
   o->warm_start = 0;
   o->solve_fp64 = 0;
   o->wait_polls = 0;
+  o->solve_mode = PD_SOLVE_AUTO;
 }
 
 const char* pd_last_error(const pd_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -173,6 +175,8 @@ int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_o
   *out = c;
   if (c->opt.aa_m < 0 || c->opt.aa_m > pdk::kMaxAA) return fail(c, PD_ERR_ARG, "aa_m must be in [0, %d]", pdk::kMaxAA);
   if (c->opt.k_max < 1 || c->opt.adj_max_iters < 1) return fail(c, PD_ERR_ARG, "k_max and adj_max_iters must be >= 1");
+  if (c->opt.solve_mode < PD_SOLVE_AUTO || c->opt.solve_mode > PD_SOLVE_T)
+    return fail(c, PD_ERR_ARG, "solve_mode must be PD_SOLVE_AUTO, PD_SOLVE_S or PD_SOLVE_T");
   for (size_t i = 0; i < c->tets.size(); ++i)
     if (c->tets[i] < 0 || c->tets[i] >= c->n_v) return fail(c, PD_ERR_ARG, "tet index out of range at %zu", i);
   for (int e = 0; e < c->n_e; ++e)
@@ -417,16 +421,50 @@ int pd_factor(pd_ctx* c) {
     if (!(std::sqrt(rn) <= 1e-8 * std::sqrt(bn))) return fail(c, PD_ERR_NOT_SPD, "factor residual %g", std::sqrt(rn / bn));
   }
   c->nnz_S = pdf::inverse_factor_nnz(c->fac);
-  if (c->nnz_S > (int64_t)2147483647) return fail(c, PD_ERR_TOO_LARGE, "nnz(S) = %lld exceeds 2^31-1", (long long)c->nnz_S);
+  // solve mode: products with S, or level-scheduled solves with L (mode T)
+  const bool has_con = !c->con_ground.empty() || !c->con_box.empty();
+  int mode = c->opt.solve_mode;
+  if (mode == PD_SOLVE_T && has_con) return fail(c, PD_ERR_ARG, "solve mode T does not support contacts");
+  // automatic choice: S while its stream stays near the L2 size (2 barriers
+  // per solve, latency-bound meshes), T once S is both large (more than 8M
+  // entries, 160 MB a solve) and several times the factor
+  if (mode == PD_SOLVE_AUTO)
+    mode = !has_con && ((c->nnz_S > 8000000 && c->nnz_S > 4 * c->fac.nnz_L) || c->nnz_S > (int64_t)2147483647)
+               ? PD_SOLVE_T
+               : PD_SOLVE_S;
+  const bool tmode = mode == PD_SOLVE_T;
+  if (!tmode && c->nnz_S > (int64_t)2147483647)
+    return fail(c, PD_ERR_TOO_LARGE, "nnz(S) = %lld exceeds 2^31-1 (solve mode T does not store S)", (long long)c->nnz_S);
   std::vector<int64_t> s_rowptr, st_ptr;
   std::vector<double> s_val, st_val;
   std::vector<int> st_idx;
-  pdf::inverse_factor(c->fac, s_rowptr, s_val, st_ptr, st_idx, st_val);
+  pdf::TSolve ts;
+  if (tmode) {
+    pdf::build_tsolve(c->fac, ts);
+    // host check of the sweeps against the factor's own solve (3 right-hand sides)
+    std::vector<double> b3(3 * (size_t)nf), x3(3 * (size_t)nf), b1(nf), x1(nf);
+    for (size_t i = 0; i < b3.size(); ++i) b3[i] = std::cos(0.731 * (double)i + 0.2);
+    pdf::tsolve_host(ts, b3.data(), x3.data());   // positions in, positions out
+    double en = 0, xn = 0;
+    for (int a = 0; a < 3; ++a) {
+      for (int k = 0; k < nf; ++k) b1[c->fac.perm[k]] = b3[3 * (size_t)k + a];
+      pdf::solve_host(c->fac, b1.data(), x1.data());
+      for (int k = 0; k < nf; ++k) {
+        const double dx = x3[3 * (size_t)k + a] - x1[c->fac.perm[k]];
+        en += dx * dx;
+        xn += x1[c->fac.perm[k]] * x1[c->fac.perm[k]];
+      }
+    }
+    if (!(std::sqrt(en) <= 1e-10 * std::sqrt(xn)))
+      return fail(c, PD_ERR_NUMERIC, "mode T host check: relative difference %g from the factor's solve", std::sqrt(en / xn));
+  } else {
+    pdf::inverse_factor(c->fac, s_rowptr, s_val, st_ptr, st_idx, st_val);
+  }
   // skyline segments of at most kSegLen entries, one warp each; the segments
   // of a split row own consecutive partial slots
   std::vector<int4> seg;
   int n_slot = 0;
-  for (int i = 0; i < nf; ++i) {
+  for (int i = 0; i < nf && !tmode; ++i) {
     const int len = i - c->fac.first_desc[i] + 1;
     const int ns = (len + pdk::kSegLen - 1) / pdk::kSegLen;
     for (int s = 0; s < ns; ++s)
@@ -447,8 +485,8 @@ int pd_factor(pd_ctx* c) {
   // contact contexts keep the products in FP64: W is formed from the FP64
   // factor, and the adjoint's projection needs the device's A^-1 to agree
   // with it (with double-float products its projected CG does not settle)
-  const bool s64 = c->opt.solve_fp64 || !c->con_ground.empty() || !c->con_box.empty();
-  if (s64) {
+  const bool s64 = c->opt.solve_fp64 || has_con;
+  if (s64 && !tmode) {
     int r0;
     if ((r0 = upload(c, &sv64, s_val, true)) || (r0 = upload(c, &stv64, st_val, true))) return r0;
   }
@@ -496,7 +534,40 @@ int pd_factor(pd_ctx* c) {
   }
   d.coef32 = c32; d.coef64 = c64; d.mu_e = mu_d; d.lam_e = lam_d; d.E = E_d; d.cA = cA_d;
   d.iperm = iperm_d; d.perm = perm_d; d.s_rowptr = srp; d.s_first = sfirst; d.s_hl = sv; d.s_seg = seg_d;
-  d.sfp64 = s64 ? 1 : 0; d.s_val64 = sv64; d.st_val64 = stv64;
+  d.sfp64 = (s64 || tmode) ? 1 : 0; d.s_val64 = sv64; d.st_val64 = stv64;
+  d.tmode = tmode ? 1 : 0;
+  d.t_nlev = 0;
+  if (tmode) {
+    auto units = [](const std::vector<int>& u) {
+      std::vector<int4> o(u.size() / 3);
+      for (size_t i = 0; i < o.size(); ++i) o[i] = make_int4(u[3 * i], u[3 * i + 1], u[3 * i + 2], 0);
+      return o;
+    };
+    const std::vector<int4> uf = units(ts.unit_f), ub = units(ts.unit_b);
+    int *c0d, *ncd, *nbd, *bld, *gpd, *gsd, *lfd, *lbd, *lwd, *wnd;
+    int64_t *bod, *pod, *god;
+    double *prd, *pcd, *Ud, *xd;
+    int4 *ufd, *ubd;
+    if ((r = upload(c, &c0d, ts.c0, true)) || (r = upload(c, &ncd, ts.nc, true)) || (r = upload(c, &nbd, ts.nb, true)) ||
+        (r = upload(c, &bod, ts.boff, true)) || (r = upload(c, &bld, ts.below, true)) ||
+        (r = upload(c, &pod, ts.poff, true)) || (r = upload(c, &prd, ts.prow, true)) ||
+        (r = upload(c, &pcd, ts.pcol, true)) || (r = upload(c, &god, ts.goff, true)) ||
+        (r = upload(c, &gpd, ts.gptr, true)) || (r = upload(c, &gsd, ts.gsrc, true)) ||
+        (r = upload(c, &lfd, ts.lev_f, true)) || (r = upload(c, &lbd, ts.lev_b, true)) ||
+        (r = upload(c, &lwd, ts.lev_w, true)) || (r = upload(c, &ufd, uf, true)) || (r = upload(c, &ubd, ub, true)) ||
+        (r = upload(c, &wnd, ts.wnode, true)) || (r = dalloc(c, &Ud, 3 * (size_t)ts.u_rows, true)) ||
+        (r = dalloc(c, &xd, 3 * (size_t)nf, true)))
+      return r;
+    d.t_nlev = ts.n_level;
+    d.t_c0 = c0d; d.t_nc = ncd; d.t_nb = nbd; d.t_boff = bod; d.t_below = bld; d.t_poff = pod;
+    d.t_prow = prd; d.t_pcol = pcd; d.t_goff = god; d.t_gptr = gpd; d.t_gsrc = gsd;
+    d.t_lev_f = lfd; d.t_lev_b = lbd; d.t_lev_w = lwd; d.t_unit_f = ufd; d.t_unit_b = ubd; d.t_wnode = wnd;
+    d.t_U = Ud; d.t_x = xd;
+  }
+  c->tmode = tmode;
+  c->solve_nnz = tmode ? ts.entries : c->nnz_S;
+  c->solve_levels = tmode ? ts.n_level : 0;
+  c->tsolve_seconds = tmode ? ts.build_seconds : 0.0;
   d.spin_limit = c->opt.wait_polls > 0 ? (unsigned int)c->opt.wait_polls : (1u << 22);
   d.n_seg = (int)seg.size(); d.st_ptr = stp; d.st_idx = sti; d.st_hl = stv;
   d.n_slot = n_slot; d.s_part = spart; d.s_cnt = scnt; d.s_part_na = spart_na; d.s_cnt_na = scnt_na;
@@ -601,8 +672,11 @@ int pd_factor(pd_ctx* c) {
   c->factored = true;
   c->factor_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   c->stats.factor_seconds = c->factor_seconds;
-  c->stats.factor_nnz = c->nnz_S;
+  c->stats.factor_nnz = c->solve_nnz;
   c->stats.n_free = nf;
+  c->stats.solve_mode = tmode ? PD_SOLVE_T : PD_SOLVE_S;
+  c->stats.solve_levels = c->solve_levels;
+  c->stats.nnz_L = c->fac.nnz_L;
   return PD_OK;
 }
 

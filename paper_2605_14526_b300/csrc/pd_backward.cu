@@ -20,6 +20,7 @@
 #include "pd_launch.h"
 #include "pd_contact.cuh"
 #include "pd_phases.cuh"
+#include "pd_tsolve.cuh"
 #include "pd_bwd_elem.cuh"
 
 namespace pdk {
@@ -480,6 +481,22 @@ __global__ void k_bwd_finish(Dev d, double* dq0, double* dv0) {
 
 // ------------------------------------------------------------ persistent backward
 
+// mode T: each finished row j of z = A^-1 r (elimination order) goes to z
+// and to this thread's partial of r . z (lanes 0..2)
+struct FinRZ {
+  const Dev* d;
+  double acc;
+  __device__ __forceinline__ void operator()(int j, double a0, double a1, double a2) {
+    const int lane = threadIdx.x & 31;
+    if (lane < 3) {
+      const size_t o = 3 * (size_t)d->perm[j] + lane;
+      const double zv = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
+      d->z[o] = zv;
+      acc += d->r[o] * zv;
+    }
+  }
+};
+
 template <typename T>
 __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a, const Team tm) {
   __shared__ BwdState S;
@@ -576,12 +593,22 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
     for (int e = re.lo + tid; e < re.hi; e += blockDim.x) bwd_setup_item<T>(d, e, qstar, tau);
     for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) bwd_init_item(d, v);
     if (!(ok = grid_sync(d, tm))) break;
-    for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, d.s_part, d.s_cnt, sg, lane);
-    if (!(ok = grid_sync(d, tm))) break;
-    if (ck && !(ok = project(ck, true))) break;
-    // S^T y row by row with the partial r . z of the row fused in (first
-    // direction p = z: beta = 0 and p_old = 0 on the first iteration)
-    auto st_rz = [&](double* prz) {
+    // z = A^-1 r (r in elimination order in bperm) with the partial r . z of
+    // each finished row fused in: S b, the contact projection, then S^T y row
+    // by row; or, in mode T, the two level sweeps over the factor's
+    // partitioned inverse (first direction p = z: beta = 0 and p_old = 0 on
+    // the first iteration)
+    auto apply_rz = [&](double* prz, bool first) -> bool {
+      if (d.tmode) {
+        FinRZ fin{&d, 0.0};
+        const bool r = tsolve_team(d, reinterpret_cast<const double*>(d.bperm), reinterpret_cast<double*>(d.y), tm,
+                                   gwarp, nwarps, fin);
+        prz[0] += fin.acc;
+        return r;
+      }
+      for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, d.s_part, d.s_cnt, sg, lane);
+      if (!grid_sync(d, tm)) return false;
+      if (ck && !project(ck, first)) return false;
       for (int j = gwarp; j < d.n_f; j += nwarps) {
         double a0, a1, a2;
         spmv_st_sum(d, d.y, j, lane, a0, a1, a2);
@@ -592,9 +619,10 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
           prz[0] += d.r[o] * zv;
         }
       }
+      return true;
     };
     double p1[1] = {0.0};
-    st_rz(p1);
+    if (!(ok = apply_rz(p1, true))) break;
     if (!(ok = grid_reduce<1>(d, tm, p1, sums))) break;
     if (tid == 0) {
       init_z_finish(&S, sums);
@@ -616,11 +644,8 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
         if (!(ok = grid_sync(d, tm))) break;
         for (int v = rv.lo + (tid >> 5); v < rv.hi; v += blockDim.x >> 5) resid_warp<T>(d, v, lane);
         if (!(ok = grid_sync(d, tm))) break;
-        for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, d.s_part, d.s_cnt, sg, lane);
-        if (!(ok = grid_sync(d, tm))) break;
-        if (ck && !(ok = project(ck, true))) break;
         double prz0[1] = {0.0};
-        st_rz(prz0);
+        if (!(ok = apply_rz(prz0, true))) break;
         if (!(ok = grid_reduce<1>(d, tm, prz0, sums))) break;
         if (tid == 0) {
           S.rz = sums[0];
@@ -645,11 +670,8 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
       const double alpha = S.alpha;
       for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) pcg_r_item(d, v, alpha, pnew);
       if (!(ok = grid_sync(d, tm))) break;
-      for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, d.s_part, d.s_cnt, sg, lane);
-      if (!(ok = grid_sync(d, tm))) break;
-      if (ck && !(ok = project(ck, false))) break;
       double prz[1] = {0.0};
-      st_rz(prz);
+      if (!(ok = apply_rz(prz, false))) break;
       if (!(ok = grid_reduce<1>(d, tm, prz, sums))) break;
       if (tid == 0) {
         pcg_z_finish(d, &S, sums);

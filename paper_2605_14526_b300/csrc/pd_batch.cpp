@@ -266,20 +266,29 @@ int batch_factor(pd_ctx* c) {
     }
     rc[i] = pd_factor(B.kids[i]);
   }
-  int64_t nnz = 0;
-  int nf = 0;
+  int64_t nnz = 0, nnzL = 0;
+  int nf = 0, smode = 0, slev = 0;
   for (int i = 0; i < B.n; ++i) {
     if (rc[i]) return fail(c, rc[i], "instance %d: %s", i, B.kids[i]->err.c_str());
     const pd_ctx* k = B.kids[i];
     const double m = k->opt.aa_m;
     // bytes per iteration (forward: local step + assembly + two SpMVs with S +
     // Anderson; backward: K apply + PCG vectors + two SpMVs)
-    B.work[0][i] = 56.0 * k->n_e + 48.0 * k->n_v + 20.0 * k->nnz_S + 96.0 * k->n_f + (2 * m + 3) * 24.0 * k->n_v;
-    B.work[1][i] = 200.0 * k->n_e + 20.0 * k->nnz_S + 240.0 * k->n_v;
-    B.inst[i].factor_nnz = k->nnz_S;
+    // (solve: 20 B per non-zero of S, or 16 B per partitioned-inverse entry
+    // in mode T: one copy per sweep)
+    const double solve_b = (k->tmode ? 16.0 : 20.0) * (double)k->solve_nnz;
+    B.work[0][i] = 56.0 * k->n_e + 48.0 * k->n_v + solve_b + 96.0 * k->n_f + (2 * m + 3) * 24.0 * k->n_v;
+    B.work[1][i] = 200.0 * k->n_e + solve_b + 240.0 * k->n_v;
+    B.inst[i].factor_nnz = k->solve_nnz;
     B.inst[i].n_free = k->n_f;
     B.inst[i].factor_seconds = k->factor_seconds;
-    nnz += k->nnz_S;
+    B.inst[i].solve_mode = k->tmode ? PD_SOLVE_T : PD_SOLVE_S;
+    B.inst[i].solve_levels = k->solve_levels;
+    B.inst[i].nnz_L = k->fac.nnz_L;
+    nnz += k->solve_nnz;
+    nnzL += k->fac.nnz_L;
+    smode = std::max(smode, B.inst[i].solve_mode);
+    slev = std::max(slev, k->solve_levels);
     nf += k->n_f;
     // per-instance Dev records must point at the batch's contiguous state
     B.kids[i]->d.ctrl = B.ctrl + i;
@@ -290,6 +299,9 @@ int batch_factor(pd_ctx* c) {
   c->stats.factor_seconds = c->factor_seconds;
   c->stats.factor_nnz = nnz;
   c->stats.n_free = nf;
+  c->stats.solve_mode = smode;
+  c->stats.solve_levels = slev;
+  c->stats.nnz_L = nnzL;
   B.devs_dirty = true;
   B.team_dirty[0] = B.team_dirty[1] = true;
   return PD_OK;

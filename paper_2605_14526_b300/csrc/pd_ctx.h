@@ -38,6 +38,12 @@ struct pd_ctx {
   pdf::Factor fac;
   int64_t nnz_S = 0;
   double factor_seconds = 0;
+  // solve mode chosen by pd_factor: T (level-scheduled partitioned-inverse
+  // triangular solves) or S (products with the inverse factor)
+  bool tmode = false;
+  int64_t solve_nnz = 0;        // stored entries the solve streams per sweep (S: nnz(S); T: one copy)
+  int solve_levels = 0;         // mode T: heights of the separator tree
+  double tsolve_seconds = 0;    // mode T: host time of the partitioned inverse
   // device
   int device = 0;
   Dev d{};

@@ -25,6 +25,7 @@ constexpr int kBwdMinBlocks = 2;
 constexpr int kRedRows = 2048;   // rows of the reduction scratch (>= any grid used)
 constexpr int kRedRep = 4;       // copies of each block's partials in the team reductions
 constexpr int kRedTeam = 16;     // values per row in the team reductions (>= 2 kMaxAA)
+constexpr int kTBlock = 256;     // threads per block, per-height kernels of solve mode T
 
 // Device-resident control word of the iteration (one per context).
 struct Ctrl {
@@ -144,6 +145,30 @@ struct Dev {
   const int64_t* st_ptr;   // S^T CSR (rows = positions)
   const int* st_idx;
   const float2* st_hl;
+  // solve mode T (tsolve.h, pd_tsolve.cuh): A^-1 by the two level-scheduled
+  // sweeps over the partitioned inverse of the factor instead of S^T S (the
+  // products run in FP64: sfp64 = 1, b and y as doubles)
+  int tmode;               // 1: mode T
+  int t_nlev;              // heights of the node tree
+  const int* t_c0;         // [nodes] first column (elimination position)
+  const int* t_nc;         // [nodes] columns
+  const int* t_nb;         // [nodes] rows below the node
+  const int64_t* t_boff;   // [nodes + 1] offset of a node's below rows / U rows
+  const int* t_below;      // below rows (positions)
+  const int64_t* t_poff;   // [nodes + 1] offset of a node's [Linv; M] entries
+  const double* t_prow;    // [Linv; M] row-major packed
+  const double* t_pcol;    // [Linv; M] column-major packed
+  const int64_t* t_goff;   // [nodes + 1] offset of a node's positions in t_gptr
+  const int* t_gptr;       // gather lists per (node, position) into t_gsrc
+  const int* t_gsrc;       // U rows of the children
+  const int* t_lev_f;      // [heights + 1] forward block units per height
+  const int* t_lev_b;      // [heights + 1] backward block units per height
+  const int* t_lev_w;      // [heights + 1] warp nodes per height
+  const int4* t_unit_f;    // {node, first row, rows, 0}
+  const int4* t_unit_b;    // {node, first column, columns, 0}
+  const int* t_wnode;      // nodes of at most 32 columns
+  double* t_U;             // [sum nb][3] updates passed up the node tree
+  double* t_x;             // [n_f][3] result of the backward sweep (elimination order)
 
   // work vectors [n_v][3] unless noted
   double* q;        // current iterate q^k

@@ -16,6 +16,7 @@
 
 #include "pd_launch.h"
 #include "pd_phases.cuh"
+#include "pd_tsolve.cuh"
 
 namespace pdk {
 
@@ -65,6 +66,33 @@ __global__ void __launch_bounds__(32 * kWarpsSpmv) k_spmv_st(Dev d, const float2
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int j = warp; j < d.n_f; j += nwarps) spmv_st_row(d, y, out, j, lane);
+}
+
+// solve mode T, one height of a sweep per launch (the kernel boundary is the
+// barrier between heights); the backward writes its finished rows to out in
+// vertex order
+struct TFinOut {
+  const int* perm;
+  double* out;
+  __device__ __forceinline__ void operator()(int j, double a0, double a1, double a2) const {
+    const int lane = threadIdx.x & 31;
+    if (lane < 3) out[3 * (size_t)perm[j] + lane] = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
+  }
+};
+
+__global__ void __launch_bounds__(kTBlock) k_tsweep_fwd(Dev d, const double* b, double* y, int h, int check_done) {
+  if (check_done == 1 && d.ctrl->done) return;
+  if (check_done == 2 && d.ctrl->adj_done) return;
+  tsweep_fwd(d, b, y, h, blockIdx.x, gridDim.x, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+             (gridDim.x * blockDim.x) >> 5);
+}
+
+__global__ void __launch_bounds__(kTBlock) k_tsweep_bwd(Dev d, const double* y, double* out, int h, int check_done) {
+  if (check_done == 1 && d.ctrl->done) return;
+  if (check_done == 2 && d.ctrl->adj_done) return;
+  TFinOut fin{d.perm, out};
+  tsweep_bwd(d, y, h, blockIdx.x, gridDim.x, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+             (gridDim.x * blockDim.x) >> 5, fin);
 }
 
 __global__ void __launch_bounds__(kVtxBlock) k_aa(Dev d) {
@@ -149,8 +177,22 @@ int spmvt_blocks(const Dev& d) {
   return b < 1 ? 1 : (b > 4096 ? 4096 : b);
 }
 
+int tsweep_blocks(const Dev& d) {
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return 2 * sms;
+}
+
 void launch_apply_inverse(const Dev& d, cudaStream_t s, const float2* xperm, float2* y, float2* part, int* cnt,
                           double* out, int check) {
+  if (d.tmode) {
+    const int g = tsweep_blocks(d);
+    const double* b = reinterpret_cast<const double*>(xperm);
+    double* yy = reinterpret_cast<double*>(y);
+    for (int h = 0; h < d.t_nlev; ++h) k_tsweep_fwd<<<g, kTBlock, 0, s>>>(d, b, yy, h, check);
+    for (int h = d.t_nlev - 1; h >= 0; --h) k_tsweep_bwd<<<g, kTBlock, 0, s>>>(d, yy, out, h, check);
+    return;
+  }
   k_spmv_s<<<spmv_blocks(d), 32 * kWarpsSpmv, 0, s>>>(d, xperm, y, part, cnt, check);
   k_spmv_st<<<spmvt_blocks(d), 32 * kWarpsSpmv, 0, s>>>(d, y, out, check);
 }

@@ -59,6 +59,11 @@ extern "C" int pd_solve_noalloc(pd_ctx* ctx, const double* b, double* x, void* s
     pd_internal_set_error(ctx, "pd_solve_noalloc is single-instance only");
     return PD_ERR_ARG;
   }
+  if (d->tmode) {
+    pd_internal_set_error(ctx, "pd_solve_noalloc applies the inverse factor S; this context factored for solve "
+                               "mode T (use pd_solve, or solve_mode = PD_SOLVE_S)");
+    return PD_ERR_ARG;
+  }
   if (d->n_f > kNoAllocMaxFree) {
     pd_internal_set_error(ctx, "pd_solve_noalloc: the mesh has more free vertices than the fixed scratch holds "
                                "(limit PD_NOALLOC_MAX_FREE = 65536); use pd_solve");

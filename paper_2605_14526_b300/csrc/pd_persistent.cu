@@ -18,6 +18,7 @@
 #include "pd_contact.cuh"
 #include "pd_launch.h"
 #include "pd_phases.cuh"
+#include "pd_tsolve.cuh"
 
 namespace pdk {
 
@@ -43,6 +44,23 @@ __device__ __forceinline__ void assemble_any(const Dev& d, int v, int k, double*
     assemble_warp<T>(d, v, k, part, lane);
   }
 }
+
+// mode T: each finished row j of q_hat (elimination order) goes to q_hat and
+// to the Anderson work of its vertex (lanes 0..2, partials in shared memory)
+struct FinAA {
+  const Dev* d;
+  AAView av;
+  double* pa;
+  __device__ __forceinline__ void operator()(int j, double a0, double a1, double a2) const {
+    const int lane = threadIdx.x & 31;
+    if (lane < 3) {
+      const size_t o = 3 * (size_t)d->perm[j] + lane;
+      const double qh = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
+      d->qhat[o] = qh;
+      aa_component(*d, o, qh, av, pa);
+    }
+  }
+};
 
 // the network warm start as a real call: it runs once per step and, inlined,
 // its registers would count against every phase of the body
@@ -146,64 +164,79 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
         __syncthreads();
         mark(PH_ASSEMBLE);
         if (S.done) break;
-        for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, d.s_part, d.s_cnt, sg, lane);
-        work_done(PH_SPMV_S);
-        if (!(ok = grid_sync(d, tm))) break;
-        mark(PH_SPMV_S);
-        if (d.n_con > 0) {
-          // contact: q_u at the candidates, normal LCP, Tresca friction, then
-          // y <- y + S J^T lam so that the S^T pass below gives A^-1 (b + J^T lam)
-          for (int c = gwarp; c < d.n_con; c += nwarps) contact_gather(d, c, t, lane);
-          if (!(ok = grid_sync(d, tm))) break;
-          if (tid == 0) fista_reset(d, &S);
-          __syncthreads();
-          const Range rk = block_range(tm, d.n_con);
-          while (!S.f_done) {
-            const int rot = S.rot_n;
-            const double beta = S.f_beta;
-            for (int c = rk.lo + tid; c < rk.hi; c += blockDim.x) normal_z_item(d, c, rot, beta);
-            if (!(ok = grid_sync(d, tm))) break;
-            double pc[3] = {0.0, 0.0, 0.0};
-            for (int c = gwarp; c < d.n_con; c += nwarps) normal_row(d, c, rot, lane, pc);
-            if (!(ok = grid_reduce<3>(d, tm, pc, sums))) break;
-            if (tid == 0) fista_finish(d, &S, &S.rot_n, sums);
-            __syncthreads();
-          }
-          if (!ok) break;
-          const double* lam_n = con_lamn(d, S.rot_n + 1);
-          if (tid == 0) fista_reset(d, &S);
-          __syncthreads();
-          while (!S.f_done) {
-            const int rot = S.rot_f;
-            const double beta = S.f_beta;
-            for (int c = rk.lo + tid; c < rk.hi; c += blockDim.x) friction_z_item(d, c, rot, beta);
-            if (!(ok = grid_sync(d, tm))) break;
-            double pc[3] = {0.0, 0.0, 0.0};
-            for (int c = gwarp; c < d.n_con; c += nwarps) friction_row(d, c, rot, lam_n, lane, pc);
-            if (!(ok = grid_reduce<3>(d, tm, pc, sums))) break;
-            if (tid == 0) fista_finish(d, &S, &S.rot_f, sums);
-            __syncthreads();
-          }
-          if (!ok) break;
-          const double* lam_f = con_lamf(d, S.rot_f + 1);
-          for (int i = gwarp; i < d.n_f; i += nwarps) contact_y_row(d, i, lam_n, lam_f, lane);
-          if (!(ok = grid_sync(d, tm))) break;
-        }
-        // S^T y row by row, with the Anderson work of that row's vertex fused in
-        // the Anderson partials of lanes 0..2 accumulate in shared memory (in
-        // registers they would stay live across the S^T loop)
+        // Anderson view and per-warp partials of lanes 0..2 (the Anderson work of
+        // every finished row of q_hat is fused into the solve)
         const AAView av = aa_view(d, S.pairs, S.ncols, S.head);
         double* pa = &s_pa[tid >> 5][lane < 3 ? lane : 0][0];
-        if (lane < 3)
-          for (int j = 0; j < 2 * kMaxAA; ++j) pa[j] = 0.0;
-        for (int j = gwarp; j < d.n_f; j += nwarps) {
-          double a0, a1, a2;
-          spmv_st_sum(d, d.y, j, lane, a0, a1, a2);
-          if (lane < 3) {
-            const size_t o = 3 * (size_t)d.perm[j] + lane;
-            const double qh = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
-            d.qhat[o] = qh;
-            aa_component(d, o, qh, av, pa);
+        if (d.tmode) {
+          // mode T: the two level-scheduled sweeps over the factor's
+          // partitioned inverse; each finished row of q_hat goes to the
+          // Anderson work as it is written
+          if (lane < 3)
+            for (int j = 0; j < 2 * kMaxAA; ++j) pa[j] = 0.0;
+          FinAA fin{&d, av, pa};
+          if (!(ok = tsolve_team(d, reinterpret_cast<const double*>(d.bperm), reinterpret_cast<double*>(d.y), tm,
+                                 gwarp, nwarps, fin)))
+            break;
+          mark(PH_SPMV_S);
+        } else {
+          for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, d.s_part, d.s_cnt, sg, lane);
+          work_done(PH_SPMV_S);
+          if (!(ok = grid_sync(d, tm))) break;
+          mark(PH_SPMV_S);
+          if (d.n_con > 0) {
+            // contact: q_u at the candidates, normal LCP, Tresca friction, then
+            // y <- y + S J^T lam so that the S^T pass below gives A^-1 (b + J^T lam)
+            for (int c = gwarp; c < d.n_con; c += nwarps) contact_gather(d, c, t, lane);
+            if (!(ok = grid_sync(d, tm))) break;
+            if (tid == 0) fista_reset(d, &S);
+            __syncthreads();
+            const Range rk = block_range(tm, d.n_con);
+            while (!S.f_done) {
+              const int rot = S.rot_n;
+              const double beta = S.f_beta;
+              for (int c = rk.lo + tid; c < rk.hi; c += blockDim.x) normal_z_item(d, c, rot, beta);
+              if (!(ok = grid_sync(d, tm))) break;
+              double pc[3] = {0.0, 0.0, 0.0};
+              for (int c = gwarp; c < d.n_con; c += nwarps) normal_row(d, c, rot, lane, pc);
+              if (!(ok = grid_reduce<3>(d, tm, pc, sums))) break;
+              if (tid == 0) fista_finish(d, &S, &S.rot_n, sums);
+              __syncthreads();
+            }
+            if (!ok) break;
+            const double* lam_n = con_lamn(d, S.rot_n + 1);
+            if (tid == 0) fista_reset(d, &S);
+            __syncthreads();
+            while (!S.f_done) {
+              const int rot = S.rot_f;
+              const double beta = S.f_beta;
+              for (int c = rk.lo + tid; c < rk.hi; c += blockDim.x) friction_z_item(d, c, rot, beta);
+              if (!(ok = grid_sync(d, tm))) break;
+              double pc[3] = {0.0, 0.0, 0.0};
+              for (int c = gwarp; c < d.n_con; c += nwarps) friction_row(d, c, rot, lam_n, lane, pc);
+              if (!(ok = grid_reduce<3>(d, tm, pc, sums))) break;
+              if (tid == 0) fista_finish(d, &S, &S.rot_f, sums);
+              __syncthreads();
+            }
+            if (!ok) break;
+            const double* lam_f = con_lamf(d, S.rot_f + 1);
+            for (int i = gwarp; i < d.n_f; i += nwarps) contact_y_row(d, i, lam_n, lam_f, lane);
+            if (!(ok = grid_sync(d, tm))) break;
+          }
+          // S^T y row by row, with the Anderson work of that row's vertex fused in
+          // the Anderson partials of lanes 0..2 accumulate in shared memory (in
+          // registers they would stay live across the S^T loop)
+          if (lane < 3)
+            for (int j = 0; j < 2 * kMaxAA; ++j) pa[j] = 0.0;
+          for (int j = gwarp; j < d.n_f; j += nwarps) {
+            double a0, a1, a2;
+            spmv_st_sum(d, d.y, j, lane, a0, a1, a2);
+            if (lane < 3) {
+              const size_t o = 3 * (size_t)d.perm[j] + lane;
+              const double qh = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
+              d.qhat[o] = qh;
+              aa_component(d, o, qh, av, pa);
+            }
           }
         }
         work_done(PH_AA);

@@ -46,6 +46,7 @@ class SolverSettings:
     adj_tol: float = 1e-10
     adj_max_iters: int = 500
     solve_fp64: bool = False     # S products in FP64 instead of double-float
+    solve_mode: int = 0          # A^-1 by: 0 auto, 1 products with S, 2 level-scheduled solves with L
 
 
 @dataclass

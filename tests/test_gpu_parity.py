@@ -248,7 +248,7 @@ def test_pd_step_one_step_and_its_adjoint():
     single pd_step is the oracle's one-step adjoint (Alg. 2): dq_t, dv_t, dE,
     dnu and df_ext of that step."""
     build()
-    sc = inputs.tiny_block(n=3, steps=2)
+    sc = inputs.tiny_block(n=3, steps=2, cell=0.1)
     pd = binding.PDContext(sc)
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda:0")
     q1, v1, q2, v2 = (torch.empty((sc.n_v, 3), dtype=torch.float64, device="cuda:0") for _ in range(4))
