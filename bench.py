@@ -15,6 +15,7 @@ rollouts (the bar's working set fits in L2).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
   python bench.py --workload batch    # 64 uneven meshes x 100 steps in one launch
+  python bench.py --workload block    # 64^3-cell block (1.31M tets), solve mode T, local step alone
 
 The batch workload (not the default line) times the batched persistent launch:
 64 seeded box/ellipsoid meshes of 1k-40k tets (about 0.58M tets in total) with
@@ -414,6 +415,158 @@ def run_contact(args, rank, world, local_rank, dev, dist):
         print(json.dumps(line))
 
 
+BLOCK_WORKLOAD = ("large heterogeneous Neo-Hookean block {n}^3 cells ({ne:,} tets, {nv:,} vertices), 8^3-cell blocks "
+                  "of 1e4 / 1e6 Pa, bottom pinned, seeded top loads, {T} steps fwd+bwd")
+
+
+def run_block(args, rank, world, local_rank, dev, dist):
+    """Large-block workload: the 64^3-cell block (1.31M tets) whose inverse
+    factor is too dense to store, so every A^-1 runs as the level-scheduled
+    triangular solves with the factor (solve mode T, FP64); plus the local
+    step alone, timed over repeated launches, against the HBM peak."""
+    import torch
+    from paper_2605_14526_b300 import binding, inputs
+
+    n = args.block_n
+    sc = inputs.large_block(n=n, steps=args.block_steps, seed=5 + rank)
+    T = sc.steps
+    opts = binding.options_for(sc.solver)
+    t0 = time.perf_counter()
+    pd = binding.PDContext(sc, opts)
+    setup_s = time.perf_counter() - t0
+    st0 = binding.pd_get_stats(pd.ctx)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    x0, v0, f = t(sc.x0), t(sc.v0), t(sc.f_ext)
+    stride = 3 * sc.n_v
+    target = t(sc.target)
+    qT, vT = torch.empty_like(x0), torch.empty_like(x0)
+    dq0, dv0 = torch.empty_like(x0), torch.empty_like(x0)
+    dE = torch.empty(sc.n_e, dtype=torch.float64, device=dev)
+    dnu = torch.empty(1, dtype=torch.float64, device=dev)
+    zero = torch.zeros_like(x0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def fwd_bwd(timed=False):
+        if timed:
+            ev[0].record(stream)
+        binding.pd_rollout(pd.ctx, T, x0, v0, f, stride, qT, vT, stream)
+        if timed:
+            ev[1].record(stream)
+        binding.pd_backward(pd.ctx, qT - target, zero, dq0, dv0, dE, dnu, None, 0, stream)
+        if timed:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        fwd_bwd()
+    torch.cuda.synchronize()
+    launches0 = binding.pd_get_stats(pd.ctx).launches
+    total_ms = fwd_ms = bwd_ms = 0.0
+    iters = adj = esc = 0
+    with ClockSampler(local_rank) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            fwd_bwd(timed=True)
+            torch.cuda.synchronize()
+            fwd_ms += ev[0].elapsed_time(ev[1])
+            bwd_ms += ev[1].elapsed_time(ev[2])
+            total_ms += ev[0].elapsed_time(ev[2])
+            st = binding.pd_get_stats(pd.ctx)
+            iters += st.iters_total
+            adj += st.adj_iters_total
+            esc += st.escalations
+    launches = binding.pd_get_stats(pd.ctx).launches - launches0
+    tmax = max_over_ranks(total_ms, dist, dev)
+    value = world * T * args.steps / (tmax / 1e3)
+    peak, peak_kind = _peaks()
+    st = binding.pd_get_stats(pd.ctx)
+    m = pd.options.aa_m
+    tmode = st.solve_mode == binding.PD_SOLVE_T
+    # algorithmic bytes per iteration: local step 56 B/element + 48 B/vertex;
+    # solve 16 B per stored entry in mode T (the row-major copy in the forward
+    # sweep, the column-major copy in the backward) or 20 B per non-zero of S;
+    # 96 B per free vertex of work vectors; Anderson (2m + 3) x 24 B/vertex
+    solve_b = (16 if tmode else 20) * st.factor_nnz
+    fwd_iter_bytes = 56 * sc.n_e + 48 * sc.n_v + solve_b + 96 * st.n_free + (2 * m + 3) * 24 * sc.n_v
+    bwd_iter_bytes = 200 * sc.n_e + solve_b + 240 * sc.n_v
+    fwd_launch_ms, bwd_launch_ms = fwd_ms / args.steps, bwd_ms / args.steps
+    fwd_bytes = fwd_iter_bytes * iters / args.steps
+    bwd_bytes = bwd_iter_bytes * adj / args.steps
+    if fwd_launch_ms >= bwd_launch_ms:
+        kname, kbytes, kms, kit = "k_fwd_rollout (persistent forward rollout)", fwd_bytes, fwd_launch_ms, iters
+    else:
+        kname, kbytes, kms, kit = "k_bwd_rollout (persistent adjoint)", bwd_bytes, bwd_launch_ms, adj
+    achieved = kbytes / (kms * 1e-3) / 1e9
+    # FP64 work of the solves: 3 right-hand sides x 2 flops per stored entry per sweep, 2 sweeps
+    fp64_flops = (12.0 * st.factor_nnz) * kit / args.steps
+    # the local step alone: repeated launches at the final state, CUDA events
+    # on the launching stream (inputs 1.3M elements: far above L2)
+    out = torch.empty_like(x0)
+    for _ in range(3):
+        binding.pd_local_rhs(pd.ctx, qT, out, stream)
+    nrep = 20
+    le = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    le[0].record(stream)
+    for _ in range(nrep):
+        binding.pd_local_rhs(pd.ctx, qT, out, stream)
+    le[1].record(stream)
+    torch.cuda.synchronize()
+    local_ms = le[0].elapsed_time(le[1]) / nrep
+    # local step algorithmic bytes (the minimum the operation must move): per
+    # element its corner indices 16, Dm^-1 36 (FP32) and w_e V_e 4 B; per
+    # vertex q read 24 B and the right-hand side written 24 B. (The
+    # implementation also writes and re-reads the 12 corner forces and the
+    # prox stretches; those are not counted.)
+    local_bytes = 56 * sc.n_e + 48 * sc.n_v
+    local_gbs = local_bytes / (local_ms * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64 (FP32 local step; FP64 RHS, factor, triangular solves, Anderson, adjoint)",
+            "data": "synthetic",
+            "config": {"workload": BLOCK_WORKLOAD.format(n=n, ne=sc.n_e, nv=sc.n_v, T=T), "pd_steps_per_bench_step": T,
+                       "l2": "flushed (256 MB write) between rollouts; the solve streams "
+                             f"{solve_b / 1e9:.2f} GB per iteration, far above L2",
+                       "gate": f"b-change {pd.options.eps_res:g}, q-step {pd.options.eps_step:g} (relative)",
+                       "solve": {"mode": "T (level-scheduled triangular solves with the factor)" if tmode else "S",
+                                 "levels": int(st.solve_levels), "stored_entries": int(st.factor_nnz),
+                                 "nnz_L": int(st.nnz_L), "setup_s": setup_s,
+                                 "factor_s": float(st0.factor_seconds)},
+                       "mean_fwd_iters_per_pd_step": iters / (args.steps * T),
+                       "mean_adjoint_iters_per_pd_step": adj / (args.steps * T),
+                       "fp64_escalations_per_rollout": esc / args.steps,
+                       "fwd_ms_per_pd_step": fwd_ms / (args.steps * T), "bwd_ms_per_pd_step": bwd_ms / (args.steps * T),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "e2e": None,
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": kname, "peak_kind": peak_kind, "avg_launch_ms": kms,
+                         "bytes_per_launch": kbytes, "fwd_launch_ms": fwd_launch_ms, "bwd_launch_ms": bwd_launch_ms,
+                         "fwd_iter_bytes": fwd_iter_bytes, "bwd_iter_bytes": bwd_iter_bytes,
+                         "fp64_solve_tflops": fp64_flops / (kms * 1e-3) / 1e12,
+                         "fp64_note": "solve FP64 flops of the dominant launch over its time; nominal B300 FP64 "
+                                      "rate 1.25 TFLOP/s"},
+            "local_step": {"achieved": local_gbs, "peak": peak, "unit": "GB/s", "frac": local_gbs / peak,
+                           "bytes_per_launch": local_bytes, "avg_ms": local_ms, "launches_timed": nrep,
+                           "kernels": "k_local_all + k_rhs_out (pd_local_rhs)", "peak_kind": peak_kind},
+            "clocks": clk.summary()}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        small = inputs.large_block(n=12, steps=1, seed=5)
+        dt, k = oracle_sample(small, 1)
+        line["cpu_baseline"] = {"value": k / dt * small.n_e / sc.n_e, "unit": UNIT, "cores": 1,
+                                "host_cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"one PD step of a 12^3-cell block ({small.n_e} tets), forward + adjoint, "
+                                          "FP64, 1 thread, scaled by element count to the workload (the oracle's "
+                                          "sparse LU of the full block does not fit a bounded sample)"}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -421,7 +574,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="bar", choices=["bar", "batch", "contact"])
+    ap.add_argument("--workload", default="bar", choices=["bar", "batch", "contact", "block"])
+    ap.add_argument("--block-n", type=int, default=64, help="block workload: cells per edge")
+    ap.add_argument("--block-steps", type=int, default=10, help="block workload: PD steps per rollout")
     ap.add_argument("--contact-steps", type=int, default=20,
                     help="contact workload: PD steps of the 300-step rollout timed per benchmark step")
     args = ap.parse_args()
@@ -446,6 +601,11 @@ def main():
     dev = torch.device("cuda", local_rank)
     if args.workload == "contact":
         run_contact(args, rank, world, local_rank, dev, dist)
+        if dist:
+            dist.destroy_process_group()
+        return
+    if args.workload == "block":
+        run_block(args, rank, world, local_rank, dev, dist)
         if dist:
             dist.destroy_process_group()
         return

@@ -279,12 +279,27 @@ int pd_backward(pd_ctx* ctx, const double* dqT, const double* dvT, double* dq0, 
                 double* dE, double* dnu, double* df_ext, int64_t df_stride, void* stream);
 
 /* x = A^-1 b on the free DoFs with the factored operator of the context,
- * evaluated as two sparse products x = S^T (S b) (Sec. 4.5 eq. two_spmv).
- * b, x: [n_v][3] device pointers (caller-owned); rows of pinned vertices of
- * b are ignored and those of x are set to 0. Uses the context's work
- * buffers, so it must not overlap a pd_rollout / pd_backward of the same
+ * in the context's solve mode: two sparse products x = S^T (S b) (Sec. 4.5
+ * eq. two_spmv), or in mode T the level-scheduled forward and backward
+ * triangular solves with the factor (one launch per separator-tree height
+ * and sweep). b, x: [n_v][3] device pointers (caller-owned); rows of pinned
+ * vertices of b are ignored and those of x are set to 0. Uses the context's
+ * work buffers, so it must not overlap a pd_rollout / pd_backward of the same
  * context on another stream. Enqueued on the stream; does not synchronise. */
 int pd_solve(pd_ctx* ctx, const double* b, double* x, void* stream);
+
+/* The local step alone (Sec. 4.1, Alg. 1 local step and RHS scatter): for
+ * positions q, every element's projection p_e* (corotated: the polar factor
+ * U V^T of F_e = G_e q; Neo-Hookean: the stretch prox of eq. nh_prox /
+ * nh_prox_normal at k_bar), and the projection part of the right-hand side
+ *   out[v] = sum_e w_e V_e G_e^T vec(p_e*)   (eq. A_basic),
+ * summed per vertex in FP64 in a fixed order; rows of pinned vertices are
+ * set to 0. The context's local precision (options.local_fp32) applies; the
+ * Neo-Hookean prox starts from each element's last stretches. q, out:
+ * [n_v][3] device pointers. After pd_factor (materials and weights);
+ * single-instance contexts. Enqueued on the stream (two launches); does not
+ * synchronise; must not overlap the context's rollouts. */
+int pd_local_rhs(pd_ctx* ctx, const double* q, double* out, void* stream);
 
 /* Same result as pd_solve, for callers that cannot allocate device memory
  * while they run (code under stream capture or in a real-time loop, hosts

@@ -103,6 +103,7 @@ def lib():
             "pd_get_checkpoint": (c_int, [P, c_int32, P]),
             "pd_get_stats": (c_int, [P, P]),
             "pd_solve": (c_int, [P, P, P, P]),
+            "pd_local_rhs": (c_int, [P, P, P, P]),
             "pd_solve_noalloc": (c_int, [P, P, P, P]),
             "pd_profile": (c_int, [P, c_int32]),
             "pd_get_profile": (c_int, [P, P]),
@@ -240,6 +241,10 @@ def pd_backward(ctx, dqT, dvT, dq0, dv0, dE, dnu, df_ext, df_stride, stream=None
 
 def pd_solve(ctx, b, x, stream=None):
     _check(ctx, lib().pd_solve(ctx, _ptr(b), _ptr(x), _stream(stream)))
+
+
+def pd_local_rhs(ctx, q, out, stream=None):
+    _check(ctx, lib().pd_local_rhs(ctx, _ptr(q), _ptr(out), _stream(stream)))
 
 
 def pd_solve_noalloc(ctx, b, x, stream=None):

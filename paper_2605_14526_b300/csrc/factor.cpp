@@ -256,59 +256,97 @@ int64_t numeric(Factor& f, const SymCSR& A) {
       }
     }
   }
-  std::fill(map.begin(), map.end(), -1);
-  std::vector<double> C;
+#ifdef _OPENMP
+  const int nth = omp_get_max_threads();
+#else
+  const int nth = 1;
+#endif
+  std::vector<std::vector<double>> Cbuf(nth);
+  std::vector<std::vector<int>> maps(nth, std::vector<int>(n, -1));
+  std::vector<int> grp;
   for (int s = 0; s < ns; ++s) {
     const int c0 = f.sup_start[s];
     const int nc = f.sup_start[s + 1] - c0;
     const int64_t nr = f.rowptr[s + 1] - f.rowptr[s];
     double* B = &f.val[f.valptr[s]];
-    // dense Cholesky of the nr x nc panel (left-looking over its columns)
+    // dense Cholesky of the nr x nc panel (left-looking over its columns;
+    // the rows of a tall panel are split over threads)
+    const bool par_panel = (double)nr * nc * nc > 4e6;
     for (int j = 0; j < nc; ++j) {
       double* cj = B + (int64_t)j * nr;
-      for (int k = 0; k < j; ++k) {
-        const double* ck = B + (int64_t)k * nr;
-        const double a = ck[j];
-        for (int64_t i = j; i < nr; ++i) cj[i] -= ck[i] * a;
-      }
+      // the diagonal entry first (it needs only rows j of earlier columns)
+      for (int k = 0; k < j; ++k) cj[j] -= B[(int64_t)k * nr + j] * B[(int64_t)k * nr + j];
       const double d = cj[j];
       if (!(d > 0.0) || !std::isfinite(d)) return 1 + c0 + j;
       const double r = std::sqrt(d);
       cj[j] = r;
       const double inv = 1.0 / r;
-      for (int64_t i = j + 1; i < nr; ++i) cj[i] *= inv;
+      const int64_t rows = nr - j - 1;
+      constexpr int64_t kChunk = 256;
+      const int64_t nchunk = (rows + kChunk - 1) / kChunk;
+#pragma omp parallel for schedule(static) if (par_panel && nchunk > 1)
+      for (int64_t ch = 0; ch < nchunk; ++ch) {
+        const int64_t i0 = j + 1 + ch * kChunk, i1 = std::min<int64_t>(nr, i0 + kChunk);
+        for (int k = 0; k < j; ++k) {
+          const double* ck = B + (int64_t)k * nr;
+          const double a = ck[j];
+          for (int64_t i = i0; i < i1; ++i) cj[i] -= ck[i] * a;
+        }
+        for (int64_t i = i0; i < i1; ++i) cj[i] *= inv;
+      }
     }
-    // push the Schur update of the below rows onto the ancestor supernodes
+    // push the Schur update of the below rows onto the ancestor supernodes:
+    // one group of rows per ancestor supernode K; the groups write disjoint
+    // columns (those of K), so they run in parallel, each thread with its own
+    // product buffer and row map
     const int nb = (int)(nr - nc);
     if (nb <= 0) continue;
     const int* R = &f.rows[f.rowptr[s] + nc];
-    int a0 = 0;
-    while (a0 < nb) {
+    grp.clear();
+    for (int a0 = 0; a0 < nb;) {
       const int K = f.col2sup[R[a0]];
       int a1 = a0;
       while (a1 < nb && f.col2sup[R[a1]] == K) ++a1;
-      const int g = a1 - a0;
-      const int64_t h = nb - a0;  // rows a0..nb-1
-      C.assign((size_t)h * g, 0.0);
-      // C[r, c] = sum_k B[nc+a0+r, k] * B[nc+a0+c, k]
-      for (int c = 0; c < g; ++c) {
-        double* Cc = &C[(size_t)c * h];
-        for (int k = 0; k < nc; ++k) {
-          const double* bk = B + (int64_t)k * nr + nc + a0;
-          const double coef = bk[c];
-          if (coef == 0.0) continue;
-          for (int64_t r = c; r < h; ++r) Cc[r] += bk[r] * coef;
+      grp.push_back(a0);
+      a0 = a1;
+    }
+    grp.push_back(nb);
+    const int ng = (int)grp.size() - 1;
+#pragma omp parallel if ((double)nb * nb * nc > 2e6 && ng > 1)
+    {
+#ifdef _OPENMP
+      const int th = omp_get_thread_num();
+#else
+      const int th = 0;
+#endif
+      std::vector<double>& C = Cbuf[th];
+      std::vector<int>& map = maps[th];
+#pragma omp for schedule(dynamic, 1)
+      for (int gi = 0; gi < ng; ++gi) {
+        const int a0 = grp[gi], a1 = grp[gi + 1];
+        const int K = f.col2sup[R[a0]];
+        const int g = a1 - a0;
+        const int64_t h = nb - a0;  // rows a0..nb-1
+        C.assign((size_t)h * g, 0.0);
+        // C[r, c] = sum_k B[nc+a0+r, k] * B[nc+a0+c, k]
+        for (int c = 0; c < g; ++c) {
+          double* Cc = &C[(size_t)c * h];
+          for (int k = 0; k < nc; ++k) {
+            const double* bk = B + (int64_t)k * nr + nc + a0;
+            const double coef = bk[c];
+            if (coef == 0.0) continue;
+            for (int64_t r = c; r < h; ++r) Cc[r] += bk[r] * coef;
+          }
+        }
+        const int64_t nrK = f.rowptr[K + 1] - f.rowptr[K];
+        for (int64_t r = 0; r < nrK; ++r) map[f.rows[f.rowptr[K] + r]] = (int)r;
+        double* BK = &f.val[f.valptr[K]];
+        for (int c = 0; c < g; ++c) {
+          double* colK = BK + (int64_t)(R[a0 + c] - f.sup_start[K]) * nrK;
+          const double* Cc = &C[(size_t)c * h];
+          for (int64_t r = c; r < h; ++r) colK[map[R[a0 + r]]] -= Cc[r];
         }
       }
-      const int64_t nrK = f.rowptr[K + 1] - f.rowptr[K];
-      for (int64_t r = 0; r < nrK; ++r) map[f.rows[f.rowptr[K] + r]] = (int)r;
-      double* BK = &f.val[f.valptr[K]];
-      for (int c = 0; c < g; ++c) {
-        double* colK = BK + (int64_t)(R[a0 + c] - f.sup_start[K]) * nrK;
-        const double* Cc = &C[(size_t)c * h];
-        for (int64_t r = c; r < h; ++r) colK[map[R[a0 + r]]] -= Cc[r];
-      }
-      a0 = a1;
     }
   }
   return 0;

@@ -1153,6 +1153,19 @@ int pd_solve(pd_ctx* c, const double* b, double* x, void* stream) {
   return PD_OK;
 }
 
+int pd_local_rhs(pd_ctx* c, const double* q, double* out, void* stream) {
+  if (!c) return PD_ERR_ARG;
+  if (c->batch) return fail(c, PD_ERR_ARG, "pd_local_rhs is single-instance only");
+  if (!c->factored) return fail(c, PD_ERR_NOT_FACTORED, "pd_factor must run before pd_local_rhs");
+  if (!q || !out) return fail(c, PD_ERR_ARG, "q and out are required");
+  if (!is_device_ptr(q) || !is_device_ptr(out)) return fail(c, PD_ERR_ARG, "q and out must be device pointers");
+  CK(cudaSetDevice(c->device));
+  pdk::launch_local_rhs(c->d, (cudaStream_t)stream, q, out);
+  c->launches += 2;
+  CK(cudaGetLastError());
+  return PD_OK;
+}
+
 int pd_profile(pd_ctx* c, int32_t enable) {
   if (!c) return PD_ERR_ARG;
   if (c->batch) return fail(c, PD_ERR_ARG, "pd_profile is single-instance only");

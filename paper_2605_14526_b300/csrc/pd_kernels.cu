@@ -34,6 +34,37 @@ __global__ void __launch_bounds__(kTetBlock) k_local(Dev d, const double* x) {
   if (e < d.n_e) local_item<T>(d, e, x);
 }
 
+// standalone local step (pd_local_rhs): every element, no iteration control
+template <typename T>
+__global__ void __launch_bounds__(kTetBlock) k_local_all(Dev d, const double* x) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < d.n_e) local_item<T>(d, e, x);
+}
+
+// the projection part of the right-hand side per vertex, sum_e w_e V_e G_e^T
+// vec(p_e), from the elements' corner forces: one warp per vertex in the
+// fixed order of the assembly (FP64); pinned rows get 0
+template <typename T>
+__global__ void __launch_bounds__(kVtxBlock) k_rhs_out(Dev d, double* out) {
+  const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (v >= d.n_v) return;
+  if (d.pinned[v]) {
+    if (lane < 3) out[3 * (size_t)v + lane] = 0.0;
+    return;
+  }
+  const T* cb = reinterpret_cast<const T*>(d.contrib);
+  double c[3] = {0.0, 0.0, 0.0};
+  for (int p = d.inc_ptr[v] + lane; p < d.inc_ptr[v + 1]; p += 32) {
+    const int ic = d.inc_idx[p];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) c[i] += (double)cb[3 * (size_t)ic + i];
+  }
+  int i;
+  const double sum = warp_sum_scatter<3>(c, lane, i);
+  if ((lane & 7) == 0 && i < 3) out[3 * (size_t)v + i] = sum;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kVtxBlock) k_assemble(Dev d) {
   if (d.ctrl->done) return;
@@ -195,6 +226,16 @@ void launch_apply_inverse(const Dev& d, cudaStream_t s, const float2* xperm, flo
   }
   k_spmv_s<<<spmv_blocks(d), 32 * kWarpsSpmv, 0, s>>>(d, xperm, y, part, cnt, check);
   k_spmv_st<<<spmvt_blocks(d), 32 * kWarpsSpmv, 0, s>>>(d, y, out, check);
+}
+
+void launch_local_rhs(const Dev& d, cudaStream_t s, const double* x, double* out) {
+  if (d.local_fp32) {
+    k_local_all<float><<<nblk(d.n_e, kTetBlock), kTetBlock, 0, s>>>(d, x);
+    k_rhs_out<float><<<nblk(32 * d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d, out);
+  } else {
+    k_local_all<double><<<nblk(d.n_e, kTetBlock), kTetBlock, 0, s>>>(d, x);
+    k_rhs_out<double><<<nblk(32 * d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d, out);
+  }
 }
 
 void launch_solve(const Dev& d, cudaStream_t s, const double* b, float2* xperm, float2* y, float2* part, int* cnt,

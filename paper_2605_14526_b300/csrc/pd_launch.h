@@ -19,6 +19,10 @@ void launch_step_end(const Dev& d, cudaStream_t s, double* qn, double* vn, doubl
 void launch_apply_inverse(const Dev& d, cudaStream_t s, const float2* xperm, float2* y, float2* part, int* cnt,
                           double* out, int check);
 
+// the local step of every element at positions x and the projection part of
+// the right-hand side, out[v] = sum_e w_e V_e G_e^T vec(p_e*) (two launches)
+void launch_local_rhs(const Dev& d, cudaStream_t s, const double* x, double* out);
+
 // x = A^-1 b for b, x in vertex order; xperm and y are [n_f][3] work buffers
 void launch_solve(const Dev& d, cudaStream_t s, const double* b, float2* xperm, float2* y, float2* part, int* cnt,
                   double* x);
