@@ -495,6 +495,14 @@ struct FinRZ {
       acc += d->r[o] * zv;
     }
   }
+  __device__ __forceinline__ void lanes(bool on, int j, double a0, double a1, double a2) {
+    if (!on) return;
+    const size_t o = 3 * (size_t)d->perm[j];
+    d->z[o] = a0;
+    d->z[o + 1] = a1;
+    d->z[o + 2] = a2;
+    acc += d->r[o] * a0 + d->r[o + 1] * a1 + d->r[o + 2] * a2;
+  }
 };
 
 template <typename T>

@@ -109,6 +109,13 @@ struct TFinOut {
     const int lane = threadIdx.x & 31;
     if (lane < 3) out[3 * (size_t)perm[j] + lane] = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
   }
+  __device__ __forceinline__ void lanes(bool on, int j, double a0, double a1, double a2) const {
+    if (!on) return;
+    double* o = out + 3 * (size_t)perm[j];
+    o[0] = a0;
+    o[1] = a1;
+    o[2] = a2;
+  }
 };
 
 __global__ void __launch_bounds__(kTBlock) k_tsweep_fwd(Dev d, const double* b, double* y, int h, int check_done) {

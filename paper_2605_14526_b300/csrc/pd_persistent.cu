@@ -50,7 +50,8 @@ __device__ __forceinline__ void assemble_any(const Dev& d, int v, int k, double*
 struct FinAA {
   const Dev* d;
   AAView av;
-  double* pa;
+  double* pa;    // this lane's partials (lanes 0..2)
+  double* pa0;   // the warp's lane-0 partials
   __device__ __forceinline__ void operator()(int j, double a0, double a1, double a2) const {
     const int lane = threadIdx.x & 31;
     if (lane < 3) {
@@ -58,6 +59,30 @@ struct FinAA {
       const double qh = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
       d->qhat[o] = qh;
       aa_component(*d, o, qh, av, pa);
+    }
+  }
+  // every lane with its own row: the three components each, then the warp's
+  // sum of the partials into lane 0's (a fixed shuffle tree)
+  __device__ __forceinline__ void lanes(bool on, int j, double a0, double a1, double a2) const {
+    double part[2 * kMaxAA];
+#pragma unroll
+    for (int i = 0; i < 2 * kMaxAA; ++i) part[i] = 0.0;
+    if (on) {
+      const size_t o = 3 * (size_t)d->perm[j];
+      d->qhat[o] = a0;
+      d->qhat[o + 1] = a1;
+      d->qhat[o + 2] = a2;
+      aa_component(*d, o, a0, av, part);
+      aa_component(*d, o + 1, a1, av, part);
+      aa_component(*d, o + 2, a2, av, part);
+    }
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < 2 * kMaxAA; ++i) {
+      double v = part[i];
+#pragma unroll
+      for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sh);
+      if (lane == 0) pa0[i] += v;
     }
   }
 };
@@ -174,7 +199,7 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
           // Anderson work as it is written
           if (lane < 3)
             for (int j = 0; j < 2 * kMaxAA; ++j) pa[j] = 0.0;
-          FinAA fin{&d, av, pa};
+          FinAA fin{&d, av, pa, &s_pa[tid >> 5][0][0]};
           if (!(ok = tsolve_team(d, reinterpret_cast<const double*>(d.bperm), reinterpret_cast<double*>(d.y), tm,
                                  gwarp, nwarps, fin)))
             break;

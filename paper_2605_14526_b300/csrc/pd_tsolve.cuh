@@ -27,8 +27,7 @@
 namespace pdk {
 
 constexpr int kTStage = 1024;      // entries of the shared staging vector (3 doubles each); = largest node
-constexpr int kTWarpCols = 32;     // nodes of at most this many columns are one warp's work
-constexpr int kTUnitCols = 8;      // columns of a backward work unit (one warp each)
+                                   // (the host's kNodeMaxCols and kStageRows)
 
 __device__ __forceinline__ int64_t t_rowoff(int nc, int o) {   // row o of the packed row-major copy
   return o < nc ? (int64_t)o * (o + 1) / 2 : (int64_t)nc * (nc + 1) / 2 + (int64_t)(o - nc) * nc;
@@ -144,7 +143,25 @@ static __device__ __noinline__ void tsweep_fwd(const Dev& d, const double* b, do
       const int o = o0 + lane;
       const bool valid = o < nc + nb;
       double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-      for (int k = 0; k < nc; ++k) {
+      int k = 0;
+      // four columns per pass (their loads in flight together); column k of
+      // the column-major copy starts at t_coloff(k) and holds rows k..
+      for (; k + 3 < nc; k += 4) {
+        double p[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          p[i] = (valid && o >= k + i) ? P[t_coloff(nc, nb, k + i) + (o - k - i)] : 0.0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const double x0 = __shfl_sync(0xffffffffu, r0, k + i);
+          const double x1 = __shfl_sync(0xffffffffu, r1, k + i);
+          const double x2 = __shfl_sync(0xffffffffu, r2, k + i);
+          a0 += p[i] * x0;
+          a1 += p[i] * x1;
+          a2 += p[i] * x2;
+        }
+      }
+      for (; k < nc; ++k) {
         const double x0 = __shfl_sync(0xffffffffu, r0, k);
         const double x1 = __shfl_sync(0xffffffffu, r1, k);
         const double x2 = __shfl_sync(0xffffffffu, r2, k);
@@ -173,46 +190,88 @@ static __device__ __noinline__ void tsweep_fwd(const Dev& d, const double* b, do
   }
 }
 
-// backward sweep, nodes of height h: y -> x (elimination order, t_x); each
-// finished row j is also handed to fin(j, x0, x1, x2), called by every lane
-// of a warp with the same values (lanes 0..2 typically consume component
-// lane)
+// backward sweep, nodes of height h: y -> x (elimination order, t_x). Each
+// finished row j is handed on: fin(j, x0, x1, x2) from a block-mode unit,
+// called by every lane of a warp with the same values (lanes 0..2 take
+// component lane); fin.lanes(on, j, x0, x1, x2) from a warp-mode node, called
+// by every lane at once, each lane with its own row (on: the lane has one).
 template <class Fin>
 __device__ __forceinline__ void tsweep_bwd(const Dev& d, const double* y, int h, int blk, int nblk, int gwarp, int nwarps,
                                            Fin& fin) {
   double* sz = t_stage();
   double* x = d.t_x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, bwarps = blockDim.x >> 5;
+  auto stage_z = [&](int c0, int nc, const int* bl, int r, double* dst) {
+    if (r < nc) {
+      const double* yr = y + 3 * (size_t)(c0 + r);
+      dst[0] = yr[0];
+      dst[1] = yr[1];
+      dst[2] = yr[2];
+    } else {
+      const double* xr = x + 3 * (size_t)bl[r - nc];
+      dst[0] = -xr[0];
+      dst[1] = -xr[1];
+      dst[2] = -xr[2];
+    }
+  };
   for (int u = d.t_lev_b[h] + blk; u < d.t_lev_b[h + 1]; u += nblk) {
     const int4 un = d.t_unit_b[u];
     const int s = un.x, k0 = un.y, ncols = un.z;
     const int c0 = d.t_c0[s], nc = d.t_nc[s], nb = d.t_nb[s];
     const int R = nc + nb;
+    const int* bl = d.t_below + d.t_boff[s];
+    const double* P = d.t_pcol + d.t_poff[s];
+    if (R <= kTStage) {
+      // the right-hand side [y_s; -x_below] staged once; warps take the
+      // unit's columns in turn
+      __syncthreads();
+      for (int r = threadIdx.x; r < R; r += blockDim.x) stage_z(c0, nc, bl, r, sz + 3 * r);
+      __syncthreads();
+      for (int kk = warp; kk < ncols; kk += bwarps) {
+        const int k = k0 + kk;
+        const double* pc = P + t_coloff(nc, nb, k) - k;   // pc[r]: row r of column k
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, e0 = 0.0, e1 = 0.0, e2 = 0.0;
+        int r = k + lane;
+        for (; r + 32 < R; r += 64) {
+          const double p = pc[r], q = pc[r + 32];
+          const double* zr = sz + 3 * r;
+          const double* zq = zr + 96;
+          a0 += p * zr[0];
+          a1 += p * zr[1];
+          a2 += p * zr[2];
+          e0 += q * zq[0];
+          e1 += q * zq[1];
+          e2 += q * zq[2];
+        }
+        if (r < R) {
+          const double p = pc[r];
+          const double* zr = sz + 3 * r;
+          a0 += p * zr[0];
+          a1 += p * zr[1];
+          a2 += p * zr[2];
+        }
+        a0 = t_warp_sum(a0 + e0);
+        a1 = t_warp_sum(a1 + e1);
+        a2 = t_warp_sum(a2 + e2);
+        if (lane == 0) {
+          double* xk = x + 3 * (size_t)(c0 + k);
+          xk[0] = a0;
+          xk[1] = a1;
+          xk[2] = a2;
+        }
+        fin(c0 + k, a0, a1, a2);
+      }
+      continue;
+    }
+    // a long right-hand side: staged in chunks, one column per warp
     const int k = k0 + warp;
     const bool mine = warp < ncols;
-    const double* pc = d.t_pcol + d.t_poff[s] + (mine ? t_coloff(nc, nb, k) - k : 0);   // pc[r]: row r of column k
-    const int* bl = d.t_below + d.t_boff[s];
+    const double* pc = P + (mine ? t_coloff(nc, nb, k) - k : 0);
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
     for (int z0 = 0; z0 < R; z0 += kTStage) {
       const int z1 = min(R, z0 + kTStage);
       __syncthreads();
-      for (int r = z0 + (int)threadIdx.x; r < z1; r += blockDim.x) {
-        double v0, v1, v2;
-        if (r < nc) {
-          const double* yr = y + 3 * (size_t)(c0 + r);
-          v0 = yr[0];
-          v1 = yr[1];
-          v2 = yr[2];
-        } else {
-          const double* xr = x + 3 * (size_t)bl[r - nc];
-          v0 = -xr[0];
-          v1 = -xr[1];
-          v2 = -xr[2];
-        }
-        sz[3 * (r - z0)] = v0;
-        sz[3 * (r - z0) + 1] = v1;
-        sz[3 * (r - z0) + 2] = v2;
-      }
+      for (int r = z0 + (int)threadIdx.x; r < z1; r += blockDim.x) stage_z(c0, nc, bl, r, sz + 3 * (r - z0));
       __syncthreads();
       if (mine)
         for (int r = max(k, z0) + lane; r < z1; r += 32) {
@@ -236,46 +295,70 @@ __device__ __forceinline__ void tsweep_bwd(const Dev& d, const double* y, int h,
       fin(c0 + k, a0, a1, a2);
     }
   }
+  __syncthreads();   // the block-mode units are done with the staging buffer
   // nodes of at most 32 columns: one warp each, lane k accumulates column k
-  // over the rows (walking the row-major copy: a row's columns are contiguous)
+  // over the rows (walking the row-major copy: a row's columns are
+  // contiguous); the rows' right-hand side goes through the warp's slice of
+  // the staging buffer in chunks
+  const int cap = kTStage / bwarps;
+  double* zw = sz + 3 * (size_t)warp * cap;
   for (int w = d.t_lev_w[h] + gwarp; w < d.t_lev_w[h + 1]; w += nwarps) {
     const int s = d.t_wnode[w];
     const int c0 = d.t_c0[s], nc = d.t_nc[s], nb = d.t_nb[s];
+    const int R = nc + nb;
     const double* P = d.t_prow + d.t_poff[s];
     const int* bl = d.t_below + d.t_boff[s];
+    const bool on = lane < nc;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    for (int r = 0; r < nc + nb; ++r) {
-      double v0, v1, v2;
-      if (r < nc) {
-        const double* yr = y + 3 * (size_t)(c0 + r);
-        v0 = yr[0];
-        v1 = yr[1];
-        v2 = yr[2];
-      } else {
-        const double* xr = x + 3 * (size_t)bl[r - nc];
-        v0 = -xr[0];
-        v1 = -xr[1];
-        v2 = -xr[2];
+    for (int r0 = 0; r0 < R; r0 += cap) {
+      const int r1 = min(R, r0 + cap);
+      __syncwarp();
+      for (int r = r0 + lane; r < r1; r += 32) stage_z(c0, nc, bl, r, zw + 3 * (r - r0));
+      __syncwarp();
+      int r = r0;
+      // rows of Linv (row r holds columns 0..r)
+      for (; r < min(r1, nc); ++r) {
+        if (on && lane <= r) {
+          const double p = P[(int64_t)r * (r + 1) / 2 + lane];
+          const double* zr = zw + 3 * (r - r0);
+          a0 += p * zr[0];
+          a1 += p * zr[1];
+          a2 += p * zr[2];
+        }
       }
-      if (lane < nc && lane <= r) {
-        const double p = P[t_rowoff(nc, r) + lane];
-        a0 += p * v0;
-        a1 += p * v1;
-        a2 += p * v2;
+      // rows of M (nc columns each), four rows per pass for loads in flight
+      const double* pm = P + (int64_t)nc * (nc + 1) / 2 - (int64_t)nc * nc;   // pm[r * nc]: row r >= nc
+      for (; r + 3 < r1; r += 4) {
+        if (on) {
+          double p[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) p[i] = pm[(int64_t)(r + i) * nc + lane];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const double* zr = zw + 3 * (r + i - r0);
+            a0 += p[i] * zr[0];
+            a1 += p[i] * zr[1];
+            a2 += p[i] * zr[2];
+          }
+        }
+      }
+      for (; r < r1; ++r) {
+        if (on) {
+          const double p = pm[(int64_t)r * nc + lane];
+          const double* zr = zw + 3 * (r - r0);
+          a0 += p * zr[0];
+          a1 += p * zr[1];
+          a2 += p * zr[2];
+        }
       }
     }
-    if (lane < nc) {
+    if (on) {
       double* xk = x + 3 * (size_t)(c0 + lane);
       xk[0] = a0;
       xk[1] = a1;
       xk[2] = a2;
     }
-    for (int kk = 0; kk < nc; ++kk) {
-      const double b0 = __shfl_sync(0xffffffffu, a0, kk);
-      const double b1 = __shfl_sync(0xffffffffu, a1, kk);
-      const double b2 = __shfl_sync(0xffffffffu, a2, kk);
-      fin(c0 + kk, b0, b1, b2);
-    }
+    fin.lanes(on, c0 + lane, a0, a1, a2);
   }
 }
 

@@ -212,16 +212,21 @@ void build_tsolve(const Factor& f, TSolve& t) {
         t.wnode.push_back(u);
         continue;
       }
+      // forward units: enough rows that staging r_s once pays off; backward
+      // units: enough columns likewise while the whole right-hand side fits
+      // the staging vector, else one column per warp with chunked staging
       const int rows = t.nc[u] + t.nb[u];
-      for (int r0 = 0; r0 < rows; r0 += kUnitRows) {
+      const int ur = std::max(kUnitRows, (kUnitEntries / t.nc[u] + 31) / 32 * 32);
+      for (int r0 = 0; r0 < rows; r0 += ur) {
         t.unit_f.push_back(u);
         t.unit_f.push_back(r0);
-        t.unit_f.push_back(std::min(kUnitRows, rows - r0));
+        t.unit_f.push_back(std::min(ur, rows - r0));
       }
-      for (int k0 = 0; k0 < t.nc[u]; k0 += kUnitCols) {
+      const int uc = rows <= kStageRows ? std::max(kUnitCols, kUnitEntries / rows) : kUnitCols;
+      for (int k0 = 0; k0 < t.nc[u]; k0 += uc) {
         t.unit_b.push_back(u);
         t.unit_b.push_back(k0);
-        t.unit_b.push_back(std::min(kUnitCols, t.nc[u] - k0));
+        t.unit_b.push_back(std::min(uc, t.nc[u] - k0));
       }
     }
     t.lev_f[h + 1] = (int)t.unit_f.size() / 3;

@@ -37,9 +37,11 @@
 namespace pdf {
 
 constexpr int kNodeMaxCols = 1024;   // columns per node (the forward stages r_s, nc x 3 FP64, in shared memory)
+constexpr int kStageRows = 1024;     // rows of the device's shared staging vector (backward right-hand side)
 constexpr int kWarpNodeCols = 32;    // nodes of at most this many columns are done by one warp
-constexpr int kUnitRows = 32;        // forward rows of a block-mode node per work unit
-constexpr int kUnitCols = 8;         // backward columns of a block-mode node per work unit
+constexpr int kUnitRows = 32;        // least forward rows of a block-mode node per work unit
+constexpr int kUnitCols = 8;         // backward columns per work unit when the right-hand side is staged in chunks
+constexpr int kUnitEntries = 16384;  // target stored entries per work unit (staging is paid once per unit)
 
 struct TSolve {
   int n = 0;                       // free vertices (positions)
