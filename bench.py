@@ -33,10 +33,6 @@ import sys
 import threading
 import time
 
-# the CPU oracle baseline runs single-threaded (set before numpy loads BLAS)
-for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-    os.environ.setdefault(_v, "1")
-
 import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -119,9 +115,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def one_thread():
+    """The oracle baseline runs single-threaded: numpy's BLAS limited to one
+    thread for the duration (the library's own host code keeps its threads)."""
+    from threadpoolctl import threadpool_limits
+    return threadpool_limits(limits=1, user_api="blas")
+
+
 def oracle_sample(scene, n_steps: int):
     """The oracle as it stands (exact fixed point + direct adjoint) on the first
     n_steps steps of the workload, single-threaded. Returns (seconds, steps)."""
+    with one_thread():
+        return _oracle_sample(scene, n_steps)
+
+
+def _oracle_sample(scene, n_steps: int):
     from oracle import adjoint, solver
     sc = scene.with_steps(n_steps)
     t0 = time.perf_counter()
@@ -145,6 +153,11 @@ def oracle_sample_mid(scene, steps=(100, 150)):
     if gold is None or "samples_v" not in gold.files:
         dt, k = oracle_sample(scene, 2)
         return dt, k, f"first {k} PD steps of the same rollout, forward (exact fixed point) + adjoint, FP64, 1 thread"
+    with one_thread():
+        return _oracle_sample_mid(scene, steps, gold, solver, adjoint)
+
+
+def _oracle_sample_mid(scene, steps, gold, solver, adjoint):
     sc = scene.with_steps(1)
     t0 = time.perf_counter()
     pb = solver.build_problem(sc)
@@ -517,6 +530,21 @@ def run_block(args, rank, world, local_rank, dev, dist):
     le[1].record(stream)
     torch.cuda.synchronize()
     local_ms = le[0].elapsed_time(le[1]) / nrep
+    # the same for the corotated model on the same block (its own context;
+    # no Newton iterations in the projection: the case the HBM roofline can
+    # bind)
+    sc_co = sc.replace(model="corotated")
+    pd_co = binding.PDContext(sc_co, binding.options_for(sc_co.solver))
+    for _ in range(3):
+        binding.pd_local_rhs(pd_co.ctx, qT, out, stream)
+    torch.cuda.synchronize()
+    le[0].record(stream)
+    for _ in range(nrep):
+        binding.pd_local_rhs(pd_co.ctx, qT, out, stream)
+    le[1].record(stream)
+    torch.cuda.synchronize()
+    local_co_ms = le[0].elapsed_time(le[1]) / nrep
+    pd_co.close()
     # local step algorithmic bytes (the minimum the operation must move): per
     # element its corner indices 16, Dm^-1 36 (FP32) and w_e V_e 4 B; per
     # vertex q read 24 B and the right-hand side written 24 B. (The
@@ -553,7 +581,11 @@ def run_block(args, rank, world, local_rank, dev, dist):
                                       "rate 1.25 TFLOP/s"},
             "local_step": {"achieved": local_gbs, "peak": peak, "unit": "GB/s", "frac": local_gbs / peak,
                            "bytes_per_launch": local_bytes, "avg_ms": local_ms, "launches_timed": nrep,
-                           "kernels": "k_local_all + k_rhs_out (pd_local_rhs)", "peak_kind": peak_kind},
+                           "kernels": "k_local_all + k_rhs_out (pd_local_rhs)", "peak_kind": peak_kind,
+                           "model": "neohookean (FP32 local step)",
+                           "corotated": {"achieved": local_bytes / (local_co_ms * 1e-3) / 1e9,
+                                         "frac": local_bytes / (local_co_ms * 1e-3) / 1e9 / peak,
+                                         "avg_ms": local_co_ms}},
             "clocks": clk.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         small = inputs.large_block(n=12, steps=1, seed=5)

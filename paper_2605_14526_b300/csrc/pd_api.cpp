@@ -539,8 +539,8 @@ int pd_factor(pd_ctx* c) {
   d.t_nlev = 0;
   if (tmode) {
     auto units = [](const std::vector<int>& u) {
-      std::vector<int4> o(u.size() / 3);
-      for (size_t i = 0; i < o.size(); ++i) o[i] = make_int4(u[3 * i], u[3 * i + 1], u[3 * i + 2], 0);
+      std::vector<int4> o(u.size() / 4);
+      for (size_t i = 0; i < o.size(); ++i) o[i] = make_int4(u[4 * i], u[4 * i + 1], u[4 * i + 2], u[4 * i + 3]);
       return o;
     };
     const std::vector<int4> uf = units(ts.unit_f), ub = units(ts.unit_b);

@@ -82,6 +82,54 @@ static __device__ __noinline__ void tsweep_fwd(const Dev& d, const double* b, do
       sr[3 * k + 2] = bk[2] - a2;
     }
     __syncthreads();
+    if (un.w) {
+      // a node of 33..256 columns: a lane per row, 32 rows per warp, walking
+      // the column-major copy (column k holds rows k..; lanes read
+      // consecutive rows) with r_k broadcast from shared memory
+      const int nb = d.t_nb[s];
+      const double* Pc = d.t_pcol + d.t_poff[s];
+      for (int g = row0 + 32 * warp; g < row0 + rows; g += 32 * bwarps) {
+        const int o = g + lane;
+        const bool valid = o < row0 + rows;
+        const int kend = valid ? (o < nc ? o + 1 : nc) : 0;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        int k = 0;
+        for (; k + 3 < kend; k += 4) {
+          double p[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) p[i] = Pc[t_coloff(nc, nb, k + i) + (o - k - i)];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const double* rk = sr + 3 * (k + i);
+            a0 += p[i] * rk[0];
+            a1 += p[i] * rk[1];
+            a2 += p[i] * rk[2];
+          }
+        }
+        for (; k < kend; ++k) {
+          const double p = Pc[t_coloff(nc, nb, k) + (o - k)];
+          const double* rk = sr + 3 * k;
+          a0 += p * rk[0];
+          a1 += p * rk[1];
+          a2 += p * rk[2];
+        }
+        if (!valid) continue;
+        if (o < nc) {
+          double* yo = y + 3 * (size_t)(c0 + o);
+          yo[0] = a0;
+          yo[1] = a1;
+          yo[2] = a2;
+        } else {
+          double g0a, g1a, g2a;
+          t_gather(d, g0 + o, g0a, g1a, g2a);
+          double* uo = d.t_U + 3 * (size_t)(d.t_boff[s] + o - nc);
+          uo[0] = a0 + g0a;
+          uo[1] = a1 + g1a;
+          uo[2] = a2 + g2a;
+        }
+      }
+      continue;
+    }
     const double* P = d.t_prow + d.t_poff[s];
     for (int o = row0 + warp; o < row0 + rows; o += bwarps) {
       const int len = o < nc ? o + 1 : nc;
@@ -221,6 +269,65 @@ __device__ __forceinline__ void tsweep_bwd(const Dev& d, const double* y, int h,
     const int R = nc + nb;
     const int* bl = d.t_below + d.t_boff[s];
     const double* P = d.t_pcol + d.t_poff[s];
+    if (un.w) {
+      // a node of 33..256 columns: a lane per column, 32 columns per warp,
+      // walking the row-major copy (row r holds columns 0..; lanes read
+      // consecutive columns) with the right-hand side staged in chunks
+      const double* Pr = d.t_prow + d.t_poff[s];
+      const int k = k0 + 32 * warp + lane;
+      const bool on = warp * 32 < ncols && k < k0 + ncols;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+      for (int z0 = 0; z0 < R; z0 += kTStage) {
+        const int z1 = min(R, z0 + kTStage);
+        __syncthreads();
+        for (int r = z0 + (int)threadIdx.x; r < z1; r += blockDim.x) stage_z(c0, nc, bl, r, sz + 3 * (r - z0));
+        __syncthreads();
+        if (warp * 32 >= ncols) continue;
+        int r = max(z0, k0 + 32 * warp);   // rows of Linv below column k0 + 32 warp .. (lanes with k > r idle)
+        for (; r < min(z1, nc); ++r)
+          if (on && k <= r) {
+            const double p = Pr[(int64_t)r * (r + 1) / 2 + k];
+            const double* zr = sz + 3 * (r - z0);
+            a0 += p * zr[0];
+            a1 += p * zr[1];
+            a2 += p * zr[2];
+          }
+        const double* pm = Pr + (int64_t)nc * (nc + 1) / 2 - (int64_t)nc * nc;   // pm[r * nc]: row r >= nc
+        r = max(r, z0);
+        for (; r + 3 < z1; r += 4) {
+          if (on) {
+            double p[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) p[i] = pm[(int64_t)(r + i) * nc + k];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const double* zr = sz + 3 * (r + i - z0);
+              a0 += p[i] * zr[0];
+              a1 += p[i] * zr[1];
+              a2 += p[i] * zr[2];
+            }
+          }
+        }
+        for (; r < z1; ++r)
+          if (on) {
+            const double p = pm[(int64_t)r * nc + k];
+            const double* zr = sz + 3 * (r - z0);
+            a0 += p * zr[0];
+            a1 += p * zr[1];
+            a2 += p * zr[2];
+          }
+      }
+      if (warp * 32 < ncols) {
+        if (on) {
+          double* xk = x + 3 * (size_t)(c0 + k);
+          xk[0] = a0;
+          xk[1] = a1;
+          xk[2] = a2;
+        }
+        fin.lanes(on, c0 + k, a0, a1, a2);
+      }
+      continue;
+    }
     if (R <= kTStage) {
       // the right-hand side [y_s; -x_below] staged once; warps take the
       // unit's columns in turn

@@ -212,25 +212,26 @@ void build_tsolve(const Factor& f, TSolve& t) {
         t.wnode.push_back(u);
         continue;
       }
-      // forward units: enough rows that staging r_s once pays off; backward
-      // units: enough columns likewise while the whole right-hand side fits
-      // the staging vector, else one column per warp with chunked staging
       const int rows = t.nc[u] + t.nb[u];
-      const int ur = std::max(kUnitRows, (kUnitEntries / t.nc[u] + 31) / 32 * 32);
-      for (int r0 = 0; r0 < rows; r0 += ur) {
-        t.unit_f.push_back(u);
-        t.unit_f.push_back(r0);
-        t.unit_f.push_back(std::min(ur, rows - r0));
+      if (t.nc[u] <= kLaneNodeCols) {
+        // lane-per-row / lane-per-column units: up to 8 groups of 32 rows
+        // (forward) and the node's columns in groups of 32 (backward)
+        for (int r0 = 0; r0 < rows; r0 += 256) {
+          t.unit_f.insert(t.unit_f.end(), {u, r0, std::min(256, rows - r0), 1});
+        }
+        t.unit_b.insert(t.unit_b.end(), {u, 0, t.nc[u], 1});
+        continue;
       }
+      // warp-per-row / warp-per-column units: 32 rows (forward); enough
+      // columns that staging pays off while the whole right-hand side fits
+      // the staging vector, else one column per warp with chunked staging
+      for (int r0 = 0; r0 < rows; r0 += kUnitRows)
+        t.unit_f.insert(t.unit_f.end(), {u, r0, std::min(kUnitRows, rows - r0), 0});
       const int uc = rows <= kStageRows ? std::max(kUnitCols, kUnitEntries / rows) : kUnitCols;
-      for (int k0 = 0; k0 < t.nc[u]; k0 += uc) {
-        t.unit_b.push_back(u);
-        t.unit_b.push_back(k0);
-        t.unit_b.push_back(std::min(uc, t.nc[u] - k0));
-      }
+      for (int k0 = 0; k0 < t.nc[u]; k0 += uc) t.unit_b.insert(t.unit_b.end(), {u, k0, std::min(uc, t.nc[u] - k0), 0});
     }
-    t.lev_f[h + 1] = (int)t.unit_f.size() / 3;
-    t.lev_b[h + 1] = (int)t.unit_b.size() / 3;
+    t.lev_f[h + 1] = (int)t.unit_f.size() / 4;
+    t.lev_b[h + 1] = (int)t.unit_b.size() / 4;
     t.lev_w[h + 1] = (int)t.wnode.size();
   }
   t.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

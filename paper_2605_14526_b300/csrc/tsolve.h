@@ -39,6 +39,7 @@ namespace pdf {
 constexpr int kNodeMaxCols = 1024;   // columns per node (the forward stages r_s, nc x 3 FP64, in shared memory)
 constexpr int kStageRows = 1024;     // rows of the device's shared staging vector (backward right-hand side)
 constexpr int kWarpNodeCols = 32;    // nodes of at most this many columns are done by one warp
+constexpr int kLaneNodeCols = 256;   // larger nodes up to this many: a lane per row / column (no reductions)
 constexpr int kUnitRows = 32;        // least forward rows of a block-mode node per work unit
 constexpr int kUnitCols = 8;         // backward columns per work unit when the right-hand side is staged in chunks
 constexpr int kUnitEntries = 16384;  // target stored entries per work unit (staging is paid once per unit)
@@ -55,10 +56,11 @@ struct TSolve {
   std::vector<int64_t> goff;       // [n_node + 1]: offset of the node's positions 0 .. nc + nb - 1 in gptr
   std::vector<int> gptr;           // [goff[n_node] + 1]: gather lists per (node, position) into gsrc
   std::vector<int> gsrc;           // U rows of the children that feed a position
-  // schedule per height: block-mode forward units {node, row0, rows},
-  // block-mode backward units {node, col0, cols}, warp-mode nodes
+  // schedule per height: block-mode forward units {node, row0, rows, lane},
+  // block-mode backward units {node, col0, cols, lane} (lane = 1: a lane per
+  // row / column, nodes of at most kLaneNodeCols columns), warp-mode nodes
   std::vector<int> lev_f, lev_b, lev_w;   // [n_level + 1] ranges into the lists below
-  std::vector<int> unit_f, unit_b;        // 3 ints per unit
+  std::vector<int> unit_f, unit_b;        // 4 ints per unit
   std::vector<int> wnode;
   int64_t entries = 0;             // stored entries of one copy ([Linv; M] over all nodes)
   int64_t u_rows = 0;              // rows of the update buffer U (sum of nb)
