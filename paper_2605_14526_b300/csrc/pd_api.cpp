@@ -544,7 +544,10 @@ int pd_factor(pd_ctx* c) {
       return o;
     };
     const std::vector<int4> uf = units(ts.unit_f), ub = units(ts.unit_b);
-    int *c0d, *ncd, *nbd, *bld, *gpd, *gsd, *lfd, *lbd, *lwd, *wnd;
+    std::vector<int2> wf(ts.wnode_f.size() / 2);
+    for (size_t i = 0; i < wf.size(); ++i) wf[i] = make_int2(ts.wnode_f[2 * i], ts.wnode_f[2 * i + 1]);
+    int *c0d, *ncd, *nbd, *bld, *gpd, *gsd, *lfd, *lbd, *lwfd, *lwbd, *wbd;
+    int2* wfd;
     int64_t *bod, *pod, *god;
     double *prd, *pcd, *Ud, *xd;
     int4 *ufd, *ubd;
@@ -554,14 +557,16 @@ int pd_factor(pd_ctx* c) {
         (r = upload(c, &pcd, ts.pcol, true)) || (r = upload(c, &god, ts.goff, true)) ||
         (r = upload(c, &gpd, ts.gptr, true)) || (r = upload(c, &gsd, ts.gsrc, true)) ||
         (r = upload(c, &lfd, ts.lev_f, true)) || (r = upload(c, &lbd, ts.lev_b, true)) ||
-        (r = upload(c, &lwd, ts.lev_w, true)) || (r = upload(c, &ufd, uf, true)) || (r = upload(c, &ubd, ub, true)) ||
-        (r = upload(c, &wnd, ts.wnode, true)) || (r = dalloc(c, &Ud, 3 * (size_t)ts.u_rows, true)) ||
+        (r = upload(c, &lwfd, ts.lev_wf, true)) || (r = upload(c, &lwbd, ts.lev_wb, true)) ||
+        (r = upload(c, &ufd, uf, true)) || (r = upload(c, &ubd, ub, true)) || (r = upload(c, &wfd, wf, true)) ||
+        (r = upload(c, &wbd, ts.wnode_b, true)) || (r = dalloc(c, &Ud, 3 * (size_t)ts.u_rows, true)) ||
         (r = dalloc(c, &xd, 3 * (size_t)nf, true)))
       return r;
     d.t_nlev = ts.n_level;
     d.t_c0 = c0d; d.t_nc = ncd; d.t_nb = nbd; d.t_boff = bod; d.t_below = bld; d.t_poff = pod;
     d.t_prow = prd; d.t_pcol = pcd; d.t_goff = god; d.t_gptr = gpd; d.t_gsrc = gsd;
-    d.t_lev_f = lfd; d.t_lev_b = lbd; d.t_lev_w = lwd; d.t_unit_f = ufd; d.t_unit_b = ubd; d.t_wnode = wnd;
+    d.t_lev_f = lfd; d.t_lev_b = lbd; d.t_lev_wf = lwfd; d.t_lev_wb = lwbd; d.t_unit_f = ufd; d.t_unit_b = ubd;
+    d.t_wnode_f = wfd; d.t_wnode_b = wbd;
     d.t_U = Ud; d.t_x = xd;
   }
   c->tmode = tmode;

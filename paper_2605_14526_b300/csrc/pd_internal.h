@@ -163,10 +163,12 @@ struct Dev {
   const int* t_gsrc;       // U rows of the children
   const int* t_lev_f;      // [heights + 1] forward block units per height
   const int* t_lev_b;      // [heights + 1] backward block units per height
-  const int* t_lev_w;      // [heights + 1] warp nodes per height
-  const int4* t_unit_f;    // {node, first row, rows, 0}
+  const int* t_lev_wf;     // [heights + 1] forward warp items per height
+  const int* t_lev_wb;     // [heights + 1] backward warp nodes per height
+  const int4* t_unit_f;    // {node, first row, rows, 1: a lane per row}
   const int4* t_unit_b;    // {node, first column, columns, 0}
-  const int* t_wnode;      // nodes of at most 32 columns
+  const int2* t_wnode_f;   // {node, first row}: 32 rows of a node of at most 32 columns
+  const int* t_wnode_b;    // nodes of at most 32 columns and 160 rows
   double* t_U;             // [sum nb][3] updates passed up the node tree
   double* t_x;             // [n_f][3] result of the backward sweep (elimination order)
 

@@ -42,27 +42,47 @@ __global__ void __launch_bounds__(kTetBlock) k_local_all(Dev d, const double* x)
 }
 
 // the projection part of the right-hand side per vertex, sum_e w_e V_e G_e^T
-// vec(p_e), from the elements' corner forces: one warp per vertex in the
-// fixed order of the assembly (FP64); pinned rows get 0
+// vec(p_e), from the elements' corner forces: one thread per vertex adds its
+// incident corners in the order of the incidence list (FP64), four loads in
+// flight; pinned rows get 0
 template <typename T>
 __global__ void __launch_bounds__(kVtxBlock) k_rhs_out(Dev d, double* out) {
-  const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= d.n_v) return;
+  double* o = out + 3 * (size_t)v;
   if (d.pinned[v]) {
-    if (lane < 3) out[3 * (size_t)v + lane] = 0.0;
+    o[0] = o[1] = o[2] = 0.0;
     return;
   }
   const T* cb = reinterpret_cast<const T*>(d.contrib);
-  double c[3] = {0.0, 0.0, 0.0};
-  for (int p = d.inc_ptr[v] + lane; p < d.inc_ptr[v + 1]; p += 32) {
-    const int ic = d.inc_idx[p];
+  double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+  int p = d.inc_ptr[v];
+  const int end = d.inc_ptr[v + 1];
+  for (; p + 3 < end; p += 4) {
+    int ic[4];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) c[i] += (double)cb[3 * (size_t)ic + i];
+    for (int i = 0; i < 4; ++i) ic[i] = d.inc_idx[p + i];
+    T f[4][3];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) f[i][j] = cb[3 * (size_t)ic[i] + j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      c0 += (double)f[i][0];
+      c1 += (double)f[i][1];
+      c2 += (double)f[i][2];
+    }
   }
-  int i;
-  const double sum = warp_sum_scatter<3>(c, lane, i);
-  if ((lane & 7) == 0 && i < 3) out[3 * (size_t)v + i] = sum;
+  for (; p < end; ++p) {
+    const T* f = cb + 3 * (size_t)d.inc_idx[p];
+    c0 += (double)f[0];
+    c1 += (double)f[1];
+    c2 += (double)f[2];
+  }
+  o[0] = c0;
+  o[1] = c1;
+  o[2] = c2;
 }
 
 template <typename T>
@@ -238,10 +258,10 @@ void launch_apply_inverse(const Dev& d, cudaStream_t s, const float2* xperm, flo
 void launch_local_rhs(const Dev& d, cudaStream_t s, const double* x, double* out) {
   if (d.local_fp32) {
     k_local_all<float><<<nblk(d.n_e, kTetBlock), kTetBlock, 0, s>>>(d, x);
-    k_rhs_out<float><<<nblk(32 * d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d, out);
+    k_rhs_out<float><<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d, out);
   } else {
     k_local_all<double><<<nblk(d.n_e, kTetBlock), kTetBlock, 0, s>>>(d, x);
-    k_rhs_out<double><<<nblk(32 * d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d, out);
+    k_rhs_out<double><<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d, out);
   }
 }
 

@@ -171,10 +171,12 @@ static __device__ __noinline__ void tsweep_fwd(const Dev& d, const double* b, do
       }
     }
   }
-  // nodes of at most 32 columns: one warp each, lane k holds r_k, lane o
-  // computes row o (walking the column-major copy: rows are contiguous)
-  for (int w = d.t_lev_w[h] + gwarp; w < d.t_lev_w[h + 1]; w += nwarps) {
-    const int s = d.t_wnode[w];
+  // nodes of at most 32 columns: one warp item per 32 rows; lane k forms
+  // r_k from the gathers, lane o computes row o (walking the column-major
+  // copy: rows are contiguous)
+  for (int w = d.t_lev_wf[h] + gwarp; w < d.t_lev_wf[h + 1]; w += nwarps) {
+    const int2 it = d.t_wnode_f[w];
+    const int s = it.x, o0 = it.y;
     const int c0 = d.t_c0[s], nc = d.t_nc[s], nb = d.t_nb[s];
     const int64_t g0 = d.t_goff[s];
     double r0 = 0.0, r1 = 0.0, r2 = 0.0;
@@ -187,7 +189,7 @@ static __device__ __noinline__ void tsweep_fwd(const Dev& d, const double* b, do
       r2 = bk[2] - a2;
     }
     const double* P = d.t_pcol + d.t_poff[s];
-    for (int o0 = 0; o0 < nc + nb; o0 += 32) {
+    {
       const int o = o0 + lane;
       const bool valid = o < nc + nb;
       double a0 = 0.0, a1 = 0.0, a2 = 0.0;
@@ -269,65 +271,6 @@ __device__ __forceinline__ void tsweep_bwd(const Dev& d, const double* y, int h,
     const int R = nc + nb;
     const int* bl = d.t_below + d.t_boff[s];
     const double* P = d.t_pcol + d.t_poff[s];
-    if (un.w) {
-      // a node of 33..256 columns: a lane per column, 32 columns per warp,
-      // walking the row-major copy (row r holds columns 0..; lanes read
-      // consecutive columns) with the right-hand side staged in chunks
-      const double* Pr = d.t_prow + d.t_poff[s];
-      const int k = k0 + 32 * warp + lane;
-      const bool on = warp * 32 < ncols && k < k0 + ncols;
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-      for (int z0 = 0; z0 < R; z0 += kTStage) {
-        const int z1 = min(R, z0 + kTStage);
-        __syncthreads();
-        for (int r = z0 + (int)threadIdx.x; r < z1; r += blockDim.x) stage_z(c0, nc, bl, r, sz + 3 * (r - z0));
-        __syncthreads();
-        if (warp * 32 >= ncols) continue;
-        int r = max(z0, k0 + 32 * warp);   // rows of Linv below column k0 + 32 warp .. (lanes with k > r idle)
-        for (; r < min(z1, nc); ++r)
-          if (on && k <= r) {
-            const double p = Pr[(int64_t)r * (r + 1) / 2 + k];
-            const double* zr = sz + 3 * (r - z0);
-            a0 += p * zr[0];
-            a1 += p * zr[1];
-            a2 += p * zr[2];
-          }
-        const double* pm = Pr + (int64_t)nc * (nc + 1) / 2 - (int64_t)nc * nc;   // pm[r * nc]: row r >= nc
-        r = max(r, z0);
-        for (; r + 3 < z1; r += 4) {
-          if (on) {
-            double p[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) p[i] = pm[(int64_t)(r + i) * nc + k];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const double* zr = sz + 3 * (r + i - z0);
-              a0 += p[i] * zr[0];
-              a1 += p[i] * zr[1];
-              a2 += p[i] * zr[2];
-            }
-          }
-        }
-        for (; r < z1; ++r)
-          if (on) {
-            const double p = pm[(int64_t)r * nc + k];
-            const double* zr = sz + 3 * (r - z0);
-            a0 += p * zr[0];
-            a1 += p * zr[1];
-            a2 += p * zr[2];
-          }
-      }
-      if (warp * 32 < ncols) {
-        if (on) {
-          double* xk = x + 3 * (size_t)(c0 + k);
-          xk[0] = a0;
-          xk[1] = a1;
-          xk[2] = a2;
-        }
-        fin.lanes(on, c0 + k, a0, a1, a2);
-      }
-      continue;
-    }
     if (R <= kTStage) {
       // the right-hand side [y_s; -x_below] staged once; warps take the
       // unit's columns in turn
@@ -409,8 +352,8 @@ __device__ __forceinline__ void tsweep_bwd(const Dev& d, const double* y, int h,
   // the staging buffer in chunks
   const int cap = kTStage / bwarps;
   double* zw = sz + 3 * (size_t)warp * cap;
-  for (int w = d.t_lev_w[h] + gwarp; w < d.t_lev_w[h + 1]; w += nwarps) {
-    const int s = d.t_wnode[w];
+  for (int w = d.t_lev_wb[h] + gwarp; w < d.t_lev_wb[h + 1]; w += nwarps) {
+    const int s = d.t_wnode_b[w];
     const int c0 = d.t_c0[s], nc = d.t_nc[s], nb = d.t_nb[s];
     const int R = nc + nb;
     const double* P = d.t_prow + d.t_poff[s];

@@ -204,35 +204,39 @@ void build_tsolve(const Factor& f, TSolve& t) {
   t.n_level = nn ? H + 1 : 0;
   t.lev_f.assign(t.n_level + 1, 0);
   t.lev_b.assign(t.n_level + 1, 0);
-  t.lev_w.assign(t.n_level + 1, 0);
+  t.lev_wf.assign(t.n_level + 1, 0);
+  t.lev_wb.assign(t.n_level + 1, 0);
   for (int h = 0; h < t.n_level; ++h) {
     for (int u = 0; u < nn; ++u) {
       if (t.height[u] != h) continue;
-      if (t.nc[u] <= kWarpNodeCols) {
-        t.wnode.push_back(u);
-        continue;
+      const int nc = t.nc[u], rows = nc + t.nb[u];
+      // forward: a node of at most 32 columns is one warp item per 32 rows
+      // (each item forms r_s from the gathers itself); up to kLaneNodeCols
+      // columns a lane per row in units of 8 x 32 rows; larger nodes a warp
+      // per row in units of 32 rows
+      if (nc <= kWarpNodeCols) {
+        for (int r0 = 0; r0 < rows; r0 += 32) t.wnode_f.insert(t.wnode_f.end(), {u, r0});
+      } else if (nc <= kLaneNodeCols) {
+        for (int r0 = 0; r0 < rows; r0 += 256) t.unit_f.insert(t.unit_f.end(), {u, r0, std::min(256, rows - r0), 1});
+      } else {
+        for (int r0 = 0; r0 < rows; r0 += kUnitRows)
+          t.unit_f.insert(t.unit_f.end(), {u, r0, std::min(kUnitRows, rows - r0), 0});
       }
-      const int rows = t.nc[u] + t.nb[u];
-      if (t.nc[u] <= kLaneNodeCols) {
-        // lane-per-row / lane-per-column units: up to 8 groups of 32 rows
-        // (forward) and the node's columns in groups of 32 (backward)
-        for (int r0 = 0; r0 < rows; r0 += 256) {
-          t.unit_f.insert(t.unit_f.end(), {u, r0, std::min(256, rows - r0), 1});
-        }
-        t.unit_b.insert(t.unit_b.end(), {u, 0, t.nc[u], 1});
-        continue;
+      // backward: a small node with a short right-hand side is one warp's
+      // (a lane per column); otherwise a warp per column in units of enough
+      // columns that staging the right-hand side once pays off, while it
+      // fits the staging vector, else 8 columns with chunked staging
+      if (nc <= kWarpNodeCols && rows <= kWarpNodeRows) {
+        t.wnode_b.push_back(u);
+      } else {
+        const int uc = rows <= kStageRows ? std::max(kUnitCols, kUnitEntries / rows) : kUnitCols;
+        for (int k0 = 0; k0 < nc; k0 += uc) t.unit_b.insert(t.unit_b.end(), {u, k0, std::min(uc, nc - k0), 0});
       }
-      // warp-per-row / warp-per-column units: 32 rows (forward); enough
-      // columns that staging pays off while the whole right-hand side fits
-      // the staging vector, else one column per warp with chunked staging
-      for (int r0 = 0; r0 < rows; r0 += kUnitRows)
-        t.unit_f.insert(t.unit_f.end(), {u, r0, std::min(kUnitRows, rows - r0), 0});
-      const int uc = rows <= kStageRows ? std::max(kUnitCols, kUnitEntries / rows) : kUnitCols;
-      for (int k0 = 0; k0 < t.nc[u]; k0 += uc) t.unit_b.insert(t.unit_b.end(), {u, k0, std::min(uc, t.nc[u] - k0), 0});
     }
     t.lev_f[h + 1] = (int)t.unit_f.size() / 4;
     t.lev_b[h + 1] = (int)t.unit_b.size() / 4;
-    t.lev_w[h + 1] = (int)t.wnode.size();
+    t.lev_wf[h + 1] = (int)t.wnode_f.size() / 2;
+    t.lev_wb[h + 1] = (int)t.wnode_b.size();
   }
   t.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }

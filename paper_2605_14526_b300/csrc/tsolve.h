@@ -39,7 +39,8 @@ namespace pdf {
 constexpr int kNodeMaxCols = 1024;   // columns per node (the forward stages r_s, nc x 3 FP64, in shared memory)
 constexpr int kStageRows = 1024;     // rows of the device's shared staging vector (backward right-hand side)
 constexpr int kWarpNodeCols = 32;    // nodes of at most this many columns are done by one warp
-constexpr int kLaneNodeCols = 256;   // larger nodes up to this many: a lane per row / column (no reductions)
+constexpr int kLaneNodeCols = 256;   // forward: larger nodes up to this many, a lane per row (no reductions)
+constexpr int kWarpNodeRows = 160;   // backward: a small node with at most this many rows is one warp's
 constexpr int kUnitRows = 32;        // least forward rows of a block-mode node per work unit
 constexpr int kUnitCols = 8;         // backward columns per work unit when the right-hand side is staged in chunks
 constexpr int kUnitEntries = 16384;  // target stored entries per work unit (staging is paid once per unit)
@@ -56,12 +57,15 @@ struct TSolve {
   std::vector<int64_t> goff;       // [n_node + 1]: offset of the node's positions 0 .. nc + nb - 1 in gptr
   std::vector<int> gptr;           // [goff[n_node] + 1]: gather lists per (node, position) into gsrc
   std::vector<int> gsrc;           // U rows of the children that feed a position
-  // schedule per height: block-mode forward units {node, row0, rows, lane},
-  // block-mode backward units {node, col0, cols, lane} (lane = 1: a lane per
-  // row / column, nodes of at most kLaneNodeCols columns), warp-mode nodes
-  std::vector<int> lev_f, lev_b, lev_w;   // [n_level + 1] ranges into the lists below
-  std::vector<int> unit_f, unit_b;        // 4 ints per unit
-  std::vector<int> wnode;
+  // schedule per height: block forward units {node, row0, rows, lane}
+  // (lane = 1: a lane per row, nodes of at most kLaneNodeCols columns),
+  // block backward units {node, col0, cols, 0}, warp forward items
+  // {node, row0} (32 rows of a node of at most kWarpNodeCols columns), warp
+  // backward nodes (at most kWarpNodeCols columns and kWarpNodeRows rows)
+  std::vector<int> lev_f, lev_b, lev_wf, lev_wb;   // [n_level + 1] ranges into the lists below
+  std::vector<int> unit_f, unit_b;                  // 4 ints per unit
+  std::vector<int> wnode_f;                         // 2 ints per item
+  std::vector<int> wnode_b;
   int64_t entries = 0;             // stored entries of one copy ([Linv; M] over all nodes)
   int64_t u_rows = 0;              // rows of the update buffer U (sum of nb)
   double build_seconds = 0;
