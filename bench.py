@@ -16,6 +16,7 @@ rollouts (the bar's working set fits in L2).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
   python bench.py --workload batch    # 64 uneven meshes x 100 steps in one launch
   python bench.py --workload block    # 64^3-cell block (1.31M tets), solve mode T, local step alone
+  python bench.py --workload warm     # learned warm start: train, then cold / constant-velocity / network
 
 The batch workload (not the default line) times the batched persistent launch:
 64 seeded box/ellipsoid meshes of 1k-40k tets (about 0.58M tets in total) with
@@ -599,6 +600,166 @@ def run_block(args, rank, world, local_rank, dev, dist):
         print(json.dumps(line))
 
 
+WARM_WORKLOAD = ("learned warm start: a 7-128-128-128-3 network trained by the library's kernels on about 10k "
+                 "plain-solver frames (heterogeneous bars, uneven batched meshes), evaluated on held-out workloads: "
+                 "cold start q_t, constant-velocity extrapolation and the network, same gate")
+
+
+def _frames(binding, torch, ctx, n_v, T, x0, v0, f, stride, keep, dev, feats, targs):
+    """Plain-solver rollout of T steps and its training samples (frames 1 .. T-1)."""
+    qT, vT = torch.empty_like(x0), torch.empty_like(x0)
+    binding.pd_rollout(ctx, T, x0, v0, f, stride, qT, vT)
+    xs = [torch.as_tensor(binding.pd_get_checkpoint(ctx, s, n_v), device=dev) for s in range(T + 1)]
+    for s in range(1, T):
+        fe = torch.empty((n_v, 7), dtype=torch.float32, device=dev)
+        tg = torch.empty((n_v, 3), dtype=torch.float32, device=dev)
+        binding.pd_mlp_sample(ctx, xs[s - 1], xs[s], xs[s + 1], fe, tg)
+        feats.append(fe[keep])
+        targs.append(tg[keep])
+    return T - 1
+
+
+def _warm_compare(binding, torch, ctx, T, x0, v0, f, stride, n_inst, stream, dev):
+    """Forward rollouts from the three starts on one context: time, iterations,
+    fallbacks and the final state of each."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    out = {}
+    for name, mode in (("cold", 0), ("constant_velocity", 2), ("network", 1)):
+        binding.pd_set_warm_start(ctx, mode)
+        qT, vT = torch.empty_like(x0), torch.empty_like(x0)
+        binding.pd_rollout(ctx, T, x0, v0, f, stride, qT, vT, stream)   # untimed (uploads, caches)
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        binding.pd_rollout(ctx, T, x0, v0, f, stride, qT, vT, stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        st = binding.pd_get_stats(ctx)
+        ms = ev[0].elapsed_time(ev[1])
+        out[name] = {"fwd_pd_steps_per_s": n_inst * T / (ms * 1e-3), "fwd_ms": ms,
+                     "iters_per_step": st.iters_total / (T * n_inst), "max_iters_step": int(st.iters_max),
+                     "fallbacks": int(st.warm_fallbacks), "fallback_rate": st.warm_fallbacks / (T * n_inst),
+                     "not_converged": int(st.not_converged), "qT": qT.clone()}
+    ref = out["cold"]["qT"]
+    for name in out:
+        q = out[name].pop("qT")
+        out[name]["qT_rel_diff_vs_cold"] = float((q - ref).norm() / ref.norm())
+    binding.pd_set_warm_start(ctx, 0)
+    return out
+
+
+def run_warm(args, rank, world, local_rank, dev, dist):
+    """Warm-start workload: train the network on plain-solver frames, then
+    time the forward rollout of held-out workloads from the three starts."""
+    import torch
+    from paper_2605_14526_b300 import binding, inputs
+
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    rng = np.random.default_rng(100 + rank)
+    feats, targs = [], []
+    n_frames = 0
+    t0 = time.perf_counter()
+    for i in range(args.warm_bars):   # heterogeneous bars: other block maps and twist rates than the benchmark's
+        sc = inputs.hetero_bar(seed=20 + i, omega0=float(rng.uniform(1.5, 2.5)))
+        pd = binding.PDContext(sc)
+        keep = torch.as_tensor(sc.pinned == 0, device=dev)
+        n_frames += _frames(binding, torch, pd.ctx, sc.n_v, sc.steps, t(sc.x0), t(sc.v0), t(sc.f_ext[0]), 0, keep,
+                            dev, feats, targs)
+        pd.close()
+    scenes = inputs.batch_meshes(seed=1011 + rank)   # batched meshes other than the benchmark batch
+    bc = binding.BatchContext(scenes)
+    keep = torch.as_tensor(bc.concat([s.pinned for s in scenes]) == 0, device=dev)
+    n_frames += len(scenes) * _frames(binding, torch, bc.ctx, bc.n_v, scenes[0].steps,
+                                      t(bc.concat([s.x0 for s in scenes]).reshape(-1, 3)),
+                                      t(bc.concat([s.v0 for s in scenes]).reshape(-1, 3)), None, 0, keep, dev, feats,
+                                      targs)
+    bc.close()
+    feat = torch.cat(feats).contiguous()
+    targ = torch.cat(targs).contiguous()
+    del feats, targs
+    frames_s = time.perf_counter() - t0
+    n = feat.shape[0]
+    net = binding.MLP(inputs.mlp_init(0), np.concatenate([np.zeros(7), np.ones(7), np.ones(3)]).astype(np.float32))
+    binding.pd_mlp_fit_normalization(net.net, feat, targ, n)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(0)
+    probe = torch.randint(0, n, (1 << 20,), device=dev, generator=gen)
+    fp, tp = feat[probe].contiguous(), targ[probe].contiguous()
+    loss0 = binding.pd_mlp_grad(net.net, fp, tp, fp.shape[0])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for it in range(args.warm_train_steps):
+        idx = torch.randint(0, n, (args.warm_batch,), device=dev, generator=gen)
+        lr = 1e-3 if it < args.warm_train_steps * 3 // 4 else 2e-4
+        binding.pd_mlp_train_step(net.net, feat[idx].contiguous(), targ[idx].contiguous(), args.warm_batch, lr,
+                                  want_loss=False)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    loss1 = binding.pd_mlp_grad(net.net, fp, tp, fp.shape[0])
+    blob = net.blob()
+    del feat, targ, fp, tp
+    # held-out workloads: the benchmark bar, the benchmark batch (one launch,
+    # the batched form) and the large block
+    res = {}
+    sc = inputs.hetero_bar(seed=2 + rank)
+    pd = binding.PDContext(sc)
+    binding.pd_mlp_load(pd.ctx, blob)
+    res["bar32x8x8_T200"] = _warm_compare(binding, torch, pd.ctx, sc.steps, t(sc.x0), t(sc.v0), t(sc.f_ext[0]), 0, 1,
+                                          stream, dev)
+    if rank == 0:
+        gold_path = os.path.join(ROOT, "tests", "golden", "bar32x8x8_T200.npz")
+        if os.path.exists(gold_path):
+            gold = np.load(gold_path)
+            for name, mode in (("cold", 0), ("network", 1)):
+                binding.pd_set_warm_start(pd.ctx, mode)
+                x0 = t(sc.x0)
+                qT, vT = torch.empty_like(x0), torch.empty_like(x0)
+                binding.pd_rollout(pd.ctx, sc.steps, x0, t(sc.v0), t(sc.f_ext[0]), 0, qT, vT, stream)
+                q = qT.cpu().numpy()
+                res["bar32x8x8_T200"][name]["qT_rel_err_vs_oracle"] = float(
+                    max(np.linalg.norm(q - gold["qT"]) / np.linalg.norm(gold["qT"]),
+                        np.abs(q - gold["qT"]).max() / np.abs(gold["qT"]).max()))
+            binding.pd_set_warm_start(pd.ctx, 0)
+    pd.close()
+    scenes = inputs.batch_meshes(seed=11 + rank)
+    bc = binding.BatchContext(scenes)
+    binding.pd_mlp_load(bc.ctx, blob)
+    res["batch64_T100"] = _warm_compare(binding, torch, bc.ctx, scenes[0].steps,
+                                        t(bc.concat([s.x0 for s in scenes]).reshape(-1, 3)),
+                                        t(bc.concat([s.v0 for s in scenes]).reshape(-1, 3)), None, 0, len(scenes), stream,
+                                        dev)
+    bc.close()
+    if args.block_n > 0:
+        sb = inputs.large_block(n=args.block_n, steps=args.block_steps, seed=5 + rank)
+        pd = binding.PDContext(sb)
+        binding.pd_mlp_load(pd.ctx, blob)
+        res[f"block{args.block_n}_T{sb.steps}"] = _warm_compare(binding, torch, pd.ctx, sb.steps, t(sb.x0), t(sb.v0),
+                                                                t(sb.f_ext), 3 * sb.n_v, 1, stream, dev)
+        pd.close()
+    head = res["batch64_T100"]
+    value = world * head["network"]["fwd_pd_steps_per_s"]
+    line = {"metric": METRIC, "value": value, "unit": "instance PD steps/s (forward, network warm start)",
+            "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": head["network"]["fwd_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 (FP32 local step; FP64 RHS, factor, Anderson; network BF16 weights, FP32 activations, "
+                     "FP32 accumulation on the tensor pipe)",
+            "data": "synthetic",
+            "config": {"workload": WARM_WORKLOAD, "training_frames": n_frames, "training_samples": int(n),
+                       "frames_s": frames_s, "train_steps": args.warm_train_steps, "train_batch": args.warm_batch,
+                       "train_s": train_s, "loss_before": loss0, "loss_after": loss1,
+                       "gate": "each workload's configured gate, the same for the three starts",
+                       "results": res,
+                       "network_vs_cold_speedup": {k: v["network"]["fwd_pd_steps_per_s"] / v["cold"]["fwd_pd_steps_per_s"]
+                                                   for k, v in res.items()},
+                       "network_vs_constant_velocity_speedup": {
+                           k: v["network"]["fwd_pd_steps_per_s"] / v["constant_velocity"]["fwd_pd_steps_per_s"]
+                           for k, v in res.items()},
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "e2e": None, "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -606,7 +767,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="bar", choices=["bar", "batch", "contact", "block"])
+    ap.add_argument("--workload", default="bar", choices=["bar", "batch", "contact", "block", "warm"])
+    ap.add_argument("--warm-bars", type=int, default=18, help="warm workload: training bars (200 frames each)")
+    ap.add_argument("--warm-train-steps", type=int, default=3000)
+    ap.add_argument("--warm-batch", type=int, default=16384)
     ap.add_argument("--block-n", type=int, default=64, help="block workload: cells per edge")
     ap.add_argument("--block-steps", type=int, default=10, help="block workload: PD steps per rollout")
     ap.add_argument("--contact-steps", type=int, default=20,
@@ -633,6 +797,11 @@ def main():
     dev = torch.device("cuda", local_rank)
     if args.workload == "contact":
         run_contact(args, rank, world, local_rank, dev, dist)
+        if dist:
+            dist.destroy_process_group()
+        return
+    if args.workload == "warm":
+        run_warm(args, rank, world, local_rank, dev, dist)
         if dist:
             dist.destroy_process_group()
         return

@@ -523,7 +523,8 @@ void pd_mlp_destroy(pd_mlp* net);
 /* Training samples of one frame of a trajectory of the context's mesh:
  * raw features feat [n_v][7] of (x_{t-1}, x_t) and, if x_tp1 is given, raw
  * targets targ [n_v][3] = x_{t+1} - (2 x_t - x_{t-1}) (device arrays, every
- * vertex in order; pinned vertices give zero rows). Single instance. */
+ * vertex in order; pinned vertices give zero rows). A batch context takes the
+ * concatenated arrays of all its instances (one launch per instance). */
 int pd_mlp_sample(pd_ctx* ctx, const double* x_tm1, const double* x_t, const double* x_tp1, float* feat,
                   float* targ, void* stream);
 
@@ -531,6 +532,13 @@ int pd_mlp_sample(pd_ctx* ctx, const double* x_tm1, const double* x_t, const dou
  * FP32 parameters [PD_MLP_PARAMS] followed by the normalisation
  * [PD_MLP_NORM], bytes = 4 x (PD_MLP_PARAMS + PD_MLP_NORM), host memory. */
 int pd_mlp_load(pd_ctx* ctx, const void* weights, size_t bytes);
+
+/* Change the start of each step's iteration (pd_options.warm_start: 0 q_t,
+ * 1 the learned warm start, 2 constant-velocity extrapolation) without
+ * recreating or refactoring the context; 1 needs a loaded network. For a
+ * batch, every instance. Takes effect at the next rollout. Not part of the
+ * paper (its iteration starts from q_t, Alg. 1). */
+int pd_set_warm_start(pd_ctx* ctx, int32_t mode);
 
 /* The warm start as the rollout computes it: q0 [n_v][3] from x_t, x_{t-1}
  * (device arrays) with options.warm_start (1: the loaded network; 2 or 0:

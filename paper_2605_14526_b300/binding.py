@@ -104,6 +104,7 @@ def lib():
             "pd_get_stats": (c_int, [P, P]),
             "pd_solve": (c_int, [P, P, P, P]),
             "pd_local_rhs": (c_int, [P, P, P, P]),
+            "pd_set_warm_start": (c_int, [P, c_int32]),
             "pd_solve_noalloc": (c_int, [P, P, P, P]),
             "pd_profile": (c_int, [P, c_int32]),
             "pd_get_profile": (c_int, [P, P]),
@@ -465,6 +466,10 @@ def pd_mlp_sample(ctx, x_tm1, x_t, x_tp1, feat, targ, stream=None):
 def pd_mlp_load(ctx, blob):
     blob = np.ascontiguousarray(blob, dtype=np.float32)
     _check(ctx, lib().pd_mlp_load(ctx, _ptr(blob, np.float32), blob.nbytes))
+
+
+def pd_set_warm_start(ctx, mode):
+    _check(ctx, lib().pd_set_warm_start(ctx, int(mode)))
 
 
 def pd_warm_start(ctx, x_t, x_tm1, q0, stream=None):

@@ -451,6 +451,23 @@ int batch_get_mass(const pd_ctx* c, double* m) {
   return PD_OK;
 }
 
+int batch_size(const pd_ctx* c) { return c->batch ? c->batch->n : 1; }
+
+void batch_set_warm(pd_ctx* c, int mode) {
+  pd_batch& B = *c->batch;
+  for (pd_ctx* k : B.kids) {
+    k->opt.warm_start = mode;
+    k->d.warm = mode;
+  }
+  B.devs_dirty = true;
+}
+
+pd_ctx* batch_kid(const pd_ctx* c, int i, int64_t* v_off) {
+  const pd_batch& B = *c->batch;
+  if (v_off) *v_off = B.off[i].v;
+  return B.kids[i];
+}
+
 int batch_get_checkpoint(const pd_ctx* c, int t, double* q_host) {
   const pd_batch& B = *c->batch;
   if (!q_host || t < 0 || t > c->last_T || !B.ckpt) return PD_ERR_ARG;

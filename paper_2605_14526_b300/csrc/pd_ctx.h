@@ -103,6 +103,9 @@ int batch_reserve(pd_ctx* c, int T);
 int batch_factor(pd_ctx* c);
 int batch_get_mass(const pd_ctx* c, double* m);
 int batch_get_checkpoint(const pd_ctx* c, int t, double* q_host);
+int batch_size(const pd_ctx* c);                            // instances (1 without a batch)
+void batch_set_warm(pd_ctx* c, int mode);                   // warm_start of every instance
+pd_ctx* batch_kid(const pd_ctx* c, int i, int64_t* v_off);  // instance i and its first vertex
 int batch_get_tau(const pd_ctx* c, double* tau_host, int T);
 void batch_destroy(pd_ctx* c);
 // warm-start network blob -> device layout (pd_mlp.cu); buffers appended to owner

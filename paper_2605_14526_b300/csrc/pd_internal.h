@@ -85,8 +85,16 @@ enum Ticket {
 constexpr int kMlpIn = 7, kMlpH = 128, kMlpOut = 3;
 constexpr int kMlpWeights = kMlpIn * kMlpH + 2 * kMlpH * kMlpH + kMlpH * kMlpOut;
 constexpr int kMlpBiases = 3 * kMlpH + kMlpOut;
+// The same weights packed in the B-fragment order of mma.sync m16n8k16
+// (BF16): for layer l, k-step ks (16 inputs), n-tile nt (8 outputs) and lane,
+// one uint2 {W[16ks+2t, n] | W[16ks+2t+1, n] << 16, W[16ks+2t+8, n] | ...}
+// with t = lane % 4, n = 8 nt + lane / 4, zero beyond the layer's sizes;
+// layers padded to 16 x 128, 128 x 128, 128 x 128, 128 x 8.
+constexpr int kMlpFrag1 = 1 * 16 * 32, kMlpFragH = 8 * 16 * 32, kMlpFrag4 = 8 * 1 * 32;
+constexpr int kMlpFrags = kMlpFrag1 + 2 * kMlpFragH + kMlpFrag4;
 struct MlpDev {
   const uint16_t* w;   // [kMlpWeights]
+  const uint2* wf;     // [kMlpFrags] fragment-packed weights (tensor-core path)
   const float* b;      // [kMlpBiases]
   float fmean[kMlpIn], fscale[kMlpIn], oscale[kMlpOut];
 };

@@ -4,8 +4,9 @@
 // kernel (features and targets from a trajectory), the warm-start evaluation
 // used by the rollout, and attaching a trained network to a context.
 //
-// Training arithmetic is FP32 on CUDA cores: a minibatch of B samples costs
-// about 3 x 35k x B multiply-adds, a few microseconds per thousand samples.
+// The training GEMMs run on the tensor pipe (mma.sync in TF32 with 3xTF32
+// operand splitting, FP32-level accuracy); the elementwise parts on CUDA
+// cores. A minibatch of B samples costs about 3 x 35k x B multiply-adds.
 // Every reduction has a fixed order, so a training step is deterministic.
 #include <cuda_runtime.h>
 
@@ -51,15 +52,33 @@ __host__ __device__ inline float bf16_value(float x) {
 // ------------------------------------------------------------ kernels
 
 // C[M][N] (+)= sum_k A(m, k) B(k, n); A(m, k) = TA ? A[k lda + m] : A[m lda + k],
-// B(k, n) = TB ? B[n ldb + k] : B[k ldb + n]. 64 x 64 tiles, 16-deep slabs,
-// 256 threads with 4 x 4 outputs each; fixed summation order.
+// B(k, n) = TB ? B[n ldb + k] : B[k ldb + n]. On the tensor pipe: 64 x 64
+// tiles, 16-deep slabs staged in shared memory, 8 warps of 16 x 32 outputs,
+// mma.sync m16n8k8 in TF32 with each operand split into a TF32 value and its
+// TF32 remainder (big + small); the three products big x big, big x small and
+// small x big keep FP32-level accuracy ("3xTF32"). Fixed summation order.
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32_1688(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float* __restrict__ A, int lda,
                                               const float* __restrict__ B, int ldb, float* __restrict__ C, int ldc,
                                               int accumulate) {
-  __shared__ float As[16][64 + 1];
-  __shared__ float Bs[16][64 + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  __shared__ float As[16][64 + 8];   // rows of 72: the fragment reads hit 32 distinct banks
+  __shared__ float Bs[16][64 + 8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int wm = 16 * (warp >> 1), wn = 32 * (warp & 1);   // the warp's 16 x 32 outputs in the tile
   const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
   float acc[4][4] = {};
   for (int k0 = 0; k0 < K; k0 += 16) {
@@ -73,27 +92,35 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float* 
     }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      float a[4], b[4];
+    for (int k8 = 0; k8 < 16; k8 += 8) {
+      const float av[4] = {As[k8 + t][wm + g], As[k8 + t][wm + g + 8], As[k8 + t + 4][wm + g],
+                           As[k8 + t + 4][wm + g + 8]};
+      uint32_t abig[4], asmall[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+      for (int i = 0; i < 4; ++i) {
+        abig[i] = tf32_rna(av[i]);
+        asmall[i] = tf32_rna(av[i] - __uint_as_float(abig[i]));
+      }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      for (int j = 0; j < 4; ++j) {
+        const float b0v = Bs[k8 + t][wn + 8 * j + g], b1v = Bs[k8 + t + 4][wn + 8 * j + g];
+        const uint32_t b0 = tf32_rna(b0v), b1 = tf32_rna(b1v);
+        const uint32_t s0 = tf32_rna(b0v - __uint_as_float(b0)), s1 = tf32_rna(b1v - __uint_as_float(b1));
+        mma_tf32_1688(acc[j], asmall, b0, b1);
+        mma_tf32_1688(acc[j], abig, s0, s1);
+        mma_tf32_1688(acc[j], abig, b0, b1);
+      }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int j = 0; j < 4; ++j)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int m = m0 + ty * 4 + i, n = n0 + tx * 4 + j;
+    for (int i = 0; i < 4; ++i) {
+      const int m = m0 + wm + g + (i >= 2 ? 8 : 0), n = n0 + wn + 8 * j + 2 * t + (i & 1);
       if (m < M && n < N) {
         float* c = C + (size_t)m * ldc + n;
-        *c = accumulate ? *c + acc[i][j] : acc[i][j];
+        *c = accumulate ? *c + acc[j][i] : acc[j][i];
       }
     }
 }
@@ -195,17 +222,17 @@ __global__ void k_sample(pdk::Dev d, const double* xtm1, const double* xt, const
   feat[NI * (size_t)v + 6] = d.logE[v];
 }
 
-// q0 of the warm start for every vertex (one warp per vertex); pinned at X
+// q0 of the warm start for every vertex (the network on the tensor pipe, 16
+// vertices per warp); pinned vertices at X
 __global__ void k_warm_eval(pdk::Dev d, const double* xt, const double* xtm1, double* q0) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int v = warp; v < d.n_v; v += nwarps) {
-    if (d.pinned[v]) {
-      if (lane < 3) q0[3 * (size_t)v + lane] = d.X[3 * (size_t)v + lane];
-      continue;
-    }
-    pdk::warm_vertex(d, v, xt, xtm1, nullptr, q0, nullptr, lane);
+  for (int v0 = 16 * warp; v0 < d.n_v; v0 += 16 * nwarps) {
+    const int v = v0 + (lane & 15);
+    if (lane < 16 && v < d.n_v && d.pinned[v])
+      for (int i = 0; i < 3; ++i) q0[3 * (size_t)v + i] = d.X[3 * (size_t)v + i];
+    pdk::warm_tile(d, v0, xt, xtm1, nullptr, q0, nullptr, lane);
   }
 }
 
@@ -455,12 +482,35 @@ void pd_mlp_destroy(pd_mlp* net) {
 int pd_mlp_sample(pd_ctx* c, const double* x_tm1, const double* x_t, const double* x_tp1, float* feat, float* targ,
                   void* stream) {
   if (!c || !x_tm1 || !x_t || !feat) return PD_ERR_ARG;
-  if (c->batch) return fail(c, PD_ERR_ARG, "pd_mlp_sample is single-instance only");
   if (!c->factored) return fail(c, PD_ERR_NOT_FACTORED, "pd_factor must run before pd_mlp_sample");
   CK(cudaSetDevice(c->device));
+  if (c->batch) {   // the concatenated arrays of a batch: one launch per instance
+    for (int i = 0; i < batch_size(c); ++i) {
+      int64_t vo = 0;
+      const pd_ctx* k = batch_kid(c, i, &vo);
+      k_sample<<<blocks(k->n_v, 256), 256, 0, (cudaStream_t)stream>>>(
+          k->d, x_tm1 + 3 * vo, x_t + 3 * vo, x_tp1 ? x_tp1 + 3 * vo : nullptr, feat + (size_t)NI * vo,
+          targ ? targ + (size_t)NO * vo : nullptr);
+    }
+    CK(cudaGetLastError());
+    c->launches += batch_size(c);
+    return PD_OK;
+  }
   k_sample<<<blocks(c->n_v, 256), 256, 0, (cudaStream_t)stream>>>(c->d, x_tm1, x_t, x_tp1, feat, targ);
   CK(cudaGetLastError());
   c->launches += 1;
+  return PD_OK;
+}
+
+int pd_set_warm_start(pd_ctx* c, int32_t mode) {
+  if (!c) return PD_ERR_ARG;
+  if (mode < 0 || mode > 2) return fail(c, PD_ERR_ARG, "warm_start must be 0, 1 or 2");
+  if (mode != 0 && !c->opt.persistent) return fail(c, PD_ERR_ARG, "the warm start needs persistent launches");
+  if (mode == 1 && !(c->batch ? batch_has_mlp(c) : c->d.mlp.w != nullptr))
+    return fail(c, PD_ERR_ARG, "warm_start = 1 needs a network (pd_mlp_load)");
+  c->opt.warm_start = mode;
+  c->d.warm = mode;
+  if (c->batch) batch_set_warm(c, mode);
   return PD_OK;
 }
 
@@ -473,7 +523,7 @@ int pd_warm_start(pd_ctx* c, const double* x_t, const double* x_tm1, double* q0,
   pdk::Dev d = c->d;
   d.warm = c->opt.warm_start ? c->opt.warm_start : 1;
   if (d.warm == 1 && !d.mlp.w) return fail(c, PD_ERR_ARG, "no network loaded (pd_mlp_load)");
-  k_warm_eval<<<blocks(32 * (size_t)c->n_v, 256), 256, 0, (cudaStream_t)stream>>>(d, x_t, x_tm1, q0);
+  k_warm_eval<<<blocks(2 * (size_t)c->n_v + 32, 256), 256, 0, (cudaStream_t)stream>>>(d, x_t, x_tm1, q0);
   CK(cudaGetLastError());
   c->launches += 1;
   return PD_OK;
@@ -508,10 +558,33 @@ int mlp_upload(pd_ctx* c, const void* blob, size_t bytes, pdk::MlpDev* out, std:
     b[2 * H + j] = th[OB3 + j];
   }
   for (int j = 0; j < NO; ++j) b[3 * H + j] = th[OB4 + j];
+  // the tensor-core copy: B fragments of mma.sync m16n8k16 per layer
+  std::vector<uint2> wf(pdk::kMlpFrags);
+  {
+    size_t f = 0;
+    auto pack = [&](int ow, int K, int N, int ksteps, int ntiles) {
+      auto wv = [&](int k, int n) -> uint32_t { return (k < K && n < N) ? bf16_bits(th[ow + n * K + k]) : 0u; };
+      for (int ks = 0; ks < ksteps; ++ks)
+        for (int nt = 0; nt < ntiles; ++nt)
+          for (int lane = 0; lane < 32; ++lane) {
+            const int t = lane & 3, n = 8 * nt + (lane >> 2), k = 16 * ks + 2 * t;
+            wf[f++] = make_uint2(wv(k, n) | wv(k + 1, n) << 16, wv(k + 8, n) | wv(k + 9, n) << 16);
+          }
+    };
+    pack(OW1, NI, H, 1, 16);
+    pack(OW2, H, H, 8, 16);
+    pack(OW3, H, H, 8, 16);
+    pack(OW4, H, NO, 8, 1);
+  }
   uint16_t* wd = nullptr;
+  uint2* wfd = nullptr;
   float* bd = nullptr;
   CK(cudaMalloc(&wd, w.size() * sizeof(uint16_t)));
   owner.push_back(wd);
+  CK(cudaMalloc(&wfd, wf.size() * sizeof(uint2)));
+  owner.push_back(wfd);
+  CK(cudaMemcpy(wfd, wf.data(), wf.size() * sizeof(uint2), cudaMemcpyHostToDevice));
+  out->wf = wfd;
   CK(cudaMalloc(&bd, b.size() * sizeof(float)));
   owner.push_back(bd);
   CK(cudaMemcpy(wd, w.data(), w.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));

@@ -92,6 +92,10 @@ struct FinAA {
 __device__ __noinline__ void warm_vertex_call(const Dev& d, int v, const double* vin, int lane) {
   warm_vertex(d, v, d.qt, nullptr, vin, d.q, d.qprev, lane);
 }
+// the network on the tensor pipe: 16 vertices per warp
+__device__ __noinline__ void warm_tile_call(const Dev& d, int v0, const double* vin, int lane) {
+  warm_tile(d, v0, d.qt, nullptr, vin, d.q, d.qprev, lane);
+}
 
 template <typename T>
 __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a, const Team tm) {
@@ -170,7 +174,10 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
     bool warm_now = d.warm != 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
       if (warm_now) {
-        for (int v = gwarp; v < d.n_v; v += nwarps) warm_vertex_call(d, v, vin, lane);
+        if (d.warm == 1)   // network: 16 vertices per warp on the tensor pipe
+          for (int v0 = 16 * gwarp; v0 < d.n_v; v0 += 16 * nwarps) warm_tile_call(d, v0, vin, lane);
+        else               // constant velocity: no network
+          for (int v = gwarp; v < d.n_v; v += nwarps) warm_vertex_call(d, v, vin, lane);
         if (!(ok = grid_sync(d, tm))) break;
       }
       double pu[2] = {0.0, 0.0};   // step norms of the last update, reduced with the next assembly
