@@ -724,10 +724,15 @@ def run_warm(args, rank, world, local_rank, dev, dist):
     scenes = inputs.batch_meshes(seed=11 + rank)
     bc = binding.BatchContext(scenes)
     binding.pd_mlp_load(bc.ctx, blob)
-    res["batch64_T100"] = _warm_compare(binding, torch, bc.ctx, scenes[0].steps,
-                                        t(bc.concat([s.x0 for s in scenes]).reshape(-1, 3)),
-                                        t(bc.concat([s.v0 for s in scenes]).reshape(-1, 3)), None, 0, len(scenes), stream,
-                                        dev)
+    bx0 = t(bc.concat([s.x0 for s in scenes]).reshape(-1, 3))
+    bv0 = t(bc.concat([s.v0 for s in scenes]).reshape(-1, 3))
+    # the launch shape as the batch benchmark picks it: one cold rollout
+    # measures each instance's iterations, then the autotuner
+    bq, bv = torch.empty_like(bx0), torch.empty_like(bx0)
+    binding.pd_rollout(bc.ctx, scenes[0].steps, bx0, bv0, None, 0, bq, bv, stream)
+    binding.pd_autotune(bc.ctx, 10, bx0, bv0, None, 0, stream)
+    res["batch64_T100"] = _warm_compare(binding, torch, bc.ctx, scenes[0].steps, bx0, bv0, None, 0, len(scenes),
+                                        stream, dev)
     bc.close()
     if args.block_n > 0:
         sb = inputs.large_block(n=args.block_n, steps=args.block_steps, seed=5 + rank)

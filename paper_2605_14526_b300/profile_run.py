@@ -1,9 +1,16 @@
 """Short, fixed workloads for profiler captures (a few thousand launches).
 
   python -m paper_2605_14526_b300.profile_run --case bar --steps 2
+  python -m paper_2605_14526_b300.profile_run --case block --n 48 --repeat 3
+  python -m paper_2605_14526_b300.profile_run --case mlp --repeat 3
 
 Runs `steps` PD steps of the named workload forward and backward once as a
-warm-up and once more, so that a profiler can skip the first pass.
+warm-up and once more, so that a profiler can skip the first pass. The block
+case factors an n^3-cell block (solve mode chosen automatically: T from
+about 24^3 cells) and repeats one solve with the factor (pd_solve, one launch
+per separator-tree height and sweep in mode T) and one standalone local step
+(pd_local_rhs). The mlp case repeats training steps of the warm-start
+network and its evaluation on the bar (pd_warm_start), on seeded data.
 """
 from __future__ import annotations
 
@@ -26,15 +33,75 @@ CASES = {
 }
 
 
+def run_block(n, repeat):
+    sc = inputs.large_block(n=n, steps=1)
+    pd = binding.PDContext(sc)
+    st = binding.pd_get_stats(pd.ctx)
+    dev = "cuda:0"
+    rng = np.random.default_rng(1)
+    b = torch.as_tensor(rng.standard_normal((sc.n_v, 3)), device=dev)
+    q = torch.as_tensor(sc.X + 0.01 * rng.standard_normal(sc.X.shape), device=dev)
+    x, out = torch.empty_like(b), torch.empty_like(b)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for r in range(repeat):
+        ev[0].record()
+        binding.pd_solve(pd.ctx, b, x)
+        ev[1].record()
+        binding.pd_local_rhs(pd.ctx, q, out)
+        ev[2].record()
+        torch.cuda.synchronize()
+        print(f"repeat {r}: solve {ev[0].elapsed_time(ev[1]):.3f} ms, local step {ev[1].elapsed_time(ev[2]):.3f} ms")
+    print(f"block{n}: {sc.n_e} tets, solve mode {st.solve_mode}, {st.solve_levels} heights, "
+          f"{st.factor_nnz} stored entries, factor {st.factor_seconds:.1f} s")
+    pd.close()
+
+
+def run_mlp(repeat):
+    dev = "cuda:0"
+    rng = np.random.default_rng(3)
+    n = 1 << 16
+    feat = torch.as_tensor(rng.standard_normal((n, 7)).astype(np.float32), device=dev)
+    targ = torch.as_tensor(1e-3 * rng.standard_normal((n, 3)).astype(np.float32), device=dev)
+    net = binding.MLP(inputs.mlp_init(0), np.concatenate([np.zeros(7), np.ones(7), np.ones(3)]).astype(np.float32))
+    binding.pd_mlp_fit_normalization(net.net, feat, targ, n)
+    sc = inputs.hetero_bar(steps=1)
+    opt = binding.options_for(sc.solver)
+    pd = binding.PDContext(sc, opt)
+    for r in range(repeat):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        binding.pd_mlp_train_step(net.net, feat, targ, n, 1e-3, want_loss=False)
+        e1.record()
+        binding.pd_mlp_load(pd.ctx, net.blob())
+        xm = torch.as_tensor(sc.X, device=dev)
+        xt = xm + 1e-3
+        q0 = torch.empty_like(xm)
+        binding.pd_set_warm_start(pd.ctx, 1)
+        binding.pd_warm_start(pd.ctx, xt, xm, q0)
+        e2.record()
+        torch.cuda.synchronize()
+        print(f"repeat {r}: train step ({n} samples) {e0.elapsed_time(e1):.3f} ms, warm start + load "
+              f"{e1.elapsed_time(e2):.3f} ms")
+    pd.close()
+    net.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="bar", choices=sorted(CASES))
+    ap.add_argument("--case", default="bar", choices=sorted(CASES) + ["block", "mlp"])
+    ap.add_argument("--n", type=int, default=48, help="block case: cells per edge")
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--repeat", type=int, default=2)
     ap.add_argument("--phases", action="store_true", help="print device phase times of the forward rollout")
     ap.add_argument("--persistent", type=int, default=1)
     args = ap.parse_args()
     build()
+    if args.case == "block":
+        run_block(args.n, args.repeat)
+        return
+    if args.case == "mlp":
+        run_mlp(args.repeat)
+        return
     sc = CASES[args.case](args.steps)
     dev = "cuda:0"
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
