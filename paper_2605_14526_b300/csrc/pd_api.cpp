@@ -247,6 +247,7 @@ int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_o
   for (double** p : vecs)
     if ((r = dalloc(c, p, nv3))) return r;
   if ((r = dalloc(c, &d.bperm, 3 * (size_t)c->n_f)) || (r = dalloc(c, &d.y, 3 * (size_t)c->n_f))) return r;  // float2
+  if ((r = dalloc(c, &d.qhl, nv3))) return r;
   d.sq = c->sq;
   d.sv = c->sv;
   const int m = std::max(c->opt.aa_m, 1);
@@ -1166,7 +1167,7 @@ int pd_local_rhs(pd_ctx* c, const double* q, double* out, void* stream) {
   if (!is_device_ptr(q) || !is_device_ptr(out)) return fail(c, PD_ERR_ARG, "q and out must be device pointers");
   CK(cudaSetDevice(c->device));
   pdk::launch_local_rhs(c->d, (cudaStream_t)stream, q, out);
-  c->launches += 2;
+  c->launches += c->d.local_fp32 ? 3 : 2;
   CK(cudaGetLastError());
   return PD_OK;
 }

@@ -141,6 +141,30 @@ __device__ __forceinline__ void deform(const double* __restrict__ x, int4 tv, co
     for (int j = 0; j < 3; ++j) F[3 * i + j] = D[3 * i] * Bm[j] + D[3 * i + 1] * Bm[3 + j] + D[3 * i + 2] * Bm[6 + j];
 }
 
+// F from positions held as float pairs x = hi + lo (the FP32 local step):
+// the edge vectors (hi_a - hi_0) + (lo_a - lo_0) on the FP32 pipe. The high
+// parts of nearby vertices differ by an exactly representable amount
+// (Sterbenz), so each edge vector is the FP64 difference rounded to FP32, as
+// in deform(), without FP64 arithmetic in the element loop.
+__device__ __forceinline__ void deform_hl(const float2* __restrict__ xhl, int4 tv, const float* Bm, float* F) {
+  const int id[4] = {tv.x, tv.y, tv.z, tv.w};
+  float2 x0[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) x0[i] = xhl[3 * id[0] + i];
+  float D[9];
+#pragma unroll
+  for (int a = 1; a < 4; ++a)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float2 xa = xhl[3 * id[a] + i];
+      D[3 * i + a - 1] = __fadd_rn(__fsub_rn(xa.x, x0[i].x), __fsub_rn(xa.y, x0[i].y));
+    }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) F[3 * i + j] = D[3 * i] * Bm[j] + D[3 * i + 1] * Bm[3 + j] + D[3 * i + 2] * Bm[6 + j];
+}
+
 // the same from the four vertex positions already loaded
 template <typename T>
 __device__ __forceinline__ void deform_x(const double (&xv)[4][3], const T* Bm, T* F) {

@@ -45,6 +45,16 @@ __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
   return make_float2(h, __fsub_rn(l, __fsub_rn(h, s)));
 }
 
+// a + x for a plain float x (TwoSum of the high part, then renormalised)
+__device__ __forceinline__ float2 df_add_f(float2 a, float x) {
+  const float s = __fadd_rn(a.x, x);
+  const float bb = __fsub_rn(s, a.x);
+  const float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  const float l = __fadd_rn(a.y, err);
+  const float h = __fadd_rn(s, l);
+  return make_float2(h, __fsub_rn(l, __fsub_rn(h, s)));
+}
+
 __device__ __forceinline__ float2 df_shfl_xor(float2 a, int o) {
   return make_float2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o));
 }

@@ -182,6 +182,7 @@ struct Dev {
 
   // work vectors [n_v][3] unless noted
   double* q;        // current iterate q^k
+  float2* qhl;      // [n_v][3] the same as float pairs hi + lo (read by the FP32 local step; kept by q's writers)
   double* qprev;    // q^{k-1}
   double* qhat;
   double* gprev;

@@ -31,14 +31,20 @@ template <typename T>
 __global__ void __launch_bounds__(kTetBlock) k_local(Dev d, const double* x) {
   if (d.ctrl->done) return;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < d.n_e) local_item<T>(d, e, x);
+  if (e < d.n_e) local_item<T>(d, e, x, d.qhl);   // x is the iterate q, d.qhl its float pairs
 }
 
-// standalone local step (pd_local_rhs): every element, no iteration control
+// standalone local step (pd_local_rhs): the positions as float pairs first
+// (FP32 step), then every element, no iteration control
+__global__ void __launch_bounds__(kVtxBlock) k_split_hl(Dev d, const double* x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 3 * d.n_v) d.qhl[i] = df_split(x[i]);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kTetBlock) k_local_all(Dev d, const double* x) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < d.n_e) local_item<T>(d, e, x);
+  if (e < d.n_e) local_item<T>(d, e, x, sizeof(T) == 4 ? d.qhl : nullptr);
 }
 
 // the projection part of the right-hand side per vertex, sum_e w_e V_e G_e^T
@@ -55,9 +61,23 @@ __global__ void __launch_bounds__(kVtxBlock) k_rhs_out(Dev d, double* out) {
     return;
   }
   const T* cb = reinterpret_cast<const T*>(d.contrib);
-  double c0 = 0.0, c1 = 0.0, c2 = 0.0;
   int p = d.inc_ptr[v];
   const int end = d.inc_ptr[v + 1];
+  if constexpr (sizeof(T) == 4) {
+    // FP32 corner forces summed in double-float on the FP32 pipe
+    float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0;
+    for (; p < end; ++p) {
+      const float* f = cb + 3 * (size_t)d.inc_idx[p];
+      a0 = df_add_f(a0, f[0]);
+      a1 = df_add_f(a1, f[1]);
+      a2 = df_add_f(a2, f[2]);
+    }
+    o[0] = df_join(a0);
+    o[1] = df_join(a1);
+    o[2] = df_join(a2);
+    return;
+  }
+  double c0 = 0.0, c1 = 0.0, c2 = 0.0;
   for (; p + 3 < end; p += 4) {
     int ic[4];
 #pragma unroll
@@ -257,6 +277,7 @@ void launch_apply_inverse(const Dev& d, cudaStream_t s, const float2* xperm, flo
 
 void launch_local_rhs(const Dev& d, cudaStream_t s, const double* x, double* out) {
   if (d.local_fp32) {
+    k_split_hl<<<nblk(3 * d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d, x);
     k_local_all<float><<<nblk(d.n_e, kTetBlock), kTetBlock, 0, s>>>(d, x);
     k_rhs_out<float><<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d, out);
   } else {

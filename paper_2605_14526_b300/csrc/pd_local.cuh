@@ -8,13 +8,20 @@ namespace pdk {
 // Local step fused with the per-element part of the RHS scatter (Alg. 1,
 // eq. nh_prox / corotated projection, eq. A_basic). The prox Newton starts
 // from this element's sigma* of its previous local step when one is stored.
+// The FP32 step reads the positions as float pairs xhl when given (the
+// iterate's copy kept by its writers), else the FP64 positions x.
 template <typename T>
-__device__ __forceinline__ void local_item(const Dev& d, int e, const double* x) {
+__device__ __forceinline__ void local_item(const Dev& d, int e, const double* x, const float2* xhl = nullptr) {
   int4 tv;
   T Bm[9], coef;
   load_elem<T>(d, e, tv, Bm, coef);
   T F[9], U[9], V[9], sF[3], ss[3], P[9], c[12];
-  deform<T>(x, tv, Bm, F);
+  if constexpr (sizeof(T) == 4) {
+    if (xhl) deform_hl(xhl, tv, Bm, F);
+    else deform<T>(x, tv, Bm, F);
+  } else {
+    deform<T>(x, tv, Bm, F);
+  }
   svd3<T>(F, U, sF, V);
   if (d.model == 0) {
     ss[0] = ss[1] = ss[2] = T(1);

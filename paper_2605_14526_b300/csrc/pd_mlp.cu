@@ -70,10 +70,13 @@ __device__ __forceinline__ void mma_tf32_1688(float (&d)[4], const uint32_t (&a)
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// Split K: block z of the grid's third dimension takes k in [z kchunk,
+// (z + 1) kchunk) and, with part given, writes its partial product to
+// part[z][M][N] (summed afterwards in z order by k_splitk_sum).
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float* __restrict__ A, int lda,
                                               const float* __restrict__ B, int ldb, float* __restrict__ C, int ldc,
-                                              int accumulate) {
+                                              int accumulate, int kchunk, float* __restrict__ part) {
   __shared__ float As[16][64 + 8];   // rows of 72: the fragment reads hit 32 distinct banks
   __shared__ float Bs[16][64 + 8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -81,14 +84,15 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float* 
   const int wm = 16 * (warp >> 1), wn = 32 * (warp & 1);   // the warp's 16 x 32 outputs in the tile
   const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
   float acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += 16) {
+  const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+  for (int k0 = kbeg; k0 < kend; k0 += 16) {
     for (int i = threadIdx.x; i < 64 * 16; i += 256) {
       const int mm = i / 16, kk = i % 16;   // A tile element (m0 + mm, k0 + kk)
       const int m = m0 + mm, k = k0 + kk;
-      As[kk][mm] = (m < M && k < K) ? (TA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k]) : 0.f;
+      As[kk][mm] = (m < M && k < kend) ? (TA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k]) : 0.f;
       const int nn = i / 16, kb = i % 16;   // B tile element (k0 + kb, n0 + nn)
       const int n = n0 + nn, kq = k0 + kb;
-      Bs[kb][nn] = (n < N && kq < K) ? (TB ? B[(size_t)n * ldb + kq] : B[(size_t)kq * ldb + n]) : 0.f;
+      Bs[kb][nn] = (n < N && kq < kend) ? (TB ? B[(size_t)n * ldb + kq] : B[(size_t)kq * ldb + n]) : 0.f;
     }
     __syncthreads();
 #pragma unroll
@@ -119,10 +123,25 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float* 
     for (int i = 0; i < 4; ++i) {
       const int m = m0 + wm + g + (i >= 2 ? 8 : 0), n = n0 + wn + 8 * j + 2 * t + (i & 1);
       if (m < M && n < N) {
-        float* c = C + (size_t)m * ldc + n;
-        *c = accumulate ? *c + acc[j][i] : acc[j][i];
+        if (part) {
+          part[((size_t)blockIdx.z * M + m) * N + n] = acc[j][i];
+        } else {
+          float* c = C + (size_t)m * ldc + n;
+          *c = accumulate ? *c + acc[j][i] : acc[j][i];
+        }
       }
     }
+}
+
+// C (+)= sum over z of part[z] (fixed order)
+__global__ void k_splitk_sum(int M, int N, int splits, const float* __restrict__ part, float* C, int ldc,
+                             int accumulate) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M * N) return;
+  float v = 0.f;
+  for (int z = 0; z < splits; ++z) v += part[(size_t)z * M * N + i];
+  float* c = C + (size_t)(i / N) * ldc + i % N;
+  *c = accumulate ? *c + v : v;
 }
 
 __global__ void k_bias_act(float* Z, const float* b, int n, int N, int relu) {
@@ -238,11 +257,25 @@ __global__ void k_warm_eval(pdk::Dev d, const double* xt, const double* xtm1, do
 
 inline unsigned blocks(size_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
+constexpr int kSplitMax = 296;   // largest K split (partials of at most 128 x 128 each)
+
+// small M x N with a long K (the weight gradients: K = samples) is split
+// over K so that the grid fills the GPU; ws holds kSplitMax x M x N floats
 template <bool TA, bool TB>
 void gemm(cudaStream_t s, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
-          int acc = 0) {
-  dim3 grid((N + 63) / 64, (M + 63) / 64);
-  k_gemm<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, acc);
+          int acc = 0, float* ws = nullptr) {
+  const int tiles = ((N + 63) / 64) * ((M + 63) / 64);
+  int splits = ws && M * N <= 128 * 128 ? std::min(kSplitMax / std::max(tiles, 1), (K + 511) / 512) : 1;
+  if (splits < 2) {
+    dim3 grid((N + 63) / 64, (M + 63) / 64, 1);
+    k_gemm<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, acc, K, nullptr);
+    return;
+  }
+  const int kchunk = ((K + splits - 1) / splits + 15) / 16 * 16;
+  splits = (K + kchunk - 1) / kchunk;
+  dim3 grid((N + 63) / 64, (M + 63) / 64, splits);
+  k_gemm<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, 0, kchunk, ws);
+  k_splitk_sum<<<(M * N + 255) / 256, 256, 0, s>>>(M, N, splits, ws, C, ldc, acc);
 }
 
 }  // namespace
@@ -260,6 +293,7 @@ struct pd_mlp {
   float* ws = nullptr;      // per-sample workspace
   size_t ws_rows = 0;
   double* part = nullptr;   // loss partials
+  float* skws = nullptr;    // split-K partials of the weight gradients
   std::string err;
 };
 
@@ -336,22 +370,22 @@ int loss_grad(pd_mlp* net, const float* feat, const float* targ, int n, cudaStre
   const float* th = net->thq;
   float* g = net->grad;
   // output layer
-  gemm<true, false>(s, NO, H, n, a.dy, NO, a.a3, H, g + OW4, H);
+  gemm<true, false>(s, NO, H, n, a.dy, NO, a.a3, H, g + OW4, H, 0, net->skws);
   k_colsum<<<NO, 256, 0, s>>>(a.dy, n, NO, g + OB4);
   gemm<false, false>(s, n, H, NO, a.dy, NO, th + OW4, H, a.dA, H);
   k_relu_mask<<<blocks((size_t)n * H, 256), 256, 0, s>>>(a.dA, a.a3, (size_t)n * H);
   // layer 3
-  gemm<true, false>(s, H, H, n, a.dA, H, a.a2, H, g + OW3, H);
+  gemm<true, false>(s, H, H, n, a.dA, H, a.a2, H, g + OW3, H, 0, net->skws);
   k_colsum<<<H, 256, 0, s>>>(a.dA, n, H, g + OB3);
   gemm<false, false>(s, n, H, H, a.dA, H, th + OW3, H, a.dB, H);
   k_relu_mask<<<blocks((size_t)n * H, 256), 256, 0, s>>>(a.dB, a.a2, (size_t)n * H);
   // layer 2
-  gemm<true, false>(s, H, H, n, a.dB, H, a.a1, H, g + OW2, H);
+  gemm<true, false>(s, H, H, n, a.dB, H, a.a1, H, g + OW2, H, 0, net->skws);
   k_colsum<<<H, 256, 0, s>>>(a.dB, n, H, g + OB2);
   gemm<false, false>(s, n, H, H, a.dB, H, th + OW2, H, a.dA, H);
   k_relu_mask<<<blocks((size_t)n * H, 256), 256, 0, s>>>(a.dA, a.a1, (size_t)n * H);
   // layer 1
-  gemm<true, false>(s, H, NI, n, a.dA, H, a.a0, NI, g + OW1, NI);
+  gemm<true, false>(s, H, NI, n, a.dA, H, a.a0, NI, g + OW1, NI, 0, net->skws);
   k_colsum<<<H, 256, 0, s>>>(a.dA, n, H, g + OB1);
   if (cudaGetLastError() != cudaSuccess) return mfail(net, PD_ERR_CUDA, "network kernel launch failed");
   if (loss) {
@@ -386,6 +420,7 @@ int pd_mlp_create(const float* theta, const float* norm, pd_mlp** out) {
   }
   MCK(cudaMalloc(&net->norm_d, NNORM * sizeof(float)));
   MCK(cudaMalloc(&net->part, kLossBlocks * sizeof(double)));
+  MCK(cudaMalloc(&net->skws, (size_t)kSplitMax * H * H * sizeof(float)));
   MCK(cudaMemcpy(net->theta, theta, NP * sizeof(float), cudaMemcpyHostToDevice));
   MCK(cudaMemcpy(net->norm_d, net->norm, NNORM * sizeof(float), cudaMemcpyHostToDevice));
   k_quantize<<<blocks(NP, 256), 256>>>(net->theta, net->thq, NP);
@@ -476,6 +511,7 @@ void pd_mlp_destroy(pd_mlp* net) {
   for (float* b : bufs)
     if (b) cudaFree(b);
   if (net->part) cudaFree(net->part);
+  if (net->skws) cudaFree(net->skws);
   delete net;
 }
 

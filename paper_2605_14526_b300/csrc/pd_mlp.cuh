@@ -10,6 +10,7 @@
 
 #include <cstdint>
 
+#include "pd_df.cuh"
 #include "pd_internal.h"
 
 namespace pdk {
@@ -225,7 +226,7 @@ __device__ __forceinline__ void mlp_eval_tile(const MlpDev& m, const float* f, f
 // owns vertex v0 + r): q0 = 2 x_t - x_{t-1} + r as in warm_vertex, the
 // network on the tensor pipe.
 __device__ __forceinline__ void warm_tile(const Dev& d, int v0, const double* xt, const double* xtm1, const double* vt,
-                                          double* out1, double* out2, int lane) {
+                                          double* out1, double* out2, int lane, float2* out1_hl = nullptr) {
   const int v = v0 + (lane & 15);
   const bool mine = lane < 16 && v < d.n_v && !d.pinned[v];
   double x[3] = {0.0, 0.0, 0.0}, xm[3] = {0.0, 0.0, 0.0};
@@ -253,6 +254,7 @@ __device__ __forceinline__ void warm_tile(const Dev& d, int v0, const double* xt
   for (int i = 0; i < 3; ++i) {
     const double q0 = ok ? 2.0 * x[i] - xm[i] + (double)r[i] : x[i];
     out1[3 * (size_t)v + i] = q0;
+    if (out1_hl) out1_hl[3 * (size_t)v + i] = df_split(q0);
     if (out2) out2[3 * (size_t)v + i] = q0;
   }
 }
@@ -262,7 +264,7 @@ __device__ __forceinline__ void warm_tile(const Dev& d, int v0, const double* xt
 // or 0 (warm = 2, constant-velocity extrapolation). A non-finite network
 // output leaves the vertex at x_t. Pinned vertices are not written.
 __device__ __forceinline__ void warm_vertex(const Dev& d, int v, const double* xt, const double* xtm1, const double* vt,
-                                            double* out1, double* out2, int lane) {
+                                            double* out1, double* out2, int lane, float2* out1_hl = nullptr) {
   if (d.pinned[v]) return;
   double x[3], xm[3];
 #pragma unroll
@@ -290,6 +292,7 @@ __device__ __forceinline__ void warm_vertex(const Dev& d, int v, const double* x
     if (lane == i) {
       const double q0 = ok ? 2.0 * x[i] - xm[i] + (double)r[i] : x[i];
       out1[3 * (size_t)v + i] = q0;
+      if (out1_hl) out1_hl[3 * (size_t)v + i] = df_split(q0);
       if (out2) out2[3 * (size_t)v + i] = q0;
     }
 }

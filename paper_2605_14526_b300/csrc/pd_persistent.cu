@@ -30,7 +30,7 @@ template <typename T>
 __device__ __forceinline__ void local_any(const Dev& d, int e, bool hi) {
   if constexpr (sizeof(T) == 4) {
     if (hi) local_item_hi(d, e);
-    else local_item<float>(d, e, d.q);
+    else local_item<float>(d, e, d.q, d.qhl);
   } else {
     local_item<T>(d, e, d.q);
   }
@@ -90,11 +90,11 @@ struct FinAA {
 // the network warm start as a real call: it runs once per step and, inlined,
 // its registers would count against every phase of the body
 __device__ __noinline__ void warm_vertex_call(const Dev& d, int v, const double* vin, int lane) {
-  warm_vertex(d, v, d.qt, nullptr, vin, d.q, d.qprev, lane);
+  warm_vertex(d, v, d.qt, nullptr, vin, d.q, d.qprev, lane, d.qhl);
 }
 // the network on the tensor pipe: 16 vertices per warp
 __device__ __noinline__ void warm_tile_call(const Dev& d, int v0, const double* vin, int lane) {
-  warm_tile(d, v0, d.qt, nullptr, vin, d.q, d.qprev, lane);
+  warm_tile(d, v0, d.qt, nullptr, vin, d.q, d.qprev, lane, d.qhl);
 }
 
 template <typename T>
@@ -310,6 +310,7 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
         for (int i = 0; i < 3; ++i) {
           const size_t o = 3 * (size_t)v + i;
           d.q[o] = d.qt[o];
+          d.qhl[o] = df_split(d.qt[o]);
           d.qprev[o] = d.qt[o];
           d.gprev[o] = 0.0;
         }

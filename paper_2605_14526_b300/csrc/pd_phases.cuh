@@ -84,6 +84,7 @@ __device__ __forceinline__ void step_begin_item(const Dev& d, int v, const doubl
   for (int i = 0; i < 3; ++i) {
     d.qt[3 * v + i] = q[i];
     d.q[3 * v + i] = q[i];
+    d.qhl[3 * v + i] = df_split(q[i]);
     d.qprev[3 * v + i] = q[i];
     d.gprev[3 * v + i] = 0.0;
     d.b0[3 * v + i] = b0[i];
@@ -115,14 +116,32 @@ __device__ __forceinline__ void assemble_warp(const Dev& d, int v, int k, double
   if (d.pinned[v]) return;
   const T* cb = reinterpret_cast<const T*>(d.contrib);
   const int beg = d.inc_ptr[v], end = d.inc_ptr[v + 1];
-  double c[3] = {0.0, 0.0, 0.0};
-  for (int p = beg + lane; p < end; p += 32) {
-    const int ic = d.inc_idx[p];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) c[i] += (double)cb[3 * (size_t)ic + i];
-  }
   int i;
-  const double sum = warp_sum_scatter<3>(c, lane, i);   // component i in lanes 8i .. 8i+7
+  double sum;
+  if constexpr (sizeof(T) == 4) {
+    // FP32 corner forces summed in double-float on the FP32 pipe (TwoSum:
+    // error about 2^-44 of the sum of magnitudes, below the forces' own
+    // FP32 rounding), one conversion to FP64 per component
+    float2 c[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    for (int p = beg + lane; p < end; p += 32) {
+      const int ic = d.inc_idx[p];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) c[j] = df_add_f(c[j], cb[3 * (size_t)ic + j]);
+    }
+    i = lane >> 3;
+    float2 s3[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) s3[j] = df_warp_sum(c[j]);
+    sum = i == 0 ? df_join(s3[0]) : (i == 1 ? df_join(s3[1]) : df_join(s3[2]));
+  } else {
+    double c[3] = {0.0, 0.0, 0.0};
+    for (int p = beg + lane; p < end; p += 32) {
+      const int ic = d.inc_idx[p];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) c[j] += (double)cb[3 * (size_t)ic + j];
+    }
+    sum = warp_sum_scatter<3>(c, lane, i);   // component i in lanes 8i .. 8i+7
+  }
   if ((lane & 7) != 0 || i >= 3) return;
   const size_t o = 3 * (size_t)v + i;
   const double acc = d.b0[o] + sum;
@@ -550,6 +569,7 @@ __device__ __forceinline__ void update_comp(const Dev& d, size_t o, int use_hat,
   part[1] += qo * qo;
   d.qprev[o] = qo;
   d.q[o] = qn;
+  d.qhl[o] = df_split(qn);
   d.bprev[o] = d.b[o];
 }
 

@@ -10,6 +10,8 @@ inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
 // product and sum is fused behind the code's back)
 struct float2 { float x, y; };
 struct int4 { int x, y, z, w; };
+struct int2 { int x, y; };
+struct uint2 { unsigned x, y; };
 inline float2 make_float2(float x, float y) { return float2{x, y}; }
 inline float __double2float_rn(double x) { return (float)x; }
 inline float __fmul_rn(float a, float b) { return a * b; }

@@ -35,8 +35,17 @@ void local_step_host(int fp64, int model, int n_e, const int* tets, const double
     d.contrib = out;
     for (int e = 0; e < n_e; ++e) local_item<double>(d, e, x);
   } else {
+    // the FP32 step reads the positions as float pairs (hi, lo), as the
+    // iterate's writers keep them on the device
+    int n_v = 0;
+    for (int i = 0; i < 4 * n_e; ++i) n_v = tets[i] + 1 > n_v ? tets[i] + 1 : n_v;
+    std::vector<float2> xhl(3 * (size_t)n_v);
+    for (size_t i = 0; i < xhl.size(); ++i) {
+      const float h = (float)x[i];
+      xhl[i] = make_float2(h, (float)(x[i] - (double)h));
+    }
     d.contrib = c32.data();
-    for (int e = 0; e < n_e; ++e) local_item<float>(d, e, x);
+    for (int e = 0; e < n_e; ++e) local_item<float>(d, e, x, xhl.data());
     for (size_t i = 0; i < c32.size(); ++i) out[i] = c32[i];
   }
 }
