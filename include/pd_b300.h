@@ -45,7 +45,13 @@ typedef enum {
   PD_ERR_TOO_LARGE = 11     /* a size exceeds a documented limit */
 } pd_status;
 
-enum { PD_COROTATED = 0, PD_NEOHOOKEAN = 1 };
+/* Energies (Sec. 4.1, Sec. 7.2): corotated rotation step (w_e = 2 mu_e);
+ * Neo-Hookean stretch prox (w_e = 2 mu_e + lambda_e); the corotated + volume
+ * composite: the rotation step with w_0 = 2 mu_e plus a volume step with
+ * w_1 = lambda_e, the closest point of the unit-determinant set in stretch
+ * space (sigma_1 sigma_2 sigma_3 = 1), both in the one operator A (weight
+ * w_0 + w_1) and in b. */
+enum { PD_COROTATED = 0, PD_NEOHOOKEAN = 1, PD_COROT_VOLUME = 2 };
 enum { PD_TR_ADAPT = 0, PD_TR_NONE = 1, PD_TR_CLAMP = 2, PD_TR_ABS = 3 };
 /* How every A^-1 application is computed (pd_options.solve_mode). */
 enum { PD_SOLVE_AUTO = 0, PD_SOLVE_S = 1, PD_SOLVE_T = 2 };
@@ -60,7 +66,7 @@ typedef struct {
 
 /* Material (Sec. 3.1 eq. lame; Sec. 4.4 eq. rayleigh), copied by pd_create. */
 typedef struct {
-  int32_t model;          /* PD_COROTATED | PD_NEOHOOKEAN */
+  int32_t model;          /* PD_COROTATED | PD_NEOHOOKEAN | PD_COROT_VOLUME */
   const double* E;        /* [n_e] Young's modulus per element (Pa), > 0 */
   double nu;              /* Poisson ratio shared by all elements, in (-1, 0.5) */
   double density;         /* kg/m^3; lumped mass density*V_e/4 per corner */

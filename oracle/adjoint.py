@@ -31,7 +31,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from . import fem, prox
-from .solver import Problem, local_step
+from .solver import Problem, local_step, rotation_share
 
 
 def local_jacobian(pb: Problem, q, tau: float, unfiltered: bool = False):
@@ -41,6 +41,15 @@ def local_jacobian(pb: Problem, q, tau: float, unfiltered: bool = False):
     if pb.model == "corotated":
         z = np.zeros((n, 3, 3))
         return prox.dp_dF_matrix(U, sF, V, ss, z, z, corot=True), 0
+    if pb.model == "corotated_volume":
+        # sigma* = a + (1 - a) sigma_v(sigma_F): the diagonal response is
+        # (1 - a) d sigma_v/d sigma_F of the volume step; no prox Hessian to
+        # filter (the trust region acts on the Neo-Hookean prox only)
+        F = fem.deformation_gradient(pb.rest, pb.tets, q)
+        a = rotation_share(pb)
+        _, (_, _, _, _, sv, nu) = prox.corot_volume_project(F, a)
+        Jd = (1.0 - a)[:, None, None] * prox.volume_sigma_jacobian(sv, nu)
+        return prox.dp_dF_matrix(U, sF, V, ss, Jd, Jd, corot=False), 0
     Jf, Jraw, n_indef = prox.filtered_sigma_jacobian(ss, pb.mat.mu_bar, pb.mat.lam_bar, pb.mat.k_bar, tau)
     Jd = Jraw if unfiltered else Jf
     return prox.dp_dF_matrix(U, sF, V, ss, Jd, Jraw, corot=False), n_indef
@@ -81,6 +90,7 @@ class StepGrad:
     dk_bar: float
     mu: np.ndarray
     n_indef: int
+    dw1: np.ndarray = None   # composite: dL/dw_1 of the volume step (dw is then dL/dw_0)
 
 
 def adjoint_solve(pb: Problem, q_star, tau: float, qbar_free):
@@ -94,7 +104,7 @@ def adjoint_solve(pb: Problem, q_star, tau: float, qbar_free):
 
 def mean_sensitivities(pb: Problem, q_star, mu_full, tau: float):
     """dL/d(mu_bar, lambda_bar, k_bar) = sum_e w_e V_e <G_e mu, dp_e/d theta>."""
-    if pb.model == "corotated":
+    if pb.model in ("corotated", "corotated_volume"):   # no mesh means inside the projections
         return 0.0, 0.0, 0.0
     _, (U, sF, V, ss) = local_step(pb, q_star)
     Jf, _, _ = prox.filtered_sigma_jacobian(ss, pb.mat.mu_bar, pb.mat.lam_bar, pb.mat.k_bar, tau)
@@ -129,27 +139,45 @@ def route_step(pb: Problem, q_t, q_star, tau: float, mu, vbar_next) -> StepGrad:
     dq_t = (1.0 + pb.alpha * h) * m / h ** 2 * mu + (pb.B @ mu) / h - vbar_next / h
     dv_t = m / h * mu
     df = mu.copy()
-    P, _ = local_step(pb, q_star)
+    P, (U, _, V, _) = local_step(pb, q_star)
     F = fem.deformation_gradient(pb.rest, pb.tets, q_star)
     Gmu = fem.deformation_gradient(pb.rest, pb.tets, mu)
-    dw = pb.rest.vol * np.einsum("nij,nij->n", Gmu, P - F)
+    dw1 = None
+    if pb.model == "corotated_volume":
+        # b carries w_0 V G^T R + w_1 V G^T p_vol and A carries (w_0 + w_1):
+        # one sensitivity per weight
+        _, (_, _, _, _, sv, _) = prox.corot_volume_project(F, rotation_share(pb))
+        R = np.einsum("nij,nkj->nik", U, V)
+        Pv = prox.compose(U, sv, V)
+        dw = pb.rest.vol * np.einsum("nij,nij->n", Gmu, R - F)
+        dw1 = pb.rest.vol * np.einsum("nij,nij->n", Gmu, Pv - F)
+    else:
+        dw = pb.rest.vol * np.einsum("nij,nij->n", Gmu, P - F)
     Fd = fem.deformation_gradient(pb.rest, pb.tets, q_star - q_t)
     dbeta = -pb.rest.vol / h * np.einsum("nij,nij->n", Gmu, Fd)
     dmu, dlam, dk = mean_sensitivities(pb, q_star, mu, tau)
     for arr in (dq_t, dv_t, df):
         arr[pb.fixed] = 0.0
-    _, n_indef = local_jacobian(pb, q_star, tau) if pb.model != "corotated" else (None, 0)
-    return StepGrad(dq_t, dv_t, df, dw, dbeta, dmu, dlam, dk, mu, n_indef)
+    _, n_indef = local_jacobian(pb, q_star, tau) if pb.model == "neohookean" else (None, 0)
+    return StepGrad(dq_t, dv_t, df, dw, dbeta, dmu, dlam, dk, mu, n_indef, dw1)
 
 
-def chain_material(pb: Problem, dw, dbeta, dmu_bar, dlam_bar, dk_bar, paper_literal: bool = False):
-    """dL/dE_e and dL/dnu from the weight, damping and mean sensitivities."""
+def chain_material(pb: Problem, dw, dbeta, dmu_bar, dlam_bar, dk_bar, paper_literal: bool = False, dw1=None):
+    """dL/dE_e and dL/dnu from the weight, damping and mean sensitivities
+    (the composite: dw = dL/dw_0 with w_0 = 2 mu, dw1 = dL/dw_1 with
+    w_1 = lambda; Sec. 7.2 and eq. lame)."""
     E, nu = pb.E, pb.nu
     n = E.shape[0]
     dmu_dE = 1.0 / (2.0 * (1.0 + nu)) * np.ones(n)
     dlam_dE = nu / ((1.0 + nu) * (1.0 - 2.0 * nu)) * np.ones(n)
     dmu_dnu = -E / (2.0 * (1.0 + nu) ** 2)
     dlam_dnu = E * (1.0 + 2.0 * nu ** 2) / ((1.0 + nu) * (1.0 - 2.0 * nu)) ** 2
+    if pb.model == "corotated_volume":
+        dw1 = np.zeros(n) if dw1 is None else dw1
+        cb = pb.beta0 / pb.mat.mu_ref
+        dE = 2.0 * dw * dmu_dE + dw1 * dlam_dE + dbeta * cb * dmu_dE
+        dnu = float(np.sum(2.0 * dw * dmu_dnu + dw1 * dlam_dnu + dbeta * cb * dmu_dnu))
+        return dE, dnu
     nh = pb.model != "corotated"
     dw_dE = 2.0 * dmu_dE + (dlam_dE if nh else 0.0)
     dw_dnu = 2.0 * dmu_dnu + (dlam_dnu if nh else 0.0)
@@ -180,6 +208,7 @@ def rollout_backward(pb: Problem, records, dqT, dvT, paper_literal: bool = False
     vbar[pb.fixed] = 0.0
     n_e = pb.tets.shape[0]
     dw_tot = np.zeros(n_e)
+    dw1_tot = np.zeros(n_e)
     db_tot = np.zeros(n_e)
     dmu = dlam = dk = 0.0
     dfs = []
@@ -187,12 +216,14 @@ def rollout_backward(pb: Problem, records, dqT, dvT, paper_literal: bool = False
         g = backward_step(pb, rec.q_t, rec.q_next, rec.tau, qbar, vbar)
         qbar, vbar = g.dq_t, g.dv_t
         dw_tot += g.dw
+        if g.dw1 is not None:
+            dw1_tot += g.dw1
         db_tot += g.dbeta
         dmu += g.dmu_bar
         dlam += g.dlam_bar
         dk += g.dk_bar
         dfs.append(g.df_ext)
-    dE, dnu = chain_material(pb, dw_tot, db_tot, dmu, dlam, dk, paper_literal)
+    dE, dnu = chain_material(pb, dw_tot, db_tot, dmu, dlam, dk, paper_literal, dw1_tot)
     return RolloutGrad(qbar, vbar, dE, dnu, np.stack(dfs[::-1]), dw_tot)
 
 

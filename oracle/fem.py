@@ -81,6 +81,9 @@ def material(E: np.ndarray, nu: float, model: str, beta0: float, mu_ref: float |
     caller may pass a frozen mu_ref (the value fixed when A was factored).
     """
     mu, lam = lame(np.asarray(E, dtype=np.float64), nu)
+    # corotated: rotation step only; Neo-Hookean: the single-energy weight;
+    # corotated + volume composite: rotation step w_0 = 2 mu plus volume step
+    # w_1 = lambda, registered together (Sec. 7.2), A carries w_0 + w_1
     w = 2.0 * mu if model == "corotated" else 2.0 * mu + lam
     if mu_ref is None:
         mu_ref = float(mu.max())

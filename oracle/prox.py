@@ -147,6 +147,73 @@ def nh_project(F: np.ndarray, mu_bar: float, lam_bar: float, k_bar: float):
     return compose(U, ss, V), (U, sF, V, ss)
 
 
+# ----------------------------------------------------------- volume step
+
+def _grad_J(s):
+    """Gradient of J = s_1 s_2 s_3 in stretch space."""
+    return np.stack([s[:, 1] * s[:, 2], s[:, 0] * s[:, 2], s[:, 0] * s[:, 1]], axis=1)
+
+
+def _kkt(s, nu):
+    """[[I + nu Hess J, grad J], [grad J^T, 0]] per element, [n,4,4]."""
+    n = s.shape[0]
+    K = np.zeros((n, 4, 4))
+    K[:, :3, :3] = np.eye(3)
+    for i in range(3):
+        for j in range(3):
+            if i != j:
+                k = 3 - i - j
+                K[:, i, j] += nu * s[:, k]
+    g = _grad_J(s)
+    K[:, :3, 3] = g
+    K[:, 3, :3] = g
+    return K
+
+
+def volume_project_sigma(sF: np.ndarray, tol: float = 1e-14, max_iter: int = 60):
+    """The volume step of the corotated + volume composite (Sec. 4.1, the
+    quadratic (J - 1)^2 volume step that pairs with the corotated rotation
+    step; Sec. 7.2 weights w_1 = lambda): the closest point of the unit
+    determinant set in stretch space,
+        sigma* = argmin 1/2 ||sigma - sigma_F||^2  s.t.  sigma_1 sigma_2 sigma_3 = 1,
+    so that p* = U diag(sigma*) V^T is the closest matrix with det = 1 to F.
+    Newton on the Lagrange system (sigma - sigma_F + nu grad J = 0, J = 1)
+    from max(sigma_F, 1e-3) scaled onto J = 1 (the stationary point in the
+    positive octant; an inverted element's negative stretch is pulled back).
+    Returns (sigma*, nu, iterations)."""
+    s = np.maximum(sF, 1e-3)
+    s = s / np.cbrt(np.prod(s, axis=1))[:, None]
+    g = _grad_J(s)
+    nu = -np.sum((s - sF) * g, axis=1) / np.sum(g * g, axis=1)
+    it = 0
+    for it in range(1, max_iter + 1):
+        g = _grad_J(s)
+        r = np.concatenate([s - sF + nu[:, None] * g, (np.prod(s, axis=1) - 1.0)[:, None]], axis=1)
+        if np.abs(r).max() <= tol * max(1.0, np.abs(sF).max()):
+            break
+        d = np.linalg.solve(_kkt(s, nu), -r[:, :, None])[:, :, 0]
+        s = s + d[:, :3]
+        nu = nu + d[:, 3]
+    return s, nu, it
+
+
+def volume_sigma_jacobian(s: np.ndarray, nu: np.ndarray) -> np.ndarray:
+    """d sigma*/d sigma_F of the volume step, by implicit differentiation of
+    its Lagrange system: the 3 x 3 leading block of the inverse KKT matrix."""
+    return np.linalg.inv(_kkt(s, nu))[:, :3, :3]
+
+
+def corot_volume_project(F: np.ndarray, a: np.ndarray):
+    """The composite's per-element projection p = (w_0 R + w_1 p_vol)/(w_0 + w_1)
+    with a = w_0/(w_0 + w_1): since R = U V^T and p_vol = U diag(sigma_v) V^T
+    share the SVD of F, p = U diag(a + (1 - a) sigma_v) V^T. Returns p and
+    (U, sigma_F, V, sigma*, sigma_v, nu)."""
+    U, sF, V = svd_rv(F)
+    sv, nu, _ = volume_project_sigma(sF)
+    ss = a[:, None] + (1.0 - a[:, None]) * sv
+    return compose(U, ss, V), (U, sF, V, ss, sv, nu)
+
+
 # ------------------------------------------------------- trust-region filter
 
 def tr_blend(H: np.ndarray, tau: float) -> np.ndarray:

@@ -96,7 +96,15 @@ def local_step(pb: Problem, q):
     if pb.model == "corotated":
         U, sF, V = prox.svd_rv(F)
         return np.einsum("nij,nkj->nik", U, V), (U, sF, V, np.ones_like(sF))
+    if pb.model == "corotated_volume":
+        P, (U, sF, V, ss, _, _) = prox.corot_volume_project(F, rotation_share(pb))
+        return P, (U, sF, V, ss)
     return prox.nh_project(F, pb.mat.mu_bar, pb.mat.lam_bar, pb.mat.k_bar)
+
+
+def rotation_share(pb: Problem) -> np.ndarray:
+    """a_e = w_0/(w_0 + w_1) = 2 mu_e/(2 mu_e + lambda_e) of the composite."""
+    return 2.0 * pb.mat.mu / (2.0 * pb.mat.mu + pb.mat.lam)
 
 
 def rhs(pb: Problem, b0, q):
@@ -291,6 +299,15 @@ def pd_energy(pb: Problem, q, q_t, q_tilde):
     val += 0.5 / pb.h * float(np.sum(dd * (pb.alpha * m * dd + pb.B @ dd)))
     P, (U, sF, V, ss) = local_step(pb, q)
     F = fem.deformation_gradient(pb.rest, pb.tets, q)
+    if pb.model == "corotated_volume":
+        # w_0/2 dist^2(F, SO(3)) + w_1/2 dist^2(F, {det = 1}), each a
+        # minimum over its own projection
+        w0, w1 = 2.0 * pb.mat.mu, pb.mat.lam
+        _, (_, _, _, _, sv, _) = prox.corot_volume_project(F, rotation_share(pb))
+        R = np.einsum("nij,nkj->nik", U, V)
+        Pv = prox.compose(U, sv, V)
+        el = 0.5 * (w0 * np.einsum("nij,nij->n", F - R, F - R) + w1 * np.einsum("nij,nij->n", F - Pv, F - Pv))
+        return val + float(np.sum(pb.rest.vol * el))
     el = 0.5 * np.einsum("nij,nij->n", F - P, F - P)
     if pb.model != "corotated":
         el = el + prox.nh_psi_sigma(ss, pb.mat.mu_bar, pb.mat.lam_bar) / pb.mat.k_bar

@@ -21,7 +21,8 @@ PD_OK = 0
 STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_MESH", 3: "PD_ERR_NOT_FACTORED", 4: "PD_ERR_NOT_SPD",
           5: "PD_ERR_NOT_CONVERGED", 6: "PD_ERR_NUMERIC", 7: "PD_ERR_TIMEOUT", 8: "PD_ERR_CUDA",
           9: "PD_ERR_OOM", 10: "PD_ERR_NO_CHECKPOINT", 11: "PD_ERR_TOO_LARGE"}
-PD_COROTATED, PD_NEOHOOKEAN = 0, 1
+PD_COROTATED, PD_NEOHOOKEAN, PD_COROT_VOLUME = 0, 1, 2
+MODELS = {"corotated": PD_COROTATED, "neohookean": PD_NEOHOOKEAN, "corotated_volume": PD_COROT_VOLUME}
 PD_TR_ADAPT, PD_TR_NONE, PD_TR_CLAMP, PD_TR_ABS = 0, 1, 2, 3
 PD_SOLVE_AUTO, PD_SOLVE_S, PD_SOLVE_T = 0, 1, 2
 
@@ -326,7 +327,7 @@ def _mesh_material(scene):
     tets = np.ascontiguousarray(scene.tets, dtype=np.int32)
     E = np.ascontiguousarray(scene.E, dtype=np.float64)
     pin = np.ascontiguousarray(scene.pinned, dtype=np.uint8)
-    model = PD_COROTATED if scene.model == "corotated" else PD_NEOHOOKEAN
+    model = MODELS[scene.model]
     mesh = pd_mesh(int(X.shape[0]), int(tets.shape[0]), _ptr(X), _ptr(tets, np.int32), _ptr(pin, np.uint8))
     mat = pd_material(model, _ptr(E), float(scene.nu), float(scene.density), float(scene.alpha), float(scene.beta0),
                       (c_double * 3)(*[float(g) for g in scene.gravity]))
@@ -527,7 +528,7 @@ class PDContext:
     def __init__(self, scene, options: pd_options | None = None, factor: bool = True):
         self.scene = scene
         self.options = options or options_for(scene.solver)
-        model = PD_COROTATED if scene.model == "corotated" else PD_NEOHOOKEAN
+        model = MODELS[scene.model]
         self.ctx = pd_create(scene.X, scene.tets, scene.pinned, scene.E, model, scene.nu, scene.density,
                              scene.alpha, scene.beta0, scene.gravity, scene.dt, self.options)
         self.n_v, self.n_e = scene.n_v, scene.n_e

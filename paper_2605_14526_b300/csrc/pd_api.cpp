@@ -154,7 +154,7 @@ int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_o
   if (!mesh || !mat || !mesh->X || !mesh->tets || !mat->E) return PD_ERR_ARG;
   if (mesh->n_v < 4 || mesh->n_e < 1 || !(dt > 0)) return PD_ERR_ARG;
   if (!(mat->nu > -1.0 && mat->nu < 0.5) || !(mat->density > 0)) return PD_ERR_ARG;
-  if (mat->model != PD_COROTATED && mat->model != PD_NEOHOOKEAN) return PD_ERR_ARG;
+  if (mat->model != PD_COROTATED && mat->model != PD_NEOHOOKEAN && mat->model != PD_COROT_VOLUME) return PD_ERR_ARG;
   c = new pd_ctx();
   c->n_v = mesh->n_v;
   c->n_e = mesh->n_e;
@@ -264,7 +264,7 @@ int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_o
   if ((r = dalloc(c, &d.red, std::max((size_t)pdk::max_reduction_blocks(c->n_v, c->n_e) * pdk::kRed,
                                       (size_t)2 * pdk::kRedRep * pdk::kRedRows * pdk::kRedTeam))))
     return r;
-  if ((r = dalloc(c, &d.dw, c->n_e)) || (r = dalloc(c, &d.dbeta, c->n_e))) return r;
+  if ((r = dalloc(c, &d.dw, c->n_e)) || (r = dalloc(c, &d.dw1, c->n_e)) || (r = dalloc(c, &d.dbeta, c->n_e))) return r;
   if ((r = dalloc(c, &d.ctrl, 1))) return r;
   CK(cudaMemset(d.ctrl, 0, sizeof(Ctrl)));
   CK(cudaMemset(d.dQG, 0, sizeof(double) * m * nv3));
@@ -341,7 +341,7 @@ int pd_factor(pd_ctx* c) {
   for (int e = 0; e < n_e; ++e) {
     mu[e] = c->E[e] / (2.0 * (1.0 + c->nu));
     lam[e] = c->E[e] * c->nu / ((1.0 + c->nu) * (1.0 - 2.0 * c->nu));
-    w[e] = 2.0 * mu[e] + (c->model == PD_NEOHOOKEAN ? lam[e] : 0.0);
+    w[e] = 2.0 * mu[e] + (c->model != PD_COROTATED ? lam[e] : 0.0);   // composite: w_0 + w_1 = 2 mu + lambda
     mu_ref = std::max(mu_ref, mu[e]);
     mu_bar += mu[e];
     lam_bar += lam[e];
@@ -588,6 +588,7 @@ int pd_factor(pd_ctx* c) {
   d.eps_tr = c->opt.eps_tr; d.adj_tol = c->opt.adj_tol;
   for (int i = 0; i < 3; ++i) d.g[i] = c->g[i];
   d.mu_bar = mu_bar; d.lam_bar = lam_bar; d.k_bar = k_bar; d.mu_ref = mu_ref; d.beta0 = c->beta0; d.nu = c->nu;
+  d.rot_share = (1.0 - 2.0 * c->nu) / (1.0 - c->nu);   // 2 mu / (2 mu + lambda) for any E
   // contacts: candidates in elimination order, W = (L_A^-1)_CC by host solves
   d.n_con = 0;
   if (!c->con_ground.empty() || !c->con_box.empty()) {

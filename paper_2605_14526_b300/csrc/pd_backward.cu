@@ -39,6 +39,7 @@ struct BwdState {
 __device__ __forceinline__ void bwd_begin_item(const Dev& d, int i, const double* dqT, const double* dvT) {
   if (i < d.n_e) {
     d.dw[i] = 0.0;
+    d.dw1[i] = 0.0;
     d.dbeta[i] = 0.0;
   }
   if (i < d.n_v) {
@@ -240,13 +241,19 @@ __device__ __forceinline__ void route_elem_item(const Dev& d, int e, const doubl
   deform<double>(qt, tv, Bm, Ft);
   double gb = 0.0;
   for (int i = 0; i < 9; ++i) gb += Gm[i] * (Fs[i] - Ft[i]);
-  double U[9], V[9], sf[3], ss[3];
+  double U[9], V[9], sf[3], ss[3], sv[3] = {1.0, 1.0, 1.0};
   svd3<double>(Fs, U, sf, V);
   NHMean<double> m{d.mu_bar, d.lam_bar, d.k_bar};
   if (d.model == 1) {
     nh_prox<double>(sf, m, ss);
   } else {
+    // corotated, and the composite's rotation weight: p = R; the composite's
+    // volume weight takes p_vol = U diag(sigma_v) V^T below
     ss[0] = ss[1] = ss[2] = 1.0;
+    if (d.model == 2) {
+      double nu;
+      vol_project<double>(sf, sv, nu);
+    }
   }
   double Md[3];  // diagonal of U^T (G mu) V
   for (int i = 0; i < 3; ++i) {
@@ -258,6 +265,11 @@ __device__ __forceinline__ void route_elem_item(const Dev& d, int e, const doubl
   double dw = 0.0;
   for (int i = 0; i < 3; ++i) dw += (ss[i] - sf[i]) * Md[i];
   d.dw[e] += d.vol[e] * dw;
+  if (d.model == 2) {   // b carries w_0 V G^T R + w_1 V G^T p_vol, A carries w_0 + w_1
+    double dw1 = 0.0;
+    for (int i = 0; i < 3; ++i) dw1 += (sv[i] - sf[i]) * Md[i];
+    d.dw1[e] += d.vol[e] * dw1;
+  }
   d.dbeta[e] += -d.vol[e] / d.h * gb;
   if (d.model == 1) {
     double Jm[9];
@@ -298,8 +310,11 @@ __device__ __forceinline__ void chain_item(const Dev& d, int e, double* dE, doub
   const double dw_dnu = 2.0 * dmu_dnu + (nh ? dlam_dnu : 0.0);
   const double cb = d.mu_ref > 0.0 ? d.beta0 / d.mu_ref : 0.0;
   const double inv_n = 1.0 / d.n_e;
-  if (dE) dE[e] = d.dw[e] * dw_dE + d.dbeta[e] * cb * dmu_dE + (am * dmu_dE + al * dlam_dE + ak * dw_dE) * inv_n;
-  part[0] += d.dw[e] * dw_dnu + d.dbeta[e] * cb * dmu_dnu;
+  // the composite's two weights: w_0 = 2 mu (dw), w_1 = lambda (dw1)
+  const double v1E = d.model == 2 ? d.dw1[e] * dlam_dE : 0.0;
+  const double v1nu = d.model == 2 ? d.dw1[e] * dlam_dnu : 0.0;
+  if (dE) dE[e] = d.dw[e] * dw_dE + v1E + d.dbeta[e] * cb * dmu_dE + (am * dmu_dE + al * dlam_dE + ak * dw_dE) * inv_n;
+  part[0] += d.dw[e] * dw_dnu + v1nu + d.dbeta[e] * cb * dmu_dnu;
   part[1] += dmu_dnu;
   part[2] += dlam_dnu;
   part[3] += dw_dnu;

@@ -30,6 +30,22 @@ __device__ __forceinline__ void bwd_setup_item(const Dev& d, int e, const double
     const T lnJ = dlog(ss[0] * ss[1] * ss[2]);
 #pragma unroll
     for (int c = 0; c < 3; ++c) Sp[c] = m.k / (m.k + m.mu + (m.mu - m.lam * lnJ) / (ss[pi[c]] * ss[pj[c]]));
+  } else if (d.model == 2) {
+    // composite: sigma* = a + (1 - a) sigma_v; d sigma*/d sigma_F = (1 - a)
+    // d sigma_v/d sigma_F (no prox Hessian, nothing to filter); with
+    // sigma_F,i = sigma_v,i + nu / sigma_v,i at the volume step's stationarity,
+    // (sigma*_i - sigma*_j)/(sigma_F,i - sigma_F,j) = (1 - a)/(1 - nu/(sigma_v,i sigma_v,j))
+    // exactly, free of cancellation near sigma_F,i = sigma_F,j
+    T sv[3], nu;
+    vol_project<T>(sF, sv, nu);
+    vol_jacobian<T>(sv, nu, J);
+    const T a = (T)d.rot_share;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) J[i] *= T(1) - a;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ss[i] = a + (T(1) - a) * sv[i];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Sp[c] = (T(1) - a) / (T(1) - nu / (sv[pi[c]] * sv[pj[c]]));
   } else {
     ss[0] = ss[1] = ss[2] = T(1);
 #pragma unroll

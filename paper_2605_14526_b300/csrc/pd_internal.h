@@ -102,7 +102,8 @@ struct MlpDev {
 // Everything the kernels need, passed by value.
 struct Dev {
   int n_v, n_e, n_f;
-  int model;          // 0 corotated, 1 Neo-Hookean
+  int model;          // 0 corotated, 1 Neo-Hookean, 2 corotated + volume composite
+  double rot_share;   // composite: a = w_0/(w_0 + w_1) = 2 mu/(2 mu + lambda) (the same for every element)
   int local_fp32;
   int aa_m, k_max, fixed_iters, tr_mode, adj_max_iters;
   int escalate;       // FP32 local step: switch to FP64 after this many iterations without progress (0 = never)
@@ -234,7 +235,8 @@ struct Dev {
   double* qbar;     // gradient on q*
   double* gq;       // running dL/dq_t
   double* gv;       // running dL/dv_t
-  double* dw;       // [n_e] accumulated dL/dw_e
+  double* dw;       // [n_e] accumulated dL/dw_e (composite: of the rotation weight w_0)
+  double* dw1;      // [n_e] composite: accumulated dL/dw_1 of the volume weight
   double* dbeta;    // [n_e]
 };
 

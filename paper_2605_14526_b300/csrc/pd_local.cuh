@@ -25,6 +25,14 @@ __device__ __forceinline__ void local_item(const Dev& d, int e, const double* x,
   svd3<T>(F, U, sF, V);
   if (d.model == 0) {
     ss[0] = ss[1] = ss[2] = T(1);
+  } else if (d.model == 2) {
+    // corotated + volume composite: p = (w_0 R + w_1 p_vol)/(w_0 + w_1) =
+    // U diag(a + (1 - a) sigma_v) V^T with a = w_0/(w_0 + w_1)
+    T sv[3], nu;
+    vol_project<T>(sF, sv, nu);
+    const T a = (T)d.rot_share;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ss[i] = a + (T(1) - a) * sv[i];
   } else {
     NHMean<T> m{(T)d.mu_bar, (T)d.lam_bar, (T)d.k_bar};
     float* ws = reinterpret_cast<float*>(d.sstar) + 3 * (size_t)e;

@@ -23,6 +23,9 @@ template <typename T> __device__ __forceinline__ T dlog(T x);
 template <> __device__ __forceinline__ float dlog<float>(float x) { return logf(x); }
 template <> __device__ __forceinline__ double dlog<double>(double x) { return log(x); }
 template <typename T> __device__ __forceinline__ T dabs(T x) { return x < T(0) ? -x : x; }
+template <typename T> __device__ __forceinline__ T dcbrt(T x);
+template <> __device__ __forceinline__ float dcbrt<float>(float x) { return cbrtf(x); }
+template <> __device__ __forceinline__ double dcbrt<double>(double x) { return cbrt(x); }
 
 // symmetric Jacobi rotation zeroing S[p][q]; S and V row-major 3x3
 template <typename T>
@@ -250,6 +253,118 @@ __device__ __forceinline__ int nh_prox_from(const T* sF, const NHMean<T>& m, con
     for (int i = 0; i < 3; ++i) s[i] = trial[i];
   }
   return it;
+}
+
+// ------------------------------------------------------------ volume step
+//
+// The volume step of the corotated + volume composite (Sec. 4.1, with the
+// corotated rotation step; Sec. 7.2 weights w_0 = 2 mu, w_1 = lambda): the
+// closest point of the unit-determinant set in stretch space,
+//   sigma_v = argmin 1/2 ||sigma - sigma_F||^2 s.t. sigma_1 sigma_2 sigma_3 = 1,
+// by Newton on the Lagrange system sigma - sigma_F + nu grad J = 0, J = 1,
+// from max(sigma_F, 1e-3) scaled onto J = 1.
+
+// x = K^-1 r for a 4 x 4 system, Gaussian elimination with partial pivoting
+template <typename T>
+__device__ __forceinline__ void solve4(T (&K)[4][4], T (&r)[4]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    int p = c;
+#pragma unroll
+    for (int i = c + 1; i < 4; ++i)
+      if (dabs(K[i][c]) > dabs(K[p][c])) p = i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const T t = K[c][j];
+      K[c][j] = K[p][j];
+      K[p][j] = t;
+    }
+    const T t = r[c];
+    r[c] = r[p];
+    r[p] = t;
+    const T inv = T(1) / K[c][c];
+#pragma unroll
+    for (int i = c + 1; i < 4; ++i) {
+      const T f = K[i][c] * inv;
+#pragma unroll
+      for (int j = c; j < 4; ++j) K[i][j] -= f * K[c][j];
+      r[i] -= f * r[c];
+    }
+  }
+#pragma unroll
+  for (int c = 3; c >= 0; --c) {
+    T acc = r[c];
+#pragma unroll
+    for (int j = c + 1; j < 4; ++j) acc -= K[c][j] * r[j];
+    r[c] = acc / K[c][c];
+  }
+}
+
+// the Lagrange system's matrix [[I + nu Hess J, grad J], [grad J^T, 0]]
+template <typename T>
+__device__ __forceinline__ void vol_kkt(const T* s, T nu, T (&K)[4][4]) {
+  const T g[3] = {s[1] * s[2], s[0] * s[2], s[0] * s[1]};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) K[i][j] = i == j ? T(1) : nu * s[3 - i - j];
+    K[i][3] = g[i];
+    K[3][i] = g[i];
+  }
+  K[3][3] = T(0);
+}
+
+// sigma_v and its multiplier; returns iterations
+template <typename T>
+__device__ __forceinline__ int vol_project(const T* sF, T* s, T& nu) {
+  const T tol = sizeof(T) == 4 ? T(2e-7) : T(1e-14);
+  T sc = T(1);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    s[i] = sF[i] > T(1e-3) ? sF[i] : T(1e-3);
+    sc = sc < dabs(sF[i]) ? dabs(sF[i]) : sc;
+  }
+  const T c = T(1) / dcbrt(s[0] * s[1] * s[2]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) s[i] *= c;
+  {
+    const T g[3] = {s[1] * s[2], s[0] * s[2], s[0] * s[1]};
+    nu = -((s[0] - sF[0]) * g[0] + (s[1] - sF[1]) * g[1] + (s[2] - sF[2]) * g[2]) /
+         (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+  }
+  int it = 0;
+  for (; it < 40; ++it) {
+    const T g[3] = {s[1] * s[2], s[0] * s[2], s[0] * s[1]};
+    T r[4] = {-(s[0] - sF[0] + nu * g[0]), -(s[1] - sF[1] + nu * g[1]), -(s[2] - sF[2] + nu * g[2]),
+              -(s[0] * s[1] * s[2] - T(1))};
+    T rmax = T(0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) rmax = rmax < dabs(r[i]) ? dabs(r[i]) : rmax;
+    if (rmax <= tol * sc) break;
+    T K[4][4];
+    vol_kkt<T>(s, nu, K);
+    solve4<T>(K, r);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) s[i] += r[i];
+    nu += r[3];
+  }
+  return it;
+}
+
+// d sigma_v / d sigma_F: the leading 3 x 3 block of the inverse Lagrange
+// matrix (symmetric), row-major
+template <typename T>
+__device__ __forceinline__ void vol_jacobian(const T* s, T nu, T* J) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    T K[4][4];
+    vol_kkt<T>(s, nu, K);
+    T r[4] = {T(0), T(0), T(0), T(0)};
+    r[c] = T(1);
+    solve4<T>(K, r);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) J[3 * i + c] = r[i];
+  }
 }
 
 // same, from s0 = max(sF, 0.1)

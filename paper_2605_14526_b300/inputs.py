@@ -21,6 +21,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 COROTATED = "corotated"
+COROT_VOLUME = "corotated_volume"   # corotated rotation step + volume step (Sec. 4.1, Sec. 7.2)
 NEOHOOKEAN = "neohookean"
 
 TR_ADAPT, TR_NONE, TR_CLAMP, TR_ABS = 0, 1, 2, 3

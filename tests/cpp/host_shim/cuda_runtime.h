@@ -4,6 +4,8 @@
 #pragma once
 #include <cmath>
 inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
+inline float cbrtf(float x) { return std::cbrt(x); }
+using std::cbrt;
 
 // explicitly rounded single-precision operations (round to nearest even, as
 // the host's SSE arithmetic does; build with -ffp-contract=off so that no

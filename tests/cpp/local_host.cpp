@@ -13,9 +13,10 @@ using namespace pdk;
 extern "C" {
 // tets [n_e][4]; Bm [n_e][9] (Dm^-1 row-major); coef [n_e] (w_e V_e); x
 // [n_v][3]; out [n_e][12] corner forces in FP64; fp64 selects the local
-// step's precision. Every element starts cold (no stored sigma*).
+// step's precision; rot_share is the composite's a = 2 mu/(2 mu + lambda).
+// Every element starts cold (no stored sigma*).
 void local_step_host(int fp64, int model, int n_e, const int* tets, const double* Bm, const double* coef,
-                     double mu_bar, double lam_bar, double k_bar, const double* x, double* out) {
+                     double mu_bar, double lam_bar, double k_bar, double rot_share, const double* x, double* out) {
   std::vector<float> Bm32(9 * (size_t)n_e), coef32(n_e), sstar(6 * (size_t)n_e, 0.0f), c32(12 * (size_t)n_e);
   for (size_t i = 0; i < Bm32.size(); ++i) Bm32[i] = (float)Bm[i];
   for (int e = 0; e < n_e; ++e) coef32[e] = (float)coef[e];
@@ -25,6 +26,7 @@ void local_step_host(int fp64, int model, int n_e, const int* tets, const double
   d.mu_bar = mu_bar;
   d.lam_bar = lam_bar;
   d.k_bar = k_bar;
+  d.rot_share = rot_share;
   d.tets = reinterpret_cast<const int4*>(tets);
   d.Bm32 = Bm32.data();
   d.Bm64 = Bm;

@@ -27,7 +27,8 @@ def _deformed(sc, seed, amp):
 @pytest.mark.parametrize("case,fp32,tol", [
     ("cube_corotated", False, 1e-12), ("cube_corotated", True, 2e-6),
     ("tiny_nh", False, 1e-12), ("tiny_nh", True, 2e-6),
-    ("bar_nh", True, 2e-6), ("block16_nh", True, 2e-6)])
+    ("bar_nh", True, 2e-6), ("block16_nh", True, 2e-6),
+    ("tiny_cv", False, 1e-12), ("tiny_cv", True, 2e-6), ("bar_cv", True, 2e-6)])
 def test_local_rhs_matches_oracle(case, fp32, tol):
     build()
     sc = {"cube_corotated": lambda: inputs.small_cube(),

@@ -31,7 +31,7 @@ def test_cube_fixed_iterations_forward_and_backward(persistent):
     assert abs(g["dnu"] - o["dnu"]) < 1e-7 * abs(o["dnu"])
 
 
-@pytest.mark.parametrize("model", ["neohookean", "corotated"])
+@pytest.mark.parametrize("model", ["neohookean", "corotated", "corotated_volume"])
 def test_tiny_fp64_converged_rollout(model):
     """FP64 local step with tight gates reaches the oracle's fixed points;
     per-step forces, damping, gravity, seeded initial velocity."""
@@ -63,6 +63,27 @@ def test_small_bar_fp32_config_gate(persistent):
     # 1% of the largest gradient carry a few 1e-4 of their own value
     assert elem_rel(g["dE"], o["dE"]) < 1e-3, elem_rel(g["dE"], o["dE"])
     assert abs(g["dnu"] - o["dnu"]) < 1e-4 * abs(o["dnu"])
+
+
+@pytest.mark.parametrize("fp32", [True, False])
+def test_small_bar_composite_energy(fp32):
+    """The corotated + volume composite (rotation step w_0 = 2 mu, volume
+    step w_1 = lambda, Sec. 4.1 and Sec. 7.2) on the heterogeneous bar, 20
+    steps: FP32 local step at the benchmark's gate, or FP64 at a tight gate."""
+    sc = inputs.hetero_bar(nx=8, ny=4, nz=4, block=4, steps=20).replace(model="corotated_volume")
+    if fp32:
+        sc = sc.replace(solver=inputs.SolverSettings(eps_res=1e-6, eps_step=1e-8))
+        tq, tg = 1e-5, 1e-4
+    else:
+        sc = sc.replace(solver=inputs.SolverSettings(eps_res=1e-11, eps_step=1e-13, local_fp32=False))
+        tq, tg = 1e-9, 1e-6
+    g = gpu_run(sc)
+    o = oracle_run(sc)
+    assert g["stats"].not_converged == 0
+    assert rel(g["qT"], o["qT"]) < tq, rel(g["qT"], o["qT"])
+    for k in ("dq0", "dv0", "dE"):
+        assert rel(g[k], o[k]) < tg, (k, rel(g[k], o[k]))
+    assert abs(g["dnu"] - o["dnu"]) < tg * abs(o["dnu"])
 
 
 def test_full_bar_first_steps_fp32_positions():

@@ -30,6 +30,9 @@ def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
+MODEL_IDS = {"corotated": 0, "neohookean": 1, "corotated_volume": 2}
+
+
 def host_rhs(lib, pb, q, fp64):
     """Elastic right-hand side sum_e w_e V_e G_e^T vec(p_e) from the host
     build's per-element corner forces, gathered per vertex in FP64."""
@@ -39,10 +42,11 @@ def host_rhs(lib, pb, q, fp64):
     coef = np.ascontiguousarray(pb.mat.w * pb.rest.vol)
     x = np.ascontiguousarray(q, dtype=np.float64)
     out = np.zeros((n_e, 12))
-    model = 0 if pb.model == "corotated" else 1
+    model = MODEL_IDS[pb.model]
     lib.local_step_host(ctypes.c_int(1 if fp64 else 0), ctypes.c_int(model), ctypes.c_int(n_e), _p(tets), _p(Bm),
                         _p(coef), ctypes.c_double(pb.mat.mu_bar), ctypes.c_double(pb.mat.lam_bar),
-                        ctypes.c_double(pb.mat.k_bar), _p(x), _p(out))
+                        ctypes.c_double(pb.mat.k_bar), ctypes.c_double(float(solver.rotation_share(pb)[0])), _p(x),
+                        _p(out))
     b = np.zeros_like(x)
     np.add.at(b, tets.ravel(), out.reshape(-1, 3))
     return b
@@ -51,10 +55,11 @@ def host_rhs(lib, pb, q, fp64):
 def _scenes():
     return [inputs.tiny_block(model="neohookean", steps=1, cell=0.1, n=3),
             inputs.tiny_block(model="corotated", steps=1, cell=0.1, n=3),
-            inputs.hetero_bar(nx=8, ny=4, nz=4, block=4, steps=1)]
+            inputs.hetero_bar(nx=8, ny=4, nz=4, block=4, steps=1),
+            inputs.tiny_block(model="corotated_volume", steps=1, cell=0.1, n=3)]
 
 
-@pytest.mark.parametrize("k", range(3))
+@pytest.mark.parametrize("k", range(4))
 @pytest.mark.parametrize("amp", [0.05, 0.3])
 def test_local_step_matches_oracle(lib, k, amp):
     """A large rotation plus per-vertex noise of amp x the 0.1 m cell; at

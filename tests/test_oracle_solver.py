@@ -53,7 +53,7 @@ def test_weights_are_energy_specific():
     assert np.allclose(m_nh.beta, 0.1 * mu / mu.max())
 
 
-@pytest.mark.parametrize("model", ["neohookean", "corotated"])
+@pytest.mark.parametrize("model", ["neohookean", "corotated", "corotated_volume"])
 def test_zero_force_at_rest_with_damping(model):
     """A X = b(X) with Rayleigh damping on (needs the damping RHS reading)."""
     sc = _scene(model, gravity=np.zeros(3))
@@ -66,7 +66,7 @@ def test_zero_force_at_rest_with_damping(model):
     assert np.allclose(q, sc.X, atol=1e-13)
 
 
-@pytest.mark.parametrize("model", ["neohookean", "corotated"])
+@pytest.mark.parametrize("model", ["neohookean", "corotated", "corotated_volume"])
 def test_free_body_closed_form(model):
     """No pins, unstrained, uniform velocity and gravity: q = (q~ + alpha h q_t)/(1 + alpha h)."""
     sc = _scene(model, pinned=np.zeros(27, dtype=np.uint8), alpha=0.3)
@@ -80,7 +80,7 @@ def test_free_body_closed_form(model):
     assert np.allclose(q, exact, atol=1e-13)
 
 
-@pytest.mark.parametrize("model", ["neohookean", "corotated"])
+@pytest.mark.parametrize("model", ["neohookean", "corotated", "corotated_volume"])
 def test_rigid_rotation_has_no_elastic_force(model):
     sc = _scene(model, pinned=np.zeros(27, dtype=np.uint8), gravity=np.zeros(3))
     pb = solver.build_problem(sc)
@@ -92,7 +92,7 @@ def test_rigid_rotation_has_no_elastic_force(model):
     assert np.allclose(q, qt, atol=1e-12)
 
 
-@pytest.mark.parametrize("model", ["neohookean", "corotated"])
+@pytest.mark.parametrize("model", ["neohookean", "corotated", "corotated_volume"])
 def test_plain_iteration_decreases_pd_energy(model):
     """Local-global is block-coordinate descent on g~(q, p) (eq. pd_surrogate)."""
     sc = inputs.hetero_bar(nx=6, ny=2, nz=2, block=2, omega0=6.0).replace(model=model)
@@ -108,7 +108,7 @@ def test_plain_iteration_decreases_pd_energy(model):
         e_prev = e
 
 
-@pytest.mark.parametrize("model", ["neohookean", "corotated"])
+@pytest.mark.parametrize("model", ["neohookean", "corotated", "corotated_volume"])
 def test_fixed_point_is_stationary(model):
     sc = inputs.hetero_bar(nx=6, ny=2, nz=2, block=2, omega0=6.0).replace(model=model)
     pb = solver.build_problem(sc)
