@@ -34,7 +34,9 @@ def test_local_rhs_matches_oracle(case, fp32, tol):
     sc = {"cube_corotated": lambda: inputs.small_cube(),
           "tiny_nh": lambda: inputs.tiny_block(n=3, cell=0.1),
           "bar_nh": lambda: inputs.hetero_bar(steps=1),
-          "block16_nh": lambda: inputs.large_block(n=16, steps=1)}[case]()
+          "block16_nh": lambda: inputs.large_block(n=16, steps=1),
+          "tiny_cv": lambda: inputs.tiny_block(n=3, cell=0.1, model="corotated_volume"),
+          "bar_cv": lambda: inputs.hetero_bar(steps=1).replace(model="corotated_volume")}[case]()
     sc = sc.replace(solver=dataclasses.replace(sc.solver, local_fp32=fp32))
     pd = binding.PDContext(sc)
     pb = solver.build_problem(sc)
