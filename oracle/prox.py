@@ -170,30 +170,56 @@ def _kkt(s, nu):
     return K
 
 
-def volume_project_sigma(sF: np.ndarray, tol: float = 1e-14, max_iter: int = 60):
+def _plus_root(a, nu):
+    """The larger root of s^2 - a s + nu = 0 (the stationarity condition
+    s - a + nu/s = 0 of one stretch on J = 1), without cancellation."""
+    r = np.sqrt(np.maximum(a * a - 4.0 * nu, 0.0))
+    safe = np.where(a - r != 0.0, a - r, -1.0)
+    return np.where(a >= 0.0, 0.5 * (a + r), 2.0 * nu / safe)
+
+
+def _volume_curve(sF, s3):
+    """The stationary curve parametrized by the smallest stretch s_3: the
+    multiplier nu = s_3 (sigma_F3 - s_3) (stationarity of s_3) and s_1, s_2
+    the larger roots of their own stationarity quadratics at that nu.
+    Returns (s [n,3], nu)."""
+    nu = s3 * (sF[:, 2] - s3)
+    s = np.stack([_plus_root(sF[:, 0], nu), _plus_root(sF[:, 1], nu), s3], axis=1)
+    return s, nu
+
+
+def volume_project_sigma(sF: np.ndarray, iters: int = 200):
     """The volume step of the corotated + volume composite (Sec. 4.1, the
     quadratic (J - 1)^2 volume step that pairs with the corotated rotation
     step; Sec. 7.2 weights w_1 = lambda): the closest point of the unit
     determinant set in stretch space,
         sigma* = argmin 1/2 ||sigma - sigma_F||^2  s.t.  sigma_1 sigma_2 sigma_3 = 1,
-    so that p* = U diag(sigma*) V^T is the closest matrix with det = 1 to F.
-    Newton on the Lagrange system (sigma - sigma_F + nu grad J = 0, J = 1)
-    from max(sigma_F, 1e-3) scaled onto J = 1 (the stationary point in the
-    positive octant; an inverted element's negative stretch is pulled back).
-    Returns (sigma*, nu, iterations)."""
-    s = np.maximum(sF, 1e-3)
-    s = s / np.cbrt(np.prod(s, axis=1))[:, None]
-    g = _grad_J(s)
-    nu = -np.sum((s - sF) * g, axis=1) / np.sum(g * g, axis=1)
+    on the positive sheet (sigma > 0), so that p* = U diag(sigma*) V^T is the
+    closest matrix with det = 1 to F (the rotation-variant order
+    sigma_F1 >= sigma_F2 >= |sigma_F3| makes the positive sheet the nearest).
+
+    Stationarity reads s_i^2 - sigma_Fi s_i + nu = 0 for every i with one
+    multiplier nu. The minimiser lies on the curve where s_1 and s_2 take the
+    larger root and s_3 is free (nu = s_3 (sigma_F3 - s_3)); along it
+    log(s_1 s_2 s_3) goes from -inf (s_3 -> 0) to +inf (s_3 -> inf) and
+    changes sign once, so the minimiser is that sign change, found here by
+    plain bisection in log s_3 over [-40, 40] (the unit-determinant set can
+    have several stationary points, e.g. for a stretched element, and a
+    Newton on the Lagrange system may settle on any of them; bisection on
+    this curve cannot). Returns (sigma*, nu, iterations)."""
+    n = sF.shape[0]
+    lo = np.full(n, -40.0)
+    hi = np.full(n, 40.0)
     it = 0
-    for it in range(1, max_iter + 1):
-        g = _grad_J(s)
-        r = np.concatenate([s - sF + nu[:, None] * g, (np.prod(s, axis=1) - 1.0)[:, None]], axis=1)
-        if np.abs(r).max() <= tol * max(1.0, np.abs(sF).max()):
+    for it in range(1, iters + 1):
+        mid = 0.5 * (lo + hi)
+        s, _ = _volume_curve(sF, np.exp(mid))
+        pos = np.sum(np.log(s), axis=1) > 0.0
+        hi = np.where(pos, mid, hi)
+        lo = np.where(pos, lo, mid)
+        if np.all(hi - lo <= 1e-15 * np.maximum(1.0, np.abs(hi))):
             break
-        d = np.linalg.solve(_kkt(s, nu), -r[:, :, None])[:, :, 0]
-        s = s + d[:, :3]
-        nu = nu + d[:, 3]
+    s, nu = _volume_curve(sF, np.exp(0.5 * (lo + hi)))
     return s, nu, it
 
 

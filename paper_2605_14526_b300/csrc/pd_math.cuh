@@ -26,6 +26,9 @@ template <typename T> __device__ __forceinline__ T dabs(T x) { return x < T(0) ?
 template <typename T> __device__ __forceinline__ T dcbrt(T x);
 template <> __device__ __forceinline__ float dcbrt<float>(float x) { return cbrtf(x); }
 template <> __device__ __forceinline__ double dcbrt<double>(double x) { return cbrt(x); }
+template <typename T> __device__ __forceinline__ T dexp(T x);
+template <> __device__ __forceinline__ float dexp<float>(float x) { return expf(x); }
+template <> __device__ __forceinline__ double dexp<double>(double x) { return exp(x); }
 
 // symmetric Jacobi rotation zeroing S[p][q]; S and V row-major 3x3
 template <typename T>
@@ -261,8 +264,13 @@ __device__ __forceinline__ int nh_prox_from(const T* sF, const NHMean<T>& m, con
 // corotated rotation step; Sec. 7.2 weights w_0 = 2 mu, w_1 = lambda): the
 // closest point of the unit-determinant set in stretch space,
 //   sigma_v = argmin 1/2 ||sigma - sigma_F||^2 s.t. sigma_1 sigma_2 sigma_3 = 1,
-// by Newton on the Lagrange system sigma - sigma_F + nu grad J = 0, J = 1,
-// from max(sigma_F, 1e-3) scaled onto J = 1.
+// on the positive sheet. Stationarity is s_i^2 - sigma_Fi s_i + nu = 0 with
+// one multiplier nu; the minimiser lies on the curve where s_1 and s_2 take
+// the larger root and s_3 is free (nu = s_3 (sigma_F3 - s_3)), at the one
+// point of it where log(s_1 s_2 s_3) changes sign. That point is found by
+// Newton in log s_3 inside a bracket that every iterate tightens, with
+// geometric bisection (or bracket expansion by 4x) whenever the Newton step
+// leaves the bracket or the curve's slope is not clearly positive.
 
 // x = K^-1 r for a 4 x 4 system, Gaussian elimination with partial pivoting
 template <typename T>
@@ -314,39 +322,41 @@ __device__ __forceinline__ void vol_kkt(const T* s, T nu, T (&K)[4][4]) {
   K[3][3] = T(0);
 }
 
+// the larger root of s^2 - a s + nu = 0, without cancellation
+template <typename T>
+__device__ __forceinline__ T vol_root(T a, T nu) {
+  const T q = a * a - T(4) * nu;
+  const T r = dsqrt(q > T(0) ? q : T(0));
+  return a >= T(0) ? T(0.5) * (a + r) : T(2) * nu / (a - r);
+}
+
 // sigma_v and its multiplier; returns iterations
 template <typename T>
 __device__ __forceinline__ int vol_project(const T* sF, T* s, T& nu) {
-  const T tol = sizeof(T) == 4 ? T(2e-7) : T(1e-14);
-  T sc = T(1);
+  const T tol = sizeof(T) == 4 ? T(3e-7) : T(1e-15);      // on log J
+  const T btol = sizeof(T) == 4 ? T(1e-6) : T(4e-16);     // relative bracket width
+  T m[3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    s[i] = sF[i] > T(1e-3) ? sF[i] : T(1e-3);
-    sc = sc < dabs(sF[i]) ? dabs(sF[i]) : sc;
-  }
-  const T c = T(1) / dcbrt(s[0] * s[1] * s[2]);
-#pragma unroll
-  for (int i = 0; i < 3; ++i) s[i] *= c;
-  {
-    const T g[3] = {s[1] * s[2], s[0] * s[2], s[0] * s[1]};
-    nu = -((s[0] - sF[0]) * g[0] + (s[1] - sF[1]) * g[1] + (s[2] - sF[2]) * g[2]) /
-         (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-  }
+  for (int i = 0; i < 3; ++i) m[i] = sF[i] > T(1e-3) ? sF[i] : T(1e-3);
+  T s3 = m[2] / dcbrt(m[0] * m[1] * m[2]);   // sigma_F scaled onto J = 1
+  T lo = T(0), hi = T(0);                    // log J(lo) < 0 < log J(hi); 0: not found yet
   int it = 0;
-  for (; it < 40; ++it) {
-    const T g[3] = {s[1] * s[2], s[0] * s[2], s[0] * s[1]};
-    T r[4] = {-(s[0] - sF[0] + nu * g[0]), -(s[1] - sF[1] + nu * g[1]), -(s[2] - sF[2] + nu * g[2]),
-              -(s[0] * s[1] * s[2] - T(1))};
-    T rmax = T(0);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) rmax = rmax < dabs(r[i]) ? dabs(r[i]) : rmax;
-    if (rmax <= tol * sc) break;
-    T K[4][4];
-    vol_kkt<T>(s, nu, K);
-    solve4<T>(K, r);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) s[i] += r[i];
-    nu += r[3];
+  for (; it < 60; ++it) {
+    nu = s3 * (sF[2] - s3);
+    s[0] = vol_root<T>(sF[0], nu);
+    s[1] = vol_root<T>(sF[1], nu);
+    s[2] = s3;
+    const T L = dlog(s[0] * s[1] * s3);
+    if (L > T(0)) hi = s3;
+    else lo = s3;
+    if (dabs(L) <= tol || (lo > T(0) && hi > T(0) && hi - lo <= btol * hi)) break;
+    // d log J / d log s_3 along the curve (2 s_i - sigma_Fi = sqrt(sigma_Fi^2 - 4 nu))
+    const T D = T(1) + s3 * (T(2) * s3 - sF[2]) *
+                           (T(1) / (s[0] * (T(2) * s[0] - sF[0])) + T(1) / (s[1] * (T(2) * s[1] - sF[1])));
+    T next = D > T(0.1) ? s3 * dexp(-L / D) : T(0);
+    if (!(next > lo && (hi == T(0) || next < hi)))
+      next = (lo > T(0) && hi > T(0)) ? dsqrt(lo * hi) : (L > T(0) ? T(0.25) * s3 : T(4) * s3);
+    s3 = next;
   }
   return it;
 }
