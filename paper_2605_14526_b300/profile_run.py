@@ -2,7 +2,7 @@
 
   python -m paper_2605_14526_b300.profile_run --case bar --steps 2
   python -m paper_2605_14526_b300.profile_run --case block --n 48 --repeat 3
-  python -m paper_2605_14526_b300.profile_run --case mlp --repeat 3
+  python -m paper_2605_14526_b300.profile_run --case mlp --repeat 3 [--n 32]
 
 Runs `steps` PD steps of the named workload forward and backward once as a
 warm-up and once more, so that a profiler can skip the first pass. The block
@@ -10,7 +10,8 @@ case factors an n^3-cell block (solve mode chosen automatically: T from
 about 24^3 cells) and repeats one solve with the factor (pd_solve, one launch
 per separator-tree height and sweep in mode T) and one standalone local step
 (pd_local_rhs). The mlp case repeats training steps of the warm-start
-network and its evaluation on the bar (pd_warm_start), on seeded data.
+network and its evaluation (pd_warm_start) on the bar, or with --n on an
+n^3-cell block, on seeded data.
 """
 from __future__ import annotations
 
@@ -56,7 +57,7 @@ def run_block(n, repeat):
     pd.close()
 
 
-def run_mlp(repeat):
+def run_mlp(repeat, n_block=0):
     dev = "cuda:0"
     rng = np.random.default_rng(3)
     n = 1 << 16
@@ -64,7 +65,7 @@ def run_mlp(repeat):
     targ = torch.as_tensor(1e-3 * rng.standard_normal((n, 3)).astype(np.float32), device=dev)
     net = binding.MLP(inputs.mlp_init(0), np.concatenate([np.zeros(7), np.ones(7), np.ones(3)]).astype(np.float32))
     binding.pd_mlp_fit_normalization(net.net, feat, targ, n)
-    sc = inputs.hetero_bar(steps=1)
+    sc = inputs.large_block(n=n_block, steps=1) if n_block else inputs.hetero_bar(steps=1)
     opt = binding.options_for(sc.solver)
     pd = binding.PDContext(sc, opt)
     for r in range(repeat):
@@ -89,7 +90,8 @@ def run_mlp(repeat):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default="bar", choices=sorted(CASES) + ["block", "mlp"])
-    ap.add_argument("--n", type=int, default=48, help="block case: cells per edge")
+    ap.add_argument("--n", type=int, default=None,
+                    help="cells per edge of the block (block case: default 48; mlp case: default the bar)")
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--repeat", type=int, default=2)
     ap.add_argument("--phases", action="store_true", help="print device phase times of the forward rollout")
@@ -97,10 +99,10 @@ def main():
     args = ap.parse_args()
     build()
     if args.case == "block":
-        run_block(args.n, args.repeat)
+        run_block(args.n or 48, args.repeat)
         return
     if args.case == "mlp":
-        run_mlp(args.repeat)
+        run_mlp(args.repeat, args.n or 0)
         return
     sc = CASES[args.case](args.steps)
     dev = "cuda:0"
