@@ -551,6 +551,60 @@ int pd_set_warm_start(pd_ctx* ctx, int32_t mode);
  * constant velocity); pinned vertices at X. Single instance. */
 int pd_warm_start(pd_ctx* ctx, const double* x_t, const double* x_tm1, double* q0, void* stream);
 
+/* ---------------------------------------------------------------------
+ * L-BFGS driver for inverse problems (the paper's optimiser for system
+ * identification and initial-state tasks, Sec. 5.4 / 5.5, run on the
+ * gradients of pd_backward).
+ *
+ * Limited-memory BFGS (Nocedal and Wright, Numerical Optimization, 2nd ed.,
+ * 2006: the two-loop recursion of Alg. 7.4 with H0 = (s^T y / y^T y) I,
+ * Sec. 7.2) with a line search satisfying the strong Wolfe conditions
+ * (Alg. 3.5 bracketing with step doubling, Alg. 3.6 zoom by safeguarded
+ * cubic interpolation, eq. 3.59). Host FP64; the parameter vector is small
+ * (per-block moduli, initial states), the simulation it wraps runs on the
+ * device.
+ *
+ * Reverse communication: the caller owns x [n] (host) and evaluates
+ * f(x), g(x) wherever the optimiser asks:
+ *   pd_lbfgs_create(n, opts, &o); evaluate f, g at x0;
+ *   loop: pd_lbfgs_next(o, x, f, g, &task)
+ *     task PD_LBFGS_EVAL:      x holds a trial point: evaluate f, g there
+ *     task PD_LBFGS_ITERATE:   x holds the accepted iterate (f, g of the
+ *                              last evaluation belong to it); call again
+ *     task PD_LBFGS_CONVERGED: max |g| <= gtol, or a relative decrease of f
+ *                              of at most ftol; x holds the last iterate
+ *     task PD_LBFGS_STOP:      max_iters or max_evals reached
+ *     task PD_LBFGS_FAILED:    the line search found no acceptable step
+ *                              along steepest descent either (x: last iterate)
+ * f and g are read on every call except right after PD_LBFGS_ITERATE. A
+ * direction that is not a descent direction, or a line search that fails
+ * with curvature pairs stored, clears the memory and restarts from
+ * steepest descent. Pairs with s^T y <= 1e-12 y^T y are skipped.
+ * Returns PD_ERR_ARG for bad sizes or options, PD_ERR_NUMERIC for a
+ * non-finite f or g at an iterate (a non-finite trial value shrinks the
+ * step instead).
+ * --------------------------------------------------------------------- */
+typedef struct pd_lbfgs pd_lbfgs;
+enum { PD_LBFGS_EVAL = 1, PD_LBFGS_ITERATE = 2, PD_LBFGS_CONVERGED = 3, PD_LBFGS_STOP = 4, PD_LBFGS_FAILED = 5 };
+typedef struct {
+  int32_t m;          /* stored curvature pairs (default 10) */
+  int32_t max_iters;  /* accepted iterations (default 100) */
+  int32_t max_evals;  /* function evaluations, the initial one included (default 200) */
+  int32_t max_ls;     /* evaluations per line search (default 20) */
+  double gtol;        /* max |g| at convergence (default 1e-8) */
+  double ftol;        /* (f_k - f_k+1) / max(|f_k|, |f_k+1|, 1) at convergence (default 1e-12) */
+  double c1, c2;      /* sufficient decrease and curvature constants (default 1e-4, 0.9) */
+  double step0;       /* length of the first trial step, steepest descent (default 1) */
+} pd_lbfgs_options;
+
+/* Defaults of every field. */
+void pd_lbfgs_default_options(pd_lbfgs_options* opts);
+int pd_lbfgs_create(int32_t n, const pd_lbfgs_options* opts, pd_lbfgs** out);
+int pd_lbfgs_next(pd_lbfgs* o, double* x, double f, const double* g, int32_t* task);
+/* Counters and the last iterate's f and max |g| (any pointer may be NULL). */
+int pd_lbfgs_info(const pd_lbfgs* o, int32_t* iters, int32_t* evals, double* f, double* gmax);
+void pd_lbfgs_destroy(pd_lbfgs* o);
+
 /* Library version string. */
 const char* pd_version(void);
 

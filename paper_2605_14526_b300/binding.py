@@ -79,6 +79,14 @@ class pd_tuning(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
 
 
+class pd_lbfgs_options(ctypes.Structure):
+    _fields_ = [("m", c_int32), ("max_iters", c_int32), ("max_evals", c_int32), ("max_ls", c_int32),
+                ("gtol", c_double), ("ftol", c_double), ("c1", c_double), ("c2", c_double), ("step0", c_double)]
+
+
+PD_LBFGS_EVAL, PD_LBFGS_ITERATE, PD_LBFGS_CONVERGED, PD_LBFGS_STOP, PD_LBFGS_FAILED = 1, 2, 3, 4, 5
+LBFGS_TASKS = {1: "eval", 2: "iterate", 3: "converged", 4: "stop", 5: "failed"}
+
 _lib = None
 
 
@@ -136,6 +144,11 @@ def lib():
             "pd_mlp_load": (c_int, [P, P, ctypes.c_size_t]),
             "pd_warm_start": (c_int, [P, P, P, P, P]),
             "pd_set_contacts": (c_int, [P, P]),
+            "pd_lbfgs_default_options": (None, [P]),
+            "pd_lbfgs_create": (c_int, [c_int32, P, P]),
+            "pd_lbfgs_next": (c_int, [P, P, c_double, P, P]),
+            "pd_lbfgs_info": (c_int, [P, P, P, P, P]),
+            "pd_lbfgs_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -462,6 +475,41 @@ def pd_mlp_destroy(net):
 def pd_mlp_sample(ctx, x_tm1, x_t, x_tp1, feat, targ, stream=None):
     _check(ctx, lib().pd_mlp_sample(ctx, _ptr(x_tm1), _ptr(x_t), _ptr(x_tp1), _ptr(feat, np.float32),
                                     _ptr(targ, np.float32), _stream(stream)))
+
+
+def pd_lbfgs_default_options() -> pd_lbfgs_options:
+    o = pd_lbfgs_options()
+    lib().pd_lbfgs_default_options(ctypes.byref(o))
+    return o
+
+
+def pd_lbfgs_create(n, options: pd_lbfgs_options | None = None):
+    out = c_void_p()
+    code = lib().pd_lbfgs_create(int(n), ctypes.byref(options) if options is not None else None, ctypes.byref(out))
+    if code != PD_OK:
+        raise PDError(code, "pd_lbfgs_create")
+    return out
+
+
+def pd_lbfgs_next(opt, x, f, g):
+    """x: float64 ndarray [n] (updated in place); g may be None right after
+    an ITERATE task. Returns the task code."""
+    task = c_int32()
+    code = lib().pd_lbfgs_next(opt, _ptr(x), float(f), _ptr(g), ctypes.byref(task))
+    if code != PD_OK:
+        raise PDError(code, "pd_lbfgs_next")
+    return task.value
+
+
+def pd_lbfgs_info(opt):
+    it, ev, f, gm = c_int32(), c_int32(), c_double(), c_double()
+    _check(None, lib().pd_lbfgs_info(opt, ctypes.byref(it), ctypes.byref(ev), ctypes.byref(f), ctypes.byref(gm)))
+    return {"iters": it.value, "evals": ev.value, "f": f.value, "gmax": gm.value}
+
+
+def pd_lbfgs_destroy(opt):
+    if opt is not None and opt.value:
+        lib().pd_lbfgs_destroy(opt)
 
 
 def pd_mlp_load(ctx, blob):

@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpd_b300.so")
-SOURCES = ["factor.cpp", "tsolve.cpp", "pd_api.cpp", "pd_batch.cpp", "pd_kernels.cu", "pd_backward.cu", "pd_noalloc.cu", "pd_persistent.cu", "pd_mlp.cu"]
+SOURCES = ["factor.cpp", "tsolve.cpp", "lbfgs.cpp", "pd_api.cpp", "pd_batch.cpp", "pd_kernels.cu", "pd_backward.cu", "pd_noalloc.cu", "pd_persistent.cu", "pd_mlp.cu"]
 # every header of csrc/ (a header edit makes the library stale)
 HEADERS = sorted(f for f in os.listdir(CSRC) if f.endswith((".h", ".cuh")))
 ROOT_INCLUDE = os.path.join(os.path.dirname(HERE), "include", "pd_b300.h")

@@ -244,6 +244,29 @@ def tiny_block(n: int = 2, cell: float = 0.01, model: str = NEOHOOKEAN, seed: in
         loss="l2_target", target=target)
 
 
+def sysid_bar(nx: int = 8, ny: int = 4, nz: int = 4, block: int = 2, cell: float = 0.1, steps: int = 10,
+              seed: int = 21, spread: float = 0.3):
+    """System-identification workload on a C2-like bar (Sec. 5.4 task class):
+    block^3-cell blocks, each with its own ground-truth log10 E drawn
+    uniformly in [4, 6]; the bar's twist, pin, nu and alpha, no stiffness
+    damping (beta0 = 0: beta_e scales with mu_e / max mu, a maximum the
+    adjoint holds fixed), FP64 local step with a tight gate. Returns
+    (scene with the ground-truth moduli, block index per element,
+    theta_true = log10 E per block, theta0 = theta_true + N(0, spread^2))."""
+    rng = np.random.default_rng(seed)
+    sc = hetero_bar(nx=nx, ny=ny, nz=nz, block=block, cell=cell, steps=steps)
+    X, tets, cells = hex_grid(nx, ny, nz, cell)
+    bx, by, bz = max(nx // block, 1), max(ny // block, 1), max(nz // block, 1)
+    bid = (np.minimum(cells[:, 0] // block, bx - 1)
+           + bx * (np.minimum(cells[:, 1] // block, by - 1) + by * np.minimum(cells[:, 2] // block, bz - 1)))
+    theta_true = rng.uniform(4.0, 6.0, bx * by * bz)
+    theta0 = theta_true + spread * rng.standard_normal(theta_true.size)
+    sc = sc.replace(name=f"sysid{nx}x{ny}x{nz}", E=np.power(10.0, theta_true)[bid], beta0=0.0,
+                    solver=SolverSettings(aa_m=5, k_max=400, eps_step=1e-13, eps_res=1e-11, eps_abs=1e-15,
+                                          local_fp32=False))
+    return sc, bid.astype(np.int64), theta_true, theta0
+
+
 def large_block(n: int = 64, cell: float = 0.1, block: int = 8, seed: int = 5, steps: int = 20) -> Scene:
     """Large heterogeneous Neo-Hookean block (n^3 cells, 5 tets each), 8^3-cell
     stiffness blocks (half soft 1e4 Pa / half stiff 1e6 Pa), bottom face

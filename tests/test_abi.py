@@ -59,6 +59,7 @@ int main(void) {
          sizeof(pd_profile_out));
   printf("%zu %zu %zu %zu\\n", offsetof(pd_material, gravity), offsetof(pd_options, eps_step),
          offsetof(pd_stats, factor_nnz), offsetof(pd_stats, last_rho));
+  printf("%zu %zu\\n", sizeof(pd_lbfgs_options), offsetof(pd_lbfgs_options, gtol));
   return 0;
 }
 ''')
@@ -69,8 +70,9 @@ int main(void) {
     assert sizes[:5] == [ctypes.sizeof(binding.pd_mesh), ctypes.sizeof(binding.pd_material),
                          ctypes.sizeof(binding.pd_options), ctypes.sizeof(binding.pd_stats),
                          ctypes.sizeof(binding.pd_profile_out)]
-    assert sizes[5:] == [binding.pd_material.gravity.offset, binding.pd_options.eps_step.offset,
-                         binding.pd_stats.factor_nnz.offset, binding.pd_stats.last_rho.offset]
+    assert sizes[5:9] == [binding.pd_material.gravity.offset, binding.pd_options.eps_step.offset,
+                          binding.pd_stats.factor_nnz.offset, binding.pd_stats.last_rho.offset]
+    assert sizes[9:] == [ctypes.sizeof(binding.pd_lbfgs_options), binding.pd_lbfgs_options.gtol.offset]
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

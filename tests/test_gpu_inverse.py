@@ -1,0 +1,110 @@
+"""GPU tests of the inverse-problem driver (paper Sec. 5.4 / 5.5 task
+classes; the library's L-BFGS on pd_rollout + pd_backward gradients):
+system identification of 16 per-block Young's moduli of a small bar and
+the initial velocity of a small block, against the oracle's rollout,
+adjoint and L-BFGS (oracle/lbfgs.py). Targets come from the oracle's
+rollout at the ground truth."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import adjoint, solver
+from oracle import lbfgs as olb
+from paper_2605_14526_b300 import binding, inputs, inverse
+from paper_2605_14526_b300.build import build
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_final(sc):
+    pb = solver.build_problem(sc)
+    qT, vT, _ = solver.rollout(pb, sc, mode=solver.mode_for(sc))
+    return qT
+
+
+def _oracle_sysid(sc, bid, target):
+    n_b = int(bid.max()) + 1
+
+    def fun(theta):
+        s2 = sc.replace(E=np.power(10.0, theta)[bid], target=target)
+        pb = solver.build_problem(s2)
+        qT, vT, recs = solver.rollout(pb, s2, mode=solver.mode_for(s2))
+        L, dq, dv = adjoint.loss_and_grad(s2, pb, qT, vT)
+        g = adjoint.rollout_backward(pb, recs, dq, dv)
+        return L, np.bincount(bid, weights=g.dE * s2.E * np.log(10.0), minlength=n_b)
+    return fun
+
+
+@pytest.fixture(scope="module")
+def sysid():
+    build()
+    sc, bid, theta_true, theta0 = inputs.sysid_bar()
+    target = _oracle_final(sc)
+    return sc, bid, theta_true, theta0, target
+
+
+def test_sysid_loss_and_gradient_match_oracle(sysid):
+    sc, bid, _, theta0, target = sysid
+    prob = inverse.BlockSysID(sc, bid, target)
+    f, g = prob(theta0)
+    fo, go = _oracle_sysid(sc, bid, target)(theta0)
+    prob.close()
+    assert abs(f - fo) <= 1e-9 * fo
+    assert np.abs(g - go).max() <= 1e-7 * np.abs(go).max(), (g, go)
+
+
+def test_sysid_first_lbfgs_iterates_match_oracle(sysid):
+    sc, bid, _, theta0, target = sysid
+    prob = inverse.BlockSysID(sc, bid, target)
+    opts = binding.pd_lbfgs_default_options()
+    opts.max_iters = 3
+    got = inverse.lbfgs(prob, theta0, opts)
+    prob.close()
+    want = olb.minimize(_oracle_sysid(sc, bid, target), theta0, max_iters=3)
+    assert got["evals"] == want["evals"] and got["iters"] == want["iters"] == 3
+    for a, b in zip(got["points"], want["points"]):
+        assert np.abs(a - b).max() <= 1e-6, (a, b)
+
+
+def test_sysid_recovers_the_ground_truth(sysid):
+    """The oracle's own L-BFGS on the oracle reaches theta_true to 4e-6 in
+    26 iterations on this problem (31 rollouts + adjoints); the library's
+    must as well."""
+    sc, bid, theta_true, theta0, target = sysid
+    prob = inverse.BlockSysID(sc, bid, target)
+    f0, _ = prob(theta0)
+    opts = binding.pd_lbfgs_default_options()
+    opts.max_iters, opts.gtol, opts.ftol = 60, 1e-12, 1e-14
+    r = inverse.lbfgs(prob, theta0, opts)
+    st = binding.pd_get_stats(prob.pd.ctx)
+    prob.close()
+    assert r["status"] in ("converged", "failed")     # failed: a line search at the rounding floor
+    assert r["f"] <= 1e-10 * f0
+    assert np.abs(r["x"] - theta_true).max() <= 1e-4, np.abs(r["x"] - theta_true).max()
+    assert st.not_converged == 0
+
+
+def test_initial_velocity_recovers_the_ground_truth():
+    build()
+    sc = inputs.tiny_block(n=3, steps=3, cell=0.1)
+    target = _oracle_final(sc)
+    prob = inverse.InitialVelocity(sc, target)
+    free = sc.pinned == 0
+    x0 = np.zeros(3 * sc.n_v)
+    f0, g0 = prob(x0)
+    # gradient at v0 = 0 against the oracle's dL/dv0
+    s0 = sc.replace(v0=np.zeros_like(sc.v0), target=target)
+    pb = solver.build_problem(s0)
+    qT, vT, recs = solver.rollout(pb, s0, mode=solver.mode_for(s0))
+    L, dq, dv = adjoint.loss_and_grad(s0, pb, qT, vT)
+    go = adjoint.rollout_backward(pb, recs, dq, dv).dv0.reshape(-1)
+    assert abs(f0 - L) <= 1e-9 * L
+    assert np.abs(g0 - go).max() <= 1e-7 * np.abs(go).max()
+    opts = binding.pd_lbfgs_default_options()
+    opts.max_iters, opts.gtol, opts.ftol = 200, 1e-14, 0.0
+    r = inverse.lbfgs(prob, x0, opts)
+    prob.close()
+    v = r["x"].reshape(-1, 3)
+    assert r["f"] <= 1e-12 * f0
+    assert np.abs(v[free] - sc.v0[free]).max() <= 1e-4 * np.abs(sc.v0[free]).max()
+    assert torch.cuda.is_available()
