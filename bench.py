@@ -116,18 +116,34 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def one_thread():
-    """The oracle baseline runs single-threaded: numpy's BLAS limited to one
-    thread for the duration (the library's own host code keeps its threads)."""
-    from threadpoolctl import threadpool_limits
-    return threadpool_limits(limits=1, user_api="blas")
+_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+                "NUMEXPR_NUM_THREADS")
+
+
+def single_threaded(fn, *args):
+    """fn(*args) in a spawned child process whose BLAS and OpenMP pools have
+    one thread (the variables are set before numpy loads there; spawn, not
+    fork, since this process may hold a CUDA context). The library's own
+    host code in this process keeps its threads."""
+    import multiprocessing as mp
+    saved = {k: os.environ.get(k) for k in _THREAD_VARS}
+    for k in _THREAD_VARS:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(1) as pool:
+            return pool.apply(fn, args)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
 
 
 def oracle_sample(scene, n_steps: int):
     """The oracle as it stands (exact fixed point + direct adjoint) on the first
     n_steps steps of the workload, single-threaded. Returns (seconds, steps)."""
-    with one_thread():
-        return _oracle_sample(scene, n_steps)
+    return single_threaded(_oracle_sample, scene, n_steps)
 
 
 def _oracle_sample(scene, n_steps: int):
@@ -142,37 +158,44 @@ def _oracle_sample(scene, n_steps: int):
     return dt, n_steps
 
 
-def oracle_sample_mid(scene, steps=(100, 150)):
+GOLD_BAR = os.path.join(ROOT, "tests", "golden", "bar32x8x8_T200.npz")
+
+
+def oracle_sample_mid(scene, steps=(100, 150), repeats=1):
     """The oracle on one PD step (forward to the exact fixed point + direct
     adjoint) from each of the mid-rollout states t = 100 and t = 150 of the
     bar (the twisting part of the trajectory), read from the oracle's stored
-    rollout; falls back to the first two steps without it. Single-threaded.
-    Returns (seconds, steps, description)."""
-    from oracle import adjoint, solver
-    gold_path = os.path.join(ROOT, "tests", "golden", "bar32x8x8_T200.npz")
-    gold = np.load(gold_path) if os.path.exists(gold_path) else None
+    rollout, `repeats` times; falls back to the first two steps without it.
+    Single-threaded, in a child process. Returns a list of (seconds, steps)
+    per repeat and a description."""
+    gold = np.load(GOLD_BAR) if os.path.exists(GOLD_BAR) else None
     if gold is None or "samples_v" not in gold.files:
-        dt, k = oracle_sample(scene, 2)
-        return dt, k, f"first {k} PD steps of the same rollout, forward (exact fixed point) + adjoint, FP64, 1 thread"
-    with one_thread():
-        return _oracle_sample_mid(scene, steps, gold, solver, adjoint)
+        res = [oracle_sample(scene, 2) for _ in range(repeats)]
+        return res, "first 2 PD steps of the same rollout, forward (exact fixed point) + adjoint, FP64, 1 thread"
+    res, picked = single_threaded(_oracle_sample_mid, scene, tuple(steps), repeats)
+    return res, (f"PD steps {picked} of the same rollout (from the oracle's stored states), forward "
+                 "(exact fixed point) + adjoint each, FP64, 1 thread")
 
 
-def _oracle_sample_mid(scene, steps, gold, solver, adjoint):
+def _oracle_sample_mid(scene, steps, repeats):
+    from oracle import adjoint, solver
+    gold = np.load(GOLD_BAR)
     sc = scene.with_steps(1)
-    t0 = time.perf_counter()
-    pb = solver.build_problem(sc)
+    out = []
     picked = []
-    for i, t in enumerate(gold["sample_steps"]):
-        if int(t) not in steps:
-            continue
-        picked.append(int(t))
-        qT, vT, recs = solver.rollout(pb, sc, mode="exact", x0=gold["samples"][i], v0=gold["samples_v"][i])
-        _, dq, dv = adjoint.loss_and_grad(sc, pb, qT, vT)
-        adjoint.rollout_backward(pb, recs, dq, dv)
-    dt = time.perf_counter() - t0
-    return dt, len(picked), (f"PD steps {picked} of the same rollout (from the oracle's stored states), forward "
-                             "(exact fixed point) + adjoint each, FP64, 1 thread")
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        pb = solver.build_problem(sc)
+        picked = []
+        for i, t in enumerate(gold["sample_steps"]):
+            if int(t) not in steps:
+                continue
+            picked.append(int(t))
+            qT, vT, recs = solver.rollout(pb, sc, mode="exact", x0=gold["samples"][i], v0=gold["samples_v"][i])
+            _, dq, dv = adjoint.loss_and_grad(sc, pb, qT, vT)
+            adjoint.rollout_backward(pb, recs, dq, dv)
+        out.append((time.perf_counter() - t0, len(picked)))
+    return out, picked
 
 
 def run_reference(args, rank, world):
@@ -182,15 +205,10 @@ def run_reference(args, rank, world):
         return
     from paper_2605_14526_b300 import inputs
     scene = inputs.hetero_bar()
-    for _ in range(args.warmup):
-        oracle_sample_mid(scene, steps=(100,))
-    tot = 0.0
-    n = 0
-    what = ""
-    for _ in range(args.steps):
-        dt, k, what = oracle_sample_mid(scene, steps=(100,))
-        tot += dt
-        n += k
+    res, what = oracle_sample_mid(scene, steps=(100,), repeats=args.warmup + args.steps)
+    res = res[args.warmup:]          # the first repeats are the warm-up
+    tot = sum(r[0] for r in res)
+    n = sum(r[1] for r in res)
     value = n / tot
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
@@ -1001,7 +1019,8 @@ def main():
             "double_float_variant": df_variant,
             "clocks": clk.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, k, what = oracle_sample_mid(scene)
+        res, what = oracle_sample_mid(scene)
+        dt, k = res[0]
         line["cpu_baseline"] = {"value": k / dt, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
                                 "kind": "oracle", "sample": what}
     if rank == 0:
