@@ -265,3 +265,37 @@ def test_full_batch_first_steps_sampled_instances_match_oracle():
     for i in (order[0], order[len(order) // 2]):
         o = oracle_run(scenes[i], backward=False)
         assert rel(q[i], o["qT"]) <= 1e-5, (i, scenes[i].n_e, rel(q[i], o["qT"]))
+
+
+def test_instances_sharded_over_ranks_match_one_batch():
+    """The batched workload split by instance (replicas.py: the LPT share of
+    each of 2 ranks, run here one after the other on this GPU, no
+    collective between their kernels) gives every instance the result of
+    the whole batch in one launch, up to the reduction order of other team
+    sizes (FP64 local step, tight gate)."""
+    import dataclasses
+
+    from paper_2605_14526_b300.replicas import ShardedBatch, gather_instances, shard_instances
+    build()
+    scenes = small_batch(n=5, steps=3, seed=31)
+    tight = dataclasses.replace(scenes[0].solver, local_fp32=False, eps_res=1e-12, eps_step=1e-14, k_max=1000)
+    scenes = [s.replace(solver=tight) for s in scenes]
+    full = ShardedBatch(scenes, range(len(scenes)))
+    ref = full.rollout_and_adjoint()
+    full.close()
+    shares = shard_instances([s.n_e for s in scenes], 2)
+    assert all(shares)
+    share_all, res_all = [], {}
+    for share in shares:
+        sb = ShardedBatch(scenes, share)
+        out = sb.rollout_and_adjoint()
+        sb.close()
+        share_all += share
+        for k, v in out.items():
+            res_all.setdefault(k, []).extend(v)
+    got = gather_instances(share_all, res_all, len(scenes))
+    for i in range(len(scenes)):
+        for k in ("qT", "dq0", "dv0", "dE"):
+            assert rel(got[k][i], ref[k][i]) <= 1e-9, (i, k, rel(got[k][i], ref[k][i]))
+        assert abs(got["loss"][i] - ref["loss"][i]) <= 1e-9 * ref["loss"][i]
+        assert abs(got["dnu"][i] - ref["dnu"][i]) <= 1e-8 * abs(ref["dnu"][i])
