@@ -114,22 +114,46 @@ class BlockSysID(_Rollout):
         return f, g
 
 
+def rigid_velocity_basis(X, pinned):
+    """[3 n_v, 6] basis of rigid initial velocities v_i = u + omega x (X_i - c)
+    (c the centroid; columns u_x, u_y, u_z, omega_x, omega_y, omega_z), zero
+    on pinned vertices: the low-dimensional initial-state parametrisation of
+    the paper's inverse-design tasks (initial linear and angular velocity)."""
+    X = np.asarray(X, dtype=np.float64)
+    r = X - X.mean(axis=0)
+    n = X.shape[0]
+    B = np.zeros((n, 3, 6))
+    for i in range(3):
+        B[:, i, i] = 1.0
+    z = np.zeros(n)
+    B[:, :, 3] = np.stack([z, -r[:, 2], r[:, 1]], axis=1)
+    B[:, :, 4] = np.stack([r[:, 2], z, -r[:, 0]], axis=1)
+    B[:, :, 5] = np.stack([-r[:, 1], r[:, 0], z], axis=1)
+    B[np.asarray(pinned) != 0] = 0.0
+    return B.reshape(3 * n, 6)
+
+
 class InitialVelocity(_Rollout):
-    """Initial-state optimisation (Sec. 5.5): the initial velocity v0 of the
-    free vertices (3 n_v values; pinned rows are ignored) such that the
-    rollout ends at x*; loss 0.5 ||x_T(v0) - x*||^2, gradient dL/dv0 from
+    """Initial-state optimisation (Sec. 5.5): the initial velocity v0 = B p
+    (B: [3 n_v, k] basis, default the identity: every coordinate free;
+    pinned rows are ignored by the library) such that the rollout ends at
+    x*; loss 0.5 ||x_T(v0) - x*||^2, gradient B^T dL/dv0 with dL/dv0 from
     pd_backward."""
 
-    def __init__(self, scene, target_qT, options=None):
+    def __init__(self, scene, target_qT, basis=None, options=None):
         super().__init__(scene, options)
         self.target = self.t(target_qT)
+        self.basis = None if basis is None else np.ascontiguousarray(basis, dtype=np.float64)
         self.dv0 = torch.empty_like(self.x0)
         self.v = torch.empty_like(self.x0)
 
-    def __call__(self, v0_flat):
-        self.v.copy_(torch.as_tensor(np.asarray(v0_flat, dtype=np.float64).reshape(-1, 3)))
+    def __call__(self, p):
+        p = np.asarray(p, dtype=np.float64)
+        v0 = p if self.basis is None else self.basis @ p
+        self.v.copy_(torch.as_tensor(v0.reshape(-1, 3)))
         self.run(v0=self.v)
         diff = self.qT - self.target
         f = 0.5 * float(torch.sum(diff * diff))
         binding.pd_backward(self.pd.ctx, diff.contiguous(), None, None, self.dv0, None, None, None, 0)
-        return f, self.dv0.cpu().numpy().reshape(-1)
+        g = self.dv0.cpu().numpy().reshape(-1)
+        return f, (g if self.basis is None else self.basis.T @ g)
