@@ -96,6 +96,9 @@ def main():
     ap.add_argument("--repeat", type=int, default=2)
     ap.add_argument("--phases", action="store_true", help="print device phase times of the forward rollout")
     ap.add_argument("--persistent", type=int, default=1)
+    ap.add_argument("--solve-fp64", type=int, default=None,
+                    help="1: FP64 products with S (the benchmark's headline), 0: double-float; default: the "
+                         "workload's setting")
     args = ap.parse_args()
     build()
     if args.case == "block":
@@ -119,6 +122,8 @@ def main():
         n_e = pd.n_e
     else:
         opt = binding.options_for(sc.solver)
+        if args.solve_fp64 is not None:
+            opt.solve_fp64 = args.solve_fp64
         opt.persistent = args.persistent
         pd = binding.PDContext(sc, opt)
         x0, v0, f0 = t(sc.x0), t(sc.v0), t(sc.f_ext[0])
