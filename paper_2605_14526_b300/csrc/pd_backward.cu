@@ -528,6 +528,7 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
   const int gtid = tm.b * blockDim.x + tid;
   const int gthreads = tm.nb * blockDim.x;
   const int lane = tid & 31, gwarp = gtid >> 5, nwarps = gthreads >> 5;
+  const int twarp = (tid >> 5) * tm.nb + tm.b;   // block-minor numbering for the row-wise products
   const size_t nv3 = 3 * (size_t)d.n_v;
   const bool writer = tm.b == 0;
   const Range re = block_range(tm, d.n_e);
@@ -625,14 +626,14 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
       if (d.tmode) {
         FinRZ fin{&d, 0.0};
         const bool r = tsolve_team(d, reinterpret_cast<const double*>(d.bperm), reinterpret_cast<double*>(d.y), tm,
-                                   gwarp, nwarps, fin);
+                                   twarp, nwarps, fin);
         prz[0] += fin.acc;
         return r;
       }
-      for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, d.s_part, d.s_cnt, sg, lane);
+      for (int sg = twarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, d.s_part, d.s_cnt, sg, lane);
       if (!grid_sync(d, tm)) return false;
       if (ck && !project(ck, first)) return false;
-      for (int j = gwarp; j < d.n_f; j += nwarps) {
+      for (int j = twarp; j < d.n_f; j += nwarps) {
         double a0, a1, a2;
         spmv_st_sum(d, d.y, j, lane, a0, a1, a2);
         if (lane < 3) {

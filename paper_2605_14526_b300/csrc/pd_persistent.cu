@@ -106,6 +106,10 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
   const int gtid = tm.b * blockDim.x + tid;
   const int gthreads = tm.nb * blockDim.x;
   const int lane = tid & 31, gwarp = gtid >> 5, nwarps = gthreads >> 5;
+  // warps numbered block-minor for the row-wise products: consecutive rows
+  // (segments of one long row of S, rows of similar length) go to different
+  // SMs, so the FP64 work of the long rows spreads over the whole team
+  const int twarp = (tid >> 5) * tm.nb + tm.b;
   const size_t nv3 = 3 * (size_t)d.n_v;
   const bool writer = tm.b == 0;
   const Range re = block_range(tm, d.n_e);
@@ -208,11 +212,11 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
             for (int j = 0; j < 2 * kMaxAA; ++j) pa[j] = 0.0;
           FinAA fin{&d, av, pa, &s_pa[tid >> 5][0][0]};
           if (!(ok = tsolve_team(d, reinterpret_cast<const double*>(d.bperm), reinterpret_cast<double*>(d.y), tm,
-                                 gwarp, nwarps, fin)))
+                                 twarp, nwarps, fin)))
             break;
           mark(PH_SPMV_S);
         } else {
-          for (int sg = gwarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, d.s_part, d.s_cnt, sg, lane);
+          for (int sg = twarp; sg < d.n_seg; sg += nwarps) spmv_s_segment(d, d.bperm, d.y, d.s_part, d.s_cnt, sg, lane);
           work_done(PH_SPMV_S);
           if (!(ok = grid_sync(d, tm))) break;
           mark(PH_SPMV_S);
@@ -260,7 +264,7 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
           // registers they would stay live across the S^T loop)
           if (lane < 3)
             for (int j = 0; j < 2 * kMaxAA; ++j) pa[j] = 0.0;
-          for (int j = gwarp; j < d.n_f; j += nwarps) {
+          for (int j = twarp; j < d.n_f; j += nwarps) {
             double a0, a1, a2;
             spmv_st_sum(d, d.y, j, lane, a0, a1, a2);
             if (lane < 3) {
