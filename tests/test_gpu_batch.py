@@ -299,3 +299,25 @@ def test_instances_sharded_over_ranks_match_one_batch():
             assert rel(got[k][i], ref[k][i]) <= 1e-9, (i, k, rel(got[k][i], ref[k][i]))
         assert abs(got["loss"][i] - ref["loss"][i]) <= 1e-9 * ref["loss"][i]
         assert abs(got["dnu"][i] - ref["dnu"][i]) <= 1e-8 * abs(ref["dnu"][i])
+
+
+def test_full_batch_100_steps_against_stored_oracle_values():
+    """The whole benchmark batch (64 meshes, seed 11) over its 100 steps at
+    the configured settings (FP32 local step, gate 1e-6 / 1e-8), in one
+    launch per rollout and per adjoint; the smallest, the median and the
+    largest instance against the oracle's exact-fixed-point rollout and
+    direct adjoint stored by tests/golden/make_golden_batch.py."""
+    import os
+    gold = np.load(os.path.join(os.path.dirname(__file__), "golden", "batch64_seed11_T100.npz"))
+    scenes = inputs.batch_meshes(seed=11)
+    g = batch_run(scenes)
+    bc = g["bc"]
+    assert all(s.not_converged == 0 for s in g["inst"])
+    q, dq0, dv0 = bc.split_v(g["qT"]), bc.split_v(g["dq0"]), bc.split_v(g["dv0"])
+    dE = bc.split_e(g["dE"])
+    for name in ("smallest", "median", "largest"):
+        i = int(gold[f"{name}_index"][0])
+        assert rel(q[i], gold[f"{name}_qT"]) <= 1e-5, (name, rel(q[i], gold[f"{name}_qT"]))
+        for k, v in (("dq0", dq0), ("dv0", dv0), ("dE", dE)):
+            assert rel(v[i], gold[f"{name}_{k}"]) <= 1e-4, (name, k, rel(v[i], gold[f"{name}_{k}"]))
+    bc.close()
