@@ -82,6 +82,11 @@ def measured_traffic(kernel: str):
     return BAR_TRAFFIC.get(kernel.split()[0])
 
 
+# FP64 rate derived from the unit counts and the clock: 148 SMs x 2 FP64
+# multiply-adds per clock per SM x 2 flops x 2.032 GHz
+FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -369,6 +374,8 @@ def run_batch(args, rank, world, local_rank, dev, dist):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "e2e": {"value": e2e, "unit": "instance PD steps/s", "h2d_bytes_per_step": 2 * nv3b + 2 * nv3b,
                     "d2h_bytes_per_step": 2 * nv3b + 2 * nv3b + 8 * bc.n_e + 8 * bc.n},
+            "forward": {"value": world * bc.n * T * args.steps / (max_over_ranks(fwd_ms, dist, dev) / 1e3),
+                        "unit": "forward instance PD steps/s", "ms_per_rollout": fwd_ms / args.steps},
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "kernel": kname, "peak_kind": peak_kind, "avg_launch_ms": kms,
@@ -465,6 +472,8 @@ def run_contact(args, rank, world, local_rank, dev, dist):
                        "adjoint_contact_cg_passes_per_step": cpass_b / (args.steps * T),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "e2e": None,
+            "forward": {"value": world * T * args.steps / (max_over_ranks(fwd_ms, dist, dev) / 1e3),
+                        "unit": "forward PD steps/s", "ms_per_rollout": fwd_ms / args.steps},
             "gpu_launches": int(launches),
             "roofline": {"bound": "fp64", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "kernel": "k_fwd_rollout (persistent forward with contact)",
@@ -617,21 +626,30 @@ def run_block(args, rank, world, local_rank, dev, dist):
                        "fwd_ms_per_pd_step": fwd_ms / (args.steps * T), "bwd_ms_per_pd_step": bwd_ms / (args.steps * T),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "e2e": None,
+            "forward": {"value": world * T * args.steps / (max_over_ranks(fwd_ms, dist, dev) / 1e3),
+                        "unit": "forward PD steps/s", "ms_per_rollout": fwd_ms / args.steps},
             "gpu_launches": int(launches),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "kernel": kname, "peak_kind": peak_kind, "avg_launch_ms": kms,
-                         "bytes_per_launch": kbytes, "fwd_launch_ms": fwd_launch_ms, "bwd_launch_ms": bwd_launch_ms,
-                         "fwd_iter_bytes": fwd_iter_bytes, "bwd_iter_bytes": bwd_iter_bytes,
-                         "fp64_solve_tflops": fp64_flops / (kms * 1e-3) / 1e12,
-                         "fp64_note": "solve FP64 flops of the dominant launch over its time; nominal B300 FP64 "
-                                      "rate 1.25 TFLOP/s"},
+            "roofline": {"bound": "alu", "achieved": fp64_flops / (kms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": fp64_flops / (kms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                         "traffic": None, "kernel": kname, "avg_launch_ms": kms,
+                         "peak_kind": "derived: 148 SMs x 2 FP64 FMA per clock x 2 flops x 2032 MHz",
+                         "flops_per_launch": fp64_flops,
+                         "note": "FP64 flops of the triangular solves (12 per stored entry and solve) in the "
+                                 "dominant launch; the sweeps run 0.75 flop/B, above the FP64 ridge",
+                         "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                                 "bytes_per_launch": kbytes, "peak_kind": peak_kind},
+                         "fwd_launch_ms": fwd_launch_ms, "bwd_launch_ms": bwd_launch_ms,
+                         "fwd_iter_bytes": fwd_iter_bytes, "bwd_iter_bytes": bwd_iter_bytes},
             "local_step": {"achieved": local_gbs, "peak": peak, "unit": "GB/s", "frac": local_gbs / peak,
                            "bytes_per_launch": local_bytes, "avg_ms": local_ms, "launches_timed": nrep,
                            "kernels": "k_local_all + k_rhs_out (pd_local_rhs)", "peak_kind": peak_kind,
                            "model": "neohookean (FP32 local step)",
                            "corotated": {"achieved": local_bytes / (local_co_ms * 1e-3) / 1e9,
                                          "frac": local_bytes / (local_co_ms * 1e-3) / 1e9 / peak,
-                                         "avg_ms": local_co_ms}},
+                                         "avg_ms": local_co_ms},
+                           "note": "k_local_all is issue-bound (ncu: 66% of issue slots, about 1,480 thread "
+                                   "instructions per element for SVD, prox Newton and corner forces), "
+                                   "profiles/local_step_block64.md"},
             "clocks": clk.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         small = inputs.large_block(n=12, steps=1, seed=5)
@@ -1073,6 +1091,8 @@ def main():
                        "mean_fwd_iters_per_pd_step": iters / (args.steps * T),
                        "mean_adjoint_iters_per_pd_step": adj / (args.steps * T)},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "forward": {"value": world * T * args.steps / (max_over_ranks(fwd_ms, dist, dev) / 1e3),
+                        "unit": "forward PD steps/s", "ms_per_rollout": fwd_ms / args.steps},
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": measured_traffic(kname), "kernel": kname,
