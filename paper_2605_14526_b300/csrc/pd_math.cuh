@@ -202,10 +202,10 @@ __device__ __forceinline__ int nh_prox_from(const T* sF, const NHMean<T>& m, con
   const T loose = f32 ? T(1e-5) : T(1e-11);
 #pragma unroll
   for (int i = 0; i < 3; ++i) s[i] = s0[i];
+  T g[3], lnJ;   // gradient at s (the accepted trial's gradient after the first iteration)
+  nh_grad(s, m, sF, g, lnJ);
   int it = 0;
   for (; it < 40; ++it) {
-    T g[3], lnJ;
-    nh_grad(s, m, sF, g, lnJ);
     const T gmax = fmax(fmax(dabs(g[0]), dabs(g[1])), dabs(g[2]));
     if (!(gmax > tol * m.k)) break;     // converged (also exits on NaN)
     T H[9], Hi[9], d[3];
@@ -230,10 +230,10 @@ __device__ __forceinline__ int nh_prox_from(const T* sF, const NHMean<T>& m, con
     T trial[3];
     T f0 = T(0);
     bool have_f0 = false;
+    T gt[3], lt = T(0);
     for (int hh = 0; hh < 40; ++hh) {
 #pragma unroll
       for (int i = 0; i < 3; ++i) trial[i] = s[i] + t * d[i];
-      T gt[3], lt;
       nh_grad(trial, m, sF, gt, lt);
       const T gtmax = fmax(fmax(dabs(gt[0]), dabs(gt[1])), dabs(gt[2]));
       if (newton && gtmax <= T(0.5) * gmax) {
@@ -253,7 +253,11 @@ __device__ __forceinline__ int nh_prox_from(const T* sF, const NHMean<T>& m, con
     }
     if (!ok) break;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) s[i] = trial[i];
+    for (int i = 0; i < 3; ++i) {
+      s[i] = trial[i];
+      g[i] = gt[i];
+    }
+    lnJ = lt;
   }
   return it;
 }
