@@ -53,3 +53,33 @@ def test_noalloc_rejects_meshes_above_its_limit():
         binding.pd_solve_noalloc(pd.ctx, x, x)
     assert e.value.code == 11 and "65536" in str(e.value)
     pd.close()
+
+
+def test_noalloc_solve_captures_into_a_cuda_graph():
+    """After one call (which looks up the scratch's address), the call only
+    enqueues kernels on the caller's stream: it can be captured into a CUDA
+    graph, and replays on new right-hand sides give pd_solve's results."""
+    build()
+    sc = inputs.hetero_bar(steps=1)
+    pd = binding.PDContext(sc)
+    rng = np.random.default_rng(12)
+    b = torch.tensor(rng.standard_normal((sc.n_v, 3)), device="cuda:0")
+    out = torch.zeros_like(b)
+    binding.pd_solve_noalloc(pd.ctx, b, out)          # warm-up outside the capture
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        binding.pd_solve_noalloc(pd.ctx, b, out, s)
+    for _ in range(2):
+        b.copy_(torch.tensor(rng.standard_normal((sc.n_v, 3)), device="cuda:0"))
+        out.fill_(float("nan"))
+        g.replay()
+        ref = torch.full_like(b, float("nan"))
+        binding.pd_solve(pd.ctx, b, ref)
+        torch.cuda.synchronize()
+        r, o = ref.cpu().numpy(), out.cpu().numpy()
+        assert np.all(np.isfinite(o))
+        assert np.linalg.norm(o - r) <= 1e-12 * np.linalg.norm(r)
+    del g
+    pd.close()
