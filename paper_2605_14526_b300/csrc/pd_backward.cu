@@ -528,7 +528,7 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
   const int gtid = tm.b * blockDim.x + tid;
   const int gthreads = tm.nb * blockDim.x;
   const int lane = tid & 31, gwarp = gtid >> 5, nwarps = gthreads >> 5;
-  const int twarp = (tid >> 5) * tm.nb + tm.b;   // block-minor numbering for the row-wise products
+  const int twarp = tm.nb >= kWideTeam ? (tid >> 5) * tm.nb + tm.b : gwarp;   // as in the forward rollout
   const size_t nv3 = 3 * (size_t)d.n_v;
   const bool writer = tm.b == 0;
   const Range re = block_range(tm, d.n_e);

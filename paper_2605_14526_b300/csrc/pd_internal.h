@@ -6,6 +6,7 @@
 namespace pdk {
 
 constexpr int kMaxAA = 8;        // largest Anderson window
+constexpr int kWideTeam = 64;    // teams of at least this many blocks number warps block-minor for row-wise products
 constexpr int kRed = 24;         // doubles per block in the reduction scratch
 constexpr int kVtxBlock = 256;   // threads per block, vertex kernels
 constexpr int kTetBlock = 128;   // threads per block, element kernels

@@ -106,10 +106,13 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
   const int gtid = tm.b * blockDim.x + tid;
   const int gthreads = tm.nb * blockDim.x;
   const int lane = tid & 31, gwarp = gtid >> 5, nwarps = gthreads >> 5;
-  // warps numbered block-minor for the row-wise products: consecutive rows
-  // (segments of one long row of S, rows of similar length) go to different
-  // SMs, so the FP64 work of the long rows spreads over the whole team
-  const int twarp = (tid >> 5) * tm.nb + tm.b;
+  // a large team numbers its warps block-minor for the row-wise products:
+  // consecutive rows (segments of one long row of S, rows of similar
+  // length) go to different SMs, so the FP64 work of the long rows spreads
+  // over the team (bar, 148 blocks: 204 -> 217.5 PD steps/s); a small team
+  // keeps neighbouring rows, whose S^T rows share their ancestors' y values,
+  // on one SM's L1 (64-mesh batch: 437 vs 414 instance PD steps/s)
+  const int twarp = tm.nb >= kWideTeam ? (tid >> 5) * tm.nb + tm.b : gwarp;
   const size_t nv3 = 3 * (size_t)d.n_v;
   const bool writer = tm.b == 0;
   const Range re = block_range(tm, d.n_e);
