@@ -61,7 +61,7 @@ def max_over_ranks(value, dist, device):
 # a full 200-step launch; profiles/bench_traffic_bar32x8x8.md), valid only
 # for the kernel sources it was taken with (their hash): reported as null
 # once any source under csrc/ has changed since.
-BAR_TRAFFIC = {"src": "598607ac0d986d0d", "k_fwd_rollout": 17577472 + 2335232, "k_bwd_rollout": 31009280 + 9857536}
+BAR_TRAFFIC = {"src": "b7107f1ec349886b", "k_fwd_rollout": 17583616 + 2621952, "k_bwd_rollout": 30786560 + 10531584}
 
 
 def csrc_hash() -> str:
