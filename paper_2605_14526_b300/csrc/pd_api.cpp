@@ -807,7 +807,7 @@ int enqueue_fwd_single(pd_ctx* c, int T, const double* q0d, const double* v0d, c
   br.f_stride = f_stride;
   br.qT = qTd;
   br.vT = vTd;
-  CK(pdk::launch_fwd_rollout(d.local_fp32 != 0, c->d_dev, c->d_team[0], c->d_off, br, grid, s));
+  CK(pdk::launch_fwd_rollout(d.local_fp32 != 0, c->d_dev, c->d_team[0], c->d_off, br, grid, d.tmode != 0, s));
   c->launches += 1;
   c->last_T = T;
   return PD_OK;
@@ -830,7 +830,7 @@ int enqueue_bwd_single(pd_ctx* c, const double* dqTd, const double* dvTd, double
   br.df = dfd;
   br.df_stride = df_stride;
   CK(cudaMemsetAsync(&d.ctrl->bar_arrive, 0, sizeof(unsigned long long), s));
-  CK(pdk::launch_bwd_rollout(d.local_fp32 != 0, c->d_dev, c->d_team[1], c->d_off, br, grid, s));
+  CK(pdk::launch_bwd_rollout(d.local_fp32 != 0, c->d_dev, c->d_team[1], c->d_off, br, grid, d.tmode != 0, s));
   c->launches += 1;
   return PD_OK;
 }

@@ -851,9 +851,10 @@ int persistent_grid_bwd(bool fp32, int blocks_per_sm) {
 }
 
 cudaError_t launch_bwd_rollout(bool fp32, const Dev* devs, const int4* team, const InstOff* off, const BatchBwd& br,
-                               int grid, cudaStream_t s) {
-  if (fp32) return coop_launch(k_bwd_rollout<float>, grid, kBwdBlock, s, devs, team, off, br);
-  return coop_launch(k_bwd_rollout<double>, grid, kBwdBlock, s, devs, team, off, br);
+                               int grid, bool tstage, cudaStream_t s) {
+  const size_t sm = tstage ? kTStageBytes : 0;
+  if (fp32) return coop_launch(k_bwd_rollout<float>, grid, kBwdBlock, sm, s, devs, team, off, br);
+  return coop_launch(k_bwd_rollout<double>, grid, kBwdBlock, sm, s, devs, team, off, br);
 }
 
 }  // namespace pdk

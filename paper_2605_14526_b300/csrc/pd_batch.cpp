@@ -54,6 +54,13 @@ struct pd_batch {
 
 namespace {
 
+// whether some instance solves in mode T (its launch requests the dynamic
+// shared staging of the triangular sweeps)
+bool any_tmode(const pd_batch& B) {
+  for (const pd_ctx* k : B.kids)
+    if (k->d.tmode) return true;
+  return false;
+}
 
 // Team sizes minimise the largest predicted instance time: every instance
 // gets one block, then blocks go one at a time to the instance whose
@@ -354,7 +361,7 @@ int batch_rollout(pd_ctx* c, int T, const double* q0, const double* v0, const do
   br.f_stride = f_stride;
   br.qT = qTd;
   br.vT = vTd;
-  CK(pdk::launch_fwd_rollout(c->opt.local_fp32 != 0, B.d_devs, B.d_team[0], B.d_off, br, B.grid[0], s));
+  CK(pdk::launch_fwd_rollout(c->opt.local_fp32 != 0, B.d_devs, B.d_team[0], B.d_off, br, B.grid[0], any_tmode(B), s));
   c->launches += 1;
   c->last_T = T;
   for (pd_ctx* k : B.kids) k->last_T = T;
@@ -420,7 +427,7 @@ int batch_backward(pd_ctx* c, const double* dqT, const double* dvT, double* dq0,
   br.dnu = dnud;
   br.df = dfd;
   br.df_stride = df_stride;
-  CK(pdk::launch_bwd_rollout(c->opt.local_fp32 != 0, B.d_devs, B.d_team[1], B.d_off, br, B.grid[1], s));
+  CK(pdk::launch_bwd_rollout(c->opt.local_fp32 != 0, B.d_devs, B.d_team[1], B.d_off, br, B.grid[1], any_tmode(B), s));
   c->launches += 1;
   if (!sync) {
     c->pending |= 2;

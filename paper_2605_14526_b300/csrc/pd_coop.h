@@ -11,14 +11,14 @@
 namespace pdk {
 
 template <typename... K, typename... A>
-inline cudaError_t coop_launch(void (*fn)(K...), int grid, int block, cudaStream_t s, A&&... args) {
+inline cudaError_t coop_launch(void (*fn)(K...), int grid, int block, size_t smem, cudaStream_t s, A&&... args) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeCooperative;
   at[0].val.cooperative = 1;
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cfg.attrs = at;
   cfg.numAttrs = 1;

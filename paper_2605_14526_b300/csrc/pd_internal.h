@@ -6,6 +6,7 @@
 namespace pdk {
 
 constexpr int kMaxAA = 8;        // largest Anderson window
+constexpr size_t kTStageBytes = 1024 * 3 * sizeof(double);   // dynamic shared staging of mode T (kTStage rows)
 constexpr int kWideTeam = 64;    // teams of at least this many blocks number warps block-minor for row-wise products
 constexpr int kRed = 24;         // doubles per block in the reduction scratch
 constexpr int kVtxBlock = 256;   // threads per block, vertex kernels

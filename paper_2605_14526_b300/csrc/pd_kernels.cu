@@ -267,8 +267,8 @@ void launch_apply_inverse(const Dev& d, cudaStream_t s, const float2* xperm, flo
     const int g = tsweep_blocks(d);
     const double* b = reinterpret_cast<const double*>(xperm);
     double* yy = reinterpret_cast<double*>(y);
-    for (int h = 0; h < d.t_nlev; ++h) k_tsweep_fwd<<<g, kTBlock, 0, s>>>(d, b, yy, h, check);
-    for (int h = d.t_nlev - 1; h >= 0; --h) k_tsweep_bwd<<<g, kTBlock, 0, s>>>(d, yy, out, h, check);
+    for (int h = 0; h < d.t_nlev; ++h) k_tsweep_fwd<<<g, kTBlock, kTStageBytes, s>>>(d, b, yy, h, check);
+    for (int h = d.t_nlev - 1; h >= 0; --h) k_tsweep_bwd<<<g, kTBlock, kTStageBytes, s>>>(d, yy, out, h, check);
     return;
   }
   k_spmv_s<<<spmv_blocks(d), 32 * kWarpsSpmv, 0, s>>>(d, xperm, y, part, cnt, check);

@@ -39,11 +39,13 @@ int coop_blocks_per_sm(const void* fn, int block, int* sms);
 // its team, team size, 0}.
 int persistent_grid(bool fp32, int blocks_per_sm);
 int persistent_grid_max(bool fp32);   // the larger grid of the two forward shapes
+// tstage: some instance of the launch solves in mode T (its dynamic shared
+// staging is requested)
 cudaError_t launch_fwd_rollout(bool fp32, const Dev* devs, const int4* team, const InstOff* off, const BatchFwd& br,
-                               int grid, cudaStream_t s);
+                               int grid, bool tstage, cudaStream_t s);
 int persistent_grid_bwd(bool fp32, int blocks_per_sm);
 cudaError_t launch_bwd_rollout(bool fp32, const Dev* devs, const int4* team, const InstOff* off, const BatchBwd& br,
-                               int grid, cudaStream_t s);
+                               int grid, bool tstage, cudaStream_t s);
 
 // backward (Alg. 2)
 void launch_bwd_setup(const Dev& d, cudaStream_t s, const double* qstar, const double* tau_t);

@@ -417,7 +417,8 @@ int coop_blocks_per_sm(const void* fn, int block, int* sms_out) {
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0) != cudaSuccess) return 0;
+  // with the mode-T staging (the larger request), so that a grid fits either launch
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, kTStageBytes) != cudaSuccess) return 0;
   if (sms_out) *sms_out = sms;
   return per_sm < 2 ? per_sm : 2;
 }
@@ -450,17 +451,18 @@ int persistent_grid_max(bool fp32) {
 
 // a grid of at most one block per SM takes the wide shape
 cudaError_t launch_fwd_rollout(bool fp32, const Dev* devs, const int4* team, const InstOff* off, const BatchFwd& br,
-                               int grid, cudaStream_t s) {
+                               int grid, bool tstage, cudaStream_t s) {
+  const size_t sm = tstage ? kTStageBytes : 0;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   if (grid <= sms) {
-    if (fp32) return coop_launch(k_fwd_rollout<float, kFwdWideBlock, 1>, grid, kFwdWideBlock, s, devs, team, off, br);
-    return coop_launch(k_fwd_rollout<double, kFwdWideBlock, 1>, grid, kFwdWideBlock, s, devs, team, off, br);
+    if (fp32) return coop_launch(k_fwd_rollout<float, kFwdWideBlock, 1>, grid, kFwdWideBlock, sm, s, devs, team, off, br);
+    return coop_launch(k_fwd_rollout<double, kFwdWideBlock, 1>, grid, kFwdWideBlock, sm, s, devs, team, off, br);
   }
-  if (fp32) return coop_launch(k_fwd_rollout<float, kFwdNarrowBlock, 2>, grid, kFwdNarrowBlock, s, devs, team, off, br);
-  return coop_launch(k_fwd_rollout<double, kFwdNarrowBlock, 2>, grid, kFwdNarrowBlock, s, devs, team, off, br);
+  if (fp32) return coop_launch(k_fwd_rollout<float, kFwdNarrowBlock, 2>, grid, kFwdNarrowBlock, sm, s, devs, team, off, br);
+  return coop_launch(k_fwd_rollout<double, kFwdNarrowBlock, 2>, grid, kFwdNarrowBlock, sm, s, devs, team, off, br);
 }
 
 }  // namespace pdk

@@ -50,9 +50,12 @@ __device__ __forceinline__ void t_gather(const Dev& d, int64_t g, double& a0, do
 
 // the shared staging vector of both sweeps (one per block; a function-scope
 // shared array is a single object per kernel)
+// the staging vector lives in dynamic shared memory, which only launches
+// that may run mode T request (kTStageBytes): a mode-S launch keeps the L1
+// share of the SM's unified L1 / shared memory for its gathers
 __device__ __forceinline__ double* t_stage() {
-  __shared__ double st[kTStage * 3];
-  return st;
+  extern __shared__ double t_stage_dyn[];
+  return t_stage_dyn;
 }
 
 __device__ __forceinline__ double t_warp_sum(double v) {
