@@ -119,3 +119,53 @@ def test_contact_impulses_match_oracle(oracle_pad):
         assert rel(ln[o], recs[t]["lam_n"]) <= 1e-6
         assert rel(lf[o], recs[t]["lam_f"]) <= 1e-5
         assert np.all(ln >= 0.0)
+
+
+def test_full_pad_steps_are_contact_fixed_points():
+    """The full pad (48x48x12 cells, 138,240 tets, 1e7 Pa core, 2,690
+    contact candidates), its first 3 steps at the configured settings (FP32
+    local step, gate 1e-6 / 1e-8). The oracle's contact rollout of this pad
+    takes hours, so each GPU step is checked by properties the oracle
+    computes at any size: the converged positions q_{t+1} and the step's
+    impulses (pd_get_contact_impulses) must be a fixed point of the
+    contact-corrected local-global map (eq. q_update: q = A^-1 (b(q) +
+    J^T lam), with the oracle's local step, assembly and sparse solve), and
+    the impulses complementary to the gaps: lam_n >= 0, no penetration
+    beyond the gate's resolution, lam_n gap = 0, and |lam_f| <= mu lam_n."""
+    build()
+    sc = inputs.contact_pad(steps=3)
+    code, qT, st, pd = _gpu(sc)
+    assert binding.STATUS[code] == "PD_OK" and st.contact_unconverged == 0
+    pb = solver.build_problem(sc)
+    spec = sc.contact
+    h = sc.dt
+    q_prev = None
+    for t in range(sc.steps):
+        q_t = binding.pd_get_checkpoint(pd.ctx, t, sc.n_v)
+        q_n = binding.pd_get_checkpoint(pd.ctx, t + 1, sc.n_v) if t + 1 < sc.steps else qT
+        v_t = sc.v0 if t == 0 else (q_t - q_prev) / h
+        verts, lam_n, lam_f = binding.pd_get_contact_impulses(pd.ctx, t)
+        D = np.where(np.isin(verts, spec.ground), 1.0, -1.0)
+        heights = np.where(D > 0, spec.ground_z, spec.box_z(t))
+        # the contact-corrected map at the GPU's converged state
+        b0 = solver.rhs_const(pb, q_t, v_t, sc.f_ext[0])
+        q_u = solver.solve_A(pb, solver.free_rhs(pb, solver.rhs(pb, b0, q_n)))
+        pos = np.searchsorted(pb.free, verts)
+        r = np.zeros((pb.free.size, 3))
+        r[pos, 0] = lam_f[:, 0]
+        r[pos, 1] = lam_f[:, 1]
+        r[pos, 2] = D * lam_n
+        q_map = q_u + solver.solve_A(pb, r)
+        err = rel(q_map, q_n[pb.free])
+        assert err <= 2e-6, (t, err)
+        # complementarity and the friction disk
+        gap = D * (q_n[verts, 2] - heights)
+        scale = np.abs(q_n[:, 2]).max()
+        assert np.all(lam_n >= 0.0)
+        assert gap.min() >= -1e-6 * scale, (t, gap.min())
+        active = lam_n > 1e-9 * lam_n.sum()
+        assert np.abs(gap[active]).max() <= 1e-6 * scale, (t, np.abs(gap[active]).max())
+        assert np.all(np.linalg.norm(lam_f, axis=1) <= spec.mu * lam_n * (1 + 1e-6) + 1e-15)
+        assert active.sum() > 100   # the box presses: many active contacts
+        q_prev = q_t
+    pd.close()
