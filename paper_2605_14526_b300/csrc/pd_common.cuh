@@ -46,21 +46,25 @@ __device__ __forceinline__ double warp_sum_scatter(const double (&v)[NV], int la
 }
 
 // block-wide sum of v[NV] (warp sums in a fixed order, then the warps in
-// order) into sh_out[NV] (shared), read by threads < NV
+// order) into sh_out[NV] (shared), read by threads < NV. Only threads below
+// `nactive` hold values (the others hold zeros): the warps past them skip
+// their FP64 shuffle tree and the final sum, which leaves the result
+// unchanged (each FP64 instruction costs a scheduler about 64 cycles here)
 template <int NV>
-__device__ __forceinline__ double block_sum_lane(double (&v)[NV]) {
+__device__ __forceinline__ double block_sum_lane(double (&v)[NV], int nactive = 1 << 30) {
   __shared__ double sh[32][NV];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = ((nactive < (int)blockDim.x ? nactive : (int)blockDim.x) + 31) >> 5;
   constexpr int P = pow2_ceil(NV);
-  int idx;
-  const double x = warp_sum_scatter<NV>(v, lane, idx);
-  if ((lane & (32 / P - 1)) == 0 && idx < NV) sh[wid][idx] = x;
+  if (wid < nw) {
+    int idx;
+    const double x = warp_sum_scatter<NV>(v, lane, idx);
+    if ((lane & (32 / P - 1)) == 0 && idx < NV) sh[wid][idx] = x;
+  }
   __syncthreads();
   double s = 0.0;
-  if (threadIdx.x < NV) {
-    const int nw = (blockDim.x + 31) >> 5;
+  if (threadIdx.x < NV)
     for (int w = 0; w < nw; ++w) s += sh[w][threadIdx.x];
-  }
   return s;
 }
 
@@ -74,8 +78,8 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* red,
 // block-wide sum of v[NV] into out[NV] (shared), visible to the whole block
 // on return
 template <int NV>
-__device__ __forceinline__ void block_reduce_to(double (&v)[NV], double* out) {
-  const double s = block_sum_lane<NV>(v);
+__device__ __forceinline__ void block_reduce_to(double (&v)[NV], double* out, int nactive = 1 << 30) {
+  const double s = block_sum_lane<NV>(v, nactive);
   if (threadIdx.x < NV) out[threadIdx.x] = s;
   __syncthreads();
 }

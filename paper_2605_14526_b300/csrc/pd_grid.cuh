@@ -110,7 +110,7 @@ __device__ __forceinline__ bool grid_reduce_all_v(const Dev& d, Team tm, double 
 #pragma unroll
       for (int j = 0; j < NV; ++j) acc[j] += w[j];
     }
-    block_reduce_to<NV>(acc, sums);
+    block_reduce_to<NV>(acc, sums, tm.nb);   // threads >= tm.nb hold no row
   }
   return !s_fail;
 }
