@@ -255,7 +255,7 @@ int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_o
   double* contrib;
   double* jac;
   double* sstar;
-  if ((r = dalloc(c, &contrib, (size_t)pdk::kElemVals * c->n_e)) || (r = dalloc(c, &jac, (size_t)pdk::kJacRec * c->n_e)) ||
+  if ((r = dalloc(c, &contrib, 12 * (size_t)c->n_e)) || (r = dalloc(c, &jac, (size_t)pdk::kJacRec * c->n_e)) ||
       (r = dalloc(c, &sstar, 3 * (size_t)c->n_e)))
     return r;
   d.contrib = contrib;

@@ -132,10 +132,9 @@ __device__ __forceinline__ void pcg_w_warp(const Dev& d, int v, const double* po
     for (int i = 0; i < 3; ++i) c[i] += a * p_next(d, pold, 3 * (size_t)u + i, beta);
   }
   for (int p = d.inc_ptr[v] + lane; p < d.inc_ptr[v + 1]; p += 32) {
-    T f[3];
-    load_corner<T>(cb, d.inc_idx[p], f);
+    const int ic = d.inc_idx[p];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) c[i] -= (double)f[i];
+    for (int i = 0; i < 3; ++i) c[i] -= (double)cb[3 * (size_t)ic + i];
   }
   int i;
   const double w = warp_sum_scatter<3>(c, lane, i);   // component i in lanes 8i .. 8i+7
@@ -162,10 +161,9 @@ __device__ __forceinline__ void resid_warp(const Dev& d, int v, int lane) {
     for (int i = 0; i < 3; ++i) c[i] += a * d.mu[3 * (size_t)u + i];
   }
   for (int p = d.inc_ptr[v] + lane; p < d.inc_ptr[v + 1]; p += 32) {
-    T f[3];
-    load_corner<T>(cb, d.inc_idx[p], f);
+    const int ic = d.inc_idx[p];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) c[i] -= (double)f[i];
+    for (int i = 0; i < 3; ++i) c[i] -= (double)cb[3 * (size_t)ic + i];
   }
   int i;
   const double w = warp_sum_scatter<3>(c, lane, i);

@@ -141,7 +141,9 @@ __device__ __forceinline__ void kapply_item(const Dev& d, int e, const double* p
     for (int j = 0; j < 3; ++j) dp[3 * i + j] = W[3 * i] * V[3 * j] + W[3 * i + 1] * V[3 * j + 1] + W[3 * i + 2] * V[3 * j + 2];
   T c12[12];
   corner_forces<T>(dp, Bm, coef, c12);
-  store_corners<T>(d.contrib, e, c12);
+  T* out = reinterpret_cast<T*>(d.contrib) + 12 * (size_t)e;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) out[i] = c12[i];
 }
 
 }  // namespace pdk

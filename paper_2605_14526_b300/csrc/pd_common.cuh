@@ -214,44 +214,6 @@ __device__ __forceinline__ void project(const Dev& d, const T* F, T* P, T* U, T*
     for (int j = 0; j < 3; ++j) P[3 * i + j] = U[3 * i] * ss[0] * V[3 * j] + U[3 * i + 1] * ss[1] * V[3 * j + 1] + U[3 * i + 2] * ss[2] * V[3 * j + 2];
 }
 
-// one corner (index ic = 4 e + a) of the corner-force buffer
-template <typename T>
-__device__ __forceinline__ void load_corner(const T* cb, int ic, T (&f)[3]);
-template <>
-__device__ __forceinline__ void load_corner<float>(const float* cb, int ic, float (&f)[3]) {
-  const float4 v = *reinterpret_cast<const float4*>(cb + kCornerVals * (size_t)ic);
-  f[0] = v.x;
-  f[1] = v.y;
-  f[2] = v.z;
-}
-template <>
-__device__ __forceinline__ void load_corner<double>(const double* cb, int ic, double (&f)[3]) {
-  const double* c = cb + kCornerVals * (size_t)ic;
-  const double2 v = *reinterpret_cast<const double2*>(c);
-  f[0] = v.x;
-  f[1] = v.y;
-  f[2] = c[2];
-}
-
-// the 12 corner values of element e (corner a: c12[3a .. 3a+2])
-template <typename T>
-__device__ __forceinline__ void store_corners(void* contrib, int e, const T (&c12)[12]);
-template <>
-__device__ __forceinline__ void store_corners<float>(void* contrib, int e, const float (&c12)[12]) {
-  float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(contrib) + kElemVals * (size_t)e);
-#pragma unroll
-  for (int a = 0; a < 4; ++a) o[a] = make_float4(c12[3 * a], c12[3 * a + 1], c12[3 * a + 2], 0.f);
-}
-template <>
-__device__ __forceinline__ void store_corners<double>(void* contrib, int e, const double (&c12)[12]) {
-  double* o = reinterpret_cast<double*>(contrib) + kElemVals * (size_t)e;
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    *reinterpret_cast<double2*>(o + kCornerVals * a) = make_double2(c12[3 * a], c12[3 * a + 1]);
-    o[kCornerVals * a + 2] = c12[3 * a + 2];
-  }
-}
-
 // acc += the corner contributions of vertex v, in incidence order. Indices
 // and values are loaded in chunks of 8 before they are added, so the
 // dependent index -> value loads of a chunk overlap instead of running one
@@ -266,10 +228,9 @@ __device__ __forceinline__ void gather_contrib(const Dev& d, int v, double* acc)
     for (int u = 0; u < 8; ++u) ic[u] = p0 + u < end ? d.inc_idx[p0 + u] : -1;
     T val[8][3];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      if (ic[u] >= 0) load_corner<T>(cb, ic[u], val[u]);
-      else val[u][0] = val[u][1] = val[u][2] = T(0);
-    }
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) val[u][i] = ic[u] >= 0 ? cb[3 * (size_t)ic[u] + i] : T(0);
 #pragma unroll
     for (int u = 0; u < 8; ++u)
       if (ic[u] >= 0)

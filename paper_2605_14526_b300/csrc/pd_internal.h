@@ -6,10 +6,6 @@
 namespace pdk {
 
 constexpr int kMaxAA = 8;        // largest Anderson window
-// the corner-force buffer: 4 corners per element, each padded from 3 to 4
-// values so that a gather reads a corner with one vector load
-constexpr int kCornerVals = 4;
-constexpr int kElemVals = 4 * kCornerVals;
 constexpr size_t kTStageBytes = 1024 * 3 * sizeof(double);   // dynamic shared staging of mode T (kTStage rows)
 constexpr int kWideTeam = 64;    // teams of at least this many blocks number warps block-minor for row-wise products
 constexpr int kRed = 24;         // doubles per block in the reduction scratch
@@ -202,7 +198,7 @@ struct Dev {
   float2* y;        // [n_f][3] S b (double-float)
   double* dQG;      // [kMaxAA][n_v][3] history sums dQ_j + dG_j
   double* dG;
-  void* contrib;    // [n_e][4 corners][kCornerVals] float or double (3 used)
+  void* contrib;    // [n_e][12] float or double
   void* sstar;      // [n_e][3] float: last prox stretches (Newton warm start; <= 0 = none)
   double* red;      // [blocks][kRed]
   Ctrl* ctrl;

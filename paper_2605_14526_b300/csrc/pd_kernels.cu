@@ -8,7 +8,7 @@
 // Data layout: vertex vectors are [n_v][3] float64; pinned vertices keep
 // q = X and carry zeros in every difference/residual vector so that norms and
 // dot products run over free DoFs only. The RHS scatter is deterministic:
-// elements write their 12 corner contributions (4 corners padded to 4 values), a per-vertex gather sums them
+// elements write their 12 corner contributions, a per-vertex gather sums them
 // in FP64 together with the constant part b0.
 #include <cuda_runtime.h>
 
@@ -67,8 +67,7 @@ __global__ void __launch_bounds__(kVtxBlock) k_rhs_out(Dev d, double* out) {
     // FP32 corner forces summed in double-float on the FP32 pipe
     float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0;
     for (; p < end; ++p) {
-      float f[3];
-      load_corner<float>(cb, d.inc_idx[p], f);
+      const float* f = cb + 3 * (size_t)d.inc_idx[p];
       a0 = df_add_f(a0, f[0]);
       a1 = df_add_f(a1, f[1]);
       a2 = df_add_f(a2, f[2]);
@@ -85,7 +84,9 @@ __global__ void __launch_bounds__(kVtxBlock) k_rhs_out(Dev d, double* out) {
     for (int i = 0; i < 4; ++i) ic[i] = d.inc_idx[p + i];
     T f[4][3];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) load_corner<T>(cb, ic[i], f[i]);
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) f[i][j] = cb[3 * (size_t)ic[i] + j];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       c0 += (double)f[i][0];
@@ -94,8 +95,7 @@ __global__ void __launch_bounds__(kVtxBlock) k_rhs_out(Dev d, double* out) {
     }
   }
   for (; p < end; ++p) {
-    T f[3];
-    load_corner<T>(cb, d.inc_idx[p], f);
+    const T* f = cb + 3 * (size_t)d.inc_idx[p];
     c0 += (double)f[0];
     c1 += (double)f[1];
     c2 += (double)f[2];

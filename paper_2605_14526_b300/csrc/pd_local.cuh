@@ -50,7 +50,9 @@ __device__ __forceinline__ void local_item(const Dev& d, int e, const double* x,
     for (int j = 0; j < 3; ++j)
       P[3 * i + j] = U[3 * i] * ss[0] * V[3 * j] + U[3 * i + 1] * ss[1] * V[3 * j + 1] + U[3 * i + 2] * ss[2] * V[3 * j + 2];
   corner_forces<T>(P, Bm, coef, c);
-  store_corners<T>(d.contrib, e, c);
+  T* out = reinterpret_cast<T*>(d.contrib) + 12 * (size_t)e;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) out[i] = c[i];
 }
 
 }  // namespace pdk

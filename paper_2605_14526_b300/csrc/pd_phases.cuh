@@ -124,10 +124,9 @@ __device__ __forceinline__ void assemble_warp(const Dev& d, int v, int k, double
     // FP32 rounding), one conversion to FP64 per component
     float2 c[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     for (int p = beg + lane; p < end; p += 32) {
-      float f[3];
-      load_corner<float>(cb, d.inc_idx[p], f);
+      const int ic = d.inc_idx[p];
 #pragma unroll
-      for (int j = 0; j < 3; ++j) c[j] = df_add_f(c[j], f[j]);
+      for (int j = 0; j < 3; ++j) c[j] = df_add_f(c[j], cb[3 * (size_t)ic + j]);
     }
     i = lane >> 3;
     float2 s3[3];
@@ -137,10 +136,9 @@ __device__ __forceinline__ void assemble_warp(const Dev& d, int v, int k, double
   } else {
     double c[3] = {0.0, 0.0, 0.0};
     for (int p = beg + lane; p < end; p += 32) {
-      T f[3];
-      load_corner<T>(cb, d.inc_idx[p], f);
+      const int ic = d.inc_idx[p];
 #pragma unroll
-      for (int j = 0; j < 3; ++j) c[j] += (double)f[j];
+      for (int j = 0; j < 3; ++j) c[j] += (double)cb[3 * (size_t)ic + j];
     }
     sum = warp_sum_scatter<3>(c, lane, i);   // component i in lanes 8i .. 8i+7
   }

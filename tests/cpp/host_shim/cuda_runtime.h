@@ -11,10 +11,6 @@ using std::cbrt;
 // the host's SSE arithmetic does; build with -ffp-contract=off so that no
 // product and sum is fused behind the code's back)
 struct float2 { float x, y; };
-struct float4 { float x, y, z, w; };
-struct double2 { double x, y; };
-inline float4 make_float4(float x, float y, float z, float w) { return float4{x, y, z, w}; }
-inline double2 make_double2(double x, double y) { return double2{x, y}; }
 struct int4 { int x, y, z, w; };
 struct int2 { int x, y; };
 struct uint2 { unsigned x, y; };

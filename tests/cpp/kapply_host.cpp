@@ -12,14 +12,12 @@ using namespace pdk;
 
 template <typename T>
 static void run(Dev& d, int n_e, const double* qstar, double tau, const double* p, double* out) {
-  std::vector<T> jac((size_t)kJacRec * n_e), c((size_t)kElemVals * n_e);
+  std::vector<T> jac((size_t)kJacRec * n_e), c(12 * (size_t)n_e);
   d.jac = jac.data();
   d.contrib = c.data();
   for (int e = 0; e < n_e; ++e) bwd_setup_item<T>(d, e, qstar, tau);
   for (int e = 0; e < n_e; ++e) kapply_item<T>(d, e, p);
-  for (int e = 0; e < n_e; ++e)   // corners padded to kCornerVals values -> [n_e][12]
-    for (int a = 0; a < 4; ++a)
-      for (int i = 0; i < 3; ++i) out[12 * (size_t)e + 3 * a + i] = (double)c[kElemVals * (size_t)e + kCornerVals * a + i];
+  for (size_t i = 0; i < c.size(); ++i) out[i] = (double)c[i];
 }
 
 extern "C" {

@@ -17,7 +17,7 @@ extern "C" {
 // Every element starts cold (no stored sigma*).
 void local_step_host(int fp64, int model, int n_e, const int* tets, const double* Bm, const double* coef,
                      double mu_bar, double lam_bar, double k_bar, double rot_share, const double* x, double* out) {
-  std::vector<float> Bm32(9 * (size_t)n_e), coef32(n_e), sstar(6 * (size_t)n_e, 0.0f), c32(kElemVals * (size_t)n_e);
+  std::vector<float> Bm32(9 * (size_t)n_e), coef32(n_e), sstar(6 * (size_t)n_e, 0.0f), c32(12 * (size_t)n_e);
   for (size_t i = 0; i < Bm32.size(); ++i) Bm32[i] = (float)Bm[i];
   for (int e = 0; e < n_e; ++e) coef32[e] = (float)coef[e];
   Dev d{};
@@ -34,12 +34,8 @@ void local_step_host(int fp64, int model, int n_e, const int* tets, const double
   d.coef64 = coef;
   d.sstar = sstar.data();
   if (fp64) {
-    std::vector<double> c64((size_t)kElemVals * n_e);
-    d.contrib = c64.data();
+    d.contrib = out;
     for (int e = 0; e < n_e; ++e) local_item<double>(d, e, x);
-    for (int e = 0; e < n_e; ++e)   // corners padded to kCornerVals values -> [n_e][12]
-      for (int a = 0; a < 4; ++a)
-        for (int i = 0; i < 3; ++i) out[12 * (size_t)e + 3 * a + i] = c64[kElemVals * (size_t)e + kCornerVals * a + i];
   } else {
     // the FP32 step reads the positions as float pairs (hi, lo), as the
     // iterate's writers keep them on the device
@@ -52,9 +48,7 @@ void local_step_host(int fp64, int model, int n_e, const int* tets, const double
     }
     d.contrib = c32.data();
     for (int e = 0; e < n_e; ++e) local_item<float>(d, e, x, xhl.data());
-    for (int e = 0; e < n_e; ++e)
-      for (int a = 0; a < 4; ++a)
-        for (int i = 0; i < 3; ++i) out[12 * (size_t)e + 3 * a + i] = c32[kElemVals * (size_t)e + kCornerVals * a + i];
+    for (size_t i = 0; i < c32.size(); ++i) out[i] = c32[i];
   }
 }
 }
