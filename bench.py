@@ -61,7 +61,7 @@ def max_over_ranks(value, dist, device):
 # a full 200-step launch; profiles/bench_traffic_bar32x8x8.md), valid only
 # for the kernel sources it was taken with (their hash): reported as null
 # once any source under csrc/ has changed since.
-BAR_TRAFFIC = {"src": "f377d23c0ec500d2", "k_fwd_rollout": 17579520 + 2585856, "k_bwd_rollout": 30757888 + 9401088}
+BAR_TRAFFIC = {"src": "aeeb1107639bdcf6", "k_fwd_rollout": 17435392 + 2558464, "k_bwd_rollout": 30842368 + 10244352}
 
 
 def csrc_hash() -> str:
