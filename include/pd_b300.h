@@ -107,7 +107,12 @@ typedef struct {
                              per non-zero). Fixed at pd_create. A context with contacts
                              (pd_set_contacts) always uses FP64 products: its Delassus
                              matrix comes from the FP64 factor and the adjoint's
-                             projection needs A^-1 to agree with it. */
+                             projection needs A^-1 to agree with it. Without contacts the
+                             persistent adjoint applies S in double-float whatever this
+                             option: there A^-1 only preconditions the conjugate gradients,
+                             whose residuals, updates and stopping test stay FP64, so the
+                             product's precision changes the iteration count, not the
+                             adjoint it converges to. */
   int32_t wait_polls;     /* persistent launches: polls (about 0.5 us each) a block spends at
                              a team barrier before it gives up, sets the timeout flag and
                              returns; the call then fails with PD_ERR_TIMEOUT and the context

@@ -762,7 +762,7 @@ int prepare_single(pd_ctx* c, cudaStream_t s, int dir, int grid) {
     const bool fp32 = c->opt.local_fp32 != 0;
     c->team_cap = std::max(std::max(pdk::persistent_grid_max(fp32), pdk::persistent_grid_bwd(fp32, 0)), 1);
     int r;
-    if ((r = dalloc(c, &c->d_dev, 1)) || (r = dalloc(c, &c->d_off, 2)) || (r = dalloc(c, &c->d_team[0], c->team_cap)) ||
+    if ((r = dalloc(c, &c->d_dev, 2)) || (r = dalloc(c, &c->d_off, 2)) || (r = dalloc(c, &c->d_team[0], c->team_cap)) ||
         (r = dalloc(c, &c->d_team[1], c->team_cap)))
       return r;
     const pdk::InstOff off[2] = {{0, 0}, {c->n_v, c->n_e}};
@@ -771,7 +771,9 @@ int prepare_single(pd_ctx* c, cudaStream_t s, int dir, int grid) {
   if (grid > c->team_cap) return fail(c, PD_ERR_ARG, "grid %d exceeds the team map (%d)", grid, c->team_cap);
   if (!same_d) {
     c->d_uploaded = c->d;
+    c->d_adjoint = adjoint_dev(c->d);   // record 1: the persistent adjoint's
     CK(cudaMemcpyAsync(c->d_dev, &c->d_uploaded, sizeof(Dev), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->d_dev + 1, &c->d_adjoint, sizeof(Dev), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     c->d_valid = true;
   }
@@ -830,7 +832,7 @@ int enqueue_bwd_single(pd_ctx* c, const double* dqTd, const double* dvTd, double
   br.df = dfd;
   br.df_stride = df_stride;
   CK(cudaMemsetAsync(&d.ctrl->bar_arrive, 0, sizeof(unsigned long long), s));
-  CK(pdk::launch_bwd_rollout(d.local_fp32 != 0, c->d_dev, c->d_team[1], c->d_off, br, grid, d.tmode != 0, s));
+  CK(pdk::launch_bwd_rollout(d.local_fp32 != 0, c->d_dev + 1, c->d_team[1], c->d_off, br, grid, d.tmode != 0, s));
   c->launches += 1;
   return PD_OK;
 }

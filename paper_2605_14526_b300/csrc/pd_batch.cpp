@@ -35,7 +35,7 @@ struct pd_batch {
   double* ckpt = nullptr;          // instance i: [(cap_T+1)][n_v_i][3] at (cap_T+1) * 3 * off[i].v
   double* tau = nullptr;           // [n][cap_T]
   int cap_T = 0;
-  Dev* d_devs = nullptr;           // [n] device copies of the instances' Dev records
+  Dev* d_devs = nullptr;           // [2n] device copies of the instances' Dev records: forward, then adjoint
   pdk::InstOff* d_off = nullptr;   // [n+1]
   int4* d_team[2] = {nullptr, nullptr};  // block -> {instance, index in team, team size} (forward, backward)
   int team_cap = 0;                // entries allocated per map
@@ -127,9 +127,12 @@ int prepare(pd_ctx* c, cudaStream_t s, int dir) {
   if ((B.devs_dirty || B.team_dirty[dir]) && capturing(s))
     return fail(c, PD_ERR_ARG, "the batch launch shape changed since the last launch: run it once before capture");
   if (B.devs_dirty) {
-    std::vector<Dev> h(B.n);
-    for (int i = 0; i < B.n; ++i) h[i] = B.kids[i]->d;
-    CK(cudaMemcpyAsync(B.d_devs, h.data(), B.n * sizeof(Dev), cudaMemcpyHostToDevice, s));
+    std::vector<Dev> h(2 * (size_t)B.n);   // the forward's records, then the adjoint's
+    for (int i = 0; i < B.n; ++i) {
+      h[i] = B.kids[i]->d;
+      h[B.n + i] = adjoint_dev(B.kids[i]->d);
+    }
+    CK(cudaMemcpyAsync(B.d_devs, h.data(), 2 * (size_t)B.n * sizeof(Dev), cudaMemcpyHostToDevice, s));
     B.devs_dirty = false;
   }
   if (B.team_dirty[dir]) {
@@ -427,7 +430,8 @@ int batch_backward(pd_ctx* c, const double* dqT, const double* dvT, double* dq0,
   br.dnu = dnud;
   br.df = dfd;
   br.df_stride = df_stride;
-  CK(pdk::launch_bwd_rollout(c->opt.local_fp32 != 0, B.d_devs, B.d_team[1], B.d_off, br, B.grid[1], any_tmode(B), s));
+  CK(pdk::launch_bwd_rollout(c->opt.local_fp32 != 0, B.d_devs + B.n, B.d_team[1], B.d_off, br, B.grid[1], any_tmode(B),
+                             s));
   c->launches += 1;
   if (!sync) {
     c->pending |= 2;
@@ -594,7 +598,7 @@ int pd_create_batch(int32_t n, const pd_mesh* meshes, const pd_material* mats, d
   CK(cudaMalloc(&B.ctrl, n * sizeof(Ctrl)));
   CK(cudaMemset(B.ctrl, 0, n * sizeof(Ctrl)));
   CK(cudaMalloc(&B.sstar, 3 * (size_t)std::max<long long>(B.off[n].e, 1) * sizeof(double)));
-  CK(cudaMalloc(&B.d_devs, n * sizeof(Dev)));
+  CK(cudaMalloc(&B.d_devs, 2 * (size_t)n * sizeof(Dev)));
   CK(cudaMalloc(&B.d_off, (n + 1) * sizeof(pdk::InstOff)));
   CK(cudaMemcpy(B.d_off, B.off.data(), (n + 1) * sizeof(pdk::InstOff), cudaMemcpyHostToDevice));
   CK(cudaMalloc(&B.d_team[0], B.team_cap * sizeof(int4)));

@@ -85,6 +85,7 @@ struct pd_ctx {
   int team_cap = 0;
   int team_grid[2] = {0, 0};
   Dev d_uploaded{};
+  Dev d_adjoint{};           // host copy of the adjoint's record (d_dev[1])
   bool d_valid = false;
   // frictional contacts (pd_set_contacts)
   std::vector<int> con_ground, con_box;
@@ -159,6 +160,16 @@ inline bool is_device_ptr(const void* p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// The Dev record of the persistent adjoint: without contacts, in mode S,
+// the products with S that precondition its conjugate gradients run in
+// double-float (the pairs are always uploaded) even where the forward uses
+// FP64 products; the CG's residuals and stopping test stay FP64.
+inline Dev adjoint_dev(const Dev& d) {
+  Dev b = d;
+  if (b.sfp64 && !b.tmode && b.n_con == 0) b.sfp64 = 0;
+  return b;
 }
 
 inline bool capturing(cudaStream_t s) {
