@@ -61,7 +61,7 @@ def max_over_ranks(value, dist, device):
 # a full 200-step launch; profiles/bench_traffic_bar32x8x8.md), valid only
 # for the kernel sources it was taken with (their hash): reported as null
 # once any source under csrc/ has changed since.
-BAR_TRAFFIC = {"src": "aeeb1107639bdcf6", "k_fwd_rollout": 17435392 + 2558464, "k_bwd_rollout": 30842368 + 10244352}
+BAR_TRAFFIC = {"src": "6973672580ebc4aa", "k_fwd_rollout": 17586688 + 2755840, "k_bwd_rollout": 30974208 + 6724096}
 
 
 def csrc_hash() -> str:
