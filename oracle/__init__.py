@@ -13,8 +13,9 @@ is silent or inconsistent, the reading taken is stated beside the code.
 
 Modules:
   fem      - rest shape, lumped mass, Lame/weights, the global operator A, G and G^T
-  prox     - rotation-variant SVD, corotated and Neo-Hookean local steps, their
-             differentials and the trust-region filter (Sec. 4.1, 4.3)
+  prox     - rotation-variant SVD, corotated, Neo-Hookean, corotated + volume and
+             corotated + log-volume barrier local steps, their differentials
+             and the trust-region filter (Sec. 4.1, 4.3)
   solver   - right-hand side b(q), fixed point of q = A^-1 b(q), Anderson +
              dual gate reference, rollouts (Alg. 1)
   adjoint  - explicit per-element K_e, the adjoint solve and gradient routing

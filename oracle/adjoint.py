@@ -31,7 +31,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from . import fem, prox
-from .solver import Problem, local_step, rotation_share
+from .solver import Problem, local_step, logvol_ratio, rotation_share
 
 
 def local_jacobian(pb: Problem, q, tau: float, unfiltered: bool = False):
@@ -50,6 +50,18 @@ def local_jacobian(pb: Problem, q, tau: float, unfiltered: bool = False):
         _, (_, _, _, _, sv, nu) = prox.corot_volume_project(F, a)
         Jd = (1.0 - a)[:, None, None] * prox.volume_sigma_jacobian(sv, nu)
         return prox.dp_dF_matrix(U, sF, V, ss, Jd, Jd, corot=False), 0
+    if pb.model == "corotated_logvol":
+        # sigma* = a + (1 - a) sigma_b(sigma_F): the diagonal response is
+        # (1 - a) times the barrier prox's filtered IFT Jacobian (its Hessian
+        # plays the part of the Neo-Hookean prox Hessian in eq. tr_blend)
+        F = fem.deformation_gradient(pb.rest, pb.tets, q)
+        a = rotation_share(pb)
+        r = logvol_ratio(pb)
+        _, (_, _, _, _, sb) = prox.corot_logvol_project(F, a, r)
+        Jf, Jraw, n_indef = prox.logvol_sigma_jacobian(sb, r, tau)
+        c = (1.0 - a)[:, None, None]
+        Jd = Jraw if unfiltered else Jf
+        return prox.dp_dF_matrix(U, sF, V, ss, c * Jd, c * Jraw, corot=False), n_indef
     Jf, Jraw, n_indef = prox.filtered_sigma_jacobian(ss, pb.mat.mu_bar, pb.mat.lam_bar, pb.mat.k_bar, tau)
     Jd = Jraw if unfiltered else Jf
     return prox.dp_dF_matrix(U, sF, V, ss, Jd, Jraw, corot=False), n_indef
@@ -91,6 +103,7 @@ class StepGrad:
     mu: np.ndarray
     n_indef: int
     dw1: np.ndarray = None   # composite: dL/dw_1 of the volume step (dw is then dL/dw_0)
+    dr: float = 0.0          # barrier variant: dL/dr through sigma_b, r = mu_e/lambda_e
 
 
 def adjoint_solve(pb: Problem, q_star, tau: float, qbar_free):
@@ -104,7 +117,7 @@ def adjoint_solve(pb: Problem, q_star, tau: float, qbar_free):
 
 def mean_sensitivities(pb: Problem, q_star, mu_full, tau: float):
     """dL/d(mu_bar, lambda_bar, k_bar) = sum_e w_e V_e <G_e mu, dp_e/d theta>."""
-    if pb.model in ("corotated", "corotated_volume"):   # no mesh means inside the projections
+    if pb.model in ("corotated", "corotated_volume", "corotated_logvol"):   # no mesh means inside the projections
         return 0.0, 0.0, 0.0
     _, (U, sF, V, ss) = local_step(pb, q_star)
     Jf, _, _ = prox.filtered_sigma_jacobian(ss, pb.mat.mu_bar, pb.mat.lam_bar, pb.mat.k_bar, tau)
@@ -120,6 +133,22 @@ def mean_sensitivities(pb: Problem, q_star, mu_full, tau: float):
         ds = -np.einsum("nij,nj->ni", Hpinv, g)
         out[key] = float(np.sum(coef * np.sum(diag * ds, axis=1)))
     return out["mu"], out["lam"], out["k"]
+
+
+def ratio_sensitivity(pb: Problem, q_star, mu_full, tau: float) -> float:
+    """dL/dr of the barrier variant, r_e = mu_e/lambda_e inside its prox:
+    sum_e lambda_e V_e <G_e mu, U diag(d sigma_b/d r) V^T> with
+    d sigma_b/d r = H~^+ (1/sigma_b) by the IFT on the stationarity
+    (ln J - r)/sigma_i + sigma_i - sigma_F,i = 0 (filtered like the Jacobian)."""
+    F = fem.deformation_gradient(pb.rest, pb.tets, q_star)
+    r = logvol_ratio(pb)
+    _, (U, _, V, _, sb) = prox.corot_logvol_project(F, rotation_share(pb), r)
+    Jf, _, _ = prox.logvol_sigma_jacobian(sb, r, tau)
+    ds = np.einsum("nij,nj->ni", Jf, 1.0 / sb)
+    Gmu = fem.deformation_gradient(pb.rest, pb.tets, mu_full)
+    Mh = np.einsum("nki,nkl,nlj->nij", U, Gmu, V)
+    diag = np.diagonal(Mh, axis1=1, axis2=2)
+    return float(np.sum(pb.mat.lam * pb.rest.vol * np.sum(diag * ds, axis=1)))
 
 
 def backward_step(pb: Problem, q_t, q_star, tau: float, qbar_next, vbar_next) -> StepGrad:
@@ -151,6 +180,13 @@ def route_step(pb: Problem, q_t, q_star, tau: float, mu, vbar_next) -> StepGrad:
         Pv = prox.compose(U, sv, V)
         dw = pb.rest.vol * np.einsum("nij,nij->n", Gmu, R - F)
         dw1 = pb.rest.vol * np.einsum("nij,nij->n", Gmu, Pv - F)
+    elif pb.model == "corotated_logvol":
+        # the same two weights, with the barrier's p_b as the volume target
+        _, (_, _, _, _, sb) = prox.corot_logvol_project(F, rotation_share(pb), logvol_ratio(pb))
+        R = np.einsum("nij,nkj->nik", U, V)
+        Pb = prox.compose(U, sb, V)
+        dw = pb.rest.vol * np.einsum("nij,nij->n", Gmu, R - F)
+        dw1 = pb.rest.vol * np.einsum("nij,nij->n", Gmu, Pb - F)
     else:
         dw = pb.rest.vol * np.einsum("nij,nij->n", Gmu, P - F)
     Fd = fem.deformation_gradient(pb.rest, pb.tets, q_star - q_t)
@@ -158,26 +194,29 @@ def route_step(pb: Problem, q_t, q_star, tau: float, mu, vbar_next) -> StepGrad:
     dmu, dlam, dk = mean_sensitivities(pb, q_star, mu, tau)
     for arr in (dq_t, dv_t, df):
         arr[pb.fixed] = 0.0
-    _, n_indef = local_jacobian(pb, q_star, tau) if pb.model == "neohookean" else (None, 0)
-    return StepGrad(dq_t, dv_t, df, dw, dbeta, dmu, dlam, dk, mu, n_indef, dw1)
+    dr = ratio_sensitivity(pb, q_star, mu, tau) if pb.model == "corotated_logvol" else 0.0
+    _, n_indef = local_jacobian(pb, q_star, tau) if pb.model in ("neohookean", "corotated_logvol") else (None, 0)
+    return StepGrad(dq_t, dv_t, df, dw, dbeta, dmu, dlam, dk, mu, n_indef, dw1, dr)
 
 
-def chain_material(pb: Problem, dw, dbeta, dmu_bar, dlam_bar, dk_bar, paper_literal: bool = False, dw1=None):
+def chain_material(pb: Problem, dw, dbeta, dmu_bar, dlam_bar, dk_bar, paper_literal: bool = False, dw1=None,
+                   dr: float = 0.0):
     """dL/dE_e and dL/dnu from the weight, damping and mean sensitivities
-    (the composite: dw = dL/dw_0 with w_0 = 2 mu, dw1 = dL/dw_1 with
-    w_1 = lambda; Sec. 7.2 and eq. lame)."""
+    (the composite and the barrier variant: dw = dL/dw_0 with w_0 = 2 mu,
+    dw1 = dL/dw_1 with w_1 = lambda; Sec. 7.2 and eq. lame; the barrier's
+    dr = dL/dr with r = mu/lambda = (1 - 2 nu)/(2 nu), dr/dnu = -1/(2 nu^2))."""
     E, nu = pb.E, pb.nu
     n = E.shape[0]
     dmu_dE = 1.0 / (2.0 * (1.0 + nu)) * np.ones(n)
     dlam_dE = nu / ((1.0 + nu) * (1.0 - 2.0 * nu)) * np.ones(n)
     dmu_dnu = -E / (2.0 * (1.0 + nu) ** 2)
     dlam_dnu = E * (1.0 + 2.0 * nu ** 2) / ((1.0 + nu) * (1.0 - 2.0 * nu)) ** 2
-    if pb.model == "corotated_volume":
+    if pb.model in ("corotated_volume", "corotated_logvol"):
         dw1 = np.zeros(n) if dw1 is None else dw1
         cb = pb.beta0 / pb.mat.mu_ref
         dE = 2.0 * dw * dmu_dE + dw1 * dlam_dE + dbeta * cb * dmu_dE
         dnu = float(np.sum(2.0 * dw * dmu_dnu + dw1 * dlam_dnu + dbeta * cb * dmu_dnu))
-        return dE, dnu
+        return dE, dnu - dr / (2.0 * nu * nu)
     nh = pb.model != "corotated"
     dw_dE = 2.0 * dmu_dE + (dlam_dE if nh else 0.0)
     dw_dnu = 2.0 * dmu_dnu + (dlam_dnu if nh else 0.0)
@@ -210,7 +249,7 @@ def rollout_backward(pb: Problem, records, dqT, dvT, paper_literal: bool = False
     dw_tot = np.zeros(n_e)
     dw1_tot = np.zeros(n_e)
     db_tot = np.zeros(n_e)
-    dmu = dlam = dk = 0.0
+    dmu = dlam = dk = dr = 0.0
     dfs = []
     for rec in reversed(records):
         g = backward_step(pb, rec.q_t, rec.q_next, rec.tau, qbar, vbar)
@@ -222,8 +261,9 @@ def rollout_backward(pb: Problem, records, dqT, dvT, paper_literal: bool = False
         dmu += g.dmu_bar
         dlam += g.dlam_bar
         dk += g.dk_bar
+        dr += g.dr
         dfs.append(g.df_ext)
-    dE, dnu = chain_material(pb, dw_tot, db_tot, dmu, dlam, dk, paper_literal, dw1_tot)
+    dE, dnu = chain_material(pb, dw_tot, db_tot, dmu, dlam, dk, paper_literal, dw1_tot, dr)
     return RolloutGrad(qbar, vbar, dE, dnu, np.stack(dfs[::-1]), dw_tot)
 
 

@@ -281,18 +281,21 @@ def rollout_backward(pb, cp: ContactProblem, records, dqT, dvT, taus=None):
     from . import adjoint
     qbar, vbar = dqT.copy(), dvT.copy()
     n_e = pb.tets.shape[0]
-    dw_tot, db_tot = np.zeros(n_e), np.zeros(n_e)
-    dmu = dlam = dk = 0.0
+    dw_tot, dw1_tot, db_tot = np.zeros(n_e), np.zeros(n_e), np.zeros(n_e)
+    dmu = dlam = dk = dr = 0.0
     dfs = []
     for t in reversed(range(len(records))):
         tau = 0.5 if taus is None else taus[t]
         g = backward_step(pb, cp, records[t], tau, qbar, vbar)
         qbar, vbar = g.dq_t, g.dv_t
         dw_tot += g.dw
+        if g.dw1 is not None:
+            dw1_tot += g.dw1
         db_tot += g.dbeta
         dmu += g.dmu_bar
         dlam += g.dlam_bar
         dk += g.dk_bar
+        dr += g.dr
         dfs.append(g.df_ext)
-    dE, dnu = adjoint.chain_material(pb, dw_tot, db_tot, dmu, dlam, dk)
+    dE, dnu = adjoint.chain_material(pb, dw_tot, db_tot, dmu, dlam, dk, dw1=dw1_tot, dr=dr)
     return adjoint.RolloutGrad(qbar, vbar, dE, dnu, np.stack(dfs[::-1]), dw_tot)

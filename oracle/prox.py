@@ -13,6 +13,8 @@
     d2 psi/d s_i^2   = mu (1 + 1/s_i^2) + lam (1 - ln J) / s_i^2
     d2 psi/d s_i s_j = lam / (s_i s_j)            (i != j).
   The prox is per unit volume (no V_e), matching eq. nh_prox_normal and Alg. 1.
+* Log-volume barrier (eq. pd_log_volume): the opt-in volume step that
+  replaces the composite's quadratic one, a stretch prox of the same kind.
 * Differential of the isotropic spectral map p(F) = U diag(f(s)) V^T (the
   "SVD differential" the paper names for eq. tr_ift), with the trust-region
   blend of eq. tr_blend applied to H_prox = H_psi + k_bar I before inversion.
@@ -82,9 +84,10 @@ def nh_hess_sigma(s, mu, lam):
     return H
 
 
-def nh_prox_sigma(sF: np.ndarray, mu: float, lam: float, k: float, tol: float = 1e-14,
-                  max_iter: int = 60):
-    """Newton on f(s) = k/2||s - sF||^2 + psi_bar(s), s > 0 (eq. nh_prox_normal).
+def _stretch_prox(sF: np.ndarray, k: float, psi, grad, hess, tol: float = 1e-14, max_iter: int = 60):
+    """Newton on f(s) = k/2||s - sF||^2 + psi(s), s > 0, in stretch space
+    (eq. nh_prox_normal: the Newton-on-stretches step with backtracking and
+    positivity that the Neo-Hookean prox and the log-volume barrier share).
 
     Start s0 = max(sF, 0.1); Newton direction if it is a descent direction of a
     positive-definite model, else the scaled gradient -g/k; step halved until
@@ -97,17 +100,17 @@ def nh_prox_sigma(sF: np.ndarray, mu: float, lam: float, k: float, tol: float = 
     active = np.ones(n, dtype=bool)
     iters = np.zeros(n, dtype=np.int64)
 
-    def f(x, ref):
-        return 0.5 * k * np.sum((x - ref) ** 2, axis=-1) + nh_psi_sigma(x, mu, lam)
+    def f(x, ref, rows):
+        return 0.5 * k * np.sum((x - ref) ** 2, axis=-1) + psi(x, rows)
 
     for _ in range(max_iter):
-        g = k * (s - sF) + nh_grad_sigma(s, mu, lam)
+        g = k * (s - sF) + grad(s, slice(None))
         active &= ~(np.abs(g).max(axis=1) <= tol * k)
         if not active.any():
             break
         a = np.nonzero(active)[0]
         sa, ga, ra = s[a], g[a], sF[a]
-        H = k * np.eye(3) + nh_hess_sigma(sa, mu, lam)
+        H = k * np.eye(3) + hess(sa, a)
         pd = np.all(np.linalg.eigvalsh(H) > 0, axis=1)
         d = -np.linalg.solve(H, ga[..., None])[..., 0]
         bad = (~pd) | (np.einsum("ni,ni->n", d, ga) >= 0)
@@ -119,15 +122,15 @@ def nh_prox_sigma(sF: np.ndarray, mu: float, lam: float, k: float, tol: float = 
             if not neg.any():
                 break
             t[neg] *= 0.5
-        f0 = f(sa, ra)
+        f0 = f(sa, ra, a)
         done = np.zeros(a.shape[0], dtype=bool)
         for _h in range(60):          # Armijo
             trial = sa + t[:, None] * d
             # sufficient decrease of f, or (Newton steps only) a halving of the
             # gradient's max-norm: in the quadratic-convergence regime the
             # decrease of f falls below its rounding and Armijo cannot see it
-            gt = k * (trial - ra) + nh_grad_sigma(trial, mu, lam)
-            ok = (f(trial, ra) <= f0 + 1e-4 * t * slope) | (
+            gt = k * (trial - ra) + grad(trial, a)
+            ok = (f(trial, ra, a) <= f0 + 1e-4 * t * slope) | (
                 (~bad) & (np.abs(gt).max(axis=1) <= 0.5 * np.abs(ga).max(axis=1)))
             done |= ok
             if done.all():
@@ -138,6 +141,16 @@ def nh_prox_sigma(sF: np.ndarray, mu: float, lam: float, k: float, tol: float = 
         iters[a] += 1
         active[a[stalled]] = False
     return s, iters
+
+
+def nh_prox_sigma(sF: np.ndarray, mu: float, lam: float, k: float, tol: float = 1e-14,
+                  max_iter: int = 60):
+    """sigma* = argmin_{sigma>0} k/2||sigma - sF||^2 + psi_bar(sigma) (eq. nh_prox,
+    nh_prox_normal) with the mesh-mean Neo-Hookean energy."""
+    return _stretch_prox(sF, k,
+                         lambda x, rows: nh_psi_sigma(x, mu, lam),
+                         lambda x, rows: nh_grad_sigma(x, mu, lam),
+                         lambda x, rows: nh_hess_sigma(x, mu, lam), tol, max_iter)
 
 
 def nh_project(F: np.ndarray, mu_bar: float, lam_bar: float, k_bar: float):
@@ -240,6 +253,70 @@ def corot_volume_project(F: np.ndarray, a: np.ndarray):
     return compose(U, ss, V), (U, sF, V, ss, sv, nu)
 
 
+# ------------------------------------------------------ log-volume barrier
+
+def logvol_ratio(mu, lam):
+    """r = mu_e / lambda_e = (1 - 2 nu)/(2 nu): the only material constant of
+    the barrier's prox once it is divided by its weight w_e = lambda_e."""
+    return np.asarray(mu, dtype=np.float64) / np.asarray(lam, dtype=np.float64)
+
+
+def logvol_phi_sigma(s, r):
+    """phi_log(sigma)/lambda_e of eq. pd_log_volume:
+    -r sum_i ln sigma_i + 1/2 (sum_j ln sigma_j)^2 with r = mu_e/lambda_e."""
+    ls = np.log(s)
+    return -r * np.sum(ls, axis=-1) + 0.5 * np.sum(ls, axis=-1) ** 2
+
+
+def logvol_grad_sigma(s, r):
+    """d(phi_log/lambda)/d sigma_i = (ln J - r)/sigma_i, ln J = sum_j ln sigma_j."""
+    lnJ = np.sum(np.log(s), axis=-1)
+    return (lnJ - r)[..., None] / s
+
+
+def logvol_hess_sigma(s, r):
+    """Its Hessian: (1 + r - ln J)/sigma_i^2 on the diagonal, 1/(sigma_i sigma_j) off it."""
+    lnJ = np.sum(np.log(s), axis=-1)
+    inv = 1.0 / s
+    H = inv[..., :, None] * inv[..., None, :]
+    idx = np.arange(3)
+    H[..., idx, idx] = (1.0 + r - lnJ)[..., None] * inv ** 2
+    return H
+
+
+def logvol_prox_sigma(sF: np.ndarray, r, tol: float = 1e-14, max_iter: int = 60):
+    """The barrier's volume step (Sec. 4.1, volume-barrier surrogate, eq.
+    pd_log_volume, registered with w_e = lambda_e): in stretch space
+        sigma_b = argmin_{sigma>0} lambda_e/2 ||sigma - sigma_F||^2 + phi_log(sigma),
+    divided by lambda_e, by the same Newton-on-stretches step as the
+    Neo-Hookean prox with the barrier's own gradient and Hessian. ``r`` is a
+    scalar or one value per element. Returns (sigma_b, iterations)."""
+    rr = np.broadcast_to(np.asarray(r, dtype=np.float64), sF.shape[:1])
+    return _stretch_prox(sF, 1.0,
+                         lambda x, rows: logvol_phi_sigma(x, rr[rows]),
+                         lambda x, rows: logvol_grad_sigma(x, rr[rows]),
+                         lambda x, rows: logvol_hess_sigma(x, rr[rows]), tol, max_iter)
+
+
+def corot_logvol_project(F: np.ndarray, a: np.ndarray, r):
+    """The barrier variant's projection: the corotated rotation step (w_0 =
+    2 mu) with the barrier's volume step (w_1 = lambda) in place of the
+    quadratic one, p = (w_0 R + w_1 p_b)/(w_0 + w_1) = U diag(a + (1 - a)
+    sigma_b) V^T. Returns p and (U, sigma_F, V, sigma*, sigma_b)."""
+    U, sF, V = svd_rv(F)
+    sb, _ = logvol_prox_sigma(sF, r)
+    ss = a[:, None] + (1.0 - a[:, None]) * sb
+    return compose(U, ss, V), (U, sF, V, ss, sb)
+
+
+def logvol_sigma_jacobian(sb: np.ndarray, r, tau: float):
+    """d sigma_b/d sigma_F = H~(tau)^+ with H = I + Hess(phi_log/lambda)(sigma_b)
+    (eq. tr_ift with k = 1 after the division by lambda_e); (filtered,
+    unfiltered, count of indefinite H)."""
+    rr = np.broadcast_to(np.asarray(r, dtype=np.float64), sb.shape[:1])
+    return filtered_inverse(np.eye(3) + logvol_hess_sigma(sb, rr), 1.0, tau)
+
+
 # ------------------------------------------------------- trust-region filter
 
 def tr_blend(H: np.ndarray, tau: float) -> np.ndarray:
@@ -249,14 +326,13 @@ def tr_blend(H: np.ndarray, tau: float) -> np.ndarray:
     return np.einsum("nij,nj,nkj->nik", Q, lt, Q)
 
 
-def filtered_sigma_jacobian(ss: np.ndarray, mu: float, lam: float, k: float, tau: float):
-    """d sigma*/d sigma_F = k H~(tau)^+ (eq. tr_ift) with H = H_psi(sigma*) + k I.
+def filtered_inverse(H: np.ndarray, k: float, tau: float):
+    """k H~(tau)^+ (eq. tr_ift) for a per-element 3x3 prox Hessian H.
 
     Eigen-directions of H~ with eigenvalue <= 1e-12 k get zero response (the
     pseudo-inverse: clamping a negative eigenvalue makes H~ singular).
     Also returns the unfiltered k H^-1 and the count of indefinite H.
     """
-    H = k * np.eye(3) + nh_hess_sigma(ss, mu, lam)
     lamH, Q = np.linalg.eigh(H)
     lt = (1.0 - tau) * lamH + tau * np.abs(lamH)
     inv = np.where(lt > 1e-12 * k, 1.0 / np.where(lt > 1e-12 * k, lt, 1.0), 0.0)
@@ -264,6 +340,12 @@ def filtered_sigma_jacobian(ss: np.ndarray, mu: float, lam: float, k: float, tau
     Jraw = k * np.linalg.inv(H)
     n_indef = int(np.sum(lamH.min(axis=1) < 0))
     return Jf, Jraw, n_indef
+
+
+def filtered_sigma_jacobian(ss: np.ndarray, mu: float, lam: float, k: float, tau: float):
+    """d sigma*/d sigma_F = k H~(tau)^+ (eq. tr_ift) with H = H_psi(sigma*) + k I
+    of the Neo-Hookean prox; (filtered, unfiltered, count of indefinite H)."""
+    return filtered_inverse(k * np.eye(3) + nh_hess_sigma(ss, mu, lam), k, tau)
 
 
 # ------------------------------------------------------ spectral differential

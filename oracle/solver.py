@@ -99,12 +99,21 @@ def local_step(pb: Problem, q):
     if pb.model == "corotated_volume":
         P, (U, sF, V, ss, _, _) = prox.corot_volume_project(F, rotation_share(pb))
         return P, (U, sF, V, ss)
+    if pb.model == "corotated_logvol":
+        P, (U, sF, V, ss, _) = prox.corot_logvol_project(F, rotation_share(pb), logvol_ratio(pb))
+        return P, (U, sF, V, ss)
     return prox.nh_project(F, pb.mat.mu_bar, pb.mat.lam_bar, pb.mat.k_bar)
 
 
 def rotation_share(pb: Problem) -> np.ndarray:
-    """a_e = w_0/(w_0 + w_1) = 2 mu_e/(2 mu_e + lambda_e) of the composite."""
+    """a_e = w_0/(w_0 + w_1) = 2 mu_e/(2 mu_e + lambda_e) of the composite
+    (and of the barrier variant, whose volume weight is also lambda_e)."""
     return 2.0 * pb.mat.mu / (2.0 * pb.mat.mu + pb.mat.lam)
+
+
+def logvol_ratio(pb: Problem) -> np.ndarray:
+    """r_e = mu_e/lambda_e of the barrier's prox (eq. pd_log_volume)."""
+    return prox.logvol_ratio(pb.mat.mu, pb.mat.lam)
 
 
 def rhs(pb: Problem, b0, q):
@@ -308,6 +317,17 @@ def pd_energy(pb: Problem, q, q_t, q_tilde):
         Pv = prox.compose(U, sv, V)
         el = 0.5 * (w0 * np.einsum("nij,nij->n", F - R, F - R) + w1 * np.einsum("nij,nij->n", F - Pv, F - Pv))
         return val + float(np.sum(pb.rest.vol * el))
+    if pb.model == "corotated_logvol":
+        # w_0/2 dist^2(F, SO(3)) + min_p [w_1/2 ||F - p||^2 + phi_log(p)],
+        # w_1 = lambda_e, the second minimum attained at the barrier's prox
+        w0, w1 = 2.0 * pb.mat.mu, pb.mat.lam
+        r = logvol_ratio(pb)
+        _, (_, _, _, _, sb) = prox.corot_logvol_project(F, rotation_share(pb), r)
+        R = np.einsum("nij,nkj->nik", U, V)
+        Pb = prox.compose(U, sb, V)
+        el = 0.5 * (w0 * np.einsum("nij,nij->n", F - R, F - R) + w1 * np.einsum("nij,nij->n", F - Pb, F - Pb))
+        el = el + w1 * prox.logvol_phi_sigma(sb, r)
+        return val + float(np.sum(pb.rest.vol * el))
     el = 0.5 * np.einsum("nij,nij->n", F - P, F - P)
     if pb.model != "corotated":
         el = el + prox.nh_psi_sigma(ss, pb.mat.mu_bar, pb.mat.lam_bar) / pb.mat.k_bar
@@ -349,7 +369,7 @@ def step(pb: Problem, q_t, v_t, f_ext, mode: str = "exact", settings=None):
         # no last increment at an exact fixed point: Delta Phi_mod = 0 < 1e-12
         # gives rho = 1 and tau = 1/2 by eq. tr_ratio
         q_prev = q
-    if pb.model == "neohookean":
+    if pb.model in ("neohookean", "corotated_logvol"):   # the models with a prox Hessian to filter
         tau, rho = tr_select(pb, q, q_prev, q_tilde, settings.eps_tr if settings else 0.1)
     else:
         tau, rho = 0.5, 1.0

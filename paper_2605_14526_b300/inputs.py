@@ -22,6 +22,7 @@ import numpy as np
 
 COROTATED = "corotated"
 COROT_VOLUME = "corotated_volume"   # corotated rotation step + volume step (Sec. 4.1, Sec. 7.2)
+COROT_LOGVOL = "corotated_logvol"   # corotated rotation step + log-volume barrier (Sec. 4.1, eq. pd_log_volume)
 NEOHOOKEAN = "neohookean"
 
 TR_ADAPT, TR_NONE, TR_CLAMP, TR_ABS = 0, 1, 2, 3

@@ -24,7 +24,7 @@ def _fd_setup(model):
     return sc, pb, loss, g, recs
 
 
-@pytest.mark.parametrize("model", ["neohookean", "corotated", "corotated_volume"])
+@pytest.mark.parametrize("model", ["neohookean", "corotated", "corotated_volume", "corotated_logvol"])
 def test_rollout_gradients_match_central_differences(model):
     sc, pb, loss, g, recs = _fd_setup(model)
     assert all(r.info["newton"] < 10 for r in recs)
@@ -74,7 +74,7 @@ def test_paper_literal_routing_misses_damping_and_mean_terms():
     assert abs(lit.dE[e] - fd) > 10 * abs(full.dE[e] - fd)
 
 
-@pytest.mark.parametrize("model", ["neohookean", "corotated", "corotated_volume"])
+@pytest.mark.parametrize("model", ["neohookean", "corotated", "corotated_volume", "corotated_logvol"])
 def test_K_is_db_dq(model):
     sc = inputs.tiny_block(model=model)
     pb = solver.build_problem(sc)

@@ -92,7 +92,7 @@ def test_rigid_rotation_has_no_elastic_force(model):
     assert np.allclose(q, qt, atol=1e-12)
 
 
-@pytest.mark.parametrize("model", ["neohookean", "corotated", "corotated_volume"])
+@pytest.mark.parametrize("model", ["neohookean", "corotated", "corotated_volume", "corotated_logvol"])
 def test_plain_iteration_decreases_pd_energy(model):
     """Local-global is block-coordinate descent on g~(q, p) (eq. pd_surrogate)."""
     sc = inputs.hetero_bar(nx=6, ny=2, nz=2, block=2, omega0=6.0).replace(model=model)
@@ -108,7 +108,7 @@ def test_plain_iteration_decreases_pd_energy(model):
         e_prev = e
 
 
-@pytest.mark.parametrize("model", ["neohookean", "corotated", "corotated_volume"])
+@pytest.mark.parametrize("model", ["neohookean", "corotated", "corotated_volume", "corotated_logvol"])
 def test_fixed_point_is_stationary(model):
     sc = inputs.hetero_bar(nx=6, ny=2, nz=2, block=2, omega0=6.0).replace(model=model)
     pb = solver.build_problem(sc)
