@@ -50,8 +50,15 @@ typedef enum {
  * composite: the rotation step with w_0 = 2 mu_e plus a volume step with
  * w_1 = lambda_e, the closest point of the unit-determinant set in stretch
  * space (sigma_1 sigma_2 sigma_3 = 1), both in the one operator A (weight
- * w_0 + w_1) and in b. */
-enum { PD_COROTATED = 0, PD_NEOHOOKEAN = 1, PD_COROT_VOLUME = 2 };
+ * w_0 + w_1) and in b; the opt-in log-volume barrier variant (Sec. 4.1,
+ * eq. pd_log_volume): the same rotation step with the barrier
+ * phi_log = -mu_e sum ln sigma_i + lambda_e/2 (sum ln sigma_j)^2 as the volume
+ * step, the stretch prox of phi_log with weight w_1 = lambda_e solved by the
+ * Neo-Hookean Newton, its differential filtered by the trust region like
+ * Neo-Hookean's. As printed, phi_log has gradient -mu_e at rest, so an
+ * unloaded body is pushed outward (a uniform stretch of about 2.8% in the
+ * volume step at nu = 0.45); it needs nu in (0, 0.5). */
+enum { PD_COROTATED = 0, PD_NEOHOOKEAN = 1, PD_COROT_VOLUME = 2, PD_COROT_LOGVOL = 3 };
 enum { PD_TR_ADAPT = 0, PD_TR_NONE = 1, PD_TR_CLAMP = 2, PD_TR_ABS = 3 };
 /* How every A^-1 application is computed (pd_options.solve_mode). */
 enum { PD_SOLVE_AUTO = 0, PD_SOLVE_S = 1, PD_SOLVE_T = 2 };
@@ -66,7 +73,7 @@ typedef struct {
 
 /* Material (Sec. 3.1 eq. lame; Sec. 4.4 eq. rayleigh), copied by pd_create. */
 typedef struct {
-  int32_t model;          /* PD_COROTATED | PD_NEOHOOKEAN | PD_COROT_VOLUME */
+  int32_t model;          /* PD_COROTATED | PD_NEOHOOKEAN | PD_COROT_VOLUME | PD_COROT_LOGVOL */
   const double* E;        /* [n_e] Young's modulus per element (Pa), > 0 */
   double nu;              /* Poisson ratio shared by all elements, in (-1, 0.5) */
   double density;         /* kg/m^3; lumped mass density*V_e/4 per corner */

@@ -21,8 +21,9 @@ PD_OK = 0
 STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_MESH", 3: "PD_ERR_NOT_FACTORED", 4: "PD_ERR_NOT_SPD",
           5: "PD_ERR_NOT_CONVERGED", 6: "PD_ERR_NUMERIC", 7: "PD_ERR_TIMEOUT", 8: "PD_ERR_CUDA",
           9: "PD_ERR_OOM", 10: "PD_ERR_NO_CHECKPOINT", 11: "PD_ERR_TOO_LARGE"}
-PD_COROTATED, PD_NEOHOOKEAN, PD_COROT_VOLUME = 0, 1, 2
-MODELS = {"corotated": PD_COROTATED, "neohookean": PD_NEOHOOKEAN, "corotated_volume": PD_COROT_VOLUME}
+PD_COROTATED, PD_NEOHOOKEAN, PD_COROT_VOLUME, PD_COROT_LOGVOL = 0, 1, 2, 3
+MODELS = {"corotated": PD_COROTATED, "neohookean": PD_NEOHOOKEAN, "corotated_volume": PD_COROT_VOLUME,
+          "corotated_logvol": PD_COROT_LOGVOL}
 PD_TR_ADAPT, PD_TR_NONE, PD_TR_CLAMP, PD_TR_ABS = 0, 1, 2, 3
 PD_SOLVE_AUTO, PD_SOLVE_S, PD_SOLVE_T = 0, 1, 2
 

@@ -154,7 +154,10 @@ int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_o
   if (!mesh || !mat || !mesh->X || !mesh->tets || !mat->E) return PD_ERR_ARG;
   if (mesh->n_v < 4 || mesh->n_e < 1 || !(dt > 0)) return PD_ERR_ARG;
   if (!(mat->nu > -1.0 && mat->nu < 0.5) || !(mat->density > 0)) return PD_ERR_ARG;
-  if (mat->model != PD_COROTATED && mat->model != PD_NEOHOOKEAN && mat->model != PD_COROT_VOLUME) return PD_ERR_ARG;
+  if (mat->model != PD_COROTATED && mat->model != PD_NEOHOOKEAN && mat->model != PD_COROT_VOLUME &&
+      mat->model != PD_COROT_LOGVOL)
+    return PD_ERR_ARG;
+  if (mat->model == PD_COROT_LOGVOL && !(mat->nu > 0.0)) return PD_ERR_ARG;   // the barrier's weight lambda_e > 0
   c = new pd_ctx();
   c->n_v = mesh->n_v;
   c->n_e = mesh->n_e;
@@ -317,6 +320,7 @@ int pd_set_materials(pd_ctx* c, const double* E, double nu) {
   if (!c || !E) return PD_ERR_ARG;
   if (c->batch) return fail(c, PD_ERR_ARG, "a batch context takes pd_set_materials_batch");
   if (!(nu > -1.0 && nu < 0.5)) return fail(c, PD_ERR_ARG, "nu must be in (-1, 0.5)");
+  if (c->model == PD_COROT_LOGVOL && !(nu > 0.0)) return fail(c, PD_ERR_ARG, "the log-volume barrier needs nu > 0");
   for (int e = 0; e < c->n_e; ++e)
     if (!(E[e] > 0)) return fail(c, PD_ERR_ARG, "E[%d] must be > 0", e);
   c->E.assign(E, E + c->n_e);
@@ -589,6 +593,7 @@ int pd_factor(pd_ctx* c) {
   for (int i = 0; i < 3; ++i) d.g[i] = c->g[i];
   d.mu_bar = mu_bar; d.lam_bar = lam_bar; d.k_bar = k_bar; d.mu_ref = mu_ref; d.beta0 = c->beta0; d.nu = c->nu;
   d.rot_share = (1.0 - 2.0 * c->nu) / (1.0 - c->nu);   // 2 mu / (2 mu + lambda) for any E
+  d.bar_r = (1.0 - 2.0 * c->nu) / (2.0 * c->nu);      // mu / lambda for any E
   // contacts: candidates in elimination order, W = (L_A^-1)_CC by host solves
   d.n_con = 0;
   if (!c->con_ground.empty() || !c->con_box.empty()) {
@@ -994,7 +999,7 @@ int pd_rollout(pd_ctx* c, int32_t T, const double* q0, const double* v0, const d
       double* qo = last && qTd ? qTd : c->sq;
       double* vo = last && vTd ? vTd : c->sv;
       pdk::launch_step_end(d, s, qo, vo, c->ckpt + (size_t)(t + 1) * nv3, c->tau);
-      c->launches += c->model == PD_NEOHOOKEAN ? 2 : 1;
+      c->launches += pdk::has_prox_hessian(c->model) ? 2 : 1;
       CK(cudaGetLastError());
     }
     d.escalate = escalate;

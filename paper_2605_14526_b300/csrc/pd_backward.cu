@@ -244,15 +244,19 @@ __device__ __forceinline__ void route_elem_item(const Dev& d, int e, const doubl
   double U[9], V[9], sf[3], ss[3], sv[3] = {1.0, 1.0, 1.0};
   svd3<double>(Fs, U, sf, V);
   NHMean<double> m{d.mu_bar, d.lam_bar, d.k_bar};
+  const NHMean<double> mb = barrier_prox_energy<double>(d);
   if (d.model == 1) {
     nh_prox<double>(sf, m, ss);
   } else {
-    // corotated, and the composite's rotation weight: p = R; the composite's
-    // volume weight takes p_vol = U diag(sigma_v) V^T below
+    // corotated, and the rotation weight of models 2 and 3: p = R; their
+    // volume weight takes p_vol = U diag(sigma_v) V^T below (sigma_v: the
+    // volume step, or the barrier's prox)
     ss[0] = ss[1] = ss[2] = 1.0;
     if (d.model == 2) {
       double nu;
       vol_project<double>(sf, sv, nu);
+    } else if (d.model == 3) {
+      nh_prox<double>(sf, mb, sv);
     }
   }
   double Md[3];  // diagonal of U^T (G mu) V
@@ -265,12 +269,27 @@ __device__ __forceinline__ void route_elem_item(const Dev& d, int e, const doubl
   double dw = 0.0;
   for (int i = 0; i < 3; ++i) dw += (ss[i] - sf[i]) * Md[i];
   d.dw[e] += d.vol[e] * dw;
-  if (d.model == 2) {   // b carries w_0 V G^T R + w_1 V G^T p_vol, A carries w_0 + w_1
+  if (d.model == 2 || d.model == 3) {   // b carries w_0 V G^T R + w_1 V G^T p_vol, A carries w_0 + w_1
     double dw1 = 0.0;
     for (int i = 0; i < 3; ++i) dw1 += (sv[i] - sf[i]) * Md[i];
     d.dw1[e] += d.vol[e] * dw1;
   }
   d.dbeta[e] += -d.vol[e] / d.h * gb;
+  if (d.model == 3) {
+    // dL/dr of the barrier (r = mu/lambda inside its prox) into the first
+    // mean slot: lambda_e V_e <G mu, U diag(d sigma_b/d r) V^T> with
+    // d sigma_b/d r = H~^+ (1/sigma_b) (the IFT on the stationarity
+    // (ln J - r)/sigma_i + sigma_i - sigma_F,i = 0, filtered like K)
+    double Jm[9];
+    filtered_jacobian<double>(sv, mb, tau, Jm);
+    const double lam_e = d.E[e] * d.nu / ((1.0 + d.nu) * (1.0 - 2.0 * d.nu));
+    const double coef = lam_e * d.vol[e];
+    for (int i = 0; i < 3; ++i) {
+      double ds = 0.0;
+      for (int j = 0; j < 3; ++j) ds += Jm[3 * i + j] / sv[j];
+      part[0] += coef * Md[i] * ds;
+    }
+  }
   if (d.model == 1) {
     double Jm[9];
     filtered_jacobian<double>(ss, m, tau, Jm);
@@ -310,10 +329,13 @@ __device__ __forceinline__ void chain_item(const Dev& d, int e, double* dE, doub
   const double dw_dnu = 2.0 * dmu_dnu + (nh ? dlam_dnu : 0.0);
   const double cb = d.mu_ref > 0.0 ? d.beta0 / d.mu_ref : 0.0;
   const double inv_n = 1.0 / d.n_e;
-  // the composite's two weights: w_0 = 2 mu (dw), w_1 = lambda (dw1)
-  const double v1E = d.model == 2 ? d.dw1[e] * dlam_dE : 0.0;
-  const double v1nu = d.model == 2 ? d.dw1[e] * dlam_dnu : 0.0;
-  if (dE) dE[e] = d.dw[e] * dw_dE + v1E + d.dbeta[e] * cb * dmu_dE + (am * dmu_dE + al * dlam_dE + ak * dw_dE) * inv_n;
+  // the two weights of models 2 and 3: w_0 = 2 mu (dw), w_1 = lambda (dw1)
+  const bool two = d.model == 2 || d.model == 3;
+  const double v1E = two ? d.dw1[e] * dlam_dE : 0.0;
+  const double v1nu = two ? d.dw1[e] * dlam_dnu : 0.0;
+  // the mesh means enter only the Neo-Hookean prox (model 3 keeps dL/dr in am)
+  const double mE = nh ? (am * dmu_dE + al * dlam_dE + ak * dw_dE) * inv_n : 0.0;
+  if (dE) dE[e] = d.dw[e] * dw_dE + v1E + d.dbeta[e] * cb * dmu_dE + mE;
   part[0] += d.dw[e] * dw_dnu + v1nu + d.dbeta[e] * cb * dmu_dnu;
   part[1] += dmu_dnu;
   part[2] += dlam_dnu;
@@ -370,6 +392,7 @@ __device__ __forceinline__ void route_finish(St* c, const double* s) {
 }
 
 __device__ __forceinline__ double chain_nu(const Dev& d, double am, double al, double ak, const double* s) {
+  if (d.model == 3) return s[0] - am / (2.0 * d.nu * d.nu);   // dL/dr dr/dnu, r = (1 - 2 nu)/(2 nu)
   const double inv_n = 1.0 / d.n_e;
   return s[0] + (am * s[1] + al * s[2] + ak * s[3]) * inv_n;
 }

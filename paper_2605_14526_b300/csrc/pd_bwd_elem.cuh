@@ -21,15 +21,28 @@ __device__ __forceinline__ void bwd_setup_item(const Dev& d, int e, const double
   T J[9] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
   T Sp[3], Tp[3];
   const int pi[3] = {0, 0, 1}, pj[3] = {1, 2, 2};
-  if (d.model == 1) {
-    NHMean<T> m{(T)d.mu_bar, (T)d.lam_bar, (T)d.k_bar};
+  if (has_prox_hessian(d.model)) {
+    // Neo-Hookean prox, or the log-volume barrier's (model 3: sigma* = a +
+    // (1 - a) sigma_b, its differential (1 - a) times the barrier prox's)
+    const bool bar = d.model == 3;
+    const NHMean<T> m = bar ? barrier_prox_energy<T>(d) : NHMean<T>{(T)d.mu_bar, (T)d.lam_bar, (T)d.k_bar};
     nh_prox<T>(sF, m, ss);
     filtered_jacobian<T>(ss, m, (T)tau, J);
-    // (s*_i - s*_j)/(s_i - s_j) = k / (k + mu + (mu - lam ln J*)/(s*_i s*_j)),
+    // (s*_i - s*_j)/(s_i - s_j) = k / (k + mu dv + (mu - lam ln J*)/(s*_i s*_j)),
     // exact at the prox stationarity and free of cancellation near s_i = s_j
     const T lnJ = dlog(ss[0] * ss[1] * ss[2]);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) Sp[c] = m.k / (m.k + m.mu + (m.mu - m.lam * lnJ) / (ss[pi[c]] * ss[pj[c]]));
+    for (int c = 0; c < 3; ++c) Sp[c] = m.k / (m.k + m.mu * m.dv + (m.mu - m.lam * lnJ) / (ss[pi[c]] * ss[pj[c]]));
+    if (bar) {
+      const T a = (T)d.rot_share;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) J[i] *= T(1) - a;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        ss[i] = a + (T(1) - a) * ss[i];
+        Sp[i] *= T(1) - a;
+      }
+    }
   } else if (d.model == 2) {
     // composite: sigma* = a + (1 - a) sigma_v; d sigma*/d sigma_F = (1 - a)
     // d sigma_v/d sigma_F (no prox Hessian, nothing to filter); with

@@ -9,6 +9,18 @@
 
 namespace pdk {
 
+// ------------------------------------------------------------ models
+
+// the log-volume barrier's prox (eq. pd_log_volume) divided by its weight
+// lambda_e, as the stretch prox of pd_math.cuh: mu = r, lam = k = 1, no
+// deviatoric term
+template <typename T>
+__device__ __forceinline__ NHMean<T> barrier_prox_energy(const Dev& d) {
+  NHMean<T> m{(T)d.bar_r, T(1), T(1)};
+  m.dv = T(0);
+  return m;
+}
+
 // ------------------------------------------------------------ reductions
 
 __host__ __device__ constexpr int pow2_ceil(int n) { return n <= 1 ? 1 : 2 * pow2_ceil((n + 1) / 2); }
@@ -197,21 +209,6 @@ __device__ __forceinline__ void corner_forces(const T* P, const T* Bm, T coef, T
     }
 #pragma unroll
   for (int i = 0; i < 3; ++i) out12[i] = -s[i];
-}
-
-template <typename T>
-__device__ __forceinline__ void project(const Dev& d, const T* F, T* P, T* U, T* sF, T* V, T* ss) {
-  svd3<T>(F, U, sF, V);
-  if (d.model == 0) {
-    ss[0] = ss[1] = ss[2] = T(1);
-  } else {
-    NHMean<T> m{(T)d.mu_bar, (T)d.lam_bar, (T)d.k_bar};
-    nh_prox<T>(sF, m, ss);
-  }
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) P[3 * i + j] = U[3 * i] * ss[0] * V[3 * j] + U[3 * i + 1] * ss[1] * V[3 * j + 1] + U[3 * i + 2] * ss[2] * V[3 * j + 2];
 }
 
 // acc += the corner contributions of vertex v, in incidence order. Indices

@@ -101,11 +101,16 @@ struct MlpDev {
   float fmean[kMlpIn], fscale[kMlpIn], oscale[kMlpOut];
 };
 
+// the models whose local step is a stretch prox with a Hessian to filter
+// (Sec. 4.3): Neo-Hookean and the log-volume barrier; they select tau per step
+__host__ __device__ constexpr bool has_prox_hessian(int model) { return model == 1 || model == 3; }
+
 // Everything the kernels need, passed by value.
 struct Dev {
   int n_v, n_e, n_f;
-  int model;          // 0 corotated, 1 Neo-Hookean, 2 corotated + volume composite
-  double rot_share;   // composite: a = w_0/(w_0 + w_1) = 2 mu/(2 mu + lambda) (the same for every element)
+  int model;          // 0 corotated, 1 Neo-Hookean, 2 corotated + volume composite, 3 corotated + log-volume barrier
+  double rot_share;   // models 2, 3: a = w_0/(w_0 + w_1) = 2 mu/(2 mu + lambda) (the same for every element)
+  double bar_r;       // model 3: r = mu/lambda = (1 - 2 nu)/(2 nu) inside the barrier's prox (the same for every element)
   int local_fp32;
   int aa_m, k_max, fixed_iters, tr_mode, adj_max_iters;
   int escalate;       // FP32 local step: switch to FP64 after this many iterations without progress (0 = never)

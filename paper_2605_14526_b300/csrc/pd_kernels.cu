@@ -314,7 +314,7 @@ void launch_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
 void launch_step_end(const Dev& d, cudaStream_t s, double* qn, double* vn, double* ckpt_next, double* tau) {
   (void)tau;
   k_step_end<<<nblk(d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d, qn, vn, ckpt_next);
-  if (d.model == 1) k_tr<<<nblk(d.n_e + d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
+  if (has_prox_hessian(d.model)) k_tr<<<nblk(d.n_e + d.n_v, kVtxBlock), kVtxBlock, 0, s>>>(d);
 }
 
 int max_reduction_blocks(int n_v, int n_e) {

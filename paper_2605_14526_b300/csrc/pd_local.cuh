@@ -34,7 +34,12 @@ __device__ __forceinline__ void local_item(const Dev& d, int e, const double* x,
 #pragma unroll
     for (int i = 0; i < 3; ++i) ss[i] = a + (T(1) - a) * sv[i];
   } else {
-    NHMean<T> m{(T)d.mu_bar, (T)d.lam_bar, (T)d.k_bar};
+    // Neo-Hookean prox (model 1), or the log-volume barrier's prox (model 3,
+    // eq. pd_log_volume) mixed with the rotation step like the composite:
+    // p = U diag(a + (1 - a) sigma_b) V^T; both warm-start from the
+    // element's previous prox stretches
+    const bool bar = d.model == 3;
+    const NHMean<T> m = bar ? barrier_prox_energy<T>(d) : NHMean<T>{(T)d.mu_bar, (T)d.lam_bar, (T)d.k_bar};
     float* ws = reinterpret_cast<float*>(d.sstar) + 3 * (size_t)e;
     T s0[3];
     const bool warm = ws[0] > 0.f && ws[1] > 0.f && ws[2] > 0.f;
@@ -43,6 +48,11 @@ __device__ __forceinline__ void local_item(const Dev& d, int e, const double* x,
     nh_prox_from<T>(sF, m, s0, ss);
 #pragma unroll
     for (int i = 0; i < 3; ++i) ws[i] = (float)ss[i];
+    if (bar) {
+      const T a = (T)d.rot_share;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) ss[i] = a + (T(1) - a) * ss[i];
+    }
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i)

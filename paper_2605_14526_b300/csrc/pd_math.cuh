@@ -8,7 +8,8 @@
 //    scheme of McAdams et al. 2011 (Jacobi eigenanalysis + QR), written with
 //    exact rotations instead of their approximate quaternion ones.
 //  * nh_prox: Newton on the Neo-Hookean stretch-space prox (Sec. 4.1,
-//    eq. nh_prox_normal) with positivity and a sufficient-decrease test.
+//    eq. nh_prox_normal) with positivity and a sufficient-decrease test; the
+//    same Newton solves the log-volume barrier's prox (eq. pd_log_volume).
 //  * filtered_jacobian: the prox's stretch Jacobian through the
 //    trust-region blend of its Hessian (Sec. 4.3, eq. tr_blend, tr_ift).
 #pragma once
@@ -132,9 +133,17 @@ __device__ __forceinline__ void svd3(const T* F, T* U, T* s, T* V) {
 
 // ------------------------------------------------------------ Neo-Hookean
 
+// The stretch-space prox energy k/2 ||s - sF||^2 + mu dv/2 (sum s^2 - 3)
+// - mu ln J + lam/2 (ln J)^2. dv = 1: the Neo-Hookean prox with the mesh
+// means (eq. nh_prox_normal). dv = 0: the log-volume barrier of eq.
+// pd_log_volume divided by its weight lambda_e (mu = r = mu_e/lambda_e,
+// lam = k = 1), whose Hessian is the Neo-Hookean one without the
+// deviatoric term. dv multiplies exactly, so the Neo-Hookean arithmetic is
+// unchanged by it.
 template <typename T>
 struct NHMean {
   T mu, lam, k;
+  T dv = T(1);
 };
 
 template <typename T>
@@ -143,7 +152,7 @@ __device__ __forceinline__ void nh_grad(const T* s, const NHMean<T>& m, const T*
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const T inv = T(1) / s[i];
-    g[i] = m.k * (s[i] - sF[i]) + m.mu * (s[i] - inv) + m.lam * lnJ * inv;
+    g[i] = m.k * (s[i] - sF[i]) + m.mu * (m.dv * s[i] - inv) + m.lam * lnJ * inv;
   }
 }
 
@@ -155,7 +164,7 @@ __device__ __forceinline__ void nh_hess(const T* s, const NHMean<T>& m, T lnJ, T
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j)
-      H[3 * i + j] = (i == j) ? m.k + m.mu * (T(1) + inv[i] * inv[i]) + m.lam * (T(1) - lnJ) * inv[i] * inv[i]
+      H[3 * i + j] = (i == j) ? m.k + m.mu * (m.dv + inv[i] * inv[i]) + m.lam * (T(1) - lnJ) * inv[i] * inv[i]
                               : m.lam * inv[i] * inv[j];
 }
 
@@ -168,7 +177,7 @@ __device__ __forceinline__ T nh_obj(const T* s, const NHMean<T>& m, const T* sF)
     d2 += (s[i] - sF[i]) * (s[i] - sF[i]);
     s2 += s[i] * s[i];
   }
-  return T(0.5) * m.k * d2 + T(0.5) * m.mu * (s2 - T(3)) - m.mu * lnJ + T(0.5) * m.lam * lnJ * lnJ;
+  return T(0.5) * m.k * d2 + T(0.5) * m.mu * (m.dv * (s2 - T(3))) - m.mu * lnJ + T(0.5) * m.lam * lnJ * lnJ;
 }
 
 // inverse of symmetric 3x3 by cofactors; returns false unless positive definite

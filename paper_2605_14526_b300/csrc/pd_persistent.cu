@@ -342,7 +342,7 @@ __device__ __forceinline__ void fwd_rollout_body(const Dev& d, const RollArgs& a
     double* vo = last && a.vT ? a.vT : a.sv;
     if (tid == 0) step_end_ctrl(d, &S, writer);
     for (int v = rv.lo + tid; v < rv.hi; v += blockDim.x) step_end_item(d, v, qo, vo, a.ckpt + (size_t)(t + 1) * nv3);
-    if (d.model == 1) {
+    if (has_prox_hessian(d.model)) {
       double p4[4] = {0.0, 0.0, 0.0, 0.0};
       for (int i = rt.lo + tid; i < rt.hi; i += blockDim.x) tr_item(d, i, p4);
       if (!(ok = grid_reduce<4>(d, tm, p4, sums))) break;

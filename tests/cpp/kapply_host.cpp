@@ -24,7 +24,7 @@ extern "C" {
 // tets [n_e][4]; Bm [n_e][9] (Dm^-1 row-major); coef [n_e] (w_e V_e);
 // qstar, p [n_v][3]; out [n_e][12]: the corner contributions of K p
 void kapply_host(int fp64, int model, int n_e, const int* tets, const double* Bm, const double* coef, double mu_bar,
-                 double lam_bar, double k_bar, double rot_share, const double* qstar, double tau, const double* p,
+                 double lam_bar, double k_bar, double rot_share, double bar_r, const double* qstar, double tau, const double* p,
                  double* out) {
   std::vector<float> Bm32(9 * (size_t)n_e), coef32(n_e);
   for (size_t i = 0; i < Bm32.size(); ++i) Bm32[i] = (float)Bm[i];
@@ -36,6 +36,7 @@ void kapply_host(int fp64, int model, int n_e, const int* tets, const double* Bm
   d.lam_bar = lam_bar;
   d.k_bar = k_bar;
   d.rot_share = rot_share;
+  d.bar_r = bar_r;
   d.tets = reinterpret_cast<const int4*>(tets);
   d.Bm32 = Bm32.data();
   d.Bm64 = Bm;

@@ -41,6 +41,23 @@ def test_binding_covers_header():
         assert getattr(L, n).argtypes is not None, n
 
 
+def test_binding_constants_equal_header_enums():
+    """Every PD_* enumerator of the header that the binding names has the
+    header's value (the model ids, trust-region and solve modes, L-BFGS
+    tasks)."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    vals = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", src, flags=re.S):
+        for name, val in re.findall(r"(PD_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
+            vals[name] = int(val)
+    assert vals["PD_COROT_LOGVOL"] == 3
+    named = [n for n in vals if hasattr(binding, n)]
+    assert {"PD_COROTATED", "PD_NEOHOOKEAN", "PD_COROT_VOLUME", "PD_COROT_LOGVOL"} <= set(named)
+    for n in named:
+        assert getattr(binding, n) == vals[n], n
+    assert sorted(binding.MODELS.values()) == [0, 1, 2, 3]
+
+
 def test_default_options_and_version(lib):
     o = binding.pd_default_options()
     assert o.aa_m == 5 and o.k_max == 200 and o.local_fp32 == 1

@@ -1,6 +1,8 @@
 """GPU tests of the standalone local step (pd_local_rhs: per-element
 projections and their scatter into the right-hand side, Sec. 4.1, eq.
-A_basic) against the oracle's local step and scatter."""
+A_basic; every energy: corotated, Neo-Hookean, the corotated + volume
+composite and the log-volume barrier variant) against the oracle's local
+step and scatter."""
 import dataclasses
 
 import numpy as np
@@ -28,7 +30,8 @@ def _deformed(sc, seed, amp):
     ("cube_corotated", False, 1e-12), ("cube_corotated", True, 2e-6),
     ("tiny_nh", False, 1e-12), ("tiny_nh", True, 2e-6),
     ("bar_nh", True, 2e-6), ("block16_nh", True, 2e-6),
-    ("tiny_cv", False, 1e-12), ("tiny_cv", True, 2e-6), ("bar_cv", True, 2e-6)])
+    ("tiny_cv", False, 1e-12), ("tiny_cv", True, 2e-6), ("bar_cv", True, 2e-6),
+    ("tiny_lv", False, 1e-12), ("tiny_lv", True, 2e-6), ("bar_lv", True, 2e-6)])
 def test_local_rhs_matches_oracle(case, fp32, tol):
     build()
     sc = {"cube_corotated": lambda: inputs.small_cube(),
@@ -36,7 +39,9 @@ def test_local_rhs_matches_oracle(case, fp32, tol):
           "bar_nh": lambda: inputs.hetero_bar(steps=1),
           "block16_nh": lambda: inputs.large_block(n=16, steps=1),
           "tiny_cv": lambda: inputs.tiny_block(n=3, cell=0.1, model="corotated_volume"),
-          "bar_cv": lambda: inputs.hetero_bar(steps=1).replace(model="corotated_volume")}[case]()
+          "bar_cv": lambda: inputs.hetero_bar(steps=1).replace(model="corotated_volume"),
+          "tiny_lv": lambda: inputs.tiny_block(n=3, cell=0.1, model="corotated_logvol"),
+          "bar_lv": lambda: inputs.hetero_bar(steps=1).replace(model="corotated_logvol")}[case]()
     sc = sc.replace(solver=dataclasses.replace(sc.solver, local_fp32=fp32))
     pd = binding.PDContext(sc)
     pb = solver.build_problem(sc)

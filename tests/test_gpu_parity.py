@@ -31,7 +31,7 @@ def test_cube_fixed_iterations_forward_and_backward(persistent):
     assert abs(g["dnu"] - o["dnu"]) < 1e-7 * abs(o["dnu"])
 
 
-@pytest.mark.parametrize("model", ["neohookean", "corotated", "corotated_volume"])
+@pytest.mark.parametrize("model", ["neohookean", "corotated", "corotated_volume", "corotated_logvol"])
 def test_tiny_fp64_converged_rollout(model):
     """FP64 local step with tight gates reaches the oracle's fixed points;
     per-step forces, damping, gravity, seeded initial velocity."""
@@ -65,12 +65,15 @@ def test_small_bar_fp32_config_gate(persistent):
     assert abs(g["dnu"] - o["dnu"]) < 1e-4 * abs(o["dnu"])
 
 
+@pytest.mark.parametrize("model", ["corotated_volume", "corotated_logvol"])
 @pytest.mark.parametrize("fp32", [True, False])
-def test_small_bar_composite_energy(fp32):
+def test_small_bar_composite_energy(fp32, model):
     """The corotated + volume composite (rotation step w_0 = 2 mu, volume
-    step w_1 = lambda, Sec. 4.1 and Sec. 7.2) on the heterogeneous bar, 20
-    steps: FP32 local step at the benchmark's gate, or FP64 at a tight gate."""
-    sc = inputs.hetero_bar(nx=8, ny=4, nz=4, block=4, steps=20).replace(model="corotated_volume")
+    step w_1 = lambda, Sec. 4.1 and Sec. 7.2), or the same rotation step
+    with the log-volume barrier as its volume step (eq. pd_log_volume), on
+    the heterogeneous bar, 20 steps: FP32 local step at the benchmark's
+    gate, or FP64 at a tight gate."""
+    sc = inputs.hetero_bar(nx=8, ny=4, nz=4, block=4, steps=20).replace(model=model)
     if fp32:
         sc = sc.replace(solver=inputs.SolverSettings(eps_res=1e-6, eps_step=1e-8))
         tq, tg = 1e-5, 1e-4
@@ -231,10 +234,12 @@ def test_single_free_vertex_and_unpinned_body():
     assert rel(g["dq0"], o["dq0"]) < 1e-6
 
 
-def test_anderson_counts_match_reference():
-    """Iterations and guard trips of the accelerated loop against the oracle's
-    FP64 restatement (FP64 local step on both sides)."""
-    sc = inputs.hetero_bar(nx=8, ny=4, nz=4, block=4, steps=4)
+@pytest.mark.parametrize("model", ["neohookean", "corotated_logvol"])
+def test_anderson_counts_match_reference(model):
+    """Iterations and guard trips of the accelerated loop, and the trust
+    region's tau per step, against the oracle's FP64 restatement (FP64 local
+    step on both sides), for both energies whose prox Hessian is filtered."""
+    sc = inputs.hetero_bar(nx=8, ny=4, nz=4, block=4, steps=4).replace(model=model)
     sc = sc.replace(solver=inputs.SolverSettings(local_fp32=False))
     g = gpu_run(sc, backward=False)
     g0 = gpu_run(sc, backward=False, persistent=0)

@@ -39,11 +39,12 @@ def host_kp(lib, pb, q, tau, p, fp64):
     Bm = np.ascontiguousarray(pb.rest.gradN[:, 1:4, :].reshape(n_e, 9))
     coef = np.ascontiguousarray(pb.mat.w * pb.rest.vol)
     out = np.zeros((n_e, 12))
-    model = {"corotated": 0, "neohookean": 1, "corotated_volume": 2}[pb.model]
+    model = {"corotated": 0, "neohookean": 1, "corotated_volume": 2, "corotated_logvol": 3}[pb.model]
     lib.kapply_host(ctypes.c_int(1 if fp64 else 0), ctypes.c_int(model), ctypes.c_int(n_e), _p(tets), _p(Bm),
                     _p(coef), ctypes.c_double(pb.mat.mu_bar), ctypes.c_double(pb.mat.lam_bar),
                     ctypes.c_double(pb.mat.k_bar), ctypes.c_double(float(solver.rotation_share(pb)[0])),
-                    _p(np.ascontiguousarray(q)), ctypes.c_double(tau), _p(np.ascontiguousarray(p)), _p(out))
+                    ctypes.c_double(float(solver.logvol_ratio(pb)[0])), _p(np.ascontiguousarray(q)),
+                    ctypes.c_double(tau), _p(np.ascontiguousarray(p)), _p(out))
     kp = np.zeros_like(q)
     np.add.at(kp, tets.ravel(), out.reshape(-1, 3))
     return kp
@@ -51,7 +52,8 @@ def host_kp(lib, pb, q, tau, p, fp64):
 
 CASES = [("neohookean", 1.0, 0.05), ("neohookean", 1.0, 0.3), ("corotated", 1.0, 0.3), ("bar", 1.0, 0.3),
          ("neohookean", 1.6, 0.05), ("corotated_volume", 1.0, 0.05), ("corotated_volume", 1.0, 0.3),
-         ("corotated_volume", 1.6, 0.05)]
+         ("corotated_volume", 1.6, 0.05), ("corotated_logvol", 1.0, 0.05), ("corotated_logvol", 1.0, 0.3),
+         ("corotated_logvol", 1.6, 0.05)]
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))

@@ -1,6 +1,6 @@
 """CPU parity of the library's local step (csrc/pd_local.cuh, Alg. 1 and
 Sec. 4.1: deformation gradient, rotation-variant SVD, corotated or
-Neo-Hookean projection, and the element's share of the right-hand side
+Neo-Hookean projection, the composite's or the barrier's, and the element's share of the right-hand side
 w_e V_e G_e^T vec(p_e), eq. A_basic) compiled as host C++
 (tests/cpp/local_host.cpp) and run over whole meshes, against the oracle's
 local step and scatter on the same deformed positions."""
@@ -30,7 +30,7 @@ def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-MODEL_IDS = {"corotated": 0, "neohookean": 1, "corotated_volume": 2}
+MODEL_IDS = {"corotated": 0, "neohookean": 1, "corotated_volume": 2, "corotated_logvol": 3}
 
 
 def host_rhs(lib, pb, q, fp64):
@@ -45,8 +45,8 @@ def host_rhs(lib, pb, q, fp64):
     model = MODEL_IDS[pb.model]
     lib.local_step_host(ctypes.c_int(1 if fp64 else 0), ctypes.c_int(model), ctypes.c_int(n_e), _p(tets), _p(Bm),
                         _p(coef), ctypes.c_double(pb.mat.mu_bar), ctypes.c_double(pb.mat.lam_bar),
-                        ctypes.c_double(pb.mat.k_bar), ctypes.c_double(float(solver.rotation_share(pb)[0])), _p(x),
-                        _p(out))
+                        ctypes.c_double(pb.mat.k_bar), ctypes.c_double(float(solver.rotation_share(pb)[0])),
+                        ctypes.c_double(float(solver.logvol_ratio(pb)[0])), _p(x), _p(out))
     b = np.zeros_like(x)
     np.add.at(b, tets.ravel(), out.reshape(-1, 3))
     return b
@@ -56,10 +56,11 @@ def _scenes():
     return [inputs.tiny_block(model="neohookean", steps=1, cell=0.1, n=3),
             inputs.tiny_block(model="corotated", steps=1, cell=0.1, n=3),
             inputs.hetero_bar(nx=8, ny=4, nz=4, block=4, steps=1),
-            inputs.tiny_block(model="corotated_volume", steps=1, cell=0.1, n=3)]
+            inputs.tiny_block(model="corotated_volume", steps=1, cell=0.1, n=3),
+            inputs.tiny_block(model="corotated_logvol", steps=1, cell=0.1, n=3)]
 
 
-@pytest.mark.parametrize("k", range(4))
+@pytest.mark.parametrize("k", range(5))
 @pytest.mark.parametrize("amp", [0.05, 0.3])
 def test_local_step_matches_oracle(lib, k, amp):
     """A large rotation plus per-vertex noise of amp x the 0.1 m cell; at
