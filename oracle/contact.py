@@ -18,6 +18,12 @@ the scalar Delassus matrix W = (L_A^-1)_CC of the candidate vertices C:
            s_c = q_u,xy[v_c] - q_t,xy[v_c]
   q        = q_u + A^-1 J^T lam,  J^T lam = (lam_f,c, n_c lam_n,c) at v_c
 
+Bilateral attachments (vertex v held at a prescribed target p(t), Sec. 4.6)
+are three equality rows at v with free multipliers: their z row joins the
+normal problem (a mixed LCP: no sign constraint, zero residual), their x and
+y rows join the friction problem (no disk), with p(t) in place of the
+obstacle height and of q_t,xy.
+
 Both subproblems are strictly convex QPs in W (SPD), so their solutions are
 unique. The normal LCP is solved exactly by Murty's least-index principal
 pivoting method (finite for positive definite matrices); the friction QP by
@@ -66,6 +72,39 @@ def lcp_murty(M: np.ndarray, q: np.ndarray, max_iter: int = 100000):
     raise RuntimeError("principal pivoting did not terminate")
 
 
+def mixed_lcp(M: np.ndarray, q: np.ndarray, free: np.ndarray):
+    """z with w = M z + q: w_F = 0 on the free rows, and z_N >= 0, w_N >= 0,
+    z_N^T w_N = 0 on the others, for positive definite M. The free rows are
+    eliminated exactly (their Schur complement is positive definite) and
+    the remaining LCP is solved by principal pivoting."""
+    F = np.asarray(free, dtype=bool)
+    N = ~F
+    z = np.zeros(q.size)
+    if not F.any():
+        return lcp_murty(M, q)
+    MFF = M[np.ix_(F, F)]
+    if N.any():
+        MFN = M[np.ix_(F, N)]
+        X = np.linalg.solve(MFF, MFN)
+        xq = np.linalg.solve(MFF, q[F])
+        z[N] = lcp_murty(M[np.ix_(N, N)] - MFN.T @ X, q[N] - MFN.T @ xq)
+        z[F] = -(xq + X @ z[N])
+    else:
+        z[F] = np.linalg.solve(MFF, -q[F])
+    return z
+
+
+def mixed_lcp_kkt(M, q, z, free) -> float:
+    """Largest violation of the mixed LCP's conditions (scaled)."""
+    F = np.asarray(free, dtype=bool)
+    w = M @ z + q
+    s = max(np.abs(q).max(initial=0.0), 1e-300)
+    viol = np.abs(w[F]).max(initial=0.0) / s
+    if (~F).any():
+        viol = max(viol, lcp_kkt(M[np.ix_(~F, ~F)], w[~F] - M[np.ix_(~F, ~F)] @ z[~F], z[~F]))
+    return float(viol)
+
+
 def lcp_kkt(M, q, z) -> float:
     """Largest violation of z >= 0, w >= 0, z_i w_i = 0 (scaled)."""
     w = M @ z + q
@@ -76,14 +115,20 @@ def lcp_kkt(M, q, z) -> float:
 
 def tresca_kkt(W, s, rho, lam) -> float:
     """KKT violation of min 1/2 lam^T (W (x) I2) lam + s^T lam over disks
-    |lam_c| <= rho_c: with slip u = s + W lam, a contact inside its disk has
-    u_c = 0, a contact on its boundary has u_c = -t lam_c, t >= 0."""
+    |lam_c| <= rho_c (rho_c = inf: a free row): with slip u = s + W lam, a
+    contact inside its disk has u_c = 0, a contact on its boundary has
+    u_c = -t lam_c, t >= 0."""
     u = s + W @ lam
     sc = max(np.abs(s).max(), 1e-300)
+    fin = np.isfinite(rho)
+    rmax = max(rho[fin].max(initial=0.0), 1e-300)
     viol = 0.0
     for c in range(lam.shape[0]):
         r = np.linalg.norm(lam[c])
-        viol = max(viol, (r - rho[c]) / max(rho.max(), 1e-300))
+        if not fin[c]:            # a free row (attachment): zero residual
+            viol = max(viol, np.linalg.norm(u[c]) / sc)
+            continue
+        viol = max(viol, (r - rho[c]) / rmax)
         if r < rho[c] * (1 - 1e-10) or rho[c] == 0.0:
             if rho[c] > 0:
                 viol = max(viol, np.linalg.norm(u[c]) / sc)
@@ -118,11 +163,12 @@ def tresca_pgs(W, s, rho, lam0, tol=1e-12, max_sweeps=200000):
             r = s[c] + W[c] @ lam
             new = lam[c] - r / W[c, c]
             nn = np.linalg.norm(new)
-            if nn > rho[c]:
+            if nn > rho[c]:           # never for a free row (rho = inf)
                 new *= rho[c] / nn
             dmax = max(dmax, np.abs(new - lam[c]).max())
             lam[c] = new
-        if dmax <= 1e-15 * max(rho.max(), 1e-300) and tresca_kkt(W, s, rho, lam) <= tol:
+        scale = max(rho[np.isfinite(rho)].max(initial=0.0), np.abs(lam).max(), 1e-300)
+        if dmax <= 1e-15 * scale and tresca_kkt(W, s, rho, lam) <= tol:
             break
     return lam
 
@@ -132,10 +178,15 @@ class ContactProblem:
 
     def __init__(self, pb: solver.Problem, spec):
         self.spec = spec
-        self.verts = np.concatenate([spec.ground, spec.box]).astype(np.int64)
-        self.normal = np.concatenate([np.ones(spec.ground.size), -np.ones(spec.box.size)])
+        att = np.asarray(spec.attach, dtype=np.int64)
+        self.verts = np.concatenate([spec.ground, spec.box, att]).astype(np.int64)
+        self.normal = np.concatenate([np.ones(spec.ground.size), -np.ones(spec.box.size), np.ones(att.size)])
+        # attachment rows: index into the spec's attachment arrays, else -1
+        self.att_index = np.concatenate([-np.ones(spec.ground.size + spec.box.size, dtype=np.int64),
+                                         np.arange(att.size)])
         order = np.argsort(self.verts, kind="stable")
-        self.verts, self.normal = self.verts[order], self.normal[order]
+        self.verts, self.normal, self.att_index = self.verts[order], self.normal[order], self.att_index[order]
+        self.is_att = self.att_index >= 0
         self.pos = np.searchsorted(pb.free, self.verts)
         self.W = delassus(pb, self.verts)
         # slip below which a contact counts as sticking: 1e-7 of the rest
@@ -144,7 +195,18 @@ class ContactProblem:
         self.slip_tol = 1e-7 * float(np.linalg.norm(X.max(axis=0) - X.min(axis=0)))
 
     def heights(self, t: int) -> np.ndarray:
-        return np.where(self.normal > 0, self.spec.ground_z, self.spec.box_z(t))
+        """Per candidate: the obstacle height, or an attachment's target z."""
+        h = np.where(self.normal > 0, self.spec.ground_z, self.spec.box_z(t) if self.spec.box.size else 0.0)
+        if self.is_att.any():
+            h = np.where(self.is_att, self.targets(t)[:, 2], h)
+        return h
+
+    def targets(self, t: int) -> np.ndarray:
+        """[K,3] attachment targets at the end of step t (zeros on obstacle rows)."""
+        out = np.zeros((self.verts.size, 3))
+        if self.is_att.any():
+            out[self.is_att] = self.spec.attach_target(t)[self.att_index[self.is_att]]
+        return out
 
 
 def correct(pb: solver.Problem, cp: ContactProblem, q_u_free, q_t, t: int, lam_f0=None):
@@ -153,10 +215,13 @@ def correct(pb: solver.Problem, cp: ContactProblem, q_u_free, q_t, t: int, lam_f
     D = cp.normal
     g = D * (q_u_free[cp.pos, 2] - cp.heights(t))
     M = (D[:, None] * cp.W) * D[None, :]
-    lam_n = lcp_murty(M, g)
-    assert lcp_kkt(M, g, lam_n) <= 1e-9, "normal LCP not solved"
-    slip = q_u_free[cp.pos, :2] - q_t[cp.verts, :2]
-    lam_f = tresca(cp.W, slip, cp.spec.mu * lam_n, lam_f0)
+    lam_n = mixed_lcp(M, g, cp.is_att)
+    assert mixed_lcp_kkt(M, g, lam_n, cp.is_att) <= 1e-9, "normal LCP not solved"
+    # tangential reference: q_t,xy for contacts, the target for attachments
+    ref = np.where(cp.is_att[:, None], cp.targets(t)[:, :2], q_t[cp.verts, :2])
+    slip = q_u_free[cp.pos, :2] - ref
+    rho = np.where(cp.is_att, np.inf, cp.spec.mu * lam_n)
+    lam_f = tresca(cp.W, slip, rho, lam_f0)
     r = np.zeros((pb.free.size, 3))
     r[cp.pos, 0] = lam_f[:, 0]
     r[cp.pos, 1] = lam_f[:, 1]
@@ -219,11 +284,14 @@ def active_sets(cp: ContactProblem, lam_n, q_next, q_t):
     sliding one has its friction on the disk boundary, so this is the same
     split as the one by the multipliers; it reads the positions, which an
     iterative inner solver determines far better than the multipliers in
-    the ill-conditioned directions of W."""
-    act = lam_n > 1e-9 * lam_n.sum()
+    the ill-conditioned directions of W. Attachments are always in both sets
+    and stay out of the impulse total."""
+    con = ~cp.is_att
+    act = con & (lam_n > 1e-9 * lam_n[con].sum())
     slip = np.linalg.norm(q_next[cp.verts, :2] - q_t[cp.verts, :2], axis=1)
     stick = act & (slip <= cp.slip_tol) & (cp.spec.mu > 0.0)   # no friction: never held
-    return act, stick
+    # attachments: all three rows are equalities at every step
+    return act | cp.is_att, stick | cp.is_att
 
 
 def constraint_rows(pb, cp: ContactProblem, act, stick):
@@ -270,7 +338,7 @@ def backward_step(pb, cp: ContactProblem, rec, tau: float, qbar_next, vbar_next)
     nu = sol[3 * pb.free.size:]
     g = adjoint.route_step(pb, q_t, q_star, tau, a, vbar_next)
     for (c, ax), val in zip(tags, nu):
-        if ax < 2:
+        if ax < 2 and not cp.is_att[c]:     # an attachment's h is its target, not q_t
             g.dq_t[cp.verts[c], ax] += val
     return g
 

@@ -400,7 +400,10 @@ class ContactSpec:
     (z >= ground_z, normal +z) for ``ground`` vertices and vertex-box-bottom
     (z <= box_z(t), normal -z) for ``box`` vertices; the rigid box moves down
     by ``box_travel`` over the first ``box_steps`` steps and is then held.
-    Coulomb coefficient ``mu`` (Tresca disks of radius mu * lambda_n)."""
+    Coulomb coefficient ``mu`` (Tresca disks of radius mu * lambda_n).
+    Bilateral attachments (Sec. 4.6): vertex ``attach[i]`` is held at
+    ``attach_target(t)[i]``, which moves from ``attach_p0[i]`` by
+    ``attach_travel[i]`` over the first ``attach_steps`` steps."""
     ground: np.ndarray          # [Kg] vertex indices
     box: np.ndarray             # [Kb] vertex indices
     ground_z: float
@@ -408,10 +411,19 @@ class ContactSpec:
     box_travel: float
     box_steps: int
     mu: float
+    attach: np.ndarray = field(default_factory=lambda: np.zeros(0, dtype=np.int64))   # [Ka]
+    attach_p0: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))          # [Ka,3]
+    attach_travel: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))      # [Ka,3]
+    attach_steps: int = 1
 
     def box_z(self, t: int) -> float:
         """Height of the box bottom at the end of step t (0-based)."""
         return self.box_z0 - self.box_travel * min(t + 1, self.box_steps) / self.box_steps
+
+    def attach_target(self, t: int) -> np.ndarray:
+        """[Ka,3] attachment targets at the end of step t (0-based)."""
+        k = min(t + 1, self.attach_steps) / self.attach_steps
+        return np.asarray(self.attach_p0, dtype=np.float64) + k * np.asarray(self.attach_travel, dtype=np.float64)
 
 
 def contact_pad(nx: int = 48, ny: int = 48, nz: int = 12, cell: float = 0.01, footprint: int = 16,
