@@ -182,7 +182,14 @@ typedef struct pd_ctx pd_ctx;
  * of a rollout, z_box(t) = box_z0 - box_travel min(t + 1, box_steps) /
  * box_steps at the end of step t. Coulomb friction with coefficient mu, as
  * Tresca disks of radius mu lambda_n on the tangential displacement since
- * q_t. Candidates must be free vertices; every index appears once. */
+ * q_t. Bilateral attachments (Sec. 4.6): vertex attach[i] is held at
+ * p_i(t) = attach_target[i] + attach_travel[i] min(t + 1, attach_steps) /
+ * attach_steps at the end of step t, by three equality rows with free
+ * multipliers (its z row solved with the normal rows, its x, y rows with the
+ * friction rows, without a disk); in the adjoint they are equality
+ * constraints at every step (no gradient with respect to the targets is
+ * returned). Candidates must be free vertices; every index appears once
+ * over ground, box and attach. */
 typedef struct {
   int32_t n_ground, n_box;
   const int32_t* ground;  /* [n_ground] vertex indices (host, copied) */
@@ -192,6 +199,11 @@ typedef struct {
   double mu;
   double tol;             /* relative tolerance of the inner solves (0: 1e-12) */
   int32_t max_iters;      /* cap on inner passes per solve (0: 2000) */
+  int32_t n_attach;
+  const int32_t* attach;        /* [n_attach] vertex indices (host, copied) */
+  const double* attach_target;  /* [n_attach][3] target at the start of the motion (m) */
+  const double* attach_travel;  /* [n_attach][3] displacement of the target; NULL: static */
+  int32_t attach_steps;         /* steps over which the targets move (>= 1 when attach_travel is set) */
 } pd_contact_desc;
 
 /* Default options (m = 5, k_max = 200, gate 1e-8 / 1e-6 / 1e-12, FP32 local,
@@ -209,8 +221,8 @@ void pd_default_options(pd_options* out);
 int pd_create(const pd_mesh* mesh, const pd_material* mat, double dt, const pd_options* opt,
               pd_ctx** out);
 
-/* Frictional contacts of a single-instance context (NULL or n_ground +
- * n_box = 0 removes them). pd_factor then also forms the dense scalar
+/* Frictional contacts and attachments of a single-instance context (NULL or
+ * n_ground + n_box + n_attach = 0 removes them). pd_factor then also forms the dense scalar
  * Delassus matrix W = (L_A^-1)_CC of the K candidates (K host solves with the
  * factor, FP64; K^2 x 8 bytes on the device). Each local-global iteration of
  * a rollout computes q_u = A^-1 b(q) at the candidates, solves the normal
@@ -225,8 +237,9 @@ int pd_set_contacts(pd_ctx* ctx, const pd_contact_desc* desc);
 
 /* Contact impulses of step t (0 <= t < T) of the last rollout: n_out = the
  * number K of candidates; vertex [K] (the candidate's vertex), lam_n [K]
- * (normal impulse, >= 0, along +z for ground and -z for box candidates),
- * lam_f [K][2] (tangential x, y impulse). Any of the three arrays may be
+ * (normal impulse, >= 0, along +z for ground and -z for box candidates;
+ * an attachment's z impulse, of either sign), lam_f [K][2] (tangential x, y
+ * impulse). Any of the three arrays may be
  * NULL (only n_out is written when all are). Host outputs; synchronous.
  * Candidates come in elimination order, not in the order of the descriptor. */
 int pd_get_contact_impulses(const pd_ctx* ctx, int32_t t, int32_t* n_out, int32_t* vertex, double* lam_n,

@@ -61,7 +61,9 @@ class pd_stats(ctypes.Structure):
 class pd_contact_desc(ctypes.Structure):
     _fields_ = [("n_ground", c_int32), ("n_box", c_int32), ("ground", c_void_p), ("box", c_void_p),
                 ("ground_z", c_double), ("box_z0", c_double), ("box_travel", c_double), ("box_steps", c_int32),
-                ("mu", c_double), ("tol", c_double), ("max_iters", c_int32)]
+                ("mu", c_double), ("tol", c_double), ("max_iters", c_int32), ("n_attach", c_int32),
+                ("attach", c_void_p), ("attach_target", c_void_p), ("attach_travel", c_void_p),
+                ("attach_steps", c_int32)]
 
 
 class pd_profile_out(ctypes.Structure):
@@ -533,9 +535,14 @@ def pd_set_contacts(ctx, spec, tol=0.0, max_iters=0):
         return
     g = np.ascontiguousarray(spec.ground, dtype=np.int32)
     b = np.ascontiguousarray(spec.box, dtype=np.int32)
+    a = np.ascontiguousarray(spec.attach, dtype=np.int32)
+    p0 = np.ascontiguousarray(spec.attach_p0, dtype=np.float64).reshape(-1, 3)
+    tr = np.ascontiguousarray(spec.attach_travel, dtype=np.float64).reshape(-1, 3)
     desc = pd_contact_desc(int(g.size), int(b.size), _ptr(g, np.int32) if g.size else None,
                            _ptr(b, np.int32) if b.size else None, float(spec.ground_z), float(spec.box_z0),
-                           float(spec.box_travel), int(spec.box_steps), float(spec.mu), float(tol), int(max_iters))
+                           float(spec.box_travel), int(spec.box_steps), float(spec.mu), float(tol), int(max_iters),
+                           int(a.size), _ptr(a, np.int32) if a.size else None, _ptr(p0) if a.size else None,
+                           _ptr(tr) if a.size else None, int(spec.attach_steps))
     _check(ctx, lib().pd_set_contacts(ctx, ctypes.byref(desc)))
 
 

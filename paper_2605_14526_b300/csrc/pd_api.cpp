@@ -283,12 +283,18 @@ int pd_set_contacts(pd_ctx* c, const pd_contact_desc* desc) {
   if (c->batch) return fail(c, PD_ERR_ARG, "pd_set_contacts is single-instance only");
   c->con_ground.clear();
   c->con_box.clear();
+  c->con_att.clear();
+  c->con_att_p0.clear();
+  c->con_att_tr.clear();
   c->con = pd_contact_desc{};
   c->factored = false;
-  if (!desc || desc->n_ground + desc->n_box == 0) return PD_OK;
-  if (desc->n_ground < 0 || desc->n_box < 0 || (desc->n_ground && !desc->ground) || (desc->n_box && !desc->box))
+  if (!desc || desc->n_ground + desc->n_box + desc->n_attach == 0) return PD_OK;
+  if (desc->n_ground < 0 || desc->n_box < 0 || desc->n_attach < 0 || (desc->n_ground && !desc->ground) ||
+      (desc->n_box && !desc->box) || (desc->n_attach && (!desc->attach || !desc->attach_target)))
     return fail(c, PD_ERR_ARG, "contact candidate arrays");
   if (desc->n_box > 0 && desc->box_steps < 1) return fail(c, PD_ERR_ARG, "box_steps must be >= 1");
+  if (desc->n_attach > 0 && desc->attach_travel && desc->attach_steps < 1)
+    return fail(c, PD_ERR_ARG, "attach_steps must be >= 1");
   if (!(desc->mu >= 0)) return fail(c, PD_ERR_ARG, "mu must be >= 0");
   std::vector<char> seen(c->n_v, 0);
   auto take = [&](const int32_t* p, int n, std::vector<int>& out) -> int {
@@ -303,14 +309,31 @@ int pd_set_contacts(pd_ctx* c, const pd_contact_desc* desc) {
     return PD_OK;
   };
   int r;
-  if ((r = take(desc->ground, desc->n_ground, c->con_ground)) || (r = take(desc->box, desc->n_box, c->con_box))) {
+  if ((r = take(desc->ground, desc->n_ground, c->con_ground)) || (r = take(desc->box, desc->n_box, c->con_box)) ||
+      (r = take(desc->attach, desc->n_attach, c->con_att))) {
     c->con_ground.clear();
     c->con_box.clear();
+    c->con_att.clear();
     return r;
+  }
+  for (int i = 0; i < 3 * desc->n_attach; ++i) {
+    const double p = desc->attach_target[i], tr = desc->attach_travel ? desc->attach_travel[i] : 0.0;
+    if (!std::isfinite(p) || !std::isfinite(tr)) {
+      c->con_ground.clear();
+      c->con_box.clear();
+      c->con_att.clear();
+      return fail(c, PD_ERR_ARG, "attachment target %d is not finite", i / 3);
+    }
+    c->con_att_p0.push_back(p);
+    c->con_att_tr.push_back(tr);
   }
   c->con = *desc;
   c->con.ground = nullptr;
   c->con.box = nullptr;
+  c->con.attach = nullptr;
+  c->con.attach_target = nullptr;
+  c->con.attach_travel = nullptr;
+  if (c->con.attach_steps < 1) c->con.attach_steps = 1;
   if (!(c->con.tol > 0)) c->con.tol = 1e-12;
   if (c->con.max_iters <= 0) c->con.max_iters = 2000;
   return PD_OK;
@@ -427,7 +450,7 @@ int pd_factor(pd_ctx* c) {
   }
   c->nnz_S = pdf::inverse_factor_nnz(c->fac);
   // solve mode: products with S, or level-scheduled solves with L (mode T)
-  const bool has_con = !c->con_ground.empty() || !c->con_box.empty();
+  const bool has_con = !c->con_ground.empty() || !c->con_box.empty() || !c->con_att.empty();
   int mode = c->opt.solve_mode;
   if (mode == PD_SOLVE_T && has_con) return fail(c, PD_ERR_ARG, "solve mode T does not support contacts");
   // automatic choice: S while its stream stays near the L2 size (2 barriers
@@ -596,20 +619,30 @@ int pd_factor(pd_ctx* c) {
   d.bar_r = (1.0 - 2.0 * c->nu) / (2.0 * c->nu);      // mu / lambda for any E
   // contacts: candidates in elimination order, W = (L_A^-1)_CC by host solves
   d.n_con = 0;
-  if (!c->con_ground.empty() || !c->con_box.empty()) {
-    std::vector<std::pair<int, int>> cand;  // (position, index into ground+box)
+  if (!c->con_ground.empty() || !c->con_box.empty() || !c->con_att.empty()) {
+    std::vector<std::pair<int, int>> cand;  // (position, index into ground+box+attach)
     std::vector<int> all(c->con_ground);
     all.insert(all.end(), c->con_box.begin(), c->con_box.end());
+    all.insert(all.end(), c->con_att.begin(), c->con_att.end());
     for (size_t i = 0; i < all.size(); ++i) cand.push_back({iperm_v[all[i]], (int)i});
     std::sort(cand.begin(), cand.end());
     const int K = (int)cand.size();
-    std::vector<int> cv(K), cp(K), cf(K);
-    std::vector<double> cn(K), W((size_t)K * K);
+    const int n_gb = (int)(c->con_ground.size() + c->con_box.size());
+    std::vector<int> cv(K), cp(K), cf(K), ca(K, 0);
+    std::vector<double> cn(K), W((size_t)K * K), ct((size_t)6 * K, 0.0);
     for (int k = 0; k < K; ++k) {
-      cv[k] = all[cand[k].second];
+      const int src = cand[k].second;
+      cv[k] = all[src];
       cp[k] = cand[k].first;
-      cn[k] = cand[k].second < (int)c->con_ground.size() ? 1.0 : -1.0;
+      cn[k] = src < (int)c->con_ground.size() || src >= n_gb ? 1.0 : -1.0;   // attachments: +z rows
       cf[k] = v2f[cv[k]];
+      if (src >= n_gb) {   // attachment: its target and the target's travel
+        ca[k] = 1;
+        for (int j = 0; j < 3; ++j) {
+          ct[6 * (size_t)k + j] = c->con_att_p0[3 * (size_t)(src - n_gb) + j];
+          ct[6 * (size_t)k + 3 + j] = c->con_att_tr[3 * (size_t)(src - n_gb) + j];
+        }
+      }
     }
 #pragma omp parallel
     {
@@ -644,11 +677,12 @@ int pd_factor(pd_ctx* c) {
       lmax = nn / std::sqrt(un);
       for (int i = 0; i < K; ++i) u[i] = w[i] / nn;
     }
-    int *cv_d, *cp_d;
-    double *cn_d, *W_d, *buf_d;
+    int *cv_d, *cp_d, *ca_d = nullptr;
+    double *cn_d, *W_d, *buf_d, *ct_d = nullptr;
     if ((r = upload(c, &cv_d, cv, true)) || (r = upload(c, &cp_d, cp, true)) || (r = upload(c, &cn_d, cn, true)) ||
         (r = upload(c, &W_d, W, true)) || (r = dalloc(c, &buf_d, 14 * (size_t)K, true)))
       return r;
+    if (!c->con_att.empty() && ((r = upload(c, &ca_d, ca, true)) || (r = upload(c, &ct_d, ct, true)))) return r;
     double* bwd_d;
     if ((r = dalloc(c, &bwd_d, 23 * (size_t)K, true))) return r;
     d.con_bwd = bwd_d;
@@ -660,6 +694,9 @@ int pd_factor(pd_ctx* c) {
     d.con_v = cv_d;
     d.con_pos = cp_d;
     d.con_n = cn_d;
+    d.con_att = ca_d;
+    d.con_tgt = ct_d;
+    d.con_att_steps = c->con.attach_steps > 0 ? c->con.attach_steps : 1;
     d.con_W = W_d;
     d.con_buf = buf_d;
     d.con_L = 1.001 * lmax;   // a little above lambda_max: the step stays below 1 / L

@@ -632,7 +632,8 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
     const double* ck = (d.n_con > 0 && d.con_ckpt) ? d.con_ckpt + (size_t)t * 3 * d.n_con : nullptr;
     if (ck) {   // the step's total normal impulse sets the normal-active threshold
       double ps[1] = {0.0};
-      for (int c = rcn.lo + tid; c < rcn.hi; c += blockDim.x) ps[0] += ck[c];
+      for (int c = rcn.lo + tid; c < rcn.hi; c += blockDim.x)
+        if (!con_is_att(d, c)) ps[0] += ck[c];   // attachments carry free-sign multipliers
       if (!(ok = grid_reduce<1>(d, tm, ps, sums))) break;
       const double thr = 1e-9 * sums[0];
       for (int c = rcn.lo + tid; c < rcn.hi; c += blockDim.x) contact_flag_item(d, ck, thr, qstar, qt, c);
@@ -745,8 +746,9 @@ __device__ __forceinline__ void bwd_rollout_body(const Dev& d, const BwdArgs& a,
     __syncthreads();
     if (ck) {
       // sticking contacts: the constraint q_xy = q_t,xy routes nu_S to dL/dq_t
+      // (attachments hold their vertices at prescribed targets instead)
       for (int c = rcn.lo + tid; c < rcn.hi; c += blockDim.x)
-        if (con_stick(d, c)) {
+        if (con_stick(d, c) && !con_is_att(d, c)) {
           const int v = d.con_v[c];
           d.gq[3 * (size_t)v] += cb_nu(d)[3 * c];
           d.gq[3 * (size_t)v + 1] += cb_nu(d)[3 * c + 1];

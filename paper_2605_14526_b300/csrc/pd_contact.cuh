@@ -28,6 +28,14 @@ __device__ __forceinline__ double con_height(const Dev& d, int c, int t) {
   return d.con_zb0 - d.con_travel * (double)k / (double)d.con_steps;
 }
 
+// bilateral attachments: three equality rows with free multipliers that
+// hold the vertex at its target p(t) = p0 + travel min(t + 1, steps)/steps
+__device__ __forceinline__ bool con_is_att(const Dev& d, int c) { return d.con_att && d.con_att[c]; }
+__device__ __forceinline__ double con_target(const Dev& d, int c, int t, int k) {
+  const double s = (double)min(t + 1, d.con_att_steps) / (double)d.con_att_steps;
+  return d.con_tgt[6 * (size_t)c + k] + s * d.con_tgt[6 * (size_t)c + 3 + k];
+}
+
 // work buffer layout: lam_n [3][K] (rotating prev / cur / next), lam_f [3][K][2],
 // gap [K], slip [K][2]
 __device__ __forceinline__ double* con_lamn(const Dev& d, int r) { return d.con_buf + (size_t)(r % 3) * d.n_con; }
@@ -41,15 +49,21 @@ __device__ __forceinline__ double* con_slip(const Dev& d) { return d.con_buf + 1
 __device__ __forceinline__ double* con_z(const Dev& d) { return d.con_buf + 12 * (size_t)d.n_con; }
 
 // warp per candidate: q_u at the candidate (row pos_c of S^T y), its gap and
-// its slip since q_t
+// its slip since q_t (an attachment: its residuals to the target)
 __device__ __forceinline__ void contact_gather(const Dev& d, int c, int t, int lane) {
   double a0, a1, a2;
   spmv_st_sum(d, d.y, d.con_pos[c], lane, a0, a1, a2);
   if (lane == 0) {
     const int v = d.con_v[c];
-    con_gap(d)[c] = d.con_n[c] * (a2 - con_height(d, c, t));
-    con_slip(d)[2 * c] = a0 - d.qt[3 * (size_t)v];
-    con_slip(d)[2 * c + 1] = a1 - d.qt[3 * (size_t)v + 1];
+    if (con_is_att(d, c)) {   // residuals to the target on all three rows
+      con_gap(d)[c] = a2 - con_target(d, c, t, 2);
+      con_slip(d)[2 * c] = a0 - con_target(d, c, t, 0);
+      con_slip(d)[2 * c + 1] = a1 - con_target(d, c, t, 1);
+    } else {
+      con_gap(d)[c] = d.con_n[c] * (a2 - con_height(d, c, t));
+      con_slip(d)[2 * c] = a0 - d.qt[3 * (size_t)v];
+      con_slip(d)[2 * c + 1] = a1 - d.qt[3 * (size_t)v + 1];
+    }
   }
 }
 
@@ -105,7 +119,8 @@ __device__ __forceinline__ void friction_z_item(const Dev& d, int c, int rot, do
 }
 
 // normal LCP pass, warp per row c: next_c = max(0, z_c - ((D W D z)_c + g_c) / L)
-// with D z from the extrapolation buffer
+// with D z from the extrapolation buffer (an attachment's row: no max, the
+// mixed LCP's free variable)
 __device__ __forceinline__ void normal_row(const Dev& d, int c, int rot, int lane, double* part) {
   const int K = d.n_con;
   const double* cur = con_lamn(d, rot + 1);
@@ -119,7 +134,7 @@ __device__ __forceinline__ void normal_row(const Dev& d, int c, int rot, int lan
   if (lane == 0) {
     const double zc = d.con_n[c] * z[c];   // n_c = +-1
     const double grad = d.con_n[c] * acc + con_gap(d)[c];
-    const double nv = fmax(0.0, zc - grad / d.con_L);
+    const double nv = con_is_att(d, c) ? zc - grad / d.con_L : fmax(0.0, zc - grad / d.con_L);   // attachment: free
     nxt[c] = nv;
     const double dl = nv - cur[c];
     part[0] += dl * dl;
@@ -128,7 +143,8 @@ __device__ __forceinline__ void normal_row(const Dev& d, int c, int rot, int lan
   }
 }
 
-// Tresca pass, warp per row c: two components, disk radius mu * lam_n,c
+// Tresca pass, warp per row c: two components, disk radius mu * lam_n,c (an
+// attachment's rows: no disk)
 __device__ __forceinline__ void friction_row(const Dev& d, int c, int rot, const double* lam_n, int lane,
                                              double* part) {
   const int K = d.n_con;
@@ -154,7 +170,7 @@ __device__ __forceinline__ void friction_row(const Dev& d, int c, int rot, const
     double ny = zy - (sy + con_slip(d)[2 * c + 1]) / d.con_L;
     const double rho = d.con_mu * lam_n[c];
     const double r = sqrt(nx * nx + ny * ny);
-    if (r > rho) {
+    if (r > rho && !con_is_att(d, c)) {   // an attachment has no disk
       const double s = r > 0.0 ? rho / r : 0.0;
       nx *= s;
       ny *= s;
@@ -220,7 +236,8 @@ __device__ __forceinline__ void contact_y_row(const Dev& d, int i, const double*
 // terms, and the CG reaches its tolerance instead of breaking down at the
 // rounding level of W_a. On exit (A - K) a + G^T nu = q_bar - r; the
 // sticking rows of nu enter dL/dq_t (the constraint q_xy = q_t,xy of a
-// sticking contact depends on q_t).
+// sticking contact depends on q_t; an attachment's rows, whose constraint is
+// its prescribed target, do not).
 
 // active sets of the step, one flag per candidate (bit 0 normal-active,
 // bit 1 sticking), formed at the step's start by contact_flag_item
@@ -236,6 +253,10 @@ __device__ __forceinline__ bool con_stick(const Dev& d, int c) { return ((int)cb
 // multipliers in the ill-conditioned directions of W)
 __device__ __forceinline__ void contact_flag_item(const Dev& d, const double* ck, double thr, const double* qnext,
                                                   const double* qt, int c) {
+  if (con_is_att(d, c)) {   // attachments: equality rows on all three axes at every step
+    cb_flag(d)[c] = 3.0;
+    return;
+  }
   const bool act = ck[c] > thr;
   const size_t v = 3 * (size_t)d.con_v[c];
   const double sx = qnext[v] - qt[v], sy = qnext[v + 1] - qt[v + 1];

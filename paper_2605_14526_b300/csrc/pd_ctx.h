@@ -88,7 +88,8 @@ struct pd_ctx {
   Dev d_adjoint{};           // host copy of the adjoint's record (d_dev[1])
   bool d_valid = false;
   // frictional contacts (pd_set_contacts)
-  std::vector<int> con_ground, con_box;
+  std::vector<int> con_ground, con_box, con_att;
+  std::vector<double> con_att_p0, con_att_tr;   // [n_attach][3] targets and their travel
   pd_contact_desc con{};
   double* con_ckpt = nullptr;   // [T][3K] converged multipliers per step
   int con_ckpt_cap = 0;

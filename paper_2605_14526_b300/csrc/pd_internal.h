@@ -208,12 +208,16 @@ struct Dev {
   double* red;      // [blocks][kRed]
   Ctrl* ctrl;
 
-  // frictional contacts (vertex-ground, vertex-box; Sec. 4.6): candidates
+  // frictional contacts (vertex-ground, vertex-box) and bilateral
+  // attachments (Sec. 4.6): candidates
   // sorted by elimination position, dense scalar Delassus W = (L_A^-1)_CC
   int n_con;               // 0: no contact
   const int* con_v;        // [K] vertex
   const int* con_pos;      // [K] elimination position (ascending)
-  const double* con_n;     // [K] normal sign: +1 ground (z >= z_g), -1 box (z <= z_box(t))
+  const double* con_n;     // [K] normal sign: +1 ground (z >= z_g), -1 box (z <= z_box(t)), +1 attachment
+  const int* con_att;      // [K] 1: bilateral attachment (free multipliers, target con_tgt), else 0; null: none
+  const double* con_tgt;   // [K][6] attachment target at the start of its motion and the motion's travel
+  int con_att_steps;       // steps over which the attachment targets move
   const double* con_W;     // [K][K]
   double con_L;            // largest eigenvalue of W (FISTA step 1/L)
   double con_mu, con_zg, con_zb0, con_travel, con_tol;

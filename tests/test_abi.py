@@ -77,6 +77,8 @@ int main(void) {
   printf("%zu %zu %zu %zu\\n", offsetof(pd_material, gravity), offsetof(pd_options, eps_step),
          offsetof(pd_stats, factor_nnz), offsetof(pd_stats, last_rho));
   printf("%zu %zu\\n", sizeof(pd_lbfgs_options), offsetof(pd_lbfgs_options, gtol));
+  printf("%zu %zu %zu\\n", sizeof(pd_contact_desc), offsetof(pd_contact_desc, attach_target),
+         offsetof(pd_contact_desc, attach_steps));
   return 0;
 }
 ''')
@@ -89,7 +91,9 @@ int main(void) {
                          ctypes.sizeof(binding.pd_profile_out)]
     assert sizes[5:9] == [binding.pd_material.gravity.offset, binding.pd_options.eps_step.offset,
                           binding.pd_stats.factor_nnz.offset, binding.pd_stats.last_rho.offset]
-    assert sizes[9:] == [ctypes.sizeof(binding.pd_lbfgs_options), binding.pd_lbfgs_options.gtol.offset]
+    assert sizes[9:11] == [ctypes.sizeof(binding.pd_lbfgs_options), binding.pd_lbfgs_options.gtol.offset]
+    assert sizes[11:] == [ctypes.sizeof(binding.pd_contact_desc), binding.pd_contact_desc.attach_target.offset,
+                          binding.pd_contact_desc.attach_steps.offset]
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
