@@ -61,7 +61,7 @@ def max_over_ranks(value, dist, device):
 # a full 200-step launch; profiles/bench_traffic_bar32x8x8.md), valid only
 # for the kernel sources it was taken with (their hash): reported as null
 # once any source under csrc/ has changed since.
-BAR_TRAFFIC = {"src": "e8cf123e60d2ffcd", "k_fwd_rollout": 17695232 + 2019840, "k_bwd_rollout": 31112192 + 8648960}
+BAR_TRAFFIC = {"src": "bf552fcb947edb34", "k_fwd_rollout": 17561600 + 2629376, "k_bwd_rollout": 30860800 + 8891136}
 
 
 def csrc_hash() -> str:
