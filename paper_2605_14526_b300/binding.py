@@ -528,21 +528,30 @@ def pd_warm_start(ctx, x_t, x_tm1, q0, stream=None):
     _check(ctx, lib().pd_warm_start(ctx, _ptr(x_t), _ptr(x_tm1), _ptr(q0), _stream(stream)))
 
 
-def pd_set_contacts(ctx, spec, tol=0.0, max_iters=0):
-    """Contacts of a workload (``inputs.ContactSpec``), or None to remove them."""
-    if spec is None:
-        _check(ctx, lib().pd_set_contacts(ctx, None))
-        return
+def contact_desc(spec, tol=0.0, max_iters=0):
+    """(pd_contact_desc, arrays) for an ``inputs.ContactSpec``: the
+    descriptor points into the returned arrays, which must outlive its use."""
     g = np.ascontiguousarray(spec.ground, dtype=np.int32)
     b = np.ascontiguousarray(spec.box, dtype=np.int32)
     a = np.ascontiguousarray(spec.attach, dtype=np.int32)
     p0 = np.ascontiguousarray(spec.attach_p0, dtype=np.float64).reshape(-1, 3)
     tr = np.ascontiguousarray(spec.attach_travel, dtype=np.float64).reshape(-1, 3)
+    if p0.shape[0] != a.size or tr.shape[0] != a.size:
+        raise ValueError("attach_p0 and attach_travel need one row per attached vertex")
     desc = pd_contact_desc(int(g.size), int(b.size), _ptr(g, np.int32) if g.size else None,
                            _ptr(b, np.int32) if b.size else None, float(spec.ground_z), float(spec.box_z0),
                            float(spec.box_travel), int(spec.box_steps), float(spec.mu), float(tol), int(max_iters),
                            int(a.size), _ptr(a, np.int32) if a.size else None, _ptr(p0) if a.size else None,
                            _ptr(tr) if a.size else None, int(spec.attach_steps))
+    return desc, (g, b, a, p0, tr)
+
+
+def pd_set_contacts(ctx, spec, tol=0.0, max_iters=0):
+    """Contacts of a workload (``inputs.ContactSpec``), or None to remove them."""
+    if spec is None:
+        _check(ctx, lib().pd_set_contacts(ctx, None))
+        return
+    desc, arrays = contact_desc(spec, tol, max_iters)
     _check(ctx, lib().pd_set_contacts(ctx, ctypes.byref(desc)))
 
 

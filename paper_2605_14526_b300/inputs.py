@@ -422,7 +422,10 @@ class ContactSpec:
 
     def attach_target(self, t: int) -> np.ndarray:
         """[Ka,3] attachment targets at the end of step t (0-based)."""
-        k = min(t + 1, self.attach_steps) / self.attach_steps
+        n = int(self.attach_steps)
+        if n < 1:   # as pd_set_contacts: the targets move over at least one step
+            raise ValueError("attach_steps must be >= 1")
+        k = min(t + 1, n) / n
         return np.asarray(self.attach_p0, dtype=np.float64) + k * np.asarray(self.attach_travel, dtype=np.float64)
 
 
