@@ -551,7 +551,7 @@ def pd_set_contacts(ctx, spec, tol=0.0, max_iters=0):
     if spec is None:
         _check(ctx, lib().pd_set_contacts(ctx, None))
         return
-    desc, arrays = contact_desc(spec, tol, max_iters)
+    desc, arrays = contact_desc(spec, tol, max_iters)   # arrays: the data desc points into, alive through the call
     _check(ctx, lib().pd_set_contacts(ctx, ctypes.byref(desc)))
 
 
