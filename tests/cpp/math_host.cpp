@@ -1,6 +1,6 @@
 // The library's per-element math (pd_math.cuh: rotation-variant 3x3 SVD,
-// Neo-Hookean stretch prox, 3x3 SPD inverse, the prox's filtered stretch
-// Jacobian) compiled as host C++ so that the CPU tests can check it against
+// Neo-Hookean stretch prox and the log-volume barrier's, 3x3 SPD inverse,
+// the prox's filtered stretch Jacobian) compiled as host C++ so that the CPU tests can check it against
 // numpy, scipy and the oracle. __device__ and __forceinline__ are defined
 // away; everything else is the header as the GPU build compiles it.
 #define __device__
@@ -28,6 +28,23 @@ void nh_prox_f32(int n, const float* sF, float mu, float lam, float k, float* s,
 }
 void nh_prox_f64(int n, const double* sF, double mu, double lam, double k, double* s, int* it) {
   prox_n<double>(n, sF, mu, lam, k, s, it);
+}
+// the log-volume barrier's prox divided by its weight: mu = r, lam = k = 1,
+// no deviatoric term (dv = 0), solved by the same Newton
+void barrier_prox_f32(int n, const float* sF, float r, float* s, int* it) {
+  NHMean<float> m{r, 1.0f, 1.0f};
+  m.dv = 0.0f;
+  for (int i = 0; i < n; ++i) it[i] = nh_prox<float>(sF + 3 * i, m, s + 3 * i);
+}
+void barrier_prox_f64(int n, const double* sF, double r, double* s, int* it) {
+  NHMean<double> m{r, 1.0, 1.0};
+  m.dv = 0.0;
+  for (int i = 0; i < n; ++i) it[i] = nh_prox<double>(sF + 3 * i, m, s + 3 * i);
+}
+void barrier_jacobian_f64(int n, const double* ss, double r, double tau, double* J) {
+  NHMean<double> m{r, 1.0, 1.0};
+  m.dv = 0.0;
+  for (int i = 0; i < n; ++i) filtered_jacobian<double>(ss + 3 * i, m, tau, J + 9 * i);
 }
 int spd_inv3_f64(const double* H, double* Hi) { return spd_inv3<double>(H, Hi) ? 1 : 0; }
 void filtered_jacobian_f64(int n, const double* ss, double mu, double lam, double k, double tau, double* J) {

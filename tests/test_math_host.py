@@ -208,3 +208,34 @@ def test_filtered_jacobian_against_oracle(lib, tau, kscale):
     blended = (1.0 - tau) * lam_h + tau * np.abs(lam_h)
     far = np.abs(blended).min(axis=1) > 0.1 * k
     assert (np.abs(J32 - Jo).max(axis=(1, 2))[far] / scale[far]).max() <= 1e-4
+
+
+@pytest.mark.parametrize("dtype,tol", [(np.float64, 1e-12), (np.float32, 3e-6)])
+def test_barrier_prox_against_oracle(lib, dtype, tol):
+    """The log-volume barrier's prox (eq. pd_log_volume divided by its weight
+    lambda_e: NHMean with mu = r, lam = k = 1 and no deviatoric term) against
+    the oracle's, on random, inverted, strongly compressed and strongly
+    stretched stretch triples, and its filtered Jacobian at tau = 1/2 and 1."""
+    rng = np.random.default_rng(12)
+    sF = np.exp(0.3 * rng.standard_normal((300, 3)))
+    sF[:30, 2] *= -0.4                           # inverted
+    sF[30:45] *= 0.2                             # strongly compressed
+    sF[45:60] *= 3.0                             # strongly stretched
+    sF = -np.sort(-np.abs(sF), axis=1) * np.where(np.arange(300)[:, None] < 30, [1.0, 1.0, -1.0], 1.0)
+    r = (1 - 2 * NU) / (2 * NU)
+    ref, _ = oprox.logvol_prox_sigma(sF, r)
+    s = np.ascontiguousarray(sF, dtype=dtype)
+    out = np.zeros_like(s)
+    it = np.zeros(300, np.int32)
+    if dtype == np.float32:
+        lib.barrier_prox_f32(ctypes.c_int(300), _p(s), ctypes.c_float(r), _p(out), _p(it))
+    else:
+        lib.barrier_prox_f64(ctypes.c_int(300), _p(s), ctypes.c_double(r), _p(out), _p(it))
+    assert np.all(out > 0)
+    assert np.abs(out - ref).max() <= tol * np.abs(ref).max()
+    for tau in (0.5, 1.0):
+        J = np.zeros((300, 9))
+        lib.barrier_jacobian_f64(ctypes.c_int(300), _p(np.ascontiguousarray(ref)), ctypes.c_double(r),
+                                 ctypes.c_double(tau), _p(J))
+        Jo, _, _ = oprox.logvol_sigma_jacobian(ref, r, tau)
+        assert np.abs(J.reshape(-1, 3, 3) - Jo).max() <= 1e-9 * np.abs(Jo).max()
